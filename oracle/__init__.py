@@ -1,0 +1,174 @@
+"""Python access to the plain CPU oracle (oracle/oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg.  The product package never imports it, and it
+never imports the product package.
+
+Every function here is argument marshalling around the C functions; the
+arithmetic, and its citations (Sec. 3.1 Eq. 1 and Fig. 7, Table 3, Sec. 4),
+live in oracle.c.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CODE_LEN = 1023
+CODE_MOD = CODE_LEN << 32
+
+_lib = None
+
+
+class OrcChan(C.Structure):
+    """Per-channel loop state (mirrors orc_chan in oracle.c)."""
+    _fields_ = [
+        ("theta", C.c_uint32),
+        ("w", C.c_int32),
+        ("phi", C.c_uint64),
+        ("r", C.c_uint64),
+        ("v", C.c_double),
+        ("f_carr", C.c_double),
+        ("f_code", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_ca_logic.argtypes = [C.c_int, P]
+        L.orc_ca_logic.restype = C.c_int
+        L.orc_ca_logic_delay.argtypes = [C.c_int, P]
+        L.orc_ca_logic_delay.restype = C.c_int
+        L.orc_ca_code.argtypes = [C.c_int, P]
+        L.orc_ca_code.restype = C.c_int
+        L.orc_sincos_table.argtypes = [P, P]
+        L.orc_sincos_table.restype = None
+        L.orc_correlate_block.argtypes = [P, C.c_uint32, C.POINTER(C.c_uint32), C.c_int32,
+                                          C.POINTER(C.c_uint64), C.c_uint64, P, C.c_uint32,
+                                          P, P]
+        L.orc_correlate_block.restype = None
+        L.orc_atan.argtypes = [C.c_double]
+        L.orc_atan.restype = C.c_double
+        L.orc_chan_init.argtypes = [C.POINTER(OrcChan), C.c_int32, C.c_uint64, C.c_uint64,
+                                    C.c_double]
+        L.orc_chan_init.restype = None
+        L.orc_track.argtypes = [C.POINTER(OrcChan), P, P, C.c_int, C.c_int, C.c_int,
+                                C.c_double, C.c_uint64, C.c_double, C.c_double]
+        L.orc_track.restype = None
+        L.orc_run_receiver.argtypes = [P, C.c_uint32, C.c_uint32, C.c_double, C.c_uint32, P,
+                                       C.c_uint32, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                                       C.c_double, C.c_double, C.POINTER(OrcChan), P]
+        L.orc_run_receiver.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def ca_logic(prn: int) -> np.ndarray:
+    """Logic-level (0/1) C/A chips of a PRN, phase-selector form."""
+    out = np.zeros(CODE_LEN, np.uint8)
+    if lib().orc_ca_logic(prn, _ptr(out)) != 0:
+        raise ValueError(f"bad PRN {prn}")
+    return out
+
+
+def ca_logic_delay(delay: int) -> np.ndarray:
+    """Logic-level C/A chips from the G2-delay form with the given delay."""
+    out = np.zeros(CODE_LEN, np.uint8)
+    lib().orc_ca_logic_delay(delay, _ptr(out))
+    return out
+
+
+def ca_code(prn: int) -> np.ndarray:
+    """Bipolar (+1/-1) C/A chips of a PRN."""
+    out = np.zeros(CODE_LEN, np.int8)
+    if lib().orc_ca_code(prn, _ptr(out)) != 0:
+        raise ValueError(f"bad PRN {prn}")
+    return out
+
+
+def sincos_table() -> tuple[np.ndarray, np.ndarray]:
+    c = np.zeros(64, np.int8)
+    s = np.zeros(64, np.int8)
+    lib().orc_sincos_table(_ptr(c), _ptr(s))
+    return c, s
+
+
+def correlate_block(iq: np.ndarray, theta0: int, w: int, phi0: int, r: int,
+                    tap_off, code: np.ndarray, acc: np.ndarray | None = None):
+    """Correlate one block; returns (acc[ntaps,2] int32, theta_end, phi_end)."""
+    iq = np.ascontiguousarray(iq, dtype=np.int8).reshape(-1)
+    assert iq.size % 2 == 0
+    taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(-1)
+    code = np.ascontiguousarray(code, dtype=np.int8)
+    assert code.size == CODE_LEN
+    if acc is None:
+        acc = np.zeros((taps.size, 2), np.int32)
+    else:
+        acc = np.ascontiguousarray(acc, dtype=np.int32).copy()
+    th = C.c_uint32(theta0 & 0xFFFFFFFF)
+    ph = C.c_uint64(phi0)
+    lib().orc_correlate_block(_ptr(iq), iq.size // 2, C.byref(th), int(np.int32(w)),
+                              C.byref(ph), r, _ptr(taps), taps.size, _ptr(code), _ptr(acc))
+    return acc, th.value, ph.value
+
+
+def atan(x: float) -> float:
+    return lib().orc_atan(float(x))
+
+
+def chan_init(w: int, phi: int, r: int, fs: float) -> OrcChan:
+    ch = OrcChan()
+    lib().orc_chan_init(C.byref(ch), int(w), int(phi), int(r), float(fs))
+    return ch
+
+
+def track(ch: OrcChan, acc: np.ndarray, tap_off, tap_e: int, tap_p: int, tap_l: int,
+          fs: float, n_accum: int, pll_bn: float, dll_bn: float) -> OrcChan:
+    """One loop-filter update in place on a copy of ch; returns the copy."""
+    out = OrcChan.from_buffer_copy(ch)
+    acc = np.ascontiguousarray(acc, dtype=np.int32).reshape(-1)
+    taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(-1)
+    lib().orc_track(C.byref(out), _ptr(acc), _ptr(taps), tap_e, tap_p, tap_l, float(fs),
+                    int(n_accum), float(pll_bn), float(dll_bn))
+    return out
+
+
+def run_receiver(iq: np.ndarray, n_blocks: int, N: int, fs: float, prn, tap_off,
+                 L: int, tap_e: int, tap_p: int, tap_l: int, pll_bn: float,
+                 dll_bn: float, chans):
+    """Closed-loop tracking of one receiver over n_blocks blocks of N samples.
+
+    chans: sequence of OrcChan (copied; not modified).  Returns (dumps, chans_out)
+    with dumps int32 [n_blocks // L, n_ch, n_taps, 2].
+    """
+    iq = np.ascontiguousarray(iq, dtype=np.int8).reshape(-1)
+    assert iq.size >= 2 * n_blocks * N
+    prn = np.ascontiguousarray(prn, dtype=np.uint8).reshape(-1)
+    n_ch = prn.size
+    taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(n_ch, -1)
+    n_taps = taps.shape[1]
+    arr = (OrcChan * n_ch)()
+    for i, ch in enumerate(chans):
+        C.memmove(C.byref(arr[i]), C.byref(ch), C.sizeof(OrcChan))
+    dumps = np.zeros((n_blocks // L, n_ch, n_taps, 2), np.int32)
+    rc = lib().orc_run_receiver(_ptr(iq), n_blocks, N, float(fs), n_ch, _ptr(prn), n_taps,
+                                _ptr(taps), L, tap_e, tap_p, tap_l, float(pll_bn),
+                                float(dll_bn), arr, _ptr(dumps))
+    if rc != 0:
+        raise ValueError("orc_run_receiver rejected its arguments")
+    return dumps, [OrcChan.from_buffer_copy(arr[i]) for i in range(n_ch)]

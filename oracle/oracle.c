@@ -1,0 +1,357 @@
+/*
+ * Plain CPU oracle for the GPS L1 C/A tracking-loop software correlator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library (the CUDA path
+ * behind include/rx.h) includes, links or calls this file; only the tests,
+ * the smoke check and the CPU-baseline leg of the benchmark do.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes, and where that is defined:
+ *   - the C/A ranging code of Sec. 3.1 (1023 chips, 1.023 Mcps, one code per
+ *     SV 1..32).  The paper gives only these properties; the generator
+ *     polynomials and the per-PRN G2 phase-selector taps are those of the
+ *     public GPS interface specification IS-GPS-200, Table 3-Ia.
+ *   - the carrier wipe-off and code-phase alignment of Sec. 3.1 (Fig. 7), in
+ *     a fixed-point form: a 32-bit carrier phase accumulator whose top 6 bits
+ *     index a 64-entry int8 cos/sin table; a 32.32 fixed-point code phase in
+ *     chips; int8 I/Q samples; int32 integrate-and-dump accumulators with
+ *     two's-complement wrap (Sec. 4: 1 ms integration).
+ *   - the tracking loops of Table 3: normalised early-minus-late envelope
+ *     DLL discriminator with carrier aiding, atan PLL discriminator, a
+ *     2nd-order PLL and a 1st-order DLL, followed by re-quantisation of the
+ *     NCO words.  Every floating-point step is a single correctly rounded
+ *     IEEE-754 binary64 operation, written one per statement, in a fixed
+ *     order; the file must be compiled with -ffp-contract=off.
+ *
+ * Everything is written the slow, literal way: each sample recomputes its
+ * carrier and code phase from the block start, every modulo is explicit.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_CODE_LEN 1023
+/* one code period in 32.32 fixed-point chips */
+#define ORC_CODE_MOD ((uint64_t)ORC_CODE_LEN << 32)
+
+/* ------------------------------------------------------------------------ */
+/* C/A code (Sec. 3.1; generator per IS-GPS-200 Sec. 3.3.2.3, Table 3-Ia)    */
+/* ------------------------------------------------------------------------ */
+
+/* G2 phase-selector tap pairs, PRN 1..32 (IS-GPS-200 Table 3-Ia). */
+static const int orc_g2_select[32][2] = {
+    {2, 6},  {3, 7},  {4, 8},  {5, 9},  {1, 9},  {2, 10}, {1, 8},  {2, 9},
+    {3, 10}, {2, 3},  {3, 4},  {5, 6},  {6, 7},  {7, 8},  {8, 9},  {9, 10},
+    {1, 4},  {2, 5},  {3, 6},  {4, 7},  {5, 8},  {6, 9},  {1, 3},  {4, 6},
+    {5, 7},  {6, 8},  {7, 9},  {8, 10}, {1, 6},  {2, 7},  {3, 8},  {4, 9}};
+
+/*
+ * Logic-level chips (0/1) of the C/A code of one PRN, by the two 10-stage
+ * shift registers: G1 = 1 + x^3 + x^10, G2 = 1 + x^2 + x^3 + x^6 + x^8 +
+ * x^9 + x^10, both preset to all ones; the chip is G1's last stage XOR the
+ * XOR of the two G2 stages selected for the PRN.
+ */
+int orc_ca_logic(int prn, uint8_t out[ORC_CODE_LEN]) {
+    if (prn < 1 || prn > 32) return -1;
+    int g1[11], g2[11];
+    for (int i = 1; i <= 10; ++i) { g1[i] = 1; g2[i] = 1; }
+    int a = orc_g2_select[prn - 1][0], b = orc_g2_select[prn - 1][1];
+    for (int n = 0; n < ORC_CODE_LEN; ++n) {
+        int g2i = g2[a] ^ g2[b];
+        out[n] = (uint8_t)(g1[10] ^ g2i);
+        int f1 = g1[3] ^ g1[10];
+        int f2 = g2[2] ^ g2[3] ^ g2[6] ^ g2[8] ^ g2[9] ^ g2[10];
+        for (int i = 10; i >= 2; --i) { g1[i] = g1[i - 1]; g2[i] = g2[i - 1]; }
+        g1[1] = f1;
+        g2[1] = f2;
+    }
+    return 0;
+}
+
+/*
+ * The same code by the equivalent "G2 delay" description: the chip at index n
+ * is G1(n) XOR G2(n - D) with D the PRN's code delay in chips.  The delays
+ * are passed in by the caller (tests take them from the specification's
+ * table) so that the two descriptions can be checked against each other.
+ */
+int orc_ca_logic_delay(int delay, uint8_t out[ORC_CODE_LEN]) {
+    uint8_t g1s[ORC_CODE_LEN], g2s[ORC_CODE_LEN];
+    int g1[11], g2[11];
+    for (int i = 1; i <= 10; ++i) { g1[i] = 1; g2[i] = 1; }
+    for (int n = 0; n < ORC_CODE_LEN; ++n) {
+        g1s[n] = (uint8_t)g1[10];
+        g2s[n] = (uint8_t)g2[10];
+        int f1 = g1[3] ^ g1[10];
+        int f2 = g2[2] ^ g2[3] ^ g2[6] ^ g2[8] ^ g2[9] ^ g2[10];
+        for (int i = 10; i >= 2; --i) { g1[i] = g1[i - 1]; g2[i] = g2[i - 1]; }
+        g1[1] = f1;
+        g2[1] = f2;
+    }
+    for (int n = 0; n < ORC_CODE_LEN; ++n) {
+        int m = ((n - delay) % ORC_CODE_LEN + ORC_CODE_LEN) % ORC_CODE_LEN;
+        out[n] = (uint8_t)(g1s[n] ^ g2s[m]);
+    }
+    return 0;
+}
+
+/* Bipolar chips: logic 0 -> +1, logic 1 -> -1. */
+int orc_ca_code(int prn, int8_t out[ORC_CODE_LEN]) {
+    uint8_t logic[ORC_CODE_LEN];
+    if (orc_ca_logic(prn, logic) != 0) return -1;
+    for (int n = 0; n < ORC_CODE_LEN; ++n) out[n] = logic[n] ? -1 : 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Carrier NCO table (Sec. 3.1 carrier wipe-off)                             */
+/* ------------------------------------------------------------------------ */
+
+/* Entry k holds round(127 cos(2 pi k / 64)), round(127 sin(2 pi k / 64)):
+ * phase taken at the start of the bin, rounding half away from zero. */
+void orc_sincos_table(int8_t cos_tab[64], int8_t sin_tab[64]) {
+    for (int k = 0; k < 64; ++k) {
+        double ang = 2.0 * M_PI * (double)k / 64.0;
+        cos_tab[k] = (int8_t)lround(127.0 * cos(ang));
+        sin_tab[k] = (int8_t)lround(127.0 * sin(ang));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Correlator: carrier wipe-off, code wipe-off at each tap, integrate        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One block of nsamp complex samples for one channel.  For sample n:
+ *   theta_n = theta0 + n*w                     (mod 2^32)
+ *   (c, s)  = TAB[theta_n >> 26]
+ *   I' = I c + Q s,  Q' = Q c - I s            (multiply by exp(-j theta))
+ *   phi_n   = phi0 + n*r                       (mod 1023 * 2^32)
+ *   chip_k  = ((phi_n + off_k) mod 1023*2^32) >> 32
+ *   A_I[k] += code[chip_k] I',  A_Q[k] += code[chip_k] Q'   (mod 2^32)
+ * and at the end theta0 += nsamp*w, phi0 = (phi0 + nsamp*r) mod 1023*2^32.
+ * acc is [ntaps][2] = {A_I, A_Q}, accumulated into (not cleared).
+ */
+void orc_correlate_block(const int8_t *iq, uint32_t nsamp, uint32_t *theta0,
+                         int32_t w, uint64_t *phi0, uint64_t r,
+                         const int64_t *tap_off, uint32_t ntaps,
+                         const int8_t code[ORC_CODE_LEN], int32_t *acc) {
+    int8_t ctab[64], stab[64];
+    orc_sincos_table(ctab, stab);
+    uint32_t *uacc = (uint32_t *)acc;
+    for (uint32_t n = 0; n < nsamp; ++n) {
+        uint32_t theta = *theta0 + n * (uint32_t)w;
+        uint32_t k = theta >> 26;
+        int32_t c = ctab[k], s = stab[k];
+        int32_t I = iq[2 * (size_t)n], Q = iq[2 * (size_t)n + 1];
+        int32_t Ip = I * c + Q * s;
+        int32_t Qp = Q * c - I * s;
+        unsigned __int128 ph = ((unsigned __int128)*phi0 +
+                                (unsigned __int128)n * r) % ORC_CODE_MOD;
+        for (uint32_t t = 0; t < ntaps; ++t) {
+            __int128 x = ((__int128)ph + tap_off[t]) % (__int128)ORC_CODE_MOD;
+            if (x < 0) x += ORC_CODE_MOD;
+            uint32_t chip = (uint32_t)((uint64_t)x >> 32);
+            int32_t g = code[chip];
+            uacc[2 * t] += (uint32_t)(g * Ip);
+            uacc[2 * t + 1] += (uint32_t)(g * Qp);
+        }
+    }
+    *theta0 = *theta0 + nsamp * (uint32_t)w;
+    *phi0 = (uint64_t)(((unsigned __int128)*phi0 +
+                        (unsigned __int128)nsamp * r) % ORC_CODE_MOD);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Arctangent (PLL discriminator, Table 3)                                   */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_PI_2 1.5707963267948966
+#define ORC_PI_6 0.5235987755982989
+#define ORC_TAN_PI_12 0.2679491924311227
+#define ORC_SQRT3 1.7320508075688772
+#define ORC_SQRT2 1.4142135623730951
+#define ORC_TWO_PI 6.283185307179586
+
+/*
+ * atan(x) by classical argument reduction and the Gregory series:
+ *   |x| > 1:              atan(x) = pi/2 - atan(1/x)
+ *   a > tan(pi/12):       atan(a) = pi/6 + atan((sqrt3 a - 1)/(sqrt3 + a))
+ *   |a| <= tan(pi/12):    atan(a) = sum_{k=0}^{12} (-1)^k a^(2k+1)/(2k+1),
+ *                          evaluated by Horner's rule in a^2.
+ * The truncation error is below a^27/27 < 2e-17.
+ */
+double orc_atan(double x) {
+    int neg = x < 0.0;
+    double a = neg ? -x : x;
+    int inv = a > 1.0;
+    if (inv) a = 1.0 / a;
+    int shift = a > ORC_TAN_PI_12;
+    if (shift) {
+        double num = ORC_SQRT3 * a;
+        num = num - 1.0;
+        double den = ORC_SQRT3 + a;
+        a = num / den;
+    }
+    double t = a * a;
+    double p = 1.0 / 25.0;
+    for (int k = 11; k >= 0; --k) {
+        double ck = ((k & 1) ? -1.0 : 1.0) / (double)(2 * k + 1);
+        p = p * t;
+        p = p + ck;
+    }
+    double y = a * p;
+    if (shift) y = ORC_PI_6 + y;
+    if (inv) y = ORC_PI_2 - y;
+    return neg ? -y : y;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tracking loops (Table 3) and NCO re-quantisation                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint32_t theta;   /* carrier phase, 2^-32 cycles */
+    int32_t w;        /* carrier phase increment per sample */
+    uint64_t phi;     /* code phase, 32.32 chips, in [0, 1023*2^32) */
+    uint64_t r;       /* code phase increment per sample, 32.32 chips */
+    double v;         /* PLL integrator, Hz */
+    double f_carr;    /* last carrier frequency from the PLL, Hz */
+    double f_code;    /* last code rate from the DLL, chips/s */
+} orc_chan;
+
+/* Initial loop state from the NCO words: the PLL integrator starts at the
+ * carrier frequency the word represents. */
+void orc_chan_init(orc_chan *ch, int32_t w, uint64_t phi, uint64_t r, double fs) {
+    ch->theta = 0;
+    ch->w = w;
+    ch->phi = phi % ORC_CODE_MOD;
+    ch->r = r;
+    double f = (double)w * fs;
+    ch->v = f / 4294967296.0;
+    ch->f_carr = ch->v;
+    double fc = (double)r * fs;
+    ch->f_code = fc / 4294967296.0;
+}
+
+/*
+ * One loop update at an integration boundary.  acc = [ntaps][2] dumped sums,
+ * n_accum = samples integrated.  Discriminators (Table 3):
+ *   PLL: e_p = atan(Q_P / I_P) / (2 pi)           cycles (two-quadrant)
+ *   DLL: e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|) chips, d = E-L spacing
+ * Filters, with T = n_accum / fs and w0 = Bn_pll / 0.53:
+ *   v      = v + (w0^2 T) e_p
+ *   f_carr = v + (sqrt2 w0) e_p
+ *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c   (carrier aided)
+ * Re-quantisation, round half to even:
+ *   w = rn(f_carr / fs * 2^32) (wrapped to int32), r = rn(f_code / fs * 2^32)
+ */
+void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
+               int tap_e, int tap_p, int tap_l, double fs, uint64_t n_accum,
+               double pll_bn, double dll_bn) {
+    double T = (double)n_accum / fs;
+
+    double ip = (double)acc[2 * tap_p], qp = (double)acc[2 * tap_p + 1];
+    double e_pll;
+    if (ip != 0.0) {
+        double q = qp / ip;
+        e_pll = orc_atan(q) / ORC_TWO_PI;
+    } else {
+        e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+    }
+    double w0 = pll_bn / 0.53;
+    double k1 = w0 * w0;
+    k1 = k1 * T;
+    double k2 = ORC_SQRT2 * w0;
+    double dv = k1 * e_pll;
+    ch->v = ch->v + dv;
+    double df = k2 * e_pll;
+    double f_carr = ch->v + df;
+
+    double ie = (double)acc[2 * tap_e], qe = (double)acc[2 * tap_e + 1];
+    double il = (double)acc[2 * tap_l], ql = (double)acc[2 * tap_l + 1];
+    double ie2 = ie * ie, qe2 = qe * qe, il2 = il * il, ql2 = ql * ql;
+    double mag_e = sqrt(ie2 + qe2);
+    double mag_l = sqrt(il2 + ql2);
+    double den = mag_e + mag_l;
+    double d_el = (double)(tap_off[tap_e] - tap_off[tap_l]) / 4294967296.0;
+    double kd = 1.0 - d_el / 2.0;
+    double e_dll = 0.0;
+    if (den > 0.0) {
+        double num = mag_e - mag_l;
+        num = kd * num;
+        e_dll = num / den;
+    }
+    double aid = f_carr / 1575.42e6;
+    aid = 1.0 + aid;
+    double f_code = 1.023e6 * aid;
+    double kdll = 4.0 * dll_bn;
+    double corr = kdll * e_dll;
+    f_code = f_code + corr;
+
+    double xw = f_carr / fs;
+    xw = xw * 4294967296.0;
+    double xr = f_code / fs;
+    xr = xr * 4294967296.0;
+    /* words: carrier wraps modulo 2^32, code rate clamped to [0, 2^40] */
+    if (xw > 9.0e18) xw = 9.0e18;
+    if (xw < -9.0e18) xw = -9.0e18;
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    ch->w = (int32_t)(uint32_t)(uint64_t)(int64_t)nearbyint(xw);
+    ch->r = (uint64_t)nearbyint(xr);
+    ch->f_carr = f_carr;
+    ch->f_code = f_code;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A whole receiver: blocks in order, channels independent (Sec. 3.5)       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * iq: n_blocks * N complex int8 samples, interleaved I,Q.
+ * tap_off: [n_ch][n_taps] 32.32 chip offsets.  Every L blocks each channel
+ * dumps its accumulators to dumps[(b+1)/L - 1][ch][tap][2], runs orc_track and
+ * clears them.  Returns 0, or -1 on bad arguments.
+ */
+int orc_run_receiver(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
+                     uint32_t n_ch, const uint8_t *prn, uint32_t n_taps,
+                     const int64_t *tap_off, uint32_t L, int tap_e, int tap_p,
+                     int tap_l, double pll_bn, double dll_bn, orc_chan *ch,
+                     int32_t *dumps) {
+    if (L == 0 || n_taps == 0) return -1;
+    if (tap_e < 0 || tap_p < 0 || tap_l < 0 || (uint32_t)tap_e >= n_taps ||
+        (uint32_t)tap_p >= n_taps || (uint32_t)tap_l >= n_taps)
+        return -1;
+    int8_t *codes = (int8_t *)malloc((size_t)n_ch * ORC_CODE_LEN);
+    int32_t *acc = (int32_t *)calloc((size_t)n_ch * n_taps * 2, sizeof(int32_t));
+    if (!codes || !acc) { free(codes); free(acc); return -1; }
+    for (uint32_t c = 0; c < n_ch; ++c) {
+        if (orc_ca_code(prn[c], codes + (size_t)c * ORC_CODE_LEN) != 0) {
+            free(codes); free(acc); return -1;
+        }
+    }
+    for (uint32_t b = 0; b < n_blocks; ++b) {
+        const int8_t *blk = iq + (size_t)b * N * 2;
+        for (uint32_t c = 0; c < n_ch; ++c) {
+            orc_correlate_block(blk, N, &ch[c].theta, ch[c].w, &ch[c].phi, ch[c].r,
+                                tap_off + (size_t)c * n_taps, n_taps,
+                                codes + (size_t)c * ORC_CODE_LEN,
+                                acc + (size_t)c * n_taps * 2);
+        }
+        if ((b + 1) % L == 0) {
+            size_t e = (b + 1) / L - 1;
+            for (uint32_t c = 0; c < n_ch; ++c) {
+                int32_t *a = acc + (size_t)c * n_taps * 2;
+                memcpy(dumps + ((e * n_ch + c) * n_taps) * 2, a,
+                       sizeof(int32_t) * n_taps * 2);
+                orc_track(&ch[c], a, tap_off + (size_t)c * n_taps, tap_e, tap_p,
+                          tap_l, fs, (uint64_t)L * N, pll_bn, dll_bn);
+                memset(a, 0, sizeof(int32_t) * n_taps * 2);
+            }
+        }
+    }
+    free(codes);
+    free(acc);
+    return 0;
+}
