@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the batched GPS L1 C/A tracking correlator on one GB300.
+
+Workload (one step): 64 receivers x 12 channels x 5 taps (VE/E/P/L/VL at
++-0.25 and +-0.5 chip), int8 I/Q at 16.368 MHz, 1 s of signal per receiver
+(1000 blocks of 1 ms), every channel's PLL/DLL closed at every 1 ms epoch.
+One step = one persistent kernel launch (a CUDA graph replay) that tracks all
+64 receivers over the whole second from the same starting state.  Signals are
+seeded synthetic data (C/N0 35-50 dB-Hz, Doppler +-5 kHz, 50 bit/s data,
+AWGN sigma 20) generated on the device before timing; the 2.1 GB input is
+larger than L2, so no flush is needed between steps.
+
+Metric: Msample*channel/s correlated (whole job over all ranks).  The JSON line
+also carries the roofline of the dominant kernel, the oracle CPU baseline, the
+end-to-end number through the C ABI with host buffers, the plain
+one-receiver-per-launch GPU form, real-time channel counts and clocks.
+
+--impl reference times the CPU oracle (the plain reference implementation of
+the same computation) on the host cores, on bounded samples of this workload.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
+METRIC = "Msample*channel/s correlated"
+INT32_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x one 32-lane warp instruction per clock
+
+
+def ops_per_sample_channel(n_taps: int) -> int:
+    """Algorithmic INT32 ops per sample*channel of the direct form: carrier phase add,
+    table index, 4 mix multiply/adds, 64-bit code phase add (2), and per tap a code sign
+    and two signed accumulates."""
+    return 8 + 3 * n_taps
+
+
+def layout(receivers):
+    offs, pos = [], 0
+    for r in receivers:
+        offs.append(pos)
+        pos += ((2 * r.n_samples + 15) // 16) * 16
+    return np.array(offs, np.uint64), pos
+
+
+def workload(rank: int):
+    from paper_1907_00463_gb300 import synth
+    return [synth.uniform_receiver(rank * N_RX + i, n_blocks=N_BLOCKS) for i in range(N_RX)]
+
+
+def sample_channels(receivers, n_blocks=None) -> int:
+    return sum(r.block_samples * len(r.channels) * (n_blocks or r.n_blocks) for r in receivers)
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) leg
+# ----------------------------------------------------------------------------
+
+def oracle_sample(receivers, host_iq, n_blocks: int, threads: int):
+    """Run the oracle over the first n_blocks of each receiver, one thread per receiver
+    (the C oracle releases the GIL).  Returns seconds."""
+    import oracle
+
+    def one(i):
+        r = receivers[i]
+        from paper_1907_00463_gb300 import synth
+        prn, w, phi, rate, taps = synth.channel_arrays(r)
+        chans = [oracle.chan_init(int(w[c]), int(phi[c]), int(rate[c]), r.fs)
+                 for c in range(len(prn))]
+        oracle.run_receiver(host_iq[i], n_blocks, r.block_samples, r.fs, prn, taps,
+                            r.integ_blocks, r.tap_early, r.tap_prompt, r.tap_late, r.pll_bn,
+                            r.dll_bn, chans)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(len(receivers))))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(receivers, get_iq, target_s: float = 15.0) -> dict:
+    """Time the oracle on a bounded sample sized for about target_s of wall time."""
+    cores = os.cpu_count() or 1
+    nrx = min(len(receivers), cores)
+    sub = receivers[:nrx]
+    iq1 = [get_iq(0, 2)]
+    t1 = oracle_sample(sub[:1], iq1, 2, 1) / 2            # seconds per receiver-block
+    blocks = int(max(2, min(N_BLOCKS, target_s / max(t1, 1e-6))))
+    iqs = [get_iq(i, blocks) for i in range(nrx)]
+    dt = oracle_sample(sub, iqs, blocks, nrx)
+    sc = sample_channels(sub, blocks)
+    return {"value": sc / dt / 1e6, "unit": "Msample*channel/s", "cores": nrx, "kind": "oracle",
+            "sample": f"{nrx} receivers x {blocks} blocks (of {N_RX} x {N_BLOCKS}), "
+                      f"one oracle thread per receiver, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle alone
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import build as obuild
+    from paper_1907_00463_gb300 import synth
+    obuild.build()
+    import torch
+    receivers = workload(0)
+    cores = os.cpu_count() or 1
+    nrx = min(N_RX, cores)
+    sub = receivers[:nrx]
+    # size one step for about 8 s of oracle work on this host
+    probe = synth.generate_iq(sub[0], 2 * sub[0].block_samples).numpy()
+    t1 = oracle_sample(sub[:1], [probe], 2, 1) / 2
+    blocks = int(max(2, min(N_BLOCKS, 8.0 / max(t1, 1e-6))))
+    iqs = [synth.generate_iq(r, blocks * r.block_samples).numpy() for r in sub]
+    for _ in range(args.warmup):
+        oracle_sample(sub, iqs, blocks, nrx)
+    times = [oracle_sample(sub, iqs, blocks, nrx) for _ in range(args.steps)]
+    sc = sample_channels(sub, blocks)
+    ms = 1000 * statistics.mean(times)
+    value = sc / (ms / 1000) / 1e6
+    del torch
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Msample*channel/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "64 receivers x 12 channels x 5 taps, int8 I/Q at 16.368 MHz, "
+                               "1 s, closed loop at 1 ms",
+                   "sample_per_step": f"{nrx} receivers x {blocks} blocks"},
+        "cpu_baseline": {"value": value, "unit": "Msample*channel/s", "cores": nrx,
+                         "kind": "oracle",
+                         "sample": f"{nrx} receivers x {blocks} blocks per step"},
+        "e2e": {"value": value, "unit": "Msample*channel/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def plain_form(rx, receivers, buf, offs, dev, stream, n_rx=4, n_blocks=100) -> dict:
+    """The plain GPU form: one rx_correlate + one rx_track_epoch launch per receiver per block."""
+    import torch
+    handles = []
+    for r in receivers[:n_rx]:
+        h = rx.rx_create(r.fs, r.block_samples, len(r.channels), r.n_taps, r.pll_bn, r.dll_bn,
+                         r.tap_early, r.tap_prompt, r.tap_late, device=dev, stream=stream)
+        rx.rx_set_channels(h, *__import__("paper_1907_00463_gb300.synth",
+                                          fromlist=["x"]).channel_arrays(r))
+        handles.append(h)
+    N = receivers[0].block_samples
+    views = [buf[int(o):int(o) + 2 * N * n_blocks].view(-1, 2) for o in offs[:n_rx]]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(n_blocks):
+        for h, v in zip(handles, views):
+            rx.rx_correlate(h, v[b * N:(b + 1) * N], N)
+            rx.rx_track_epoch(h)
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    for h in handles:
+        rx.rx_destroy(h)
+    sc = sample_channels(receivers[:n_rx], n_blocks)
+    return {"value": sc / dt / 1e6, "unit": "Msample*channel/s",
+            "sample": f"{n_rx} receivers x {n_blocks} blocks, 2 launches per receiver-block",
+            "launches": 2 * n_rx * n_blocks}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1907_00463_gb300 import rx, synth
+
+    receivers = workload(rank)
+    offs, total = layout(receivers)
+    buf = torch.zeros(total, dtype=torch.int8, device=dev)
+    for r, o in zip(receivers, offs):
+        iq = synth.generate_iq(r, device=dev)
+        buf[int(o):int(o) + iq.numel()] = iq.view(-1)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream(dev)
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], N_BLOCKS, device=local,
+                           stream=stream)
+    for i, r in enumerate(receivers):
+        rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+    if args.tiles:
+        rx.rx_batch_set_tiles(b, *[int(x) for x in args.tiles.split(",")])
+
+    def step(src=buf):
+        rx.rx_batch_run(b, src, offs, N_BLOCKS, rx.RX_RUN_RESTART)
+
+    for _ in range(args.warmup):
+        step()
+    rx.rx_batch_sync(b)
+    tiles = rx.rx_batch_get_tiles(b)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    rx.rx_batch_sync(b)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = args.steps * rx.rx_batch_last_launches(b)
+    total_ms = t_start.elapsed_time(t_end)
+    per_launch = [e0.elapsed_time(e1) for e0, e1 in ev]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    sc = sample_channels(receivers)
+    value = world * sc / (ms / 1000) / 1e6
+
+    # roofline of the persistent kernel (all of a step's device time)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_tops = props.multi_processor_count * INT32_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    launch_ms = statistics.mean(per_launch)
+    alg_ops = sc * ops_per_sample_channel(5)
+    achieved = alg_ops / (launch_ms / 1000) / 1e12
+    in_bytes = sum(2 * r.n_samples for r in receivers)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # end to end through the C ABI with host buffers: H2D of every input byte and D2H of
+    # every dump inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.empty(total, dtype=torch.int8, pin_memory=True)
+        hbuf.copy_(buf)
+        dumps = [np.zeros((N_BLOCKS, len(r.channels), r.n_taps, 2), np.int32) for r in receivers]
+        d2h = sum(d.nbytes for d in dumps)
+        rx.rx_batch_run(b, hbuf, offs, N_BLOCKS, rx.RX_RUN_RESTART)     # warm the staging path
+        rx.rx_batch_sync(b)
+        n_e2e = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            rx.rx_batch_run(b, hbuf, offs, N_BLOCKS, rx.RX_RUN_RESTART)
+            for i, r in enumerate(receivers):
+                dumps[i] = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, N_BLOCKS)
+        dt = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * sc / dt / 1e6, "unit": "Msample*channel/s",
+               "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": dt * 1000}
+        del hbuf
+
+    plain = None
+    cpu = None
+    if rank == 0 and world == 1:
+        if not args.no_plain:
+            plain = plain_form(rx, receivers, buf, offs, local, stream)
+        if not args.no_cpu_baseline:
+            host_cache = {}
+
+            def get_iq(i, blocks):
+                r = receivers[i]
+                n = blocks * r.block_samples
+                o = int(offs[i])
+                return buf[o:o + 2 * n].cpu().numpy()
+            cpu = cpu_baseline(receivers, get_iq)
+            del host_cache
+    rx.rx_batch_destroy(b)
+
+    rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
+    line = {
+        "metric": METRIC, "value": value, "unit": "Msample*channel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "64 receivers x 12 channels x 5 taps (VE/E/P/L/VL), int8 I/Q at "
+                               "16.368 MHz, 1 s per receiver, PLL 15 Hz / DLL 1 Hz closed every "
+                               "1 ms; one persistent launch per step",
+                   "receivers_per_gpu": N_RX, "blocks": N_BLOCKS, "channels": 12, "taps": 5,
+                   "fs_hz": FS, "tiles": {"channels_per_item": tiles[0], "threads": tiles[1],
+                                          "ctas_per_sm": tiles[2]},
+                   "l2": "inputs (2.1 GB per GPU) larger than L2; no flush",
+                   "parallelism": f"receivers sharded over {world} GPU(s), no collective"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "model": "INT32 ops = sample*channel x (8 + 3T), T = 5; peak = SMs x 128 "
+                              "lanes x max SM clock (derived, not measured)",
+                     "launch_ms": launch_ms,
+                     "hbm_gbs": in_bytes / (launch_ms / 1000) / 1e9,
+                     "hbm_frac_of_measured": in_bytes / (launch_ms / 1000) / 1e9 / hbm_peak},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "realtime_channels": {"per_gpu_at_16.368MHz": rt_channels / world,
+                              "paper_definition": "1 ms / time per channel-epoch"},
+        "plain_form": plain,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--tiles", default="", help="channels_per_item,threads,ctas_per_sm")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,264 @@
+/*
+ * rx.h -- C ABI of librx: the GPS L1 C/A tracking-loop software correlator
+ * (carrier NCO, code NCO with early/prompt/late taps, integrate-and-dump, and
+ * the PLL/DLL that closes the loop) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method is the tracking stage of the receiver in Schmidt & Akopian,
+ * "Exploiting Acceleration Features of LabVIEW platform for Real-Time GNSS
+ * Software Receiver Optimization" (arXiv:1907.00463):
+ *   - signal and code: Sec. 3.1, Eq. (1) (C/A branch), 1023-chip PRN codes at
+ *     1.023 Mcps, 50 bit/s navigation data;
+ *   - carrier wipe-off and code-phase alignment: Sec. 3.1 and Fig. 7;
+ *   - loop configuration: Table 3 (normalised early-minus-late envelope DLL
+ *     with carrier aiding, atan PLL discriminator, 2nd-order PLL);
+ *   - 1 ms integrate-and-dump epochs on interleaved int8 I/Q: Sec. 4;
+ *   - one tracking call per channel, channels independent: Sec. 3.4-3.5
+ *     (do_tracking(raw block, size, system parameters, channel array by
+ *     reference)).
+ *
+ * Fixed-point definition (the paper names a "SIMD software correlator" but not
+ * its number formats; this library fixes them so results are reproducible):
+ *   samples      int8 I/Q, interleaved [I0, Q0, I1, Q1, ...]
+ *   carrier NCO  theta (uint32, 2^-32 cycles), word w (int32) added per sample;
+ *                table index theta >> 26 into 64 entries
+ *                (round(127 cos 2 pi k/64), round(127 sin 2 pi k/64));
+ *                mixing multiplies by exp(-j theta): I' = I c + Q s,
+ *                Q' = Q c - I s
+ *   code NCO     phi (uint64, 32.32 chips, in [0, 1023 * 2^32)), word r
+ *                (uint64, 32.32 chips per sample, must be < 2^32);
+ *                tap k reads chip ((phi + off_k) mod 1023*2^32) >> 32,
+ *                off_k signed 32.32 chips with |off_k| <= 64 chips;
+ *                a positive offset is an early tap
+ *   code value   logic 0 -> +1, logic 1 -> -1 (IS-GPS-200 C/A codes)
+ *   accumulate   A_I[k] += g I', A_Q[k] += g Q', int32 with wrap mod 2^32
+ * Loop filters (FP64, every operation correctly rounded, fixed order), at each
+ * integration boundary of T seconds:
+ *   e_p = atan(Q_P / I_P) / (2 pi)                         (quarter cycle if I_P = 0)
+ *   w0 = Bn_pll / 0.53;  v += (w0^2 T) e_p;  f_carr = v + (sqrt2 w0) e_p
+ *   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|), d = E-L spacing in chips
+ *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c
+ *   w = rn(f_carr / fs * 2^32) mod 2^32,  r = rn(f_code / fs * 2^32)
+ * rn rounds half to even.
+ *
+ * Conventions for every function:
+ *   - Returns rx_status; nothing else signals errors (no exceptions, no exit).
+ *     rx_last_error / rx_batch_last_error give a message for the last failure.
+ *   - The caller owns every buffer it passes.  Input buffers may be reused as
+ *     soon as the call returns, unless the function says it is stream-ordered.
+ *   - The library owns all device state; work is ordered on the handle's CUDA
+ *     stream (cudaStream_t passed as void*; NULL = legacy default stream).
+ *   - There is no CPU path: without a usable CUDA device rx_create and
+ *     rx_batch_create return RX_ECUDA.
+ *   - Handles are not thread-safe; use one host thread per handle.
+ */
+#ifndef RX_H
+#define RX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RX_OK = 0,
+    RX_EINVAL = 1,    /* bad argument: size, range, alignment, null pointer */
+    RX_ENOMEM = 2,    /* device or pinned host allocation failed */
+    RX_EBUDGET = 3,   /* admission refused: device-memory budget exhausted */
+    RX_ECUDA = 4,     /* CUDA runtime error, or no usable device */
+    RX_ETIMEOUT = 5,  /* a bounded device-side wait gave up (see rx_last_error) */
+    RX_ESTATE = 6,    /* call not valid in the handle's current state */
+    RX_EAGAIN = 7     /* nothing ready yet; try again */
+} rx_status;
+
+#define RX_CODE_LEN 1023
+#define RX_MAX_TAPS 128          /* taps per channel */
+#define RX_MAX_TAP_CHIPS 64      /* |tap offset| limit, chips */
+#define RX_MAX_CHANNELS 1024     /* channels per receiver handle */
+#define RX_MAX_BLOCK_SAMPLES (1u << 20)  /* samples per rx_correlate call */
+
+/* Human-readable name of a status code (static string). */
+const char *rx_status_string(rx_status s);
+
+/* ------------------------------------------------------------------------ */
+/* Per-channel state, for read-back and checkpoint / resume                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint32_t carrier_phase;      /* theta at the next sample, 2^-32 cycles */
+    int32_t carrier_word;        /* w */
+    uint64_t code_phase;         /* phi at the next sample, 32.32 chips, < 1023*2^32 */
+    uint64_t code_rate;          /* r, 32.32 chips per sample */
+    double pll_integrator_hz;    /* v, the PLL's frequency integrator */
+    double carrier_hz;           /* last PLL output f_carr */
+    double code_hz;              /* last DLL output f_code */
+    uint32_t prn;                /* 1..32 */
+    uint32_t epochs;             /* integration boundaries passed (dumps) */
+} rx_channel_state;
+
+/* ------------------------------------------------------------------------ */
+/* Plain form: one receiver, one call per block (Sec. 3.4 do_tracking)      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double fs_hz;                /* sample rate, Hz; > 1.1e6 so that r < 2^32 */
+    uint32_t max_block_samples;  /* largest nsamp any rx_correlate call will pass */
+    uint32_t max_channels;       /* 1..RX_MAX_CHANNELS */
+    uint32_t max_taps;           /* 1..RX_MAX_TAPS */
+    double pll_bn_hz;            /* PLL noise bandwidth (2nd order) */
+    double dll_bn_hz;            /* DLL noise bandwidth (1st order, carrier aided) */
+    int32_t tap_early;           /* tap index used as E by the DLL discriminator */
+    int32_t tap_prompt;          /* tap index used as P by the PLL discriminator */
+    int32_t tap_late;            /* tap index used as L by the DLL discriminator */
+    int32_t device;              /* CUDA device ordinal */
+    void *cuda_stream;           /* cudaStream_t for all work of this handle, or NULL */
+} rx_config;
+
+typedef struct rx_handle_s *rx_handle;
+
+/* Allocate a receiver on cfg->device: per-channel NCO, loop and accumulator
+ * state in device memory, a device staging buffer of max_block_samples, and
+ * the C/A and carrier tables.  *out receives the handle.  RX_EINVAL on a bad
+ * config, RX_ECUDA without a device, RX_ENOMEM if allocation fails. */
+rx_status rx_create(const rx_config *cfg, rx_handle *out);
+
+/* Synchronise the handle's stream and free everything it owns.  NULL is OK. */
+rx_status rx_destroy(rx_handle h);
+
+/* Start (or restart) tracking n channels with ntaps taps each.  Host arrays:
+ * prn[n] (1..32), carrier_word[n], code_phase_word[n] (reduced modulo
+ * 1023*2^32), code_rate_word[n] (< 2^32), tap_offsets[n*ntaps] (row-major,
+ * 32.32 chips, |x| <= RX_MAX_TAP_CHIPS chips).  Carrier phases start at 0,
+ * accumulators are cleared, the PLL integrator starts at w*fs/2^32 Hz.
+ * The E/P/L indices of the config must be < ntaps.  Copied before return. */
+rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn,
+                          const int32_t *carrier_word,
+                          const uint64_t *code_phase_word,
+                          const uint64_t *code_rate_word,
+                          const int64_t *tap_offsets, uint32_t ntaps);
+
+/* Correlate the next nsamp samples (1..max_block_samples) for every channel
+ * and add them to the accumulators; the NCO phases advance by nsamp samples.
+ * iq holds 2*nsamp int8 values.  A device pointer (cudaMalloc'd or managed,
+ * 2-byte aligned; 16-byte alignment is fastest) is read in stream order, so it
+ * must stay valid until the stream reaches this call; any other pointer is
+ * treated as host memory and copied to the device before return (pinned
+ * memory is faster). */
+rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp);
+
+/* Integration boundary: run the discriminators and loop filters on the
+ * accumulators (T = samples correlated since the last boundary / fs), load
+ * the re-quantised carrier and code words, clear the accumulators.  Stream
+ * ordered.  RX_ESTATE if nothing was correlated since the last boundary. */
+rx_status rx_track_epoch(rx_handle h);
+
+/* Copy the current accumulators, int32 [n][ntaps][2] = {A_I, A_Q}, to host
+ * memory out (cap elements available), and, if n_accum is not NULL, the
+ * number of samples integrated into them since the last boundary.
+ * Synchronises the stream.  Read it before rx_track_epoch to obtain an
+ * epoch's dump. */
+rx_status rx_read_accumulators(rx_handle h, int32_t *out, uint32_t cap,
+                               uint64_t *n_accum);
+
+/* Replace the accumulators and their integrated-sample count (checkpoint /
+ * resume).  in has n*ntaps*2 values. */
+rx_status rx_write_accumulators(rx_handle h, const int32_t *in, uint32_t count,
+                                uint64_t n_accum);
+
+/* Copy the per-channel state at the current sample position to out[cap].
+ * Synchronises the stream. */
+rx_status rx_read_state(rx_handle h, rx_channel_state *out, uint32_t cap);
+
+/* Load per-channel state (checkpoint / resume) for the n channels already set
+ * by rx_set_channels; prn must match.  Accumulators are left as they are. */
+rx_status rx_write_state(rx_handle h, const rx_channel_state *in, uint32_t n);
+
+/* Message for the last failed call on h (static storage inside the handle). */
+const char *rx_last_error(rx_handle h);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many receivers of uneven shape in one persistent launch     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double fs_hz;                /* sample rate, Hz */
+    uint32_t block_samples;      /* N: samples per block (1 ms at fs) */
+    uint32_t n_channels;         /* channels of this receiver */
+    uint32_t n_taps;             /* taps per channel, 1..RX_MAX_TAPS */
+    uint32_t integ_blocks;       /* L: blocks per integrate-and-dump epoch */
+    double pll_bn_hz;
+    double dll_bn_hz;
+    int32_t tap_early, tap_prompt, tap_late;
+} rx_receiver_desc;
+
+typedef struct rx_batch_s *rx_batch;
+
+/* Describe n_rx receivers that are correlated together.  max_blocks bounds the
+ * blocks per receiver between restarts (it sizes the dump buffer:
+ * max_blocks / integ_blocks dumps per receiver).  stream as in rx_config. */
+rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx,
+                          uint32_t max_blocks, int32_t device,
+                          void *cuda_stream, rx_batch *out);
+
+rx_status rx_batch_destroy(rx_batch b);
+
+/* Starting state of receiver rx's channels; arrays as in rx_set_channels with
+ * n = desc.n_channels and ntaps = desc.n_taps.  Also recorded as the state
+ * that RX_RUN_RESTART returns to. */
+rx_status rx_batch_set_channels(rx_batch b, uint32_t rx, const uint8_t *prn,
+                                const int32_t *carrier_word,
+                                const uint64_t *code_phase_word,
+                                const uint64_t *code_rate_word,
+                                const int64_t *tap_offsets);
+
+#define RX_RUN_RESTART 1u   /* restore the set_channels state and clear dumps first */
+#define RX_RUN_NO_GRAPH 2u  /* launch directly instead of through a CUDA graph */
+
+/* Track n_blocks consecutive blocks of every receiver, closing each receiver's
+ * loops at its own integration boundaries, in one persistent kernel launch.
+ * Receiver r's samples are the 2*N_r*n_blocks int8 values at iq +
+ * rx_byte_offset[r] (16-byte aligned offsets; host array of n_rx entries).
+ * iq is a device pointer (read in stream order) or host memory (copied to a
+ * library-owned device buffer inside the call).  The launch is recorded in a
+ * CUDA graph on first use and replayed while iq, offsets and n_blocks repeat.
+ * Dumps append to each receiver's dump buffer.  A device wait that exceeds its
+ * bound returns RX_ETIMEOUT (the stream is synchronised in that case). */
+rx_status rx_batch_run(rx_batch b, const int8_t *iq,
+                       const uint64_t *rx_byte_offset, uint32_t n_blocks,
+                       uint32_t flags);
+
+/* Block until the batch's stream is idle; report a device-side timeout. */
+rx_status rx_batch_sync(rx_batch b);
+
+/* Copy receiver rx's dumps, int32 [n_dumps][n_channels][n_taps][2], into
+ * out (cap elements).  *n_dumps receives the count.  Synchronises. */
+rx_status rx_batch_read_dumps(rx_batch b, uint32_t rx, int32_t *out,
+                              size_t cap, uint32_t *n_dumps);
+
+/* Per-channel state of receiver rx after the last run.  Synchronises. */
+rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
+                              uint32_t cap);
+
+/* Work decomposition of the persistent kernel.  channels_per_item: channels
+ * correlated together by one CTA per block (0 = choose); threads: CTA size
+ * (128, 256 or 512; 0 = choose); ctas_per_sm: resident CTAs per SM (0 =
+ * choose).  Takes effect at the next run (the graph is re-recorded). */
+rx_status rx_batch_set_tiles(rx_batch b, uint32_t channels_per_item,
+                             uint32_t threads, uint32_t ctas_per_sm);
+
+/* Read back the tiles in use (after the first run or set_tiles). */
+rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
+                             uint32_t *threads, uint32_t *ctas_per_sm);
+
+/* Number of kernel launches the last rx_batch_run issued (graph nodes
+ * included), for accounting. */
+uint32_t rx_batch_last_launches(rx_batch b);
+
+const char *rx_batch_last_error(rx_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RX_H */

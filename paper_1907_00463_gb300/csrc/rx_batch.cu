@@ -1,0 +1,798 @@
+// Batched form: many receivers of uneven shape (sample rate, channel count, tap
+// count, integration length) tracked together by ONE persistent kernel launch,
+// recorded once in a CUDA graph and replayed.
+//
+// Work decomposition.  Each receiver's channels are split into groups of at most
+// `cpg` channels.  A work item is (block b, group g); items are handed out by an
+// atomic ticket in block-major order t = b*G + g.  Item (b, g) may start only when
+// item (b-1, g) has finished (its loops were closed and the new NCO words stored):
+// the CTA holding it waits on a per-group counter with a bounded spin.  Because
+// tickets are taken in order and only by running CTAs, the oldest unfinished item
+// always has its predecessor done, so the schedule cannot deadlock whatever the
+// residency.  Channels of a receiver are independent (Sec. 3.5: the parallelizable
+// loop over channels); blocks of one channel are sequential (the tracking loop).
+//
+// Inside an item the CTA correlates the group's channels over the block's N
+// samples (direct form, rx_device.cuh), reduces per (channel, tap), then closes
+// the loops (Table 3) for channels at an integration boundary and publishes the
+// group's counter with release semantics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rx_device.cuh"
+#include "rx_internal.h"
+
+using namespace rxd;
+
+namespace {
+
+struct GroupDesc {
+    uint32_t rx;          // receiver index
+    uint32_t ch0;         // global index of the group's first channel
+    uint32_t nch;         // channels in the group
+    uint32_t ntaps;
+    uint32_t N;           // samples per block
+    uint32_t L;           // blocks per integration
+    int32_t tap_e, tap_p, tap_l;
+    uint32_t rx_nch;      // channels of the receiver (dump row length)
+    uint32_t ch_in_rx;    // index of ch0 inside its receiver
+    uint32_t max_dumps;   // dump slots per channel
+    uint64_t tap_base;    // index of channel ch0's first tap in the global tap array
+    uint64_t dump_base;   // index (int32 elements) of the receiver's dump 0
+    double fs, pll_bn, dll_bn;
+};
+
+// Mutable per-channel state: one contiguous block so that a restart is one copy.
+struct BatchState {
+    uint32_t *theta;
+    int32_t *w;
+    uint64_t *phi;
+    uint64_t *r;
+    double *v, *fcarr, *fcode;
+    uint32_t *epochs;      // dumps done
+    uint32_t *acc_blocks;  // blocks integrated since the last dump
+    int32_t *acc;          // [tap_base*2 ...]: running sums when L > 1
+};
+
+struct BatchConst {
+    const uint32_t *prn;
+    const int64_t *taps;
+    const GroupDesc *groups;
+    const uint64_t *rx_off;   // byte offset of each receiver's samples
+    int32_t *dumps;
+    const uint32_t *code_tab;
+    const uint32_t *carrier_tab;
+};
+
+struct BatchScratch {
+    uint32_t *ticket;
+    uint32_t *done;   // [G]
+    uint32_t *err;    // [4]: code, ticket, group, block
+};
+
+struct RunArgs {
+    const int8_t *iq;
+    uint32_t n_blocks;
+    uint32_t G;
+    uint32_t cpg;
+    uint32_t max_taps;
+    uint64_t timeout_ns;
+};
+
+constexpr uint32_t kErrTimeout = 1;
+
+template <int TT, int NT>
+__device__ __forceinline__ void item_group(const int8_t *blk, uint32_t N, bool a16, bool a4,
+                                           uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
+                                           const int64_t *s_taps, const uint32_t *s_code,
+                                           const uint32_t *s_tab, int32_t *s_red) {
+    int32_t sI = 0, sQ = 0, mI[TT], mQ[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) mI[k] = mQ[k] = 0;
+    const uint32_t nchunks = (N + SPT - 1) / SPT;
+    for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
+        const uint32_t s0 = j * SPT;
+        uint32_t x[SPT];
+        load_chunk(blk, s0, N, a16, a4, x);
+        const uint32_t th0 = theta + s0 * w;
+        const uint64_t ph0 = reduce_code_phase(phi + (uint64_t)s0 * r);
+        corr_chunk<TT>(x, th0, w, ph0, r, s_taps, s_code, s_tab, sI, sQ, mI, mQ);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        uint32_t vi = __reduce_add_sync(0xffffffffu, (uint32_t)sI + 2u * (uint32_t)mI[k]);
+        uint32_t vq = __reduce_add_sync(0xffffffffu, (uint32_t)sQ + 2u * (uint32_t)mQ[k]);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&s_red[2 * k], vi);
+            atomicAdd((unsigned *)&s_red[2 * k + 1], vq);
+        }
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchState st, BatchConst kc, BatchScratch sc,
+                                              RunArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t cpg = a.cpg, mt = a.max_taps;
+    int64_t *s_taps = reinterpret_cast<int64_t *>(smem);                       // [cpg*mt]
+    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + (size_t)cpg * mt);  // [64]
+    uint32_t *s_code = s_tab + 64;                                              // [cpg][EXT]
+    int32_t *s_acc = reinterpret_cast<int32_t *>(s_code + (size_t)cpg * EXT_WORDS);  // [cpg*mt*2]
+    uint32_t *s_theta = reinterpret_cast<uint32_t *>(s_acc + (size_t)cpg * mt * 2);  // [cpg]
+    uint32_t *s_w = s_theta + cpg;
+    uint32_t *s_ab = s_w + cpg;                                                 // acc_blocks
+    uint64_t *s_phi = reinterpret_cast<uint64_t *>(s_ab + cpg + (cpg & 1));     // [cpg]
+    uint32_t *s_r = reinterpret_cast<uint32_t *>(s_phi + cpg);
+    __shared__ uint32_t s_ticket, s_abort;
+
+    for (uint32_t i = threadIdx.x; i < 64; i += NT) s_tab[i] = kc.carrier_tab[i];
+    const uint32_t total = a.G * a.n_blocks;
+
+    for (;;) {
+        __syncthreads();  // previous item fully consumed its shared state
+        if (threadIdx.x == 0) {
+            s_abort = 0;
+            s_ticket = atomicAdd(sc.ticket, 1u);
+        }
+        __syncthreads();
+        const uint32_t t = s_ticket;
+        if (t >= total) return;
+        const uint32_t b = t / a.G, g = t - b * a.G;
+        const GroupDesc gd = kc.groups[g];
+
+        if (threadIdx.x == 0) {
+            // Bounded wait for item (b-1, g): time and iteration limits, then a
+            // recorded error instead of a hang.
+            const uint64_t t_start = globaltimer_ns();
+            uint32_t ns = 32;
+            for (uint32_t it = 0;; ++it) {
+                if (ld_acquire(sc.done + g) == b) break;
+                if (*(volatile uint32_t *)sc.err != 0) {
+                    s_abort = 1;
+                    break;
+                }
+                if (it > (1u << 24) || globaltimer_ns() - t_start > a.timeout_ns) {
+                    if (atomicCAS(sc.err, 0u, kErrTimeout) == 0u) {
+                        sc.err[1] = t;
+                        sc.err[2] = g;
+                        sc.err[3] = b;
+                    }
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
+        }
+        __syncthreads();
+        if (s_abort) return;
+
+        // Stage the group's constants and state.
+        const uint32_t nch = gd.nch, nt = gd.ntaps;
+        for (uint32_t i = threadIdx.x; i < nch * nt; i += NT) s_taps[i] = kc.taps[gd.tap_base + i];
+        for (uint32_t i = threadIdx.x; i < nch * EXT_WORDS; i += NT) {
+            const uint32_t j = i / EXT_WORDS;
+            s_code[i] = kc.code_tab[(size_t)kc.prn[gd.ch0 + j] * EXT_WORDS + (i - j * EXT_WORDS)];
+        }
+        for (uint32_t i = threadIdx.x; i < nch * nt * 2; i += NT) s_acc[i] = 0;
+        for (uint32_t j = threadIdx.x; j < nch; j += NT) {
+            const uint32_t c = gd.ch0 + j;
+            s_theta[j] = __ldcg(st.theta + c);
+            s_w[j] = (uint32_t)__ldcg(st.w + c);
+            s_phi[j] = __ldcg((const unsigned long long *)st.phi + c);
+            s_r[j] = (uint32_t)__ldcg((const unsigned long long *)st.r + c);
+            s_ab[j] = __ldcg(st.acc_blocks + c);
+        }
+        __syncthreads();
+
+        const int8_t *blk = a.iq + kc.rx_off[gd.rx] + (size_t)b * 2 * gd.N;
+        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+        for (uint32_t j = 0; j < nch; ++j) {
+            const uint32_t theta = s_theta[j], w = s_w[j], r = s_r[j];
+            const uint64_t phi = s_phi[j];
+            const int64_t *tp = s_taps + (size_t)j * nt;
+            const uint32_t *cd = s_code + (size_t)j * EXT_WORDS;
+            int32_t *red = s_acc + (size_t)j * nt * 2;
+            for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
+                switch (min((uint32_t)TAP_GROUP, nt - t0)) {
+                    case 1: item_group<1, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 2: item_group<2, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 3: item_group<3, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 4: item_group<4, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 5: item_group<5, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 6: item_group<6, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    case 7: item_group<7, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                    default: item_group<8, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
+                }
+            }
+        }
+        __syncthreads();
+
+        // Accumulate across blocks of an integration; dump at the boundary.
+        const uint32_t per_ch = nt * 2;
+        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
+            const uint32_t j = i / per_ch, e = i - j * per_ch;
+            const uint64_t ga = (gd.tap_base + (uint64_t)j * nt) * 2 + e;
+            uint32_t v = (uint32_t)s_acc[i];
+            if (s_ab[j] != 0) v += (uint32_t)__ldcg(st.acc + ga);
+            if (s_ab[j] + 1 == gd.L) {
+                const uint32_t ep = __ldcg(st.epochs + gd.ch0 + j);
+                if (ep < gd.max_dumps)
+                    kc.dumps[gd.dump_base +
+                             ((uint64_t)ep * gd.rx_nch + gd.ch_in_rx + j) * per_ch + e] = (int32_t)v;
+                s_acc[i] = (int32_t)v;
+            } else {
+                __stcg(st.acc + ga, (int32_t)v);
+            }
+        }
+        __syncthreads();
+
+        // Advance the NCOs over the block; close the loops at the boundary.
+        for (uint32_t j = threadIdx.x; j < nch; j += NT) {
+            const uint32_t c = gd.ch0 + j;
+            const uint32_t w = s_w[j];
+            __stcg(st.theta + c, s_theta[j] + gd.N * w);
+            __stcg((unsigned long long *)st.phi + c,
+                   (unsigned long long)reduce_code_phase(s_phi[j] + (uint64_t)gd.N * s_r[j]));
+            const uint32_t ab = s_ab[j] + 1;
+            if (ab == gd.L) {
+                const int32_t *A = s_acc + (size_t)j * per_ch;
+                const int64_t *tp = s_taps + (size_t)j * nt;
+                LoopOut o = loop_update(__ldcg(st.v + c), A[2 * gd.tap_e], A[2 * gd.tap_e + 1],
+                                        A[2 * gd.tap_p], A[2 * gd.tap_p + 1], A[2 * gd.tap_l],
+                                        A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.fs,
+                                        (uint64_t)gd.L * gd.N, gd.pll_bn, gd.dll_bn);
+                __stcg(st.v + c, o.v);
+                __stcg(st.fcarr + c, o.f_carr);
+                __stcg(st.fcode + c, o.f_code);
+                __stcg(st.w + c, o.w);
+                __stcg((unsigned long long *)st.r + c, (unsigned long long)o.r);
+                __stcg(st.epochs + c, __ldcg(st.epochs + c) + 1);
+                __stcg(st.acc_blocks + c, 0u);
+            } else {
+                __stcg(st.acc_blocks + c, ab);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(sc.done + g, b + 1);
+        }
+    }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+size_t batch_smem_bytes(uint32_t cpg, uint32_t mt) {
+    size_t s = (size_t)cpg * mt * 8 + 64 * 4 + (size_t)cpg * EXT_WORDS * 4 + (size_t)cpg * mt * 8;
+    s += (size_t)cpg * 4 * 3 + (cpg & 1) * 4;
+    s += (size_t)cpg * 8 + (size_t)cpg * 4;
+    return align_up(s, 16);
+}
+
+}  // namespace
+
+struct rx_batch_s {
+    std::vector<rx_receiver_desc> rx;
+    uint32_t n_rx = 0, max_blocks = 0, max_taps = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    const rxh::DeviceTables *tables = nullptr;
+    // channel bookkeeping
+    std::vector<uint32_t> rx_ch0;        // first global channel of each receiver
+    std::vector<uint64_t> rx_tap0;       // first global tap of each receiver
+    std::vector<uint64_t> rx_dump0;      // first dump element of each receiver
+    std::vector<uint32_t> rx_set;        // set_channels called
+    uint32_t n_ch = 0;
+    uint64_t n_taps_total = 0, dump_elems = 0;
+    // device memory
+    void *d_state = nullptr, *d_snap = nullptr;
+    size_t state_bytes = 0;
+    BatchState st{};
+    uint32_t *d_prn = nullptr;
+    int64_t *d_taps = nullptr;
+    int32_t *d_dumps = nullptr;
+    GroupDesc *d_groups = nullptr;
+    uint64_t *d_rxoff = nullptr;
+    uint32_t *d_scratch = nullptr;  // ticket, err[4], done[G]
+    uint32_t *h_err = nullptr;      // pinned copy of err[4]
+    int8_t *d_stage = nullptr;
+    size_t stage_bytes = 0;
+    // tiles
+    uint32_t cpg = 0, threads = 0, ctas_per_sm = 0, G = 0, grid = 0;
+    bool groups_dirty = true;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    const int8_t *g_iq = nullptr;
+    std::vector<uint64_t> g_off;
+    uint32_t g_blocks = 0, g_flags = 0, g_cpg = 0, g_threads = 0, g_ctas = 0;
+    uint32_t last_launches = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    std::string err;
+};
+
+namespace {
+
+rx_status berr(rx_batch b, rx_status s, const std::string &m) {
+    if (b) b->err = m;
+    return s;
+}
+
+uint32_t default_cpg(const rx_batch b) {
+    // Enough groups to cover the device about twice, with at least one channel each.
+    const uint32_t target = 2u * (uint32_t)b->tables->sm_count * 2u;
+    uint32_t best = 1;
+    for (uint32_t c : {8u, 6u, 4u, 3u, 2u, 1u}) {
+        uint32_t G = 0;
+        for (auto &d : b->rx) G += (d.n_channels + c - 1) / c;
+        if (G >= target) {
+            best = c;
+            break;
+        }
+    }
+    return best;
+}
+
+template <int NT>
+rx_status launch_nt(rx_batch b, const RunArgs &ra, BatchScratch sc, BatchConst kc, size_t smem) {
+    auto kern = k_batch<NT>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<b->grid, NT, smem, b->stream>>>(b->st, kc, sc, ra);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(e)));
+    return RX_OK;
+}
+
+template <int NT>
+int occupancy(size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<NT>, NT, smem);
+    return n;
+}
+
+rx_status build_groups(rx_batch b) {
+    if (b->cpg == 0) b->cpg = default_cpg(b);
+    if (b->threads == 0) b->threads = 256;
+    std::vector<GroupDesc> gs;
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        const rx_receiver_desc &d = b->rx[r];
+        for (uint32_t c0 = 0; c0 < d.n_channels; c0 += b->cpg) {
+            GroupDesc g{};
+            g.rx = r;
+            g.ch0 = b->rx_ch0[r] + c0;
+            g.nch = std::min(b->cpg, d.n_channels - c0);
+            g.ntaps = d.n_taps;
+            g.N = d.block_samples;
+            g.L = d.integ_blocks;
+            g.tap_e = d.tap_early;
+            g.tap_p = d.tap_prompt;
+            g.tap_l = d.tap_late;
+            g.rx_nch = d.n_channels;
+            g.ch_in_rx = c0;
+            g.max_dumps = b->max_blocks / d.integ_blocks;
+            g.tap_base = b->rx_tap0[r] + (uint64_t)c0 * d.n_taps;
+            g.dump_base = b->rx_dump0[r];
+            g.fs = d.fs_hz;
+            g.pll_bn = d.pll_bn_hz;
+            g.dll_bn = d.dll_bn_hz;
+            gs.push_back(g);
+        }
+    }
+    // Longest items first inside each block: the tail of every block is short.
+    std::stable_sort(gs.begin(), gs.end(), [](const GroupDesc &x, const GroupDesc &y) {
+        return (uint64_t)x.N * x.nch * (8 + 6 * x.ntaps) > (uint64_t)y.N * y.nch * (8 + 6 * y.ntaps);
+    });
+    std::string &E = b->err;
+    if (b->d_groups) cudaFree(b->d_groups);
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    b->d_groups = nullptr;
+    b->d_scratch = nullptr;
+    RX_CUDA_TRY(cudaMalloc(&b->d_groups, gs.size() * sizeof(GroupDesc)), E);
+    RX_CUDA_TRY(cudaMemcpy(b->d_groups, gs.data(), gs.size() * sizeof(GroupDesc), cudaMemcpyHostToDevice), E);
+    b->G = (uint32_t)gs.size();
+    RX_CUDA_TRY(cudaMalloc(&b->d_scratch, (5 + (size_t)b->G) * 4), E);
+    RX_CUDA_TRY(cudaMemset(b->d_scratch, 0, (5 + (size_t)b->G) * 4), E);
+    size_t smem = batch_smem_bytes(b->cpg, b->max_taps);
+    int occ = b->threads == 128 ? occupancy<128>(smem) : b->threads == 512 ? occupancy<512>(smem) : occupancy<256>(smem);
+    if (occ <= 0) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
+    uint32_t per_sm = b->ctas_per_sm ? std::min<uint32_t>(b->ctas_per_sm, occ) : (uint32_t)occ;
+    b->ctas_per_sm = per_sm;
+    b->grid = std::max(1u, std::min<uint32_t>(per_sm * b->tables->sm_count, b->G));
+    b->groups_dirty = false;
+    return RX_OK;
+}
+
+void drop_graph(rx_batch b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+// Enqueue one run on b->stream (also used under stream capture).
+rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t flags) {
+    std::string &E = b->err;
+    if (flags & RX_RUN_RESTART)
+        RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
+    RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, (5 + (size_t)b->G) * 4, b->stream), E);
+    BatchScratch sc{b->d_scratch, b->d_scratch + 5, b->d_scratch + 1};
+    BatchConst kc{b->d_prn, b->d_taps, b->d_groups, b->d_rxoff, b->d_dumps, b->tables->code, b->tables->tab};
+    RunArgs ra{iq, n_blocks, b->G, b->cpg, b->max_taps, b->timeout_ns};
+    size_t smem = batch_smem_bytes(b->cpg, b->max_taps);
+    rx_status s;
+    if (b->threads == 128) s = launch_nt<128>(b, ra, sc, kc, smem);
+    else if (b->threads == 512) s = launch_nt<512>(b, ra, sc, kc, smem);
+    else s = launch_nt<256>(b, ra, sc, kc, smem);
+    if (s != RX_OK) return s;
+    RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
+    return RX_OK;
+}
+
+rx_status check_err(rx_batch b) {
+    if (b->h_err[0] == 0) return RX_OK;
+    rx_status s = berr(b, RX_ETIMEOUT,
+                       rxh::fmt("device wait timed out: ticket %u group %u block %u", b->h_err[1],
+                                b->h_err[2], b->h_err[3]));
+    b->h_err[0] = 0;
+    return s;
+}
+
+}  // namespace
+
+extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, uint32_t max_blocks,
+                                     int32_t device, void *cuda_stream, rx_batch *out) {
+    if (!rx || !out || n_rx == 0 || max_blocks == 0) return RX_EINVAL;
+    *out = nullptr;
+    uint64_t n_ch = 0;
+    for (uint32_t r = 0; r < n_rx; ++r) {
+        const rx_receiver_desc &d = rx[r];
+        if (!(d.fs_hz > 1.1e6) || d.block_samples == 0 || (d.block_samples & 1) ||
+            d.block_samples > RX_MAX_BLOCK_SAMPLES || d.n_channels == 0 || d.n_taps == 0 ||
+            d.n_taps > RX_MAX_TAPS || d.integ_blocks == 0 || d.tap_early < 0 || d.tap_prompt < 0 ||
+            d.tap_late < 0 || (uint32_t)d.tap_early >= d.n_taps ||
+            (uint32_t)d.tap_prompt >= d.n_taps || (uint32_t)d.tap_late >= d.n_taps)
+            return RX_EINVAL;
+        n_ch += d.n_channels;
+    }
+    if (n_ch > (1u << 24)) return RX_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return RX_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return RX_ECUDA;
+    rx_batch b = new (std::nothrow) rx_batch_s();
+    if (!b) return RX_ENOMEM;
+    b->rx.assign(rx, rx + n_rx);
+    b->n_rx = n_rx;
+    b->max_blocks = max_blocks;
+    b->device = device;
+    std::string e;
+    b->tables = rxh::tables_for_device(device, e);
+    if (!b->tables) {
+        delete b;
+        return RX_ECUDA;
+    }
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return RX_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    uint64_t taps = 0, dumps = 0;
+    uint32_t ch = 0;
+    for (uint32_t r = 0; r < n_rx; ++r) {
+        const rx_receiver_desc &d = rx[r];
+        b->rx_ch0.push_back(ch);
+        b->rx_tap0.push_back(taps);
+        b->rx_dump0.push_back(dumps);
+        ch += d.n_channels;
+        taps += (uint64_t)d.n_channels * d.n_taps;
+        dumps += (uint64_t)(max_blocks / d.integ_blocks) * d.n_channels * d.n_taps * 2;
+        b->max_taps = std::max(b->max_taps, d.n_taps);
+    }
+    b->rx_set.assign(n_rx, 0);
+    b->n_ch = ch;
+    b->n_taps_total = taps;
+    b->dump_elems = dumps;
+    const size_t C = ch;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    size_t o_theta = take(C * 4), o_w = take(C * 4), o_phi = take(C * 8), o_r = take(C * 8),
+           o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8), o_ep = take(C * 4),
+           o_ab = take(C * 4), o_acc = take(taps * 8);
+    b->state_bytes = off;
+    auto fail = [&](rx_status s) {
+        rx_batch_destroy(b);
+        return s;
+    };
+    if (cudaMalloc(&b->d_state, off) != cudaSuccess || cudaMalloc(&b->d_snap, off) != cudaSuccess ||
+        cudaMalloc(&b->d_prn, C * 4) != cudaSuccess || cudaMalloc(&b->d_taps, taps * 8) != cudaSuccess ||
+        cudaMalloc(&b->d_dumps, std::max<uint64_t>(dumps, 1) * 4) != cudaSuccess ||
+        cudaMalloc(&b->d_rxoff, n_rx * 8) != cudaSuccess ||
+        cudaMallocHost(&b->h_err, 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RX_ENOMEM);
+    }
+    std::memset(b->h_err, 0, 16);
+    char *p = (char *)b->d_state;
+    b->st.theta = (uint32_t *)(p + o_theta);
+    b->st.w = (int32_t *)(p + o_w);
+    b->st.phi = (uint64_t *)(p + o_phi);
+    b->st.r = (uint64_t *)(p + o_r);
+    b->st.v = (double *)(p + o_v);
+    b->st.fcarr = (double *)(p + o_fc);
+    b->st.fcode = (double *)(p + o_fk);
+    b->st.epochs = (uint32_t *)(p + o_ep);
+    b->st.acc_blocks = (uint32_t *)(p + o_ab);
+    b->st.acc = (int32_t *)(p + o_acc);
+    if (cudaMemset(b->d_state, 0, off) != cudaSuccess || cudaMemset(b->d_snap, 0, off) != cudaSuccess ||
+        cudaMemset(b->d_prn, 0, C * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RX_ECUDA);
+    }
+    *out = b;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_destroy(rx_batch b) {
+    if (!b) return RX_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    void *ptrs[] = {b->d_state, b->d_snap, b->d_prn, b->d_taps, b->d_dumps, b->d_groups, b->d_rxoff,
+                    b->d_scratch, b->d_stage};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8_t *prn,
+                                           const int32_t *carrier_word,
+                                           const uint64_t *code_phase_word,
+                                           const uint64_t *code_rate_word,
+                                           const int64_t *tap_offsets) {
+    if (!b) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    if (!prn || !carrier_word || !code_phase_word || !code_rate_word || !tap_offsets)
+        return berr(b, RX_EINVAL, "null array");
+    const rx_receiver_desc &d = b->rx[rxi];
+    const uint32_t n = d.n_channels, nt = d.n_taps;
+    for (uint32_t c = 0; c < n; ++c) {
+        std::string m = rxh::check_channel(prn[c], code_rate_word[c], tap_offsets + (size_t)c * nt, nt);
+        if (!m.empty()) return berr(b, RX_EINVAL, rxh::fmt("rx %u channel %u: %s", rxi, c, m.c_str()));
+    }
+    std::vector<uint32_t> vprn(n), zero(n, 0);
+    std::vector<uint64_t> phi(n);
+    std::vector<double> v(n), fk(n);
+    for (uint32_t c = 0; c < n; ++c) {
+        vprn[c] = prn[c];
+        phi[c] = code_phase_word[c] % rxh::kCodeMod;
+        v[c] = rxh::carrier_word_to_hz(carrier_word[c], d.fs_hz);
+        fk[c] = rxh::code_word_to_hz(code_rate_word[c], d.fs_hz);
+    }
+    cudaSetDevice(b->device);
+    std::string &E = b->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+    const uint32_t c0 = b->rx_ch0[rxi];
+    const BatchState &s = b->st;
+    RX_CUDA_TRY(cudaMemcpy(s.theta + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.w + c0, carrier_word, n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.phi + c0, phi.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.r + c0, code_rate_word, n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.v + c0, v.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.fcarr + c0, v.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.fcode + c0, fk.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.epochs + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(s.acc_blocks + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemset(s.acc + b->rx_tap0[rxi] * 2, 0, (size_t)n * nt * 8), E);
+    RX_CUDA_TRY(cudaMemcpy(b->d_prn + c0, vprn.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(b->d_taps + b->rx_tap0[rxi], tap_offsets, (size_t)n * nt * 8, cudaMemcpyHostToDevice), E);
+    // The restart snapshot mirrors the state block byte for byte.
+    const size_t diff = (char *)b->d_snap - (char *)b->d_state;
+    auto snap = [&](void *dev, size_t bytes) {
+        return cudaMemcpy((char *)dev + diff, dev, bytes, cudaMemcpyDeviceToDevice);
+    };
+    RX_CUDA_TRY(snap(s.theta + c0, n * 4), E);
+    RX_CUDA_TRY(snap(s.w + c0, n * 4), E);
+    RX_CUDA_TRY(snap(s.phi + c0, n * 8), E);
+    RX_CUDA_TRY(snap(s.r + c0, n * 8), E);
+    RX_CUDA_TRY(snap(s.v + c0, n * 8), E);
+    RX_CUDA_TRY(snap(s.fcarr + c0, n * 8), E);
+    RX_CUDA_TRY(snap(s.fcode + c0, n * 8), E);
+    RX_CUDA_TRY(snap(s.epochs + c0, n * 4), E);
+    RX_CUDA_TRY(snap(s.acc_blocks + c0, n * 4), E);
+    RX_CUDA_TRY(snap(s.acc + b->rx_tap0[rxi] * 2, (size_t)n * nt * 8), E);
+    b->rx_set[rxi] = 1;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threads, uint32_t ctas_per_sm) {
+    if (!b) return RX_EINVAL;
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
+        return berr(b, RX_EINVAL, "threads must be 128, 256 or 512");
+    if (cpg > 64) return berr(b, RX_EINVAL, "channels_per_item must be <= 64");
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->cpg = cpg;
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    b->groups_dirty = true;
+    drop_graph(b);
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *threads, uint32_t *ctas) {
+    if (!b || !cpg || !threads || !ctas) return RX_EINVAL;
+    if (b->groups_dirty) {
+        cudaSetDevice(b->device);
+        rx_status s = build_groups(b);
+        if (s != RX_OK) return s;
+    }
+    *cpg = b->cpg;
+    *threads = b->threads;
+    *ctas = b->ctas_per_sm;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
+                                  uint32_t n_blocks, uint32_t flags) {
+    if (!b) return RX_EINVAL;
+    if (!iq || !rx_byte_offset || n_blocks == 0) return berr(b, RX_EINVAL, "null input or zero blocks");
+    if (n_blocks > b->max_blocks) return berr(b, RX_EINVAL, "n_blocks > max_blocks");
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        if (!b->rx_set[r]) return berr(b, RX_ESTATE, rxh::fmt("receiver %u has no channels set", r));
+        if (rx_byte_offset[r] & 15) return berr(b, RX_EINVAL, "receiver offsets must be 16-byte aligned");
+    }
+    cudaSetDevice(b->device);
+    std::string &E = b->err;
+    rx_status s;
+    if (b->groups_dirty) {
+        drop_graph(b);
+        if ((s = build_groups(b)) != RX_OK) return s;
+    }
+    const int8_t *src = iq;
+    if (!rxh::is_device_pointer(iq)) {
+        // Host input: copy each receiver's span into the device staging buffer.
+        size_t need = 0;
+        for (uint32_t r = 0; r < b->n_rx; ++r)
+            need = std::max(need, (size_t)rx_byte_offset[r] + (size_t)n_blocks * 2 * b->rx[r].block_samples);
+        if (need > b->stage_bytes) {
+            drop_graph(b);
+            if (b->d_stage) cudaFree(b->d_stage);
+            b->d_stage = nullptr;
+            b->stage_bytes = 0;
+            if (cudaMalloc(&b->d_stage, need) != cudaSuccess) {
+                cudaGetLastError();
+                return berr(b, RX_ENOMEM, "staging buffer");
+            }
+            b->stage_bytes = need;
+        }
+        for (uint32_t r = 0; r < b->n_rx; ++r) {
+            size_t bytes = (size_t)n_blocks * 2 * b->rx[r].block_samples;
+            RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + rx_byte_offset[r], iq + rx_byte_offset[r], bytes,
+                                        cudaMemcpyHostToDevice, b->stream), E);
+        }
+        src = b->d_stage;
+    }
+    std::vector<uint64_t> off(rx_byte_offset, rx_byte_offset + b->n_rx);
+    if (b->g_off != off) {
+        RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+        RX_CUDA_TRY(cudaMemcpy(b->d_rxoff, off.data(), off.size() * 8, cudaMemcpyHostToDevice), E);
+        drop_graph(b);
+        b->g_off = off;
+    }
+    if (flags & RX_RUN_NO_GRAPH) {
+        s = enqueue_run(b, src, n_blocks, flags);
+        b->last_launches = 1;
+        return s;
+    }
+    if (b->gexec && (b->g_iq != src || b->g_blocks != n_blocks || b->g_flags != flags)) drop_graph(b);
+    if (!b->gexec) {
+        cudaGraph_t graph = nullptr;
+        RX_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), E);
+        s = enqueue_run(b, src, n_blocks, flags);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+        if (s != RX_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("capture: %s", cudaGetErrorString(ce)));
+        ce = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            b->gexec = nullptr;
+            return berr(b, RX_ECUDA, rxh::fmt("instantiate: %s", cudaGetErrorString(ce)));
+        }
+        b->g_iq = src;
+        b->g_blocks = n_blocks;
+        b->g_flags = flags;
+    }
+    RX_CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream), E);
+    b->last_launches = 1;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_sync(rx_batch b) {
+    if (!b) return RX_EINVAL;
+    cudaSetDevice(b->device);
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), b->err);
+    return check_err(b);
+}
+
+extern "C" rx_status rx_batch_read_dumps(rx_batch b, uint32_t rxi, int32_t *out, size_t cap,
+                                         uint32_t *n_dumps) {
+    if (!b || !out || !n_dumps) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    rx_status s = rx_batch_sync(b);
+    if (s != RX_OK) return s;
+    const rx_receiver_desc &d = b->rx[rxi];
+    uint32_t ep = 0;
+    RX_CUDA_TRY(cudaMemcpy(&ep, b->st.epochs + b->rx_ch0[rxi], 4, cudaMemcpyDeviceToHost), b->err);
+    const uint32_t nd = std::min(ep, b->max_blocks / d.integ_blocks);
+    const size_t elems = (size_t)nd * d.n_channels * d.n_taps * 2;
+    if (cap < elems) return berr(b, RX_EINVAL, rxh::fmt("cap %zu < %zu", cap, elems));
+    if (elems)
+        RX_CUDA_TRY(cudaMemcpy(out, b->d_dumps + b->rx_dump0[rxi], elems * 4, cudaMemcpyDeviceToHost), b->err);
+    *n_dumps = nd;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_read_state(rx_batch b, uint32_t rxi, rx_channel_state *out, uint32_t cap) {
+    if (!b || !out) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    const uint32_t n = b->rx[rxi].n_channels;
+    if (cap < n) return berr(b, RX_EINVAL, "cap < channels");
+    rx_status s = rx_batch_sync(b);
+    if (s != RX_OK) return s;
+    const uint32_t c0 = b->rx_ch0[rxi];
+    std::vector<uint32_t> theta(n), prn(n), ep(n);
+    std::vector<int32_t> w(n);
+    std::vector<uint64_t> phi(n), r(n);
+    std::vector<double> v(n), fc(n), fk(n);
+    std::string &E = b->err;
+    const BatchState &st = b->st;
+    RX_CUDA_TRY(cudaMemcpy(theta.data(), st.theta + c0, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(w.data(), st.w + c0, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(phi.data(), st.phi + c0, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(r.data(), st.r + c0, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(v.data(), st.v + c0, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(fc.data(), st.fcarr + c0, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(fk.data(), st.fcode + c0, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(ep.data(), st.epochs + c0, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(prn.data(), b->d_prn + c0, n * 4, cudaMemcpyDeviceToHost), E);
+    for (uint32_t c = 0; c < n; ++c) {
+        out[c].carrier_phase = theta[c];
+        out[c].carrier_word = w[c];
+        out[c].code_phase = phi[c];
+        out[c].code_rate = r[c];
+        out[c].pll_integrator_hz = v[c];
+        out[c].carrier_hz = fc[c];
+        out[c].code_hz = fk[c];
+        out[c].prn = prn[c];
+        out[c].epochs = ep[c];
+    }
+    return RX_OK;
+}
+
+extern "C" uint32_t rx_batch_last_launches(rx_batch b) { return b ? b->last_launches : 0; }
+
+extern "C" const char *rx_batch_last_error(rx_batch b) { return b ? b->err.c_str() : "null handle"; }

@@ -1,0 +1,261 @@
+// Device-side building blocks of the tracking correlator (sm_103a).
+//
+// Shared by the plain per-receiver kernels (rx_plain.cu) and the persistent
+// batched kernel (rx_batch.cu).  Everything on the correlator path is integer
+// arithmetic; the loop filter is FP64 written with explicit round-to-nearest
+// intrinsics so that no operation is contracted or reassociated.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rxd {
+
+constexpr int CODE_LEN = 1023;
+constexpr uint64_t CODE_MOD = (uint64_t)CODE_LEN << 32;
+// Extended, bit-packed C/A table: chip c (c in [-EXT_BASE, EXT_WORDS*32 - EXT_BASE))
+// sits at bit index i = c + EXT_BASE, most significant bit first inside each 32-bit
+// word, and holds the logic level of chip (c mod 1023).  One block's chips, plus tap
+// offsets of up to 64 chips, stay inside the table without any per-sample modulo.
+constexpr int EXT_BASE = 256;
+constexpr int EXT_WORDS = 80;
+constexpr int SPT = 16;        // samples per thread chunk
+constexpr int TAP_GROUP = 8;   // taps correlated per pass over a chunk
+
+// ----------------------------------------------------------------------------
+// small PTX helpers
+// ----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Two complex int8 samples (I0, Q0, I1, Q1 in byte order) -> two words, each
+// holding the sample as a pair of sign-extended int16 (I in the low half).
+__device__ __forceinline__ void unpack2(uint32_t v, uint32_t &s0, uint32_t &s1) {
+    s0 = prmt(v, 0u, 0x9180u);
+    s1 = prmt(v, 0u, 0xB3A2u);
+}
+
+__device__ __forceinline__ uint32_t unpack1(uint16_t v) {
+    return prmt((uint32_t)v, 0u, 0x9180u);
+}
+
+__device__ __forceinline__ uint64_t reduce_code_phase(uint64_t x) {
+    uint32_t hi = (uint32_t)(x >> 32) % (uint32_t)CODE_LEN;
+    return ((uint64_t)hi << 32) | (uint32_t)x;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ----------------------------------------------------------------------------
+// samples
+// ----------------------------------------------------------------------------
+
+// Load SPT samples starting at sample s0 of a block of n samples; samples at
+// or beyond n read as zero (they add nothing to any accumulator).  blk must be
+// at least 2-byte aligned; aligned16 says blk is 16-byte aligned, aligned4 that
+// it is 4-byte aligned.
+__device__ __forceinline__ void load_chunk(const int8_t *__restrict__ blk, uint32_t s0,
+                                           uint32_t n, bool aligned16, bool aligned4,
+                                           uint32_t (&x)[SPT]) {
+    if (s0 + SPT <= n && aligned16) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blk + 2 * (size_t)s0);
+        uint4 a = __ldg(p), b = __ldg(p + 1);
+        unpack2(a.x, x[0], x[1]);
+        unpack2(a.y, x[2], x[3]);
+        unpack2(a.z, x[4], x[5]);
+        unpack2(a.w, x[6], x[7]);
+        unpack2(b.x, x[8], x[9]);
+        unpack2(b.y, x[10], x[11]);
+        unpack2(b.z, x[12], x[13]);
+        unpack2(b.w, x[14], x[15]);
+    } else if (s0 + SPT <= n && aligned4) {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(blk + 2 * (size_t)s0);
+#pragma unroll
+        for (int j = 0; j < SPT / 2; ++j) unpack2(__ldg(p + j), x[2 * j], x[2 * j + 1]);
+    } else {
+        const uint16_t *p = reinterpret_cast<const uint16_t *>(blk + 2 * (size_t)s0);
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) x[j] = (s0 + j < n) ? unpack1(__ldg(p + j)) : 0u;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// direct-form correlation of one chunk for one channel and TT taps
+// ----------------------------------------------------------------------------
+
+// Carrier table entry k packs the int8 bytes (c_k, s_k, -s_k, c_k), so that for a
+// sample packed as int16 (I, Q):  dp2a.lo = I c + Q s = I',  dp2a.hi = -I s + Q c = Q'.
+//
+// Code sign: for each tap the thread keeps the 32.32 position relative to a 32-chip
+// window of code bits loaded at its first sample; the chip's logic level becomes
+// m = 0 / -1 (code value +1 / -1) and the tap accumulates m*I', so that
+//   A_I = sum(I') + 2 sum(m I')
+// which the caller forms once per chunk.
+//
+// theta0: carrier phase at the chunk's first sample; w: carrier word.
+// phi0:   code phase at the chunk's first sample, reduced to [0, 1023*2^32).
+// r:      code word (< 2^32).
+// off:    TT tap offsets; code: the channel's extended code table; tab: carrier table.
+template <int TT>
+__device__ __forceinline__ void corr_chunk(const uint32_t (&x)[SPT], uint32_t theta0, uint32_t w,
+                                           uint64_t phi0, uint32_t r, const int64_t *off,
+                                           const uint32_t *code, const uint32_t *tab,
+                                           int32_t &sI, int32_t &sQ, int32_t (&mI)[TT],
+                                           int32_t (&mQ)[TT]) {
+    uint64_t pos[TT];
+    uint32_t win[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        int64_t p = (int64_t)phi0 + off[k];
+        int32_t cb = (int32_t)(p >> 32);               // first chip of this tap in the chunk
+        uint32_t bit = (uint32_t)(cb + EXT_BASE);
+        uint32_t w0 = code[bit >> 5], w1 = code[(bit >> 5) + 1];
+        win[k] = __funnelshift_l(w1, w0, bit & 31);    // bit 31 <- chip cb
+        pos[k] = (uint64_t)(uint32_t)p;                // chips since cb in the high word
+    }
+    uint32_t th = theta0;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+        uint32_t e = tab[th >> 26];
+        th += w;
+        int32_t ip = __dp2a_lo((int)x[i], (int)e, 0);
+        int32_t qp = __dp2a_hi((int)x[i], (int)e, 0);
+        sI += ip;
+        sQ += qp;
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            int32_t m = (int32_t)(win[k] << (uint32_t)(pos[k] >> 32)) >> 31;
+            mI[k] += m * ip;
+            mQ[k] += m * qp;
+            pos[k] += r;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// loop filter (Table 3), FP64, bit-identical to the CPU definition
+// ----------------------------------------------------------------------------
+
+#define RXD_PI_2 1.5707963267948966
+#define RXD_PI_6 0.5235987755982989
+#define RXD_TAN_PI_12 0.2679491924311227
+#define RXD_SQRT3 1.7320508075688772
+#define RXD_SQRT2 1.4142135623730951
+#define RXD_TWO_PI 6.283185307179586
+#define RXD_TWO32 4294967296.0
+
+// atan(x): reduce |x| > 1 by atan(x) = pi/2 - atan(1/x), then a > tan(pi/12) by
+// atan(a) = pi/6 + atan((sqrt3 a - 1)/(sqrt3 + a)), then the Gregory series to
+// degree 25 by Horner's rule.
+__device__ __forceinline__ double own_atan(double x) {
+    bool neg = x < 0.0;
+    double a = neg ? -x : x;
+    bool inv = a > 1.0;
+    if (inv) a = __ddiv_rn(1.0, a);
+    bool shift = a > RXD_TAN_PI_12;
+    if (shift) {
+        double num = __dmul_rn(RXD_SQRT3, a);
+        num = __dsub_rn(num, 1.0);
+        double den = __dadd_rn(RXD_SQRT3, a);
+        a = __ddiv_rn(num, den);
+    }
+    double t = __dmul_rn(a, a);
+    double p = __ddiv_rn(1.0, 25.0);
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+        double ck = __ddiv_rn((k & 1) ? -1.0 : 1.0, (double)(2 * k + 1));
+        p = __dmul_rn(p, t);
+        p = __dadd_rn(p, ck);
+    }
+    double y = __dmul_rn(a, p);
+    if (shift) y = __dadd_rn(RXD_PI_6, y);
+    if (inv) y = __dsub_rn(RXD_PI_2, y);
+    return neg ? -y : y;
+}
+
+struct LoopOut {
+    double v, f_carr, f_code;
+    int32_t w;
+    uint64_t r;
+};
+
+// One loop update from the dumped E/P/L sums.  n_accum: samples integrated.
+__device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
+                                               int32_t qpr, int32_t il, int32_t ql,
+                                               int64_t off_e, int64_t off_l, double fs,
+                                               uint64_t n_accum, double pll_bn, double dll_bn) {
+    LoopOut o;
+    double T = __ddiv_rn((double)n_accum, fs);
+    double ip = (double)ipr, qp = (double)qpr;
+    double e_pll;
+    if (ip != 0.0) {
+        double q = __ddiv_rn(qp, ip);
+        e_pll = __ddiv_rn(own_atan(q), RXD_TWO_PI);
+    } else {
+        e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+    }
+    double w0 = __ddiv_rn(pll_bn, 0.53);
+    double k1 = __dmul_rn(w0, w0);
+    k1 = __dmul_rn(k1, T);
+    double k2 = __dmul_rn(RXD_SQRT2, w0);
+    double dv = __dmul_rn(k1, e_pll);
+    v = __dadd_rn(v, dv);
+    double df = __dmul_rn(k2, e_pll);
+    double f_carr = __dadd_rn(v, df);
+
+    double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
+    double ie2 = __dmul_rn(dIe, dIe), qe2 = __dmul_rn(dQe, dQe);
+    double il2 = __dmul_rn(dIl, dIl), ql2 = __dmul_rn(dQl, dQl);
+    double mag_e = __dsqrt_rn(__dadd_rn(ie2, qe2));
+    double mag_l = __dsqrt_rn(__dadd_rn(il2, ql2));
+    double den = __dadd_rn(mag_e, mag_l);
+    double d_el = __ddiv_rn((double)(off_e - off_l), RXD_TWO32);
+    double kd = __dsub_rn(1.0, __ddiv_rn(d_el, 2.0));
+    double e_dll = 0.0;
+    if (den > 0.0) {
+        double num = __dsub_rn(mag_e, mag_l);
+        num = __dmul_rn(kd, num);
+        e_dll = __ddiv_rn(num, den);
+    }
+    double aid = __ddiv_rn(f_carr, 1575.42e6);
+    aid = __dadd_rn(1.0, aid);
+    double f_code = __dmul_rn(1.023e6, aid);
+    double kdll = __dmul_rn(4.0, dll_bn);
+    double corr = __dmul_rn(kdll, e_dll);
+    f_code = __dadd_rn(f_code, corr);
+
+    double xw = __ddiv_rn(f_carr, fs);
+    xw = __dmul_rn(xw, RXD_TWO32);
+    double xr = __ddiv_rn(f_code, fs);
+    xr = __dmul_rn(xr, RXD_TWO32);
+    if (xw > 9.0e18) xw = 9.0e18;
+    if (xw < -9.0e18) xw = -9.0e18;
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
+    o.r = (uint64_t)__double2ll_rn(xr);
+    o.v = v;
+    o.f_carr = f_carr;
+    o.f_code = f_code;
+    return o;
+}
+
+}  // namespace rxd

@@ -1,0 +1,436 @@
+// Plain form: one receiver per handle, one kernel launch per rx_correlate call
+// and one per rx_track_epoch (the per-call structure of the paper's
+// do_tracking(raw block, size, system parameters, channel array), Sec. 3.4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rx_device.cuh"
+#include "rx_internal.h"
+
+using namespace rxd;
+
+namespace {
+
+constexpr int kPlainThreads = 128;
+constexpr uint64_t kFoldLimit = 1ull << 31;  // samples correlated before the phases are folded
+
+struct PlainState {
+    uint32_t *theta;   // carrier phase at the last fold
+    int32_t *w;
+    uint64_t *phi;     // code phase at the last fold, reduced
+    uint64_t *r;
+    uint32_t *prn;
+    double *v, *fcarr, *fcode;
+    uint32_t *epochs;
+    int64_t *taps;     // [n][ntaps]
+    int32_t *acc;      // [n][ntaps][2]
+};
+
+template <int TT>
+__device__ __forceinline__ void plain_group(const uint32_t (&x)[SPT], uint32_t theta0, uint32_t w,
+                                            uint64_t phi0, uint32_t r, const int64_t *s_taps,
+                                            const uint32_t *s_code, const uint32_t *s_tab, int t0,
+                                            int32_t *s_red) {
+    int32_t sI = 0, sQ = 0, mI[TT], mQ[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) mI[k] = mQ[k] = 0;
+    corr_chunk<TT>(x, theta0, w, phi0, r, s_taps + t0, s_code, s_tab, sI, sQ, mI, mQ);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        uint32_t vi = (uint32_t)sI + 2u * (uint32_t)mI[k];
+        uint32_t vq = (uint32_t)sQ + 2u * (uint32_t)mQ[k];
+        vi = __reduce_add_sync(0xffffffffu, vi);
+        vq = __reduce_add_sync(0xffffffffu, vq);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&s_red[2 * (t0 + k)], vi);
+            atomicAdd((unsigned *)&s_red[2 * (t0 + k) + 1], vq);
+        }
+    }
+}
+
+// grid = (sample tiles of kPlainThreads*SPT, channels); each thread one chunk.
+__global__ void __launch_bounds__(kPlainThreads)
+    k_plain_correlate(const int8_t *__restrict__ iq, uint32_t nsamp, uint64_t n_before,
+                      bool a16, bool a4, PlainState st, uint32_t ntaps, const uint32_t *__restrict__ code_tab,
+                      const uint32_t *__restrict__ carrier_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int64_t *s_taps = reinterpret_cast<int64_t *>(smem);                 // [ntaps]
+    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + ntaps);      // [64]
+    uint32_t *s_code = s_tab + 64;                                        // [EXT_WORDS]
+    int32_t *s_red = reinterpret_cast<int32_t *>(s_code + EXT_WORDS);    // [2*ntaps]
+
+    const uint32_t ch = blockIdx.y;
+    const uint32_t prn = st.prn[ch];
+    for (uint32_t i = threadIdx.x; i < ntaps; i += blockDim.x) s_taps[i] = st.taps[(size_t)ch * ntaps + i];
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) s_tab[i] = carrier_tab[i];
+    for (uint32_t i = threadIdx.x; i < EXT_WORDS; i += blockDim.x)
+        s_code[i] = code_tab[(size_t)prn * EXT_WORDS + i];
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) s_red[i] = 0;
+    __syncthreads();
+
+    const uint32_t s0 = (blockIdx.x * blockDim.x + threadIdx.x) * SPT;
+    uint32_t x[SPT];
+    if (s0 < nsamp) {
+        load_chunk(iq, s0, nsamp, a16, a4, x);
+    } else {
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) x[i] = 0u;
+    }
+    const uint32_t w = (uint32_t)st.w[ch];
+    const uint32_t r = (uint32_t)st.r[ch];
+    const uint64_t n0 = n_before + s0;
+    const uint32_t theta0 = st.theta[ch] + (uint32_t)n0 * w;
+    const uint64_t phi0 = reduce_code_phase(st.phi[ch] + n0 * (uint64_t)r);
+
+    for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
+        switch (min((uint32_t)TAP_GROUP, ntaps - t0)) {
+            case 1: plain_group<1>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 2: plain_group<2>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 3: plain_group<3>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 4: plain_group<4>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 5: plain_group<5>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 6: plain_group<6>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            case 7: plain_group<7>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            default: plain_group<8>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+        }
+    }
+    __syncthreads();
+    int32_t *acc = st.acc + (size_t)ch * ntaps * 2;
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x)
+        atomicAdd((unsigned *)&acc[i], (unsigned)s_red[i]);
+}
+
+// Advance the stored phases by n samples (mod 2^32 / mod 1023*2^32).
+__global__ void k_plain_fold(PlainState st, uint32_t n_ch, uint64_t n) {
+    uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_ch) return;
+    st.theta[c] = st.theta[c] + (uint32_t)n * (uint32_t)st.w[c];
+    st.phi[c] = reduce_code_phase(st.phi[c] + n * st.r[c]);
+}
+
+// Integration boundary, one thread per channel: fold phases, run the loops,
+// load the new words, clear the accumulators.
+__global__ void k_plain_track(PlainState st, uint32_t n_ch, uint32_t ntaps, uint64_t n_fold,
+                              uint64_t n_accum, double fs, double pll_bn, double dll_bn,
+                              int tap_e, int tap_p, int tap_l) {
+    uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_ch) return;
+    st.theta[c] = st.theta[c] + (uint32_t)n_fold * (uint32_t)st.w[c];
+    st.phi[c] = reduce_code_phase(st.phi[c] + n_fold * st.r[c]);
+    int32_t *a = st.acc + (size_t)c * ntaps * 2;
+    const int64_t *t = st.taps + (size_t)c * ntaps;
+    LoopOut o = loop_update(st.v[c], a[2 * tap_e], a[2 * tap_e + 1], a[2 * tap_p], a[2 * tap_p + 1],
+                            a[2 * tap_l], a[2 * tap_l + 1], t[tap_e], t[tap_l], fs, n_accum, pll_bn,
+                            dll_bn);
+    st.v[c] = o.v;
+    st.fcarr[c] = o.f_carr;
+    st.fcode[c] = o.f_code;
+    st.w[c] = o.w;
+    st.r[c] = o.r;
+    st.epochs[c] += 1;
+    for (uint32_t i = 0; i < 2 * ntaps; ++i) a[i] = 0;
+}
+
+}  // namespace
+
+struct rx_handle_s {
+    rx_config cfg{};
+    cudaStream_t stream = nullptr;
+    const rxh::DeviceTables *tables = nullptr;
+    uint32_t n_ch = 0, n_taps = 0;
+    PlainState st{};
+    void *d_block = nullptr;   // one allocation holding every state array
+    int8_t *d_stage = nullptr; // staging buffer for host input
+    uint64_t n_since_fold = 0;
+    uint64_t n_accum = 0;
+    std::string err;
+};
+
+namespace {
+
+rx_status set_err(rx_handle h, rx_status s, const std::string &m) {
+    if (h) h->err = m;
+    return s;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
+    if (!cfg || !out) return RX_EINVAL;
+    *out = nullptr;
+    if (!(cfg->fs_hz > 1.1e6) || cfg->max_block_samples == 0 ||
+        cfg->max_block_samples > RX_MAX_BLOCK_SAMPLES || cfg->max_channels == 0 ||
+        cfg->max_channels > RX_MAX_CHANNELS || cfg->max_taps == 0 || cfg->max_taps > RX_MAX_TAPS ||
+        cfg->tap_early < 0 || cfg->tap_prompt < 0 || cfg->tap_late < 0 ||
+        (uint32_t)cfg->tap_early >= cfg->max_taps || (uint32_t)cfg->tap_prompt >= cfg->max_taps ||
+        (uint32_t)cfg->tap_late >= cfg->max_taps || !(cfg->pll_bn_hz >= 0) || !(cfg->dll_bn_hz >= 0))
+        return RX_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= cfg->device || cfg->device < 0) {
+        cudaGetLastError();
+        return RX_ECUDA;
+    }
+    rx_handle h = new (std::nothrow) rx_handle_s();
+    if (!h) return RX_ENOMEM;
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)cfg->cuda_stream;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        delete h;
+        return RX_ECUDA;
+    }
+    std::string e;
+    h->tables = rxh::tables_for_device(cfg->device, e);
+    if (!h->tables) {
+        delete h;
+        return RX_ECUDA;
+    }
+    const size_t C = cfg->max_channels, T = cfg->max_taps;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    size_t o_theta = take(C * 4), o_w = take(C * 4), o_phi = take(C * 8), o_r = take(C * 8),
+           o_prn = take(C * 4), o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8),
+           o_ep = take(C * 4), o_taps = take(C * T * 8), o_acc = take(C * T * 8),
+           o_stage = take(2 * (size_t)cfg->max_block_samples + 64);
+    if (cudaMalloc(&h->d_block, off) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return RX_ENOMEM;
+    }
+    char *b = (char *)h->d_block;
+    h->st.theta = (uint32_t *)(b + o_theta);
+    h->st.w = (int32_t *)(b + o_w);
+    h->st.phi = (uint64_t *)(b + o_phi);
+    h->st.r = (uint64_t *)(b + o_r);
+    h->st.prn = (uint32_t *)(b + o_prn);
+    h->st.v = (double *)(b + o_v);
+    h->st.fcarr = (double *)(b + o_fc);
+    h->st.fcode = (double *)(b + o_fk);
+    h->st.epochs = (uint32_t *)(b + o_ep);
+    h->st.taps = (int64_t *)(b + o_taps);
+    h->st.acc = (int32_t *)(b + o_acc);
+    h->d_stage = (int8_t *)(b + o_stage);
+    if (cudaMemsetAsync(h->d_block, 0, off, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->d_block);
+        delete h;
+        return RX_ECUDA;
+    }
+    *out = h;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_destroy(rx_handle h) {
+    if (!h) return RX_OK;
+    cudaSetDevice(h->cfg.device);
+    cudaStreamSynchronize(h->stream);
+    if (h->d_block) cudaFree(h->d_block);
+    cudaGetLastError();
+    delete h;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn,
+                                     const int32_t *carrier_word, const uint64_t *code_phase_word,
+                                     const uint64_t *code_rate_word, const int64_t *tap_offsets,
+                                     uint32_t ntaps) {
+    if (!h) return RX_EINVAL;
+    if (!prn || !carrier_word || !code_phase_word || !code_rate_word || !tap_offsets)
+        return set_err(h, RX_EINVAL, "null array");
+    if (n == 0 || n > h->cfg.max_channels || ntaps == 0 || ntaps > h->cfg.max_taps)
+        return set_err(h, RX_EINVAL, rxh::fmt("n=%u ntaps=%u outside the handle's limits", n, ntaps));
+    if ((uint32_t)h->cfg.tap_early >= ntaps || (uint32_t)h->cfg.tap_prompt >= ntaps ||
+        (uint32_t)h->cfg.tap_late >= ntaps)
+        return set_err(h, RX_EINVAL, "E/P/L tap index >= ntaps");
+    for (uint32_t c = 0; c < n; ++c) {
+        std::string m = rxh::check_channel(prn[c], code_rate_word[c], tap_offsets + (size_t)c * ntaps, ntaps);
+        if (!m.empty()) return set_err(h, RX_EINVAL, rxh::fmt("channel %u: %s", c, m.c_str()));
+    }
+    const double fs = h->cfg.fs_hz;
+    std::vector<uint32_t> theta(n, 0), vprn(n), ep(n, 0);
+    std::vector<uint64_t> phi(n);
+    std::vector<double> v(n), fk(n);
+    for (uint32_t c = 0; c < n; ++c) {
+        vprn[c] = prn[c];
+        phi[c] = code_phase_word[c] % rxh::kCodeMod;
+        v[c] = rxh::carrier_word_to_hz(carrier_word[c], fs);
+        fk[c] = rxh::code_word_to_hz(code_rate_word[c], fs);
+    }
+    cudaSetDevice(h->cfg.device);
+    cudaStream_t s = h->stream;
+    std::string &E = h->err;
+    // Synchronous copies from pageable memory: the call's inputs may be freed on return.
+    RX_CUDA_TRY(cudaStreamSynchronize(s), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.theta, theta.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.w, carrier_word, n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.phi, phi.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.r, code_rate_word, n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.prn, vprn.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.v, v.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.fcarr, v.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.fcode, fk.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.epochs, ep.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.taps, tap_offsets, (size_t)n * ntaps * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemset(h->st.acc, 0, (size_t)n * ntaps * 8), E);
+    h->n_ch = n;
+    h->n_taps = ntaps;
+    h->n_since_fold = 0;
+    h->n_accum = 0;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp) {
+    if (!h) return RX_EINVAL;
+    if (h->n_ch == 0) return set_err(h, RX_ESTATE, "rx_set_channels has not been called");
+    if (!iq || nsamp == 0 || nsamp > h->cfg.max_block_samples)
+        return set_err(h, RX_EINVAL, rxh::fmt("nsamp=%u outside 1..%u", nsamp, h->cfg.max_block_samples));
+    cudaSetDevice(h->cfg.device);
+    std::string &E = h->err;
+    const int8_t *src = iq;
+    if (rxh::is_device_pointer(iq)) {
+        if (((uintptr_t)iq & 1) != 0) return set_err(h, RX_EINVAL, "device iq must be 2-byte aligned");
+    } else {
+        RX_CUDA_TRY(cudaMemcpyAsync(h->d_stage, iq, 2 * (size_t)nsamp, cudaMemcpyHostToDevice, h->stream), E);
+        RX_CUDA_TRY(cudaStreamSynchronize(h->stream), E);
+        src = h->d_stage;
+    }
+    if (h->n_since_fold + nsamp > kFoldLimit) {
+        k_plain_fold<<<(h->n_ch + 127) / 128, 128, 0, h->stream>>>(h->st, h->n_ch, h->n_since_fold);
+        RX_CUDA_TRY(cudaGetLastError(), E);
+        h->n_since_fold = 0;
+    }
+    const uint32_t per_cta = kPlainThreads * SPT;
+    dim3 grid((nsamp + per_cta - 1) / per_cta, h->n_ch);
+    size_t smem = (size_t)h->n_taps * 8 + 64 * 4 + EXT_WORDS * 4 + (size_t)h->n_taps * 8;
+    const bool a16 = ((uintptr_t)src & 15) == 0, a4 = ((uintptr_t)src & 3) == 0;
+    k_plain_correlate<<<grid, kPlainThreads, smem, h->stream>>>(src, nsamp, h->n_since_fold, a16, a4, h->st,
+                                                                 h->n_taps, h->tables->code,
+                                                                 h->tables->tab);
+    RX_CUDA_TRY(cudaGetLastError(), E);
+    h->n_since_fold += nsamp;
+    h->n_accum += nsamp;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_track_epoch(rx_handle h) {
+    if (!h) return RX_EINVAL;
+    if (h->n_ch == 0 || h->n_accum == 0)
+        return set_err(h, RX_ESTATE, "no samples correlated since the last boundary");
+    cudaSetDevice(h->cfg.device);
+    k_plain_track<<<(h->n_ch + 63) / 64, 64, 0, h->stream>>>(
+        h->st, h->n_ch, h->n_taps, h->n_since_fold, h->n_accum, h->cfg.fs_hz, h->cfg.pll_bn_hz,
+        h->cfg.dll_bn_hz, h->cfg.tap_early, h->cfg.tap_prompt, h->cfg.tap_late);
+    RX_CUDA_TRY(cudaGetLastError(), h->err);
+    h->n_since_fold = 0;
+    h->n_accum = 0;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_read_accumulators(rx_handle h, int32_t *out, uint32_t cap,
+                                          uint64_t *n_accum) {
+    if (!h || !out) return RX_EINVAL;
+    size_t need = (size_t)h->n_ch * h->n_taps * 2;
+    if (cap < need) return set_err(h, RX_EINVAL, rxh::fmt("cap %u < %zu", cap, need));
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaMemcpyAsync(out, h->st.acc, need * 4, cudaMemcpyDeviceToHost, h->stream), h->err);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    if (n_accum) *n_accum = h->n_accum;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_write_accumulators(rx_handle h, const int32_t *in, uint32_t count,
+                                           uint64_t n_accum) {
+    if (!h || !in) return RX_EINVAL;
+    size_t need = (size_t)h->n_ch * h->n_taps * 2;
+    if (count != need) return set_err(h, RX_EINVAL, rxh::fmt("count %u != %zu", count, need));
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    RX_CUDA_TRY(cudaMemcpy(h->st.acc, in, need * 4, cudaMemcpyHostToDevice), h->err);
+    h->n_accum = n_accum;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_read_state(rx_handle h, rx_channel_state *out, uint32_t cap) {
+    if (!h || !out) return RX_EINVAL;
+    if (cap < h->n_ch) return set_err(h, RX_EINVAL, "cap < channels");
+    const uint32_t n = h->n_ch;
+    std::vector<uint32_t> theta(n), prn(n), ep(n);
+    std::vector<int32_t> w(n);
+    std::vector<uint64_t> phi(n), r(n);
+    std::vector<double> v(n), fc(n), fk(n);
+    cudaSetDevice(h->cfg.device);
+    std::string &E = h->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), E);
+    RX_CUDA_TRY(cudaMemcpy(theta.data(), h->st.theta, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(w.data(), h->st.w, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(phi.data(), h->st.phi, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(r.data(), h->st.r, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(prn.data(), h->st.prn, n * 4, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(v.data(), h->st.v, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(fc.data(), h->st.fcarr, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(fk.data(), h->st.fcode, n * 8, cudaMemcpyDeviceToHost), E);
+    RX_CUDA_TRY(cudaMemcpy(ep.data(), h->st.epochs, n * 4, cudaMemcpyDeviceToHost), E);
+    const uint64_t k = h->n_since_fold;
+    for (uint32_t c = 0; c < n; ++c) {
+        rx_channel_state &s = out[c];
+        s.carrier_phase = theta[c] + (uint32_t)k * (uint32_t)w[c];
+        s.carrier_word = w[c];
+        unsigned __int128 p = (unsigned __int128)phi[c] + (unsigned __int128)k * r[c];
+        s.code_phase = (uint64_t)(p % rxh::kCodeMod);
+        s.code_rate = r[c];
+        s.pll_integrator_hz = v[c];
+        s.carrier_hz = fc[c];
+        s.code_hz = fk[c];
+        s.prn = prn[c];
+        s.epochs = ep[c];
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_write_state(rx_handle h, const rx_channel_state *in, uint32_t n) {
+    if (!h || !in) return RX_EINVAL;
+    if (n != h->n_ch || n == 0) return set_err(h, RX_ESTATE, "n must equal the channels set");
+    std::vector<uint32_t> theta(n), prn(n), ep(n);
+    std::vector<int32_t> w(n);
+    std::vector<uint64_t> phi(n), r(n);
+    std::vector<double> v(n), fc(n), fk(n);
+    cudaSetDevice(h->cfg.device);
+    std::string &E = h->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), E);
+    RX_CUDA_TRY(cudaMemcpy(prn.data(), h->st.prn, n * 4, cudaMemcpyDeviceToHost), E);
+    for (uint32_t c = 0; c < n; ++c) {
+        if (in[c].prn != prn[c]) return set_err(h, RX_EINVAL, rxh::fmt("channel %u: PRN mismatch", c));
+        if (in[c].code_rate >= (1ull << 32)) return set_err(h, RX_EINVAL, "code rate word >= 2^32");
+        theta[c] = in[c].carrier_phase;
+        w[c] = in[c].carrier_word;
+        phi[c] = in[c].code_phase % rxh::kCodeMod;
+        r[c] = in[c].code_rate;
+        v[c] = in[c].pll_integrator_hz;
+        fc[c] = in[c].carrier_hz;
+        fk[c] = in[c].code_hz;
+        ep[c] = in[c].epochs;
+    }
+    RX_CUDA_TRY(cudaMemcpy(h->st.theta, theta.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.w, w.data(), n * 4, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.phi, phi.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.r, r.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.v, v.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.fcarr, fc.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.fcode, fk.data(), n * 8, cudaMemcpyHostToDevice), E);
+    RX_CUDA_TRY(cudaMemcpy(h->st.epochs, ep.data(), n * 4, cudaMemcpyHostToDevice), E);
+    h->n_since_fold = 0;
+    return RX_OK;
+}
+
+extern "C" const char *rx_last_error(rx_handle h) { return h ? h->err.c_str() : "null handle"; }

@@ -1,0 +1,303 @@
+"""Thin Python binding of librx (include/rx.h): same function names, argument
+marshalling only.  Every step of the correlator and loop filter runs in the
+library's CUDA kernels; there is no CPU path.  PyTorch is used only for device
+buffers and streams (a torch tensor's data_ptr() and a torch stream's handle are
+passed straight through).
+
+Importing this module does not build anything; `load()` raises if librx.so is
+missing, so a missing extension fails loudly instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librx.so")
+
+RX_OK, RX_EINVAL, RX_ENOMEM, RX_EBUDGET, RX_ECUDA, RX_ETIMEOUT, RX_ESTATE, RX_EAGAIN = range(8)
+RX_RUN_RESTART = 1
+RX_RUN_NO_GRAPH = 2
+
+
+class RxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class rx_config(C.Structure):
+    _fields_ = [("fs_hz", C.c_double), ("max_block_samples", C.c_uint32),
+                ("max_channels", C.c_uint32), ("max_taps", C.c_uint32),
+                ("pll_bn_hz", C.c_double), ("dll_bn_hz", C.c_double),
+                ("tap_early", C.c_int32), ("tap_prompt", C.c_int32), ("tap_late", C.c_int32),
+                ("device", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class rx_channel_state(C.Structure):
+    _fields_ = [("carrier_phase", C.c_uint32), ("carrier_word", C.c_int32),
+                ("code_phase", C.c_uint64), ("code_rate", C.c_uint64),
+                ("pll_integrator_hz", C.c_double), ("carrier_hz", C.c_double),
+                ("code_hz", C.c_double), ("prn", C.c_uint32), ("epochs", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rx_receiver_desc(C.Structure):
+    _fields_ = [("fs_hz", C.c_double), ("block_samples", C.c_uint32),
+                ("n_channels", C.c_uint32), ("n_taps", C.c_uint32),
+                ("integ_blocks", C.c_uint32), ("pll_bn_hz", C.c_double),
+                ("dll_bn_hz", C.c_double), ("tap_early", C.c_int32),
+                ("tap_prompt", C.c_int32), ("tap_late", C.c_int32)]
+
+
+# (name, restype, argtypes) for every symbol include/rx.h declares.
+P = C.c_void_p
+SIGNATURES = [
+    ("rx_status_string", C.c_char_p, [C.c_int]),
+    ("rx_create", C.c_int, [C.POINTER(rx_config), C.POINTER(P)]),
+    ("rx_destroy", C.c_int, [P]),
+    ("rx_set_channels", C.c_int, [P, C.c_uint32, P, P, P, P, P, C.c_uint32]),
+    ("rx_correlate", C.c_int, [P, P, C.c_uint32]),
+    ("rx_track_epoch", C.c_int, [P]),
+    ("rx_read_accumulators", C.c_int, [P, P, C.c_uint32, C.POINTER(C.c_uint64)]),
+    ("rx_write_accumulators", C.c_int, [P, P, C.c_uint32, C.c_uint64]),
+    ("rx_read_state", C.c_int, [P, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_write_state", C.c_int, [P, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_last_error", C.c_char_p, [P]),
+    ("rx_batch_create", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, C.c_uint32, C.c_int32,
+                                  P, C.POINTER(P)]),
+    ("rx_batch_destroy", C.c_int, [P]),
+    ("rx_batch_set_channels", C.c_int, [P, C.c_uint32, P, P, P, P, P]),
+    ("rx_batch_run", C.c_int, [P, P, P, C.c_uint32, C.c_uint32]),
+    ("rx_batch_sync", C.c_int, [P]),
+    ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
+    ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32]),
+    ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                     C.POINTER(C.c_uint32)]),
+    ("rx_batch_last_launches", C.c_uint32, [P]),
+    ("rx_batch_last_error", C.c_char_p, [P]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librx.so (built by build.py / __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librx.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["RX_OK", "RX_EINVAL", "RX_ENOMEM", "RX_EBUDGET", "RX_ECUDA", "RX_ETIMEOUT",
+             "RX_ESTATE", "RX_EAGAIN"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _ptr(a) -> int:
+    """Address of a C-contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _arr(x, dt) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x), dtype=dt)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------------------
+# plain form
+# ----------------------------------------------------------------------------
+
+def _check(h, s, err_fn):
+    if s != RX_OK:
+        msg = err_fn(h).decode() if h else ""
+        raise RxError(s, msg)
+
+
+def rx_create(fs_hz: float, max_block_samples: int, max_channels: int, max_taps: int,
+              pll_bn_hz: float = 15.0, dll_bn_hz: float = 1.0, tap_early: int = 2,
+              tap_prompt: int = 1, tap_late: int = 0, device: int = 0, stream=None):
+    lib = load()
+    cfg = rx_config(fs_hz, max_block_samples, max_channels, max_taps, pll_bn_hz, dll_bn_hz,
+                    tap_early, tap_prompt, tap_late, device, _stream_handle(stream))
+    h = P()
+    s = lib.rx_create(C.byref(cfg), C.byref(h))
+    if s != RX_OK:
+        raise RxError(s, "rx_create")
+    return h
+
+
+def rx_destroy(h) -> None:
+    load().rx_destroy(h)
+
+
+def rx_set_channels(h, prn, carrier_word, code_phase_word, code_rate_word, tap_offsets) -> None:
+    lib = load()
+    prn = _arr(prn, np.uint8)
+    n = prn.size
+    w = _arr(carrier_word, np.int32)
+    phi = _arr(code_phase_word, np.uint64)
+    r = _arr(code_rate_word, np.uint64)
+    taps = _arr(tap_offsets, np.int64).reshape(n, -1)
+    _check(h, lib.rx_set_channels(h, n, _ptr(prn), _ptr(w), _ptr(phi), _ptr(r), _ptr(taps),
+                                  taps.shape[1]), lib.rx_last_error)
+
+
+def rx_correlate(h, iq, nsamp: int | None = None) -> None:
+    """iq: int8 [nsamp, 2] numpy array (host) or torch tensor (host or CUDA)."""
+    lib = load()
+    if nsamp is None:
+        nsamp = (iq.numel() if hasattr(iq, "numel") else iq.size) // 2
+    _check(h, lib.rx_correlate(h, _ptr(iq), nsamp), lib.rx_last_error)
+
+
+def rx_track_epoch(h) -> None:
+    lib = load()
+    _check(h, lib.rx_track_epoch(h), lib.rx_last_error)
+
+
+def rx_read_accumulators(h, n_ch: int, n_taps: int, with_count: bool = False):
+    """Accumulators [n_ch, n_taps, 2]; with_count also returns the samples integrated."""
+    lib = load()
+    out = np.zeros((n_ch, n_taps, 2), np.int32)
+    n = C.c_uint64()
+    _check(h, lib.rx_read_accumulators(h, _ptr(out), out.size, C.byref(n)), lib.rx_last_error)
+    return (out, n.value) if with_count else out
+
+
+def rx_write_accumulators(h, acc, n_accum: int) -> None:
+    lib = load()
+    acc = _arr(acc, np.int32)
+    _check(h, lib.rx_write_accumulators(h, _ptr(acc), acc.size, n_accum), lib.rx_last_error)
+
+
+def rx_read_state(h, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_state * n_ch)()
+    _check(h, lib.rx_read_state(h, arr, n_ch), lib.rx_last_error)
+    return list(arr)
+
+
+def rx_write_state(h, states) -> None:
+    lib = load()
+    n = len(states)
+    arr = (rx_channel_state * n)(*states)
+    _check(h, lib.rx_write_state(h, arr, n), lib.rx_last_error)
+
+
+def rx_last_error(h) -> str:
+    return load().rx_last_error(h).decode()
+
+
+# ----------------------------------------------------------------------------
+# batched form
+# ----------------------------------------------------------------------------
+
+def rx_batch_create(descs, max_blocks: int, device: int = 0, stream=None):
+    lib = load()
+    n = len(descs)
+    arr = (rx_receiver_desc * n)(*descs)
+    b = P()
+    s = lib.rx_batch_create(arr, n, max_blocks, device, _stream_handle(stream), C.byref(b))
+    if s != RX_OK:
+        raise RxError(s, "rx_batch_create")
+    return b
+
+
+def rx_batch_destroy(b) -> None:
+    load().rx_batch_destroy(b)
+
+
+def rx_batch_set_channels(b, rx: int, prn, carrier_word, code_phase_word, code_rate_word,
+                          tap_offsets) -> None:
+    lib = load()
+    prn = _arr(prn, np.uint8)
+    w = _arr(carrier_word, np.int32)
+    phi = _arr(code_phase_word, np.uint64)
+    r = _arr(code_rate_word, np.uint64)
+    taps = _arr(tap_offsets, np.int64)
+    _check(b, lib.rx_batch_set_channels(b, rx, _ptr(prn), _ptr(w), _ptr(phi), _ptr(r),
+                                        _ptr(taps)), lib.rx_batch_last_error)
+
+
+def rx_batch_run(b, iq, rx_byte_offset, n_blocks: int, flags: int = 0) -> None:
+    lib = load()
+    off = _arr(rx_byte_offset, np.uint64)
+    _check(b, lib.rx_batch_run(b, _ptr(iq), _ptr(off), n_blocks, flags), lib.rx_batch_last_error)
+
+
+def rx_batch_sync(b) -> None:
+    lib = load()
+    _check(b, lib.rx_batch_sync(b), lib.rx_batch_last_error)
+
+
+def rx_batch_read_dumps(b, rx: int, n_ch: int, n_taps: int, max_dumps: int) -> np.ndarray:
+    lib = load()
+    out = np.zeros((max_dumps, n_ch, n_taps, 2), np.int32)
+    nd = C.c_uint32()
+    _check(b, lib.rx_batch_read_dumps(b, rx, _ptr(out), out.size, C.byref(nd)),
+           lib.rx_batch_last_error)
+    return out[:nd.value]
+
+
+def rx_batch_read_state(b, rx: int, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_state * n_ch)()
+    _check(b, lib.rx_batch_read_state(b, rx, arr, n_ch), lib.rx_batch_last_error)
+    return list(arr)
+
+
+def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per_sm: int = 0):
+    lib = load()
+    _check(b, lib.rx_batch_set_tiles(b, channels_per_item, threads, ctas_per_sm),
+           lib.rx_batch_last_error)
+
+
+def rx_batch_get_tiles(b) -> tuple[int, int, int]:
+    lib = load()
+    a, t, c = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(b, lib.rx_batch_get_tiles(b, C.byref(a), C.byref(t), C.byref(c)),
+           lib.rx_batch_last_error)
+    return a.value, t.value, c.value
+
+
+def rx_batch_last_launches(b) -> int:
+    return int(load().rx_batch_last_launches(b))
+
+
+def rx_batch_last_error(b) -> str:
+    return load().rx_batch_last_error(b).decode()
+
+
+def receiver_desc(rx) -> rx_receiver_desc:
+    """rx_receiver_desc from a synth.Receiver-like object (fields fs, block_samples, ...)."""
+    return rx_receiver_desc(rx.fs, rx.block_samples, len(rx.channels), rx.n_taps,
+                            rx.integ_blocks, rx.pll_bn, rx.dll_bn, rx.tap_early, rx.tap_prompt,
+                            rx.tap_late)

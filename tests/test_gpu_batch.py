@@ -1,0 +1,173 @@
+"""GPU parity of the batched persistent kernel (rx_batch_* through the C ABI)
+against the CPU oracle, for the uniform, uneven and multi-correlator workloads:
+dumps and final loop state bit-exact; results independent of the batch mix,
+the tile shape, graph replay and host-vs-device input."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1907_00463_gb300 import rx, synth
+
+from helpers import assert_states_equal, batch_layout, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _pack(receivers, n_blocks):
+    offs, total = batch_layout(receivers)
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for rxr, o in zip(receivers, offs):
+        iq = synth.generate_iq(rxr, n_blocks * rxr.block_samples).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    return buf, offs, sigs
+
+
+def _batch(receivers, max_blocks, tiles=None):
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], max_blocks)
+    for i, r in enumerate(receivers):
+        rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+    if tiles:
+        rx.rx_batch_set_tiles(b, *tiles)
+    return b
+
+
+def _read(b, receivers, max_blocks):
+    out = []
+    for i, r in enumerate(receivers):
+        d = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, max_blocks // r.integ_blocks)
+        s = rx.rx_batch_read_state(b, i, len(r.channels))
+        out.append((d, s))
+    return out
+
+
+def _check_against_oracle(receivers, sigs, results, n_blocks):
+    for r, iq, (d, s) in zip(receivers, sigs, results):
+        od, os_ = oracle_run(r, iq, n_blocks)
+        assert d.shape == od.shape, (d.shape, od.shape)
+        assert np.array_equal(d, od), r.meta
+        assert_states_equal(s, os_)
+
+
+def test_uniform_batch_matches_oracle():
+    recv = [synth.uniform_receiver(i, n_blocks=12) for i in range(4)]
+    buf, offs, sigs = _pack(recv, 12)
+    b = _batch(recv, 12)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 12)
+        res = _read(b, recv, 12)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 12)
+
+
+def test_uneven_batch_matches_oracle():
+    recv = [synth.uneven_receiver(i, n_blocks=40) for i in range(8)]
+    assert len({r.fs for r in recv}) >= 3 and len({r.integ_blocks for r in recv}) >= 3
+    buf, offs, sigs = _pack(recv, 40)
+    b = _batch(recv, 40)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 40)
+        res = _read(b, recv, 40)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 40)
+
+
+def test_multicorrelator_101_taps_matches_oracle():
+    recv = [synth.multicorrelator_receiver(i, n_blocks=3) for i in range(2)]
+    buf, offs, sigs = _pack(recv, 3)
+    b = _batch(recv, 3)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 3)
+        res = _read(b, recv, 3)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 3)
+
+
+def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
+    recv = [synth.uneven_receiver(i, n_blocks=20) for i in range(6)]
+    buf, offs, sigs = _pack(recv, 20)
+    dev = torch.from_numpy(buf).cuda()
+    results = []
+    for tiles in [None, (1, 128, 0), (3, 256, 2), (8, 512, 1)]:
+        b = _batch(recv, 20, tiles)
+        try:
+            rx.rx_batch_run(b, dev, offs, 20)
+            results.append(_read(b, recv, 20))
+        finally:
+            rx.rx_batch_destroy(b)
+    for other in results[1:]:
+        for (d0, _), (d1, _) in zip(results[0], other):
+            assert np.array_equal(d0, d1)
+    # receiver 4 alone
+    alone = [recv[4]]
+    b = _batch(alone, 20)
+    try:
+        o = np.array([0], np.uint64)
+        rx.rx_batch_run(b, torch.from_numpy(sigs[4].reshape(-1).copy()).cuda(), o, 20)
+        (d, _), = _read(b, alone, 20)
+    finally:
+        rx.rx_batch_destroy(b)
+    assert np.array_equal(d, results[0][4][0])
+
+
+def test_graph_replay_restart_continue_and_host_input():
+    recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
+    buf, offs, sigs = _pack(recv, 16)
+    dev = torch.from_numpy(buf).cuda()
+    b = _batch(recv, 16)
+    try:
+        # first half, then the second half continuing (device input, no graph)
+        half = [np.ascontiguousarray(s[:8 * r.block_samples]) for s, r in zip(sigs, recv)]
+        buf1, offs1 = np.zeros_like(buf), offs
+        for s, o in zip(half, offs):
+            buf1[int(o):int(o) + s.size] = s.reshape(-1)
+        rx.rx_batch_run(b, torch.from_numpy(buf1).cuda(), offs1, 8, rx.RX_RUN_NO_GRAPH)
+        buf2 = np.zeros_like(buf)
+        for s, r, o in zip(sigs, recv, offs):
+            tail = s[8 * r.block_samples:16 * r.block_samples].reshape(-1)
+            buf2[int(o):int(o) + tail.size] = tail
+        rx.rx_batch_run(b, buf2, offs, 8)          # host input, graph
+        cont = _read(b, recv, 16)
+        # full run twice from the start through the same graph
+        rx.rx_batch_run(b, dev, offs, 16, rx.RX_RUN_RESTART)
+        first = _read(b, recv, 16)
+        rx.rx_batch_run(b, dev, offs, 16, rx.RX_RUN_RESTART)
+        second = _read(b, recv, 16)
+        assert rx.rx_batch_last_launches(b) == 1
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, first, 16)
+    for x, y, z in zip(first, second, cont):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[0], z[0])
+
+
+def test_batch_invalid_arguments():
+    recv = [synth.uniform_receiver(0, n_blocks=2)]
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in recv], 4)
+    try:
+        buf = torch.zeros(2 * 2 * 16368, dtype=torch.int8, device="cuda")
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_run(b, buf, [0], 2)
+        assert e.value.status == rx.RX_ESTATE              # channels not set
+        rx.rx_batch_set_channels(b, 0, *synth.channel_arrays(recv[0]))
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_run(b, buf, [8], 2)
+        assert e.value.status == rx.RX_EINVAL              # misaligned offset
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_run(b, buf, [0], 5)
+        assert e.value.status == rx.RX_EINVAL              # beyond max_blocks
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 0, 200, 0)
+        assert e.value.status == rx.RX_EINVAL
+    finally:
+        rx.rx_batch_destroy(b)
