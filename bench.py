@@ -54,9 +54,9 @@ def layout(receivers):
     return np.array(offs, np.uint64), pos
 
 
-def workload(rank: int):
+def workload(rank: int, n_rx: int = N_RX, n_blocks: int = N_BLOCKS):
     from paper_1907_00463_gb300 import synth
-    return [synth.uniform_receiver(rank * N_RX + i, n_blocks=N_BLOCKS) for i in range(N_RX)]
+    return [synth.uniform_receiver(rank * N_RX + i, n_blocks=n_blocks) for i in range(n_rx)]
 
 
 def sample_channels(receivers, n_blocks=None) -> int:
@@ -169,10 +169,10 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     nrx = min(N_RX, cores)
     sub = receivers[:nrx]
-    # size one step for about 8 s of oracle work on this host
+    # size one step for about 5 s of oracle work on this host
     probe = synth.generate_iq(sub[0], 2 * sub[0].block_samples).numpy()
     t1 = oracle_sample(sub[:1], [probe], 2, 1) / 2
-    blocks = int(max(2, min(N_BLOCKS, 8.0 / max(t1, 1e-6))))
+    blocks = int(max(2, min(N_BLOCKS, 5.0 / max(t1, 1e-6))))
     iqs = [synth.generate_iq(r, blocks * r.block_samples).numpy() for r in sub]
     for _ in range(args.warmup):
         oracle_sample(sub, iqs, blocks, nrx)
@@ -247,7 +247,8 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1907_00463_gb300 import rx, synth
 
-    receivers = workload(rank)
+    receivers = workload(rank, args.receivers, args.blocks)
+    n_blocks = args.blocks
     offs, total = layout(receivers)
     buf = torch.zeros(total, dtype=torch.int8, device=dev)
     for r, o in zip(receivers, offs):
@@ -256,7 +257,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     stream = torch.cuda.Stream(dev)
-    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], N_BLOCKS, device=local,
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], n_blocks, device=local,
                            stream=stream)
     for i, r in enumerate(receivers):
         rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
@@ -264,7 +265,7 @@ def run_ours(args):
         rx.rx_batch_set_tiles(b, *[int(x) for x in args.tiles.split(",")])
 
     def step(src=buf):
-        rx.rx_batch_run(b, src, offs, N_BLOCKS, rx.RX_RUN_RESTART)
+        rx.rx_batch_run(b, src, offs, n_blocks, rx.RX_RUN_RESTART)
 
     for _ in range(args.warmup):
         step()
@@ -322,17 +323,17 @@ def run_ours(args):
     if not args.no_e2e:
         hbuf = torch.empty(total, dtype=torch.int8, pin_memory=True)
         hbuf.copy_(buf)
-        dumps = [np.zeros((N_BLOCKS, len(r.channels), r.n_taps, 2), np.int32) for r in receivers]
+        dumps = [np.zeros((n_blocks, len(r.channels), r.n_taps, 2), np.int32) for r in receivers]
         d2h = sum(d.nbytes for d in dumps)
-        rx.rx_batch_run(b, hbuf, offs, N_BLOCKS, rx.RX_RUN_RESTART)     # warm the staging path
+        rx.rx_batch_run(b, hbuf, offs, n_blocks, rx.RX_RUN_RESTART)     # warm the staging path
         rx.rx_batch_sync(b)
         n_e2e = max(1, min(3, args.steps))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            rx.rx_batch_run(b, hbuf, offs, N_BLOCKS, rx.RX_RUN_RESTART)
+            rx.rx_batch_run(b, hbuf, offs, n_blocks, rx.RX_RUN_RESTART)
             for i, r in enumerate(receivers):
-                dumps[i] = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, N_BLOCKS)
+                dumps[i] = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, n_blocks)
         dt = (time.perf_counter() - t0) / n_e2e
         if world > 1:
             t = torch.tensor([dt], device=dev)
@@ -366,13 +367,14 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "64 receivers x 12 channels x 5 taps (VE/E/P/L/VL), int8 I/Q at "
-                               "16.368 MHz, 1 s per receiver, PLL 15 Hz / DLL 1 Hz closed every "
-                               "1 ms; one persistent launch per step",
-                   "receivers_per_gpu": N_RX, "blocks": N_BLOCKS, "channels": 12, "taps": 5,
+        "config": {"workload": f"{len(receivers)} receivers x 12 channels x 5 taps (VE/E/P/L/VL), "
+                               f"int8 I/Q at 16.368 MHz, {n_blocks} ms per receiver, PLL 15 Hz / "
+                               "DLL 1 Hz closed every 1 ms; one persistent launch per step",
+                   "receivers_per_gpu": len(receivers), "blocks": n_blocks, "channels": 12, "taps": 5,
                    "fs_hz": FS, "tiles": {"channels_per_item": tiles[0], "threads": tiles[1],
                                           "ctas_per_sm": tiles[2]},
-                   "l2": "inputs (2.1 GB per GPU) larger than L2; no flush",
+                   "l2": ("inputs larger than L2; no flush" if in_bytes > 129e6 else
+                          "inputs fit in L2 (profiling case only)"),
                    "parallelism": f"receivers sharded over {world} GPU(s), no collective"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved / peak_tops, "traffic": None,
@@ -403,6 +405,10 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--tiles", default="", help="channels_per_item,threads,ctas_per_sm")
+    p.add_argument("--receivers", type=int, default=N_RX,
+                   help="receivers per GPU (default: the full workload; smaller only for profiling)")
+    p.add_argument("--blocks", type=int, default=N_BLOCKS,
+                   help="1 ms blocks per receiver (default: the full second; smaller only for profiling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
