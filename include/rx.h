@@ -257,6 +257,53 @@ uint32_t rx_batch_last_launches(rx_batch b);
 
 const char *rx_batch_last_error(rx_batch b);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free batched tracking                                         */
+/* ------------------------------------------------------------------------ */
+
+/* The paper has no counterpart to this call.  It runs the batched closed-loop
+ * tracking of rx_batch_run for callers that cannot allocate GPU memory: a
+ * host with a fixed memory plan that forbids allocation once it is running
+ * (a real-time receiver loop), a plug-in that lives inside another program's
+ * allocator, or a program capturing a CUDA graph around the call.  It calls no
+ * cudaMalloc / cudaFree and no allocating library routine.  The caller passes
+ * every input and output buffer; the kernel's scratch (tickets, per-channel
+ * progress counters, the error word, the work table and multi-block running
+ * sums) lives in one fixed 4 MiB __device__ array inside librx, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   rx, n_rx      host array of receiver descriptors.  Limits per call: 1024
+ *                 receivers, 16384 channels and 131072 channel-taps in total;
+ *                 larger calls return RX_EINVAL.
+ *   iq            device samples (2-byte aligned); receiver r's n_blocks
+ *                 blocks start at iq + rx_byte_offset[r] (host array of n_rx
+ *                 offsets, each 16-byte aligned).
+ *   n_blocks      blocks per receiver, a multiple of every integ_blocks; the
+ *                 call starts at an integration boundary.
+ *   state         device array (8-byte aligned) of rx_channel_state, every
+ *                 channel of every receiver in order: read as the starting
+ *                 state, overwritten with the final state.  A new channel has
+ *                 carrier_phase 0, pll_integrator_hz = carrier_hz =
+ *                 carrier_word * fs / 2^32, code_hz = code_rate * fs / 2^32,
+ *                 epochs 0.
+ *   tap_offsets   device int64, each channel's n_taps offsets in order.
+ *   dumps         device int32 output; per receiver [n_blocks/L][C][T][2],
+ *                 receivers back to back.
+ * Synchronous: returns once the work has finished.  Returns RX_EINVAL for
+ * arguments beyond the limits and for device-resident inputs out of range (PRN
+ * outside 1..32, code rate >= 2^32, tap offset beyond 64 chips), RX_ETIMEOUT if
+ * a bounded device wait gave up, RX_ECUDA on a CUDA error.
+ * The first call on a device looks up the array's device address and loads the
+ * code tables into fixed device arrays, with that device current; make that
+ * first call before any stream capture.  All calls on a GPU share the one
+ * scratch array and each call re-initialises what it needs, so calls whose
+ * work overlaps on the same GPU race with each other. */
+rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
+                          const int8_t *iq, const uint64_t *rx_byte_offset,
+                          uint32_t n_blocks, rx_channel_state *state,
+                          const int64_t *tap_offsets, int32_t *dumps,
+                          int32_t device, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

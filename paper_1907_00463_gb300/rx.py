@@ -81,6 +81,8 @@ SIGNATURES = [
                                      C.POINTER(C.c_uint32)]),
     ("rx_batch_last_launches", C.c_uint32, [P]),
     ("rx_batch_last_error", C.c_char_p, [P]),
+    ("rx_track_static", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, P, P, C.c_uint32, P, P,
+                                  P, C.c_int32, P]),
 ]
 
 _lib = None
@@ -301,3 +303,21 @@ def receiver_desc(rx) -> rx_receiver_desc:
     return rx_receiver_desc(rx.fs, rx.block_samples, len(rx.channels), rx.n_taps,
                             rx.integ_blocks, rx.pll_bn, rx.dll_bn, rx.tap_early, rx.tap_prompt,
                             rx.tap_late)
+
+
+# ----------------------------------------------------------------------------
+# allocation-free batched tracking
+# ----------------------------------------------------------------------------
+
+def rx_track_static(descs, iq, rx_byte_offset, n_blocks: int, state, tap_offsets, dumps,
+                    device: int = 0, stream=None) -> None:
+    """iq, state (bytes of rx_channel_state records), tap_offsets and dumps are caller-owned
+    device tensors; descs and rx_byte_offset live on the host."""
+    lib = load()
+    n = len(descs)
+    arr = (rx_receiver_desc * n)(*descs)
+    off = _arr(rx_byte_offset, np.uint64)
+    s = lib.rx_track_static(arr, n, _ptr(iq), _ptr(off), n_blocks, _ptr(state), _ptr(tap_offsets),
+                            _ptr(dumps), device, _stream_handle(stream))
+    if s != RX_OK:
+        raise RxError(s, "rx_track_static")
