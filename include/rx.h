@@ -240,22 +240,141 @@ rx_status rx_batch_read_dumps(rx_batch b, uint32_t rx, int32_t *out,
 rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
                               uint32_t cap);
 
+#define RX_SCHED_DYNAMIC 0u  /* work items (channel group, block) by atomic ticket */
+#define RX_SCHED_STATIC 1u   /* one CTA per channel group for the whole run */
+
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
- * correlated together by one CTA per block (0 = choose); threads: CTA size
- * (128, 256 or 512; 0 = choose); ctas_per_sm: resident CTAs per SM (0 =
- * choose).  Takes effect at the next run (the graph is re-recorded). */
+ * correlated together by one CTA (0 = choose); threads: CTA size (128, 256 or
+ * 512; 0 = choose); ctas_per_sm: resident CTAs per SM for the dynamic
+ * schedule (0 = as many as fit); schedule: RX_SCHED_DYNAMIC or
+ * RX_SCHED_STATIC.  Both schedules give identical results.  Takes effect at
+ * the next run (the graph is re-recorded). */
 rx_status rx_batch_set_tiles(rx_batch b, uint32_t channels_per_item,
-                             uint32_t threads, uint32_t ctas_per_sm);
+                             uint32_t threads, uint32_t ctas_per_sm,
+                             uint32_t schedule);
 
 /* Read back the tiles in use (after the first run or set_tiles). */
 rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
-                             uint32_t *threads, uint32_t *ctas_per_sm);
+                             uint32_t *threads, uint32_t *ctas_per_sm,
+                             uint32_t *schedule);
 
 /* Number of kernel launches the last rx_batch_run issued (graph nodes
  * included), for accounting. */
 uint32_t rx_batch_last_launches(rx_batch b);
 
 const char *rx_batch_last_error(rx_batch b);
+
+/* ------------------------------------------------------------------------ */
+/* Serving form: continuous batching of 1 ms blocks from many streams        */
+/* ------------------------------------------------------------------------ */
+/* The paper's producer/consumer loops (Sec. 3.2-3.3, Figs. 10-11): blocks are
+ * pushed as they arrive; a service thread inside the library launches one
+ * persistent-kernel "tick" over every waiting block of every stream whenever
+ * blocks wait (at most two ticks in flight, so blocks arriving during a tick
+ * join the next).  Each stream's NCO, loop and accumulator state stays in
+ * device memory between ticks.  Streams are admitted while their state fits
+ * in a fixed device-memory budget and queued (FIFO) otherwise. */
+
+typedef struct {
+    uint32_t max_streams;             /* stream slots */
+    uint32_t max_channels_per_stream;
+    uint32_t max_taps;
+    uint32_t max_block_samples;       /* largest block of any stream */
+    uint32_t ring_blocks;             /* blocks that can wait (pinned + device ring) */
+    uint32_t dump_slots;              /* per-stream ring of the latest dumps */
+    uint32_t channels_per_item;       /* channels per work item (0 = 2) */
+    int32_t device;
+    uint64_t hbm_budget_bytes;        /* device pool for per-stream state and dumps */
+} rx_serve_config;
+
+typedef struct rx_serve_s *rx_serve;
+
+typedef struct {
+    uint64_t blocks_done;             /* since the last reset */
+    uint64_t deadline_misses;         /* blocks whose latency exceeded 1 ms */
+    uint64_t dropped_blocks;          /* pushes refused because the ring was full */
+    uint64_t ticks;
+    double mean_items_per_tick;
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* push -> completion latency */
+    uint32_t active_streams, queued_streams;
+    uint64_t active_channels;
+    uint64_t pool_bytes_used, pool_bytes_total;
+    uint32_t device_timeouts;
+} rx_serve_stats;
+
+/* Create a server (allocates the budget pool, rings, and starts its service
+ * thread on its own CUDA stream). */
+rx_status rx_serve_create(const rx_serve_config *cfg, rx_serve *out);
+
+/* Stop the service thread after the waiting blocks are processed; free all. */
+rx_status rx_serve_destroy(rx_serve s);
+
+/* Admit a stream with its starting channel state (arrays as in
+ * rx_set_channels).  *id receives the stream id in both outcomes: RX_OK = the
+ * stream is active; RX_EBUDGET = it is queued and becomes active by itself
+ * when released streams free enough of the budget (FIFO). */
+rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *desc, const uint8_t *prn,
+                         const int32_t *carrier_word, const uint64_t *code_phase_word,
+                         const uint64_t *code_rate_word, const int64_t *tap_offsets,
+                         uint32_t *id);
+
+/* The stream leaves: it takes no more blocks and its memory is returned once
+ * its waiting blocks are processed. */
+rx_status rx_serve_release(rx_serve s, uint32_t id);
+
+/* Queue the stream's next block (2*N int8 of host memory, copied before
+ * return).  RX_EAGAIN if the ring is full or the stream is still queued. */
+rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block);
+
+/* Block until every pushed block has been processed. */
+rx_status rx_serve_drain(rx_serve s);
+
+rx_status rx_serve_get_stats(rx_serve s, rx_serve_stats *out);
+rx_status rx_serve_reset_stats(rx_serve s);
+
+/* state: 0 free, 1 queued, 2 active, 3 leaving. */
+rx_status rx_serve_stream_status(rx_serve s, uint32_t id, uint32_t *state,
+                                 uint64_t *pushed, uint64_t *done);
+
+/* The stream's latest dumps, oldest first, int32 [n][C][T][2] (at most
+ * dump_slots of them); drains first. */
+rx_status rx_serve_read_dumps(rx_serve s, uint32_t id, int32_t *out, size_t cap,
+                              uint32_t *n_dumps);
+
+rx_status rx_serve_read_state(rx_serve s, uint32_t id, rx_channel_state *out,
+                              uint32_t cap);
+
+const char *rx_serve_last_error(rx_serve s);
+
+/* Replay of recorded streams (the receiver's offline "simulation" mode,
+ * Sec. 3): each stream's blocks arrive as a Poisson process; producers run on
+ * host threads and push through rx_serve_push. */
+typedef struct {
+    const rx_receiver_desc *desc;
+    const uint8_t *prn;
+    const int32_t *carrier_word;
+    const uint64_t *code_phase_word;
+    const uint64_t *code_rate_word;
+    const int64_t *tap_offsets;
+    const int8_t *recording;          /* rec_blocks blocks of 2*N int8 (host) */
+    uint32_t rec_blocks;
+    uint32_t max_blocks;              /* blocks to send; 0 = loop until the end */
+    uint32_t churn;                   /* 1 = may leave and rejoin (fresh state) */
+} rx_replay_stream;
+
+typedef struct {
+    double rate_hz;                   /* mean arrivals per second per stream */
+    double rate_jitter;               /* stream rate = rate_hz * U(1-j, 1+j), 0 <= j < 1 */
+    double duration_s;
+    double churn_per_s;               /* leave-and-rejoin events per second */
+    uint64_t seed;
+    uint32_t producer_threads;        /* 0 = 4 */
+} rx_replay_config;
+
+/* Admit the n streams, run the arrival processes for duration_s, then drain.
+ * ids_out (optional, n entries) receives each stream's final id. */
+rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *streams, uint32_t n,
+                          const rx_replay_config *cfg, uint32_t *ids_out);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free batched tracking                                         */

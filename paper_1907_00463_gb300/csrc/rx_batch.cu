@@ -24,28 +24,12 @@
 #include <string>
 #include <vector>
 
-#include "rx_device.cuh"
 #include "rx_internal.h"
+#include "rx_item.cuh"
 
 using namespace rxd;
 
 namespace {
-
-struct GroupDesc {
-    uint32_t rx;          // receiver index
-    uint32_t ch0;         // global index of the group's first channel
-    uint32_t nch;         // channels in the group
-    uint32_t ntaps;
-    uint32_t N;           // samples per block
-    uint32_t L;           // blocks per integration
-    int32_t tap_e, tap_p, tap_l;
-    uint32_t rx_nch;      // channels of the receiver (dump row length)
-    uint32_t ch_in_rx;    // index of ch0 inside its receiver
-    uint32_t max_dumps;   // dump slots per channel
-    uint64_t tap_base;    // index of channel ch0's first tap in the global tap array
-    uint64_t dump_base;   // index (int32 elements) of the receiver's dump 0
-    double fs, pll_bn, dll_bn;
-};
 
 // Mutable per-channel state: one contiguous block so that a restart is one copy.
 struct BatchState {
@@ -59,24 +43,14 @@ struct BatchState {
     int32_t *acc;          // [tap_base*2 ...]: running sums when L > 1
 };
 
-struct BatchConst {
-    const uint32_t *prn;
-    const int64_t *taps;
+struct BatchArgs {
     const GroupDesc *groups;
-    const uint64_t *rx_off;   // byte offset of each receiver's samples
-    int32_t *dumps;
-    const uint32_t *code_tab;
-    const uint32_t *carrier_tab;
-};
-
-struct BatchScratch {
-    uint32_t *ticket;
-    uint32_t *done;   // [G]
-    uint32_t *err;    // [4]: code, ticket, group, block
-};
-
-struct RunArgs {
+    const uint64_t *src_off;  // byte offset of each receiver's samples
     const int8_t *iq;
+    Tables tb;
+    uint32_t *ticket;
+    uint32_t *done;           // [G]
+    uint32_t *err;            // [4]: code, ticket, group, block
     uint32_t n_blocks;
     uint32_t G;
     uint32_t cpg;
@@ -84,197 +58,141 @@ struct RunArgs {
     uint64_t timeout_ns;
 };
 
-constexpr uint32_t kErrTimeout = 1;
-
-template <int TT, int NT>
-__device__ __forceinline__ void item_group(const int8_t *blk, uint32_t N, bool a16, bool a4,
-                                           uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
-                                           const int64_t *s_taps, const uint32_t *s_code,
-                                           const uint32_t *s_tab, int32_t *s_red) {
-    int32_t sI = 0, sQ = 0, mI[TT], mQ[TT];
-#pragma unroll
-    for (int k = 0; k < TT; ++k) mI[k] = mQ[k] = 0;
-    const uint32_t nchunks = (N + SPT - 1) / SPT;
-    for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
-        const uint32_t s0 = j * SPT;
-        uint32_t x[SPT];
-        load_chunk(blk, s0, N, a16, a4, x);
-        const uint32_t th0 = theta + s0 * w;
-        const uint64_t ph0 = reduce_code_phase(phi + (uint64_t)s0 * r);
-        corr_chunk<TT>(x, th0, w, ph0, r, s_taps, s_code, s_tab, sI, sQ, mI, mQ);
-    }
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < TT; ++k) {
-        uint32_t vi = __reduce_add_sync(0xffffffffu, (uint32_t)sI + 2u * (uint32_t)mI[k]);
-        uint32_t vq = __reduce_add_sync(0xffffffffu, (uint32_t)sQ + 2u * (uint32_t)mQ[k]);
-        if (lane == 0) {
-            atomicAdd((unsigned *)&s_red[2 * k], vi);
-            atomicAdd((unsigned *)&s_red[2 * k + 1], vq);
-        }
-    }
-}
-
+// Persistent kernel: items t = b * G + g in ticket order.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchState st, BatchConst kc, BatchScratch sc,
-                                              RunArgs a) {
+__global__ void __launch_bounds__(NT) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t cpg = a.cpg, mt = a.max_taps;
-    int64_t *s_taps = reinterpret_cast<int64_t *>(smem);                       // [cpg*mt]
-    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + (size_t)cpg * mt);  // [64]
-    uint32_t *s_code = s_tab + 64;                                              // [cpg][EXT]
-    int32_t *s_acc = reinterpret_cast<int32_t *>(s_code + (size_t)cpg * EXT_WORDS);  // [cpg*mt*2]
-    uint32_t *s_theta = reinterpret_cast<uint32_t *>(s_acc + (size_t)cpg * mt * 2);  // [cpg]
-    uint32_t *s_w = s_theta + cpg;
-    uint32_t *s_ab = s_w + cpg;                                                 // acc_blocks
-    uint64_t *s_phi = reinterpret_cast<uint64_t *>(s_ab + cpg + (cpg & 1));     // [cpg]
-    uint32_t *s_r = reinterpret_cast<uint32_t *>(s_phi + cpg);
+    const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
     __shared__ uint32_t s_ticket, s_abort;
-
-    for (uint32_t i = threadIdx.x; i < 64; i += NT) s_tab[i] = kc.carrier_tab[i];
+    for (uint32_t i = threadIdx.x; i < 64; i += NT) sm.tab[i] = a.tb.carrier[i];
     const uint32_t total = a.G * a.n_blocks;
-
     for (;;) {
-        __syncthreads();  // previous item fully consumed its shared state
-        if (threadIdx.x == 0) {
-            s_abort = 0;
-            s_ticket = atomicAdd(sc.ticket, 1u);
-        }
+        __syncthreads();  // the previous item has finished with shared memory
+        if (threadIdx.x == 0) s_ticket = atomicAdd(a.ticket, 1u);
         __syncthreads();
         const uint32_t t = s_ticket;
         if (t >= total) return;
         const uint32_t b = t / a.G, g = t - b * a.G;
-        const GroupDesc gd = kc.groups[g];
-
-        if (threadIdx.x == 0) {
-            // Bounded wait for item (b-1, g): time and iteration limits, then a
-            // recorded error instead of a hang.
-            const uint64_t t_start = globaltimer_ns();
-            uint32_t ns = 32;
-            for (uint32_t it = 0;; ++it) {
-                if (ld_acquire(sc.done + g) == b) break;
-                if (*(volatile uint32_t *)sc.err != 0) {
-                    s_abort = 1;
-                    break;
-                }
-                if (it > (1u << 24) || globaltimer_ns() - t_start > a.timeout_ns) {
-                    if (atomicCAS(sc.err, 0u, kErrTimeout) == 0u) {
-                        sc.err[1] = t;
-                        sc.err[2] = g;
-                        sc.err[3] = b;
-                    }
-                    s_abort = 1;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 1024) ns <<= 1;
-            }
-        }
+        if (threadIdx.x == 0) s_abort = wait_counter(a.done + g, b, a.err, a.timeout_ns, t, g);
         __syncthreads();
         if (s_abort) return;
-
-        // Stage the group's constants and state.
-        const uint32_t nch = gd.nch, nt = gd.ntaps;
-        for (uint32_t i = threadIdx.x; i < nch * nt; i += NT) s_taps[i] = kc.taps[gd.tap_base + i];
-        for (uint32_t i = threadIdx.x; i < nch * EXT_WORDS; i += NT) {
-            const uint32_t j = i / EXT_WORDS;
-            s_code[i] = kc.code_tab[(size_t)kc.prn[gd.ch0 + j] * EXT_WORDS + (i - j * EXT_WORDS)];
-        }
-        for (uint32_t i = threadIdx.x; i < nch * nt * 2; i += NT) s_acc[i] = 0;
-        for (uint32_t j = threadIdx.x; j < nch; j += NT) {
-            const uint32_t c = gd.ch0 + j;
-            s_theta[j] = __ldcg(st.theta + c);
-            s_w[j] = (uint32_t)__ldcg(st.w + c);
-            s_phi[j] = __ldcg((const unsigned long long *)st.phi + c);
-            s_r[j] = (uint32_t)__ldcg((const unsigned long long *)st.r + c);
-            s_ab[j] = __ldcg(st.acc_blocks + c);
-        }
-        __syncthreads();
-
-        const int8_t *blk = a.iq + kc.rx_off[gd.rx] + (size_t)b * 2 * gd.N;
-        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-        for (uint32_t j = 0; j < nch; ++j) {
-            const uint32_t theta = s_theta[j], w = s_w[j], r = s_r[j];
-            const uint64_t phi = s_phi[j];
-            const int64_t *tp = s_taps + (size_t)j * nt;
-            const uint32_t *cd = s_code + (size_t)j * EXT_WORDS;
-            int32_t *red = s_acc + (size_t)j * nt * 2;
-            for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
-                switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-                    case 1: item_group<1, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 2: item_group<2, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 3: item_group<3, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 4: item_group<4, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 5: item_group<5, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 6: item_group<6, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    case 7: item_group<7, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                    default: item_group<8, NT>(blk, gd.N, a16, a4, theta, w, phi, r, tp + t0, cd, s_tab, red + 2 * t0); break;
-                }
-            }
-        }
-        __syncthreads();
-
-        // Accumulate across blocks of an integration; dump at the boundary.
-        const uint32_t per_ch = nt * 2;
-        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
-            const uint32_t j = i / per_ch, e = i - j * per_ch;
-            const uint64_t ga = (gd.tap_base + (uint64_t)j * nt) * 2 + e;
-            uint32_t v = (uint32_t)s_acc[i];
-            if (s_ab[j] != 0) v += (uint32_t)__ldcg(st.acc + ga);
-            if (s_ab[j] + 1 == gd.L) {
-                const uint32_t ep = __ldcg(st.epochs + gd.ch0 + j);
-                if (ep < gd.max_dumps)
-                    kc.dumps[gd.dump_base +
-                             ((uint64_t)ep * gd.rx_nch + gd.ch_in_rx + j) * per_ch + e] = (int32_t)v;
-                s_acc[i] = (int32_t)v;
-            } else {
-                __stcg(st.acc + ga, (int32_t)v);
-            }
-        }
-        __syncthreads();
-
-        // Advance the NCOs over the block; close the loops at the boundary.
-        for (uint32_t j = threadIdx.x; j < nch; j += NT) {
-            const uint32_t c = gd.ch0 + j;
-            const uint32_t w = s_w[j];
-            __stcg(st.theta + c, s_theta[j] + gd.N * w);
-            __stcg((unsigned long long *)st.phi + c,
-                   (unsigned long long)reduce_code_phase(s_phi[j] + (uint64_t)gd.N * s_r[j]));
-            const uint32_t ab = s_ab[j] + 1;
-            if (ab == gd.L) {
-                const int32_t *A = s_acc + (size_t)j * per_ch;
-                const int64_t *tp = s_taps + (size_t)j * nt;
-                LoopOut o = loop_update(__ldcg(st.v + c), A[2 * gd.tap_e], A[2 * gd.tap_e + 1],
-                                        A[2 * gd.tap_p], A[2 * gd.tap_p + 1], A[2 * gd.tap_l],
-                                        A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.fs,
-                                        (uint64_t)gd.L * gd.N, gd.pll_bn, gd.dll_bn);
-                __stcg(st.v + c, o.v);
-                __stcg(st.fcarr + c, o.f_carr);
-                __stcg(st.fcode + c, o.f_code);
-                __stcg(st.w + c, o.w);
-                __stcg((unsigned long long *)st.r + c, (unsigned long long)o.r);
-                __stcg(st.epochs + c, __ldcg(st.epochs + c) + 1);
-                __stcg(st.acc_blocks + c, 0u);
-            } else {
-                __stcg(st.acc_blocks + c, ab);
-            }
-            __threadfence();
-        }
-        __syncthreads();
+        const GroupDesc gd = a.groups[g];
+        process_item<NT>(gd, a.iq + a.src_off[gd.src] + (size_t)b * 2 * gd.N, a.tb, sm);
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release(sc.done + g, b + 1);
+            st_release(a.done + g, b + 1);
         }
     }
 }
 
+struct StaticArgs {
+    const GroupDesc *groups;
+    const uint64_t *src_off;
+    const int8_t *iq;
+    Tables tb;
+    uint32_t n_blocks;
+    uint32_t cpg;
+    uint32_t max_taps;
+};
+
+// Static schedule: CTA g owns channel group g for the whole run.  The group's NCO
+// and loop state and its multi-block running sums stay in shared memory / registers
+// between blocks; the next block is prefetched into L2 while the current one is
+// correlated; state is written back once at the end.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch_static(StaticArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
+    int32_t *run = reinterpret_cast<int32_t *>(smem + item_smem_bytes(a.cpg, a.max_taps, NT));
+    uint32_t *s_ep = reinterpret_cast<uint32_t *>(run + (size_t)a.cpg * a.max_taps * 2);
+    const GroupDesc gd = a.groups[blockIdx.x];
+    const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
+    for (uint32_t i = threadIdx.x; i < 64; i += NT) sm.tab[i] = a.tb.carrier[i];
+    stage_constants<NT>(gd, a.tb, sm);
+    double v = 0.0, fc = 0.0, fk = 0.0;
+    if (threadIdx.x < nch) {
+        const uint32_t j = threadIdx.x;
+        sm.theta[j] = gd.theta[j];
+        sm.w[j] = (uint32_t)gd.w[j];
+        sm.phi[j] = gd.phi[j];
+        sm.r[j] = (uint32_t)gd.r[j];
+        sm.ab[j] = gd.acc_blocks[j];
+        s_ep[j] = gd.epochs[j];
+        v = gd.v[j];
+        fc = gd.fcarr[j];
+        fk = gd.fcode[j];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT)
+        run[i] = sm.ab[i / per_ch] ? gd.acc[i] : 0;
+    const int8_t *base = a.iq + a.src_off[gd.src];
+    for (uint32_t b = 0; b < a.n_blocks; ++b) {
+        const int8_t *blk = base + (size_t)b * 2 * N;
+        if (threadIdx.x == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
+        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
+        __syncthreads();
+        correlate_group<NT>(nch, nt, N, blk, sm, sm.acc);
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
+            const uint32_t j = i / per_ch, e = i - j * per_ch;
+            const uint32_t val = (uint32_t)sm.acc[i] + (uint32_t)run[i];
+            if (sm.ab[j] + 1 == gd.L) {
+                const uint32_t ep = s_ep[j];
+                if (gd.dump_wrap || ep < gd.dump_slots) {
+                    const uint32_t slot = gd.dump_wrap ? ep % gd.dump_slots : ep;
+                    gd.dumps[(uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch + e] = (int32_t)val;
+                }
+                sm.acc[i] = (int32_t)val;
+                run[i] = 0;
+            } else {
+                run[i] = (int32_t)val;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nch) {
+            const uint32_t j = threadIdx.x, w = sm.w[j];
+            sm.theta[j] = sm.theta[j] + N * w;
+            sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
+            const uint32_t ab = sm.ab[j] + 1;
+            if (ab == gd.L) {
+                const int32_t *A = sm.acc + (size_t)j * per_ch;
+                const int64_t *tp = sm.taps + (size_t)j * nt;
+                LoopOut o = loop_update(v, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
+                                        A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
+                                        tp[gd.tap_e], tp[gd.tap_l], gd.fs, (uint64_t)gd.L * N,
+                                        gd.pll_bn, gd.dll_bn);
+                v = o.v;
+                fc = o.f_carr;
+                fk = o.f_code;
+                sm.w[j] = (uint32_t)o.w;
+                sm.r[j] = (uint32_t)o.r;
+                s_ep[j] += 1;
+                sm.ab[j] = 0;
+            } else {
+                sm.ab[j] = ab;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < nch) {
+        const uint32_t j = threadIdx.x;
+        gd.theta[j] = sm.theta[j];
+        gd.w[j] = (int32_t)sm.w[j];
+        gd.phi[j] = sm.phi[j];
+        gd.r[j] = sm.r[j];
+        gd.acc_blocks[j] = sm.ab[j];
+        gd.epochs[j] = s_ep[j];
+        gd.v[j] = v;
+        gd.fcarr[j] = fc;
+        gd.fcode[j] = fk;
+    }
+    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) gd.acc[i] = run[i];
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-size_t batch_smem_bytes(uint32_t cpg, uint32_t mt) {
-    size_t s = (size_t)cpg * mt * 8 + 64 * 4 + (size_t)cpg * EXT_WORDS * 4 + (size_t)cpg * mt * 8;
-    s += (size_t)cpg * 4 * 3 + (cpg & 1) * 4;
-    s += (size_t)cpg * 8 + (size_t)cpg * 4;
-    return align_up(s, 16);
+size_t batch_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt_threads) {
+    return item_smem_bytes(cpg, mt, nt_threads);
 }
 
 }  // namespace
@@ -307,7 +225,7 @@ struct rx_batch_s {
     int8_t *d_stage = nullptr;
     size_t stage_bytes = 0;
     // tiles
-    uint32_t cpg = 0, threads = 0, ctas_per_sm = 0, G = 0, grid = 0;
+    uint32_t cpg = 0, threads = 0, ctas_per_sm = 0, G = 0, grid = 0, schedule = RX_SCHED_DYNAMIC;
     bool groups_dirty = true;
     // graph
     cudaGraphExec_t gexec = nullptr;
@@ -341,21 +259,62 @@ uint32_t default_cpg(const rx_batch b) {
     return best;
 }
 
+size_t static_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt) {
+    return item_smem_bytes(cpg, mt, nt) + (size_t)cpg * mt * 8 + (size_t)cpg * 4 + 16;
+}
+
 template <int NT>
-rx_status launch_nt(rx_batch b, const RunArgs &ra, BatchScratch sc, BatchConst kc, size_t smem) {
-    auto kern = k_batch<NT>;
+rx_status launch_static(rx_batch b, const StaticArgs &sa, size_t smem) {
+    auto kern = k_batch_static<NT>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<b->grid, NT, smem, b->stream>>>(b->st, kc, sc, ra);
+    kern<<<b->G, NT, smem, b->stream>>>(sa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(e)));
     return RX_OK;
 }
 
 template <int NT>
-int occupancy(size_t smem) {
+rx_status launch_nt(rx_batch b, const BatchArgs &ba, size_t smem) {
+    auto kern = k_batch<NT>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<b->grid, NT, smem, b->stream>>>(ba);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(e)));
+    return RX_OK;
+}
+
+template <int NT>
+int occupancy_static(size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_batch_static<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<NT>, NT, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_static<NT>, NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <int NT>
+int occupancy(size_t smem) {
+    // raise the kernel's dynamic shared-memory limit first, or the query reports 0
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_batch<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<NT>, NT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return n;
 }
 
@@ -366,9 +325,22 @@ rx_status build_groups(rx_batch b) {
     for (uint32_t r = 0; r < b->n_rx; ++r) {
         const rx_receiver_desc &d = b->rx[r];
         for (uint32_t c0 = 0; c0 < d.n_channels; c0 += b->cpg) {
+            const uint32_t ch = b->rx_ch0[r] + c0;
+            const uint64_t tap0 = b->rx_tap0[r] + (uint64_t)c0 * d.n_taps;
             GroupDesc g{};
-            g.rx = r;
-            g.ch0 = b->rx_ch0[r] + c0;
+            g.theta = b->st.theta + ch;
+            g.w = b->st.w + ch;
+            g.phi = b->st.phi + ch;
+            g.r = b->st.r + ch;
+            g.v = b->st.v + ch;
+            g.fcarr = b->st.fcarr + ch;
+            g.fcode = b->st.fcode + ch;
+            g.epochs = b->st.epochs + ch;
+            g.acc_blocks = b->st.acc_blocks + ch;
+            g.acc = b->st.acc + tap0 * 2;
+            g.prn = b->d_prn + ch;
+            g.taps = b->d_taps + tap0;
+            g.dumps = b->d_dumps + b->rx_dump0[r] + (uint64_t)c0 * d.n_taps * 2;
             g.nch = std::min(b->cpg, d.n_channels - c0);
             g.ntaps = d.n_taps;
             g.N = d.block_samples;
@@ -376,11 +348,10 @@ rx_status build_groups(rx_batch b) {
             g.tap_e = d.tap_early;
             g.tap_p = d.tap_prompt;
             g.tap_l = d.tap_late;
-            g.rx_nch = d.n_channels;
-            g.ch_in_rx = c0;
-            g.max_dumps = b->max_blocks / d.integ_blocks;
-            g.tap_base = b->rx_tap0[r] + (uint64_t)c0 * d.n_taps;
-            g.dump_base = b->rx_dump0[r];
+            g.dump_stride = d.n_channels * d.n_taps * 2;
+            g.dump_slots = b->max_blocks / d.integ_blocks;
+            g.dump_wrap = 0;
+            g.src = r;
             g.fs = d.fs_hz;
             g.pll_bn = d.pll_bn_hz;
             g.dll_bn = d.dll_bn_hz;
@@ -401,8 +372,13 @@ rx_status build_groups(rx_batch b) {
     b->G = (uint32_t)gs.size();
     RX_CUDA_TRY(cudaMalloc(&b->d_scratch, (5 + (size_t)b->G) * 4), E);
     RX_CUDA_TRY(cudaMemset(b->d_scratch, 0, (5 + (size_t)b->G) * 4), E);
-    size_t smem = batch_smem_bytes(b->cpg, b->max_taps);
+    size_t smem = batch_smem_bytes(b->cpg, b->max_taps, b->threads);
     int occ = b->threads == 128 ? occupancy<128>(smem) : b->threads == 512 ? occupancy<512>(smem) : occupancy<256>(smem);
+    if (b->schedule == RX_SCHED_STATIC) {
+        const size_t ss = static_smem_bytes(b->cpg, b->max_taps, b->threads);
+        occ = b->threads == 128 ? occupancy_static<128>(ss)
+                                : b->threads == 512 ? occupancy_static<512>(ss) : occupancy_static<256>(ss);
+    }
     if (occ <= 0) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
     uint32_t per_sm = b->ctas_per_sm ? std::min<uint32_t>(b->ctas_per_sm, occ) : (uint32_t)occ;
     b->ctas_per_sm = per_sm;
@@ -422,14 +398,34 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     if (flags & RX_RUN_RESTART)
         RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
     RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, (5 + (size_t)b->G) * 4, b->stream), E);
-    BatchScratch sc{b->d_scratch, b->d_scratch + 5, b->d_scratch + 1};
-    BatchConst kc{b->d_prn, b->d_taps, b->d_groups, b->d_rxoff, b->d_dumps, b->tables->code, b->tables->tab};
-    RunArgs ra{iq, n_blocks, b->G, b->cpg, b->max_taps, b->timeout_ns};
-    size_t smem = batch_smem_bytes(b->cpg, b->max_taps);
+    BatchArgs ba;
+    ba.groups = b->d_groups;
+    ba.src_off = b->d_rxoff;
+    ba.iq = iq;
+    ba.tb = Tables{b->tables->code, b->tables->tab, b->tables->pair};
+    ba.ticket = b->d_scratch;
+    ba.err = b->d_scratch + 1;
+    ba.done = b->d_scratch + 5;
+    ba.n_blocks = n_blocks;
+    ba.G = b->G;
+    ba.cpg = b->cpg;
+    ba.max_taps = b->max_taps;
+    ba.timeout_ns = b->timeout_ns;
     rx_status s;
-    if (b->threads == 128) s = launch_nt<128>(b, ra, sc, kc, smem);
-    else if (b->threads == 512) s = launch_nt<512>(b, ra, sc, kc, smem);
-    else s = launch_nt<256>(b, ra, sc, kc, smem);
+    if (b->schedule == RX_SCHED_STATIC) {
+        StaticArgs sa{b->d_groups, b->d_rxoff, iq, ba.tb, n_blocks, b->cpg, b->max_taps};
+        const size_t ss = static_smem_bytes(b->cpg, b->max_taps, b->threads);
+        if (b->threads == 128) s = launch_static<128>(b, sa, ss);
+        else if (b->threads == 512) s = launch_static<512>(b, sa, ss);
+        else s = launch_static<256>(b, sa, ss);
+        if (s != RX_OK) return s;
+        RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
+        return RX_OK;
+    }
+    size_t smem = batch_smem_bytes(b->cpg, b->max_taps, b->threads);
+    if (b->threads == 128) s = launch_nt<128>(b, ba, smem);
+    else if (b->threads == 512) s = launch_nt<512>(b, ba, smem);
+    else s = launch_nt<256>(b, ba, smem);
     if (s != RX_OK) return s;
     RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
     return RX_OK;
@@ -625,8 +621,11 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
     return RX_OK;
 }
 
-extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threads, uint32_t ctas_per_sm) {
+extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threads, uint32_t ctas_per_sm,
+                                        uint32_t schedule) {
     if (!b) return RX_EINVAL;
+    if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC)
+        return berr(b, RX_EINVAL, "unknown schedule");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return berr(b, RX_EINVAL, "threads must be 128, 256 or 512");
     if (cpg > 64) return berr(b, RX_EINVAL, "channels_per_item must be <= 64");
@@ -635,13 +634,15 @@ extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threa
     b->cpg = cpg;
     b->threads = threads;
     b->ctas_per_sm = ctas_per_sm;
+    b->schedule = schedule;
     b->groups_dirty = true;
     drop_graph(b);
     return RX_OK;
 }
 
-extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *threads, uint32_t *ctas) {
-    if (!b || !cpg || !threads || !ctas) return RX_EINVAL;
+extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *threads, uint32_t *ctas,
+                                        uint32_t *schedule) {
+    if (!b || !cpg || !threads || !ctas || !schedule) return RX_EINVAL;
     if (b->groups_dirty) {
         cudaSetDevice(b->device);
         rx_status s = build_groups(b);
@@ -650,6 +651,7 @@ extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *thr
     *cpg = b->cpg;
     *threads = b->threads;
     *ctas = b->ctas_per_sm;
+    *schedule = b->schedule;
     return RX_OK;
 }
 

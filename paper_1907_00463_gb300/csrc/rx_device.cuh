@@ -58,6 +58,15 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Hint the L2 to fetch [p, p + bytes): the 16-byte aligned interior of the range.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a))
+                     : "memory");
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -146,6 +155,120 @@ __device__ __forceinline__ void corr_chunk(const uint32_t (&x)[SPT], uint32_t th
             mI[k] += m * ip;
             mQ[k] += m * qp;
             pos[k] += r;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// chip-segment form of one chunk (same sums as corr_chunk, fewer operations)
+// ----------------------------------------------------------------------------
+//
+// The code replica is piecewise constant: when (S-1) r < 2^32 every tap stays on
+// one chip or crosses exactly one chip boundary within a run of S samples.  With
+// P_b = sum of the mixed samples 0..b-1 of the run and b the first sample on the
+// next chip (b = S if none),
+//   sum_i g_i I'_i = g(c0) P_b + g(c0+1) (P_S - P_b) = g(c0+1) P_S + (g(c0) - g(c0+1)) P_b.
+// The mixing is done once per sample for all taps; each tap then costs one exact
+// integer division for b, one prefix read and one chip-pair table read.  All sums
+// are int32 with wrap, so the result equals corr_chunk's bit for bit.
+
+constexpr int PAIR_BASE = 64;     // pair table entry of chip c is c + PAIR_BASE
+constexpr int PAIR_LEN = 1168;    // chips -64 .. 1103
+constexpr int SLICE_INT4 = 9;     // per-thread running-sum slice: 8 int4 + 1 pad (bank spread)
+
+// 16 if a 16-sample run crosses at most one chip boundary per tap, 8 if an 8-sample
+// run does, 0 if neither (the direct form is used then).
+__device__ __forceinline__ int seg_mode(uint32_t r) {
+    const uint64_t r64 = r;
+    return (r64 * 15u < (1ull << 32)) ? 16 : ((r64 * 7u < (1ull << 32)) ? 8 : 0);
+}
+
+// ceil(2^32 / r), r >= 2: floor(n * magic / 2^32) is floor(n / r) or one more.
+__device__ __forceinline__ uint32_t seg_magic(uint32_t r) {
+    return (uint32_t)(((1ull << 32) + r - 1) / r);
+}
+
+// Mix a chunk and store running sums: viewed as int2, entry e holds the sums of I', Q'
+// over samples 0..e of its run (S = 16: one run; S = 8: runs 0..7 and 8..15 restart).
+template <int S>
+__device__ __forceinline__ void seg_prefix(const uint32_t (&x)[SPT], uint32_t theta0, uint32_t w,
+                                           const uint32_t *tab, int4 *slice) {
+    uint32_t th = theta0;
+    int32_t sI = 0, sQ = 0;
+#pragma unroll
+    for (int i = 0; i < SPT; i += 2) {
+        if (S == 8 && i == 8) {
+            sI = 0;
+            sQ = 0;
+        }
+        const uint32_t e0 = tab[th >> 26];
+        th += w;
+        sI += __dp2a_lo((int)x[i], (int)e0, 0);
+        sQ += __dp2a_hi((int)x[i], (int)e0, 0);
+        const int32_t aI = sI, aQ = sQ;
+        const uint32_t e1 = tab[th >> 26];
+        th += w;
+        sI += __dp2a_lo((int)x[i + 1], (int)e1, 0);
+        sQ += __dp2a_hi((int)x[i + 1], (int)e1, 0);
+        slice[i >> 1] = make_int4(aI, aQ, sI, sQ);
+    }
+}
+
+template <int S, int TT>
+__device__ __forceinline__ void seg_run_taps(const int2 *pre, uint64_t phi0, uint32_t r,
+                                             uint32_t magic, const int64_t *off,
+                                             const uint16_t *pair, int32_t (&aI)[TT],
+                                             int32_t (&aQ)[TT]) {
+    const int2 tot = pre[S - 1];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const int64_t p = (int64_t)phi0 + off[k];
+        const int32_t c0 = (int32_t)(p >> 32);           // chip of sample 0
+        const uint32_t nf = ~(uint32_t)p;                 // 2^32 - 1 - fraction
+        // samples i >= 1 still on chip c0: i r <= nf; their count, capped at S - 1
+        uint32_t q = min(__umulhi(nf, magic), (uint32_t)(S - 1));
+        if (q * r > nf) q -= 1;
+        const int2 pb = pre[q];                            // P_b with b = q + 1
+        const uint32_t e = pair[c0 + PAIR_BASE];
+        const int32_t g1 = (int32_t)prmt(e, 0u, 0x8880u);  // g(c0 + 1)
+        const int32_t dg = (int32_t)prmt(e, 0u, 0x9991u);  // g(c0) - g(c0 + 1)
+        aI[k] += g1 * tot.x + dg * pb.x;
+        aQ[k] += g1 * tot.y + dg * pb.y;
+    }
+}
+
+// Taps of one chunk from its running sums; phi0 is the code phase of sample 0.
+template <int S, int TT>
+__device__ __forceinline__ void seg_taps(const int4 *slice, uint64_t phi0, uint32_t r,
+                                         uint32_t magic, const int64_t *off, const uint16_t *pair,
+                                         int32_t (&aI)[TT], int32_t (&aQ)[TT]) {
+    const int2 *pre = reinterpret_cast<const int2 *>(slice);
+    if (S == 16) {
+        seg_run_taps<16, TT>(pre, phi0, r, magic, off, pair, aI, aQ);
+    } else {
+        seg_run_taps<8, TT>(pre, phi0, r, magic, off, pair, aI, aQ);
+        seg_run_taps<8, TT>(pre + 8, phi0 + 8ull * r, r, magic, off, pair, aI, aQ);
+    }
+}
+
+// Taps of one tap group for one chunk, reduced over the warp and added to s_red
+// ([TT][2] int32 in shared memory).  Every lane of the warp must call it.
+template <int S, int TT>
+__device__ __forceinline__ void seg_group_reduce(const int4 *slice, uint64_t ph0, uint32_t r,
+                                                 uint32_t magic, const int64_t *s_taps,
+                                                 const uint16_t *s_pair, int32_t *s_red) {
+    int32_t aI[TT], aQ[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) aI[k] = aQ[k] = 0;
+    seg_taps<S, TT>(slice, ph0, r, magic, s_taps, s_pair, aI, aQ);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const uint32_t vi = __reduce_add_sync(0xffffffffu, (uint32_t)aI[k]);
+        const uint32_t vq = __reduce_add_sync(0xffffffffu, (uint32_t)aQ[k]);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&s_red[2 * k], vi);
+            atomicAdd((unsigned *)&s_red[2 * k + 1], vq);
         }
     }
 }

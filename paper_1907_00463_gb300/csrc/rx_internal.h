@@ -18,6 +18,7 @@ namespace rxh {
 struct DeviceTables {
     uint32_t *code = nullptr;   // device
     uint32_t *tab = nullptr;    // device
+    uint16_t *pair = nullptr;   // device, [33][PAIR_LEN] chip-pair entries
     int sm_count = 0;
     int max_smem_optin = 0;
 };
@@ -29,6 +30,9 @@ const DeviceTables *tables_for_device(int device, std::string &err);
 // Host copies of the tables (the same bits the device holds).
 void build_code_table(uint32_t *out /* [33][EXT_WORDS] */);
 void build_carrier_table(uint32_t *out /* [64] */);
+// Chip-pair table: entry c + PAIR_BASE (c in [-PAIR_BASE, PAIR_LEN - PAIR_BASE)) holds the
+// code values around chip c as int8 bytes: low byte g(c+1), next byte g(c) - g(c+1).
+void build_pair_table(uint16_t *out /* [33][PAIR_LEN] */);
 
 inline std::string fmt(const char *f, ...) {
     char buf[512];

@@ -1,0 +1,351 @@
+// One work item of the persistent kernels: correlate a channel group over one
+// block, fold the block into the group's integrate-and-dump sums, and at an
+// integration boundary dump the sums and close the loops (Table 3).  Shared by
+// the batched kernel (rx_batch.cu) and the serving kernel (rx_serve.cu).
+#pragma once
+
+#include "rx_device.cuh"
+
+namespace rxd {
+
+// A channel group's state, constants and outputs.  Every pointer is already
+// offset to the group's first channel; arrays are per channel (structure of
+// arrays), taps and running sums are [channel][tap] / [channel][tap][2].
+struct GroupDesc {
+    uint32_t *theta;      // carrier phase at the next block
+    int32_t *w;           // carrier word
+    uint64_t *phi;        // code phase at the next block, reduced
+    uint64_t *r;          // code word
+    double *v, *fcarr, *fcode;
+    uint32_t *epochs;     // integration boundaries passed
+    uint32_t *acc_blocks; // blocks folded into the running sums
+    int32_t *acc;         // running sums while an integration spans several blocks
+    const uint32_t *prn;
+    const int64_t *taps;
+    int32_t *dumps;       // dump slot 0, channel 0, tap 0, I
+    uint32_t nch, ntaps, N, L;
+    int32_t tap_e, tap_p, tap_l;
+    uint32_t dump_stride; // int32 elements from one dump slot to the next
+    uint32_t dump_slots;  // slots available
+    uint32_t dump_wrap;   // 1: slot = epoch mod dump_slots; 0: epochs past the last slot are dropped
+    uint32_t src;         // index into the sample-offset table
+    uint32_t pad;
+    double fs, pll_bn, dll_bn;
+};
+
+struct Tables {
+    const uint32_t *code;     // extended bit-packed C/A codes [33][EXT_WORDS]
+    const uint32_t *carrier;  // 64 packed (c, s, -s, c)
+    const uint16_t *pair;     // chip-pair entries [33][PAIR_LEN]
+};
+
+// Shared-memory carve-up for a CTA of NT threads handling at most cpg channels of
+// at most mt taps.
+struct ItemSmem {
+    int64_t *taps;     // [cpg * mt]
+    uint32_t *tab;     // [64]
+    uint32_t *code;    // [cpg][EXT_WORDS]
+    int32_t *acc;      // [cpg * mt * 2]
+    uint32_t *theta, *w, *ab, *r;  // [cpg]
+    uint64_t *phi;     // [cpg]
+    int4 *slices;      // [NT][SLICE_INT4]
+    uint16_t *pair;    // [cpg][PAIR_LEN]
+};
+
+__host__ __device__ inline size_t item_smem_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t item_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt) {
+    size_t s = (size_t)cpg * mt * 8 + 64 * 4 + (size_t)cpg * EXT_WORDS * 4 + (size_t)cpg * mt * 8;
+    s = item_smem_align(s + (size_t)cpg * 16) + (size_t)cpg * 8;
+    s = item_smem_align(s) + (size_t)nt * SLICE_INT4 * 16 + (size_t)cpg * PAIR_LEN * 2;
+    return item_smem_align(s);
+}
+
+__device__ inline ItemSmem carve_item_smem(unsigned char *base, uint32_t cpg, uint32_t mt, uint32_t nt) {
+    ItemSmem m;
+    size_t o = 0;
+    m.taps = reinterpret_cast<int64_t *>(base + o);
+    o += (size_t)cpg * mt * 8;
+    m.tab = reinterpret_cast<uint32_t *>(base + o);
+    o += 64 * 4;
+    m.code = reinterpret_cast<uint32_t *>(base + o);
+    o += (size_t)cpg * EXT_WORDS * 4;
+    m.acc = reinterpret_cast<int32_t *>(base + o);
+    o += (size_t)cpg * mt * 8;
+    m.theta = reinterpret_cast<uint32_t *>(base + o);
+    m.w = m.theta + cpg;
+    m.ab = m.w + cpg;
+    m.r = m.ab + cpg;
+    o = item_smem_align(o + (size_t)cpg * 16);
+    m.phi = reinterpret_cast<uint64_t *>(base + o);
+    o = item_smem_align(o + (size_t)cpg * 8);
+    m.slices = reinterpret_cast<int4 *>(base + o);
+    o += (size_t)nt * SLICE_INT4 * 16;
+    m.pair = reinterpret_cast<uint16_t *>(base + o);
+    return m;
+}
+
+template <int TT, int NT>
+__device__ __forceinline__ void item_direct(const int8_t *blk, uint32_t N, bool a16, bool a4,
+                                            uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
+                                            const int64_t *s_taps, const uint32_t *s_code,
+                                            const uint32_t *s_tab, int32_t *s_red) {
+    int32_t sI = 0, sQ = 0, mI[TT], mQ[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) mI[k] = mQ[k] = 0;
+    const uint32_t nchunks = (N + SPT - 1) / SPT;
+    for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
+        const uint32_t s0 = j * SPT;
+        uint32_t x[SPT];
+        load_chunk(blk, s0, N, a16, a4, x);
+        corr_chunk<TT>(x, theta + s0 * w, w, reduce_code_phase(phi + (uint64_t)s0 * r), r, s_taps,
+                       s_code, s_tab, sI, sQ, mI, mQ);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const uint32_t vi = __reduce_add_sync(0xffffffffu, (uint32_t)sI + 2u * (uint32_t)mI[k]);
+        const uint32_t vq = __reduce_add_sync(0xffffffffu, (uint32_t)sQ + 2u * (uint32_t)mQ[k]);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&s_red[2 * k], vi);
+            atomicAdd((unsigned *)&s_red[2 * k + 1], vq);
+        }
+    }
+}
+
+// Chip-segment form with all taps of one channel in registers across passes (T <= 8).
+template <int S, int TT, int NT>
+__device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16, bool a4,
+                                         uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
+                                         uint32_t magic, const int64_t *s_taps,
+                                         const uint16_t *s_pair, const uint32_t *s_tab,
+                                         int4 *slice, int32_t *s_red) {
+    int32_t aI[TT], aQ[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) aI[k] = aQ[k] = 0;
+    const uint32_t nchunks = (N + SPT - 1) / SPT;
+    for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
+        const uint32_t s0 = j * SPT;
+        uint32_t x[SPT];
+        load_chunk(blk, s0, N, a16, a4, x);
+        seg_prefix<S>(x, theta + s0 * w, w, s_tab, slice);
+        seg_taps<S, TT>(slice, reduce_code_phase(phi + (uint64_t)s0 * r), r, magic, s_taps, s_pair,
+                        aI, aQ);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const uint32_t vi = __reduce_add_sync(0xffffffffu, (uint32_t)aI[k]);
+        const uint32_t vq = __reduce_add_sync(0xffffffffu, (uint32_t)aQ[k]);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&s_red[2 * k], vi);
+            atomicAdd((unsigned *)&s_red[2 * k + 1], vq);
+        }
+    }
+}
+
+// Chip-segment form for many taps: a chunk's running sums are made once and shared
+// by every tap group, which reduces after each pass.
+template <int S, int NT>
+__device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, bool a16, bool a4,
+                                              uint32_t theta, uint32_t w, uint64_t phi,
+                                              uint32_t r, uint32_t magic, uint32_t nt,
+                                              const int64_t *s_taps, const uint16_t *s_pair,
+                                              const uint32_t *s_tab, int4 *slice,
+                                              int32_t *s_red) {
+    const uint32_t nchunks = (N + SPT - 1) / SPT;
+    const uint32_t npass = (nchunks + NT - 1) / NT;
+    for (uint32_t p = 0; p < npass; ++p) {
+        const uint32_t j = p * NT + threadIdx.x;
+        const uint32_t s0 = j * SPT;
+        uint32_t x[SPT];
+        if (j < nchunks) {
+            load_chunk(blk, s0, N, a16, a4, x);
+        } else {
+#pragma unroll
+            for (int i = 0; i < SPT; ++i) x[i] = 0u;
+        }
+        seg_prefix<S>(x, theta + s0 * w, w, s_tab, slice);
+        const uint64_t ph0 = reduce_code_phase(phi + (uint64_t)s0 * r);
+        for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
+            const int64_t *tp = s_taps + t0;
+            int32_t *red = s_red + 2 * t0;
+            switch (min((uint32_t)TAP_GROUP, nt - t0)) {
+                case 1: seg_group_reduce<S, 1>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 2: seg_group_reduce<S, 2>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 3: seg_group_reduce<S, 3>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 4: seg_group_reduce<S, 4>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 5: seg_group_reduce<S, 5>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 6: seg_group_reduce<S, 6>(slice, ph0, r, magic, tp, s_pair, red); break;
+                case 7: seg_group_reduce<S, 7>(slice, ph0, r, magic, tp, s_pair, red); break;
+                default: seg_group_reduce<S, 8>(slice, ph0, r, magic, tp, s_pair, red); break;
+            }
+        }
+    }
+}
+
+template <int S, int NT>
+__device__ __forceinline__ void channel_seg(const int8_t *blk, uint32_t N, bool a16, bool a4,
+                                            uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
+                                            uint32_t nt, const int64_t *tp, const uint16_t *pr,
+                                            const uint32_t *s_tab, int4 *slice, int32_t *red) {
+    const uint32_t mg = seg_magic(r);
+    switch (nt) {
+        case 1: item_seg<S, 1, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 2: item_seg<S, 2, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 3: item_seg<S, 3, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 4: item_seg<S, 4, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 5: item_seg<S, 5, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 6: item_seg<S, 6, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 7: item_seg<S, 7, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 8: item_seg<S, 8, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        default: item_seg_many<S, NT>(blk, N, a16, a4, theta, w, phi, r, mg, nt, tp, pr, s_tab, slice, red); break;
+    }
+}
+
+// Bounded wait (thread 0 only) until *counter == want.  Returns 0 when satisfied, 1 if
+// another CTA already flagged an error, 2 after recording a timeout in err[0..3].
+__device__ inline int wait_counter(const uint32_t *counter, uint32_t want, uint32_t *err,
+                                   uint64_t timeout_ns, uint32_t ticket, uint32_t group) {
+    const uint64_t t_start = globaltimer_ns();
+    uint32_t ns = 32;
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire(counter) == want) return 0;
+        if (*(volatile uint32_t *)err != 0) return 1;
+        if (it > (1u << 24) || globaltimer_ns() - t_start > timeout_ns) {
+            if (atomicCAS(err, 0u, 1u) == 0u) {
+                err[1] = ticket;
+                err[2] = group;
+                err[3] = want;
+            }
+            return 2;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
+
+// Copy a group's constants (taps, bit-packed code, chip-pair table) into shared memory.
+template <int NT>
+__device__ __forceinline__ void stage_constants(const GroupDesc &gd, const Tables &tb,
+                                                const ItemSmem &sm) {
+    const uint32_t nch = gd.nch, nt = gd.ntaps;
+    for (uint32_t i = threadIdx.x; i < nch * nt; i += NT) sm.taps[i] = gd.taps[i];
+    for (uint32_t i = threadIdx.x; i < nch * EXT_WORDS; i += NT) {
+        const uint32_t j = i / EXT_WORDS;
+        sm.code[i] = tb.code[(size_t)gd.prn[j] * EXT_WORDS + (i - j * EXT_WORDS)];
+    }
+    for (uint32_t i = threadIdx.x; i < nch * (PAIR_LEN / 8); i += NT) {
+        const uint32_t j = i / (PAIR_LEN / 8), q = i - j * (PAIR_LEN / 8);
+        reinterpret_cast<uint4 *>(sm.pair + (size_t)j * PAIR_LEN)[q] =
+            reinterpret_cast<const uint4 *>(tb.pair + (size_t)gd.prn[j] * PAIR_LEN)[q];
+    }
+}
+
+// Correlate the group's channels over one block into red[channel][tap][2] (shared,
+// zeroed by the caller).  NCO state at the block start comes from sm.theta/w/phi/r.
+template <int NT>
+__device__ __forceinline__ void correlate_group(uint32_t nch, uint32_t nt, uint32_t N,
+                                                const int8_t *blk, const ItemSmem &sm,
+                                                int32_t *red_base) {
+    const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+    int4 *slice = sm.slices + threadIdx.x * SLICE_INT4;
+    for (uint32_t j = 0; j < nch; ++j) {
+        const uint32_t theta = sm.theta[j], w = sm.w[j], r = sm.r[j];
+        const uint64_t phi = sm.phi[j];
+        const int64_t *tp = sm.taps + (size_t)j * nt;
+        int32_t *red = red_base + (size_t)j * nt * 2;
+        const int mode = seg_mode(r);
+        if (mode == 16) {
+            channel_seg<16, NT>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
+                                sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
+        } else if (mode == 8) {
+            channel_seg<8, NT>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
+                               sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
+        } else {
+            const uint32_t *cd = sm.code + (size_t)j * EXT_WORDS;
+            for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
+                switch (min((uint32_t)TAP_GROUP, nt - t0)) {
+                    case 1: item_direct<1, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 2: item_direct<2, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 3: item_direct<3, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 4: item_direct<4, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 5: item_direct<5, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 6: item_direct<6, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    case 7: item_direct<7, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                    default: item_direct<8, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                }
+            }
+        }
+    }
+}
+
+// The item body: all threads of the CTA call it; the caller has waited for the
+// group's previous block and publishes the group's counter afterwards.  sm.tab must
+// already hold the carrier table.
+template <int NT>
+__device__ __forceinline__ void process_item(const GroupDesc &gd, const int8_t *blk,
+                                             const Tables &tb, const ItemSmem &sm) {
+    const uint32_t nch = gd.nch, nt = gd.ntaps;
+    stage_constants<NT>(gd, tb, sm);
+    for (uint32_t i = threadIdx.x; i < nch * nt * 2; i += NT) sm.acc[i] = 0;
+    for (uint32_t j = threadIdx.x; j < nch; j += NT) {
+        sm.theta[j] = __ldcg(gd.theta + j);
+        sm.w[j] = (uint32_t)__ldcg(gd.w + j);
+        sm.phi[j] = __ldcg((const unsigned long long *)gd.phi + j);
+        sm.r[j] = (uint32_t)__ldcg((const unsigned long long *)gd.r + j);
+        sm.ab[j] = __ldcg(gd.acc_blocks + j);
+    }
+    __syncthreads();
+    correlate_group<NT>(nch, nt, gd.N, blk, sm, sm.acc);
+    __syncthreads();
+
+    // Fold the block into the running sums; dump at the integration boundary.
+    const uint32_t per_ch = nt * 2;
+    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
+        const uint32_t j = i / per_ch, e = i - j * per_ch;
+        uint32_t v = (uint32_t)sm.acc[i];
+        if (sm.ab[j] != 0) v += (uint32_t)__ldcg(gd.acc + i);
+        if (sm.ab[j] + 1 == gd.L) {
+            const uint32_t ep = __ldcg(gd.epochs + j);
+            if (gd.dump_wrap || ep < gd.dump_slots) {
+                const uint32_t slot = gd.dump_wrap ? ep % gd.dump_slots : ep;
+                gd.dumps[(uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch + e] = (int32_t)v;
+            }
+            sm.acc[i] = (int32_t)v;
+        } else {
+            __stcg(gd.acc + i, (int32_t)v);
+        }
+    }
+    __syncthreads();
+
+    // Advance the NCOs over the block; close the loops at the boundary.
+    for (uint32_t j = threadIdx.x; j < nch; j += NT) {
+        const uint32_t w = sm.w[j];
+        __stcg(gd.theta + j, sm.theta[j] + gd.N * w);
+        __stcg((unsigned long long *)gd.phi + j,
+               (unsigned long long)reduce_code_phase(sm.phi[j] + (uint64_t)gd.N * sm.r[j]));
+        const uint32_t ab = sm.ab[j] + 1;
+        if (ab == gd.L) {
+            const int32_t *A = sm.acc + (size_t)j * per_ch;
+            const int64_t *tp = sm.taps + (size_t)j * nt;
+            LoopOut o = loop_update(__ldcg(gd.v + j), A[2 * gd.tap_e], A[2 * gd.tap_e + 1],
+                                    A[2 * gd.tap_p], A[2 * gd.tap_p + 1], A[2 * gd.tap_l],
+                                    A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.fs,
+                                    (uint64_t)gd.L * gd.N, gd.pll_bn, gd.dll_bn);
+            __stcg(gd.v + j, o.v);
+            __stcg(gd.fcarr + j, o.f_carr);
+            __stcg(gd.fcode + j, o.f_code);
+            __stcg(gd.w + j, o.w);
+            __stcg((unsigned long long *)gd.r + j, (unsigned long long)o.r);
+            __stcg(gd.epochs + j, __ldcg(gd.epochs + j) + 1);
+            __stcg(gd.acc_blocks + j, 0u);
+        } else {
+            __stcg(gd.acc_blocks + j, ab);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+}  // namespace rxd

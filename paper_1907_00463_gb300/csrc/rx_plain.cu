@@ -57,13 +57,16 @@ __device__ __forceinline__ void plain_group(const uint32_t (&x)[SPT], uint32_t t
 // grid = (sample tiles of kPlainThreads*SPT, channels); each thread one chunk.
 __global__ void __launch_bounds__(kPlainThreads)
     k_plain_correlate(const int8_t *__restrict__ iq, uint32_t nsamp, uint64_t n_before,
-                      bool a16, bool a4, PlainState st, uint32_t ntaps, const uint32_t *__restrict__ code_tab,
-                      const uint32_t *__restrict__ carrier_tab) {
+                      bool a16, bool a4, PlainState st, uint32_t ntaps,
+                      const uint32_t *__restrict__ code_tab, const uint32_t *__restrict__ carrier_tab,
+                      const uint16_t *__restrict__ pair_tab) {
     extern __shared__ __align__(16) unsigned char smem[];
-    int64_t *s_taps = reinterpret_cast<int64_t *>(smem);                 // [ntaps]
-    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + ntaps);      // [64]
-    uint32_t *s_code = s_tab + 64;                                        // [EXT_WORDS]
-    int32_t *s_red = reinterpret_cast<int32_t *>(s_code + EXT_WORDS);    // [2*ntaps]
+    int4 *s_slices = reinterpret_cast<int4 *>(smem);                                 // [threads][SLICE_INT4]
+    uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_slices + kPlainThreads * SLICE_INT4);  // [PAIR_LEN]
+    int64_t *s_taps = reinterpret_cast<int64_t *>(s_pair + PAIR_LEN);               // [ntaps]
+    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + ntaps);                  // [64]
+    uint32_t *s_code = s_tab + 64;                                                    // [EXT_WORDS]
+    int32_t *s_red = reinterpret_cast<int32_t *>(s_code + EXT_WORDS);                // [2*ntaps]
 
     const uint32_t ch = blockIdx.y;
     const uint32_t prn = st.prn[ch];
@@ -72,6 +75,9 @@ __global__ void __launch_bounds__(kPlainThreads)
     for (uint32_t i = threadIdx.x; i < EXT_WORDS; i += blockDim.x)
         s_code[i] = code_tab[(size_t)prn * EXT_WORDS + i];
     for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) s_red[i] = 0;
+    for (uint32_t i = threadIdx.x; i < PAIR_LEN / 8; i += blockDim.x)
+        reinterpret_cast<uint4 *>(s_pair)[i] =
+            reinterpret_cast<const uint4 *>(pair_tab + (size_t)prn * PAIR_LEN)[i];
     __syncthreads();
 
     const uint32_t s0 = (blockIdx.x * blockDim.x + threadIdx.x) * SPT;
@@ -88,6 +94,42 @@ __global__ void __launch_bounds__(kPlainThreads)
     const uint32_t theta0 = st.theta[ch] + (uint32_t)n0 * w;
     const uint64_t phi0 = reduce_code_phase(st.phi[ch] + n0 * (uint64_t)r);
 
+    const int mode = seg_mode(r);
+    if (mode != 0) {
+        // chip-segment form: mix once, every tap group reads the running sums
+        int4 *slice = s_slices + threadIdx.x * SLICE_INT4;
+        const uint32_t mg = seg_magic(r);
+        if (mode == 16) seg_prefix<16>(x, theta0, w, s_tab, slice);
+        else seg_prefix<8>(x, theta0, w, s_tab, slice);
+        for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
+            const int64_t *tp = s_taps + t0;
+            int32_t *red = s_red + 2 * t0;
+            const uint32_t tt = min((uint32_t)TAP_GROUP, ntaps - t0);
+            if (mode == 16) {
+                switch (tt) {
+                    case 1: seg_group_reduce<16, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 2: seg_group_reduce<16, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 3: seg_group_reduce<16, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 4: seg_group_reduce<16, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 5: seg_group_reduce<16, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 6: seg_group_reduce<16, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 7: seg_group_reduce<16, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    default: seg_group_reduce<16, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
+                }
+            } else {
+                switch (tt) {
+                    case 1: seg_group_reduce<8, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 2: seg_group_reduce<8, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 3: seg_group_reduce<8, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 4: seg_group_reduce<8, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 5: seg_group_reduce<8, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 6: seg_group_reduce<8, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 7: seg_group_reduce<8, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    default: seg_group_reduce<8, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
+                }
+            }
+        }
+    } else {
     for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
         switch (min((uint32_t)TAP_GROUP, ntaps - t0)) {
             case 1: plain_group<1>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
@@ -99,6 +141,7 @@ __global__ void __launch_bounds__(kPlainThreads)
             case 7: plain_group<7>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
             default: plain_group<8>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
         }
+    }
     }
     __syncthreads();
     int32_t *acc = st.acc + (size_t)ch * ntaps * 2;
@@ -312,11 +355,12 @@ extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp)
     }
     const uint32_t per_cta = kPlainThreads * SPT;
     dim3 grid((nsamp + per_cta - 1) / per_cta, h->n_ch);
-    size_t smem = (size_t)h->n_taps * 8 + 64 * 4 + EXT_WORDS * 4 + (size_t)h->n_taps * 8;
+    size_t smem = (size_t)kPlainThreads * SLICE_INT4 * 16 + PAIR_LEN * 2 + (size_t)h->n_taps * 8 +
+                  64 * 4 + EXT_WORDS * 4 + (size_t)h->n_taps * 8;
     const bool a16 = ((uintptr_t)src & 15) == 0, a4 = ((uintptr_t)src & 3) == 0;
     k_plain_correlate<<<grid, kPlainThreads, smem, h->stream>>>(src, nsamp, h->n_since_fold, a16, a4, h->st,
                                                                  h->n_taps, h->tables->code,
-                                                                 h->tables->tab);
+                                                                 h->tables->tab, h->tables->pair);
     RX_CUDA_TRY(cudaGetLastError(), E);
     h->n_since_fold += nsamp;
     h->n_accum += nsamp;

@@ -21,6 +21,8 @@ namespace {
 
 constexpr int kExtBase = 256;
 constexpr int kExtWords = 80;
+constexpr int kPairBase = 64;
+constexpr int kPairLen = 1168;
 
 // IS-GPS-200 Table 3-Ia, G2 delay in chips, PRN 1..32.
 const int kG2Delay[32] = {5,   6,   7,   8,   17,  18,  139, 140, 141, 251, 252,
@@ -61,6 +63,29 @@ void build_code_table(uint32_t *out) {
     }
 }
 
+void build_pair_table(uint16_t *out) {
+    static const int g1_taps[] = {3, 10};
+    static const int g2_taps[] = {2, 3, 6, 8, 9, 10};
+    uint8_t g1[RX_CODE_LEN], g2[RX_CODE_LEN];
+    m_sequence(g1_taps, 2, g1);
+    m_sequence(g2_taps, 6, g2);
+    std::memset(out, 0, sizeof(uint16_t) * 33 * kPairLen);
+    for (int prn = 1; prn <= 32; ++prn) {
+        int d = kG2Delay[prn - 1];
+        auto g = [&](int chip) {
+            int n = ((chip % RX_CODE_LEN) + RX_CODE_LEN) % RX_CODE_LEN;
+            int m = ((n - d) % RX_CODE_LEN + RX_CODE_LEN) % RX_CODE_LEN;
+            return (g1[n] ^ g2[m]) ? -1 : 1;
+        };
+        uint16_t *row = out + (size_t)prn * kPairLen;
+        for (int i = 0; i < kPairLen; ++i) {
+            int c = i - kPairBase;
+            int gc = g(c), gn = g(c + 1);
+            row[i] = (uint16_t)((uint8_t)(int8_t)gn | ((uint16_t)(uint8_t)(int8_t)(gc - gn) << 8));
+        }
+    }
+}
+
 void build_carrier_table(uint32_t *out) {
     const double pi = 3.14159265358979323846;
     for (int k = 0; k < 64; ++k) {
@@ -85,10 +110,15 @@ const DeviceTables *tables_for_device(int device, std::string &err) {
     if (per_dev[device]) return per_dev[device];
     DeviceTables *t = new DeviceTables();
     std::vector<uint32_t> code(33 * kExtWords), tab(64);
+    std::vector<uint16_t> pair(33 * kPairLen);
     build_code_table(code.data());
     build_carrier_table(tab.data());
+    build_pair_table(pair.data());
     cudaError_t e = cudaMalloc(&t->code, code.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&t->tab, tab.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&t->pair, pair.size() * sizeof(uint16_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->pair, pair.data(), pair.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(t->code, code.data(), code.size() * sizeof(uint32_t),
                        cudaMemcpyHostToDevice);
@@ -101,6 +131,7 @@ const DeviceTables *tables_for_device(int device, std::string &err) {
         err = fmt("building device tables: %s", cudaGetErrorString(e));
         if (t->code) cudaFree(t->code);
         if (t->tab) cudaFree(t->tab);
+        if (t->pair) cudaFree(t->pair);
         delete t;
         return nullptr;
     }

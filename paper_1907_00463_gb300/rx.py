@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(HERE, "_build", "librx.so")
 RX_OK, RX_EINVAL, RX_ENOMEM, RX_EBUDGET, RX_ECUDA, RX_ETIMEOUT, RX_ESTATE, RX_EAGAIN = range(8)
 RX_RUN_RESTART = 1
 RX_RUN_NO_GRAPH = 2
+RX_SCHED_DYNAMIC = 0
+RX_SCHED_STATIC = 1
 
 
 class RxError(RuntimeError):
@@ -54,6 +56,41 @@ class rx_receiver_desc(C.Structure):
                 ("tap_prompt", C.c_int32), ("tap_late", C.c_int32)]
 
 
+class rx_serve_config(C.Structure):
+    _fields_ = [("max_streams", C.c_uint32), ("max_channels_per_stream", C.c_uint32),
+                ("max_taps", C.c_uint32), ("max_block_samples", C.c_uint32),
+                ("ring_blocks", C.c_uint32), ("dump_slots", C.c_uint32),
+                ("channels_per_item", C.c_uint32), ("device", C.c_int32),
+                ("hbm_budget_bytes", C.c_uint64)]
+
+
+class rx_serve_stats(C.Structure):
+    _fields_ = [("blocks_done", C.c_uint64), ("deadline_misses", C.c_uint64),
+                ("dropped_blocks", C.c_uint64), ("ticks", C.c_uint64),
+                ("mean_items_per_tick", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("mean_ms", C.c_double),
+                ("active_streams", C.c_uint32), ("queued_streams", C.c_uint32),
+                ("active_channels", C.c_uint64), ("pool_bytes_used", C.c_uint64),
+                ("pool_bytes_total", C.c_uint64), ("device_timeouts", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rx_replay_stream(C.Structure):
+    _fields_ = [("desc", C.POINTER(rx_receiver_desc)), ("prn", C.c_void_p),
+                ("carrier_word", C.c_void_p), ("code_phase_word", C.c_void_p),
+                ("code_rate_word", C.c_void_p), ("tap_offsets", C.c_void_p),
+                ("recording", C.c_void_p), ("rec_blocks", C.c_uint32),
+                ("max_blocks", C.c_uint32), ("churn", C.c_uint32)]
+
+
+class rx_replay_config(C.Structure):
+    _fields_ = [("rate_hz", C.c_double), ("rate_jitter", C.c_double),
+                ("duration_s", C.c_double), ("churn_per_s", C.c_double),
+                ("seed", C.c_uint64), ("producer_threads", C.c_uint32)]
+
+
 # (name, restype, argtypes) for every symbol include/rx.h declares.
 P = C.c_void_p
 SIGNATURES = [
@@ -76,13 +113,29 @@ SIGNATURES = [
     ("rx_batch_sync", C.c_int, [P]),
     ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
-    ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32]),
+    ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
-                                     C.POINTER(C.c_uint32)]),
+                                     C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     ("rx_batch_last_launches", C.c_uint32, [P]),
     ("rx_batch_last_error", C.c_char_p, [P]),
     ("rx_track_static", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, P, P, C.c_uint32, P, P,
                                   P, C.c_int32, P]),
+    ("rx_serve_create", C.c_int, [C.POINTER(rx_serve_config), C.POINTER(P)]),
+    ("rx_serve_destroy", C.c_int, [P]),
+    ("rx_serve_admit", C.c_int, [P, C.POINTER(rx_receiver_desc), P, P, P, P, P,
+                                 C.POINTER(C.c_uint32)]),
+    ("rx_serve_release", C.c_int, [P, C.c_uint32]),
+    ("rx_serve_push", C.c_int, [P, C.c_uint32, P]),
+    ("rx_serve_drain", C.c_int, [P]),
+    ("rx_serve_get_stats", C.c_int, [P, C.POINTER(rx_serve_stats)]),
+    ("rx_serve_reset_stats", C.c_int, [P]),
+    ("rx_serve_stream_status", C.c_int, [P, C.c_uint32, C.POINTER(C.c_uint32),
+                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("rx_serve_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
+    ("rx_serve_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_serve_last_error", C.c_char_p, [P]),
+    ("rx_serve_replay", C.c_int, [P, C.POINTER(rx_replay_stream), C.c_uint32,
+                                  C.POINTER(rx_replay_config), C.POINTER(C.c_uint32)]),
 ]
 
 _lib = None
@@ -276,18 +329,19 @@ def rx_batch_read_state(b, rx: int, n_ch: int) -> list:
     return list(arr)
 
 
-def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per_sm: int = 0):
+def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per_sm: int = 0,
+                       schedule: int = RX_SCHED_DYNAMIC):
     lib = load()
-    _check(b, lib.rx_batch_set_tiles(b, channels_per_item, threads, ctas_per_sm),
+    _check(b, lib.rx_batch_set_tiles(b, channels_per_item, threads, ctas_per_sm, schedule),
            lib.rx_batch_last_error)
 
 
-def rx_batch_get_tiles(b) -> tuple[int, int, int]:
+def rx_batch_get_tiles(b) -> tuple[int, int, int, int]:
     lib = load()
-    a, t, c = C.c_uint32(), C.c_uint32(), C.c_uint32()
-    _check(b, lib.rx_batch_get_tiles(b, C.byref(a), C.byref(t), C.byref(c)),
+    a, t, c, sc = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(b, lib.rx_batch_get_tiles(b, C.byref(a), C.byref(t), C.byref(c), C.byref(sc)),
            lib.rx_batch_last_error)
-    return a.value, t.value, c.value
+    return a.value, t.value, c.value, sc.value
 
 
 def rx_batch_last_launches(b) -> int:
@@ -321,3 +375,129 @@ def rx_track_static(descs, iq, rx_byte_offset, n_blocks: int, state, tap_offsets
                             _ptr(dumps), device, _stream_handle(stream))
     if s != RX_OK:
         raise RxError(s, "rx_track_static")
+
+
+# ----------------------------------------------------------------------------
+# serving form
+# ----------------------------------------------------------------------------
+
+def rx_serve_create(max_streams: int, max_channels_per_stream: int, max_taps: int,
+                    max_block_samples: int, ring_blocks: int = 4096, dump_slots: int = 64,
+                    channels_per_item: int = 0, hbm_budget_bytes: int = 1 << 30,
+                    device: int = 0):
+    lib = load()
+    cfg = rx_serve_config(max_streams, max_channels_per_stream, max_taps, max_block_samples,
+                          ring_blocks, dump_slots, channels_per_item, device, hbm_budget_bytes)
+    s = P()
+    st = lib.rx_serve_create(C.byref(cfg), C.byref(s))
+    if st != RX_OK:
+        raise RxError(st, "rx_serve_create")
+    return s
+
+
+def rx_serve_destroy(s) -> None:
+    load().rx_serve_destroy(s)
+
+
+def rx_serve_admit(s, desc, prn, carrier_word, code_phase_word, code_rate_word, tap_offsets):
+    """Returns (id, active): active False means queued behind the memory budget."""
+    lib = load()
+    prn = _arr(prn, np.uint8)
+    w = _arr(carrier_word, np.int32)
+    phi = _arr(code_phase_word, np.uint64)
+    r = _arr(code_rate_word, np.uint64)
+    taps = _arr(tap_offsets, np.int64)
+    i = C.c_uint32()
+    st = lib.rx_serve_admit(s, C.byref(desc), _ptr(prn), _ptr(w), _ptr(phi), _ptr(r), _ptr(taps),
+                            C.byref(i))
+    if st not in (RX_OK, RX_EBUDGET):
+        _check(s, st, lib.rx_serve_last_error)
+    return i.value, st == RX_OK
+
+
+def rx_serve_release(s, sid: int) -> None:
+    lib = load()
+    _check(s, lib.rx_serve_release(s, sid), lib.rx_serve_last_error)
+
+
+def rx_serve_push(s, sid: int, block) -> int:
+    """Returns the status (RX_OK or RX_EAGAIN); other errors raise."""
+    lib = load()
+    st = lib.rx_serve_push(s, sid, _ptr(block))
+    if st not in (RX_OK, RX_EAGAIN):
+        _check(s, st, lib.rx_serve_last_error)
+    return st
+
+
+def rx_serve_drain(s) -> None:
+    lib = load()
+    _check(s, lib.rx_serve_drain(s), lib.rx_serve_last_error)
+
+
+def rx_serve_get_stats(s) -> dict:
+    lib = load()
+    out = rx_serve_stats()
+    _check(s, lib.rx_serve_get_stats(s, C.byref(out)), lib.rx_serve_last_error)
+    return out.as_dict()
+
+
+def rx_serve_reset_stats(s) -> None:
+    lib = load()
+    _check(s, lib.rx_serve_reset_stats(s), lib.rx_serve_last_error)
+
+
+def rx_serve_stream_status(s, sid: int) -> tuple[int, int, int]:
+    lib = load()
+    st, pu, do = C.c_uint32(), C.c_uint64(), C.c_uint64()
+    _check(s, lib.rx_serve_stream_status(s, sid, C.byref(st), C.byref(pu), C.byref(do)),
+           lib.rx_serve_last_error)
+    return st.value, pu.value, do.value
+
+
+def rx_serve_read_dumps(s, sid: int, n_ch: int, n_taps: int, max_dumps: int) -> np.ndarray:
+    lib = load()
+    out = np.zeros((max_dumps, n_ch, n_taps, 2), np.int32)
+    nd = C.c_uint32()
+    _check(s, lib.rx_serve_read_dumps(s, sid, _ptr(out), out.size, C.byref(nd)),
+           lib.rx_serve_last_error)
+    return out[:nd.value]
+
+
+def rx_serve_read_state(s, sid: int, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_state * n_ch)()
+    _check(s, lib.rx_serve_read_state(s, sid, arr, n_ch), lib.rx_serve_last_error)
+    return list(arr)
+
+
+def rx_serve_last_error(s) -> str:
+    return load().rx_serve_last_error(s).decode()
+
+
+def rx_serve_replay(s, streams, rate_hz: float = 1000.0, rate_jitter: float = 0.1,
+                    duration_s: float = 1.0, churn_per_s: float = 0.0, seed: int = 0,
+                    producer_threads: int = 0):
+    """streams: list of dicts with keys desc (rx_receiver_desc), prn, carrier_word,
+    code_phase_word, code_rate_word, tap_offsets, recording (int8 host array),
+    max_blocks (0 = loop), churn (bool).  Returns the final stream ids."""
+    lib = load()
+    keep = []
+    arr = (rx_replay_stream * len(streams))()
+    for k, d in enumerate(streams):
+        desc = d["desc"]
+        prn = _arr(d["prn"], np.uint8)
+        w = _arr(d["carrier_word"], np.int32)
+        phi = _arr(d["code_phase_word"], np.uint64)
+        r = _arr(d["code_rate_word"], np.uint64)
+        taps = _arr(d["tap_offsets"], np.int64)
+        rec = np.ascontiguousarray(d["recording"], dtype=np.int8)
+        nblk = rec.size // (2 * desc.block_samples)
+        keep += [desc, prn, w, phi, r, taps, rec]
+        arr[k] = rx_replay_stream(C.pointer(desc), _ptr(prn), _ptr(w), _ptr(phi), _ptr(r),
+                                  _ptr(taps), _ptr(rec), nblk, d.get("max_blocks", 0),
+                                  1 if d.get("churn", False) else 0)
+    cfg = rx_replay_config(rate_hz, rate_jitter, duration_s, churn_per_s, seed, producer_threads)
+    ids = (C.c_uint32 * len(streams))()
+    _check(s, lib.rx_serve_replay(s, arr, len(streams), C.byref(cfg), ids), lib.rx_serve_last_error)
+    del keep
+    return list(ids)
