@@ -261,8 +261,12 @@ def run_ours(args):
                            stream=stream)
     for i, r in enumerate(receivers):
         rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+    tune = None
     if args.tiles:
         rx.rx_batch_set_tiles(b, *[int(x) for x in args.tiles.split(",")])
+    else:
+        t_tiles, t_ms = rx.rx_batch_autotune(b, buf, offs, min(64, n_blocks))
+        tune = {"probe_blocks": min(64, n_blocks), "best_probe_ms": t_ms}
 
     def step(src=buf):
         rx.rx_batch_run(b, src, offs, n_blocks, rx.RX_RUN_RESTART)
@@ -374,6 +378,7 @@ def run_ours(args):
                    "fs_hz": FS, "tiles": {"channels_per_item": tiles[0], "threads": tiles[1],
                                           "ctas_per_sm": tiles[2],
                                           "schedule": ["dynamic", "static"][tiles[3]]},
+                   "autotune": tune,
                    "l2": ("inputs larger than L2; no flush" if in_bytes > 129e6 else
                           "inputs fit in L2 (profiling case only)"),
                    "parallelism": f"receivers sharded over {world} GPU(s), no collective"},

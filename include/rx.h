@@ -258,6 +258,18 @@ rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
                              uint32_t *threads, uint32_t *ctas_per_sm,
                              uint32_t *schedule);
 
+/* Autotuner: time each candidate tile shape (both schedules; 1-16 channels per
+ * item; 128/256/512 threads) on the first probe_blocks blocks of the caller's
+ * input (arguments as in rx_batch_run), keep the fastest, and return the
+ * receivers to their starting state.  The choice is cached in the process per
+ * workload shape (sample rates, block sizes, channel/tap counts, integration
+ * lengths, device); a cached shape is applied without timing (*ms_out = -1).
+ * tiles_out (4 entries, optional) receives {channels_per_item, threads,
+ * ctas_per_sm, schedule}; ms_out (optional) the best probe time. */
+rx_status rx_batch_autotune(rx_batch b, const int8_t *iq,
+                            const uint64_t *rx_byte_offset, uint32_t probe_blocks,
+                            uint32_t *tiles_out, float *ms_out);
+
 /* Number of kernel launches the last rx_batch_run issued (graph nodes
  * included), for accounting. */
 uint32_t rx_batch_last_launches(rx_batch b);

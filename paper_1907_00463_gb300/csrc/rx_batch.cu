@@ -19,7 +19,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -60,7 +63,7 @@ struct BatchArgs {
 
 // Persistent kernel: items t = b * G + g in ticket order.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
     __shared__ uint32_t s_ticket, s_abort;
@@ -100,7 +103,7 @@ struct StaticArgs {
 // between blocks; the next block is prefetched into L2 while the current one is
 // correlated; state is written back once at the end.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch_static(StaticArgs a) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static(StaticArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
     int32_t *run = reinterpret_cast<int32_t *>(smem + item_smem_bytes(a.cpg, a.max_taps, NT));
@@ -792,6 +795,103 @@ extern "C" rx_status rx_batch_read_state(rx_batch b, uint32_t rxi, rx_channel_st
         out[c].prn = prn[c];
         out[c].epochs = ep[c];
     }
+    return RX_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Autotuner: time every candidate tile shape on a short probe of the caller's input
+// ----------------------------------------------------------------------------
+
+namespace {
+
+struct TuneKey {
+    std::vector<double> v;
+    bool operator<(const TuneKey &o) const { return v < o.v; }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<uint32_t, 4>> g_tune_cache;
+
+TuneKey tune_key(rx_batch b, int device) {
+    TuneKey k;
+    k.v.push_back(device);
+    for (const rx_receiver_desc &d : b->rx) {
+        k.v.push_back(d.fs_hz);
+        k.v.push_back(d.block_samples);
+        k.v.push_back(d.n_channels);
+        k.v.push_back(d.n_taps);
+        k.v.push_back(d.integ_blocks);
+    }
+    return k;
+}
+
+}  // namespace
+
+extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
+                                       uint32_t probe_blocks, uint32_t *tiles_out, float *ms_out) {
+    if (!b || !iq || !rx_byte_offset || probe_blocks == 0) return RX_EINVAL;
+    probe_blocks = std::min(probe_blocks, b->max_blocks);
+    cudaSetDevice(b->device);
+    const TuneKey key = tune_key(b, b->device);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const auto &t = it->second;
+            rx_status s = rx_batch_set_tiles(b, t[0], t[1], t[2], t[3]);
+            if (s == RX_OK && tiles_out) std::copy(t.begin(), t.end(), tiles_out);
+            if (ms_out) *ms_out = -1.0f;
+            return s;
+        }
+    }
+    uint32_t max_ch = 1;
+    for (const rx_receiver_desc &d : b->rx) max_ch = std::max(max_ch, d.n_channels);
+    std::vector<std::array<uint32_t, 4>> cands;
+    for (uint32_t sched : {RX_SCHED_STATIC, RX_SCHED_DYNAMIC})
+        for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u, 8u, 12u, 16u}) {
+            if (cpg > max_ch) continue;
+            for (uint32_t nt : {128u, 256u, 512u}) {
+                if (sched == RX_SCHED_DYNAMIC && nt == 512) continue;
+                cands.push_back({cpg, nt, 0u, sched});
+            }
+        }
+    cudaEvent_t e0, e1;
+    std::string &E = b->err;
+    RX_CUDA_TRY(cudaEventCreate(&e0), E);
+    RX_CUDA_TRY(cudaEventCreate(&e1), E);
+    float best_ms = 1e30f;
+    std::array<uint32_t, 4> best = cands.front();
+    for (const auto &c : cands) {
+        if (rx_batch_set_tiles(b, c[0], c[1], c[2], c[3]) != RX_OK) continue;
+        // one warm run, then one timed run, both from the starting state
+        if (rx_batch_run(b, iq, rx_byte_offset, probe_blocks, RX_RUN_RESTART | RX_RUN_NO_GRAPH) != RX_OK)
+            continue;
+        cudaEventRecord(e0, b->stream);
+        if (rx_batch_run(b, iq, rx_byte_offset, probe_blocks, RX_RUN_RESTART | RX_RUN_NO_GRAPH) != RX_OK)
+            continue;
+        cudaEventRecord(e1, b->stream);
+        if (rx_batch_sync(b) != RX_OK) continue;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f) return berr(b, RX_ECUDA, "no tile shape ran");
+    rx_status s = rx_batch_set_tiles(b, best[0], best[1], best[2], best[3]);
+    if (s != RX_OK) return s;
+    // leave the receivers at their starting state
+    RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (tiles_out) std::copy(best.begin(), best.end(), tiles_out);
+    if (ms_out) *ms_out = best_ms;
     return RX_OK;
 }
 

@@ -57,7 +57,7 @@ struct ServeArgs {
 };
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_serve(ServeArgs a) {
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_serve(ServeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
     __shared__ uint32_t s_ticket, s_abort;

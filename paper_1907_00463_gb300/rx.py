@@ -116,6 +116,8 @@ SIGNATURES = [
     ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                      C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+    ("rx_batch_autotune", C.c_int, [P, P, P, C.c_uint32, C.POINTER(C.c_uint32),
+                                    C.POINTER(C.c_float)]),
     ("rx_batch_last_launches", C.c_uint32, [P]),
     ("rx_batch_last_error", C.c_char_p, [P]),
     ("rx_track_static", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, P, P, C.c_uint32, P, P,
@@ -342,6 +344,17 @@ def rx_batch_get_tiles(b) -> tuple[int, int, int, int]:
     _check(b, lib.rx_batch_get_tiles(b, C.byref(a), C.byref(t), C.byref(c), C.byref(sc)),
            lib.rx_batch_last_error)
     return a.value, t.value, c.value, sc.value
+
+
+def rx_batch_autotune(b, iq, rx_byte_offset, probe_blocks: int = 64):
+    """Pick the fastest tile shape on a probe of this input; returns (tiles, best_ms)."""
+    lib = load()
+    off = _arr(rx_byte_offset, np.uint64)
+    tiles = (C.c_uint32 * 4)()
+    ms = C.c_float()
+    _check(b, lib.rx_batch_autotune(b, _ptr(iq), _ptr(off), probe_blocks, tiles, C.byref(ms)),
+           lib.rx_batch_last_error)
+    return tuple(tiles), ms.value
 
 
 def rx_batch_last_launches(b) -> int:

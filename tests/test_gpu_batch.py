@@ -98,7 +98,8 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     buf, offs, sigs = _pack(recv, 20)
     dev = torch.from_numpy(buf).cuda()
     results = []
-    for tiles in [None, (1, 128, 0), (3, 256, 2), (8, 512, 1)]:
+    for tiles in [None, (1, 128, 0), (3, 256, 2), (8, 512, 1), (1, 128, 0, rx.RX_SCHED_STATIC),
+                  (2, 256, 0, rx.RX_SCHED_STATIC), (5, 512, 0, rx.RX_SCHED_STATIC)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -120,11 +121,13 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     assert np.array_equal(d, results[0][4][0])
 
 
-def test_graph_replay_restart_continue_and_host_input():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_graph_replay_restart_continue_and_host_input(schedule):
     recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
+    recv[1].integ_blocks = 5                     # an integration spans the two runs (8 + 8 blocks)
     buf, offs, sigs = _pack(recv, 16)
     dev = torch.from_numpy(buf).cuda()
-    b = _batch(recv, 16)
+    b = _batch(recv, 16, (2, 128, 0, schedule))
     try:
         # first half, then the second half continuing (device input, no graph)
         half = [np.ascontiguousarray(s[:8 * r.block_samples]) for s, r in zip(sigs, recv)]
