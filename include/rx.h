@@ -37,7 +37,10 @@
  *   w0 = Bn_pll / 0.53;  v += (w0^2 T) e_p;  f_carr = v + (sqrt2 w0) e_p
  *   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|), d = E-L spacing in chips
  *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c
- *   w = rn(f_carr / fs * 2^32) mod 2^32,  r = rn(f_code / fs * 2^32)
+ *   w = rn(f_carr * 2^32/fs) mod 2^32,  r = rn(f_code * 2^32/fs)
+ * atan(Q/I) is evaluated by table-driven argument reduction about tan(k pi/32)
+ * with one division; divisions by 2 pi and 1575.42e6 are multiplications by
+ * the correctly rounded reciprocals.
  * rn rounds half to even.
  *
  * Conventions for every function:

@@ -163,47 +163,73 @@ void orc_correlate_block(const int8_t *iq, uint32_t nsamp, uint32_t *theta0,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Arctangent (PLL discriminator, Table 3)                                   */
+/* Arctangent of a ratio (PLL discriminator, Table 3)                        */
 /* ------------------------------------------------------------------------ */
 
 #define ORC_PI_2 1.5707963267948966
-#define ORC_PI_6 0.5235987755982989
-#define ORC_TAN_PI_12 0.2679491924311227
-#define ORC_SQRT3 1.7320508075688772
 #define ORC_SQRT2 1.4142135623730951
-#define ORC_TWO_PI 6.283185307179586
+#define ORC_INV_2PI 0.15915494309189535
+#define ORC_INV_L1 6.347513678891978e-10 /* 1 / 1575.42e6 */
+#define ORC_TWO_M32 2.3283064365386963e-10 /* 2^-32, exact */
+
+/* Breakpoints c_k = tan(k pi/32) and their angles k pi/32, k = 0..8, and the
+ * single-precision midpoints tan((j + 1/2) pi/32), j = 0..7, that choose k.
+ * All are the correctly rounded values. */
+static const double orc_tan_k[9] = {0.0, 0.09849140335716425, 0.198912367379658,
+                                    0.3033466836073424, 0.41421356237309503,
+                                    0.5345111359507917, 0.6681786379192989,
+                                    0.8206787908286604, 1.0};
+static const double orc_ang_k[9] = {0.0, 0.09817477042468103, 0.19634954084936207,
+                                    0.2945243112740431, 0.39269908169872414,
+                                    0.4908738521234052, 0.5890486225480862,
+                                    0.6872233929727672, 0.7853981633974483};
+static const float orc_mid_k[8] = {0.049126848578453064f, 0.1483359932899475f,
+                                   0.25048696994781494f, 0.3578057289123535f,
+                                   0.4729647636413574f, 0.599376916885376f,
+                                   0.7416505217552185f, 0.9063471555709839f};
+/* Gregory series coefficients (-1)^j / (2j + 1), j = 0..7 */
+static const double orc_series[8] = {1.0,        -1.0 / 3.0, 1.0 / 5.0,  -1.0 / 7.0,
+                                     1.0 / 9.0,  -1.0 / 11.0, 1.0 / 13.0, -1.0 / 15.0};
 
 /*
- * atan(x) by classical argument reduction and the Gregory series:
- *   |x| > 1:              atan(x) = pi/2 - atan(1/x)
- *   a > tan(pi/12):       atan(a) = pi/6 + atan((sqrt3 a - 1)/(sqrt3 + a))
- *   |a| <= tan(pi/12):    atan(a) = sum_{k=0}^{12} (-1)^k a^(2k+1)/(2k+1),
- *                          evaluated by Horner's rule in a^2.
- * The truncation error is below a^27/27 < 2e-17.
+ * atan(q / i) for i != 0 (two-quadrant), by table-driven argument reduction:
+ *   a = |q|, b = |i|; if a > b swap them and use atan(x) = pi/2 - atan(1/x);
+ *   pick k = the breakpoint whose midpoint interval holds a/b (estimated in
+ *   single precision; any k near a/b gives the same accuracy);
+ *   atan(a/b) = k pi/32 + atan(t),  t = (a - c_k b) / (b + c_k a),  |t| <~ 0.05;
+ *   atan(t) = t (1 - t^2/3 + t^4/5 - ... - t^14/15) by Horner's rule in t^2,
+ *   truncation error below |t|^17 / 17 < 1e-23;
+ * the sign is that of q / i.  One division.
  */
-double orc_atan(double x) {
-    int neg = x < 0.0;
-    double a = neg ? -x : x;
-    int inv = a > 1.0;
-    if (inv) a = 1.0 / a;
-    int shift = a > ORC_TAN_PI_12;
-    if (shift) {
-        double num = ORC_SQRT3 * a;
-        num = num - 1.0;
-        double den = ORC_SQRT3 + a;
-        a = num / den;
+double orc_atan_ratio(double q, double i) {
+    double a = fabs(q), b = fabs(i);
+    int swap = a > b;
+    if (swap) {
+        double tmp = a;
+        a = b;
+        b = tmp;
     }
-    double t = a * a;
-    double p = 1.0 / 25.0;
-    for (int k = 11; k >= 0; --k) {
-        double ck = ((k & 1) ? -1.0 : 1.0) / (double)(2 * k + 1);
-        p = p * t;
-        p = p + ck;
+    float rf = (float)a / (float)b;
+    int k = 0;
+    for (int j = 0; j < 8; ++j)
+        if (rf >= orc_mid_k[j]) k = j + 1;
+    double c = orc_tan_k[k];
+    double num = c * b;
+    num = a - num;
+    double den = c * a;
+    den = b + den;
+    double t = num / den;
+    double u = t * t;
+    double p = orc_series[7];
+    for (int j = 6; j >= 0; --j) {
+        p = p * u;
+        p = p + orc_series[j];
     }
-    double y = a * p;
-    if (shift) y = ORC_PI_6 + y;
-    if (inv) y = ORC_PI_2 - y;
-    return neg ? -y : y;
+    double y = t * p;
+    y = orc_ang_k[k] + y;
+    if (swap) y = ORC_PI_2 - y;
+    if ((q < 0.0) != (i < 0.0)) y = -y;
+    return y;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -243,26 +269,30 @@ void orc_chan_init(orc_chan *ch, int32_t w, uint64_t phi, uint64_t r, double fs)
  *   v      = v + (w0^2 T) e_p
  *   f_carr = v + (sqrt2 w0) e_p
  *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c   (carrier aided)
- * Re-quantisation, round half to even:
- *   w = rn(f_carr / fs * 2^32) (wrapped to int32), r = rn(f_code / fs * 2^32)
+ * Re-quantisation, round half to even, with s = 2^32 / fs:
+ *   w = rn(f_carr s) (wrapped to int32), r = rn(f_code s)
+ * Divisions by the constants 2 pi and 1575.42e6 are multiplications by their
+ * correctly rounded reciprocals.
  */
 void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
                int tap_e, int tap_p, int tap_l, double fs, uint64_t n_accum,
                double pll_bn, double dll_bn) {
     double T = (double)n_accum / fs;
-
-    double ip = (double)acc[2 * tap_p], qp = (double)acc[2 * tap_p + 1];
-    double e_pll;
-    if (ip != 0.0) {
-        double q = qp / ip;
-        e_pll = orc_atan(q) / ORC_TWO_PI;
-    } else {
-        e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
-    }
     double w0 = pll_bn / 0.53;
     double k1 = w0 * w0;
     k1 = k1 * T;
     double k2 = ORC_SQRT2 * w0;
+    double kdll = 4.0 * dll_bn;
+    double sfs = 4294967296.0 / fs;
+
+    double ip = (double)acc[2 * tap_p], qp = (double)acc[2 * tap_p + 1];
+    double e_pll;
+    if (ip != 0.0) {
+        double y = orc_atan_ratio(qp, ip);
+        e_pll = y * ORC_INV_2PI;
+    } else {
+        e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+    }
     double dv = k1 * e_pll;
     ch->v = ch->v + dv;
     double df = k2 * e_pll;
@@ -274,25 +304,23 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
     double mag_e = sqrt(ie2 + qe2);
     double mag_l = sqrt(il2 + ql2);
     double den = mag_e + mag_l;
-    double d_el = (double)(tap_off[tap_e] - tap_off[tap_l]) / 4294967296.0;
-    double kd = 1.0 - d_el / 2.0;
+    double d_el = (double)(tap_off[tap_e] - tap_off[tap_l]) * ORC_TWO_M32;
+    double kd = d_el * 0.5;
+    kd = 1.0 - kd;
     double e_dll = 0.0;
     if (den > 0.0) {
         double num = mag_e - mag_l;
         num = kd * num;
         e_dll = num / den;
     }
-    double aid = f_carr / 1575.42e6;
+    double aid = f_carr * ORC_INV_L1;
     aid = 1.0 + aid;
     double f_code = 1.023e6 * aid;
-    double kdll = 4.0 * dll_bn;
     double corr = kdll * e_dll;
     f_code = f_code + corr;
 
-    double xw = f_carr / fs;
-    xw = xw * 4294967296.0;
-    double xr = f_code / fs;
-    xr = xr * 4294967296.0;
+    double xw = f_carr * sfs;
+    double xr = f_code * sfs;
     /* words: carrier wraps modulo 2^32, code rate clamped to [0, 2^40] */
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;

@@ -162,8 +162,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static
                 const int64_t *tp = sm.taps + (size_t)j * nt;
                 LoopOut o = loop_update(v, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
                                         A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
-                                        tp[gd.tap_e], tp[gd.tap_l], gd.fs, (uint64_t)gd.L * N,
-                                        gd.pll_bn, gd.dll_bn);
+                                        tp[gd.tap_e], tp[gd.tap_l], gd.lc);
                 v = o.v;
                 fc = o.f_carr;
                 fk = o.f_code;
@@ -355,9 +354,8 @@ rx_status build_groups(rx_batch b) {
             g.dump_slots = b->max_blocks / d.integ_blocks;
             g.dump_wrap = 0;
             g.src = r;
-            g.fs = d.fs_hz;
-            g.pll_bn = d.pll_bn_hz;
-            g.dll_bn = d.dll_bn_hz;
+            g.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
+                                    d.dll_bn_hz);
             gs.push_back(g);
         }
     }

@@ -278,40 +278,86 @@ __device__ __forceinline__ void seg_group_reduce(const int4 *slice, uint64_t ph0
 // ----------------------------------------------------------------------------
 
 #define RXD_PI_2 1.5707963267948966
-#define RXD_PI_6 0.5235987755982989
-#define RXD_TAN_PI_12 0.2679491924311227
-#define RXD_SQRT3 1.7320508075688772
 #define RXD_SQRT2 1.4142135623730951
-#define RXD_TWO_PI 6.283185307179586
-#define RXD_TWO32 4294967296.0
+#define RXD_INV_2PI 0.15915494309189535
+#define RXD_INV_L1 6.347513678891978e-10 /* 1 / 1575.42e6 */
+#define RXD_TWO_M32 2.3283064365386963e-10 /* 2^-32, exact */
 
-// atan(x): reduce |x| > 1 by atan(x) = pi/2 - atan(1/x), then a > tan(pi/12) by
-// atan(a) = pi/6 + atan((sqrt3 a - 1)/(sqrt3 + a)), then the Gregory series to
-// degree 25 by Horner's rule.
-__device__ __forceinline__ double own_atan(double x) {
-    bool neg = x < 0.0;
-    double a = neg ? -x : x;
-    bool inv = a > 1.0;
-    if (inv) a = __ddiv_rn(1.0, a);
-    bool shift = a > RXD_TAN_PI_12;
-    if (shift) {
-        double num = __dmul_rn(RXD_SQRT3, a);
-        num = __dsub_rn(num, 1.0);
-        double den = __dadd_rn(RXD_SQRT3, a);
-        a = __ddiv_rn(num, den);
+// Breakpoints tan(k pi/32), angles k pi/32 (k = 0..8), single-precision midpoints
+// tan((j + 1/2) pi/32) (j = 0..7) and the Gregory coefficients (-1)^j / (2j + 1):
+// correctly rounded values.
+static __constant__ double kAtanTan[9] = {0.0, 0.09849140335716425, 0.198912367379658,
+                                          0.3033466836073424, 0.41421356237309503,
+                                          0.5345111359507917, 0.6681786379192989,
+                                          0.8206787908286604, 1.0};
+static __constant__ double kAtanAng[9] = {0.0, 0.09817477042468103, 0.19634954084936207,
+                                          0.2945243112740431, 0.39269908169872414,
+                                          0.4908738521234052, 0.5890486225480862,
+                                          0.6872233929727672, 0.7853981633974483};
+static __constant__ float kAtanMid[8] = {0.049126848578453064f, 0.1483359932899475f,
+                                         0.25048696994781494f, 0.3578057289123535f,
+                                         0.4729647636413574f, 0.599376916885376f,
+                                         0.7416505217552185f, 0.9063471555709839f};
+static __constant__ double kAtanSeries[8] = {1.0,       -1.0 / 3.0,  1.0 / 5.0,  -1.0 / 7.0,
+                                             1.0 / 9.0, -1.0 / 11.0, 1.0 / 13.0, -1.0 / 15.0};
+
+// atan(q / i), i != 0, two-quadrant, by table-driven argument reduction: with
+// a = |q|, b = |i| (swapped if a > b, atan(x) = pi/2 - atan(1/x)), the breakpoint
+// c_k = tan(k pi/32) nearest a/b (chosen from a single-precision estimate),
+// atan(a/b) = k pi/32 + atan(t), t = (a - c_k b) / (b + c_k a), and atan(t) by the
+// Gregory series to t^15 in Horner form.  One division.
+__device__ __forceinline__ double atan_ratio(double q, double i) {
+    double a = fabs(q), b = fabs(i);
+    const bool swap = a > b;
+    if (swap) {
+        const double tmp = a;
+        a = b;
+        b = tmp;
     }
-    double t = __dmul_rn(a, a);
-    double p = __ddiv_rn(1.0, 25.0);
+    const float rf = __fdiv_rn(__double2float_rn(a), __double2float_rn(b));
+    int k = 0;
 #pragma unroll
-    for (int k = 11; k >= 0; --k) {
-        double ck = __ddiv_rn((k & 1) ? -1.0 : 1.0, (double)(2 * k + 1));
-        p = __dmul_rn(p, t);
-        p = __dadd_rn(p, ck);
+    for (int j = 0; j < 8; ++j)
+        if (rf >= kAtanMid[j]) k = j + 1;
+    const double c = kAtanTan[k];
+    double num = __dmul_rn(c, b);
+    num = __dsub_rn(a, num);
+    double den = __dmul_rn(c, a);
+    den = __dadd_rn(b, den);
+    const double t = __ddiv_rn(num, den);
+    const double u = __dmul_rn(t, t);
+    double p = kAtanSeries[7];
+#pragma unroll
+    for (int j = 6; j >= 0; --j) {
+        p = __dmul_rn(p, u);
+        p = __dadd_rn(p, kAtanSeries[j]);
     }
-    double y = __dmul_rn(a, p);
-    if (shift) y = __dadd_rn(RXD_PI_6, y);
-    if (inv) y = __dsub_rn(RXD_PI_2, y);
-    return neg ? -y : y;
+    double y = __dmul_rn(t, p);
+    y = __dadd_rn(kAtanAng[k], y);
+    if (swap) y = __dsub_rn(RXD_PI_2, y);
+    if ((q < 0.0) != (i < 0.0)) y = -y;
+    return y;
+}
+
+// Per-receiver loop constants, computed on the host once per integration length:
+//   T = n_accum / fs, w0 = Bn_pll / 0.53, k1 = (w0 w0) T, k2 = sqrt2 w0,
+//   kdll = 4 Bn_dll, sfs = 2^32 / fs.
+struct LoopConsts {
+    double k1, k2, kdll, sfs;
+};
+
+__host__ inline LoopConsts make_loop_consts(double fs, uint64_t n_accum, double pll_bn,
+                                            double dll_bn) {
+    LoopConsts c;
+    const double T = (double)n_accum / fs;
+    const double w0 = pll_bn / 0.53;
+    double k1 = w0 * w0;
+    k1 = k1 * T;
+    c.k1 = k1;
+    c.k2 = RXD_SQRT2 * w0;
+    c.kdll = 4.0 * dll_bn;
+    c.sfs = 4294967296.0 / fs;
+    return c;
 }
 
 struct LoopOut {
@@ -320,55 +366,49 @@ struct LoopOut {
     uint64_t r;
 };
 
-// One loop update from the dumped E/P/L sums.  n_accum: samples integrated.
+// One loop update (Table 3) from the dumped E/P/L sums:
+//   e_p = atan(Q_P / I_P) / (2 pi) (+-1/4 if I_P = 0);  v += k1 e_p;  f_carr = v + k2 e_p
+//   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|);  f_code = 1.023e6 (1 + f_carr / 1575.42e6) + kdll e_c
+//   w = rn(f_carr sfs) mod 2^32,  r = rn(f_code sfs)
 __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
                                                int32_t qpr, int32_t il, int32_t ql,
-                                               int64_t off_e, int64_t off_l, double fs,
-                                               uint64_t n_accum, double pll_bn, double dll_bn) {
+                                               int64_t off_e, int64_t off_l,
+                                               const LoopConsts &lc) {
     LoopOut o;
-    double T = __ddiv_rn((double)n_accum, fs);
-    double ip = (double)ipr, qp = (double)qpr;
+    const double ip = (double)ipr, qp = (double)qpr;
     double e_pll;
     if (ip != 0.0) {
-        double q = __ddiv_rn(qp, ip);
-        e_pll = __ddiv_rn(own_atan(q), RXD_TWO_PI);
+        e_pll = __dmul_rn(atan_ratio(qp, ip), RXD_INV_2PI);
     } else {
         e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
     }
-    double w0 = __ddiv_rn(pll_bn, 0.53);
-    double k1 = __dmul_rn(w0, w0);
-    k1 = __dmul_rn(k1, T);
-    double k2 = __dmul_rn(RXD_SQRT2, w0);
-    double dv = __dmul_rn(k1, e_pll);
+    const double dv = __dmul_rn(lc.k1, e_pll);
     v = __dadd_rn(v, dv);
-    double df = __dmul_rn(k2, e_pll);
-    double f_carr = __dadd_rn(v, df);
+    const double df = __dmul_rn(lc.k2, e_pll);
+    const double f_carr = __dadd_rn(v, df);
 
-    double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
-    double ie2 = __dmul_rn(dIe, dIe), qe2 = __dmul_rn(dQe, dQe);
-    double il2 = __dmul_rn(dIl, dIl), ql2 = __dmul_rn(dQl, dQl);
-    double mag_e = __dsqrt_rn(__dadd_rn(ie2, qe2));
-    double mag_l = __dsqrt_rn(__dadd_rn(il2, ql2));
-    double den = __dadd_rn(mag_e, mag_l);
-    double d_el = __ddiv_rn((double)(off_e - off_l), RXD_TWO32);
-    double kd = __dsub_rn(1.0, __ddiv_rn(d_el, 2.0));
+    const double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
+    const double ie2 = __dmul_rn(dIe, dIe), qe2 = __dmul_rn(dQe, dQe);
+    const double il2 = __dmul_rn(dIl, dIl), ql2 = __dmul_rn(dQl, dQl);
+    const double mag_e = __dsqrt_rn(__dadd_rn(ie2, qe2));
+    const double mag_l = __dsqrt_rn(__dadd_rn(il2, ql2));
+    const double den = __dadd_rn(mag_e, mag_l);
+    const double d_el = __dmul_rn((double)(off_e - off_l), RXD_TWO_M32);
+    const double kd = __dsub_rn(1.0, __dmul_rn(d_el, 0.5));
     double e_dll = 0.0;
     if (den > 0.0) {
         double num = __dsub_rn(mag_e, mag_l);
         num = __dmul_rn(kd, num);
         e_dll = __ddiv_rn(num, den);
     }
-    double aid = __ddiv_rn(f_carr, 1575.42e6);
+    double aid = __dmul_rn(f_carr, RXD_INV_L1);
     aid = __dadd_rn(1.0, aid);
     double f_code = __dmul_rn(1.023e6, aid);
-    double kdll = __dmul_rn(4.0, dll_bn);
-    double corr = __dmul_rn(kdll, e_dll);
+    const double corr = __dmul_rn(lc.kdll, e_dll);
     f_code = __dadd_rn(f_code, corr);
 
-    double xw = __ddiv_rn(f_carr, fs);
-    xw = __dmul_rn(xw, RXD_TWO32);
-    double xr = __ddiv_rn(f_code, fs);
-    xr = __dmul_rn(xr, RXD_TWO32);
+    double xw = __dmul_rn(f_carr, lc.sfs);
+    double xr = __dmul_rn(f_code, lc.sfs);
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
     if (!(xr > 0.0)) xr = 0.0;

@@ -30,7 +30,7 @@ struct GroupDesc {
     uint32_t dump_wrap;   // 1: slot = epoch mod dump_slots; 0: epochs past the last slot are dropped
     uint32_t src;         // index into the sample-offset table
     uint32_t pad;
-    double fs, pll_bn, dll_bn;
+    LoopConsts lc;        // loop constants for one integration (L blocks)
 };
 
 struct Tables {
@@ -331,8 +331,7 @@ __device__ __forceinline__ void process_item(const GroupDesc &gd, const int8_t *
             const int64_t *tp = sm.taps + (size_t)j * nt;
             LoopOut o = loop_update(__ldcg(gd.v + j), A[2 * gd.tap_e], A[2 * gd.tap_e + 1],
                                     A[2 * gd.tap_p], A[2 * gd.tap_p + 1], A[2 * gd.tap_l],
-                                    A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.fs,
-                                    (uint64_t)gd.L * gd.N, gd.pll_bn, gd.dll_bn);
+                                    A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.lc);
             __stcg(gd.v + j, o.v);
             __stcg(gd.fcarr + j, o.f_carr);
             __stcg(gd.fcode + j, o.f_code);

@@ -160,8 +160,7 @@ __global__ void k_plain_fold(PlainState st, uint32_t n_ch, uint64_t n) {
 // Integration boundary, one thread per channel: fold phases, run the loops,
 // load the new words, clear the accumulators.
 __global__ void k_plain_track(PlainState st, uint32_t n_ch, uint32_t ntaps, uint64_t n_fold,
-                              uint64_t n_accum, double fs, double pll_bn, double dll_bn,
-                              int tap_e, int tap_p, int tap_l) {
+                              LoopConsts lc, int tap_e, int tap_p, int tap_l) {
     uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_ch) return;
     st.theta[c] = st.theta[c] + (uint32_t)n_fold * (uint32_t)st.w[c];
@@ -169,8 +168,7 @@ __global__ void k_plain_track(PlainState st, uint32_t n_ch, uint32_t ntaps, uint
     int32_t *a = st.acc + (size_t)c * ntaps * 2;
     const int64_t *t = st.taps + (size_t)c * ntaps;
     LoopOut o = loop_update(st.v[c], a[2 * tap_e], a[2 * tap_e + 1], a[2 * tap_p], a[2 * tap_p + 1],
-                            a[2 * tap_l], a[2 * tap_l + 1], t[tap_e], t[tap_l], fs, n_accum, pll_bn,
-                            dll_bn);
+                            a[2 * tap_l], a[2 * tap_l + 1], t[tap_e], t[tap_l], lc);
     st.v[c] = o.v;
     st.fcarr[c] = o.f_carr;
     st.fcode[c] = o.f_code;
@@ -373,8 +371,9 @@ extern "C" rx_status rx_track_epoch(rx_handle h) {
         return set_err(h, RX_ESTATE, "no samples correlated since the last boundary");
     cudaSetDevice(h->cfg.device);
     k_plain_track<<<(h->n_ch + 63) / 64, 64, 0, h->stream>>>(
-        h->st, h->n_ch, h->n_taps, h->n_since_fold, h->n_accum, h->cfg.fs_hz, h->cfg.pll_bn_hz,
-        h->cfg.dll_bn_hz, h->cfg.tap_early, h->cfg.tap_prompt, h->cfg.tap_late);
+        h->st, h->n_ch, h->n_taps, h->n_since_fold,
+        make_loop_consts(h->cfg.fs_hz, h->n_accum, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz), h->cfg.tap_early,
+        h->cfg.tap_prompt, h->cfg.tap_late);
     RX_CUDA_TRY(cudaGetLastError(), h->err);
     h->n_since_fold = 0;
     h->n_accum = 0;

@@ -312,9 +312,8 @@ rx_status activate(rx_serve s, uint32_t id) {
         gd.dump_slots = s->cfg.dump_slots;
         gd.dump_wrap = 1;
         gd.src = id;
-        gd.fs = d.fs_hz;
-        gd.pll_bn = d.pll_bn_hz;
-        gd.dll_bn = d.dll_bn_hz;
+        gd.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
+                                 d.dll_bn_hz);
         up(s->d_groups + g, &gd, sizeof(GroupDesc));
         if (e == cudaSuccess) e = cudaMemsetAsync(s->d_done + g, 0, 4, cs);
     }

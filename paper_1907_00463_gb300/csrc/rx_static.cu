@@ -43,7 +43,7 @@ struct SGroup {            // one channel's work unit
     uint32_t rx_nch, ch_in_rx;
     uint64_t tap_base;     // first tap of this channel in the caller's tap array
     uint64_t dump_base;    // first int32 of this receiver's dumps
-    double fs, pll_bn, dll_bn;
+    LoopConsts lc;
 };
 
 // Scratch layout (byte offsets inside the array).
@@ -127,9 +127,13 @@ __global__ void k_static_setup(unsigned char *scratch, uint32_t n_rx, uint32_t n
             g.ch_in_rx = c;
             g.tap_base = tap + (uint64_t)c * d.n_taps;
             g.dump_base = dump;
-            g.fs = d.fs_hz;
-            g.pll_bn = d.pll_bn_hz;
-            g.dll_bn = d.dll_bn_hz;
+            // loop constants, same operations and order as make_loop_consts on the host
+            const double T = __ddiv_rn((double)((uint64_t)d.integ_blocks * d.block_samples), d.fs_hz);
+            const double w0 = __ddiv_rn(d.pll_bn_hz, 0.53);
+            g.lc.k1 = __dmul_rn(__dmul_rn(w0, w0), T);
+            g.lc.k2 = __dmul_rn(RXD_SQRT2, w0);
+            g.lc.kdll = __dmul_rn(4.0, d.dll_bn_hz);
+            g.lc.sfs = __ddiv_rn(4294967296.0, d.fs_hz);
             gs[ch + c] = g;
         }
         ch += d.n_channels;
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kThreads)
                 LoopOut o = loop_update(st.pll_integrator_hz, s_acc[2 * gd.tap_e], s_acc[2 * gd.tap_e + 1],
                                         s_acc[2 * gd.tap_p], s_acc[2 * gd.tap_p + 1], s_acc[2 * gd.tap_l],
                                         s_acc[2 * gd.tap_l + 1], s_taps[gd.tap_e], s_taps[gd.tap_l],
-                                        gd.fs, (uint64_t)gd.L * gd.N, gd.pll_bn, gd.dll_bn);
+                                        gd.lc);
                 st.pll_integrator_hz = o.v;
                 st.carrier_hz = o.f_carr;
                 st.code_hz = o.f_code;

@@ -2,8 +2,8 @@
 normalised early-minus-late envelope DLL with carrier aiding, 2nd-order PLL,
 1st-order DLL) and NCO re-quantisation.
 
-The arctangent is checked against the C library's atan (error bound), by its
-identities; the loop update by closed forms (zero error leaves the carrier word
+The arctangent of Q/I is checked against the C library's atan (error bound),
+by its symmetries and at the reduction's breakpoints; the loop update by closed forms (zero error leaves the carrier word
 fixed; a constant error grows the integrator arithmetically; a known E/L pair
 gives a known code-rate correction); the quantiser by exact half-way cases; the
 closed loop by convergence on a synthetic signal with known Doppler and code
@@ -26,25 +26,35 @@ def _ulp_diff(a, b):
     return abs(a - b) / math.ulp(max(abs(a), abs(b)))
 
 
-def test_atan_against_libm():
-    xs = [0.0, 1e-300, 1e-12, 1e-3, 0.1, 0.2679491924311227, 0.26794919243112275, 0.5, 0.75,
-          1.0, 1.0000000000000002, 1.5, 2.0, 3.7320508075688772, 10.0, 1e3, 1e12, 1e300]
+def test_atan_ratio_against_libm():
+    # integer numerators/denominators as the accumulators give them, every octant
     g = np.random.default_rng(1)
-    xs += list(g.standard_cauchy(4000)) + list(g.uniform(-2, 2, 4000))
+    pairs = [(0, 5), (1, 1), (-1, 1), (7, -7), (3, 4), (2**31 - 1, 1), (1, 2**31 - 1),
+             (-(2**31), 3), (123456789, 987654321)]
+    pairs += [(int(a), int(b)) for a, b in g.integers(-(2**31), 2**31, size=(20000, 2)) if b != 0]
+    pairs += [(int(a), int(b)) for a, b in g.integers(-3000, 3000, size=(20000, 2)) if b != 0]
     worst = 0.0
-    for x in xs:
-        for v in (x, -x):
-            worst = max(worst, _ulp_diff(oracle.atan(v), math.atan(v)))
+    for q, i in pairs:
+        y = oracle.atan_ratio(q, i)
+        ref = math.atan(q / i)
+        worst = max(worst, abs(y - ref) / math.ulp(max(abs(ref), 1e-300)))
     assert worst <= 4.0, worst
 
 
-def test_atan_identities():
-    assert oracle.atan(0.0) == 0.0
-    assert _ulp_diff(oracle.atan(1.0), math.pi / 4) <= 1
+def test_atan_ratio_identities():
+    assert oracle.atan_ratio(0.0, 1.0) == 0.0
+    assert oracle.atan_ratio(1.0, 1.0) == math.pi / 4
     g = np.random.default_rng(2)
-    for x in g.uniform(1e-3, 1e3, 2000):
-        assert oracle.atan(-x) == -oracle.atan(x)
-        assert abs(oracle.atan(x) + oracle.atan(1.0 / x) - math.pi / 2) < 4e-16 * 4
+    for q, i in g.integers(1, 10**6, size=(3000, 2)):
+        q, i = float(q), float(i)
+        assert oracle.atan_ratio(-q, i) == -oracle.atan_ratio(q, i)
+        assert oracle.atan_ratio(q, -i) == -oracle.atan_ratio(q, i)
+        assert oracle.atan_ratio(-q, -i) == oracle.atan_ratio(q, i)
+        assert abs(oracle.atan_ratio(q, i) + oracle.atan_ratio(i, q) - math.pi / 2) < 8.9e-16
+    # at every breakpoint tan(k pi/32) the reduction leaves t = 0 and returns k pi/32
+    for k in range(9):
+        c = math.tan(k * math.pi / 32)
+        assert abs(oracle.atan_ratio(c, 1.0) - k * math.pi / 32) < 4.5e-16
 
 
 def _acc(ip, qp, e=(0, 0), l=(0, 0)):
