@@ -129,36 +129,56 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static
     for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT)
         run[i] = sm.ab[i / per_ch] ? gd.acc[i] : 0;
     const int8_t *base = a.iq + a.src_off[gd.src];
+    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
+    __syncthreads();
+    const bool own_fold = nt <= 16;  // a channel's own thread folds its sums
     for (uint32_t b = 0; b < a.n_blocks; ++b) {
         const int8_t *blk = base + (size_t)b * 2 * N;
         if (threadIdx.x == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
-        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
-        __syncthreads();
         correlate_group<NT>(nch, nt, N, blk, sm, sm.acc);
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
-            const uint32_t j = i / per_ch, e = i - j * per_ch;
-            const uint32_t val = (uint32_t)sm.acc[i] + (uint32_t)run[i];
-            if (sm.ab[j] + 1 == gd.L) {
-                const uint32_t ep = s_ep[j];
-                if (gd.dump_wrap || ep < gd.dump_slots) {
-                    const uint32_t slot = gd.dump_wrap ? ep % gd.dump_slots : ep;
-                    gd.dumps[(uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch + e] = (int32_t)val;
+        if (!own_fold) {
+            for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
+                const uint32_t j = i / per_ch, e = i - j * per_ch;
+                const uint32_t val = (uint32_t)sm.acc[i] + (uint32_t)run[i];
+                if (sm.ab[j] + 1 == gd.L) {
+                    const uint32_t ep = s_ep[j];
+                    if (gd.dump_wrap || ep < gd.dump_slots) {
+                        const uint32_t slot = gd.dump_wrap ? ep % gd.dump_slots : ep;
+                        gd.dumps[(uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch + e] = (int32_t)val;
+                    }
+                    sm.acc[i] = (int32_t)val;
+                    run[i] = 0;
+                } else {
+                    run[i] = (int32_t)val;
                 }
-                sm.acc[i] = (int32_t)val;
-                run[i] = 0;
-            } else {
-                run[i] = (int32_t)val;
             }
+            __syncthreads();
         }
-        __syncthreads();
         if (threadIdx.x < nch) {
             const uint32_t j = threadIdx.x, w = sm.w[j];
+            const bool boundary = sm.ab[j] + 1 == gd.L;
+            int32_t *A = sm.acc + (size_t)j * per_ch;
+            int32_t *R = run + (size_t)j * per_ch;
+            if (own_fold) {
+                for (uint32_t e = 0; e < per_ch; ++e) {
+                    const uint32_t val = (uint32_t)A[e] + (uint32_t)R[e];
+                    if (boundary) {
+                        A[e] = (int32_t)val;
+                        R[e] = 0;
+                    } else {
+                        R[e] = (int32_t)val;
+                    }
+                }
+                if (boundary && (gd.dump_wrap || s_ep[j] < gd.dump_slots)) {
+                    const uint32_t slot = gd.dump_wrap ? s_ep[j] % gd.dump_slots : s_ep[j];
+                    int32_t *dst = gd.dumps + (uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch;
+                    for (uint32_t e = 0; e < per_ch; ++e) dst[e] = A[e];
+                }
+            }
             sm.theta[j] = sm.theta[j] + N * w;
             sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
-            const uint32_t ab = sm.ab[j] + 1;
-            if (ab == gd.L) {
-                const int32_t *A = sm.acc + (size_t)j * per_ch;
+            if (boundary) {
                 const int64_t *tp = sm.taps + (size_t)j * nt;
                 LoopOut o = loop_update(v, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
                                         A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
@@ -171,8 +191,14 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static
                 s_ep[j] += 1;
                 sm.ab[j] = 0;
             } else {
-                sm.ab[j] = ab;
+                sm.ab[j] = sm.ab[j] + 1;
             }
+            if (own_fold)
+                for (uint32_t e = 0; e < per_ch; ++e) A[e] = 0;
+        }
+        if (!own_fold) {
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
         }
         __syncthreads();
     }
