@@ -38,9 +38,9 @@
  *   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|), d = E-L spacing in chips
  *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c
  *   w = rn(f_carr * 2^32/fs) mod 2^32,  r = rn(f_code * 2^32/fs)
- * atan(Q/I) is evaluated by table-driven argument reduction about tan(k pi/32)
- * with one division; divisions by 2 pi and 1575.42e6 are multiplications by
- * the correctly rounded reciprocals.
+ * atan(Q/I)/(2 pi) is evaluated by table-driven argument reduction about
+ * tan(k pi/256) with one division and a short Gregory series in Estrin form;
+ * the carrier aiding is 1.023e6 + f_carr * (1/1540), 1/1540 correctly rounded.
  * rn rounds half to even.
  *
  * Conventions for every function:

@@ -57,8 +57,8 @@ def lib():
                                           C.POINTER(C.c_uint64), C.c_uint64, P, C.c_uint32,
                                           P, P]
         L.orc_correlate_block.restype = None
-        L.orc_atan_ratio.argtypes = [C.c_double, C.c_double]
-        L.orc_atan_ratio.restype = C.c_double
+        L.orc_atan_cycles.argtypes = [C.c_double, C.c_double]
+        L.orc_atan_cycles.restype = C.c_double
         L.orc_chan_init.argtypes = [C.POINTER(OrcChan), C.c_int32, C.c_uint64, C.c_uint64,
                                     C.c_double]
         L.orc_chan_init.restype = None
@@ -127,9 +127,9 @@ def correlate_block(iq: np.ndarray, theta0: int, w: int, phi0: int, r: int,
     return acc, th.value, ph.value
 
 
-def atan_ratio(q: float, i: float) -> float:
-    """atan(q / i) for i != 0 (two-quadrant)."""
-    return lib().orc_atan_ratio(float(q), float(i))
+def atan_cycles(q: float, i: float) -> float:
+    """atan(q / i) / (2 pi), in cycles, for i != 0 (two-quadrant)."""
+    return lib().orc_atan_cycles(float(q), float(i))
 
 
 def chan_init(w: int, phi: int, r: int, fs: float) -> OrcChan:

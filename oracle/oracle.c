@@ -163,45 +163,71 @@ void orc_correlate_block(const int8_t *iq, uint32_t nsamp, uint32_t *theta0,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Arctangent of a ratio (PLL discriminator, Table 3)                        */
+/* Arctangent of a ratio, in cycles (PLL discriminator, Table 3)            */
 /* ------------------------------------------------------------------------ */
 
-#define ORC_PI_2 1.5707963267948966
 #define ORC_SQRT2 1.4142135623730951
-#define ORC_INV_2PI 0.15915494309189535
-#define ORC_INV_L1 6.347513678891978e-10 /* 1 / 1575.42e6 */
+#define ORC_KAID 0.0006493506493506494 /* 1 / 1540 = 1.023e6 / 1575.42e6 */
 #define ORC_TWO_M32 2.3283064365386963e-10 /* 2^-32, exact */
 
-/* Breakpoints c_k = tan(k pi/32) and their angles k pi/32, k = 0..8, and the
- * single-precision midpoints tan((j + 1/2) pi/32), j = 0..7, that choose k.
- * All are the correctly rounded values. */
-static const double orc_tan_k[9] = {0.0, 0.09849140335716425, 0.198912367379658,
-                                    0.3033466836073424, 0.41421356237309503,
-                                    0.5345111359507917, 0.6681786379192989,
-                                    0.8206787908286604, 1.0};
-static const double orc_ang_k[9] = {0.0, 0.09817477042468103, 0.19634954084936207,
-                                    0.2945243112740431, 0.39269908169872414,
-                                    0.4908738521234052, 0.5890486225480862,
-                                    0.6872233929727672, 0.7853981633974483};
-static const float orc_mid_k[8] = {0.049126848578453064f, 0.1483359932899475f,
-                                   0.25048696994781494f, 0.3578057289123535f,
-                                   0.4729647636413574f, 0.599376916885376f,
-                                   0.7416505217552185f, 0.9063471555709839f};
-/* Gregory series coefficients (-1)^j / (2j + 1), j = 0..7 */
-static const double orc_series[8] = {1.0,        -1.0 / 3.0, 1.0 / 5.0,  -1.0 / 7.0,
-                                     1.0 / 9.0,  -1.0 / 11.0, 1.0 / 13.0, -1.0 / 15.0};
+/* Breakpoints c_k = tan(k pi/256), k = 0..64 (correctly rounded). */
+static const double orc_tan_k[65] = {
+    0.0, 0.012272462379566276, 0.024548622108925444, 0.03683218099484564,
+    0.049126849769467254, 0.061436352581593766, 0.07376443152244928, 0.0861148511976279,
+    0.09849140335716425, 0.11089791159591303, 0.12333823613673868, 0.13581627870938773,
+    0.14833598753834742, 0.16090136245348916, 0.17351646013785577, 0.18618539952758373,
+    0.198912367379658, 0.21170162402398335, 0.2245575093171293, 0.23748444881607017,
+    0.25048696019130545, 0.263569659899918, 0.2767372701404143, 0.2899946261126061,
+    0.3033466836073424, 0.3167985269526038, 0.3303553773443339, 0.3440226015924263,
+    0.3578057213145241, 0.37171042261274345, 0.38574256627112125, 0.3999081985145372,
+    0.41421356237309503, 0.4286651096994995, 0.44326951389086433, 0.4580336833706724,
+    0.4729647758913199, 0.48807021372286286, 0.5033576997992942, 0.5188352348999757,
+    0.5345111359507917, 0.5503940555372641, 0.566493002730344, 0.5828173653349761,
+    0.5993769336819238, 0.6161819260948661, 0.6332430161775692, 0.6505713620801533,
+    0.6681786379192989, 0.6860770675448629, 0.7042794608650442, 0.7227992529642059,
+    0.7416505462720354, 0.7608481560702512, 0.7804076596539437, 0.8003454494993201,
+    0.8206787908286604, 0.8414258840072548, 0.8626059322567399, 0.8842392152253499,
+    0.9063471690191471, 0.9289524733703675, 0.9520791467009253, 0.9757526499323765,
+    1.0,
+};
+/* Single-precision midpoints tan((j + 1/2) pi/256), j = 0..63, that choose k. */
+static const float orc_mid_k[64] = {
+    0.006136000156402588f, 0.0184098482131958f, 0.030689245089888573f, 0.042977895587682724f,
+    0.05527951195836067f, 0.06759783625602722f, 0.07993661612272263f, 0.09229962527751923f,
+    0.10469067096710205f, 0.11711360514163971f, 0.1295723021030426f, 0.1420706808567047f,
+    0.1546127200126648f, 0.1672024428844452f, 0.179843932390213f, 0.19254136085510254f,
+    0.20529894530773163f, 0.21812096238136292f, 0.23101182281970978f, 0.24397596716880798f,
+    0.25701799988746643f, 0.2701425552368164f, 0.28335443139076233f, 0.2966585159301758f,
+    0.3100598156452179f, 0.32356348633766174f, 0.3371748626232147f, 0.3508993089199066f,
+    0.3647425174713135f, 0.37871018052101135f, 0.39280831813812256f, 0.4070430099964142f,
+    0.4214206635951996f, 0.4359477758407593f, 0.45063120126724243f, 0.46547791361808777f,
+    0.4804952144622803f, 0.4956907033920288f, 0.5110722184181213f, 0.5266478657722473f,
+    0.5424261689186096f, 0.558415949344635f, 0.5746263861656189f, 0.5910671353340149f,
+    0.6077480912208557f, 0.6246797442436218f, 0.6418730616569519f, 0.6593393683433533f,
+    0.6770906448364258f, 0.695139467716217f, 0.7134988307952881f, 0.7321825623512268f,
+    0.7512050867080688f, 0.7705816626548767f, 0.7903282046318054f, 0.8104615807533264f,
+    0.8309994339942932f, 0.8519605398178101f, 0.8733646273612976f, 0.8952324986457825f,
+    0.9175862073898315f, 0.940449059009552f, 0.9638459086418152f, 0.9878028631210327f,
+};
+/* Gregory coefficients divided by 2 pi: (-1)^j / ((2j + 1) 2 pi), j = 0..4. */
+static const double orc_series[5] = {0.15915494309189535, -0.05305164769729845, 0.03183098861837907,
+                                     -0.022736420441699334, 0.017683882565766147};
 
 /*
- * atan(q / i) for i != 0 (two-quadrant), by table-driven argument reduction:
+ * atan(q / i) / (2 pi), in cycles, for i != 0 (two-quadrant), by table-driven
+ * argument reduction:
  *   a = |q|, b = |i|; if a > b swap them and use atan(x) = pi/2 - atan(1/x);
- *   pick k = the breakpoint whose midpoint interval holds a/b (estimated in
- *   single precision; any k near a/b gives the same accuracy);
- *   atan(a/b) = k pi/32 + atan(t),  t = (a - c_k b) / (b + c_k a),  |t| <~ 0.05;
- *   atan(t) = t (1 - t^2/3 + t^4/5 - ... - t^14/15) by Horner's rule in t^2,
- *   truncation error below |t|^17 / 17 < 1e-23;
- * the sign is that of q / i.  One division.
+ *   k = the number of midpoints at or below a/b (single-precision estimate of
+ *   a/b, binary search), so that c_k = tan(k pi/256) is the breakpoint nearest
+ *   a/b (or a neighbour of it);
+ *   atan(a/b) = k pi/256 + atan(t),  t = (a - c_k b) / (b + c_k a),  |t| < 0.019;
+ *   atan(t) / (2 pi) = t (D0 + D1 u + D2 u^2 + D3 u^3 + D4 u^4), u = t^2, the
+ *   Gregory series to t^9 (truncation below t^10 / 11 < 4e-19 relative),
+ *   evaluated by Estrin's scheme: (D0 + D1 u) + u^2 ((D2 + D3 u) + u^2 D4);
+ *   k pi/256 is k / 512 cycles and pi/2 is 1/4 cycle, both exact.
+ * The sign is that of q / i.  One division.
  */
-double orc_atan_ratio(double q, double i) {
+double orc_atan_cycles(double q, double i) {
     double a = fabs(q), b = fabs(i);
     int swap = a > b;
     if (swap) {
@@ -211,8 +237,8 @@ double orc_atan_ratio(double q, double i) {
     }
     float rf = (float)a / (float)b;
     int k = 0;
-    for (int j = 0; j < 8; ++j)
-        if (rf >= orc_mid_k[j]) k = j + 1;
+    for (int step = 32; step >= 1; step >>= 1)
+        if (rf >= orc_mid_k[k + step - 1]) k += step;
     double c = orc_tan_k[k];
     double num = c * b;
     num = a - num;
@@ -220,14 +246,18 @@ double orc_atan_ratio(double q, double i) {
     den = b + den;
     double t = num / den;
     double u = t * t;
-    double p = orc_series[7];
-    for (int j = 6; j >= 0; --j) {
-        p = p * u;
-        p = p + orc_series[j];
-    }
+    double u2 = u * u;
+    double p01 = orc_series[1] * u;
+    p01 = orc_series[0] + p01;
+    double p23 = orc_series[3] * u;
+    p23 = orc_series[2] + p23;
+    double p4 = orc_series[4] * u2;
+    double hi = p23 + p4;
+    hi = hi * u2;
+    double p = p01 + hi;
     double y = t * p;
-    y = orc_ang_k[k] + y;
-    if (swap) y = ORC_PI_2 - y;
+    y = (double)k / 512.0 + y;
+    if (swap) y = 0.25 - y;
     if ((q < 0.0) != (i < 0.0)) y = -y;
     return y;
 }
@@ -271,8 +301,8 @@ void orc_chan_init(orc_chan *ch, int32_t w, uint64_t phi, uint64_t r, double fs)
  *   f_code = 1.023e6 (1 + f_carr / 1575.42e6) + (4 Bn_dll) e_c   (carrier aided)
  * Re-quantisation, round half to even, with s = 2^32 / fs:
  *   w = rn(f_carr s) (wrapped to int32), r = rn(f_code s)
- * Divisions by the constants 2 pi and 1575.42e6 are multiplications by their
- * correctly rounded reciprocals.
+ * The carrier aiding is evaluated as 1.023e6 + f_carr / 1540 (1575.42 / 1.023
+ * = 1540), the division by a multiplication with the correctly rounded 1/1540.
  */
 void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
                int tap_e, int tap_p, int tap_l, double fs, uint64_t n_accum,
@@ -288,8 +318,7 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
     double ip = (double)acc[2 * tap_p], qp = (double)acc[2 * tap_p + 1];
     double e_pll;
     if (ip != 0.0) {
-        double y = orc_atan_ratio(qp, ip);
-        e_pll = y * ORC_INV_2PI;
+        e_pll = orc_atan_cycles(qp, ip);
     } else {
         e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
     }
@@ -313,10 +342,9 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
         num = kd * num;
         e_dll = num / den;
     }
-    double aid = f_carr * ORC_INV_L1;
-    aid = 1.0 + aid;
-    double f_code = 1.023e6 * aid;
+    double aid = f_carr * ORC_KAID;
     double corr = kdll * e_dll;
+    double f_code = 1.023e6 + aid;
     f_code = f_code + corr;
 
     double xw = f_carr * sfs;

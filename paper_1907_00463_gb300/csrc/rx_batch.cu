@@ -107,112 +107,93 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static
     extern __shared__ __align__(16) unsigned char smem[];
     const ItemSmem sm = carve_item_smem(smem, a.cpg, a.max_taps, NT);
     int32_t *run = reinterpret_cast<int32_t *>(smem + item_smem_bytes(a.cpg, a.max_taps, NT));
-    uint32_t *s_ep = reinterpret_cast<uint32_t *>(run + (size_t)a.cpg * a.max_taps * 2);
+    double *s_v = reinterpret_cast<double *>(run + (size_t)a.cpg * a.max_taps * 2);  // [cpg] x 3
+    double *s_fc = s_v + a.cpg, *s_fk = s_fc + a.cpg;
+    uint32_t *s_ep = reinterpret_cast<uint32_t *>(s_fk + a.cpg);
     const GroupDesc gd = a.groups[blockIdx.x];
     const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = NT / 32;
     for (uint32_t i = threadIdx.x; i < 64; i += NT) sm.tab[i] = a.tb.carrier[i];
     stage_constants<NT>(gd, a.tb, sm);
-    double v = 0.0, fc = 0.0, fk = 0.0;
-    if (threadIdx.x < nch) {
-        const uint32_t j = threadIdx.x;
+    for (uint32_t j = threadIdx.x; j < nch; j += NT) {
         sm.theta[j] = gd.theta[j];
         sm.w[j] = (uint32_t)gd.w[j];
         sm.phi[j] = gd.phi[j];
         sm.r[j] = (uint32_t)gd.r[j];
         sm.ab[j] = gd.acc_blocks[j];
         s_ep[j] = gd.epochs[j];
-        v = gd.v[j];
-        fc = gd.fcarr[j];
-        fk = gd.fcode[j];
+        s_v[j] = gd.v[j];
+        s_fc[j] = gd.fcarr[j];
+        s_fk[j] = gd.fcode[j];
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT)
+    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
         run[i] = sm.ab[i / per_ch] ? gd.acc[i] : 0;
-    const int8_t *base = a.iq + a.src_off[gd.src];
-    for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
+        sm.acc[i] = 0;
+    }
     __syncthreads();
-    const bool own_fold = nt <= 16;  // a channel's own thread folds its sums
+    const int8_t *base = a.iq + a.src_off[gd.src];
     for (uint32_t b = 0; b < a.n_blocks; ++b) {
         const int8_t *blk = base + (size_t)b * 2 * N;
         if (threadIdx.x == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
         correlate_group<NT>(nch, nt, N, blk, sm, sm.acc);
         __syncthreads();
-        if (!own_fold) {
-            for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) {
-                const uint32_t j = i / per_ch, e = i - j * per_ch;
-                const uint32_t val = (uint32_t)sm.acc[i] + (uint32_t)run[i];
-                if (sm.ab[j] + 1 == gd.L) {
-                    const uint32_t ep = s_ep[j];
-                    if (gd.dump_wrap || ep < gd.dump_slots) {
-                        const uint32_t slot = gd.dump_wrap ? ep % gd.dump_slots : ep;
-                        gd.dumps[(uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch + e] = (int32_t)val;
-                    }
-                    sm.acc[i] = (int32_t)val;
-                    run[i] = 0;
-                } else {
-                    run[i] = (int32_t)val;
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x < nch) {
-            const uint32_t j = threadIdx.x, w = sm.w[j];
+        // channel j: its sums are folded by the lanes of warp j mod nwarps, whose lane 0
+        // then advances the NCOs and, at an integration boundary, closes the loops
+        for (uint32_t j = warp; j < nch; j += nwarps) {
             const bool boundary = sm.ab[j] + 1 == gd.L;
             int32_t *A = sm.acc + (size_t)j * per_ch;
             int32_t *R = run + (size_t)j * per_ch;
-            if (own_fold) {
-                for (uint32_t e = 0; e < per_ch; ++e) {
-                    const uint32_t val = (uint32_t)A[e] + (uint32_t)R[e];
-                    if (boundary) {
-                        A[e] = (int32_t)val;
-                        R[e] = 0;
-                    } else {
-                        R[e] = (int32_t)val;
-                    }
-                }
-                if (boundary && (gd.dump_wrap || s_ep[j] < gd.dump_slots)) {
-                    const uint32_t slot = gd.dump_wrap ? s_ep[j] % gd.dump_slots : s_ep[j];
-                    int32_t *dst = gd.dumps + (uint64_t)slot * gd.dump_stride + (uint64_t)j * per_ch;
-                    for (uint32_t e = 0; e < per_ch; ++e) dst[e] = A[e];
+            const uint32_t ep = s_ep[j];
+            const bool store = boundary && (gd.dump_wrap || ep < gd.dump_slots);
+            int32_t *dst = gd.dumps + (uint64_t)(gd.dump_wrap ? ep % gd.dump_slots : ep) * gd.dump_stride +
+                           (uint64_t)j * per_ch;
+            for (uint32_t e = lane; e < per_ch; e += 32) {
+                const uint32_t val = (uint32_t)A[e] + (uint32_t)R[e];
+                if (boundary) {
+                    A[e] = (int32_t)val;
+                    R[e] = 0;
+                    if (store) dst[e] = (int32_t)val;
+                } else {
+                    R[e] = (int32_t)val;
                 }
             }
-            sm.theta[j] = sm.theta[j] + N * w;
-            sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
-            if (boundary) {
-                const int64_t *tp = sm.taps + (size_t)j * nt;
-                LoopOut o = loop_update(v, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
-                                        A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
-                                        tp[gd.tap_e], tp[gd.tap_l], gd.lc);
-                v = o.v;
-                fc = o.f_carr;
-                fk = o.f_code;
-                sm.w[j] = (uint32_t)o.w;
-                sm.r[j] = (uint32_t)o.r;
-                s_ep[j] += 1;
-                sm.ab[j] = 0;
-            } else {
-                sm.ab[j] = sm.ab[j] + 1;
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t w = sm.w[j];
+                sm.theta[j] = sm.theta[j] + N * w;
+                sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
+                if (boundary) {
+                    const int64_t *tp = sm.taps + (size_t)j * nt;
+                    LoopOut o = loop_update(s_v[j], A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
+                                            A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
+                                            tp[gd.tap_e], tp[gd.tap_l], gd.lc);
+                    s_v[j] = o.v;
+                    s_fc[j] = o.f_carr;
+                    s_fk[j] = o.f_code;
+                    sm.w[j] = (uint32_t)o.w;
+                    sm.r[j] = (uint32_t)o.r;
+                    s_ep[j] = ep + 1;
+                    sm.ab[j] = 0;
+                } else {
+                    sm.ab[j] = sm.ab[j] + 1;
+                }
             }
-            if (own_fold)
-                for (uint32_t e = 0; e < per_ch; ++e) A[e] = 0;
-        }
-        if (!own_fold) {
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) sm.acc[i] = 0;
+            __syncwarp();
+            for (uint32_t e = lane; e < per_ch; e += 32) A[e] = 0;
         }
         __syncthreads();
     }
-    if (threadIdx.x < nch) {
-        const uint32_t j = threadIdx.x;
+    for (uint32_t j = threadIdx.x; j < nch; j += NT) {
         gd.theta[j] = sm.theta[j];
         gd.w[j] = (int32_t)sm.w[j];
         gd.phi[j] = sm.phi[j];
         gd.r[j] = sm.r[j];
         gd.acc_blocks[j] = sm.ab[j];
         gd.epochs[j] = s_ep[j];
-        gd.v[j] = v;
-        gd.fcarr[j] = fc;
-        gd.fcode[j] = fk;
+        gd.v[j] = s_v[j];
+        gd.fcarr[j] = s_fc[j];
+        gd.fcode[j] = s_fk[j];
     }
     for (uint32_t i = threadIdx.x; i < nch * per_ch; i += NT) gd.acc[i] = run[i];
 }
@@ -288,7 +269,7 @@ uint32_t default_cpg(const rx_batch b) {
 }
 
 size_t static_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt) {
-    return item_smem_bytes(cpg, mt, nt) + (size_t)cpg * mt * 8 + (size_t)cpg * 4 + 16;
+    return item_smem_bytes(cpg, mt, nt) + (size_t)cpg * mt * 8 + (size_t)cpg * 24 + (size_t)cpg * 4 + 16;
 }
 
 template <int NT>

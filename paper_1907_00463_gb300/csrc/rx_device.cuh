@@ -277,36 +277,60 @@ __device__ __forceinline__ void seg_group_reduce(const int4 *slice, uint64_t ph0
 // loop filter (Table 3), FP64, bit-identical to the CPU definition
 // ----------------------------------------------------------------------------
 
-#define RXD_PI_2 1.5707963267948966
 #define RXD_SQRT2 1.4142135623730951
-#define RXD_INV_2PI 0.15915494309189535
-#define RXD_INV_L1 6.347513678891978e-10 /* 1 / 1575.42e6 */
+#define RXD_KAID 0.0006493506493506494 /* 1 / 1540 = 1.023e6 / 1575.42e6 */
 #define RXD_TWO_M32 2.3283064365386963e-10 /* 2^-32, exact */
 
-// Breakpoints tan(k pi/32), angles k pi/32 (k = 0..8), single-precision midpoints
-// tan((j + 1/2) pi/32) (j = 0..7) and the Gregory coefficients (-1)^j / (2j + 1):
-// correctly rounded values.
-static __constant__ double kAtanTan[9] = {0.0, 0.09849140335716425, 0.198912367379658,
-                                          0.3033466836073424, 0.41421356237309503,
-                                          0.5345111359507917, 0.6681786379192989,
-                                          0.8206787908286604, 1.0};
-static __constant__ double kAtanAng[9] = {0.0, 0.09817477042468103, 0.19634954084936207,
-                                          0.2945243112740431, 0.39269908169872414,
-                                          0.4908738521234052, 0.5890486225480862,
-                                          0.6872233929727672, 0.7853981633974483};
-static __constant__ float kAtanMid[8] = {0.049126848578453064f, 0.1483359932899475f,
-                                         0.25048696994781494f, 0.3578057289123535f,
-                                         0.4729647636413574f, 0.599376916885376f,
-                                         0.7416505217552185f, 0.9063471555709839f};
-static __constant__ double kAtanSeries[8] = {1.0,       -1.0 / 3.0,  1.0 / 5.0,  -1.0 / 7.0,
-                                             1.0 / 9.0, -1.0 / 11.0, 1.0 / 13.0, -1.0 / 15.0};
+// Breakpoints tan(k pi/256) (k = 0..64), single-precision midpoints
+// tan((j + 1/2) pi/256) (j = 0..63), and the Gregory coefficients divided by 2 pi,
+// (-1)^j / ((2j + 1) 2 pi) (j = 0..4): correctly rounded values.
+static __constant__ double kAtanTan[65] = {
+    0.0, 0.012272462379566276, 0.024548622108925444, 0.03683218099484564,
+    0.049126849769467254, 0.061436352581593766, 0.07376443152244928, 0.0861148511976279,
+    0.09849140335716425, 0.11089791159591303, 0.12333823613673868, 0.13581627870938773,
+    0.14833598753834742, 0.16090136245348916, 0.17351646013785577, 0.18618539952758373,
+    0.198912367379658, 0.21170162402398335, 0.2245575093171293, 0.23748444881607017,
+    0.25048696019130545, 0.263569659899918, 0.2767372701404143, 0.2899946261126061,
+    0.3033466836073424, 0.3167985269526038, 0.3303553773443339, 0.3440226015924263,
+    0.3578057213145241, 0.37171042261274345, 0.38574256627112125, 0.3999081985145372,
+    0.41421356237309503, 0.4286651096994995, 0.44326951389086433, 0.4580336833706724,
+    0.4729647758913199, 0.48807021372286286, 0.5033576997992942, 0.5188352348999757,
+    0.5345111359507917, 0.5503940555372641, 0.566493002730344, 0.5828173653349761,
+    0.5993769336819238, 0.6161819260948661, 0.6332430161775692, 0.6505713620801533,
+    0.6681786379192989, 0.6860770675448629, 0.7042794608650442, 0.7227992529642059,
+    0.7416505462720354, 0.7608481560702512, 0.7804076596539437, 0.8003454494993201,
+    0.8206787908286604, 0.8414258840072548, 0.8626059322567399, 0.8842392152253499,
+    0.9063471690191471, 0.9289524733703675, 0.9520791467009253, 0.9757526499323765,
+    1.0,
+};
+static __constant__ float kAtanMid[64] = {
+    0.006136000156402588f, 0.0184098482131958f, 0.030689245089888573f, 0.042977895587682724f,
+    0.05527951195836067f, 0.06759783625602722f, 0.07993661612272263f, 0.09229962527751923f,
+    0.10469067096710205f, 0.11711360514163971f, 0.1295723021030426f, 0.1420706808567047f,
+    0.1546127200126648f, 0.1672024428844452f, 0.179843932390213f, 0.19254136085510254f,
+    0.20529894530773163f, 0.21812096238136292f, 0.23101182281970978f, 0.24397596716880798f,
+    0.25701799988746643f, 0.2701425552368164f, 0.28335443139076233f, 0.2966585159301758f,
+    0.3100598156452179f, 0.32356348633766174f, 0.3371748626232147f, 0.3508993089199066f,
+    0.3647425174713135f, 0.37871018052101135f, 0.39280831813812256f, 0.4070430099964142f,
+    0.4214206635951996f, 0.4359477758407593f, 0.45063120126724243f, 0.46547791361808777f,
+    0.4804952144622803f, 0.4956907033920288f, 0.5110722184181213f, 0.5266478657722473f,
+    0.5424261689186096f, 0.558415949344635f, 0.5746263861656189f, 0.5910671353340149f,
+    0.6077480912208557f, 0.6246797442436218f, 0.6418730616569519f, 0.6593393683433533f,
+    0.6770906448364258f, 0.695139467716217f, 0.7134988307952881f, 0.7321825623512268f,
+    0.7512050867080688f, 0.7705816626548767f, 0.7903282046318054f, 0.8104615807533264f,
+    0.8309994339942932f, 0.8519605398178101f, 0.8733646273612976f, 0.8952324986457825f,
+    0.9175862073898315f, 0.940449059009552f, 0.9638459086418152f, 0.9878028631210327f,
+};
+static __constant__ double kAtanSeries[5] = {0.15915494309189535, -0.05305164769729845, 0.03183098861837907,
+                                             -0.022736420441699334, 0.017683882565766147};
 
-// atan(q / i), i != 0, two-quadrant, by table-driven argument reduction: with
-// a = |q|, b = |i| (swapped if a > b, atan(x) = pi/2 - atan(1/x)), the breakpoint
-// c_k = tan(k pi/32) nearest a/b (chosen from a single-precision estimate),
-// atan(a/b) = k pi/32 + atan(t), t = (a - c_k b) / (b + c_k a), and atan(t) by the
-// Gregory series to t^15 in Horner form.  One division.
-__device__ __forceinline__ double atan_ratio(double q, double i) {
+// atan(q / i) / (2 pi), in cycles, i != 0, two-quadrant, by table-driven argument
+// reduction: with a = |q|, b = |i| (swapped if a > b: atan(x) = pi/2 - atan(1/x)),
+// k = the number of midpoints at or below a/b (single-precision estimate, binary
+// search), atan(a/b) = k pi/256 + atan(t), t = (a - c_k b) / (b + c_k a), and
+// atan(t) / (2 pi) from the Gregory series to t^9 by Estrin's scheme.  k pi/256 is
+// k / 512 cycles and pi/2 is 1/4 cycle, exactly.  One division.
+__device__ __forceinline__ double atan_cycles(double q, double i) {
     double a = fabs(q), b = fabs(i);
     const bool swap = a > b;
     if (swap) {
@@ -317,8 +341,8 @@ __device__ __forceinline__ double atan_ratio(double q, double i) {
     const float rf = __fdiv_rn(__double2float_rn(a), __double2float_rn(b));
     int k = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (rf >= kAtanMid[j]) k = j + 1;
+    for (int step = 32; step >= 1; step >>= 1)
+        if (rf >= kAtanMid[k + step - 1]) k += step;
     const double c = kAtanTan[k];
     double num = __dmul_rn(c, b);
     num = __dsub_rn(a, num);
@@ -326,15 +350,18 @@ __device__ __forceinline__ double atan_ratio(double q, double i) {
     den = __dadd_rn(b, den);
     const double t = __ddiv_rn(num, den);
     const double u = __dmul_rn(t, t);
-    double p = kAtanSeries[7];
-#pragma unroll
-    for (int j = 6; j >= 0; --j) {
-        p = __dmul_rn(p, u);
-        p = __dadd_rn(p, kAtanSeries[j]);
-    }
+    const double u2 = __dmul_rn(u, u);
+    double p01 = __dmul_rn(kAtanSeries[1], u);
+    p01 = __dadd_rn(kAtanSeries[0], p01);
+    double p23 = __dmul_rn(kAtanSeries[3], u);
+    p23 = __dadd_rn(kAtanSeries[2], p23);
+    const double p4 = __dmul_rn(kAtanSeries[4], u2);
+    double hi = __dadd_rn(p23, p4);
+    hi = __dmul_rn(hi, u2);
+    const double p = __dadd_rn(p01, hi);
     double y = __dmul_rn(t, p);
-    y = __dadd_rn(kAtanAng[k], y);
-    if (swap) y = __dsub_rn(RXD_PI_2, y);
+    y = __dadd_rn((double)k / 512.0, y);
+    if (swap) y = __dsub_rn(0.25, y);
     if ((q < 0.0) != (i < 0.0)) y = -y;
     return y;
 }
@@ -368,7 +395,7 @@ struct LoopOut {
 
 // One loop update (Table 3) from the dumped E/P/L sums:
 //   e_p = atan(Q_P / I_P) / (2 pi) (+-1/4 if I_P = 0);  v += k1 e_p;  f_carr = v + k2 e_p
-//   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|);  f_code = 1.023e6 (1 + f_carr / 1575.42e6) + kdll e_c
+//   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|);  f_code = 1.023e6 + f_carr / 1540 + kdll e_c
 //   w = rn(f_carr sfs) mod 2^32,  r = rn(f_code sfs)
 __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
                                                int32_t qpr, int32_t il, int32_t ql,
@@ -378,7 +405,7 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
     const double ip = (double)ipr, qp = (double)qpr;
     double e_pll;
     if (ip != 0.0) {
-        e_pll = __dmul_rn(atan_ratio(qp, ip), RXD_INV_2PI);
+        e_pll = atan_cycles(qp, ip);
     } else {
         e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
     }
@@ -401,10 +428,9 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
         num = __dmul_rn(kd, num);
         e_dll = __ddiv_rn(num, den);
     }
-    double aid = __dmul_rn(f_carr, RXD_INV_L1);
-    aid = __dadd_rn(1.0, aid);
-    double f_code = __dmul_rn(1.023e6, aid);
+    const double aid = __dmul_rn(f_carr, RXD_KAID);
     const double corr = __dmul_rn(lc.kdll, e_dll);
+    double f_code = __dadd_rn(1.023e6, aid);
     f_code = __dadd_rn(f_code, corr);
 
     double xw = __dmul_rn(f_carr, lc.sfs);

@@ -2,8 +2,8 @@
 normalised early-minus-late envelope DLL with carrier aiding, 2nd-order PLL,
 1st-order DLL) and NCO re-quantisation.
 
-The arctangent of Q/I is checked against the C library's atan (error bound),
-by its symmetries and at the reduction's breakpoints; the loop update by closed forms (zero error leaves the carrier word
+The arctangent of Q/I (in cycles) is checked against the C library's atan
+(error bound), by its symmetries and at the reduction's breakpoints; the loop update by closed forms (zero error leaves the carrier word
 fixed; a constant error grows the integrator arithmetically; a known E/L pair
 gives a known code-rate correction); the quantiser by exact half-way cases; the
 closed loop by convergence on a synthetic signal with known Doppler and code
@@ -26,7 +26,10 @@ def _ulp_diff(a, b):
     return abs(a - b) / math.ulp(max(abs(a), abs(b)))
 
 
-def test_atan_ratio_against_libm():
+TWO_PI = 2 * math.pi
+
+
+def test_atan_cycles_against_libm():
     # integer numerators/denominators as the accumulators give them, every octant
     g = np.random.default_rng(1)
     pairs = [(0, 5), (1, 1), (-1, 1), (7, -7), (3, 4), (2**31 - 1, 1), (1, 2**31 - 1),
@@ -35,26 +38,26 @@ def test_atan_ratio_against_libm():
     pairs += [(int(a), int(b)) for a, b in g.integers(-3000, 3000, size=(20000, 2)) if b != 0]
     worst = 0.0
     for q, i in pairs:
-        y = oracle.atan_ratio(q, i)
-        ref = math.atan(q / i)
+        y = oracle.atan_cycles(q, i)
+        ref = math.atan(q / i) / TWO_PI
         worst = max(worst, abs(y - ref) / math.ulp(max(abs(ref), 1e-300)))
     assert worst <= 4.0, worst
 
 
-def test_atan_ratio_identities():
-    assert oracle.atan_ratio(0.0, 1.0) == 0.0
-    assert oracle.atan_ratio(1.0, 1.0) == math.pi / 4
+def test_atan_cycles_identities():
+    assert oracle.atan_cycles(0.0, 1.0) == 0.0
+    assert oracle.atan_cycles(1.0, 1.0) == 0.125            # pi/4 = 1/8 cycle, exactly
     g = np.random.default_rng(2)
     for q, i in g.integers(1, 10**6, size=(3000, 2)):
         q, i = float(q), float(i)
-        assert oracle.atan_ratio(-q, i) == -oracle.atan_ratio(q, i)
-        assert oracle.atan_ratio(q, -i) == -oracle.atan_ratio(q, i)
-        assert oracle.atan_ratio(-q, -i) == oracle.atan_ratio(q, i)
-        assert abs(oracle.atan_ratio(q, i) + oracle.atan_ratio(i, q) - math.pi / 2) < 8.9e-16
-    # at every breakpoint tan(k pi/32) the reduction leaves t = 0 and returns k pi/32
-    for k in range(9):
-        c = math.tan(k * math.pi / 32)
-        assert abs(oracle.atan_ratio(c, 1.0) - k * math.pi / 32) < 4.5e-16
+        assert oracle.atan_cycles(-q, i) == -oracle.atan_cycles(q, i)
+        assert oracle.atan_cycles(q, -i) == -oracle.atan_cycles(q, i)
+        assert oracle.atan_cycles(-q, -i) == oracle.atan_cycles(q, i)
+        assert abs(oracle.atan_cycles(q, i) + oracle.atan_cycles(i, q) - 0.25) < 1.2e-16
+    # at a breakpoint tan(k pi/256) the reduction leaves t ~ 0 and returns k/512 cycles
+    for k in range(65):
+        c = math.tan(k * math.pi / 256)
+        assert abs(oracle.atan_cycles(c, 1.0) - k / 512) < 1.2e-16
 
 
 def _acc(ip, qp, e=(0, 0), l=(0, 0)):
