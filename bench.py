@@ -441,7 +441,7 @@ def run_ours(args):
                    "receivers_per_gpu": len(receivers), "blocks": n_blocks, "channels": 12, "taps": 5,
                    "fs_hz": FS, "tiles": {"channels_per_item": tiles[0], "threads": tiles[1],
                                           "ctas_per_sm": tiles[2],
-                                          "schedule": ["dynamic", "static"][tiles[3]]},
+                                          "schedule": ["dynamic", "static", "pipelined"][tiles[3]]},
                    "autotune": tune,
                    "l2": ("inputs larger than L2; no flush" if in_bytes > 129e6 else
                           "inputs fit in L2 (profiling case only)"),

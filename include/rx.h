@@ -245,16 +245,31 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
 
 #define RX_SCHED_DYNAMIC 0u  /* work items (channel group, block) by atomic ticket */
 #define RX_SCHED_STATIC 1u   /* one CTA per channel group for the whole run */
+#define RX_SCHED_PIPE 2u     /* as STATIC, with correlation and loop-filter warps
+                                overlapped across the group's channels */
 
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
- * correlated together by one CTA (0 = choose); threads: CTA size (128, 256 or
- * 512; 0 = choose); ctas_per_sm: resident CTAs per SM for the dynamic
- * schedule (0 = as many as fit); schedule: RX_SCHED_DYNAMIC or
- * RX_SCHED_STATIC.  Both schedules give identical results.  Takes effect at
- * the next run (the graph is re-recorded). */
+ * correlated together by one CTA (0 = choose); threads: correlating threads
+ * of a CTA (128, 256 or 512; 0 = choose; RX_SCHED_PIPE adds one filter warp,
+ * two from 4 channels per item); ctas_per_sm: resident CTAs per SM for the
+ * dynamic schedule (0 = as many as fit); schedule: RX_SCHED_DYNAMIC,
+ * RX_SCHED_STATIC or RX_SCHED_PIPE.  All schedules give identical results.
+ * Takes effect at the next run (the graph is re-recorded).  A wait inside a
+ * CTA of RX_SCHED_PIPE that exceeds the handle's time limit ends the run with
+ * RX_ETIMEOUT at the next synchronising call. */
 rx_status rx_batch_set_tiles(rx_batch b, uint32_t channels_per_item,
                              uint32_t threads, uint32_t ctas_per_sm,
                              uint32_t schedule);
+
+#define RX_WAIT_TEST_STALL 1u /* failure-detection test hook, see below */
+
+/* Time limit of every wait inside the persistent kernel (default 2 s; from
+ * 1 us to 60 s), after which the run stops and the next synchronising call
+ * returns RX_ETIMEOUT; the handle stays usable.  flags: 0, or
+ * RX_WAIT_TEST_STALL, which makes the first CTA of every RX_SCHED_PIPE run
+ * wait on a barrier that nothing completes, so that the limit and its report
+ * can be tested without any device fault.  Takes effect at the next run. */
+rx_status rx_batch_set_wait_limit(rx_batch b, uint64_t timeout_ns, uint32_t flags);
 
 /* Read back the tiles in use (after the first run or set_tiles). */
 rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,

@@ -243,6 +243,8 @@ struct rx_batch_s {
     uint32_t g_blocks = 0, g_flags = 0, g_cpg = 0, g_threads = 0, g_ctas = 0;
     uint32_t last_launches = 0;
     uint64_t timeout_ns = 2000000000ull;
+    uint32_t stall = 0;
+    uint32_t pipe_stage = 0;        // staging buffer bytes of the pipelined schedule (0: none)
     std::string err;
 };
 
@@ -267,6 +269,10 @@ uint32_t default_cpg(const rx_batch b) {
     }
     return best;
 }
+
+// Filter warps of the pipelined schedule: one closes up to three channels' loops per
+// block in the shadow of the correlation; beyond that two share them.
+uint32_t pipe_filter_warps(uint32_t cpg) { return cpg >= 4 ? 2u : 1u; }
 
 size_t static_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt) {
     return item_smem_bytes(cpg, mt, nt) + (size_t)cpg * mt * 8 + (size_t)cpg * 24 + (size_t)cpg * 4 + 16;
@@ -386,6 +392,18 @@ rx_status build_groups(rx_batch b) {
         const size_t ss = static_smem_bytes(b->cpg, b->max_taps, b->threads);
         occ = b->threads == 128 ? occupancy_static<128>(ss)
                                 : b->threads == 512 ? occupancy_static<512>(ss) : occupancy_static<256>(ss);
+    } else if (b->schedule == RX_SCHED_PIPE) {
+        // Stage blocks in shared memory when that still lets every group be resident
+        // at once (or at least keeps as many resident as reading from global would).
+        uint32_t max_n = 0;
+        for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
+        const uint32_t fw = pipe_filter_warps(b->cpg);
+        const uint32_t sb = (uint32_t)pipe_stage_bytes(max_n);
+        const int occ_st = pipe_occupancy(b->threads, fw, true, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, sb));
+        const int occ_gl = pipe_occupancy(b->threads, fw, false, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, 0));
+        const bool one_wave = (uint64_t)occ_st * b->tables->sm_count >= b->G;
+        b->pipe_stage = (occ_st > 0 && (one_wave || occ_st >= occ_gl)) ? sb : 0u;
+        occ = b->pipe_stage ? occ_st : occ_gl;
     }
     if (occ <= 0) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
     uint32_t per_sm = b->ctas_per_sm ? std::min<uint32_t>(b->ctas_per_sm, occ) : (uint32_t)occ;
@@ -420,6 +438,16 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     ba.max_taps = b->max_taps;
     ba.timeout_ns = b->timeout_ns;
     rx_status s;
+    if (b->schedule == RX_SCHED_PIPE) {
+        PipeArgs pa{b->d_groups, b->d_rxoff, iq,       ba.tb,      ba.err,        b->timeout_ns,
+                    n_blocks,    b->cpg,     b->max_taps, b->stall, b->pipe_stage};
+        cudaError_t ce = pipe_launch(b->threads, pipe_filter_warps(b->cpg), b->G,
+                                     pipe_smem_bytes(b->cpg, b->max_taps, b->threads, b->pipe_stage), b->stream,
+                                     pa);
+        if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(ce)));
+        RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
+        return RX_OK;
+    }
     if (b->schedule == RX_SCHED_STATIC) {
         StaticArgs sa{b->d_groups, b->d_rxoff, iq, ba.tb, n_blocks, b->cpg, b->max_taps};
         const size_t ss = static_smem_bytes(b->cpg, b->max_taps, b->threads);
@@ -632,7 +660,7 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
 extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threads, uint32_t ctas_per_sm,
                                         uint32_t schedule) {
     if (!b) return RX_EINVAL;
-    if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC)
+    if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC && schedule != RX_SCHED_PIPE)
         return berr(b, RX_EINVAL, "unknown schedule");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return berr(b, RX_EINVAL, "threads must be 128, 256 or 512");
@@ -644,6 +672,19 @@ extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threa
     b->ctas_per_sm = ctas_per_sm;
     b->schedule = schedule;
     b->groups_dirty = true;
+    drop_graph(b);
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_set_wait_limit(rx_batch b, uint64_t timeout_ns, uint32_t flags) {
+    if (!b) return RX_EINVAL;
+    if (timeout_ns < 1000ull || timeout_ns > 60000000000ull)
+        return berr(b, RX_EINVAL, "timeout_ns must be in [1 us, 60 s]");
+    if (flags & ~RX_WAIT_TEST_STALL) return berr(b, RX_EINVAL, "unknown wait flags");
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->timeout_ns = timeout_ns;
+    b->stall = (flags & RX_WAIT_TEST_STALL) ? 1u : 0u;
     drop_graph(b);
     return RX_OK;
 }
@@ -852,9 +893,10 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
     uint32_t max_ch = 1;
     for (const rx_receiver_desc &d : b->rx) max_ch = std::max(max_ch, d.n_channels);
     std::vector<std::array<uint32_t, 4>> cands;
-    for (uint32_t sched : {RX_SCHED_STATIC, RX_SCHED_DYNAMIC})
+    for (uint32_t sched : {RX_SCHED_PIPE, RX_SCHED_STATIC, RX_SCHED_DYNAMIC})
         for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u, 8u, 12u, 16u}) {
             if (cpg > max_ch) continue;
+            if (sched == RX_SCHED_PIPE && cpg == 1 && max_ch > 1) continue;  // nothing to overlap
             for (uint32_t nt : {128u, 256u, 512u}) {
                 if (sched == RX_SCHED_DYNAMIC && nt == 512) continue;
                 cands.push_back({cpg, nt, 0u, sched});

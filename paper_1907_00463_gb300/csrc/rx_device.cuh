@@ -106,6 +106,57 @@ __device__ __forceinline__ void load_chunk(const int8_t *__restrict__ blk, uint3
     }
 }
 
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint16_t lds16(uint32_t a) {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+
+// load_chunk for a block staged in shared memory (same contract; blk is a generic
+// pointer into this CTA's shared memory).
+__device__ __forceinline__ void load_chunk_shared(const int8_t *blk, uint32_t s0, uint32_t n,
+                                                  bool aligned16, bool aligned4, uint32_t (&x)[SPT]) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(blk) + 2u * s0;
+    if (s0 + SPT <= n && aligned16) {
+        const uint4 u = lds128(a), v = lds128(a + 16);
+        unpack2(u.x, x[0], x[1]);
+        unpack2(u.y, x[2], x[3]);
+        unpack2(u.z, x[4], x[5]);
+        unpack2(u.w, x[6], x[7]);
+        unpack2(v.x, x[8], x[9]);
+        unpack2(v.y, x[10], x[11]);
+        unpack2(v.z, x[12], x[13]);
+        unpack2(v.w, x[14], x[15]);
+    } else if (s0 + SPT <= n && aligned4) {
+#pragma unroll
+        for (int j = 0; j < SPT / 2; ++j) unpack2(lds32(a + 4 * j), x[2 * j], x[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) x[j] = (s0 + j < n) ? unpack1(lds16(a + 2 * j)) : 0u;
+    }
+}
+
+template <bool SH>
+__device__ __forceinline__ void load_chunk_from(const int8_t *blk, uint32_t s0, uint32_t n, bool aligned16,
+                                                bool aligned4, uint32_t (&x)[SPT]) {
+    if constexpr (SH)
+        load_chunk_shared(blk, s0, n, aligned16, aligned4, x);
+    else
+        load_chunk(blk, s0, n, aligned16, aligned4, x);
+}
+
 // ----------------------------------------------------------------------------
 // direct-form correlation of one chunk for one channel and TT taps
 // ----------------------------------------------------------------------------

@@ -85,7 +85,7 @@ __device__ inline ItemSmem carve_item_smem(unsigned char *base, uint32_t cpg, ui
     return m;
 }
 
-template <int TT, int NT>
+template <int TT, int NT, bool SH = false>
 __device__ __forceinline__ void item_direct(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                             uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                             const int64_t *s_taps, const uint32_t *s_code,
@@ -97,7 +97,7 @@ __device__ __forceinline__ void item_direct(const int8_t *blk, uint32_t N, bool 
     for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
-        load_chunk(blk, s0, N, a16, a4, x);
+        load_chunk_from<SH>(blk, s0, N, a16, a4, x);
         corr_chunk<TT>(x, theta + s0 * w, w, reduce_code_phase(phi + (uint64_t)s0 * r), r, s_taps,
                        s_code, s_tab, sI, sQ, mI, mQ);
     }
@@ -114,7 +114,7 @@ __device__ __forceinline__ void item_direct(const int8_t *blk, uint32_t N, bool 
 }
 
 // Chip-segment form with all taps of one channel in registers across passes (T <= 8).
-template <int S, int TT, int NT>
+template <int S, int TT, int NT, bool SH = false>
 __device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                          uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                          uint32_t magic, const int64_t *s_taps,
@@ -127,7 +127,7 @@ __device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16
     for (uint32_t j = threadIdx.x; j < nchunks; j += NT) {
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
-        load_chunk(blk, s0, N, a16, a4, x);
+        load_chunk_from<SH>(blk, s0, N, a16, a4, x);
         seg_prefix<S>(x, theta + s0 * w, w, s_tab, slice);
         seg_taps<S, TT>(slice, reduce_code_phase(phi + (uint64_t)s0 * r), r, magic, s_taps, s_pair,
                         aI, aQ);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16
 
 // Chip-segment form for many taps: a chunk's running sums are made once and shared
 // by every tap group, which reduces after each pass.
-template <int S, int NT>
+template <int S, int NT, bool SH = false>
 __device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                               uint32_t theta, uint32_t w, uint64_t phi,
                                               uint32_t r, uint32_t magic, uint32_t nt,
@@ -160,7 +160,7 @@ __device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, boo
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
         if (j < nchunks) {
-            load_chunk(blk, s0, N, a16, a4, x);
+            load_chunk_from<SH>(blk, s0, N, a16, a4, x);
         } else {
 #pragma unroll
             for (int i = 0; i < SPT; ++i) x[i] = 0u;
@@ -184,22 +184,22 @@ __device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, boo
     }
 }
 
-template <int S, int NT>
+template <int S, int NT, bool SH = false>
 __device__ __forceinline__ void channel_seg(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                             uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                             uint32_t nt, const int64_t *tp, const uint16_t *pr,
                                             const uint32_t *s_tab, int4 *slice, int32_t *red) {
     const uint32_t mg = seg_magic(r);
     switch (nt) {
-        case 1: item_seg<S, 1, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 2: item_seg<S, 2, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 3: item_seg<S, 3, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 4: item_seg<S, 4, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 5: item_seg<S, 5, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 6: item_seg<S, 6, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 7: item_seg<S, 7, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        case 8: item_seg<S, 8, NT>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
-        default: item_seg_many<S, NT>(blk, N, a16, a4, theta, w, phi, r, mg, nt, tp, pr, s_tab, slice, red); break;
+        case 1: item_seg<S, 1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 2: item_seg<S, 2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 3: item_seg<S, 3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 4: item_seg<S, 4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 5: item_seg<S, 5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 6: item_seg<S, 6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 7: item_seg<S, 7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        case 8: item_seg<S, 8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red); break;
+        default: item_seg_many<S, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, nt, tp, pr, s_tab, slice, red); break;
     }
 }
 
@@ -242,42 +242,50 @@ __device__ __forceinline__ void stage_constants(const GroupDesc &gd, const Table
     }
 }
 
+// Correlate channel j of the group over one block into red[tap][2] (shared, zeroed
+// by the caller; every warp adds its partial sums with shared atomics).  Threads
+// 0..NT-1 take part; NCO state at the block start comes from sm.theta/w/phi/r.
+template <int NT, bool SH = false>
+__device__ __forceinline__ void correlate_channel(uint32_t j, uint32_t nt, uint32_t N,
+                                                  const int8_t *blk, bool a16, bool a4,
+                                                  const ItemSmem &sm, int32_t *red) {
+    int4 *slice = sm.slices + threadIdx.x * SLICE_INT4;
+    const uint32_t theta = sm.theta[j], w = sm.w[j], r = sm.r[j];
+    const uint64_t phi = sm.phi[j];
+    const int64_t *tp = sm.taps + (size_t)j * nt;
+    const int mode = seg_mode(r);
+    if (mode == 16) {
+        channel_seg<16, NT, SH>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
+                            sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
+    } else if (mode == 8) {
+        channel_seg<8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
+                           sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
+    } else {
+        const uint32_t *cd = sm.code + (size_t)j * EXT_WORDS;
+        for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
+            switch (min((uint32_t)TAP_GROUP, nt - t0)) {
+                case 1: item_direct<1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 2: item_direct<2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 3: item_direct<3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 4: item_direct<4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 5: item_direct<5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 6: item_direct<6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                case 7: item_direct<7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+                default: item_direct<8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
+            }
+        }
+    }
+}
+
 // Correlate the group's channels over one block into red[channel][tap][2] (shared,
-// zeroed by the caller).  NCO state at the block start comes from sm.theta/w/phi/r.
+// zeroed by the caller).
 template <int NT>
 __device__ __forceinline__ void correlate_group(uint32_t nch, uint32_t nt, uint32_t N,
                                                 const int8_t *blk, const ItemSmem &sm,
                                                 int32_t *red_base) {
     const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-    int4 *slice = sm.slices + threadIdx.x * SLICE_INT4;
-    for (uint32_t j = 0; j < nch; ++j) {
-        const uint32_t theta = sm.theta[j], w = sm.w[j], r = sm.r[j];
-        const uint64_t phi = sm.phi[j];
-        const int64_t *tp = sm.taps + (size_t)j * nt;
-        int32_t *red = red_base + (size_t)j * nt * 2;
-        const int mode = seg_mode(r);
-        if (mode == 16) {
-            channel_seg<16, NT>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
-                                sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
-        } else if (mode == 8) {
-            channel_seg<8, NT>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
-                               sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red);
-        } else {
-            const uint32_t *cd = sm.code + (size_t)j * EXT_WORDS;
-            for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
-                switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-                    case 1: item_direct<1, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 2: item_direct<2, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 3: item_direct<3, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 4: item_direct<4, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 5: item_direct<5, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 6: item_direct<6, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    case 7: item_direct<7, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                    default: item_direct<8, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0); break;
-                }
-            }
-        }
-    }
+    for (uint32_t j = 0; j < nch; ++j)
+        correlate_channel<NT>(j, nt, N, blk, a16, a4, sm, red_base + (size_t)j * nt * 2);
 }
 
 // The item body: all threads of the CTA call it; the caller has waited for the
@@ -346,5 +354,33 @@ __device__ __forceinline__ void process_item(const GroupDesc &gd, const int8_t *
     }
     __syncthreads();
 }
+
+// ----------------------------------------------------------------------------
+// Pipelined static schedule (rx_pipe.cu)
+// ----------------------------------------------------------------------------
+
+struct PipeArgs {
+    const GroupDesc *groups;
+    const uint64_t *src_off;   // byte offset of each receiver's samples
+    const int8_t *iq;
+    Tables tb;
+    uint32_t *err;             // [4]: code, 0xffffffff, group, block
+    uint64_t timeout_ns;       // limit on any one wait inside a CTA
+    uint32_t n_blocks;
+    uint32_t cpg;
+    uint32_t max_taps;
+    uint32_t stall;            // 1: CTA 0 first waits on a barrier that nothing completes
+    uint32_t stage_bytes;      // bytes of one staging buffer (0: samples read from global)
+};
+
+// Staging buffer for blocks of at most max_n samples.
+size_t pipe_stage_bytes(uint32_t max_n);
+// Dynamic shared memory of one CTA with nt correlation threads (stage_bytes 0: unstaged).
+size_t pipe_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t stage_bytes);
+// Resident CTAs per SM for nt correlation threads and filter_warps filter warps.
+int pipe_occupancy(uint32_t nt, uint32_t filter_warps, bool staged, size_t smem);
+// One CTA per group (grid = number of groups).
+cudaError_t pipe_launch(uint32_t nt, uint32_t filter_warps, uint32_t grid, size_t smem,
+                        cudaStream_t stream, const PipeArgs &a);
 
 }  // namespace rxd

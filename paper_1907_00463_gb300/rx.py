@@ -22,6 +22,8 @@ RX_RUN_RESTART = 1
 RX_RUN_NO_GRAPH = 2
 RX_SCHED_DYNAMIC = 0
 RX_SCHED_STATIC = 1
+RX_SCHED_PIPE = 2
+RX_WAIT_TEST_STALL = 1
 
 
 class RxError(RuntimeError):
@@ -114,6 +116,7 @@ SIGNATURES = [
     ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
+    ("rx_batch_set_wait_limit", C.c_int, [P, C.c_uint64, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                      C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     ("rx_batch_autotune", C.c_int, [P, P, P, C.c_uint32, C.POINTER(C.c_uint32),
@@ -336,6 +339,11 @@ def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per
     lib = load()
     _check(b, lib.rx_batch_set_tiles(b, channels_per_item, threads, ctas_per_sm, schedule),
            lib.rx_batch_last_error)
+
+
+def rx_batch_set_wait_limit(b, timeout_ns: int, flags: int = 0):
+    lib = load()
+    _check(b, lib.rx_batch_set_wait_limit(b, int(timeout_ns), int(flags)), lib.rx_batch_last_error)
 
 
 def rx_batch_get_tiles(b) -> tuple[int, int, int, int]:

@@ -81,10 +81,11 @@ def test_uneven_batch_matches_oracle():
     _check_against_oracle(recv, sigs, res, 40)
 
 
-def test_multicorrelator_101_taps_matches_oracle():
+@pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE)])
+def test_multicorrelator_101_taps_matches_oracle(tiles):
     recv = [synth.multicorrelator_receiver(i, n_blocks=3) for i in range(2)]
     buf, offs, sigs = _pack(recv, 3)
-    b = _batch(recv, 3)
+    b = _batch(recv, 3, tiles)
     try:
         rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 3)
         res = _read(b, recv, 3)
@@ -99,7 +100,9 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     dev = torch.from_numpy(buf).cuda()
     results = []
     for tiles in [None, (1, 128, 0), (3, 256, 2), (8, 512, 1), (1, 128, 0, rx.RX_SCHED_STATIC),
-                  (2, 256, 0, rx.RX_SCHED_STATIC), (5, 512, 0, rx.RX_SCHED_STATIC)]:
+                  (2, 256, 0, rx.RX_SCHED_STATIC), (5, 512, 0, rx.RX_SCHED_STATIC),
+                  (1, 128, 0, rx.RX_SCHED_PIPE), (2, 128, 0, rx.RX_SCHED_PIPE),
+                  (3, 256, 0, rx.RX_SCHED_PIPE), (5, 512, 0, rx.RX_SCHED_PIPE)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -121,7 +124,7 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     assert np.array_equal(d, results[0][4][0])
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE])
 def test_graph_replay_restart_continue_and_host_input(schedule):
     recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
     recv[1].integ_blocks = 5                     # an integration spans the two runs (8 + 8 blocks)
@@ -174,3 +177,30 @@ def test_batch_invalid_arguments():
         assert e.value.status == rx.RX_EINVAL
     finally:
         rx.rx_batch_destroy(b)
+
+
+def test_wait_limit_reports_timeout_and_the_handle_recovers():
+    """A wait that cannot finish (the test hook's barrier, which nothing completes)
+    ends the run with RX_ETIMEOUT after the limit; the next run is exact."""
+    recv = [synth.uniform_receiver(i, n_blocks=6, fs=4.092e6) for i in range(3)]
+    buf, offs, sigs = _pack(recv, 6)
+    dev = torch.from_numpy(buf).cuda()
+    b = _batch(recv, 6, (2, 128, 0, rx.RX_SCHED_PIPE))
+    try:
+        rx.rx_batch_set_wait_limit(b, 1_000_000, rx.RX_WAIT_TEST_STALL)
+        rx.rx_batch_run(b, dev, offs, 6, rx.RX_RUN_RESTART)
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_sync(b)
+        assert e.value.status == rx.RX_ETIMEOUT
+        rx.rx_batch_set_wait_limit(b, 2_000_000_000, 0)
+        rx.rx_batch_run(b, dev, offs, 6, rx.RX_RUN_RESTART)
+        res = _read(b, recv, 6)
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_wait_limit(b, 10, 0)
+        assert e.value.status == rx.RX_EINVAL
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_wait_limit(b, 2_000_000_000, 4)
+        assert e.value.status == rx.RX_EINVAL
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 6)
