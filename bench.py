@@ -57,9 +57,38 @@ def layout(receivers):
     return np.array(offs, np.uint64), pos
 
 
+def rank_receiver_ids(rank: int, n_rx: int = N_RX) -> list[int]:
+    """Receivers of one rank: rank k tracks receivers k*n_rx .. k*n_rx + n_rx - 1, so the
+    ranks' workloads are disjoint and of the same shape (weak scaling, no collective on
+    the data path)."""
+    return [rank * n_rx + i for i in range(n_rx)]
+
+
 def workload(rank: int, n_rx: int = N_RX, n_blocks: int = N_BLOCKS):
     from paper_1907_00463_gb300 import synth
-    return [synth.uniform_receiver(rank * N_RX + i, n_blocks=n_blocks) for i in range(n_rx)]
+    return [synth.uniform_receiver(i, n_blocks=n_blocks) for i in rank_receiver_ids(rank, n_rx)]
+
+
+def job_time(local: float, world: int, device) -> float:
+    """Whole-job time: the slowest rank's (MAX all-reduce)."""
+    if world == 1:
+        return local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_units(local: int, world: int, device) -> int:
+    """Units processed by all ranks together (SUM all-reduce)."""
+    if world == 1:
+        return local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
 
 
 def sample_channels(receivers, n_blocks=None) -> int:
@@ -357,15 +386,12 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     launches = args.steps * rx.rx_batch_last_launches(b)
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = job_time(t_start.elapsed_time(t_end), world, dev)
     per_launch = [e0.elapsed_time(e1) for e0, e1 in ev]
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms = total_ms / args.steps
     sc = sample_channels(receivers)
-    value = world * sc / (ms / 1000) / 1e6
+    sc_job = job_units(sc, world, dev)
+    value = sc_job / (ms / 1000) / 1e6
 
     # roofline of the persistent kernel (all of a step's device time)
     props = torch.cuda.get_device_properties(dev)
@@ -399,12 +425,8 @@ def run_ours(args):
             rx.rx_batch_run(b, hbuf, offs, n_blocks, rx.RX_RUN_RESTART)
             for i, r in enumerate(receivers):
                 dumps[i] = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, n_blocks)
-        dt = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * sc / dt / 1e6, "unit": "Msample*channel/s",
+        dt = job_time((time.perf_counter() - t0) / n_e2e, world, dev)
+        e2e = {"value": sc_job / dt / 1e6, "unit": "Msample*channel/s",
                "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": dt * 1000}
         del hbuf

@@ -254,13 +254,13 @@ __device__ __forceinline__ void seg_prefix(const uint32_t (&x)[SPT], uint32_t th
         }
         const uint32_t e0 = tab[th >> 26];
         th += w;
-        sI += __dp2a_lo((int)x[i], (int)e0, 0);
-        sQ += __dp2a_hi((int)x[i], (int)e0, 0);
+        sI = __dp2a_lo((int)x[i], (int)e0, sI);
+        sQ = __dp2a_hi((int)x[i], (int)e0, sQ);
         const int32_t aI = sI, aQ = sQ;
         const uint32_t e1 = tab[th >> 26];
         th += w;
-        sI += __dp2a_lo((int)x[i + 1], (int)e1, 0);
-        sQ += __dp2a_hi((int)x[i + 1], (int)e1, 0);
+        sI = __dp2a_lo((int)x[i + 1], (int)e1, sI);
+        sQ = __dp2a_hi((int)x[i + 1], (int)e1, sQ);
         slice[i >> 1] = make_int4(aI, aQ, sI, sQ);
     }
 }

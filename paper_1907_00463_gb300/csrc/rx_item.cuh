@@ -43,7 +43,7 @@ struct Tables {
 // at most mt taps.
 struct ItemSmem {
     int64_t *taps;     // [cpg * mt]
-    uint32_t *tab;     // [64]
+    uint32_t *tab;     // [64], static shared memory
     uint32_t *code;    // [cpg][EXT_WORDS]
     int32_t *acc;      // [cpg * mt * 2]
     uint32_t *theta, *w, *ab, *r;  // [cpg]
@@ -52,10 +52,14 @@ struct ItemSmem {
     uint16_t *pair;    // [cpg][PAIR_LEN]
 };
 
+// The carrier table lives in static shared memory, so that its address is a
+// constant and a lookup is one shift and one load.
+static __shared__ uint32_t g_item_tab[64];
+
 __host__ __device__ inline size_t item_smem_align(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline size_t item_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt) {
-    size_t s = (size_t)cpg * mt * 8 + 64 * 4 + (size_t)cpg * EXT_WORDS * 4 + (size_t)cpg * mt * 8;
+    size_t s = (size_t)cpg * mt * 8 + (size_t)cpg * EXT_WORDS * 4 + (size_t)cpg * mt * 8;
     s = item_smem_align(s + (size_t)cpg * 16) + (size_t)cpg * 8;
     s = item_smem_align(s) + (size_t)nt * SLICE_INT4 * 16 + (size_t)cpg * PAIR_LEN * 2;
     return item_smem_align(s);
@@ -66,8 +70,7 @@ __device__ inline ItemSmem carve_item_smem(unsigned char *base, uint32_t cpg, ui
     size_t o = 0;
     m.taps = reinterpret_cast<int64_t *>(base + o);
     o += (size_t)cpg * mt * 8;
-    m.tab = reinterpret_cast<uint32_t *>(base + o);
-    o += 64 * 4;
+    m.tab = g_item_tab;
     m.code = reinterpret_cast<uint32_t *>(base + o);
     o += (size_t)cpg * EXT_WORDS * 4;
     m.acc = reinterpret_cast<int32_t *>(base + o);
