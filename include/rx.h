@@ -250,8 +250,9 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
 
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
  * correlated together by one CTA (0 = choose); threads: correlating threads
- * of a CTA (128, 256 or 512; 0 = choose; RX_SCHED_PIPE adds one filter warp,
- * two from 4 channels per item); ctas_per_sm: resident CTAs per SM for the
+ * of a CTA (128, 256 or 512, and 224 with RX_SCHED_PIPE and at most 3
+ * channels per item; 0 = choose; RX_SCHED_PIPE adds one filter warp, two
+ * from 4 channels per item); ctas_per_sm: resident CTAs per SM for the
  * dynamic schedule (0 = as many as fit); schedule: RX_SCHED_DYNAMIC,
  * RX_SCHED_STATIC or RX_SCHED_PIPE.  All schedules give identical results.
  * Takes effect at the next run (the graph is re-recorded).  A wait inside a

@@ -662,8 +662,10 @@ extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threa
     if (!b) return RX_EINVAL;
     if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC && schedule != RX_SCHED_PIPE)
         return berr(b, RX_EINVAL, "unknown schedule");
-    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
-        return berr(b, RX_EINVAL, "threads must be 128, 256 or 512");
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512 &&
+        !(threads == 224 && schedule == RX_SCHED_PIPE))
+        return berr(b, RX_EINVAL, "threads must be 128, 256 or 512 (or 224 with RX_SCHED_PIPE)");
+    if (threads == 224 && cpg > 3) return berr(b, RX_EINVAL, "224 threads take at most 3 channels per item");
     if (cpg > 64) return berr(b, RX_EINVAL, "channels_per_item must be <= 64");
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
@@ -897,8 +899,9 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
         for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u, 8u, 12u, 16u}) {
             if (cpg > max_ch) continue;
             if (sched == RX_SCHED_PIPE && cpg == 1 && max_ch > 1) continue;  // nothing to overlap
-            for (uint32_t nt : {128u, 256u, 512u}) {
+            for (uint32_t nt : {128u, 224u, 256u, 512u}) {
                 if (sched == RX_SCHED_DYNAMIC && nt == 512) continue;
+                if (nt == 224 && (sched != RX_SCHED_PIPE || cpg > 3)) continue;
                 cands.push_back({cpg, nt, 0u, sched});
             }
         }

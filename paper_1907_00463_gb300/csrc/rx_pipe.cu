@@ -154,8 +154,15 @@ __device__ __forceinline__ void stage_block(const int8_t *src, uint32_t bytes, u
     if (n) bulk_g2s(buf, reinterpret_cast<const void *>(a0), n, bar);
 }
 
+// Launch bounds: NT correlation threads plus up to two filter warps (one for NT = 224,
+// which is sized for three CTAs of eight warps per SM at 80 registers).
+template <int NT>
+constexpr int pipe_max_threads() { return NT == 224 ? NT + 32 : NT + 64; }
+template <int NT>
+constexpr int pipe_min_blocks() { return NT == 128 ? 4 : NT == 224 ? 3 : NT == 256 ? 2 : 1; }
+
 template <int NT, bool SH>
-__global__ void __launch_bounds__(NT + 64, (NT == 128 ? 4 : NT == 256 ? 2 : 1)) k_batch_pipe(PipeArgs a) {
+__global__ void __launch_bounds__(pipe_max_threads<NT>(), pipe_min_blocks<NT>()) k_batch_pipe(PipeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t cpg = a.cpg, mt = a.max_taps;
     unsigned char *stage = smem;                               // [2][stage_bytes] when SH
@@ -208,6 +215,8 @@ __global__ void __launch_bounds__(NT + 64, (NT == 128 ? 4 : NT == 256 ? 2 : 1)) 
 
     const int8_t *base = a.iq + a.src_off[gd.src];
     const uint32_t blk_bytes = 2 * N;
+    const uint32_t rem = ((N + SPT - 1) / SPT) % NT;         // chunks of the ragged last pass
+    uint32_t rot = 0;
     if (tid < NT) {
         // correlation warps
         bool ok = true;
@@ -249,8 +258,9 @@ __global__ void __launch_bounds__(NT + 64, (NT == 128 ? 4 : NT == 256 ? 2 : 1)) 
                     ok = false;
                     break;
                 }
-                correlate_channel<NT, SH>(j, nt, N, blk, a16, a4, sm, sm.acc + (size_t)j * per_ch);
+                correlate_channel<NT, SH>(j, nt, N, blk, a16, a4, sm, sm.acc + (size_t)j * per_ch, rot);
                 mbar_arrive(full + j);
+                rot = (rot + rem) % NT;
             }
         }
         if (SH && tid == 0) {
@@ -366,6 +376,7 @@ size_t pipe_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t stage_by
 
 int pipe_occupancy(uint32_t nt, uint32_t fw, bool staged, size_t smem) {
     if (fw < 1 || fw > 2) return 0;
+    if (nt == 224) return fw == 1 ? (staged ? occupancy_nt<224, true>(fw, smem) : occupancy_nt<224, false>(fw, smem)) : 0;
     if (nt == 128) return staged ? occupancy_nt<128, true>(fw, smem) : occupancy_nt<128, false>(fw, smem);
     if (nt == 256) return staged ? occupancy_nt<256, true>(fw, smem) : occupancy_nt<256, false>(fw, smem);
     if (nt == 512) return staged ? occupancy_nt<512, true>(fw, smem) : occupancy_nt<512, false>(fw, smem);
@@ -376,6 +387,10 @@ cudaError_t pipe_launch(uint32_t nt, uint32_t fw, uint32_t grid, size_t smem, cu
                         const PipeArgs &a) {
     if (fw < 1 || fw > 2) return cudaErrorInvalidValue;
     const bool st = a.stage_bytes != 0;
+    if (nt == 224) {
+        if (fw != 1) return cudaErrorInvalidValue;
+        return st ? launch_nt<224, true>(fw, grid, smem, stream, a) : launch_nt<224, false>(fw, grid, smem, stream, a);
+    }
     if (nt == 128) return st ? launch_nt<128, true>(fw, grid, smem, stream, a) : launch_nt<128, false>(fw, grid, smem, stream, a);
     if (nt == 256) return st ? launch_nt<256, true>(fw, grid, smem, stream, a) : launch_nt<256, false>(fw, grid, smem, stream, a);
     if (nt == 512) return st ? launch_nt<512, true>(fw, grid, smem, stream, a) : launch_nt<512, false>(fw, grid, smem, stream, a);

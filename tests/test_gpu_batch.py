@@ -102,7 +102,8 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     for tiles in [None, (1, 128, 0), (3, 256, 2), (8, 512, 1), (1, 128, 0, rx.RX_SCHED_STATIC),
                   (2, 256, 0, rx.RX_SCHED_STATIC), (5, 512, 0, rx.RX_SCHED_STATIC),
                   (1, 128, 0, rx.RX_SCHED_PIPE), (2, 128, 0, rx.RX_SCHED_PIPE),
-                  (3, 256, 0, rx.RX_SCHED_PIPE), (5, 512, 0, rx.RX_SCHED_PIPE)]:
+                  (3, 256, 0, rx.RX_SCHED_PIPE), (5, 512, 0, rx.RX_SCHED_PIPE),
+                  (2, 224, 0, rx.RX_SCHED_PIPE), (3, 224, 0, rx.RX_SCHED_PIPE)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -174,6 +175,9 @@ def test_batch_invalid_arguments():
         assert e.value.status == rx.RX_EINVAL              # beyond max_blocks
         with pytest.raises(rx.RxError) as e:
             rx.rx_batch_set_tiles(b, 0, 200, 0)
+        assert e.value.status == rx.RX_EINVAL
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 2, 224, 0, rx.RX_SCHED_STATIC)   # 224 is for the pipeline only
         assert e.value.status == rx.RX_EINVAL
     finally:
         rx.rx_batch_destroy(b)
