@@ -104,6 +104,21 @@ __device__ __forceinline__ bool corr_barrier_and(bool ok) {
     return r != 0;
 }
 
+// As mbar_try_wait, but the thread may stay suspended in the instruction for up to
+// hint_ns (it resumes as soon as the phase completes), so that a waiting warp polls
+// rarely and leaves the issue slots to the warps that work.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity.  Warp-uniform result: false when
 // this or any other thread of the CTA gave up.
 __device__ __forceinline__ bool pipe_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
@@ -112,7 +127,7 @@ __device__ __forceinline__ bool pipe_wait(uint64_t *bar, uint32_t parity, volati
     if (!ok) {
         const uint64_t t0 = globaltimer_ns();
         for (uint32_t it = 0;; ++it) {
-            if (mbar_try_wait(bar, parity)) {
+            if (mbar_try_wait_hint(bar, parity, 100000u)) {
                 ok = true;
                 break;
             }
