@@ -38,6 +38,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
+
+# DRAM bytes (read + write) per receiver-block of the timed kernel and its executed
+# thread instructions per sample*channel, from the ncu captures summarised under
+# profiles/ (64 receivers x 100 blocks, larger than L2; a launch of B blocks is B/100
+# times that case).  Keyed by (schedule, correlating threads, channels per item).  An
+# entry is removed whenever its kernel changes and restored from a new capture.
+PROFILED = {
+    ("static", 128, 1): {"bytes_per_rx_block": 33983, "thread_inst_per_sample_channel": 19.7,
+                         "capture": "profiles/k_batch_static128_uniform_64rx_100blk.md"},
+}
 METRIC = "Msample*channel/s correlated"
 INT32_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x one 32-lane warp instruction per clock
 
@@ -452,6 +462,14 @@ def run_ours(args):
     rx.rx_batch_destroy(b)
 
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
+    sched_name = ["dynamic", "static", "pipelined"][tiles[3]]
+    prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
+    traffic = prof["bytes_per_rx_block"] * len(receivers) * n_blocks if prof else None
+    executed = None
+    if prof:
+        ex_rate = sc * prof["thread_inst_per_sample_channel"] / (launch_ms / 1000) / 1e12
+        executed = {"thread_inst_per_sample_channel": prof["thread_inst_per_sample_channel"],
+                    "achieved": ex_rate, "frac": ex_rate / peak_tops, "capture": prof["capture"]}
     line = {
         "metric": METRIC, "value": value, "unit": "Msample*channel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -463,15 +481,17 @@ def run_ours(args):
                    "receivers_per_gpu": len(receivers), "blocks": n_blocks, "channels": 12, "taps": 5,
                    "fs_hz": FS, "tiles": {"channels_per_item": tiles[0], "threads": tiles[1],
                                           "ctas_per_sm": tiles[2],
-                                          "schedule": ["dynamic", "static", "pipelined"][tiles[3]]},
+                                          "schedule": sched_name},
                    "autotune": tune,
                    "l2": ("inputs larger than L2; no flush" if in_bytes > 129e6 else
                           "inputs fit in L2 (profiling case only)"),
                    "parallelism": f"receivers sharded over {world} GPU(s), no collective"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved / peak_tops, "traffic": None,
+                     "frac": achieved / peak_tops, "traffic": traffic,
                      "model": "INT32 ops = sample*channel x (8 + 3T), T = 5; peak = SMs x 128 "
                               "lanes x max SM clock (derived, not measured)",
+                     "executed": executed,
+                     "smem_lookup_bound_Msample_channel_s": peak_tops * 1e6 / 4,
                      "launch_ms": launch_ms,
                      "hbm_gbs": in_bytes / (launch_ms / 1000) / 1e9,
                      "hbm_frac_of_measured": in_bytes / (launch_ms / 1000) / 1e9 / hbm_peak},
