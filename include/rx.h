@@ -247,14 +247,22 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
 #define RX_SCHED_STATIC 1u   /* one CTA per channel group for the whole run */
 #define RX_SCHED_PIPE 2u     /* as STATIC, with correlation and loop-filter warps
                                 overlapped across the group's channels */
+#define RX_SCHED_BALANCED 3u /* one cooperative launch of ctas_per_sm CTAs per SM,
+                                each with an equal share of the whole job: channels
+                                cut between CTAs exchange partial sums each block;
+                                enqueued directly, not through a graph */
 
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
- * correlated together by one CTA (0 = choose); threads: correlating threads
- * of a CTA (128, 256 or 512, and 224 with RX_SCHED_PIPE and at most 3
- * channels per item; 0 = choose; RX_SCHED_PIPE adds one filter warp, two
- * from 4 channels per item); ctas_per_sm: resident CTAs per SM for the
- * dynamic schedule (0 = as many as fit); schedule: RX_SCHED_DYNAMIC,
- * RX_SCHED_STATIC or RX_SCHED_PIPE.  All schedules give identical results.
+ * correlated together by one CTA (0 = choose; for RX_SCHED_BALANCED the
+ * segments a CTA may hold, 0 = as the partition needs); threads: correlating
+ * threads of a CTA (128, 256 or 512, and 224 with RX_SCHED_PIPE and at most
+ * 3 channels per item or with RX_SCHED_BALANCED, 192 with RX_SCHED_BALANCED;
+ * 0 = choose; RX_SCHED_PIPE adds one filter warp, two from 4 channels per
+ * item, RX_SCHED_BALANCED two, three with 512, one with 224);
+ * ctas_per_sm: resident CTAs per SM for the dynamic and balanced schedules
+ * (0 = as many as fit; at most 8 for RX_SCHED_BALANCED); schedule:
+ * RX_SCHED_DYNAMIC, RX_SCHED_STATIC, RX_SCHED_PIPE or RX_SCHED_BALANCED.
+ * All schedules give identical results.
  * Takes effect at the next run (the graph is re-recorded).  A wait inside a
  * CTA of RX_SCHED_PIPE that exceeds the handle's time limit ends the run with
  * RX_ETIMEOUT at the next synchronising call. */

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstring>
 #include <map>
@@ -245,6 +246,12 @@ struct rx_batch_s {
     uint64_t timeout_ns = 2000000000ull;
     uint32_t stall = 0;
     uint32_t pipe_stage = 0;        // staging buffer bytes of the pipelined schedule (0: none)
+    // balanced schedule: per-CTA segments and the exchange of cut channels
+    SegDesc *d_segs = nullptr;
+    uint32_t *d_nseg = nullptr;
+    int32_t *d_xpart = nullptr;
+    uint32_t *d_xflag = nullptr;    // [slots]
+    uint32_t n_slots = 0, bal_maxseg = 0;
     std::string err;
 };
 
@@ -333,43 +340,187 @@ int occupancy(size_t smem) {
     return n;
 }
 
+// Descriptor of channels c0 .. c0 + nch - 1 of receiver r.
+GroupDesc make_group(rx_batch b, uint32_t r, uint32_t c0, uint32_t nch) {
+    const rx_receiver_desc &d = b->rx[r];
+    const uint32_t ch = b->rx_ch0[r] + c0;
+    const uint64_t tap0 = b->rx_tap0[r] + (uint64_t)c0 * d.n_taps;
+    GroupDesc g{};
+    g.theta = b->st.theta + ch;
+    g.w = b->st.w + ch;
+    g.phi = b->st.phi + ch;
+    g.r = b->st.r + ch;
+    g.v = b->st.v + ch;
+    g.fcarr = b->st.fcarr + ch;
+    g.fcode = b->st.fcode + ch;
+    g.epochs = b->st.epochs + ch;
+    g.acc_blocks = b->st.acc_blocks + ch;
+    g.acc = b->st.acc + tap0 * 2;
+    g.prn = b->d_prn + ch;
+    g.taps = b->d_taps + tap0;
+    g.dumps = b->d_dumps + b->rx_dump0[r] + (uint64_t)c0 * d.n_taps * 2;
+    g.nch = nch;
+    g.ntaps = d.n_taps;
+    g.N = d.block_samples;
+    g.L = d.integ_blocks;
+    g.tap_e = d.tap_early;
+    g.tap_p = d.tap_prompt;
+    g.tap_l = d.tap_late;
+    g.dump_stride = d.n_channels * d.n_taps * 2;
+    g.dump_slots = b->max_blocks / d.integ_blocks;
+    g.dump_wrap = 0;
+    g.src = r;
+    g.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz, d.dll_bn_hz);
+    return g;
+}
+
+uint32_t bal_default_per_sm(uint32_t nt) { return nt == 128 ? 4 : (nt == 192 || nt == 224) ? 3 : nt == 256 ? 2 : 1; }
+
+// Balanced schedule: cut the (channel, chunk) sequence, receiver by receiver, into
+// equal-cost slices, one per CTA, and build each CTA's segment list.
+rx_status build_balanced(rx_batch b) {
+    std::string &E = b->err;
+    const uint32_t sms = (uint32_t)b->tables->sm_count;
+    struct Chan {
+        uint32_t r, c, nchunks;
+        uint64_t cost;  // per chunk: the direct-form op model 8 + 3T
+    };
+    std::vector<Chan> ch;
+    uint64_t total = 0, chunks = 0;
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        const rx_receiver_desc &d = b->rx[r];
+        for (uint32_t c = 0; c < d.n_channels; ++c) {
+            Chan x{r, c, (d.block_samples + SPT - 1) / SPT, 8u + 3u * d.n_taps};
+            total += x.cost * x.nchunks;
+            chunks += x.nchunks;
+            ch.push_back(x);
+        }
+    }
+    uint32_t per_sm = b->ctas_per_sm ? b->ctas_per_sm : bal_default_per_sm(b->threads);
+    for (;; --per_sm) {
+        if (per_sm == 0) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
+        const uint32_t P = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * sms, chunks);
+        // 1) every CTA takes whole channels, in order, while they fit its share;
+        // 2) the channels left over are cut into pieces that fill each CTA's remaining
+        //    share, in CTA order, so that cut channels are few and their pieces small.
+        struct Seg {
+            uint32_t k, jbeg, jend, cta;
+        };
+        std::vector<Seg> segs;
+        const double share = (double)total / P;
+        std::vector<double> load(P, 0.0);
+        size_t k = 0;
+        for (uint32_t p = 0; p < P && k < ch.size(); ++p) {
+            while (k < ch.size() && load[p] + (double)(ch[k].cost * ch[k].nchunks) <= share) {
+                segs.push_back({(uint32_t)k, 0u, ch[k].nchunks, p});
+                load[p] += (double)(ch[k].cost * ch[k].nchunks);
+                ++k;
+            }
+        }
+        uint32_t j = 0;
+        for (uint32_t p = 0; p < P && k < ch.size(); ++p) {
+            const bool last = p + 1 == P;
+            while (k < ch.size() && (last || load[p] < share)) {
+                const Chan &x = ch[k];
+                uint64_t take = last ? (uint64_t)(x.nchunks - j)
+                                     : (uint64_t)std::ceil((share - load[p]) / (double)x.cost);
+                take = std::max<uint64_t>(1, std::min<uint64_t>(take, x.nchunks - j));
+                segs.push_back({(uint32_t)k, j, (uint32_t)(j + take), p});
+                j += (uint32_t)take;
+                load[p] += (double)(take * x.cost);
+                if (j == x.nchunks) {
+                    ++k;
+                    j = 0;
+                }
+            }
+        }
+        // parts per channel, in CTA order; one exchange slot per part of a cut channel
+        std::vector<uint32_t> nparts(ch.size(), 0), slot0(ch.size(), 0);
+        for (const Seg &g : segs) ++nparts[g.k];
+        uint32_t slots = 0;
+        for (size_t c = 0; c < ch.size(); ++c) {
+            slot0[c] = slots;
+            if (nparts[c] > 1) slots += nparts[c];
+        }
+        std::vector<std::vector<SegDesc>> per_cta(P);
+        std::vector<uint32_t> seen(ch.size(), 0);
+        for (const Seg &g : segs) {
+            SegDesc d{};
+            const Chan &x = ch[g.k];
+            d.g = make_group(b, x.r, x.c, 1);
+            d.jbeg = g.jbeg;
+            d.jend = g.jend;
+            d.part = seen[g.k]++;
+            d.nparts = nparts[g.k];
+            d.chan = b->rx_ch0[x.r] + x.c;
+            d.slot0 = slot0[g.k];
+            per_cta[g.cta].push_back(d);
+        }
+        uint32_t maxseg = 1;
+        for (auto &v : per_cta) {
+            // cut channels first, whole channels after
+            std::stable_sort(v.begin(), v.end(),
+                             [](const SegDesc &x, const SegDesc &y) { return (x.nparts > 1) > (y.nparts > 1); });
+            maxseg = std::max<uint32_t>(maxseg, (uint32_t)v.size());
+        }
+        if (b->cpg && b->cpg < maxseg)
+            return berr(b, RX_EINVAL,
+                        rxh::fmt("balanced schedule needs %u segments per CTA (channels_per_item %u)", maxseg,
+                                 b->cpg));
+        if (b->cpg) maxseg = b->cpg;
+        const size_t smem = bal_smem_bytes(maxseg, b->max_taps, b->threads);
+        const int occ = bal_occupancy(b->threads, smem);
+        if (occ < (int)per_sm) {
+            if (b->ctas_per_sm) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
+            continue;
+        }
+        std::vector<SegDesc> flat((size_t)P * maxseg);
+        std::vector<uint32_t> nseg(P);
+        for (uint32_t p = 0; p < P; ++p) {
+            nseg[p] = (uint32_t)per_cta[p].size();
+            std::copy(per_cta[p].begin(), per_cta[p].end(), flat.begin() + (size_t)p * maxseg);
+        }
+        void *old[] = {b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag};
+        for (void *q : old)
+            if (q) cudaFree(q);
+        b->d_segs = nullptr;
+        b->d_nseg = nullptr;
+        b->d_xpart = nullptr;
+        b->d_xflag = nullptr;
+        RX_CUDA_TRY(cudaMalloc(&b->d_segs, flat.size() * sizeof(SegDesc)), E);
+        RX_CUDA_TRY(cudaMemcpy(b->d_segs, flat.data(), flat.size() * sizeof(SegDesc), cudaMemcpyHostToDevice), E);
+        RX_CUDA_TRY(cudaMalloc(&b->d_nseg, (size_t)P * 4), E);
+        RX_CUDA_TRY(cudaMemcpy(b->d_nseg, nseg.data(), (size_t)P * 4, cudaMemcpyHostToDevice), E);
+        RX_CUDA_TRY(cudaMalloc(&b->d_xpart, std::max<size_t>(1, (size_t)slots * 2 * b->max_taps * 2) * 4), E);
+        RX_CUDA_TRY(cudaMalloc(&b->d_xflag, std::max<size_t>(1, slots) * 4), E);
+        b->n_slots = slots;
+        b->bal_maxseg = maxseg;
+        b->ctas_per_sm = per_sm;
+        b->G = P;
+        b->grid = P;
+        return RX_OK;
+    }
+}
+
 rx_status build_groups(rx_batch b) {
-    if (b->cpg == 0) b->cpg = default_cpg(b);
-    if (b->threads == 0) b->threads = 256;
+    if (b->cpg == 0 && b->schedule != RX_SCHED_BALANCED) b->cpg = default_cpg(b);
+    if (b->threads == 0) b->threads = b->schedule == RX_SCHED_BALANCED ? 224 : 256;
+    if (b->schedule == RX_SCHED_BALANCED) {
+        rx_status s = build_balanced(b);
+        if (s == RX_OK) {
+            if (b->d_scratch) cudaFree(b->d_scratch);
+            b->d_scratch = nullptr;
+            RX_CUDA_TRY(cudaMalloc(&b->d_scratch, (5 + (size_t)b->G) * 4), b->err);
+            RX_CUDA_TRY(cudaMemset(b->d_scratch, 0, (5 + (size_t)b->G) * 4), b->err);
+            b->groups_dirty = false;
+        }
+        return s;
+    }
     std::vector<GroupDesc> gs;
     for (uint32_t r = 0; r < b->n_rx; ++r) {
         const rx_receiver_desc &d = b->rx[r];
         for (uint32_t c0 = 0; c0 < d.n_channels; c0 += b->cpg) {
-            const uint32_t ch = b->rx_ch0[r] + c0;
-            const uint64_t tap0 = b->rx_tap0[r] + (uint64_t)c0 * d.n_taps;
-            GroupDesc g{};
-            g.theta = b->st.theta + ch;
-            g.w = b->st.w + ch;
-            g.phi = b->st.phi + ch;
-            g.r = b->st.r + ch;
-            g.v = b->st.v + ch;
-            g.fcarr = b->st.fcarr + ch;
-            g.fcode = b->st.fcode + ch;
-            g.epochs = b->st.epochs + ch;
-            g.acc_blocks = b->st.acc_blocks + ch;
-            g.acc = b->st.acc + tap0 * 2;
-            g.prn = b->d_prn + ch;
-            g.taps = b->d_taps + tap0;
-            g.dumps = b->d_dumps + b->rx_dump0[r] + (uint64_t)c0 * d.n_taps * 2;
-            g.nch = std::min(b->cpg, d.n_channels - c0);
-            g.ntaps = d.n_taps;
-            g.N = d.block_samples;
-            g.L = d.integ_blocks;
-            g.tap_e = d.tap_early;
-            g.tap_p = d.tap_prompt;
-            g.tap_l = d.tap_late;
-            g.dump_stride = d.n_channels * d.n_taps * 2;
-            g.dump_slots = b->max_blocks / d.integ_blocks;
-            g.dump_wrap = 0;
-            g.src = r;
-            g.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
-                                    d.dll_bn_hz);
-            gs.push_back(g);
+            gs.push_back(make_group(b, r, c0, std::min(b->cpg, d.n_channels - c0)));
         }
     }
     // Longest items first inside each block: the tail of every block is short.
@@ -438,6 +589,16 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     ba.max_taps = b->max_taps;
     ba.timeout_ns = b->timeout_ns;
     rx_status s;
+    if (b->schedule == RX_SCHED_BALANCED) {
+        RX_CUDA_TRY(cudaMemsetAsync(b->d_xflag, 0, std::max<size_t>(1, b->n_slots) * 4, b->stream), E);
+        BalArgs la{b->d_segs,   b->d_nseg,     b->d_rxoff,    iq,         ba.tb,   b->d_xpart,
+                   b->d_xflag,  ba.err,        b->timeout_ns, n_blocks,   b->bal_maxseg, b->max_taps};
+        cudaError_t ce = bal_launch(b->threads, b->grid, bal_smem_bytes(b->bal_maxseg, b->max_taps, b->threads),
+                                    b->stream, la);
+        if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(ce)));
+        RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
+        return RX_OK;
+    }
     if (b->schedule == RX_SCHED_PIPE) {
         PipeArgs pa{b->d_groups, b->d_rxoff, iq,       ba.tb,      ba.err,        b->timeout_ns,
                     n_blocks,    b->cpg,     b->max_taps, b->stall, b->pipe_stage};
@@ -586,8 +747,8 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
-    void *ptrs[] = {b->d_state, b->d_snap, b->d_prn, b->d_taps, b->d_dumps, b->d_groups, b->d_rxoff,
-                    b->d_scratch, b->d_stage};
+    void *ptrs[] = {b->d_state, b->d_snap, b->d_prn,   b->d_taps, b->d_dumps, b->d_groups, b->d_rxoff,
+                    b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_err) cudaFreeHost(b->h_err);
@@ -660,12 +821,18 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
 extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threads, uint32_t ctas_per_sm,
                                         uint32_t schedule) {
     if (!b) return RX_EINVAL;
-    if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC && schedule != RX_SCHED_PIPE)
+    if (schedule != RX_SCHED_DYNAMIC && schedule != RX_SCHED_STATIC && schedule != RX_SCHED_PIPE &&
+        schedule != RX_SCHED_BALANCED)
         return berr(b, RX_EINVAL, "unknown schedule");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512 &&
-        !(threads == 224 && schedule == RX_SCHED_PIPE))
-        return berr(b, RX_EINVAL, "threads must be 128, 256 or 512 (or 224 with RX_SCHED_PIPE)");
-    if (threads == 224 && cpg > 3) return berr(b, RX_EINVAL, "224 threads take at most 3 channels per item");
+        !(threads == 224 && (schedule == RX_SCHED_PIPE || schedule == RX_SCHED_BALANCED)) &&
+        !(threads == 192 && schedule == RX_SCHED_BALANCED))
+        return berr(b, RX_EINVAL,
+                    "threads must be 128, 256 or 512 (or 224 with the pipelined or balanced schedule, "
+                    "192 with the balanced one)");
+    if (threads == 224 && schedule == RX_SCHED_PIPE && cpg > 3)
+        return berr(b, RX_EINVAL, "224 threads take at most 3 channels per item");
+    if (schedule == RX_SCHED_BALANCED && ctas_per_sm > 8) return berr(b, RX_EINVAL, "ctas_per_sm must be <= 8");
     if (cpg > 64) return berr(b, RX_EINVAL, "channels_per_item must be <= 64");
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
@@ -699,7 +866,7 @@ extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *thr
         rx_status s = build_groups(b);
         if (s != RX_OK) return s;
     }
-    *cpg = b->cpg;
+    *cpg = (b->schedule == RX_SCHED_BALANCED && b->cpg == 0) ? b->bal_maxseg : b->cpg;
     *threads = b->threads;
     *ctas = b->ctas_per_sm;
     *schedule = b->schedule;
@@ -753,7 +920,9 @@ extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *
         drop_graph(b);
         b->g_off = off;
     }
-    if (flags & RX_RUN_NO_GRAPH) {
+    // The balanced schedule's launch is cooperative (its CTAs wait on one another), which
+    // a graph cannot hold: it is enqueued directly, still one launch per run.
+    if ((flags & RX_RUN_NO_GRAPH) || b->schedule == RX_SCHED_BALANCED) {
         s = enqueue_run(b, src, n_blocks, flags);
         b->last_launches = 1;
         return s;
@@ -895,6 +1064,11 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
     uint32_t max_ch = 1;
     for (const rx_receiver_desc &d : b->rx) max_ch = std::max(max_ch, d.n_channels);
     std::vector<std::array<uint32_t, 4>> cands;
+    for (uint32_t nt : {192u, 224u, 128u, 256u, 512u})
+        for (uint32_t per_sm : {1u, 2u, 3u, 4u, 6u}) {
+            if (per_sm > bal_default_per_sm(nt) + 2) continue;
+            cands.push_back({0u, nt, per_sm, RX_SCHED_BALANCED});
+        }
     for (uint32_t sched : {RX_SCHED_PIPE, RX_SCHED_STATIC, RX_SCHED_DYNAMIC})
         for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u, 8u, 12u, 16u}) {
             if (cpg > max_ch) continue;

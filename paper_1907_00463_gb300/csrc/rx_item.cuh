@@ -92,12 +92,13 @@ template <int TT, int NT, bool SH = false>
 __device__ __forceinline__ void item_direct(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                             uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                             const int64_t *s_taps, const uint32_t *s_code,
-                                            const uint32_t *s_tab, int32_t *s_red, uint32_t rot = 0) {
+                                            const uint32_t *s_tab, int32_t *s_red, uint32_t rot = 0,
+                                            uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     int32_t sI = 0, sQ = 0, mI[TT], mQ[TT];
 #pragma unroll
     for (int k = 0; k < TT; ++k) mI[k] = mQ[k] = 0;
-    const uint32_t nchunks = (N + SPT - 1) / SPT;
-    for (uint32_t j = (threadIdx.x + rot) % NT; j < nchunks; j += NT) {
+    const uint32_t jlim = min(jend, (N + SPT - 1) / SPT);
+    for (uint32_t j = jbeg + (threadIdx.x + rot) % NT; j < jlim; j += NT) {
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
         load_chunk_from<SH>(blk, s0, N, a16, a4, x);
@@ -122,12 +123,13 @@ __device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16
                                          uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                          uint32_t magic, const int64_t *s_taps,
                                          const uint16_t *s_pair, const uint32_t *s_tab,
-                                         int4 *slice, int32_t *s_red, uint32_t rot = 0) {
+                                         int4 *slice, int32_t *s_red, uint32_t rot = 0,
+                                         uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     int32_t aI[TT], aQ[TT];
 #pragma unroll
     for (int k = 0; k < TT; ++k) aI[k] = aQ[k] = 0;
-    const uint32_t nchunks = (N + SPT - 1) / SPT;
-    for (uint32_t j = (threadIdx.x + rot) % NT; j < nchunks; j += NT) {
+    const uint32_t jlim = min(jend, (N + SPT - 1) / SPT);
+    for (uint32_t j = jbeg + (threadIdx.x + rot) % NT; j < jlim; j += NT) {
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
         load_chunk_from<SH>(blk, s0, N, a16, a4, x);
@@ -155,15 +157,16 @@ __device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, boo
                                               uint32_t r, uint32_t magic, uint32_t nt,
                                               const int64_t *s_taps, const uint16_t *s_pair,
                                               const uint32_t *s_tab, int4 *slice,
-                                              int32_t *s_red, uint32_t rot = 0) {
-    const uint32_t nchunks = (N + SPT - 1) / SPT;
-    const uint32_t npass = (nchunks + NT - 1) / NT;
+                                              int32_t *s_red, uint32_t rot = 0, uint32_t jbeg = 0,
+                                              uint32_t jend = 0xffffffffu) {
+    const uint32_t jlim = min(jend, (N + SPT - 1) / SPT);
+    const uint32_t npass = jlim > jbeg ? (jlim - jbeg + NT - 1) / NT : 0u;
     const uint32_t t0 = (threadIdx.x + rot) % NT;
     for (uint32_t p = 0; p < npass; ++p) {
-        const uint32_t j = p * NT + t0;
+        const uint32_t j = jbeg + p * NT + t0;
         const uint32_t s0 = j * SPT;
         uint32_t x[SPT];
-        if (j < nchunks) {
+        if (j < jlim) {
             load_chunk_from<SH>(blk, s0, N, a16, a4, x);
         } else {
 #pragma unroll
@@ -193,18 +196,18 @@ __device__ __forceinline__ void channel_seg(const int8_t *blk, uint32_t N, bool 
                                             uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                             uint32_t nt, const int64_t *tp, const uint16_t *pr,
                                             const uint32_t *s_tab, int4 *slice, int32_t *red,
-                                            uint32_t rot = 0) {
+                                            uint32_t rot = 0, uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     const uint32_t mg = seg_magic(r);
     switch (nt) {
-        case 1: item_seg<S, 1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 2: item_seg<S, 2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 3: item_seg<S, 3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 4: item_seg<S, 4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 5: item_seg<S, 5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 6: item_seg<S, 6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 7: item_seg<S, 7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        case 8: item_seg<S, 8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot); break;
-        default: item_seg_many<S, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, nt, tp, pr, s_tab, slice, red, rot); break;
+        case 1: item_seg<S, 1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 2: item_seg<S, 2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 3: item_seg<S, 3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 4: item_seg<S, 4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 5: item_seg<S, 5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 6: item_seg<S, 6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 7: item_seg<S, 7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        case 8: item_seg<S, 8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
+        default: item_seg_many<S, NT, SH>(blk, N, a16, a4, theta, w, phi, r, mg, nt, tp, pr, s_tab, slice, red, rot, jbeg, jend); break;
     }
 }
 
@@ -249,40 +252,50 @@ __device__ __forceinline__ void stage_constants(const GroupDesc &gd, const Table
 
 // Correlate channel j of the group over one block into red[tap][2] (shared, zeroed
 // by the caller; every warp adds its partial sums with shared atomics).  Threads
-// 0..NT-1 take part; NCO state at the block start comes from sm.theta/w/phi/r.
-// Thread t takes the chunks c with c = t + rot (mod NT): rotating rot from call to
-// call spreads the ragged last pass over all threads when NT does not divide the
-// chunk count.
+// 0..NT-1 take part; the NCO state at the block start is (theta, w, phi, r) (from
+// sm.theta/w/phi/r[j] in correlate_channel).
+// Thread t takes the chunks c in [jbeg, jend) with c - jbeg = t + rot (mod NT):
+// rotating rot from call to call spreads the ragged last pass over all threads when
+// NT does not divide the chunk count.  [jbeg, jend) defaults to the whole block.
 template <int NT, bool SH = false>
-__device__ __forceinline__ void correlate_channel(uint32_t j, uint32_t nt, uint32_t N,
-                                                  const int8_t *blk, bool a16, bool a4,
-                                                  const ItemSmem &sm, int32_t *red, uint32_t rot = 0) {
+__device__ __forceinline__ void correlate_channel_at(uint32_t j, uint32_t nt, uint32_t N,
+                                                     const int8_t *blk, bool a16, bool a4,
+                                                     const ItemSmem &sm, int32_t *red, uint32_t theta,
+                                                     uint32_t w, uint64_t phi, uint32_t r, uint32_t rot = 0,
+                                                     uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     int4 *slice = sm.slices + threadIdx.x * SLICE_INT4;
-    const uint32_t theta = sm.theta[j], w = sm.w[j], r = sm.r[j];
-    const uint64_t phi = sm.phi[j];
     const int64_t *tp = sm.taps + (size_t)j * nt;
     const int mode = seg_mode(r);
     if (mode == 16) {
         channel_seg<16, NT, SH>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
-                            sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red, rot);
+                            sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red, rot, jbeg, jend);
     } else if (mode == 8) {
         channel_seg<8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, nt, tp,
-                           sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red, rot);
+                           sm.pair + (size_t)j * PAIR_LEN, sm.tab, slice, red, rot, jbeg, jend);
     } else {
         const uint32_t *cd = sm.code + (size_t)j * EXT_WORDS;
         for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
             switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-                case 1: item_direct<1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 2: item_direct<2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 3: item_direct<3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 4: item_direct<4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 5: item_direct<5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 6: item_direct<6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                case 7: item_direct<7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
-                default: item_direct<8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot); break;
+                case 1: item_direct<1, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 2: item_direct<2, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 3: item_direct<3, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 4: item_direct<4, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 5: item_direct<5, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 6: item_direct<6, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                case 7: item_direct<7, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
+                default: item_direct<8, NT, SH>(blk, N, a16, a4, theta, w, phi, r, tp + t0, cd, sm.tab, red + 2 * t0, rot, jbeg, jend); break;
             }
         }
     }
+}
+
+template <int NT, bool SH = false>
+__device__ __forceinline__ void correlate_channel(uint32_t j, uint32_t nt, uint32_t N,
+                                                  const int8_t *blk, bool a16, bool a4,
+                                                  const ItemSmem &sm, int32_t *red, uint32_t rot = 0,
+                                                  uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
+    correlate_channel_at<NT, SH>(j, nt, N, blk, a16, a4, sm, red, sm.theta[j], sm.w[j], sm.phi[j], sm.r[j], rot,
+                                 jbeg, jend);
 }
 
 // Correlate the group's channels over one block into red[channel][tap][2] (shared,
@@ -390,5 +403,40 @@ int pipe_occupancy(uint32_t nt, uint32_t filter_warps, bool staged, size_t smem)
 // One CTA per group (grid = number of groups).
 cudaError_t pipe_launch(uint32_t nt, uint32_t filter_warps, uint32_t grid, size_t smem,
                         cudaStream_t stream, const PipeArgs &a);
+
+// ----------------------------------------------------------------------------
+// Balanced schedule (rx_balance.cu)
+// ----------------------------------------------------------------------------
+
+// One segment of a CTA's work: chunks [jbeg, jend) of one channel's blocks.  A channel
+// cut between CTAs has parts 0..nparts-1, each publishing its partial sums through
+// exchange slot slot0 + part; part 0's CTA owns the channel (dumps, final state).
+struct SegDesc {
+    GroupDesc g;       // nch = 1: the channel's pointers and constants
+    uint32_t jbeg, jend;
+    uint32_t part, nparts;
+    uint32_t chan;     // channel index in the batch
+    uint32_t slot0;    // first exchange slot of the channel's parts (cut channels)
+};
+
+struct BalArgs {
+    const SegDesc *segs;       // [grid][maxseg]
+    const uint32_t *nseg;      // [grid]
+    const uint64_t *src_off;
+    const int8_t *iq;
+    Tables tb;
+    int32_t *xpart;            // [slots][2][max_taps][2] parts' sums, by block parity
+    uint32_t *xflag;           // [slots]: b + 1 once block b's sums are published
+    uint32_t *err;             // [4]
+    uint64_t timeout_ns;
+    uint32_t n_blocks;
+    uint32_t maxseg;
+    uint32_t max_taps;
+};
+
+size_t bal_smem_bytes(uint32_t maxseg, uint32_t mt, uint32_t nt);
+int bal_occupancy(uint32_t nt, size_t smem);
+// Cooperative launch (every CTA resident at once: CTAs wait on one another).
+cudaError_t bal_launch(uint32_t nt, uint32_t grid, size_t smem, cudaStream_t stream, const BalArgs &a);
 
 }  // namespace rxd

@@ -23,6 +23,7 @@ RX_RUN_NO_GRAPH = 2
 RX_SCHED_DYNAMIC = 0
 RX_SCHED_STATIC = 1
 RX_SCHED_PIPE = 2
+RX_SCHED_BALANCED = 3
 RX_WAIT_TEST_STALL = 1
 
 

@@ -56,10 +56,11 @@ def _check_against_oracle(receivers, sigs, results, n_blocks):
         assert_states_equal(s, os_)
 
 
-def test_uniform_batch_matches_oracle():
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED)])
+def test_uniform_batch_matches_oracle(tiles):
     recv = [synth.uniform_receiver(i, n_blocks=12) for i in range(4)]
     buf, offs, sigs = _pack(recv, 12)
-    b = _batch(recv, 12)
+    b = _batch(recv, 12, tiles)
     try:
         rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 12)
         res = _read(b, recv, 12)
@@ -68,11 +69,12 @@ def test_uniform_batch_matches_oracle():
     _check_against_oracle(recv, sigs, res, 12)
 
 
-def test_uneven_batch_matches_oracle():
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED)])
+def test_uneven_batch_matches_oracle(tiles):
     recv = [synth.uneven_receiver(i, n_blocks=40) for i in range(8)]
     assert len({r.fs for r in recv}) >= 3 and len({r.integ_blocks for r in recv}) >= 3
     buf, offs, sigs = _pack(recv, 40)
-    b = _batch(recv, 40)
+    b = _batch(recv, 40, tiles)
     try:
         rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 40)
         res = _read(b, recv, 40)
@@ -81,7 +83,7 @@ def test_uneven_batch_matches_oracle():
     _check_against_oracle(recv, sigs, res, 40)
 
 
-@pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE)])
+@pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE), (0, 224, 3, rx.RX_SCHED_BALANCED)])
 def test_multicorrelator_101_taps_matches_oracle(tiles):
     recv = [synth.multicorrelator_receiver(i, n_blocks=3) for i in range(2)]
     buf, offs, sigs = _pack(recv, 3)
@@ -103,7 +105,10 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
                   (2, 256, 0, rx.RX_SCHED_STATIC), (5, 512, 0, rx.RX_SCHED_STATIC),
                   (1, 128, 0, rx.RX_SCHED_PIPE), (2, 128, 0, rx.RX_SCHED_PIPE),
                   (3, 256, 0, rx.RX_SCHED_PIPE), (5, 512, 0, rx.RX_SCHED_PIPE),
-                  (2, 224, 0, rx.RX_SCHED_PIPE), (3, 224, 0, rx.RX_SCHED_PIPE)]:
+                  (2, 224, 0, rx.RX_SCHED_PIPE), (3, 224, 0, rx.RX_SCHED_PIPE),
+                  (0, 224, 3, rx.RX_SCHED_BALANCED), (0, 128, 4, rx.RX_SCHED_BALANCED),
+                  (0, 256, 1, rx.RX_SCHED_BALANCED), (0, 512, 1, rx.RX_SCHED_BALANCED),
+                  (0, 192, 3, rx.RX_SCHED_BALANCED)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -125,13 +130,15 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     assert np.array_equal(d, results[0][4][0])
 
 
-@pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE])
+@pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE,
+                                      rx.RX_SCHED_BALANCED])
 def test_graph_replay_restart_continue_and_host_input(schedule):
     recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
     recv[1].integ_blocks = 5                     # an integration spans the two runs (8 + 8 blocks)
     buf, offs, sigs = _pack(recv, 16)
     dev = torch.from_numpy(buf).cuda()
-    b = _batch(recv, 16, (2, 128, 0, schedule))
+    tiles = (0, 128, 0, schedule) if schedule == rx.RX_SCHED_BALANCED else (2, 128, 0, schedule)
+    b = _batch(recv, 16, tiles)
     try:
         # first half, then the second half continuing (device input, no graph)
         half = [np.ascontiguousarray(s[:8 * r.block_samples]) for s, r in zip(sigs, recv)]
@@ -177,7 +184,10 @@ def test_batch_invalid_arguments():
             rx.rx_batch_set_tiles(b, 0, 200, 0)
         assert e.value.status == rx.RX_EINVAL
         with pytest.raises(rx.RxError) as e:
-            rx.rx_batch_set_tiles(b, 2, 224, 0, rx.RX_SCHED_STATIC)   # 224 is for the pipeline only
+            rx.rx_batch_set_tiles(b, 2, 224, 0, rx.RX_SCHED_STATIC)   # 224: pipelined or balanced only
+        assert e.value.status == rx.RX_EINVAL
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 0, 224, 9, rx.RX_SCHED_BALANCED)
         assert e.value.status == rx.RX_EINVAL
     finally:
         rx.rx_batch_destroy(b)
