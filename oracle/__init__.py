@@ -39,6 +39,28 @@ class OrcChan(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class OrcExt(C.Structure):
+    """Extra per-channel state of Table 3's full loop set and the health
+    indicators (mirrors orc_ext in oracle.c)."""
+    _fields_ = [
+        ("prev_ip", C.c_int32),
+        ("prev_qp", C.c_int32),
+        ("have_prev", C.c_uint32),
+        ("window_count", C.c_uint32),
+        ("dll_u", C.c_double),
+        ("sum_abs_ip", C.c_double),
+        ("sum_power", C.c_double),
+        ("sum_diff", C.c_double),
+        ("cn0_hz", C.c_double),
+        ("lock_ratio", C.c_double),
+        ("lock_fail", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -69,6 +91,17 @@ def lib():
                                        C.c_uint32, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                        C.c_double, C.c_double, C.POINTER(OrcChan), P]
         L.orc_run_receiver.restype = C.c_int
+        L.orc_atan2_cycles.argtypes = [C.c_double, C.c_double]
+        L.orc_atan2_cycles.restype = C.c_double
+        L.orc_track_table3.argtypes = [C.POINTER(OrcChan), C.POINTER(OrcExt), P, P, C.c_int, C.c_int,
+                                       C.c_int, C.c_double, C.c_uint64, C.c_double, C.c_double,
+                                       C.c_double, C.c_uint32]
+        L.orc_track_table3.restype = None
+        L.orc_run_receiver_table3.argtypes = [P, C.c_uint32, C.c_uint32, C.c_double, C.c_uint32, P,
+                                              C.c_uint32, P, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                                              C.c_double, C.c_double, C.c_double, C.c_uint32,
+                                              C.POINTER(OrcChan), C.POINTER(OrcExt), P]
+        L.orc_run_receiver_table3.restype = C.c_int
         _lib = L
     return _lib
 
@@ -173,3 +206,50 @@ def run_receiver(iq: np.ndarray, n_blocks: int, N: int, fs: float, prn, tap_off,
     if rc != 0:
         raise ValueError("orc_run_receiver rejected its arguments")
     return dumps, [OrcChan.from_buffer_copy(arr[i]) for i in range(n_ch)]
+
+
+def atan2_cycles(y: float, x: float) -> float:
+    """atan2(y, x) / (2 pi), in cycles, four quadrants."""
+    return lib().orc_atan2_cycles(float(y), float(x))
+
+
+def track_table3(ch: OrcChan, ex: OrcExt, acc: np.ndarray, tap_off, tap_e: int, tap_p: int,
+                 tap_l: int, fs: float, n_accum: int, pll_bn: float, dll_bn: float,
+                 fll_bn: float, window: int):
+    """One update of Table 3's full loop set on copies of (ch, ex); returns the copies."""
+    out = OrcChan.from_buffer_copy(ch)
+    ox = OrcExt.from_buffer_copy(ex)
+    acc = np.ascontiguousarray(acc, dtype=np.int32).reshape(-1)
+    taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(-1)
+    lib().orc_track_table3(C.byref(out), C.byref(ox), _ptr(acc), _ptr(taps), tap_e, tap_p, tap_l,
+                           float(fs), int(n_accum), float(pll_bn), float(dll_bn), float(fll_bn),
+                           int(window))
+    return out, ox
+
+
+def run_receiver_table3(iq: np.ndarray, n_blocks: int, N: int, fs: float, prn, tap_off,
+                        L: int, tap_e: int, tap_p: int, tap_l: int, pll_bn: float,
+                        dll_bn: float, fll_bn: float, window: int, chans, exts=None):
+    """run_receiver with Table 3's full loop set.  Returns (dumps, chans_out, exts_out)."""
+    iq = np.ascontiguousarray(iq, dtype=np.int8).reshape(-1)
+    assert iq.size >= 2 * n_blocks * N
+    prn = np.ascontiguousarray(prn, dtype=np.uint8).reshape(-1)
+    n_ch = prn.size
+    taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(n_ch, -1)
+    n_taps = taps.shape[1]
+    arr = (OrcChan * n_ch)()
+    ext = (OrcExt * n_ch)()
+    for i, ch in enumerate(chans):
+        C.memmove(C.byref(arr[i]), C.byref(ch), C.sizeof(OrcChan))
+    if exts is not None:
+        for i, ex in enumerate(exts):
+            C.memmove(C.byref(ext[i]), C.byref(ex), C.sizeof(OrcExt))
+    dumps = np.zeros((n_blocks // L, n_ch, n_taps, 2), np.int32)
+    rc = lib().orc_run_receiver_table3(_ptr(iq), n_blocks, N, float(fs), n_ch, _ptr(prn), n_taps,
+                                       _ptr(taps), L, tap_e, tap_p, tap_l, float(pll_bn),
+                                       float(dll_bn), float(fll_bn), int(window), arr, ext,
+                                       _ptr(dumps))
+    if rc != 0:
+        raise ValueError("orc_run_receiver_table3 rejected its arguments")
+    return (dumps, [OrcChan.from_buffer_copy(arr[i]) for i in range(n_ch)],
+            [OrcExt.from_buffer_copy(ext[i]) for i in range(n_ch)])

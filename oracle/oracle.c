@@ -19,7 +19,9 @@
  *   - the tracking loops of Table 3: normalised early-minus-late envelope
  *     DLL discriminator with carrier aiding, atan PLL discriminator, a
  *     2nd-order PLL and a 1st-order DLL, followed by re-quantisation of the
- *     NCO words.  Every floating-point step is a single correctly rounded
+ *     NCO words; and Table 3's full set (2nd-order PLL with a 1st-order atan2
+ *     FLL assist, 2nd-order DLL) with Sec. 4's channel-health indicators
+ *     (C/N0, carrier lock ratio, lock-fail count).  Every floating-point step is a single correctly rounded
  *     IEEE-754 binary64 operation, written one per statement, in a fixed
  *     order; the file must be compiled with -ffp-contract=off.
  *
@@ -361,6 +363,185 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Table 3's full loop set and the channel-health indicators of Sec. 4       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * atan2(y, x) / (2 pi) in cycles, four quadrants, in (-1/2, 1/2]: the FLL's
+ * discriminator (Table 3: FLL atan2).  Built on orc_atan_cycles (two
+ * quadrants) by the quadrant of (x, y); +-1/2 cycle is exact.
+ */
+double orc_atan2_cycles(double y, double x) {
+    if (x == 0.0) return y > 0.0 ? 0.25 : (y < 0.0 ? -0.25 : 0.0);
+    double a = orc_atan_cycles(y, x);
+    if (x > 0.0) return a;
+    if (y >= 0.0) return a + 0.5;
+    return a - 0.5;
+}
+
+/* Extra per-channel state of the full loop set and the health indicators. */
+typedef struct {
+    int32_t prev_ip, prev_qp;  /* the previous integration's prompt (FLL) */
+    uint32_t have_prev;        /* 1 once a previous prompt exists */
+    uint32_t window_count;     /* integrations in the current health window */
+    double dll_u;              /* 2nd-order DLL's rate integrator, chips/s */
+    double sum_abs_ip;         /* window sums: |I_P| */
+    double sum_power;          /*   I_P^2 + Q_P^2 */
+    double sum_diff;           /*   I_P^2 - Q_P^2 */
+    double cn0_hz;             /* last C/N0, linear (Hz); 0 before the first window */
+    double lock_ratio;         /* last carrier lock ratio (cos of twice the phase error) */
+    uint32_t lock_fail;        /* windows whose lock ratio was below 0.85 */
+    uint32_t pad;
+} orc_ext;
+
+void orc_ext_init(orc_ext *ex) { memset(ex, 0, sizeof *ex); }
+
+/*
+ * One update of Table 3's full loop set at an integration boundary (T =
+ * n_accum / fs):
+ *   PLL discriminator   e_p = atan(Q_P / I_P) / (2 pi)                 cycles
+ *   FLL discriminator   e_f = atan2(s cross, s dot) / (2 pi) / T       Hz
+ *                       cross = I1 Q2 - I2 Q1, dot = I1 I2 + Q1 Q2 (1 = previous,
+ *                       2 = this integration's prompt; e_f = 0 without a previous one),
+ *                       s = sign(dot): the decision on the product of the two data bits,
+ *                       removed so that a bit change does not read as a frequency error
+ *   carrier filter      2nd-order PLL with 1st-order FLL assist, w0p = Bn_pll / 0.53,
+ *                       w0f = 4 Bn_fll:
+ *                         v      = v + (w0p^2 T) e_p + (w0f T) e_f
+ *                         f_carr = v + (sqrt2 w0p) e_p
+ *   DLL discriminator   e_c as in orc_track (normalised E-L envelope)
+ *   code filter         2nd-order DLL, carrier aided, w0d = Bn_dll / 0.53:
+ *                         u      = u + (w0d^2 T) e_c
+ *                         f_code = 1.023e6 + f_carr / 1540 + (u + (sqrt2 w0d) e_c)
+ * and the words as in orc_track.  Health (Sec. 4's channel-health indicators),
+ * over windows of `window` integrations: C/N0 by the signal-to-noise-variance
+ * estimator, Pd = (mean |I_P|)^2, Pn = mean(I_P^2 + Q_P^2) - Pd, C/N0 = Pd / Pn / T
+ * (linear, Hz; 0 if Pn <= 0); carrier lock ratio sum(I_P^2 - Q_P^2) / sum(I_P^2 +
+ * Q_P^2), the estimate of cos(2 x phase error); the lock-fail count grows by one for
+ * each window whose ratio is below 0.85.  One IEEE op per statement, in order.
+ */
+void orc_track_table3(orc_chan *ch, orc_ext *ex, const int32_t *acc, const int64_t *tap_off,
+                      int tap_e, int tap_p, int tap_l, double fs, uint64_t n_accum,
+                      double pll_bn, double dll_bn, double fll_bn, uint32_t window) {
+    double T = (double)n_accum / fs;
+    double inv_T = fs / (double)n_accum;
+    double w0p = pll_bn / 0.53;
+    double k1 = w0p * w0p;
+    k1 = k1 * T;
+    double k2 = ORC_SQRT2 * w0p;
+    double kf = 4.0 * fll_bn;
+    kf = kf * T;
+    double w0d = dll_bn / 0.53;
+    double kd1 = w0d * w0d;
+    kd1 = kd1 * T;
+    double kd2 = ORC_SQRT2 * w0d;
+    double sfs = 4294967296.0 / fs;
+
+    int32_t ipi = acc[2 * tap_p], qpi = acc[2 * tap_p + 1];
+    double ip = (double)ipi, qp = (double)qpi;
+    double e_p;
+    if (ip != 0.0) {
+        e_p = orc_atan_cycles(qp, ip);
+    } else {
+        e_p = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+    }
+    double e_f = 0.0;
+    if (ex->have_prev) {
+        double i1 = (double)ex->prev_ip, q1 = (double)ex->prev_qp;
+        double a = i1 * qp;
+        double b = ip * q1;
+        double cross = a - b;
+        double c = i1 * ip;
+        double d = q1 * qp;
+        double dot = c + d;
+        /* a data-bit change between the two integrations turns the prompt by half a
+         * cycle; the product of the two bits is taken as sign(dot) and removed */
+        if (dot < 0.0) {
+            cross = -cross;
+            dot = -dot;
+        }
+        double ef = orc_atan2_cycles(cross, dot);
+        e_f = ef * inv_T;
+    }
+    double dv = k1 * e_p;
+    double dvf = kf * e_f;
+    double v = ch->v + dv;
+    v = v + dvf;
+    ch->v = v;
+    double df = k2 * e_p;
+    double f_carr = v + df;
+
+    double ie = (double)acc[2 * tap_e], qe = (double)acc[2 * tap_e + 1];
+    double il = (double)acc[2 * tap_l], ql = (double)acc[2 * tap_l + 1];
+    double ie2 = ie * ie, qe2 = qe * qe, il2 = il * il, ql2 = ql * ql;
+    double mag_e = sqrt(ie2 + qe2);
+    double mag_l = sqrt(il2 + ql2);
+    double den = mag_e + mag_l;
+    double d_el = (double)(tap_off[tap_e] - tap_off[tap_l]) * ORC_TWO_M32;
+    double kd = d_el * 0.5;
+    kd = 1.0 - kd;
+    double e_c = 0.0;
+    if (den > 0.0) {
+        double num = mag_e - mag_l;
+        num = kd * num;
+        e_c = num / den;
+    }
+    double du = kd1 * e_c;
+    double u = ex->dll_u + du;
+    ex->dll_u = u;
+    double aid = f_carr * ORC_KAID;
+    double f_code = 1.023e6 + aid;
+    double prop = kd2 * e_c;
+    prop = u + prop;
+    f_code = f_code + prop;
+
+    double xw = f_carr * sfs;
+    double xr = f_code * sfs;
+    if (xw > 9.0e18) xw = 9.0e18;
+    if (xw < -9.0e18) xw = -9.0e18;
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    ch->w = (int32_t)(uint32_t)(uint64_t)(int64_t)nearbyint(xw);
+    ch->r = (uint64_t)nearbyint(xr);
+    ch->f_carr = f_carr;
+    ch->f_code = f_code;
+
+    /* health window */
+    double ip2 = ip * ip;
+    double qp2 = qp * qp;
+    double pw = ip2 + qp2;
+    double df2 = ip2 - qp2;
+    ex->sum_abs_ip = ex->sum_abs_ip + fabs(ip);
+    ex->sum_power = ex->sum_power + pw;
+    ex->sum_diff = ex->sum_diff + df2;
+    ex->window_count = ex->window_count + 1;
+    if (window > 0 && ex->window_count == window) {
+        double K = (double)window;
+        double m = ex->sum_abs_ip / K;
+        double pd = m * m;
+        double pt = ex->sum_power / K;
+        double pn = pt - pd;
+        double cn0 = 0.0;
+        if (pn > 0.0) {
+            cn0 = pd / pn;
+            cn0 = cn0 * inv_T;
+        }
+        double lock = 0.0;
+        if (ex->sum_power > 0.0) lock = ex->sum_diff / ex->sum_power;
+        ex->cn0_hz = cn0;
+        ex->lock_ratio = lock;
+        if (lock < 0.85) ex->lock_fail = ex->lock_fail + 1;
+        ex->sum_abs_ip = 0.0;
+        ex->sum_power = 0.0;
+        ex->sum_diff = 0.0;
+        ex->window_count = 0;
+    }
+    ex->prev_ip = ipi;
+    ex->prev_qp = qpi;
+    ex->have_prev = 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A whole receiver: blocks in order, channels independent (Sec. 3.5)       */
 /* ------------------------------------------------------------------------ */
 
@@ -370,11 +551,38 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
  * dumps its accumulators to dumps[(b+1)/L - 1][ch][tap][2], runs orc_track and
  * clears them.  Returns 0, or -1 on bad arguments.
  */
+static int orc_run(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
+                   uint32_t n_ch, const uint8_t *prn, uint32_t n_taps,
+                   const int64_t *tap_off, uint32_t L, int tap_e, int tap_p,
+                   int tap_l, double pll_bn, double dll_bn, double fll_bn,
+                   uint32_t window, orc_chan *ch, orc_ext *ex, int32_t *dumps);
+
 int orc_run_receiver(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
                      uint32_t n_ch, const uint8_t *prn, uint32_t n_taps,
                      const int64_t *tap_off, uint32_t L, int tap_e, int tap_p,
                      int tap_l, double pll_bn, double dll_bn, orc_chan *ch,
                      int32_t *dumps) {
+    return orc_run(iq, n_blocks, N, fs, n_ch, prn, n_taps, tap_off, L, tap_e, tap_p, tap_l,
+                   pll_bn, dll_bn, 0.0, 0, ch, NULL, dumps);
+}
+
+/* As orc_run_receiver with Table 3's full loop set (orc_track_table3); ex holds
+ * each channel's extra state (in and out). */
+int orc_run_receiver_table3(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
+                            uint32_t n_ch, const uint8_t *prn, uint32_t n_taps,
+                            const int64_t *tap_off, uint32_t L, int tap_e, int tap_p,
+                            int tap_l, double pll_bn, double dll_bn, double fll_bn,
+                            uint32_t window, orc_chan *ch, orc_ext *ex, int32_t *dumps) {
+    if (!ex) return -1;
+    return orc_run(iq, n_blocks, N, fs, n_ch, prn, n_taps, tap_off, L, tap_e, tap_p, tap_l,
+                   pll_bn, dll_bn, fll_bn, window, ch, ex, dumps);
+}
+
+static int orc_run(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
+                   uint32_t n_ch, const uint8_t *prn, uint32_t n_taps,
+                   const int64_t *tap_off, uint32_t L, int tap_e, int tap_p,
+                   int tap_l, double pll_bn, double dll_bn, double fll_bn,
+                   uint32_t window, orc_chan *ch, orc_ext *ex, int32_t *dumps) {
     if (L == 0 || n_taps == 0) return -1;
     if (tap_e < 0 || tap_p < 0 || tap_l < 0 || (uint32_t)tap_e >= n_taps ||
         (uint32_t)tap_p >= n_taps || (uint32_t)tap_l >= n_taps)
@@ -401,8 +609,13 @@ int orc_run_receiver(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
                 int32_t *a = acc + (size_t)c * n_taps * 2;
                 memcpy(dumps + ((e * n_ch + c) * n_taps) * 2, a,
                        sizeof(int32_t) * n_taps * 2);
-                orc_track(&ch[c], a, tap_off + (size_t)c * n_taps, tap_e, tap_p,
-                          tap_l, fs, (uint64_t)L * N, pll_bn, dll_bn);
+                if (ex)
+                    orc_track_table3(&ch[c], &ex[c], a, tap_off + (size_t)c * n_taps, tap_e,
+                                     tap_p, tap_l, fs, (uint64_t)L * N, pll_bn, dll_bn, fll_bn,
+                                     window);
+                else
+                    orc_track(&ch[c], a, tap_off + (size_t)c * n_taps, tap_e, tap_p,
+                              tap_l, fs, (uint64_t)L * N, pll_bn, dll_bn);
                 memset(a, 0, sizeof(int32_t) * n_taps * 2);
             }
         }
