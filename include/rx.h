@@ -116,7 +116,51 @@ typedef struct {
     int32_t tap_late;            /* tap index used as L by the DLL discriminator */
     int32_t device;              /* CUDA device ordinal */
     void *cuda_stream;           /* cudaStream_t for all work of this handle, or NULL */
+    uint32_t loop_set;           /* RX_LOOPS_PLL2_DLL1 (0) or RX_LOOPS_TABLE3 (1) */
+    uint32_t health_window;      /* RX_LOOPS_TABLE3: integrations per C/N0 and lock-ratio
+                                    estimate (0 = no estimates) */
+    double fll_bn_hz;            /* RX_LOOPS_TABLE3: FLL noise bandwidth (1st order, assists the
+                                    PLL); 0 = no FLL; with RX_LOOPS_TABLE3 dll_bn_hz is the
+                                    bandwidth of a 2nd-order DLL */
 } rx_config;
+
+/* Loop sets of the plain form.  RX_LOOPS_PLL2_DLL1: 2nd-order PLL, 1st-order
+ * carrier-aided DLL (the loops of rx_track_epoch above; the batched and served
+ * forms always use these).  RX_LOOPS_TABLE3: Table 3's full set, with Sec. 4's
+ * channel-health indicators:
+ *   e_p  = atan(Q_P / I_P) / (2 pi)                                   cycles
+ *   e_f  = atan2(s cross, s dot) / (2 pi) / T                         Hz,
+ *          cross = I1 Q2 - I2 Q1, dot = I1 I2 + Q1 Q2 over the previous (1) and
+ *          this (2) prompt, s = sign(dot) (the data-bit product, removed);
+ *          e_f = 0 for a channel's first integration
+ *   v      += (w0p^2 T) e_p + (4 Bn_fll T) e_f,  f_carr = v + (sqrt2 w0p) e_p,
+ *             w0p = Bn_pll / 0.53                (2nd-order PLL + 1st-order FLL)
+ *   u      += (w0d^2 T) e_c,  f_code = 1.023e6 + f_carr / 1540 + u + (sqrt2 w0d) e_c,
+ *             w0d = Bn_dll / 0.53                (2nd-order DLL, carrier aided)
+ * with e_c the normalised early-minus-late envelope as above.  Every
+ * health_window integrations: C/N0 = Pd / Pn / T (signal-to-noise variance:
+ * Pd = mean(|I_P|)^2, Pn = mean(I_P^2 + Q_P^2) - Pd; linear Hz), the carrier
+ * lock ratio sum(I_P^2 - Q_P^2) / sum(I_P^2 + Q_P^2) (an estimate of the cosine
+ * of twice the phase error) and a lock-fail count of windows whose ratio was
+ * below 0.85. */
+#define RX_LOOPS_PLL2_DLL1 0u
+#define RX_LOOPS_TABLE3 1u
+
+/* Extra per-channel state of RX_LOOPS_TABLE3 (zero after rx_set_channels). */
+typedef struct {
+    double cn0_hz;               /* last C/N0 estimate, linear (10 log10 for dB-Hz); 0 before
+                                    the first window */
+    double lock_ratio;           /* last carrier lock ratio, -1..1 */
+    uint32_t lock_fail_count;    /* windows whose lock ratio was below 0.85 */
+    uint32_t window_count;       /* integrations in the current window */
+    double sum_abs_ip;           /* the current window's sums of |I_P|, */
+    double sum_power;            /*   I_P^2 + Q_P^2 and */
+    double sum_diff;             /*   I_P^2 - Q_P^2 */
+    double dll_integrator_hz;    /* 2nd-order DLL's rate integrator, chips/s */
+    int32_t prev_ip, prev_qp;    /* previous integration's prompt (FLL) */
+    uint32_t have_prev;          /* 1 once the channel has a previous prompt */
+    uint32_t pad;
+} rx_channel_health;
 
 typedef struct rx_handle_s *rx_handle;
 
@@ -176,6 +220,12 @@ rx_status rx_read_state(rx_handle h, rx_channel_state *out, uint32_t cap);
 /* Load per-channel state (checkpoint / resume) for the n channels already set
  * by rx_set_channels; prn must match.  Accumulators are left as they are. */
 rx_status rx_write_state(rx_handle h, const rx_channel_state *in, uint32_t n);
+
+/* RX_LOOPS_TABLE3 state and health indicators of every channel (cap >=
+ * channels; synchronises), and its restore for checkpoint/resume (n =
+ * channels). */
+rx_status rx_read_health(rx_handle h, rx_channel_health *out, uint32_t cap);
+rx_status rx_write_health(rx_handle h, const rx_channel_health *in, uint32_t n);
 
 /* Message for the last failed call on h (static storage inside the handle). */
 const char *rx_last_error(rx_handle h);

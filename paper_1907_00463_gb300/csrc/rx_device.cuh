@@ -498,4 +498,144 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
     return o;
 }
 
+// ----------------------------------------------------------------------------
+// Table 3's full loop set and Sec. 4's channel-health indicators
+// ----------------------------------------------------------------------------
+
+// atan2(y, x) / (2 pi) in cycles, four quadrants, in (-1/2, 1/2] (the FLL's atan2).
+__device__ __forceinline__ double atan2_cycles(double y, double x) {
+    if (x == 0.0) return y > 0.0 ? 0.25 : (y < 0.0 ? -0.25 : 0.0);
+    const double a = atan_cycles(y, x);
+    if (x > 0.0) return a;
+    return y >= 0.0 ? __dadd_rn(a, 0.5) : __dsub_rn(a, 0.5);
+}
+
+// Per-integration constants of the full loop set, T = n_accum / fs:
+//   k1 = (Bn_pll / 0.53)^2 T, k2 = sqrt2 Bn_pll / 0.53, kf = 4 Bn_fll T,
+//   kd1 = (Bn_dll / 0.53)^2 T, kd2 = sqrt2 Bn_dll / 0.53, sfs = 2^32 / fs, inv_T = fs / n_accum.
+struct LoopConsts3 {
+    double k1, k2, kf, kd1, kd2, sfs, inv_T;
+};
+
+__host__ inline LoopConsts3 make_loop_consts3(double fs, uint64_t n_accum, double pll_bn, double dll_bn,
+                                              double fll_bn) {
+    LoopConsts3 c;
+    const double T = (double)n_accum / fs;
+    c.inv_T = fs / (double)n_accum;
+    const double w0p = pll_bn / 0.53;
+    double k1 = w0p * w0p;
+    k1 = k1 * T;
+    c.k1 = k1;
+    c.k2 = RXD_SQRT2 * w0p;
+    double kf = 4.0 * fll_bn;
+    c.kf = kf * T;
+    const double w0d = dll_bn / 0.53;
+    double kd1 = w0d * w0d;
+    c.kd1 = kd1 * T;
+    c.kd2 = RXD_SQRT2 * w0d;
+    c.sfs = 4294967296.0 / fs;
+    return c;
+}
+
+// Extra per-channel state of the full loop set and the health indicators.
+struct LoopExt {
+    int32_t prev_ip, prev_qp;   // previous integration's prompt (FLL)
+    uint32_t have_prev;
+    uint32_t window_count;
+    double dll_u;               // 2nd-order DLL's rate integrator, chips/s
+    double sum_abs, sum_pow, sum_diff;   // window sums of |I_P|, I_P^2 + Q_P^2, I_P^2 - Q_P^2
+    double cn0;                 // last C/N0 (linear, Hz)
+    double lock;                // last carrier lock ratio
+    uint32_t lock_fail;         // windows with lock ratio below 0.85
+};
+
+// One update of the full loop set (Table 3):
+//   e_p = atan(Q_P / I_P) / (2 pi);  e_f = atan2(s cross, s dot) / (2 pi) / T with
+//   cross = I1 Q2 - I2 Q1, dot = I1 I2 + Q1 Q2 of the previous and this prompt and
+//   s = sign(dot) (the data-bit product, removed);  v += k1 e_p + kf e_f;
+//   f_carr = v + k2 e_p;  e_c as in loop_update;  u += kd1 e_c;
+//   f_code = 1.023e6 + f_carr / 1540 + (u + kd2 e_c);  words as in loop_update.
+// Health over `window` integrations: C/N0 = Pd / Pn / T (signal-to-noise variance:
+// Pd = mean(|I_P|)^2, Pn = mean(I_P^2 + Q_P^2) - Pd), lock = sum(I_P^2 - Q_P^2) /
+// sum(I_P^2 + Q_P^2), lock_fail += (lock < 0.85).  Same operations, same order,
+// as the CPU definition.
+__device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t ie, int32_t qe, int32_t ipr,
+                                                int32_t qpr, int32_t il, int32_t ql, int64_t off_e,
+                                                int64_t off_l, const LoopConsts3 &lc, uint32_t window) {
+    LoopOut o;
+    const double ip = (double)ipr, qp = (double)qpr;
+    double e_p;
+    if (ip != 0.0) {
+        e_p = atan_cycles(qp, ip);
+    } else {
+        e_p = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+    }
+    double e_f = 0.0;
+    if (ex.have_prev) {
+        const double i1 = (double)ex.prev_ip, q1 = (double)ex.prev_qp;
+        double cross = __dsub_rn(__dmul_rn(i1, qp), __dmul_rn(ip, q1));
+        double dot = __dadd_rn(__dmul_rn(i1, ip), __dmul_rn(q1, qp));
+        if (dot < 0.0) {
+            cross = -cross;
+            dot = -dot;
+        }
+        e_f = __dmul_rn(atan2_cycles(cross, dot), lc.inv_T);
+    }
+    v = __dadd_rn(v, __dmul_rn(lc.k1, e_p));
+    v = __dadd_rn(v, __dmul_rn(lc.kf, e_f));
+    const double f_carr = __dadd_rn(v, __dmul_rn(lc.k2, e_p));
+
+    const double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
+    const double mag_e = __dsqrt_rn(__dadd_rn(__dmul_rn(dIe, dIe), __dmul_rn(dQe, dQe)));
+    const double mag_l = __dsqrt_rn(__dadd_rn(__dmul_rn(dIl, dIl), __dmul_rn(dQl, dQl)));
+    const double den = __dadd_rn(mag_e, mag_l);
+    const double d_el = __dmul_rn((double)(off_e - off_l), RXD_TWO_M32);
+    const double kd = __dsub_rn(1.0, __dmul_rn(d_el, 0.5));
+    double e_c = 0.0;
+    if (den > 0.0) e_c = __ddiv_rn(__dmul_rn(kd, __dsub_rn(mag_e, mag_l)), den);
+    const double u = __dadd_rn(ex.dll_u, __dmul_rn(lc.kd1, e_c));
+    ex.dll_u = u;
+    double f_code = __dadd_rn(1.023e6, __dmul_rn(f_carr, RXD_KAID));
+    f_code = __dadd_rn(f_code, __dadd_rn(u, __dmul_rn(lc.kd2, e_c)));
+
+    double xw = __dmul_rn(f_carr, lc.sfs);
+    double xr = __dmul_rn(f_code, lc.sfs);
+    if (xw > 9.0e18) xw = 9.0e18;
+    if (xw < -9.0e18) xw = -9.0e18;
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
+    o.r = (uint64_t)__double2ll_rn(xr);
+    o.v = v;
+    o.f_carr = f_carr;
+    o.f_code = f_code;
+
+    const double ip2 = __dmul_rn(ip, ip), qp2 = __dmul_rn(qp, qp);
+    ex.sum_abs = __dadd_rn(ex.sum_abs, fabs(ip));
+    ex.sum_pow = __dadd_rn(ex.sum_pow, __dadd_rn(ip2, qp2));
+    ex.sum_diff = __dadd_rn(ex.sum_diff, __dsub_rn(ip2, qp2));
+    ex.window_count += 1;
+    if (window > 0 && ex.window_count == window) {
+        const double K = (double)window;
+        const double m = __ddiv_rn(ex.sum_abs, K);
+        const double pd = __dmul_rn(m, m);
+        const double pn = __dsub_rn(__ddiv_rn(ex.sum_pow, K), pd);
+        double cn0 = 0.0;
+        if (pn > 0.0) cn0 = __dmul_rn(__ddiv_rn(pd, pn), lc.inv_T);
+        double lock = 0.0;
+        if (ex.sum_pow > 0.0) lock = __ddiv_rn(ex.sum_diff, ex.sum_pow);
+        ex.cn0 = cn0;
+        ex.lock = lock;
+        if (lock < 0.85) ex.lock_fail += 1;
+        ex.sum_abs = 0.0;
+        ex.sum_pow = 0.0;
+        ex.sum_diff = 0.0;
+        ex.window_count = 0;
+    }
+    ex.prev_ip = ipr;
+    ex.prev_qp = qpr;
+    ex.have_prev = 1;
+    return o;
+}
+
 }  // namespace rxd

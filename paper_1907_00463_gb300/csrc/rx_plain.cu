@@ -29,6 +29,7 @@ struct PlainState {
     uint32_t *epochs;
     int64_t *taps;     // [n][ntaps]
     int32_t *acc;      // [n][ntaps][2]
+    LoopExt *ext;      // [n], RX_LOOPS_TABLE3
 };
 
 template <int TT>
@@ -178,6 +179,28 @@ __global__ void k_plain_track(PlainState st, uint32_t n_ch, uint32_t ntaps, uint
     for (uint32_t i = 0; i < 2 * ntaps; ++i) a[i] = 0;
 }
 
+// As k_plain_track with Table 3's full loop set and the health indicators.
+__global__ void k_plain_track3(PlainState st, uint32_t n_ch, uint32_t ntaps, uint64_t n_fold,
+                               LoopConsts3 lc, int tap_e, int tap_p, int tap_l, uint32_t window) {
+    uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_ch) return;
+    st.theta[c] = st.theta[c] + (uint32_t)n_fold * (uint32_t)st.w[c];
+    st.phi[c] = reduce_code_phase(st.phi[c] + n_fold * st.r[c]);
+    int32_t *a = st.acc + (size_t)c * ntaps * 2;
+    const int64_t *t = st.taps + (size_t)c * ntaps;
+    LoopExt ex = st.ext[c];
+    LoopOut o = loop_update3(st.v[c], ex, a[2 * tap_e], a[2 * tap_e + 1], a[2 * tap_p], a[2 * tap_p + 1],
+                             a[2 * tap_l], a[2 * tap_l + 1], t[tap_e], t[tap_l], lc, window);
+    st.ext[c] = ex;
+    st.v[c] = o.v;
+    st.fcarr[c] = o.f_carr;
+    st.fcode[c] = o.f_code;
+    st.w[c] = o.w;
+    st.r[c] = o.r;
+    st.epochs[c] += 1;
+    for (uint32_t i = 0; i < 2 * ntaps; ++i) a[i] = 0;
+}
+
 }  // namespace
 
 struct rx_handle_s {
@@ -212,7 +235,8 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
         cfg->max_channels > RX_MAX_CHANNELS || cfg->max_taps == 0 || cfg->max_taps > RX_MAX_TAPS ||
         cfg->tap_early < 0 || cfg->tap_prompt < 0 || cfg->tap_late < 0 ||
         (uint32_t)cfg->tap_early >= cfg->max_taps || (uint32_t)cfg->tap_prompt >= cfg->max_taps ||
-        (uint32_t)cfg->tap_late >= cfg->max_taps || !(cfg->pll_bn_hz >= 0) || !(cfg->dll_bn_hz >= 0))
+        (uint32_t)cfg->tap_late >= cfg->max_taps || !(cfg->pll_bn_hz >= 0) || !(cfg->dll_bn_hz >= 0) ||
+        cfg->loop_set > RX_LOOPS_TABLE3 || !(cfg->fll_bn_hz >= 0))
         return RX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= cfg->device || cfg->device < 0) {
@@ -243,7 +267,7 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
     size_t o_theta = take(C * 4), o_w = take(C * 4), o_phi = take(C * 8), o_r = take(C * 8),
            o_prn = take(C * 4), o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8),
            o_ep = take(C * 4), o_taps = take(C * T * 8), o_acc = take(C * T * 8),
-           o_stage = take(2 * (size_t)cfg->max_block_samples + 64);
+           o_ext = take(C * sizeof(LoopExt)), o_stage = take(2 * (size_t)cfg->max_block_samples + 64);
     if (cudaMalloc(&h->d_block, off) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -261,6 +285,7 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
     h->st.epochs = (uint32_t *)(b + o_ep);
     h->st.taps = (int64_t *)(b + o_taps);
     h->st.acc = (int32_t *)(b + o_acc);
+    h->st.ext = (LoopExt *)(b + o_ext);
     h->d_stage = (int8_t *)(b + o_stage);
     if (cudaMemsetAsync(h->d_block, 0, off, h->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -324,6 +349,7 @@ extern "C" rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn
     RX_CUDA_TRY(cudaMemcpy(h->st.epochs, ep.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemcpy(h->st.taps, tap_offsets, (size_t)n * ntaps * 8, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemset(h->st.acc, 0, (size_t)n * ntaps * 8), E);
+    RX_CUDA_TRY(cudaMemset(h->st.ext, 0, (size_t)n * sizeof(LoopExt)), E);
     h->n_ch = n;
     h->n_taps = ntaps;
     h->n_since_fold = 0;
@@ -370,10 +396,16 @@ extern "C" rx_status rx_track_epoch(rx_handle h) {
     if (h->n_ch == 0 || h->n_accum == 0)
         return set_err(h, RX_ESTATE, "no samples correlated since the last boundary");
     cudaSetDevice(h->cfg.device);
-    k_plain_track<<<(h->n_ch + 63) / 64, 64, 0, h->stream>>>(
-        h->st, h->n_ch, h->n_taps, h->n_since_fold,
-        make_loop_consts(h->cfg.fs_hz, h->n_accum, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz), h->cfg.tap_early,
-        h->cfg.tap_prompt, h->cfg.tap_late);
+    if (h->cfg.loop_set == RX_LOOPS_TABLE3)
+        k_plain_track3<<<(h->n_ch + 63) / 64, 64, 0, h->stream>>>(
+            h->st, h->n_ch, h->n_taps, h->n_since_fold,
+            make_loop_consts3(h->cfg.fs_hz, h->n_accum, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz, h->cfg.fll_bn_hz),
+            h->cfg.tap_early, h->cfg.tap_prompt, h->cfg.tap_late, h->cfg.health_window);
+    else
+        k_plain_track<<<(h->n_ch + 63) / 64, 64, 0, h->stream>>>(
+            h->st, h->n_ch, h->n_taps, h->n_since_fold,
+            make_loop_consts(h->cfg.fs_hz, h->n_accum, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz), h->cfg.tap_early,
+            h->cfg.tap_prompt, h->cfg.tap_late);
     RX_CUDA_TRY(cudaGetLastError(), h->err);
     h->n_since_fold = 0;
     h->n_accum = 0;
@@ -477,3 +509,53 @@ extern "C" rx_status rx_write_state(rx_handle h, const rx_channel_state *in, uin
 }
 
 extern "C" const char *rx_last_error(rx_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" rx_status rx_read_health(rx_handle h, rx_channel_health *out, uint32_t cap) {
+    if (!h || !out) return RX_EINVAL;
+    if (cap < h->n_ch) return set_err(h, RX_EINVAL, "cap < channels");
+    std::vector<LoopExt> ex(h->n_ch);
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    if (h->n_ch)
+        RX_CUDA_TRY(cudaMemcpy(ex.data(), h->st.ext, h->n_ch * sizeof(LoopExt), cudaMemcpyDeviceToHost), h->err);
+    for (uint32_t c = 0; c < h->n_ch; ++c) {
+        rx_channel_health &o = out[c];
+        o.cn0_hz = ex[c].cn0;
+        o.lock_ratio = ex[c].lock;
+        o.lock_fail_count = ex[c].lock_fail;
+        o.window_count = ex[c].window_count;
+        o.sum_abs_ip = ex[c].sum_abs;
+        o.sum_power = ex[c].sum_pow;
+        o.sum_diff = ex[c].sum_diff;
+        o.dll_integrator_hz = ex[c].dll_u;
+        o.prev_ip = ex[c].prev_ip;
+        o.prev_qp = ex[c].prev_qp;
+        o.have_prev = ex[c].have_prev;
+        o.pad = 0;
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_write_health(rx_handle h, const rx_channel_health *in, uint32_t n) {
+    if (!h || !in) return RX_EINVAL;
+    if (n != h->n_ch) return set_err(h, RX_EINVAL, "n != channels");
+    std::vector<LoopExt> ex(n);
+    for (uint32_t c = 0; c < n; ++c) {
+        const rx_channel_health &i = in[c];
+        ex[c].cn0 = i.cn0_hz;
+        ex[c].lock = i.lock_ratio;
+        ex[c].lock_fail = i.lock_fail_count;
+        ex[c].window_count = i.window_count;
+        ex[c].sum_abs = i.sum_abs_ip;
+        ex[c].sum_pow = i.sum_power;
+        ex[c].sum_diff = i.sum_diff;
+        ex[c].dll_u = i.dll_integrator_hz;
+        ex[c].prev_ip = i.prev_ip;
+        ex[c].prev_qp = i.prev_qp;
+        ex[c].have_prev = i.have_prev ? 1u : 0u;
+    }
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    if (n) RX_CUDA_TRY(cudaMemcpy(h->st.ext, ex.data(), n * sizeof(LoopExt), cudaMemcpyHostToDevice), h->err);
+    return RX_OK;
+}

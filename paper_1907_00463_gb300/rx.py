@@ -25,6 +25,8 @@ RX_SCHED_STATIC = 1
 RX_SCHED_PIPE = 2
 RX_SCHED_BALANCED = 3
 RX_WAIT_TEST_STALL = 1
+RX_LOOPS_PLL2_DLL1 = 0
+RX_LOOPS_TABLE3 = 1
 
 
 class RxError(RuntimeError):
@@ -38,7 +40,19 @@ class rx_config(C.Structure):
                 ("max_channels", C.c_uint32), ("max_taps", C.c_uint32),
                 ("pll_bn_hz", C.c_double), ("dll_bn_hz", C.c_double),
                 ("tap_early", C.c_int32), ("tap_prompt", C.c_int32), ("tap_late", C.c_int32),
-                ("device", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("device", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("loop_set", C.c_uint32), ("health_window", C.c_uint32), ("fll_bn_hz", C.c_double)]
+
+
+class rx_channel_health(C.Structure):
+    _fields_ = [("cn0_hz", C.c_double), ("lock_ratio", C.c_double),
+                ("lock_fail_count", C.c_uint32), ("window_count", C.c_uint32),
+                ("sum_abs_ip", C.c_double), ("sum_power", C.c_double), ("sum_diff", C.c_double),
+                ("dll_integrator_hz", C.c_double), ("prev_ip", C.c_int32), ("prev_qp", C.c_int32),
+                ("have_prev", C.c_uint32), ("pad", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class rx_channel_state(C.Structure):
@@ -107,6 +121,8 @@ SIGNATURES = [
     ("rx_write_accumulators", C.c_int, [P, P, C.c_uint32, C.c_uint64]),
     ("rx_read_state", C.c_int, [P, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_write_state", C.c_int, [P, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_read_health", C.c_int, [P, C.POINTER(rx_channel_health), C.c_uint32]),
+    ("rx_write_health", C.c_int, [P, C.POINTER(rx_channel_health), C.c_uint32]),
     ("rx_last_error", C.c_char_p, [P]),
     ("rx_batch_create", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, C.c_uint32, C.c_int32,
                                   P, C.POINTER(P)]),
@@ -204,10 +220,12 @@ def _check(h, s, err_fn):
 
 def rx_create(fs_hz: float, max_block_samples: int, max_channels: int, max_taps: int,
               pll_bn_hz: float = 15.0, dll_bn_hz: float = 1.0, tap_early: int = 2,
-              tap_prompt: int = 1, tap_late: int = 0, device: int = 0, stream=None):
+              tap_prompt: int = 1, tap_late: int = 0, device: int = 0, stream=None,
+              loop_set: int = 0, health_window: int = 0, fll_bn_hz: float = 0.0):
     lib = load()
     cfg = rx_config(fs_hz, max_block_samples, max_channels, max_taps, pll_bn_hz, dll_bn_hz,
-                    tap_early, tap_prompt, tap_late, device, _stream_handle(stream))
+                    tap_early, tap_prompt, tap_late, device, _stream_handle(stream), loop_set,
+                    health_window, fll_bn_hz)
     h = P()
     s = lib.rx_create(C.byref(cfg), C.byref(h))
     if s != RX_OK:
@@ -271,6 +289,20 @@ def rx_write_state(h, states) -> None:
     n = len(states)
     arr = (rx_channel_state * n)(*states)
     _check(h, lib.rx_write_state(h, arr, n), lib.rx_last_error)
+
+
+def rx_read_health(h, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_health * n_ch)()
+    _check(h, lib.rx_read_health(h, arr, n_ch), lib.rx_last_error)
+    return list(arr)
+
+
+def rx_write_health(h, health) -> None:
+    lib = load()
+    n = len(health)
+    arr = (rx_channel_health * n)(*health)
+    _check(h, lib.rx_write_health(h, arr, n), lib.rx_last_error)
 
 
 def rx_last_error(h) -> str:

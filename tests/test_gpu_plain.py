@@ -189,3 +189,69 @@ def test_invalid_arguments_rejected():
         assert e.value.status == rx.RX_ESTATE
     finally:
         rx.rx_destroy(h)
+
+
+def _health_equal(gpu, ext):
+    for i, (g, o) in enumerate(zip(gpu, ext)):
+        assert g.cn0_hz == o.cn0_hz and g.lock_ratio == o.lock_ratio, (i, g.cn0_hz, o.cn0_hz)
+        assert g.lock_fail_count == o.lock_fail and g.window_count == o.window_count, i
+        assert (g.sum_abs_ip, g.sum_power, g.sum_diff) == (o.sum_abs_ip, o.sum_power, o.sum_diff), i
+        assert g.dll_integrator_hz == o.dll_u, (i, g.dll_integrator_hz, o.dll_u)
+        assert (g.prev_ip, g.prev_qp, g.have_prev) == (o.prev_ip, o.prev_qp, o.have_prev), i
+
+
+def test_table3_loops_and_health_bit_exact_with_checkpoint():
+    """Table 3's full loop set (FLL-assisted PLL, 2nd-order DLL) with the health
+    indicators, from 60 Hz beyond the acquisition error: accumulators, words, loop state
+    and health match the oracle bit for bit; a checkpoint at block 97 (mid window)
+    restored into a fresh handle continues identically."""
+    r = synth.single_receiver(n_blocks=200)
+    iq = synth.generate_iq(r).numpy()
+    prn, w, phi, rate, taps = synth.channel_arrays(r)
+    w = (w.astype(np.int64) + int(round(60.0 / r.fs * 2**32))).astype(np.int32)
+    chans = [oracle.chan_init(int(w[i]), int(phi[i]), int(rate[i]), r.fs) for i in range(len(prn))]
+    dumps, ostate, oext = oracle.run_receiver_table3(iq, r.n_blocks, r.block_samples, r.fs, prn, taps, 1,
+                                                     r.tap_early, r.tap_prompt, r.tap_late, r.pll_bn,
+                                                     r.dll_bn, 10.0, 20, chans)
+    N = r.block_samples
+
+    def handle():
+        return rx.rx_create(r.fs, N, 8, 3, r.pll_bn, r.dll_bn, r.tap_early, r.tap_prompt, r.tap_late,
+                            device=0, loop_set=rx.RX_LOOPS_TABLE3, health_window=20, fll_bn_hz=10.0)
+
+    dev = torch.from_numpy(iq).cuda()
+    gpu = []
+    h1 = handle()
+    try:
+        rx.rx_set_channels(h1, prn, w, phi, rate, taps)
+        for b in range(97):
+            rx.rx_correlate(h1, dev[b * N:(b + 1) * N], N)
+            gpu.append(rx.rx_read_accumulators(h1, 8, 3))
+            rx.rx_track_epoch(h1)
+        saved = (rx.rx_read_state(h1, 8), rx.rx_read_health(h1, 8))
+    finally:
+        rx.rx_destroy(h1)
+    h2 = handle()
+    try:
+        rx.rx_set_channels(h2, prn, w, phi, rate, taps)
+        rx.rx_write_state(h2, saved[0])
+        rx.rx_write_health(h2, saved[1])
+        for b in range(97, r.n_blocks):
+            rx.rx_correlate(h2, dev[b * N:(b + 1) * N], N)
+            gpu.append(rx.rx_read_accumulators(h2, 8, 3))
+            rx.rx_track_epoch(h2)
+        st = rx.rx_read_state(h2, 8)
+        hl = rx.rx_read_health(h2, 8)
+    finally:
+        rx.rx_destroy(h2)
+    assert np.array_equal(np.stack(gpu), dumps)
+    assert_states_equal(st, ostate)
+    _health_equal(hl, oext)
+    assert all(x.cn0_hz > 0 for x in hl)
+
+
+def test_table3_config_rejected_when_invalid():
+    with pytest.raises(rx.RxError):
+        rx.rx_create(4.092e6, 4092, 4, 3, device=0, loop_set=2)
+    with pytest.raises(rx.RxError):
+        rx.rx_create(4.092e6, 4092, 4, 3, device=0, loop_set=1, fll_bn_hz=-1.0)
