@@ -18,9 +18,10 @@
 //     its own copy of the channel's NCO and loop state.  Every copy applies the same
 //     integer sums to the same FP64 sequence, so all copies stay bit-identical; part 0's
 //     CTA owns the channel: it writes the dumps and the final state.
-// No CTA waits for another CTA's loop update, only for partial sums that are published
-// early in each block: the cut segments come first in every CTA's order, whole
-// channels after.  Inside a CTA the hand-off between correlation warps and filter warps
+// No CTA waits for another CTA's loop update, only for partial sums.  The cut segments
+// come last in every CTA's block, so the exchange of a block's sums has nearly a whole
+// block of slack before the next block needs the loops closed, and a CTA that waits
+// leaves its SM to the other CTAs there.  Inside a CTA the hand-off between correlation warps and filter warps
 // is the pipelined schedule's (full/ready mbarriers per segment); filter warps for cut
 // segments are separate from those for whole channels.  The launch is cooperative:
 // CTAs wait on one another, so all must be resident.  Every wait is bounded and
@@ -70,8 +71,38 @@ __global__ void __launch_bounds__(NT + 32 * bal_filter_warps<NT>(), bal_min_bloc
     volatile uint32_t *s_abort = reinterpret_cast<uint32_t *>(s_dumps + ms);
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nthreads = blockDim.x;
-    const uint32_t nseg = a.nseg[blockIdx.x];
-    const SegDesc *segs = a.segs + (size_t)blockIdx.x * ms;
+    // The work is laid out per SM (group g, slot s): the CTA takes the next slot of the
+    // SM it runs on; the first CTA on an SM draws the SM's group.  Exactly k CTAs are
+    // resident on every SM, so every (group, slot) is taken once.
+    __shared__ uint32_t s_work;
+    if (tid == 0) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        uint32_t work = 0xffffffffu;
+        if (smid < 1024) {
+            const uint32_t slot = atomicAdd(a.sm_map + 1024 + smid, 1u);
+            uint32_t g1 = 0;
+            if (slot == 0) {
+                g1 = atomicAdd(a.next_group, 1u) + 1;
+                st_release(a.sm_map + smid, g1);
+            } else {
+                const uint64_t t0 = globaltimer_ns();
+                for (uint32_t it = 0; it < (1u << 24) && (g1 = ld_acquire(a.sm_map + smid)) == 0; ++it)
+                    if (globaltimer_ns() - t0 > a.timeout_ns) break;
+            }
+            if (g1 != 0 && g1 <= a.n_groups && slot < a.k) work = (g1 - 1) * a.k + slot;
+        }
+        if (work == 0xffffffffu && atomicCAS(a.err, 0u, 1u) == 0u) {
+            a.err[1] = 0xfffffffdu;
+            a.err[2] = blockIdx.x;
+            a.err[3] = smid;
+        }
+        s_work = work;
+    }
+    __syncthreads();
+    const uint32_t work = s_work;
+    const uint32_t nseg = work == 0xffffffffu ? 0u : a.nseg[work];
+    const SegDesc *segs = a.segs + (size_t)(work == 0xffffffffu ? 0u : work) * ms;
 
     for (uint32_t i = tid; i < 64; i += nthreads) sm.tab[i] = a.tb.carrier[i];
     for (uint32_t s = tid; s < nseg; s += nthreads) {
@@ -192,23 +223,35 @@ __global__ void __launch_bounds__(NT + 32 * bal_filter_warps<NT>(), bal_min_bloc
             }
         }
     } else {
-        // filter warps.  Segments are ordered cut channels, then whole channels.  With
-        // FW >= 2, warps 0 .. FC-1 take the cut segments (one each, in turn) and the
-        // others the whole channels; with FW == 1 the one warp takes them all.
+        // filter warps.  Segments are ordered whole channels, then cut channels.  With
+        // FW >= 2, warps 0 .. FC-1 take the cut segments (in turn) and the others the
+        // whole channels (in turn); with FW == 1 the one warp takes them all, whole first.
         constexpr uint32_t FW = bal_filter_warps<NT>();
         const uint32_t f = warp - NT / 32;
-        uint32_t n_cut = 0;
-        while (n_cut < nseg && ss[n_cut].nparts > 1) ++n_cut;
-        const uint32_t FC = FW == 1 ? 1u : (FW + 1) / 2;        // warps on cut segments
+        uint32_t n_whole = 0;
+        while (n_whole < nseg && ss[n_whole].nparts == 1) ++n_whole;
+        const uint32_t n_cut = nseg - n_whole;
+        // warps on cut segments: one per cut segment, up to half of them, and none
+        // without cut segments (then every filter warp takes whole channels)
+        const uint32_t FC = FW == 1 ? 1u : (n_cut == 0 ? 0u : (n_cut < FW / 2 ? n_cut : FW / 2));
         const bool on_cut = FW == 1 || f < FC;
-        const uint32_t c0 = FW == 1 ? 0u : f, cstep = FW == 1 ? 1u : FC;
-        const uint32_t w0 = FW == 1 ? n_cut : n_cut + (f - FC), wstep = FW == 1 ? 1u : FW - FC;
+        const uint32_t c0 = n_whole + (FW == 1 ? 0u : f), cstep = FW == 1 ? 1u : (FC ? FC : 1u);
+        const uint32_t w0 = FW == 1 ? 0u : f - FC, wstep = FW == 1 ? 1u : FW - FC;
         bool ok = true;
         for (uint32_t b = 0; b < a.n_blocks && ok; ++b) {
+            if (FW == 1 || !on_cut) {
+                for (uint32_t s = w0; s < n_whole && ok; s += wstep) {
+                    if (!pipe_wait(full + s, b & 1u, s_abort, a.err, a.timeout_ns, b)) {
+                        ok = false;
+                        break;
+                    }
+                    close_loops(s, ss[s], true);
+                }
+            }
             if (on_cut) {
                 // publish this CTA's part of each cut channel first, so that no update waits
                 // behind another CTA's update
-                for (uint32_t s = c0; s < n_cut && ok; s += cstep) {
+                for (uint32_t s = c0; s < nseg && ok; s += cstep) {
                     if (!pipe_wait(full + s, b & 1u, s_abort, a.err, a.timeout_ns, b)) {
                         ok = false;
                         break;
@@ -224,7 +267,7 @@ __global__ void __launch_bounds__(NT + 32 * bal_filter_warps<NT>(), bal_min_bloc
                     }
                 }
                 // then every part's sums: each CTA holding a part closes the loops itself
-                for (uint32_t s = c0; s < n_cut && ok; s += cstep) {
+                for (uint32_t s = c0; s < nseg && ok; s += cstep) {
                     const SegSmall q = ss[s];
                     bool got = true;
                     for (uint32_t k = lane; k < q.nparts; k += 32)
@@ -246,15 +289,6 @@ __global__ void __launch_bounds__(NT + 32 * bal_filter_warps<NT>(), bal_min_bloc
                     }
                     __syncwarp();
                     close_loops(s, q, q.part == 0);
-                }
-            }
-            if (FW == 1 || !on_cut) {
-                for (uint32_t s = w0; s < nseg && ok; s += wstep) {
-                    if (!pipe_wait(full + s, b & 1u, s_abort, a.err, a.timeout_ns, b)) {
-                        ok = false;
-                        break;
-                    }
-                    close_loops(s, ss[s], true);
                 }
             }
         }

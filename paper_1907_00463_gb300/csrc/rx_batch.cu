@@ -251,7 +251,9 @@ struct rx_batch_s {
     uint32_t *d_nseg = nullptr;
     int32_t *d_xpart = nullptr;
     uint32_t *d_xflag = nullptr;    // [slots]
-    uint32_t n_slots = 0, bal_maxseg = 0;
+    uint32_t *d_smmap = nullptr;    // per %smid: group + 1, next slot; then the group counter
+    uint32_t n_slots = 0, bal_maxseg = 0, bal_groups = 0;
+    size_t bal_smem = 0;
     std::string err;
 };
 
@@ -397,70 +399,112 @@ rx_status build_balanced(rx_batch b) {
         }
     }
     uint32_t per_sm = b->ctas_per_sm ? b->ctas_per_sm : bal_default_per_sm(b->threads);
+    int smem_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, b->device);
+    // The work is balanced per SM: each SM group (one per SM) gets an equal share of
+    // the cost, laid over its k CTAs.
+    const uint32_t G = sms;
+    // 1) every group takes whole channels, in order, while they fit its share;
+    // 2) the channels left over are cut into pieces that fill each group's remaining
+    //    share, in group order, so that cut channels are few and their pieces small.
+    struct Seg {
+        uint32_t k, jbeg, jend, grp;
+    };
+    std::vector<Seg> segs;
+    const double share = (double)total / G;
+    std::vector<double> load(G, 0.0);
+    size_t k = 0;
+    for (uint32_t p = 0; p < G && k < ch.size(); ++p) {
+        while (k < ch.size() && load[p] + (double)(ch[k].cost * ch[k].nchunks) <= share) {
+            segs.push_back({(uint32_t)k, 0u, ch[k].nchunks, p});
+            load[p] += (double)(ch[k].cost * ch[k].nchunks);
+            ++k;
+        }
+    }
+    // 2) the channels left over: each is cut into a few equal pieces (two, or more when
+    //    few groups would otherwise take them), each piece to the least loaded group that
+    //    holds no other piece, so that the groups coupled through a cut channel are few,
+    //    small and independent of one another
+    const size_t n_left = ch.size() - k;
+    if (n_left) {
+        const uint32_t pieces = (uint32_t)std::max<size_t>(2, std::min<size_t>(G / std::max<size_t>(n_left, 1), 2));
+        std::vector<uint8_t> has_piece(G, 0);
+        for (; k < ch.size(); ++k) {
+            const Chan &x = ch[k];
+            const uint32_t np = std::min<uint32_t>(pieces, x.nchunks);
+            for (uint32_t q = 0; q < np; ++q) {
+                const uint32_t jb = (uint32_t)((uint64_t)x.nchunks * q / np);
+                const uint32_t je = (uint32_t)((uint64_t)x.nchunks * (q + 1) / np);
+                // least loaded group without a piece, else least loaded group
+                uint32_t best = G;
+                for (int pass = 0; pass < 2 && best == G; ++pass) {
+                    double bl = 0.0;
+                    for (uint32_t p = 0; p < G; ++p) {
+                        if (pass == 0 && has_piece[p]) continue;
+                        if (best == G || load[p] < bl) {
+                            bl = load[p];
+                            best = p;
+                        }
+                    }
+                }
+                segs.push_back({(uint32_t)k, jb, je, best});
+                load[best] += (double)(je - jb) * (double)x.cost;
+                has_piece[best] = 1;
+            }
+        }
+    }
+    (void)chunks;
+    // parts per channel, in group order; one exchange slot per part of a cut channel
+    std::vector<uint32_t> nparts(ch.size(), 0), slot0(ch.size(), 0);
+    for (const Seg &g : segs) ++nparts[g.k];
+    uint32_t slots = 0;
+    for (size_t c = 0; c < ch.size(); ++c) {
+        slot0[c] = slots;
+        if (nparts[c] > 1) slots += nparts[c];
+    }
+    std::vector<std::vector<SegDesc>> per_grp(G);
+    std::vector<std::vector<double>> seg_cost(G);
+    std::vector<uint32_t> seen(ch.size(), 0);
+    for (const Seg &g : segs) {
+        SegDesc d{};
+        const Chan &x = ch[g.k];
+        d.g = make_group(b, x.r, x.c, 1);
+        d.jbeg = g.jbeg;
+        d.jend = g.jend;
+        d.part = seen[g.k]++;
+        d.nparts = nparts[g.k];
+        d.chan = b->rx_ch0[x.r] + x.c;
+        d.slot0 = slot0[g.k];
+        per_grp[g.grp].push_back(d);
+        seg_cost[g.grp].push_back((double)(g.jend - g.jbeg) * (double)x.cost);
+    }
     for (;; --per_sm) {
         if (per_sm == 0) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
-        const uint32_t P = (uint32_t)std::min<uint64_t>((uint64_t)per_sm * sms, chunks);
-        // 1) every CTA takes whole channels, in order, while they fit its share;
-        // 2) the channels left over are cut into pieces that fill each CTA's remaining
-        //    share, in CTA order, so that cut channels are few and their pieces small.
-        struct Seg {
-            uint32_t k, jbeg, jend, cta;
-        };
-        std::vector<Seg> segs;
-        const double share = (double)total / P;
-        std::vector<double> load(P, 0.0);
-        size_t k = 0;
-        for (uint32_t p = 0; p < P && k < ch.size(); ++p) {
-            while (k < ch.size() && load[p] + (double)(ch[k].cost * ch[k].nchunks) <= share) {
-                segs.push_back({(uint32_t)k, 0u, ch[k].nchunks, p});
-                load[p] += (double)(ch[k].cost * ch[k].nchunks);
-                ++k;
-            }
-        }
-        uint32_t j = 0;
-        for (uint32_t p = 0; p < P && k < ch.size(); ++p) {
-            const bool last = p + 1 == P;
-            while (k < ch.size() && (last || load[p] < share)) {
-                const Chan &x = ch[k];
-                uint64_t take = last ? (uint64_t)(x.nchunks - j)
-                                     : (uint64_t)std::ceil((share - load[p]) / (double)x.cost);
-                take = std::max<uint64_t>(1, std::min<uint64_t>(take, x.nchunks - j));
-                segs.push_back({(uint32_t)k, j, (uint32_t)(j + take), p});
-                j += (uint32_t)take;
-                load[p] += (double)(take * x.cost);
-                if (j == x.nchunks) {
-                    ++k;
-                    j = 0;
-                }
-            }
-        }
-        // parts per channel, in CTA order; one exchange slot per part of a cut channel
-        std::vector<uint32_t> nparts(ch.size(), 0), slot0(ch.size(), 0);
-        for (const Seg &g : segs) ++nparts[g.k];
-        uint32_t slots = 0;
-        for (size_t c = 0; c < ch.size(); ++c) {
-            slot0[c] = slots;
-            if (nparts[c] > 1) slots += nparts[c];
-        }
+        // lay each group's segments over its per_sm slots: whole channels longest first onto
+        // the least loaded slot, then the cut pieces
+        const uint32_t P = G * per_sm;
         std::vector<std::vector<SegDesc>> per_cta(P);
-        std::vector<uint32_t> seen(ch.size(), 0);
-        for (const Seg &g : segs) {
-            SegDesc d{};
-            const Chan &x = ch[g.k];
-            d.g = make_group(b, x.r, x.c, 1);
-            d.jbeg = g.jbeg;
-            d.jend = g.jend;
-            d.part = seen[g.k]++;
-            d.nparts = nparts[g.k];
-            d.chan = b->rx_ch0[x.r] + x.c;
-            d.slot0 = slot0[g.k];
-            per_cta[g.cta].push_back(d);
+        for (uint32_t g = 0; g < G; ++g) {
+            std::vector<size_t> order(per_grp[g].size());
+            for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+                const bool cx = per_grp[g][x].nparts > 1, cy = per_grp[g][y].nparts > 1;
+                if (cx != cy) return !cx;
+                return seg_cost[g][x] > seg_cost[g][y];
+            });
+            std::vector<double> sl(per_sm, 0.0);
+            for (size_t i : order) {
+                const uint32_t t = (uint32_t)(std::min_element(sl.begin(), sl.end()) - sl.begin());
+                sl[t] += seg_cost[g][i];
+                per_cta[(size_t)g * per_sm + t].push_back(per_grp[g][i]);
+            }
         }
         uint32_t maxseg = 1;
         for (auto &v : per_cta) {
-            // cut channels first, whole channels after
+            // whole channels first, cut channels last
             std::stable_sort(v.begin(), v.end(),
-                             [](const SegDesc &x, const SegDesc &y) { return (x.nparts > 1) > (y.nparts > 1); });
+                             [](const SegDesc &x, const SegDesc &y) { return (x.nparts > 1) < (y.nparts > 1); });
             maxseg = std::max<uint32_t>(maxseg, (uint32_t)v.size());
         }
         if (b->cpg && b->cpg < maxseg)
@@ -468,10 +512,19 @@ rx_status build_balanced(rx_batch b) {
                         rxh::fmt("balanced schedule needs %u segments per CTA (channels_per_item %u)", maxseg,
                                  b->cpg));
         if (b->cpg) maxseg = b->cpg;
-        const size_t smem = bal_smem_bytes(maxseg, b->max_taps, b->threads);
+        // shared memory: what the CTA needs, and at least enough that a (k+1)-th CTA
+        // cannot fit an SM, so that exactly k are resident on every SM
+        size_t smem = bal_smem_bytes(maxseg, b->max_taps, b->threads);
+        if (smem_sm > 0) {
+            const size_t guard = (size_t)smem_sm / (per_sm + 1) + 16 - std::min<size_t>(reserved, 1024);
+            smem = std::max(smem, (guard + 15) / 16 * 16);
+        }
         const int occ = bal_occupancy(b->threads, smem);
-        if (occ < (int)per_sm) {
-            if (b->ctas_per_sm) return berr(b, RX_EINVAL, "tile shape does not fit on an SM");
+        if (occ != (int)per_sm) {
+            if (b->ctas_per_sm)
+                return berr(b, RX_EINVAL,
+                            rxh::fmt("tile shape does not fit on an SM (%u CTAs of %zu bytes, %d fit)", per_sm,
+                                     smem, occ));
             continue;
         }
         std::vector<SegDesc> flat((size_t)P * maxseg);
@@ -480,21 +533,25 @@ rx_status build_balanced(rx_batch b) {
             nseg[p] = (uint32_t)per_cta[p].size();
             std::copy(per_cta[p].begin(), per_cta[p].end(), flat.begin() + (size_t)p * maxseg);
         }
-        void *old[] = {b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag};
+        void *old[] = {b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag, b->d_smmap};
         for (void *q : old)
             if (q) cudaFree(q);
         b->d_segs = nullptr;
         b->d_nseg = nullptr;
         b->d_xpart = nullptr;
         b->d_xflag = nullptr;
+        b->d_smmap = nullptr;
         RX_CUDA_TRY(cudaMalloc(&b->d_segs, flat.size() * sizeof(SegDesc)), E);
         RX_CUDA_TRY(cudaMemcpy(b->d_segs, flat.data(), flat.size() * sizeof(SegDesc), cudaMemcpyHostToDevice), E);
         RX_CUDA_TRY(cudaMalloc(&b->d_nseg, (size_t)P * 4), E);
         RX_CUDA_TRY(cudaMemcpy(b->d_nseg, nseg.data(), (size_t)P * 4, cudaMemcpyHostToDevice), E);
         RX_CUDA_TRY(cudaMalloc(&b->d_xpart, std::max<size_t>(1, (size_t)slots * 2 * b->max_taps * 2) * 4), E);
         RX_CUDA_TRY(cudaMalloc(&b->d_xflag, std::max<size_t>(1, slots) * 4), E);
+        RX_CUDA_TRY(cudaMalloc(&b->d_smmap, (2 * 1024 + 1) * 4), E);
         b->n_slots = slots;
         b->bal_maxseg = maxseg;
+        b->bal_smem = smem;
+        b->bal_groups = G;
         b->ctas_per_sm = per_sm;
         b->G = P;
         b->grid = P;
@@ -591,10 +648,11 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     rx_status s;
     if (b->schedule == RX_SCHED_BALANCED) {
         RX_CUDA_TRY(cudaMemsetAsync(b->d_xflag, 0, std::max<size_t>(1, b->n_slots) * 4, b->stream), E);
-        BalArgs la{b->d_segs,   b->d_nseg,     b->d_rxoff,    iq,         ba.tb,   b->d_xpart,
-                   b->d_xflag,  ba.err,        b->timeout_ns, n_blocks,   b->bal_maxseg, b->max_taps};
-        cudaError_t ce = bal_launch(b->threads, b->grid, bal_smem_bytes(b->bal_maxseg, b->max_taps, b->threads),
-                                    b->stream, la);
+        RX_CUDA_TRY(cudaMemsetAsync(b->d_smmap, 0, (2 * 1024 + 1) * 4, b->stream), E);
+        BalArgs la{b->d_segs,   b->d_nseg,      b->d_rxoff,      iq,         ba.tb,          b->d_xpart,
+                   b->d_xflag,  ba.err,         b->timeout_ns,   n_blocks,   b->bal_maxseg,  b->max_taps,
+                   b->ctas_per_sm, b->bal_groups, b->d_smmap,   b->d_smmap + 2 * 1024};
+        cudaError_t ce = bal_launch(b->threads, b->grid, b->bal_smem, b->stream, la);
         if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(ce)));
         RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
         return RX_OK;
@@ -748,7 +806,7 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     void *ptrs[] = {b->d_state, b->d_snap, b->d_prn,   b->d_taps, b->d_dumps, b->d_groups, b->d_rxoff,
-                    b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag};
+                    b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag, b->d_smmap};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_err) cudaFreeHost(b->h_err);

@@ -420,8 +420,8 @@ struct SegDesc {
 };
 
 struct BalArgs {
-    const SegDesc *segs;       // [grid][maxseg]
-    const uint32_t *nseg;      // [grid]
+    const SegDesc *segs;       // [groups * k][maxseg]: work of slot s of SM group g at g * k + s
+    const uint32_t *nseg;      // [groups * k]
     const uint64_t *src_off;
     const int8_t *iq;
     Tables tb;
@@ -432,6 +432,10 @@ struct BalArgs {
     uint32_t n_blocks;
     uint32_t maxseg;
     uint32_t max_taps;
+    uint32_t k;                // CTAs per SM (exactly k are resident on every SM)
+    uint32_t n_groups;         // SM groups = SMs
+    uint32_t *sm_map;          // [2 * 1024]: per %smid, group + 1 and the next slot; zeroed per run
+    uint32_t *next_group;      // zeroed per run
 };
 
 size_t bal_smem_bytes(uint32_t maxseg, uint32_t mt, uint32_t nt);
