@@ -45,7 +45,9 @@ N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 # times that case).  Keyed by (schedule, correlating threads, channels per item).  An
 # entry is removed whenever its kernel changes and restored from a new capture.
 PROFILED = {
-    ("static", 128, 1): {"bytes_per_rx_block": 33983, "thread_inst_per_sample_channel": 19.7,
+    ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
+                            "capture": "profiles/k_batch_pipe224_uniform_64rx_100blk.md"},
+    ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
                          "capture": "profiles/k_batch_static128_uniform_64rx_100blk.md"},
 }
 METRIC = "Msample*channel/s correlated"
@@ -462,7 +464,7 @@ def run_ours(args):
     rx.rx_batch_destroy(b)
 
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
-    sched_name = ["dynamic", "static", "pipelined"][tiles[3]]
+    sched_name = ["dynamic", "static", "pipelined", "balanced"][tiles[3]]
     prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
     traffic = prof["bytes_per_rx_block"] * len(receivers) * n_blocks if prof else None
     executed = None
