@@ -5,7 +5,7 @@ benchmark's CPU-baseline leg.  The product package never imports it, and it
 never imports the product package.
 
 Every function here is argument marshalling around the C functions; the
-arithmetic, and its citations (Sec. 3.1 Eq. 1 and Fig. 7, Table 3, Sec. 4),
+arithmetic, and its citations (Sec. 3.1 Eq. 1 and Fig. 7, Table 3, Sec. 3.3, 3.6, 3.7, Sec. 4),
 live in oracle.c.
 """
 from __future__ import annotations
@@ -61,6 +61,19 @@ class OrcExt(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class OrcAcqResult(C.Structure):
+    """One PRN's acquisition result (mirrors orc_acq_result in oracle.c)."""
+    _fields_ = [
+        ("peak", C.c_uint64),
+        ("second", C.c_uint64),
+        ("dopp_bin", C.c_uint32),
+        ("code_phase", C.c_uint32),
+    ]
+
+    def as_tuple(self) -> tuple:
+        return (self.peak, self.second, self.dopp_bin, self.code_phase)
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -102,6 +115,12 @@ def lib():
                                               C.c_double, C.c_double, C.c_double, C.c_uint32,
                                               C.POINTER(OrcChan), C.POINTER(OrcExt), P]
         L.orc_run_receiver_table3.restype = C.c_int
+        L.orc_acquire.argtypes = [P, C.c_uint32, C.c_uint32, C.c_int, C.c_uint32, P, C.c_uint64,
+                                  P, C.POINTER(OrcAcqResult)]
+        L.orc_acquire.restype = C.c_int
+        L.orc_acq_handoff.argtypes = [C.c_int32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
+                                      C.c_double, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+        L.orc_acq_handoff.restype = None
         _lib = L
     return _lib
 
@@ -253,3 +272,31 @@ def run_receiver_table3(iq: np.ndarray, n_blocks: int, N: int, fs: float, prn, t
         raise ValueError("orc_run_receiver_table3 rejected its arguments")
     return (dumps, [OrcChan.from_buffer_copy(arr[i]) for i in range(n_ch)],
             [OrcExt.from_buffer_copy(ext[i]) for i in range(n_ch)])
+
+
+def acquire(iq: np.ndarray, N: int, n_ms: int, prn: int, carrier_words, r0: int,
+            want_grid: bool = False):
+    """Acquisition search of one PRN over an n_ms-block buffer.
+
+    iq: at least n_ms * N complex int8 samples.  Returns (OrcAcqResult, grid)
+    with grid uint64 [n_dopp, N] (S of every cell) or None.
+    """
+    iq = np.ascontiguousarray(iq, dtype=np.int8).reshape(-1)
+    assert iq.size >= 2 * N * n_ms
+    w = np.ascontiguousarray(carrier_words, dtype=np.int32).reshape(-1)
+    grid = np.zeros((w.size, N), np.uint64) if want_grid else None
+    res = OrcAcqResult()
+    rc = lib().orc_acquire(_ptr(iq), N, n_ms, int(prn), w.size, _ptr(w), int(r0),
+                           _ptr(grid) if grid is not None else None, C.byref(res))
+    if rc != 0:
+        raise ValueError("orc_acquire: bad arguments")
+    return res, grid
+
+
+def acq_handoff(w: int, code_phase: int, N: int, n_ms: int, r0: int, fs: float):
+    """(phi, r): tracking code phase at the first sample after the buffer, code rate word."""
+    phi = C.c_uint64()
+    r = C.c_uint64()
+    lib().orc_acq_handoff(int(w), int(code_phase), int(N), int(n_ms), int(r0), float(fs),
+                          C.byref(phi), C.byref(r))
+    return phi.value, r.value

@@ -21,7 +21,13 @@
  *     2nd-order PLL and a 1st-order DLL, followed by re-quantisation of the
  *     NCO words; and Table 3's full set (2nd-order PLL with a 1st-order atan2
  *     FLL assist, 2nd-order DLL) with Sec. 4's channel-health indicators
- *     (C/N0, carrier lock ratio, lock-fail count).  Every floating-point step is a single correctly rounded
+ *     (C/N0, carrier lock ratio, lock-fail count).
+ *   - the acquisition search of Sec. 3.3 / 3.6 / 3.7: for each PRN, the power
+ *     of the circular correlation of the carrier-wiped buffer with the local
+ *     code over a grid of Doppler bins and all code delays (the quantity a
+ *     parallel-code-phase FFT search computes), its peak, the second peak of
+ *     the peak's Doppler row, and the hand-over of the result to tracking.
+ *   Every floating-point step is a single correctly rounded
  *     IEEE-754 binary64 operation, written one per statement, in a fixed
  *     order; the file must be compiled with -ffp-contract=off.
  *
@@ -623,4 +629,141 @@ static int orc_run(const int8_t *iq, uint32_t n_blocks, uint32_t N, double fs,
     free(codes);
     free(acc);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Acquisition search (Sec. 3.3 ACQ module, Sec. 3.6 outputs, Sec. 3.7)     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t peak;       /* S at the best cell */
+    uint64_t second;     /* best S in the best cell's Doppler row, more than a chip away */
+    uint32_t dopp_bin;   /* Doppler bin of the best cell */
+    uint32_t code_phase; /* code delay of the best cell, samples, 0..N-1 */
+} orc_acq_result;
+
+/*
+ * Search one PRN over n_dopp Doppler bins (carrier words w[d]) and every code
+ * delay of an acquisition buffer of n_ms blocks of N samples: the ACQ
+ * module's buffer of Sec. 3.3, filled for the configured integration length,
+ * and the outputs of Sec. 3.6 (PRN, acquisition ratio, coarse Doppler, code
+ * delay).  The parallel-code-phase search of Sec. 3.7 evaluates with FFTs the
+ * circular correlation of each carrier-wiped block with the local code at all
+ * delays at once; here that correlation is written out by its definition, one
+ * delay at a time:
+ *
+ *   g[k]   = code[((k r0) mod 1023*2^32) >> 32],  k = 0..N-1
+ *            (the local code sampled from phase 0 with code rate word r0)
+ *   theta  = (m N + k) w[d]                       (mod 2^32, 0 at the buffer start)
+ *   (c, s) = TAB[theta >> 26]
+ *   I'[k]  = I c + Q s,  Q'[k] = Q c - I s        (sample m N + k; exp(-j theta))
+ *   Z_I(c) = sum_k I'[k] g[(k - c) mod N],  Z_Q(c) likewise      (exact)
+ *   S[d][c] = sum over blocks m of Z_I(c)^2 + Z_Q(c)^2             (mod 2^64)
+ *
+ * c is the delay of the local code in samples.  The best cell is the largest
+ * S, the first in (d, c) order among equals.  With E = ceil(N / 1023) samples
+ * (one chip), second is the largest S[d_best][c] over delays whose circular
+ * distance min(|c - c_best|, N - |c - c_best|) exceeds E, or 0 if none does.
+ * grid, when not NULL, receives S as [n_dopp][N].  Returns 0, or -1 on bad
+ * arguments.
+ */
+int orc_acquire(const int8_t *iq, uint32_t N, uint32_t n_ms, int prn, uint32_t n_dopp,
+                const int32_t *w, uint64_t r0, uint64_t *grid, orc_acq_result *out) {
+    if (N == 0 || n_ms == 0 || n_dopp == 0 || !iq || !w || !out) return -1;
+    int8_t code[ORC_CODE_LEN];
+    if (orc_ca_code(prn, code) != 0) return -1;
+    int8_t ctab[64], stab[64];
+    orc_sincos_table(ctab, stab);
+
+    int8_t *g = (int8_t *)malloc(N);
+    int64_t *Ip = (int64_t *)malloc(sizeof(int64_t) * N);
+    int64_t *Qp = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint64_t *S = grid ? grid : (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n_dopp * N);
+    if (!g || !Ip || !Qp || !S) {
+        free(g); free(Ip); free(Qp);
+        if (!grid) free(S);
+        return -1;
+    }
+    for (uint32_t k = 0; k < N; ++k) {
+        uint64_t ph = (uint64_t)(((unsigned __int128)k * r0) % ORC_CODE_MOD);
+        g[k] = code[ph >> 32];
+    }
+    memset(S, 0, sizeof(uint64_t) * (size_t)n_dopp * N);
+
+    for (uint32_t d = 0; d < n_dopp; ++d) {
+        for (uint32_t m = 0; m < n_ms; ++m) {
+            const int8_t *blk = iq + (size_t)m * N * 2;
+            for (uint32_t k = 0; k < N; ++k) {
+                uint32_t n = m * N + k;                     /* sample index, mod 2^32 */
+                uint32_t theta = n * (uint32_t)w[d];
+                uint32_t t = theta >> 26;
+                int64_t c = ctab[t], s = stab[t];
+                int64_t I = blk[2 * (size_t)k], Q = blk[2 * (size_t)k + 1];
+                Ip[k] = I * c + Q * s;
+                Qp[k] = Q * c - I * s;
+            }
+            for (uint32_t c = 0; c < N; ++c) {
+                int64_t zi = 0, zq = 0;
+                for (uint32_t k = 0; k < N; ++k) {
+                    uint32_t j = k >= c ? k - c : k + N - c;
+                    zi += Ip[k] * g[j];
+                    zq += Qp[k] * g[j];
+                }
+                S[(size_t)d * N + c] += (uint64_t)(zi * zi) + (uint64_t)(zq * zq);
+            }
+        }
+    }
+
+    uint64_t best = S[0];
+    uint32_t bd = 0, bc = 0;
+    for (uint32_t d = 0; d < n_dopp; ++d)
+        for (uint32_t c = 0; c < N; ++c)
+            if (S[(size_t)d * N + c] > best) {
+                best = S[(size_t)d * N + c];
+                bd = d;
+                bc = c;
+            }
+    uint32_t E = (N + ORC_CODE_LEN - 1) / ORC_CODE_LEN;
+    uint64_t second = 0;
+    for (uint32_t c = 0; c < N; ++c) {
+        uint32_t dist = c > bc ? c - bc : bc - c;
+        if (N - dist < dist) dist = N - dist;
+        if (dist > E && S[(size_t)bd * N + c] > second) second = S[(size_t)bd * N + c];
+    }
+    out->peak = best;
+    out->second = second;
+    out->dopp_bin = bd;
+    out->code_phase = bc;
+
+    free(g); free(Ip); free(Qp);
+    if (!grid) free(S);
+    return 0;
+}
+
+/*
+ * Starting NCO words of a tracking channel from an acquisition result (the
+ * hand-over from ACQ to tracking of Sec. 3.3).  The local code delayed by c
+ * samples matched the received code, so the received code phase at buffer
+ * sample 0 is ((N - c) mod N) r0; it advances at the handed-over rate r for
+ * the n_ms N samples of the buffer.  The carrier word is the bin's; the code
+ * rate is carrier aided as in the loop update of orc_track:
+ *   f = w fs / 2^32;  f_code = 1.023e6 + f / 1540;  r = rn(f_code 2^32 / fs)
+ *   phi = ((N - c) mod N) r0 + n_ms N r               (mod 1023*2^32)
+ * phi is the code phase at the first sample after the buffer.
+ */
+void orc_acq_handoff(int32_t w, uint32_t code_phase, uint32_t N, uint32_t n_ms, uint64_t r0,
+                     double fs, uint64_t *phi, uint64_t *r) {
+    double f = (double)w * fs;
+    f = f / 4294967296.0;
+    double aid = f * ORC_KAID;
+    double f_code = 1.023e6 + aid;
+    double sfs = 4294967296.0 / fs;
+    double xr = f_code * sfs;
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    *r = (uint64_t)nearbyint(xr);
+    uint32_t lag = code_phase % N;
+    lag = lag == 0 ? 0 : N - lag;
+    unsigned __int128 p = (unsigned __int128)lag * r0 + (unsigned __int128)n_ms * N * (*r);
+    *phi = (uint64_t)(p % ORC_CODE_MOD);
 }
