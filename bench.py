@@ -16,7 +16,10 @@ end-to-end number through the C ABI with host buffers, the plain
 one-receiver-per-launch GPU form, real-time channel counts, clocks, and the
 serving leg: 512 streams at 8.184 MHz (12 channels x 5 taps) with Poisson 1 kHz
 block arrivals served by continuous batching, with p50/p99 epoch latency and the
-largest stream count that keeps p99 under the 1 ms deadline.
+largest stream count that keeps p99 under the 1 ms deadline; and the acquisition
+leg: the cold-start search of every receiver (first 1 ms, 32 PRNs x 29 Doppler bins
+x all code delays) with its own rate, roofline, end-to-end number and oracle
+baseline.
 
 --impl reference times the CPU oracle (the plain reference implementation of
 the same computation) on the host cores, on bounded samples of this workload.
@@ -333,6 +336,134 @@ def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_
             "realtime_channels_p99_under_1ms": 12 * cap, "capacity_probes": probes}
 
 
+ACQ_BINS_HZ = np.arange(-7000.0, 7001.0, 500.0)     # 29 Doppler bins: +-7 kHz at 500 Hz
+ACQ_PRNS = list(range(1, 33))
+
+
+def acq_ops_model(N: int, M: int, n_ms: int, n_rx: int, n_prn: int, n_bins: int) -> dict:
+    """INT32 operations of one search as the kernels execute it (field-transform form).
+    A butterfly is a Montgomery product (7: two 32x32 products and their high halves,
+    subtract, conditional add as add + min) plus a modular add and subtract (3 each): 13.
+    A length-M transform has M/2 log2 M butterflies.  Per (receiver, block, bin): two
+    forward transforms of the wiped rails (mix: 8 per sample).  Per (receiver, bin, PRN)
+    row: per block and rail a pointwise product (7 per element) and an inverse transform
+    whose last stage keeps half its outputs, then |Z|^2 accumulation (5 per delay)."""
+    lg = M.bit_length() - 1
+    bf = M // 2 * lg
+    fwd = n_rx * n_ms * n_bins * 2 * (13 * bf + 8 * N)
+    inv_bf = bf - M // 4
+    rows = n_rx * n_bins * n_prn * n_ms * 2 * (7 * M + 13 * inv_bf + 5 * N)
+    direct = n_rx * n_bins * n_prn * n_ms * N * (N * 4 + 8)     # 2 rails x (MAC = 2) per term
+    return {"fwd": fwd, "rows": rows, "total": fwd + rows, "direct_definition": direct}
+
+
+def acquisition_leg(rx, synth, receivers, buf, offs, dev, stream, steps, warmup, peak_tops,
+                    cpu_leg: bool) -> dict:
+    """Cold-start acquisition of every receiver of the workload: the first 1 ms block of
+    each, 32 PRNs x 29 Doppler bins x all N code delays, one rx_acq_run per step."""
+    import torch
+    N = receivers[0].block_samples
+    fs = receivers[0].fs
+    n_rx, n_prn, n_ms = len(receivers), len(ACQ_PRNS), 1
+    words = np.array([int(np.rint(f / fs * 2**32)) for f in ACQ_BINS_HZ], np.int32)
+    acq_iq = torch.empty((n_rx * N, 2), dtype=torch.int8, device=dev)
+    for i, o in enumerate(offs[:n_rx]):
+        acq_iq[i * N:(i + 1) * N] = buf[int(o):int(o) + 2 * N].view(-1, 2)
+    a = rx.rx_acq_create(fs, N, n_ms, n_rx, n_prn, len(words), device=dev.index or 0, stream=stream)
+    try:
+        rx.rx_acq_set_search(a, ACQ_PRNS, words, 0)
+        M, threads, per_pass = rx.rx_acq_get_shape(a)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+        for _ in range(warmup):
+            rx.rx_acq_run(a, acq_iq, n_rx)
+        rx.rx_acq_sync(a)
+        times = []
+        launches = 0
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rx.rx_acq_run(a, acq_iq, n_rx)
+            e1.record(stream)
+            launches += rx.rx_acq_last_launches(a)
+            rx.rx_acq_sync(a)
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        res = rx.rx_acq_read_results(a, n_rx, n_prn)
+        detected = sum(1 for row in res for x in row if x.peak > 2.5 * max(x.second, 1))
+        # end to end with host buffers: H2D of the buffers, D2H of the results, every step
+        hbuf = torch.empty((n_rx * N, 2), dtype=torch.int8, pin_memory=True)
+        hbuf.copy_(acq_iq)
+        rx.rx_acq_run(a, hbuf, n_rx)
+        rx.rx_acq_read_results(a, n_rx, n_prn)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            rx.rx_acq_run(a, hbuf, n_rx)
+            rx.rx_acq_read_results(a, n_rx, n_prn)
+        e2e_s = (time.perf_counter() - t0) / steps
+        del flush, hbuf
+    finally:
+        rx.rx_acq_destroy(a)
+    cells = n_rx * n_prn * len(words) * N * n_ms
+    ops = acq_ops_model(N, M, n_ms, n_rx, n_prn, len(words))
+    achieved = ops["total"] / (ms / 1000) / 1e12
+    out = {
+        "metric": "acquisition search cells/s (PRN x Doppler bin x code delay, 1 ms coherent)",
+        "value": cells / (ms / 1000) / 1e9, "unit": "Gcell/s", "ms_per_step": ms,
+        "steps": steps, "warmup": warmup, "dtype": "int32 (exact field transform mod 15*2^27+1)",
+        "config": {"workload": f"{n_rx} receivers x {n_prn} PRNs x {len(words)} Doppler bins "
+                               f"(+-7 kHz at 500 Hz) x {N} code delays, first 1 ms of each receiver "
+                               "of the tracking workload, fs 16.368 MHz",
+                   "transform_len": M, "threads": threads, "receivers_per_pass": per_pass,
+                   "l2": "256 MB written between steps (flush); transform scratch "
+                         f"{n_rx * len(words) * 2 * M * 4 / 1e6:.0f} MB per step"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "model": "field-transform INT32 ops of all three kernels per step "
+                              "(bench.acq_ops_model) / step time; peak derived as for tracking",
+                     "ops_per_step": ops["total"],
+                     "direct_definition_ops_per_step": ops["direct_definition"],
+                     "effective_direct_Tops": ops["direct_definition"] / (ms / 1000) / 1e12},
+        "e2e": {"value": cells / e2e_s / 1e9, "unit": "Gcell/s", "ms_per_step": e2e_s * 1000,
+                "h2d_bytes_per_step": n_rx * N * 2,
+                "d2h_bytes_per_step": n_rx * n_prn * 24},
+        "gpu_launches": launches,
+        "detected_ratio_over_2.5": detected,
+        "receivers_per_s": n_rx / (ms / 1000),
+    }
+    if cpu_leg:
+        out["cpu_baseline"] = acq_cpu_baseline(acq_iq.cpu().numpy(), N, fs, words)
+    return out
+
+
+def acq_cpu_baseline(host_iq, N: int, fs: float, words, target_s: float = 12.0) -> dict:
+    """The oracle's search on a bounded sample: (receiver, PRN) pairs over all bins, one
+    thread per pair, as many pairs as cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    r0 = int(np.rint(1.023e6 / fs * 2**32))
+    # size the bins per pair so that one pair takes about target_s
+    t0 = time.perf_counter()
+    oracle.acquire(host_iq[:N], N, 1, 1, words[:1], r0)
+    t_bin = time.perf_counter() - t0
+    nb = int(max(1, min(len(words), target_s / max(t_bin, 1e-6))))
+    pairs = [(i % (len(host_iq) // N), 1 + i % 32) for i in range(cores)]
+
+    def one(pr):
+        r, p = pr
+        oracle.acquire(host_iq[r * N:(r + 1) * N], N, 1, p, words[:nb], r0)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, pairs))
+    dt = time.perf_counter() - t0
+    cells = len(pairs) * nb * N
+    return {"value": cells / dt / 1e9, "unit": "Gcell/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pairs)} (receiver, PRN) pairs x {nb} bins x {N} delays, one oracle "
+                      f"thread per pair, {dt:.1f} s"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -463,6 +594,12 @@ def run_ours(args):
             del host_cache
     rx.rx_batch_destroy(b)
 
+    acquisition = None
+    if not args.no_acq:
+        acquisition = acquisition_leg(rx, synth, receivers[:args.acq_receivers], buf, offs, dev,
+                                      stream, args.steps, args.warmup, peak_tops,
+                                      cpu_leg=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
     sched_name = ["dynamic", "static", "pipelined", "balanced"][tiles[3]]
     prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
@@ -507,6 +644,7 @@ def run_ours(args):
                                   serving["realtime_channels_p99_under_1ms"] if serving else None},
         "serving": serving,
         "plain_form": plain,
+        "acquisition": acquisition,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -530,6 +668,9 @@ def main():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-acq", action="store_true")
+    p.add_argument("--acq-receivers", type=int, default=N_RX,
+                   help="receivers searched by the acquisition leg (default: all of the workload)")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be at least 3")

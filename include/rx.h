@@ -512,6 +512,108 @@ rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
                           const int64_t *tap_offsets, int32_t *dumps,
                           int32_t device, void *cuda_stream);
 
+/* ------------------------------------------------------------------------ */
+/* Acquisition (Sec. 3.3 ACQ module, Sec. 3.6 outputs, Sec. 3.7 PCS search) */
+/* ------------------------------------------------------------------------ */
+
+/* The ACQ module of Sec. 3.3 fills a buffer for the configured integration
+ * length and searches it; Sec. 3.6 lists what the search reports per PRN (the
+ * acquisition ratio, the coarse Doppler and the code delay); Sec. 3.7 names the
+ * method, a parallel-code-phase search by FFT.  These calls run that search for
+ * a batch of receiver buffers at once.  For each buffer (n_ms blocks of N
+ * samples), PRN p, Doppler bin d (carrier word w_d) and code delay c (samples):
+ *
+ *   g[k]    = C/A chip of p at floor(k r0 / 2^32) mod 1023, k = 0..N-1
+ *   theta   = (m N + k) w_d (mod 2^32, zero at the buffer start); (c, s) = the
+ *             64-entry carrier table of the tracking correlator at theta >> 26
+ *   I'[k] = I c + Q s,  Q'[k] = Q c - I s      (sample m N + k of the buffer)
+ *   Z(c)  = sum_k (I'[k], Q'[k]) g[(k - c) mod N]
+ *   S[d][c] = sum over blocks m of Z_I(c)^2 + Z_Q(c)^2
+ *
+ * and reduces S to the best cell (largest S, first in (d, c) order among
+ * equals) and the second peak: the largest S in the best cell's Doppler row at
+ * a circular distance of more than E = ceil(N / 1023) samples (one chip) from
+ * its delay.  The acquisition ratio of Sec. 3.6 is peak / second.
+ *
+ * All of it is exact integer arithmetic: |Z| <= 32512 N, and S stays below
+ * 2^64 for every size these calls accept.  The GPU evaluates the correlation
+ * over all delays as a convolution by a number-theoretic transform over the
+ * prime 15 * 2^27 + 1, which yields the same integers as the sum above. */
+
+#define RX_ACQ_MIN_N 1024              /* samples per block, lower limit */
+#define RX_ACQ_MAX_N 16384             /* upper limit: transform of 2^15 in shared memory */
+#define RX_ACQ_MAX_MS 16               /* blocks per buffer */
+#define RX_ACQ_MAX_RECEIVERS 4096      /* buffers per rx_acq_run call */
+#define RX_ACQ_MAX_BINS 1024           /* Doppler bins */
+
+typedef struct rx_acq_s *rx_acq;
+
+typedef struct {
+    double fs_hz;                /* sample rate, Hz (> 1.1e6) */
+    uint32_t block_samples;      /* N: samples per block (one code period at fs) */
+    uint32_t n_ms;               /* blocks per buffer, summed non-coherently */
+    uint32_t max_receivers;      /* largest n_rx of any rx_acq_run */
+    uint32_t max_prns;           /* 1..32 */
+    uint32_t max_doppler_bins;   /* 1..RX_ACQ_MAX_BINS */
+    uint32_t keep_grid;          /* nonzero: keep every cell's S for rx_acq_read_grid */
+    int32_t device;              /* CUDA device ordinal */
+    void *cuda_stream;           /* cudaStream_t for all work; NULL = default stream */
+} rx_acq_config;
+
+typedef struct {
+    uint64_t peak;               /* S at the best cell */
+    uint64_t second;             /* second peak as defined above; 0 if no delay qualifies */
+    uint32_t doppler_bin;        /* index of the best cell's carrier word */
+    uint32_t code_phase;         /* delay c of the best cell, samples, 0..N-1 */
+} rx_acq_result;
+
+/* Allocate a search handle (device memory for every buffer up to the maxima;
+ * its transform scratch covers as many receivers as fit in 1 GiB, and larger
+ * batches run in passes).  RX_EINVAL for sizes outside the limits, RX_ECUDA
+ * without a usable device, RX_ENOMEM if the allocation fails. */
+rx_status rx_acq_create(const rx_acq_config *cfg, rx_acq *out);
+rx_status rx_acq_destroy(rx_acq a);
+
+/* The search grid: n_prn PRNs (host array, 1..32 each), n_doppler carrier
+ * words (host or device array, int32, 2^-32 cycles per sample) and the local
+ * code rate word r0 (32.32 chips per sample; 0 = rn(1.023e6 / fs 2^32)).
+ * Computes the code spectra on the device; synchronous. */
+rx_status rx_acq_set_search(rx_acq a, uint32_t n_prn, const uint8_t *prn, uint32_t n_doppler,
+                            const int32_t *carrier_words, uint64_t code_rate_word);
+
+/* Search n_rx buffers: iq holds n_rx * n_ms * N complex int8 samples,
+ * interleaved I, Q, buffer after buffer (2-byte aligned).  A host pointer is
+ * copied to the device first; a device pointer is read in stream order.
+ * Returns once the work is enqueued (RX_ESTATE before rx_acq_set_search). */
+rx_status rx_acq_run(rx_acq a, const int8_t *iq, uint32_t n_rx);
+rx_status rx_acq_sync(rx_acq a);
+
+/* Results of the last run, [n_rx][n_prn] in the order given to
+ * rx_acq_set_search; cap counts entries.  Synchronises the stream. */
+rx_status rx_acq_read_results(rx_acq a, rx_acq_result *out, uint32_t cap);
+
+/* Every cell's S of the last run, [n_rx][n_prn][n_doppler][N] (keep_grid
+ * handles only, else RX_ESTATE); cap counts entries.  Synchronises. */
+rx_status rx_acq_read_grid(rx_acq a, uint64_t *out, size_t cap);
+
+/* Kernel launches of the last rx_acq_run; the transform length, threads per
+ * block and receivers per pass the handle uses. */
+uint32_t rx_acq_last_launches(rx_acq a);
+rx_status rx_acq_get_shape(rx_acq a, uint32_t *transform_len, uint32_t *threads,
+                           uint32_t *receivers_per_pass);
+const char *rx_acq_last_error(rx_acq a);
+
+/* Hand-over from a search result to a tracking channel (Sec. 3.3: tracking
+ * starts on the coarsely found channels).  Host arithmetic, no device work:
+ *   f = carrier_word fs / 2^32;  f_code = 1.023e6 + f / 1540
+ *   *code_rate_out   = rn(f_code 2^32 / fs)   (round half even, clamped to [0, 2^40])
+ *   *code_phase_word = ((N - c) mod N) r0 + n_ms N (*code_rate_out)  (mod 1023 2^32)
+ * i.e. the received code phase at the first sample after the buffer; the
+ * carrier word is the bin's own.  code_rate_word 0 = rn(1.023e6 / fs 2^32). */
+rx_status rx_acq_handoff(double fs_hz, uint32_t block_samples, uint32_t n_ms,
+                         uint64_t code_rate_word, int32_t carrier_word, uint32_t code_phase,
+                         uint64_t *code_phase_word, uint64_t *code_rate_out);
+
 #ifdef __cplusplus
 }
 #endif

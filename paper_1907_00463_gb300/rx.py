@@ -109,6 +109,25 @@ class rx_replay_config(C.Structure):
 
 
 # (name, restype, argtypes) for every symbol include/rx.h declares.
+class rx_acq_config(C.Structure):
+    _fields_ = [("fs_hz", C.c_double), ("block_samples", C.c_uint32), ("n_ms", C.c_uint32),
+                ("max_receivers", C.c_uint32), ("max_prns", C.c_uint32),
+                ("max_doppler_bins", C.c_uint32), ("keep_grid", C.c_uint32), ("device", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class rx_acq_result(C.Structure):
+    _fields_ = [("peak", C.c_uint64), ("second", C.c_uint64), ("doppler_bin", C.c_uint32),
+                ("code_phase", C.c_uint32)]
+
+    def as_tuple(self) -> tuple:
+        return (self.peak, self.second, self.doppler_bin, self.code_phase)
+
+
+RX_ACQ_MIN_N = 1024
+RX_ACQ_MAX_N = 16384
+RX_ACQ_MAX_MS = 16
+
 P = C.c_void_p
 SIGNATURES = [
     ("rx_status_string", C.c_char_p, [C.c_int]),
@@ -158,6 +177,19 @@ SIGNATURES = [
     ("rx_serve_last_error", C.c_char_p, [P]),
     ("rx_serve_replay", C.c_int, [P, C.POINTER(rx_replay_stream), C.c_uint32,
                                   C.POINTER(rx_replay_config), C.POINTER(C.c_uint32)]),
+    ("rx_acq_create", C.c_int, [C.POINTER(rx_acq_config), C.POINTER(P)]),
+    ("rx_acq_destroy", C.c_int, [P]),
+    ("rx_acq_set_search", C.c_int, [P, C.c_uint32, P, C.c_uint32, P, C.c_uint64]),
+    ("rx_acq_run", C.c_int, [P, P, C.c_uint32]),
+    ("rx_acq_sync", C.c_int, [P]),
+    ("rx_acq_read_results", C.c_int, [P, P, C.c_uint32]),
+    ("rx_acq_read_grid", C.c_int, [P, P, C.c_size_t]),
+    ("rx_acq_last_launches", C.c_uint32, [P]),
+    ("rx_acq_get_shape", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                   C.POINTER(C.c_uint32)]),
+    ("rx_acq_last_error", C.c_char_p, [P]),
+    ("rx_acq_handoff", C.c_int, [C.c_double, C.c_uint32, C.c_uint32, C.c_uint64, C.c_int32,
+                                 C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
 ]
 
 _lib = None
@@ -555,3 +587,85 @@ def rx_serve_replay(s, streams, rate_hz: float = 1000.0, rate_jitter: float = 0.
     _check(s, lib.rx_serve_replay(s, arr, len(streams), C.byref(cfg), ids), lib.rx_serve_last_error)
     del keep
     return list(ids)
+
+
+# ----------------------------------------------------------------------------
+# acquisition search
+# ----------------------------------------------------------------------------
+
+def rx_acq_create(fs_hz: float, block_samples: int, n_ms: int, max_receivers: int,
+                  max_prns: int = 32, max_doppler_bins: int = 64, keep_grid: bool = False,
+                  device: int = 0, stream=None):
+    lib = load()
+    cfg = rx_acq_config(fs_hz, block_samples, n_ms, max_receivers, max_prns, max_doppler_bins,
+                        1 if keep_grid else 0, device, _stream_handle(stream))
+    a = P()
+    s = lib.rx_acq_create(C.byref(cfg), C.byref(a))
+    if s != RX_OK:
+        raise RxError(s, "rx_acq_create")
+    return a
+
+
+def rx_acq_destroy(a) -> None:
+    load().rx_acq_destroy(a)
+
+
+def rx_acq_set_search(a, prn, carrier_words, code_rate_word: int = 0) -> None:
+    lib = load()
+    prn = _arr(prn, np.uint8)
+    w = _arr(carrier_words, np.int32)
+    _check(a, lib.rx_acq_set_search(a, prn.size, _ptr(prn), w.size, _ptr(w), int(code_rate_word)),
+           lib.rx_acq_last_error)
+
+
+def rx_acq_run(a, iq, n_rx: int) -> None:
+    """iq: int8 [n_rx * n_ms * N, 2], numpy (host) or torch (host or CUDA)."""
+    lib = load()
+    _check(a, lib.rx_acq_run(a, _ptr(iq), n_rx), lib.rx_acq_last_error)
+
+
+def rx_acq_sync(a) -> None:
+    lib = load()
+    _check(a, lib.rx_acq_sync(a), lib.rx_acq_last_error)
+
+
+def rx_acq_read_results(a, n_rx: int, n_prn: int) -> list:
+    """[n_rx][n_prn] rx_acq_result as nested lists."""
+    lib = load()
+    arr = (rx_acq_result * (n_rx * n_prn))()
+    _check(a, lib.rx_acq_read_results(a, arr, n_rx * n_prn), lib.rx_acq_last_error)
+    return [list(arr[r * n_prn:(r + 1) * n_prn]) for r in range(n_rx)]
+
+
+def rx_acq_read_grid(a, n_rx: int, n_prn: int, n_doppler: int, N: int) -> np.ndarray:
+    lib = load()
+    out = np.zeros((n_rx, n_prn, n_doppler, N), np.uint64)
+    _check(a, lib.rx_acq_read_grid(a, _ptr(out), out.size), lib.rx_acq_last_error)
+    return out
+
+
+def rx_acq_last_launches(a) -> int:
+    return int(load().rx_acq_last_launches(a))
+
+
+def rx_acq_get_shape(a) -> tuple:
+    lib = load()
+    m, t, c = C.c_uint32(), C.c_uint32(), C.c_uint32()
+    _check(a, lib.rx_acq_get_shape(a, C.byref(m), C.byref(t), C.byref(c)), lib.rx_acq_last_error)
+    return m.value, t.value, c.value
+
+
+def rx_acq_last_error(a) -> str:
+    return load().rx_acq_last_error(a).decode()
+
+
+def rx_acq_handoff(fs_hz: float, block_samples: int, n_ms: int, code_rate_word: int,
+                   carrier_word: int, code_phase: int) -> tuple:
+    """(code_phase_word, code_rate_word) of a tracking channel started from a result."""
+    lib = load()
+    phi, r = C.c_uint64(), C.c_uint64()
+    s = lib.rx_acq_handoff(float(fs_hz), block_samples, n_ms, int(code_rate_word), int(carrier_word),
+                           int(code_phase), C.byref(phi), C.byref(r))
+    if s != RX_OK:
+        raise RxError(s, "rx_acq_handoff")
+    return phi.value, r.value

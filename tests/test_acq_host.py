@@ -1,0 +1,35 @@
+"""Host side of the acquisition boundary (no GPU): the hand-over arithmetic of
+rx_acq_handoff against the oracle's, and no CPU fallback for the search itself."""
+import numpy as np
+import pytest
+
+import oracle
+
+TWO32 = 1 << 32
+
+
+def test_handoff_matches_the_oracle():
+    from paper_1907_00463_gb300 import rx
+    g = np.random.Generator(np.random.Philox(key=[463012, 0]))
+    for fs, N in [(2.046e6, 2046), (4.092e6, 4092), (16.368e6, 16368), (5.0e6, 5000)]:
+        r0 = int(np.rint(1.023e6 / fs * TWO32))
+        for _ in range(50):
+            w = int(g.integers(-(1 << 31), 1 << 31))
+            c = int(g.integers(0, N))
+            n_ms = int(g.integers(1, 17))
+            assert rx.rx_acq_handoff(fs, N, n_ms, r0, w, c) == oracle.acq_handoff(w, c, N, n_ms, r0, fs)
+        # r0 = 0 selects the nominal chip rate word
+        assert rx.rx_acq_handoff(fs, N, 1, 0, 0, 5) == oracle.acq_handoff(0, 5, N, 1, r0, fs)
+
+
+def test_no_cpu_fallback_for_the_search():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1907_00463_gb300 import rx
+    with pytest.raises(rx.RxError) as e:
+        rx.rx_acq_create(4.092e6, 4092, 1, 4)
+    assert e.value.status == rx.RX_ECUDA
+    with pytest.raises(rx.RxError) as e:                    # sizes are checked first
+        rx.rx_acq_create(4.092e6, 100, 1, 4)
+    assert e.value.status == rx.RX_EINVAL
