@@ -549,7 +549,7 @@ rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
 typedef struct rx_acq_s *rx_acq;
 
 typedef struct {
-    double fs_hz;                /* sample rate, Hz (> 1.1e6) */
+    double fs_hz;                /* sample rate, Hz (> 1.023e6: the code rate word stays < 2^32) */
     uint32_t block_samples;      /* N: samples per block (one code period at fs) */
     uint32_t n_ms;               /* blocks per buffer, summed non-coherently */
     uint32_t max_receivers;      /* largest n_rx of any rx_acq_run */

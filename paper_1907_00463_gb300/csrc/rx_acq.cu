@@ -498,7 +498,7 @@ extern "C" rx_status rx_acq_create(const rx_acq_config *cfg, rx_acq *out) {
     if (!cfg || !out) return RX_EINVAL;
     *out = nullptr;
     const uint32_t N = cfg->block_samples;
-    if (!(cfg->fs_hz > 1.1e6) || N < RX_ACQ_MIN_N || N > RX_ACQ_MAX_N || cfg->n_ms == 0 ||
+    if (!(cfg->fs_hz > 1.023e6) || N < RX_ACQ_MIN_N || N > RX_ACQ_MAX_N || cfg->n_ms == 0 ||
         cfg->n_ms > RX_ACQ_MAX_MS || cfg->max_receivers == 0 ||
         cfg->max_receivers > RX_ACQ_MAX_RECEIVERS || cfg->max_prns == 0 || cfg->max_prns > 32 ||
         cfg->max_doppler_bins == 0 || cfg->max_doppler_bins > RX_ACQ_MAX_BINS)

@@ -33,3 +33,19 @@ def test_no_cpu_fallback_for_the_search():
     with pytest.raises(rx.RxError) as e:                    # sizes are checked first
         rx.rx_acq_create(4.092e6, 100, 1, 4)
     assert e.value.status == rx.RX_EINVAL
+
+
+@pytest.mark.parametrize("fs,N,n_ms,ok", [
+    (1.024e6, 1024, 1, True), (1.023e6, 1024, 1, False), (16.384e6, 16384, 16, True),
+    (16.385e6, 16385, 1, False), (4.092e6, 1023, 1, False), (4.092e6, 4092, 17, False),
+    (4.092e6, 4092, 0, False)])
+def test_create_argument_limits(fs, N, n_ms, ok):
+    """Sizes within the documented limits pass validation (and then fail only for
+    want of a device here); sizes outside them are RX_EINVAL."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1907_00463_gb300 import rx
+    with pytest.raises(rx.RxError) as e:
+        rx.rx_acq_create(fs, N, n_ms, 2)
+    assert e.value.status == (rx.RX_ECUDA if ok else rx.RX_EINVAL)
