@@ -342,17 +342,18 @@ ACQ_PRNS = list(range(1, 33))
 
 def acq_ops_model(N: int, M: int, n_ms: int, n_rx: int, n_prn: int, n_bins: int) -> dict:
     """INT32 operations of one search as the kernels execute it (field-transform form).
-    A butterfly is a Montgomery product (7: two 32x32 products and their high halves,
-    subtract, conditional add as add + min) plus a modular add and subtract (3 each): 13.
-    A length-M transform has M/2 log2 M butterflies.  Per (receiver, block, bin): two
-    forward transforms of the wiped rails (mix: 8 per sample).  Per (receiver, bin, PRN)
-    row: per block and rail a pointwise product (7 per element) and an inverse transform
-    whose last stage keeps half its outputs, then |Z|^2 accumulation (5 per delay)."""
+    A butterfly with lazy reduction is 7: a product by a twiddle with a precomputed
+    quotient (one high and two low 32x32 products), the sum and difference (one add, one
+    three-input add) and one conditional subtract (add + min).  A length-M transform has
+    M/2 log2 M butterflies.  Per (receiver, block, bin): two forward transforms of the
+    wiped rails (mix: 8 per sample).  Per (receiver, bin, PRN) row: per block and rail a
+    pointwise product (3 per element) and an inverse transform whose last stage keeps
+    half its outputs, then reduction and |Z|^2 accumulation (9 per delay)."""
     lg = M.bit_length() - 1
     bf = M // 2 * lg
-    fwd = n_rx * n_ms * n_bins * 2 * (13 * bf + 8 * N)
+    fwd = n_rx * n_ms * n_bins * 2 * (7 * bf + 8 * N)
     inv_bf = bf - M // 4
-    rows = n_rx * n_bins * n_prn * n_ms * 2 * (7 * M + 13 * inv_bf + 5 * N)
+    rows = n_rx * n_bins * n_prn * n_ms * 2 * (3 * M + 7 * inv_bf + 9 * N)
     direct = n_rx * n_bins * n_prn * n_ms * N * (N * 4 + 8)     # 2 rails x (MAC = 2) per term
     return {"fwd": fwd, "rows": rows, "total": fwd + rows, "direct_definition": direct}
 

@@ -535,10 +535,11 @@ rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
  * a circular distance of more than E = ceil(N / 1023) samples (one chip) from
  * its delay.  The acquisition ratio of Sec. 3.6 is peak / second.
  *
- * All of it is exact integer arithmetic: |Z| <= 32512 N, and S stays below
- * 2^64 for every size these calls accept.  The GPU evaluates the correlation
- * over all delays as a convolution by a number-theoretic transform over the
- * prime 15 * 2^27 + 1, which yields the same integers as the sum above. */
+ * All of it is exact integer arithmetic: the carrier table's largest |c| + |s|
+ * is 180, so |I'|, |Q'| <= 23040, |Z| <= 23040 N, and S stays below 2^64 for
+ * every size these calls accept.  The GPU evaluates the correlation over all
+ * delays as a convolution by a number-theoretic transform over the prime
+ * 2^30 - 2^18 + 1, which yields the same integers as the sum above. */
 
 #define RX_ACQ_MIN_N 1024              /* samples per block, lower limit */
 #define RX_ACQ_MAX_N 16384             /* upper limit: transform of 2^15 in shared memory */

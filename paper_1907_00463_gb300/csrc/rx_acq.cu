@@ -9,7 +9,8 @@
 // number-theoretic transform of rx_ntt.cuh (length M = 2^ceil(log2 2N), so the
 // circular wrap of length N never aliases):
 //   k_acq_code   per PRN: the local code, index-reversed and wrapped into
-//                length M, forward transform, times M^-1 (Montgomery form);
+//                length M, forward transform, times M^-1, each element stored
+//                with its quotient for the pointwise product;
 //   k_acq_fwd    per (receiver, block, bin, rail): carrier wipe-off with the
 //                64-entry table (the tracking correlator's NCO), forward
 //                transform of the rail (I' or Q') padded with zeros;
@@ -39,16 +40,16 @@ constexpr int kExtBase = 256;    // bit index of chip 0 in a code-table row
 constexpr int kExtWords = 80;    // words per code-table row
 constexpr int kMinLog = 11, kMaxLog = rxn::kMaxLog;
 
-// Twiddles of the five register stages: entries 1..31 of T (0..31) and of Ti
-// (32..63).  They do not depend on the transform size; the unrolled register
-// stages read them as constant-bank operands.
-__constant__ uint32_t c_acq_tw[64];
+// Twiddles (with quotients) of the five register stages: entries 1..31 of T
+// (0..31) and of Ti (32..63).  They do not depend on the transform size; the
+// unrolled register stages read them as constant-bank operands.
+__constant__ uint2 c_acq_tw[64];
 
 struct TwF {
-    __device__ __forceinline__ uint32_t operator[](int k) const { return c_acq_tw[k]; }
+    __device__ __forceinline__ uint2 operator[](int k) const { return c_acq_tw[k]; }
 };
 struct TwI {
-    __device__ __forceinline__ uint32_t operator[](int k) const { return c_acq_tw[32 + k]; }
+    __device__ __forceinline__ uint2 operator[](int k) const { return c_acq_tw[32 + k]; }
 };
 
 struct AcqRow {
@@ -70,7 +71,7 @@ struct Shape {
 // Forward transform of the block in shared memory (all threads take part)
 // ---------------------------------------------------------------------------
 template <int LOGM>
-__device__ __forceinline__ void forward(uint32_t *s, const uint32_t *__restrict__ T) {
+__device__ __forceinline__ void forward(uint32_t *s, const uint2 *__restrict__ T) {
     constexpr uint32_t M = Shape<LOGM>::M, NT = Shape<LOGM>::NT;
     const uint32_t tid = threadIdx.x;
     int lg = LOGM - 1;
@@ -98,22 +99,14 @@ __device__ __forceinline__ void forward(uint32_t *s, const uint32_t *__restrict_
     __syncthreads();
 }
 
-// Coalesced store of the transformed block (bit-reversed order, as held).
+// Coalesced store of the transformed block (bit-reversed order, as held,
+// values in [0, 2p)).
 template <int LOGM>
-__device__ __forceinline__ void store_block(uint32_t *__restrict__ dst, const uint32_t *s,
-                                            uint32_t scale_or_zero) {
+__device__ __forceinline__ void store_block(uint32_t *__restrict__ dst, const uint32_t *s) {
     constexpr uint32_t M = Shape<LOGM>::M, NT = Shape<LOGM>::NT;
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    for (uint32_t i4 = threadIdx.x; i4 < M / 4; i4 += NT) {
-        uint4 v = *reinterpret_cast<const uint4 *>(s + rxn::pad(4 * i4));
-        if (scale_or_zero) {
-            v.x = rxn::mont(v.x, scale_or_zero);
-            v.y = rxn::mont(v.y, scale_or_zero);
-            v.z = rxn::mont(v.z, scale_or_zero);
-            v.w = rxn::mont(v.w, scale_or_zero);
-        }
-        d4[i4] = v;
-    }
+    for (uint32_t i4 = threadIdx.x; i4 < M / 4; i4 += NT)
+        d4[i4] = *reinterpret_cast<const uint4 *>(s + rxn::pad(4 * i4));
 }
 
 // ---------------------------------------------------------------------------
@@ -124,12 +117,13 @@ __device__ __forceinline__ void store_block(uint32_t *__restrict__ dst, const ui
 // h[M - j] = g[j] for 0 < j < N (zero elsewhere), g[k] = code chip at
 // floor(k r0 / 2^32) mod 1023, so that sum_k a[k] h[(c - k) mod M] is the
 // circular correlation sum_k a[k] g[(k - c) mod N] for every c < N.  Stored
-// times M^-1 (scale = M^-1 R^2 mod p, applied by a Montgomery product).
+// times M^-1 (minv = (M^-1 mod p, its quotient)), reduced to [0, p), each
+// element with its own quotient floor(h 2^32 / p).
 template <int LOGM>
 __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
-    k_acq_code(uint32_t *__restrict__ H, const uint32_t *__restrict__ code_tab,
-               const uint8_t *__restrict__ prn, uint32_t N, unsigned long long r0, uint32_t scale,
-               const uint32_t *__restrict__ T) {
+    k_acq_code(uint2 *__restrict__ H, const uint32_t *__restrict__ code_tab,
+               const uint8_t *__restrict__ prn, uint32_t N, unsigned long long r0, uint2 minv,
+               const uint2 *__restrict__ T) {
     constexpr uint32_t M = Shape<LOGM>::M, NT = Shape<LOGM>::NT;
     extern __shared__ __align__(16) uint32_t s[];
     const uint32_t *row = code_tab + (size_t)prn[blockIdx.x] * kExtWords;
@@ -154,7 +148,11 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
     }
     __syncthreads();
     forward<LOGM>(s, T);
-    store_block<LOGM>(H + (size_t)blockIdx.x * M, s, scale);
+    uint2 *h = H + (size_t)blockIdx.x * M;
+    for (uint32_t i = threadIdx.x; i < M; i += NT) {
+        uint32_t v = rxn::csub(rxn::shoup(s[rxn::pad(i)], minv), kP);
+        h[i] = make_uint2(v, (uint32_t)(((unsigned long long)v << 32) / kP));
+    }
 }
 
 // Carrier wipe-off and forward transform of one rail of one block.
@@ -163,7 +161,7 @@ template <int LOGM>
 __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
     k_acq_fwd(uint32_t *__restrict__ A, const int8_t *__restrict__ iq, const int32_t *__restrict__ words,
               const uint32_t *__restrict__ carrier_tab, uint32_t N, uint32_t n_ms, uint32_t n_dopp,
-              const uint32_t *__restrict__ T) {
+              const uint2 *__restrict__ T) {
     constexpr uint32_t M = Shape<LOGM>::M, NT = Shape<LOGM>::NT;
     extern __shared__ __align__(16) uint32_t s[];
     __shared__ uint32_t tab[64];
@@ -189,7 +187,7 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
     }
     __syncthreads();
     forward<LOGM>(s, T);
-    store_block<LOGM>(A + (size_t)blockIdx.x * M, s, 0);
+    store_block<LOGM>(A + (size_t)blockIdx.x * M, s);
 }
 
 __device__ __forceinline__ bool better(unsigned long long v, uint32_t c, unsigned long long bv,
@@ -201,8 +199,8 @@ __device__ __forceinline__ bool better(unsigned long long v, uint32_t c, unsigne
 template <int LOGM>
 __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
     k_acq_rows(AcqRow *__restrict__ rows, unsigned long long *__restrict__ grid,
-               const uint32_t *__restrict__ A, const uint32_t *__restrict__ H, uint32_t N,
-               uint32_t n_ms, uint32_t n_dopp, uint32_t n_prn, const uint32_t *__restrict__ Ti) {
+               const uint32_t *__restrict__ A, const uint2 *__restrict__ H, uint32_t N,
+               uint32_t n_ms, uint32_t n_dopp, uint32_t n_prn, const uint2 *__restrict__ Ti) {
     using SH = Shape<LOGM>;
     using LH = rxn::LastHalf<LOGM, SH::NT>;
     constexpr uint32_t M = SH::M, NT = SH::NT, SLOTS = LH::kSlots;
@@ -211,7 +209,7 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
     const uint32_t p = blockIdx.x % n_prn;
     const uint32_t d = (blockIdx.x / n_prn) % n_dopp;
     const uint32_t rx = blockIdx.x / (n_prn * n_dopp);
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(H + (size_t)p * M);
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(H + (size_t)p * M);   // two pairs each
 
     unsigned long long S[SLOTS];
 #pragma unroll
@@ -222,9 +220,11 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
             const uint4 *a4 = reinterpret_cast<const uint4 *>(
                 A + ((((size_t)rx * n_ms + m) * n_dopp + d) * 2 + rail) * M);
             for (uint32_t i4 = tid; i4 < M / 4; i4 += NT) {
-                uint4 a = a4[i4], h = h4[i4];
-                uint4 v = make_uint4(rxn::mont(a.x, h.x), rxn::mont(a.y, h.y), rxn::mont(a.z, h.z),
-                                     rxn::mont(a.w, h.w));
+                uint4 a = a4[i4], h01 = h4[2 * i4], h23 = h4[2 * i4 + 1];
+                uint4 v = make_uint4(rxn::shoup(a.x, make_uint2(h01.x, h01.y)),
+                                     rxn::shoup(a.y, make_uint2(h01.z, h01.w)),
+                                     rxn::shoup(a.z, make_uint2(h23.x, h23.y)),
+                                     rxn::shoup(a.w, make_uint2(h23.z, h23.w)));
                 *reinterpret_cast<uint4 *>(s + rxn::pad(4 * i4)) = v;
             }
             __syncthreads();
@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
                 rxn::dit_pass4(s, lgH, tid, NT, M, Ti);
                 __syncthreads();
             }
-            LH::run(s, tid, Ti, [&](uint32_t slot, uint32_t c, uint32_t r) {
-                long long z = rxn::to_signed(r);
+            LH::run(s, tid, Ti, [&](uint32_t slot, uint32_t c, int32_t zi) {
+                long long z = zi;
                 if (c < N) S[slot] += (unsigned long long)(z * z);
             });
             __syncthreads();
@@ -373,20 +373,20 @@ uint32_t powmod(uint64_t a, uint64_t e) {
     }
     return (uint32_t)r;
 }
+uint2 with_quotient(uint32_t w) { return make_uint2(w, (uint32_t)(((uint64_t)w << 32) / kP)); }
 
-// T[L + j] = w_{2L}^j R, Ti[L + j] = w_{2L}^-j R (mod p), L = 1 .. 2^14.
-void build_twiddles(std::vector<uint32_t> &T, std::vector<uint32_t> &Ti) {
+// T[L + j] = w_{2L}^j, Ti[L + j] = w_{2L}^-j (mod p) with quotients, L = 1 .. 2^14.
+void build_twiddles(std::vector<uint2> &T, std::vector<uint2> &Ti) {
     const uint32_t n = 1u << kMaxLog;
-    T.assign(n, 0);
-    Ti.assign(n, 0);
-    const uint64_t R = (1ull << 32) % kP;
+    T.assign(n, make_uint2(0, 0));
+    Ti.assign(n, make_uint2(0, 0));
     for (uint32_t L = 1; L < n; L *= 2) {
-        uint32_t w = powmod(31, (kP - 1) / (2 * L));
+        uint32_t w = powmod(rxn::kGen, (kP - 1) / (2 * L));
         uint32_t wi = powmod(w, kP - 2);
         uint64_t a = 1, b = 1;
         for (uint32_t j = 0; j < L; ++j) {
-            T[L + j] = mulmod(a, R);
-            Ti[L + j] = mulmod(b, R);
+            T[L + j] = with_quotient((uint32_t)a);
+            Ti[L + j] = with_quotient((uint32_t)b);
             a = a * w % kP;
             b = b * wi % kP;
         }
@@ -406,12 +406,12 @@ cudaError_t set_smem_attrs() {
 
 struct Launch {
     cudaError_t (*attrs)();
-    void (*code)(dim3, cudaStream_t, uint32_t *, const uint32_t *, const uint8_t *, uint32_t,
-                 unsigned long long, uint32_t, const uint32_t *);
+    void (*code)(dim3, cudaStream_t, uint2 *, const uint32_t *, const uint8_t *, uint32_t,
+                 unsigned long long, uint2, const uint2 *);
     void (*fwd)(dim3, cudaStream_t, uint32_t *, const int8_t *, const int32_t *, const uint32_t *,
-                uint32_t, uint32_t, uint32_t, const uint32_t *);
+                uint32_t, uint32_t, uint32_t, const uint2 *);
     void (*rows)(dim3, cudaStream_t, AcqRow *, unsigned long long *, const uint32_t *,
-                 const uint32_t *, uint32_t, uint32_t, uint32_t, uint32_t, const uint32_t *);
+                 const uint2 *, uint32_t, uint32_t, uint32_t, uint32_t, const uint2 *);
     uint32_t nt;
     size_t smem;
 };
@@ -420,17 +420,17 @@ template <int LOGM>
 Launch make_launch() {
     Launch l;
     l.attrs = &set_smem_attrs<LOGM>;
-    l.code = [](dim3 g, cudaStream_t st, uint32_t *H, const uint32_t *ct, const uint8_t *prn,
-                uint32_t N, unsigned long long r0, uint32_t scale, const uint32_t *T) {
-        k_acq_code<LOGM><<<g, Shape<LOGM>::NT, Shape<LOGM>::SMEM, st>>>(H, ct, prn, N, r0, scale, T);
+    l.code = [](dim3 g, cudaStream_t st, uint2 *H, const uint32_t *ct, const uint8_t *prn,
+                uint32_t N, unsigned long long r0, uint2 minv, const uint2 *T) {
+        k_acq_code<LOGM><<<g, Shape<LOGM>::NT, Shape<LOGM>::SMEM, st>>>(H, ct, prn, N, r0, minv, T);
     };
     l.fwd = [](dim3 g, cudaStream_t st, uint32_t *A, const int8_t *iq, const int32_t *w,
-               const uint32_t *tab, uint32_t N, uint32_t n_ms, uint32_t n_dopp, const uint32_t *T) {
+               const uint32_t *tab, uint32_t N, uint32_t n_ms, uint32_t n_dopp, const uint2 *T) {
         k_acq_fwd<LOGM><<<g, Shape<LOGM>::NT, Shape<LOGM>::SMEM, st>>>(A, iq, w, tab, N, n_ms, n_dopp, T);
     };
     l.rows = [](dim3 g, cudaStream_t st, AcqRow *rows, unsigned long long *grid, const uint32_t *A,
-                const uint32_t *H, uint32_t N, uint32_t n_ms, uint32_t n_dopp, uint32_t n_prn,
-                const uint32_t *Ti) {
+                const uint2 *H, uint32_t N, uint32_t n_ms, uint32_t n_dopp, uint32_t n_prn,
+                const uint2 *Ti) {
         k_acq_rows<LOGM><<<g, Shape<LOGM>::NT, Shape<LOGM>::SMEM, st>>>(rows, grid, A, H, N, n_ms, n_dopp,
                                                                         n_prn, Ti);
     };
@@ -461,8 +461,8 @@ struct rx_acq_s {
     cudaStream_t stream = nullptr;
     const rxh::DeviceTables *tables = nullptr;
     void *d_block = nullptr;              // one allocation for everything below
-    uint32_t *T = nullptr, *Ti = nullptr; // twiddles
-    uint32_t *H = nullptr;                // [max_prns][M]
+    uint2 *T = nullptr, *Ti = nullptr;    // twiddles with quotients
+    uint2 *H = nullptr;                   // [max_prns][M] code spectra with quotients
     uint32_t *A = nullptr;                // [chunk][n_ms][max_bins][2][M]
     int32_t *words = nullptr;             // [max_bins]
     uint8_t *prn = nullptr;               // [32]
@@ -471,7 +471,7 @@ struct rx_acq_s {
     unsigned long long *grid = nullptr;   // [max_receivers][max_prns][max_bins][N] or null
     int8_t *stage = nullptr;              // [max_receivers][n_ms][N][2]
     uint32_t chunk = 0;                   // receivers per transform pass
-    uint32_t scale = 0;                   // M^-1 R^2 mod p
+    uint2 minv{};                         // M^-1 mod p with its quotient
     uint32_t n_prn = 0, n_dopp = 0;
     uint64_t r0 = 0;
     uint32_t last_rx = 0;
@@ -542,8 +542,8 @@ extern "C" rx_status rx_acq_create(const rx_acq_config *cfg, rx_acq *out) {
         off = align_up(off + bytes, 256);
         return o;
     };
-    size_t o_T = take((size_t)4 << kMaxLog), o_Ti = take((size_t)4 << kMaxLog),
-           o_H = take(P * a->M * 4), o_A = take((size_t)a->chunk * per_rx), o_w = take(B * 4),
+    size_t o_T = take((size_t)8 << kMaxLog), o_Ti = take((size_t)8 << kMaxLog),
+           o_H = take(P * a->M * 8), o_A = take((size_t)a->chunk * per_rx), o_w = take(B * 4),
            o_prn = take(32), o_rows = take((size_t)a->chunk * B * P * sizeof(AcqRow)),
            o_res = take(R * P * sizeof(rx_acq_result)), o_stage = take(R * cfg->n_ms * N * 2),
            o_grid = cfg->keep_grid ? take(R * P * B * N * 8) : 0;
@@ -553,9 +553,9 @@ extern "C" rx_status rx_acq_create(const rx_acq_config *cfg, rx_acq *out) {
         return RX_ENOMEM;
     }
     char *b = (char *)a->d_block;
-    a->T = (uint32_t *)(b + o_T);
-    a->Ti = (uint32_t *)(b + o_Ti);
-    a->H = (uint32_t *)(b + o_H);
+    a->T = (uint2 *)(b + o_T);
+    a->Ti = (uint2 *)(b + o_Ti);
+    a->H = (uint2 *)(b + o_H);
     a->A = (uint32_t *)(b + o_A);
     a->words = (int32_t *)(b + o_w);
     a->prn = (uint8_t *)(b + o_prn);
@@ -563,17 +563,16 @@ extern "C" rx_status rx_acq_create(const rx_acq_config *cfg, rx_acq *out) {
     a->res = (rx_acq_result *)(b + o_res);
     a->stage = (int8_t *)(b + o_stage);
     a->grid = cfg->keep_grid ? (unsigned long long *)(b + o_grid) : nullptr;
-    std::vector<uint32_t> T, Ti;
+    std::vector<uint2> T, Ti;
     build_twiddles(T, Ti);
-    uint32_t small[64];
+    uint2 small[64];
     for (int k = 0; k < 32; ++k) {
         small[k] = T[k];
         small[32 + k] = Ti[k];
     }
-    const uint64_t Rm = (1ull << 32) % kP;
-    a->scale = mulmod(powmod(a->M, kP - 2), mulmod(Rm, Rm));
-    if (cudaMemcpy(a->T, T.data(), T.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(a->Ti, Ti.data(), Ti.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+    a->minv = with_quotient(powmod(a->M, kP - 2));
+    if (cudaMemcpy(a->T, T.data(), T.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(a->Ti, Ti.data(), Ti.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpyToSymbol(c_acq_tw, small, sizeof small) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(a->d_block);
@@ -615,7 +614,7 @@ extern "C" rx_status rx_acq_set_search(rx_acq a, uint32_t n_prn, const uint8_t *
     ACQ_CUDA(a, cudaMemcpyAsync(a->words, carrier_words, n_doppler * 4, cudaMemcpyDefault, a->stream));
     ACQ_CUDA(a, cudaMemcpyAsync(a->prn, prn, n_prn, cudaMemcpyDefault, a->stream));
     a->L.code(dim3(n_prn), a->stream, a->H, a->tables->code, a->prn, a->cfg.block_samples, r0,
-              a->scale, a->T);
+              a->minv, a->T);
     ACQ_CUDA(a, cudaGetLastError());
     ACQ_CUDA(a, a->stream ? cudaStreamSynchronize(a->stream) : cudaDeviceSynchronize());
     a->n_prn = n_prn;

@@ -1,22 +1,34 @@
-// Number-theoretic transform over the prime field GF(p), p = 15 * 2^27 + 1, for
+// Number-theoretic transform over the prime field GF(p), p = 2^30 - 2^18 + 1, for
 // the acquisition search's circular correlation (Sec. 3.7: the parallel-code-
 // phase search correlates every carrier-wiped block with the local code at all
 // code delays through a transform, a pointwise product and an inverse).
 //
 // Why a field transform and not a floating-point FFT: every correlation value
-// is an integer with |Z| <= 32512 N < (p - 1) / 2 for N <= 30961 samples, so the
-// transform computes it exactly modulo p and the signed residue IS the value.
-// The result is bit-identical to the direct sum, in integer arithmetic only.
+// is an integer.  The carrier table's largest |c| + |s| is 180, so a wiped
+// sample has |I'|, |Q'| <= 128 * 180 = 23040 and |Z| <= 23040 N <= (p - 1) / 2
+// for N <= 23296 samples.  The transform therefore computes Z exactly modulo p,
+// and the signed residue IS the value: bit-identical to the direct sum, in
+// integer arithmetic only.
 //
-// Conventions (all residues in [0, p)):
-//   - twiddle table T[L + j] = w_{2L}^j R mod p for L = 1, 2, 4, ..., j < L, with
-//     w_{2L} the principal 2L-th root of unity 31^((p-1)/(2L)) (31 generates
-//     GF(p)*) and R = 2^32 (Montgomery form); Ti holds the inverse roots.  The
-//     entries do not depend on the transform size, so one table of 2^15 words
-//     serves every size up to 2^15.
-//   - forward: decimation in frequency, natural order in, bit-reversed out.
-//   - inverse: decimation in time, bit-reversed in, natural order out, without
-//     the 1/M factor (the caller folds it into one operand of the product).
+// Arithmetic (p < 2^30, so 4p < 2^32):
+//   - a twiddle w is held with its quotient w' = floor(w 2^32 / p); for any
+//     x < 2^32, x w - floor(x w' / 2^32) p lies in [0, 2p) (one high and two
+//     low 32-bit products, no correction);
+//   - butterflies keep their values in [0, 2p) (forward) or [0, 4p)
+//     (inverse) and reduce only where a bound would be exceeded (lazy
+//     reduction in the manner of Harvey's NTT butterflies): 7 integer
+//     instructions and 3 multiplies per butterfly.
+// Conventions:
+//   - twiddle table T[L + j] = (w_{2L}^j mod p, its quotient) for L = 1, 2, 4, ...
+//     and j < L, w_{2L} the principal 2L-th root of unity 11^((p-1)/(2L)) (11
+//     generates GF(p)*); Ti holds the inverse roots.  The entries do not depend
+//     on the transform size, so one table of 2^15 pairs serves every size up to
+//     2^15.
+//   - forward: decimation in frequency, natural order in, bit-reversed out,
+//     inputs in [0, 2p), outputs in [0, 2p).
+//   - inverse: decimation in time, bit-reversed in, natural order out, inputs
+//     in [0, 4p), outputs in [0, 4p), without the 1/M factor (the caller folds
+//     it into one operand of the product).
 //   - shared-memory layout: element i at word pad(i) = i + 4 (i / 32), so that a
 //     thread's 32 consecutive elements start 36 words after its neighbour's
 //     (128-bit accesses of 8 threads fill the 32 banks) and strided accesses
@@ -33,15 +45,20 @@
 #define RXN_HD __host__ __device__ __forceinline__
 #else
 #define RXN_HD inline
+struct uint2 {
+    uint32_t x, y;
+};
 #endif
 
 namespace rxn {
 
-constexpr uint32_t kP = 2013265921u;        // 15 * 2^27 + 1
-constexpr uint32_t kPinv = 0x88000001u;     // p^-1 mod 2^32
+constexpr uint32_t kP = 1073479681u;        // 2^30 - 2^18 + 1
+constexpr uint32_t k2P = 2 * kP;
 constexpr uint32_t kHalfP = (kP - 1) / 2;
+constexpr uint32_t kGen = 11;               // generates GF(p)*
 constexpr int kMaxLog = 15;                 // largest transform: 2^15
-constexpr uint32_t kMaxN = 30961;           // 32512 N < (p - 1) / 2
+constexpr uint32_t kMaxAbsWiped = 23040;    // 128 * max(|c| + |s|) of the carrier table
+constexpr uint32_t kMaxN = kHalfP / kMaxAbsWiped;   // 23296
 
 RXN_HD uint32_t umulhi(uint32_t a, uint32_t b) {
 #if defined(__CUDA_ARCH__)
@@ -53,35 +70,39 @@ RXN_HD uint32_t umulhi(uint32_t a, uint32_t b) {
 
 RXN_HD uint32_t min_u32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
-// (a + b) mod p and (a - b) mod p for a, b < p: the wrapped candidate is the
-// smaller one as an unsigned number.
-RXN_HD uint32_t add(uint32_t a, uint32_t b) {
-    uint32_t s = a + b;
-    return min_u32(s, s - kP);
-}
-RXN_HD uint32_t sub(uint32_t a, uint32_t b) {
-    uint32_t d = a - b;
-    return min_u32(d, d + kP);
-}
+// x reduced by m once if x >= m (x < 2m): the wrapped candidate is the larger
+// unsigned number.
+RXN_HD uint32_t csub(uint32_t x, uint32_t m) { return min_u32(x, x - m); }
 
-// Montgomery product a b 2^-32 mod p for a, b < p: with m = (a b mod 2^32) p^-1
-// (mod 2^32), a b - m p is a multiple of 2^32 and (a b - m p) / 2^32 lies in
-// (-p, p); its high words differ by exactly that quotient.
-RXN_HD uint32_t mont(uint32_t a, uint32_t b) {
-    uint32_t lo = a * b;
-    uint32_t hi = umulhi(a, b);
-    uint32_t m = lo * kPinv;
-    uint32_t mh = umulhi(m, kP);
-    uint32_t u = hi - mh;
-    return min_u32(u, u + kP);
+// x w mod p, up to one p: in [0, 2p) for any x < 2^32 (t = (w, w')).
+RXN_HD uint32_t shoup(uint32_t x, uint2 t) {
+    uint32_t q = umulhi(x, t.y);
+    return x * t.x - q * kP;
 }
 
 // Signed integer residue -> [0, p); |v| < p.
 RXN_HD uint32_t from_signed(int32_t v) { return v < 0 ? (uint32_t)(v + (int32_t)kP) : (uint32_t)v; }
-// [0, p) -> the representative in (-p/2, p/2].
-RXN_HD int32_t to_signed(uint32_t r) { return r > kHalfP ? (int32_t)(r - kP) : (int32_t)r; }
+// [0, 4p) -> the representative in [-(p-1)/2, (p-1)/2].
+RXN_HD int32_t to_signed_lazy(uint32_t r) {
+    r = csub(csub(r, k2P), kP);
+    return r > kHalfP ? (int32_t)(r - kP) : (int32_t)r;
+}
 
 RXN_HD uint32_t pad(uint32_t i) { return i + ((i >> 5) << 2); }
+
+// Forward (Gentleman-Sande) butterfly, values in [0, 2p).
+RXN_HD void bf_dif(uint32_t &x, uint32_t &y, uint2 w) {
+    uint32_t s = csub(x + y, k2P);
+    y = shoup(x - y + k2P, w);
+    x = s;
+}
+// Inverse (Cooley-Tukey) butterfly, values in [0, 4p).
+RXN_HD void bf_dit(uint32_t &x, uint32_t &y, uint2 w) {
+    uint32_t u = csub(x, k2P);
+    uint32_t t = shoup(y, w);
+    x = u + t;
+    y = u - t + k2P;
+}
 
 // ---------------------------------------------------------------------------
 // Forward transform (decimation in frequency)
@@ -89,32 +110,35 @@ RXN_HD uint32_t pad(uint32_t i) { return i + ((i >> 5) << 2); }
 
 // One radix-2 stage of half-length L = 2^lgL.
 RXN_HD void dif_pass2(uint32_t *s, int lgL, uint32_t tid, uint32_t nt, uint32_t M,
-                      const uint32_t *T) {
+                      const uint2 *T) {
     const uint32_t L = 1u << lgL;
     for (uint32_t b = tid; b < M / 2; b += nt) {
         uint32_t j = b & (L - 1);
         uint32_t i0 = ((b >> lgL) << (lgL + 1)) + j;
         uint32_t u = s[pad(i0)], v = s[pad(i0 + L)];
-        s[pad(i0)] = add(u, v);
-        s[pad(i0 + L)] = mont(sub(u, v), T[L + j]);
+        bf_dif(u, v, T[L + j]);
+        s[pad(i0)] = u;
+        s[pad(i0 + L)] = v;
     }
 }
 
 // Two stages fused: half-length L = 2^(lgH+1) then H = L / 2 (H >= 32).
 RXN_HD void dif_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t M,
-                      const uint32_t *T) {
+                      const uint2 *T) {
     const uint32_t H = 1u << lgH, L = 2 * H;
     for (uint32_t g = tid; g < M / 4; g += nt) {
         uint32_t j = g & (H - 1);
         uint32_t i = ((g >> lgH) << (lgH + 2)) + j;
         uint32_t x0 = s[pad(i)], x1 = s[pad(i + H)], x2 = s[pad(i + L)], x3 = s[pad(i + L + H)];
-        uint32_t wa = T[L + j], wb = T[L + j + H], wc = T[H + j];
-        uint32_t y0 = add(x0, x2), y2 = mont(sub(x0, x2), wa);
-        uint32_t y1 = add(x1, x3), y3 = mont(sub(x1, x3), wb);
-        s[pad(i)] = add(y0, y1);
-        s[pad(i + H)] = mont(sub(y0, y1), wc);
-        s[pad(i + L)] = add(y2, y3);
-        s[pad(i + L + H)] = mont(sub(y2, y3), wc);
+        uint2 wa = T[L + j], wb = T[L + j + H], wc = T[H + j];
+        bf_dif(x0, x2, wa);
+        bf_dif(x1, x3, wb);
+        bf_dif(x0, x1, wc);
+        bf_dif(x2, x3, wc);
+        s[pad(i)] = x0;
+        s[pad(i + H)] = x1;
+        s[pad(i + L)] = x2;
+        s[pad(i + L + H)] = x3;
     }
 }
 
@@ -129,11 +153,7 @@ struct DifReg {
 #pragma unroll
         for (int st = 0; st < 32; st += 2 * L) {
 #pragma unroll
-            for (int j = 0; j < L; ++j) {
-                uint32_t u = x[st + j], v = x[st + j + L];
-                x[st + j] = add(u, v);
-                x[st + j + L] = mont(sub(u, v), tw[L + j]);
-            }
+            for (int j = 0; j < L; ++j) bf_dif(x[st + j], x[st + j + L], tw[L + j]);
         }
         if constexpr (LG > 0) DifReg<LG - 1>::run(x, tw);
     }
@@ -154,11 +174,7 @@ struct DitReg {
 #pragma unroll
         for (int st = 0; st < 32; st += 2 * L) {
 #pragma unroll
-            for (int j = 0; j < L; ++j) {
-                uint32_t u = x[st + j], v = mont(x[st + j + L], twi[L + j]);
-                x[st + j] = add(u, v);
-                x[st + j + L] = sub(u, v);
-            }
+            for (int j = 0; j < L; ++j) bf_dit(x[st + j], x[st + j + L], twi[L + j]);
         }
         if constexpr (LG < 4) DitReg<LG + 1>::run(x, twi);
     }
@@ -168,34 +184,35 @@ RXN_HD void dit_reg32(uint32_t (&x)[32], const TW &twi) { DitReg<0>::run(x, twi)
 
 // Two stages fused: half-length H = 2^lgH then L = 2 H (H >= 32).
 RXN_HD void dit_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t M,
-                      const uint32_t *Ti) {
+                      const uint2 *Ti) {
     const uint32_t H = 1u << lgH, L = 2 * H;
     for (uint32_t g = tid; g < M / 4; g += nt) {
         uint32_t j = g & (H - 1);
         uint32_t i = ((g >> lgH) << (lgH + 2)) + j;
         uint32_t x0 = s[pad(i)], x1 = s[pad(i + H)], x2 = s[pad(i + L)], x3 = s[pad(i + L + H)];
-        uint32_t wc = Ti[H + j], wa = Ti[L + j], wb = Ti[L + j + H];
-        uint32_t t1 = mont(x1, wc), t3 = mont(x3, wc);
-        uint32_t y0 = add(x0, t1), y1 = sub(x0, t1);
-        uint32_t y2 = add(x2, t3), y3 = sub(x2, t3);
-        uint32_t u2 = mont(y2, wa), u3 = mont(y3, wb);
-        s[pad(i)] = add(y0, u2);
-        s[pad(i + L)] = sub(y0, u2);
-        s[pad(i + H)] = add(y1, u3);
-        s[pad(i + L + H)] = sub(y1, u3);
+        uint2 wc = Ti[H + j], wa = Ti[L + j], wb = Ti[L + j + H];
+        bf_dit(x0, x1, wc);
+        bf_dit(x2, x3, wc);
+        bf_dit(x0, x2, wa);
+        bf_dit(x1, x3, wb);
+        s[pad(i)] = x0;
+        s[pad(i + H)] = x1;
+        s[pad(i + L)] = x2;
+        s[pad(i + L + H)] = x3;
     }
 }
 
 // One radix-2 stage of half-length L = 2^lgL.
 RXN_HD void dit_pass2(uint32_t *s, int lgL, uint32_t tid, uint32_t nt, uint32_t M,
-                      const uint32_t *Ti) {
+                      const uint2 *Ti) {
     const uint32_t L = 1u << lgL;
     for (uint32_t b = tid; b < M / 2; b += nt) {
         uint32_t j = b & (L - 1);
         uint32_t i0 = ((b >> lgL) << (lgL + 1)) + j;
-        uint32_t u = s[pad(i0)], v = mont(s[pad(i0 + L)], Ti[L + j]);
-        s[pad(i0)] = add(u, v);
-        s[pad(i0 + L)] = sub(u, v);
+        uint32_t u = s[pad(i0)], v = s[pad(i0 + L)];
+        bf_dit(u, v, Ti[L + j]);
+        s[pad(i0)] = u;
+        s[pad(i0 + L)] = v;
     }
 }
 
@@ -203,12 +220,12 @@ RXN_HD void dit_pass2(uint32_t *s, int lgL, uint32_t tid, uint32_t nt, uint32_t 
 RXN_HD int smem_stages(int logM) { return logM - 5; }
 
 // The outputs of the inverse's last stage that fall below M / 2, for the
-// elements thread tid owns.  With an even number of shared-memory stages the
-// last pass is radix-4 (H = M/4) and owns, for group g = tid + q nt, outputs g
-// and g + M/4 (slots 2q, 2q + 1); with an odd number it is radix-2 (L = M/2) and
-// owns output b = tid + q nt (slot q).  Both give M / (2 nt) slots per thread,
-// and the counts are compile-time so that per-slot accumulators stay in
-// registers.  out_slot(slot, index, residue) receives each output.
+// elements thread tid owns, as signed integers.  With an even number of
+// shared-memory stages the last pass is radix-4 (H = M/4) and owns, for group
+// g = tid + q nt, outputs g and g + M/4 (slots 2q, 2q + 1); with an odd number
+// it is radix-2 (L = M/2) and owns output b = tid + q nt (slot q).  Both give
+// M / (2 nt) slots per thread, and the counts are compile-time so that per-slot
+// accumulators stay in registers.  out_slot(slot, index, value) receives each.
 template <int LOGM, uint32_t NT>
 struct LastHalf {
     static constexpr uint32_t M = 1u << LOGM;
@@ -221,7 +238,7 @@ struct LastHalf {
     }
 
     template <class F>
-    RXN_HD static void run(const uint32_t *s, uint32_t tid, const uint32_t *Ti, F &&out_slot) {
+    RXN_HD static void run(const uint32_t *s, uint32_t tid, const uint2 *Ti, F &&out_slot) {
         if (kRadix4) {
             const uint32_t H = M / 4, L = M / 2;
 #pragma unroll
@@ -229,20 +246,22 @@ struct LastHalf {
                 uint32_t g = tid + q * NT;
                 uint32_t x0 = s[pad(g)], x1 = s[pad(g + H)], x2 = s[pad(g + L)],
                          x3 = s[pad(g + L + H)];
-                uint32_t wc = Ti[H + g], wa = Ti[L + g], wb = Ti[L + g + H];
-                uint32_t t1 = mont(x1, wc), t3 = mont(x3, wc);
-                uint32_t y0 = add(x0, t1), y1 = sub(x0, t1);
-                uint32_t y2 = add(x2, t3), y3 = sub(x2, t3);
-                out_slot(2 * q, g, add(y0, mont(y2, wa)));
-                out_slot(2 * q + 1, g + H, add(y1, mont(y3, wb)));
+                uint2 wc = Ti[H + g], wa = Ti[L + g], wb = Ti[L + g + H];
+                bf_dit(x0, x1, wc);
+                bf_dit(x2, x3, wc);
+                // last stage: only the sums (indices below M/2) are needed
+                uint32_t z0 = csub(x0, k2P) + shoup(x2, wa);
+                uint32_t z1 = csub(x1, k2P) + shoup(x3, wb);
+                out_slot(2 * q, g, to_signed_lazy(z0));
+                out_slot(2 * q + 1, g + H, to_signed_lazy(z1));
             }
         } else {
             const uint32_t L = M / 2;
 #pragma unroll
             for (uint32_t q = 0; q < kSlots; ++q) {
                 uint32_t b = tid + q * NT;
-                uint32_t u = s[pad(b)], v = mont(s[pad(b + L)], Ti[L + b]);
-                out_slot(q, b, add(u, v));
+                uint32_t z = csub(s[pad(b)], k2P) + shoup(s[pad(b + L)], Ti[L + b]);
+                out_slot(q, b, to_signed_lazy(z));
             }
         }
     }
