@@ -74,6 +74,30 @@ class OrcAcqResult(C.Structure):
         return (self.peak, self.second, self.dopp_bin, self.code_phase)
 
 
+class OrcBitSync(C.Structure):
+    """Bit-synchroniser state (mirrors orc_bitsync in oracle.c)."""
+    _fields_ = [
+        ("last_ip", C.c_int32),
+        ("have_last", C.c_uint32),
+        ("hist", C.c_uint32 * 20),
+        ("n_changes", C.c_uint32),
+        ("epoch", C.c_uint32),
+        ("sync", C.c_uint32),
+        ("edge", C.c_uint32),
+        ("bit_active", C.c_uint32),
+        ("n_bits", C.c_uint32),
+        ("bit_acc", C.c_int64),
+        ("bits", C.c_uint64),
+        ("first_bit_epoch", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        d["hist"] = list(self.hist)
+        return d
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -121,6 +145,13 @@ def lib():
         L.orc_acq_handoff.argtypes = [C.c_int32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
                                       C.c_double, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
         L.orc_acq_handoff.restype = None
+        L.orc_bitsync_update.argtypes = [C.POINTER(OrcBitSync), C.c_int32, C.c_uint32]
+        L.orc_bitsync_update.restype = None
+        L.orc_track_code_channel.argtypes = [P, C.c_uint64, C.c_double, C.c_int, C.c_uint32, P,
+                                             C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                             C.c_uint32, C.POINTER(OrcChan), C.POINTER(OrcBitSync),
+                                             P, C.POINTER(C.c_uint32), C.c_uint32, P, P]
+        L.orc_track_code_channel.restype = C.c_int
         _lib = L
     return _lib
 
@@ -300,3 +331,40 @@ def acq_handoff(w: int, code_phase: int, N: int, n_ms: int, r0: int, fs: float):
     lib().orc_acq_handoff(int(w), int(code_phase), int(N), int(n_ms), int(r0), float(fs),
                           C.byref(phi), C.byref(r))
     return phi.value, r.value
+
+
+def bitsync_update(bs: OrcBitSync, ip: int, k: int) -> OrcBitSync:
+    """One epoch of the bit synchroniser, on a copy of bs; returns the copy."""
+    out = OrcBitSync.from_buffer_copy(bs)
+    lib().orc_bitsync_update(C.byref(out), int(ip), int(k))
+    return out
+
+
+class CodeChannel:
+    """One channel tracked in code-period epochs: the loop state, the bit
+    synchroniser and the open epoch (accumulators and sample count), carried
+    from call to call."""
+
+    def __init__(self, prn: int, ch: OrcChan, n_taps: int):
+        self.prn = int(prn)
+        self.ch = OrcChan.from_buffer_copy(ch)
+        self.bs = OrcBitSync()
+        self.acc = np.zeros((n_taps, 2), np.int32)
+        self.n_in = C.c_uint32(0)
+
+    def track(self, iq: np.ndarray, nsamp: int, fs: float, tap_off, tap_e: int, tap_p: int,
+              tap_l: int, pll_bn: float, dll_bn: float, sync_k: int, max_epochs: int = 64):
+        """Correlate nsamp samples; returns (dumps [E, n_taps, 2], epoch sample counts [E])."""
+        iq = np.ascontiguousarray(iq, dtype=np.int8).reshape(-1)
+        assert iq.size >= 2 * nsamp
+        taps = np.ascontiguousarray(tap_off, dtype=np.int64).reshape(-1)
+        dumps = np.zeros((max_epochs, taps.size, 2), np.int32)
+        lens = np.zeros(max_epochs, np.uint32)
+        n = lib().orc_track_code_channel(_ptr(iq), nsamp, float(fs), self.prn, taps.size,
+                                         _ptr(taps), tap_e, tap_p, tap_l, float(pll_bn),
+                                         float(dll_bn), int(sync_k), C.byref(self.ch),
+                                         C.byref(self.bs), _ptr(self.acc), C.byref(self.n_in),
+                                         max_epochs, _ptr(dumps), _ptr(lens))
+        if n < 0:
+            raise ValueError(f"orc_track_code_channel: {n}")
+        return dumps[:n], lens[:n]

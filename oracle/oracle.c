@@ -27,6 +27,10 @@
  *     code over a grid of Doppler bins and all code delays (the quantity a
  *     parallel-code-phase FFT search computes), its peak, the second peak of
  *     the peak's Doppler row, and the hand-over of the result to tracking.
+ *   - tracking in code-period epochs (one dump per period of each channel's
+ *     own prompt code, of varying sample count) and bit synchronisation by a
+ *     histogram of prompt sign changes over the 20 code periods of a bit
+ *     (Sec. 3.1), with the decoded bits.
  *   Every floating-point step is a single correctly rounded
  *     IEEE-754 binary64 operation, written one per statement, in a fixed
  *     order; the file must be compiled with -ffp-contract=off.
@@ -766,4 +770,123 @@ void orc_acq_handoff(int32_t w, uint32_t code_phase, uint32_t N, uint32_t n_ms, 
     lag = lag == 0 ? 0 : N - lag;
     unsigned __int128 p = (unsigned __int128)lag * r0 + (unsigned __int128)n_ms * N * (*r);
     *phi = (uint64_t)(p % ORC_CODE_MOD);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Code-period epochs and bit synchronisation (Sec. 3.1, Fig. 7, Sec. 3.6)  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t last_ip;          /* prompt I of the previous epoch */
+    uint32_t have_last;
+    uint32_t hist[20];        /* sign changes by epoch index mod 20 */
+    uint32_t n_changes;
+    uint32_t epoch;           /* epochs seen so far (index of the next one) */
+    uint32_t sync;            /* 1 once the bit edge is found */
+    uint32_t edge;            /* epoch index mod 20 at which a bit starts */
+    uint32_t bit_active;      /* 1 while a bit is being integrated */
+    uint32_t n_bits;          /* bits decoded */
+    int64_t bit_acc;          /* prompt I summed over the current bit's epochs */
+    uint64_t bits;            /* the last 64 decoded bits, newest in bit 0 (1 = negative sum) */
+    uint32_t first_bit_epoch; /* epoch index at which the first decoded bit starts */
+    uint32_t pad;
+} orc_bitsync;
+
+/*
+ * Bit synchronisation by a histogram of prompt sign changes.  A data bit lasts
+ * 20 code periods (Sec. 3.1), so data transitions fall only on every 20th
+ * code epoch.  Called once per closed one-period epoch with its prompt I:
+ *   - a change of sign from the previous epoch (negative = below zero) counts
+ *     in bin (epoch index mod 20);
+ *   - before synchronisation: when the fullest bin m (the first among equals)
+ *     holds at least k changes and at least 3 times as many as any other bin,
+ *     the bit edge is m;
+ *   - after it: the prompt I is summed over each bit, from an epoch with index
+ *     = edge (mod 20) to the next; at that next epoch the sum's sign is the
+ *     decoded bit (1 for a negative sum), shifted into `bits`.
+ */
+void orc_bitsync_update(orc_bitsync *b, int32_t ip, uint32_t k) {
+    uint32_t e = b->epoch;
+    uint32_t bin = e % 20;
+    if (b->have_last && ((ip < 0) != (b->last_ip < 0))) {
+        b->hist[bin] += 1;
+        b->n_changes += 1;
+    }
+    b->last_ip = ip;
+    b->have_last = 1;
+    if (b->sync) {
+        if (bin == b->edge) {
+            if (b->bit_active) {
+                b->bits = (b->bits << 1) | (uint64_t)(b->bit_acc < 0 ? 1 : 0);
+                b->n_bits += 1;
+            } else {
+                b->first_bit_epoch = e;
+            }
+            b->bit_active = 1;
+            b->bit_acc = 0;
+        }
+        if (b->bit_active) b->bit_acc += ip;
+    } else {
+        uint32_t m = 0;
+        for (uint32_t j = 1; j < 20; ++j)
+            if (b->hist[j] > b->hist[m]) m = j;
+        uint32_t second = 0;
+        for (uint32_t j = 0; j < 20; ++j)
+            if (j != m && b->hist[j] > second) second = b->hist[j];
+        if (b->hist[m] >= k && b->hist[m] >= 3 * second) {
+            b->sync = 1;
+            b->edge = m;
+        }
+    }
+    b->epoch = e + 1;
+}
+
+/*
+ * Tracking of one channel in code-period epochs, the classic receiver's
+ * integrate-and-dump (one code period, Sec. 3.1 / Fig. 7), instead of the
+ * fixed sample blocks of orc_run_receiver.  The samples are correlated with
+ * the definition of orc_correlate_block.  An epoch ends after the sample at
+ * which the prompt code phase, advanced by r, reaches the end of the period:
+ * from phase phi that is b = ceil((1023*2^32 - phi) / r) samples.  At the end
+ * the accumulators are dumped with the epoch's sample count n, the loops of
+ * orc_track run with n_accum = n (T = n / fs), the bit synchroniser gets the
+ * prompt I, and the accumulators clear.  acc ([n_taps][2]) and *n_in (samples
+ * so far in the open epoch) carry a partial epoch from call to call.  Up to
+ * max_epochs closed epochs go to dumps ([max_epochs][n_taps][2]) and
+ * epoch_len.  Returns the number of epochs closed, -1 on bad arguments, -2 if
+ * more than max_epochs closed.
+ */
+int orc_track_code_channel(const int8_t *iq, uint64_t nsamp, double fs, int prn,
+                           uint32_t n_taps, const int64_t *tap_off, int tap_e, int tap_p,
+                           int tap_l, double pll_bn, double dll_bn, uint32_t sync_k,
+                           orc_chan *ch, orc_bitsync *bs, int32_t *acc, uint32_t *n_in,
+                           uint32_t max_epochs, int32_t *dumps, uint32_t *epoch_len) {
+    int8_t code[ORC_CODE_LEN];
+    if (orc_ca_code(prn, code) != 0 || n_taps == 0) return -1;
+    if (tap_e < 0 || tap_p < 0 || tap_l < 0 || (uint32_t)tap_e >= n_taps ||
+        (uint32_t)tap_p >= n_taps || (uint32_t)tap_l >= n_taps)
+        return -1;
+    uint32_t closed = 0;
+    uint64_t pos = 0;
+    while (pos < nsamp) {
+        uint64_t left = nsamp - pos;
+        uint64_t b = UINT64_MAX;                     /* samples to the end of the period */
+        if (ch->r != 0) b = (ORC_CODE_MOD - ch->phi + ch->r - 1) / ch->r;
+        uint64_t seg = b < left ? b : left;
+        orc_correlate_block(iq + 2 * pos, (uint32_t)seg, &ch->theta, ch->w, &ch->phi, ch->r, tap_off,
+                            n_taps, code, acc);
+        *n_in += (uint32_t)seg;
+        pos += seg;
+        if (seg == b) {
+            if (closed >= max_epochs) return -2;
+            memcpy(dumps + (size_t)closed * n_taps * 2, acc, sizeof(int32_t) * n_taps * 2);
+            epoch_len[closed] = *n_in;
+            orc_track(ch, acc, tap_off, tap_e, tap_p, tap_l, fs, *n_in, pll_bn, dll_bn);
+            orc_bitsync_update(bs, acc[2 * tap_p], sync_k);
+            memset(acc, 0, sizeof(int32_t) * n_taps * 2);
+            *n_in = 0;
+            closed += 1;
+        }
+    }
+    return (int)closed;
 }

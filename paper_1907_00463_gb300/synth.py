@@ -13,8 +13,11 @@ Signal recipe (all draws seeded):
   t = n / fs; carrier_cycles = psi + f_D t + a t^2 / 2;
   chip(t) = chip0 + 1.023e6 t + (f_D t + a t^2/2) / 1540     (code Doppler)
   A_sv = sqrt(2 sigma^2 10^(CN0/10) / fs)  (per-component noise sigma)
-  d_sv: +-1, transitions only at multiples of 20 ms of receiver time (Sec. 3.1:
-  a data bit lasts 20 code periods)
+  d_sv: +-1, a data bit lasts 20 code periods (Sec. 3.1); transitions at
+  multiples of 20 ms of receiver time (the default, so that fixed-length
+  integrations never straddle one), or, with bits_on_code_epochs, at every 20th
+  boundary of the SV's own received code periods, as the broadcast signal has
+  them (bit b covers received code periods 20b .. 20b + 19)
   I, Q = clip(round_half_even(Re, Im), -128, 127)
 """
 from __future__ import annotations
@@ -109,6 +112,7 @@ class Receiver:
     seed: int = 0
     nav_bits: bool = True
     meta: dict = field(default_factory=dict)
+    bits_on_code_epochs: bool = False
 
     @property
     def n_taps(self) -> int:
@@ -135,6 +139,14 @@ def _start_channel(fs: float, sv: SV, taps: list[int], rng: np.random.Generator,
     return Channel(sv.prn, w, phi, r, list(taps))
 
 
+def nav_bit_values(rx: Receiver, prn: int, n_bits: int) -> np.ndarray:
+    """The +-1 data bits of one SV of a scenario.  With bits_on_code_epochs, entry
+    b + 1 covers received code periods 20b .. 20b + 19 (entry 0 covers a delayed
+    path's periods before period 0); otherwise entry b covers receiver time
+    [20b, 20b + 20) ms."""
+    return _nav_bits(rx.seed, prn, n_bits)
+
+
 def _nav_bits(seed: int, prn: int, n_bits: int) -> np.ndarray:
     g = np.random.Generator(np.random.Philox(key=[seed & 0xFFFFFFFFFFFFFFFF, 7000 + prn]))
     return np.where(g.integers(0, 2, n_bits) == 0, 1.0, -1.0)
@@ -149,7 +161,7 @@ def generate_iq(rx: Receiver, n_samples: int | None = None, device="cpu",
     out = torch.empty((n_samples, 2), dtype=torch.int8, device=dev)
     ca = torch.from_numpy(ca_table().astype(np.float64)).to(dev)
     fs = float(rx.fs)
-    n_bits = int(math.ceil(n_samples / fs / 0.02)) + 2
+    n_bits = int(math.ceil(n_samples / fs / 0.02)) + 4
     nav = {sv.prn: torch.from_numpy(_nav_bits(rx.seed, sv.prn, n_bits)).to(dev) for sv in rx.svs}
     for c0 in range(0, n_samples, chunk):
         n = min(chunk, n_samples - c0)
@@ -171,6 +183,9 @@ def generate_iq(rx: Receiver, n_samples: int | None = None, device="cpu",
                 idx = torch.remainder(torch.floor(chip), CODE_LEN).long()
                 code = ca[sv.prn][idx]
                 ang = (2.0 * math.pi) * torch.remainder(carr, 1.0)
+                if rx.nav_bits and rx.bits_on_code_epochs:
+                    # bit b spans received code periods 20b .. 20b + 19 (period 0 holds t = 0)
+                    d = nav[sv.prn][torch.floor(chip / (20.0 * CODE_LEN)).long() + 1]
                 s = a * d * code
                 re += s * torch.cos(ang)
                 im += s * torch.sin(ang)
