@@ -122,6 +122,10 @@ typedef struct {
     double fll_bn_hz;            /* RX_LOOPS_TABLE3: FLL noise bandwidth (1st order, assists the
                                     PLL); 0 = no FLL; with RX_LOOPS_TABLE3 dll_bn_hz is the
                                     bandwidth of a 2nd-order DLL */
+    uint32_t epoch_mode;         /* RX_EPOCH_BLOCKS (0): rx_correlate + rx_track_epoch;
+                                    RX_EPOCH_CODE (1): rx_track_code (RX_LOOPS_PLL2_DLL1 only) */
+    uint32_t bitsync_count;      /* RX_EPOCH_CODE: sign changes the fullest bin needs before
+                                    the bit edge is declared; 0 = 8 */
 } rx_config;
 
 /* Loop sets of the plain form.  RX_LOOPS_PLL2_DLL1: 2nd-order PLL, 1st-order
@@ -161,6 +165,42 @@ typedef struct {
     uint32_t have_prev;          /* 1 once the channel has a previous prompt */
     uint32_t pad;
 } rx_channel_health;
+
+/* Epoch modes of the plain form.  RX_EPOCH_BLOCKS: the caller's blocks set
+ * the integrations (rx_correlate, rx_track_epoch).  RX_EPOCH_CODE: each
+ * channel integrates over whole periods of its own prompt code (Sec. 3.1: the
+ * C/A code repeats every 1023 chips; Fig. 7's integrate-and-dump), the
+ * classic receiver's epoch, of N - 1, N or N + 1 samples as the code Doppler
+ * moves it (rx_track_code). */
+#define RX_EPOCH_BLOCKS 0u
+#define RX_EPOCH_CODE 1u
+
+/* Per-channel state of RX_EPOCH_CODE: the open epoch's sample count and the
+ * bit synchroniser (zero after rx_set_channels).  A data bit lasts 20 code
+ * periods (Sec. 3.1).  At each closed epoch (index e, prompt I = ip):
+ *   - a change of sign from the previous epoch's prompt I (negative = below
+ *     zero) counts in hist[e mod 20];
+ *   - before synchronisation: when the fullest bin m (the first among equals)
+ *     holds at least bitsync_count changes and at least 3 times as many as any
+ *     other bin, sync = 1 and edge = m;
+ *   - after it: ip is summed from an epoch with e = edge (mod 20) to the next;
+ *     at that next epoch the sum's sign (1 = negative) is shifted into bits as
+ *     a decoded data bit.  first_bit_epoch is where the first decoded bit began. */
+typedef struct {
+    int32_t last_ip;             /* prompt I of the previous epoch */
+    uint32_t have_last;
+    uint32_t hist[20];           /* sign changes by epoch index mod 20 */
+    uint32_t n_changes;
+    uint32_t epoch;              /* epochs closed since rx_set_channels */
+    uint32_t sync;
+    uint32_t edge;
+    uint32_t bit_active;         /* a bit is being summed */
+    uint32_t n_bits;             /* bits decoded */
+    int64_t bit_acc;             /* the current bit's sum of prompt I */
+    uint64_t bits;               /* last 64 decoded bits, newest in bit 0 */
+    uint32_t first_bit_epoch;
+    uint32_t samples_in_epoch;   /* samples correlated in the open epoch */
+} rx_code_state;
 
 typedef struct rx_handle_s *rx_handle;
 
@@ -228,6 +268,31 @@ rx_status rx_read_health(rx_handle h, rx_channel_health *out, uint32_t cap);
 rx_status rx_write_health(rx_handle h, const rx_channel_health *in, uint32_t n);
 
 /* Message for the last failed call on h (static storage inside the handle). */
+/* RX_EPOCH_CODE: correlate nsamp samples (host or device, as rx_correlate),
+ * closing an epoch for a channel each time its prompt code phase, advanced
+ * sample by sample by its code word r, passes the end of the code period:
+ * from phase phi that is b = ceil((1023 2^32 - phi) / r) samples.  At a closed
+ * epoch of n samples the accumulators are dumped, the loops run as in
+ * rx_track_epoch with T = n / fs, the new words take effect from the next
+ * sample, the bit synchroniser sees the prompt I, and the accumulators clear.
+ * A partial epoch carries into the next call.  Synchronous.  RX_ESTATE in
+ * RX_EPOCH_BLOCKS, RX_EINVAL if a channel closed more epochs than the handle
+ * holds per call (max_block_samples / (0.9 fs / 1000) + 2: only a code rate
+ * beyond 1.1 times the chip rate does that) or its code word reached 2^32. */
+rx_status rx_track_code(rx_handle h, const int8_t *iq, uint32_t nsamp);
+
+/* The epochs closed by the last rx_track_code: dumps [n_ch][max_epochs][ntaps][2]
+ * and their sample counts [n_ch][max_epochs] (entries beyond n_epochs[c] are
+ * zero), n_epochs [n_ch].  RX_EINVAL if a channel closed more than
+ * max_epochs. */
+rx_status rx_read_code_epochs(rx_handle h, int32_t *dumps, uint32_t *epoch_samples,
+                              uint32_t *n_epochs, uint32_t max_epochs);
+
+/* RX_EPOCH_CODE state of every channel, for read-back and checkpoint/resume
+ * (with rx_read_state and rx_read_accumulators). */
+rx_status rx_read_code_state(rx_handle h, rx_code_state *out, uint32_t cap);
+rx_status rx_write_code_state(rx_handle h, const rx_code_state *in, uint32_t n);
+
 const char *rx_last_error(rx_handle h);
 
 /* ------------------------------------------------------------------------ */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -30,6 +31,12 @@ struct PlainState {
     int64_t *taps;     // [n][ntaps]
     int32_t *acc;      // [n][ntaps][2]
     LoopExt *ext;      // [n], RX_LOOPS_TABLE3
+    // RX_EPOCH_CODE
+    rx_code_state *cs; // [n] open epoch and bit synchroniser
+    int32_t *cdump;    // [n][cap][ntaps][2] epochs closed by the last call
+    uint32_t *clen;    // [n][cap] their sample counts
+    uint32_t *cnum;    // [n] epochs closed by the last call
+    uint32_t *cerr;    // [1] bit 0: ring overflow, bit 1: code word reached 2^32
 };
 
 template <int TT>
@@ -51,6 +58,65 @@ __device__ __forceinline__ void plain_group(const uint32_t (&x)[SPT], uint32_t t
         if (lane == 0) {
             atomicAdd((unsigned *)&s_red[2 * (t0 + k)], vi);
             atomicAdd((unsigned *)&s_red[2 * (t0 + k) + 1], vq);
+        }
+    }
+}
+
+// Correlate one chunk of SPT samples (first sample at carrier phase theta0 and
+// code phase phi0) for every tap of a channel, adding into s_red [ntaps][2]:
+// the chip-segment form when the code rate allows it, else the direct form.
+__device__ __forceinline__ void plain_chunk(const uint32_t (&x)[SPT], uint32_t theta0, uint32_t w,
+                                            uint64_t phi0, uint32_t r, uint32_t ntaps,
+                                            const int64_t *s_taps, const uint32_t *s_code,
+                                            const uint32_t *s_tab, const uint16_t *s_pair,
+                                            int4 *s_slices, int32_t *s_red) {
+    const int mode = seg_mode(r);
+    if (mode != 0) {
+        // chip-segment form: mix once, every tap group reads the running sums
+        int4 *slice = s_slices + threadIdx.x * SLICE_INT4;
+        const uint32_t mg = seg_magic(r);
+        if (mode == 16) seg_prefix<16>(x, theta0, w, s_tab, slice);
+        else seg_prefix<8>(x, theta0, w, s_tab, slice);
+        for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
+            const int64_t *tp = s_taps + t0;
+            int32_t *red = s_red + 2 * t0;
+            const uint32_t tt = min((uint32_t)TAP_GROUP, ntaps - t0);
+            if (mode == 16) {
+                switch (tt) {
+                    case 1: seg_group_reduce<16, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 2: seg_group_reduce<16, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 3: seg_group_reduce<16, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 4: seg_group_reduce<16, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 5: seg_group_reduce<16, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 6: seg_group_reduce<16, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 7: seg_group_reduce<16, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    default: seg_group_reduce<16, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
+                }
+            } else {
+                switch (tt) {
+                    case 1: seg_group_reduce<8, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 2: seg_group_reduce<8, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 3: seg_group_reduce<8, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 4: seg_group_reduce<8, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 5: seg_group_reduce<8, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 6: seg_group_reduce<8, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    case 7: seg_group_reduce<8, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
+                    default: seg_group_reduce<8, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
+                }
+            }
+        }
+    } else {
+        for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
+            switch (min((uint32_t)TAP_GROUP, ntaps - t0)) {
+                case 1: plain_group<1>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 2: plain_group<2>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 3: plain_group<3>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 4: plain_group<4>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 5: plain_group<5>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 6: plain_group<6>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                case 7: plain_group<7>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+                default: plain_group<8>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
+            }
         }
     }
 }
@@ -95,55 +161,7 @@ __global__ void __launch_bounds__(kPlainThreads)
     const uint32_t theta0 = st.theta[ch] + (uint32_t)n0 * w;
     const uint64_t phi0 = reduce_code_phase(st.phi[ch] + n0 * (uint64_t)r);
 
-    const int mode = seg_mode(r);
-    if (mode != 0) {
-        // chip-segment form: mix once, every tap group reads the running sums
-        int4 *slice = s_slices + threadIdx.x * SLICE_INT4;
-        const uint32_t mg = seg_magic(r);
-        if (mode == 16) seg_prefix<16>(x, theta0, w, s_tab, slice);
-        else seg_prefix<8>(x, theta0, w, s_tab, slice);
-        for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
-            const int64_t *tp = s_taps + t0;
-            int32_t *red = s_red + 2 * t0;
-            const uint32_t tt = min((uint32_t)TAP_GROUP, ntaps - t0);
-            if (mode == 16) {
-                switch (tt) {
-                    case 1: seg_group_reduce<16, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 2: seg_group_reduce<16, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 3: seg_group_reduce<16, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 4: seg_group_reduce<16, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 5: seg_group_reduce<16, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 6: seg_group_reduce<16, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 7: seg_group_reduce<16, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    default: seg_group_reduce<16, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
-                }
-            } else {
-                switch (tt) {
-                    case 1: seg_group_reduce<8, 1>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 2: seg_group_reduce<8, 2>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 3: seg_group_reduce<8, 3>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 4: seg_group_reduce<8, 4>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 5: seg_group_reduce<8, 5>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 6: seg_group_reduce<8, 6>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    case 7: seg_group_reduce<8, 7>(slice, phi0, r, mg, tp, s_pair, red); break;
-                    default: seg_group_reduce<8, 8>(slice, phi0, r, mg, tp, s_pair, red); break;
-                }
-            }
-        }
-    } else {
-    for (uint32_t t0 = 0; t0 < ntaps; t0 += TAP_GROUP) {
-        switch (min((uint32_t)TAP_GROUP, ntaps - t0)) {
-            case 1: plain_group<1>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 2: plain_group<2>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 3: plain_group<3>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 4: plain_group<4>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 5: plain_group<5>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 6: plain_group<6>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            case 7: plain_group<7>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-            default: plain_group<8>(x, theta0, w, phi0, r, s_taps, s_code, s_tab, t0, s_red); break;
-        }
-    }
-    }
+    plain_chunk(x, theta0, w, phi0, r, ntaps, s_taps, s_code, s_tab, s_pair, s_slices, s_red);
     __syncthreads();
     int32_t *acc = st.acc + (size_t)ch * ntaps * 2;
     for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x)
@@ -201,6 +219,169 @@ __global__ void k_plain_track3(PlainState st, uint32_t n_ch, uint32_t ntaps, uin
     for (uint32_t i = 0; i < 2 * ntaps; ++i) a[i] = 0;
 }
 
+// Loop constants of RX_EPOCH_CODE: k1 = w0^2 T depends on each epoch's length,
+// so only w0^2 is precomputed and k1 = w0sq (n / fs) is formed per epoch with
+// the same two correctly rounded operations as make_loop_consts.
+struct CodeLoop {
+    double w0sq, k2, kdll, sfs, fs;
+};
+
+// One closed epoch of the bit synchroniser (the rules are in rx_code_state's
+// description in rx.h).
+__device__ void bitsync_step(rx_code_state &b, int32_t ip, uint32_t k) {
+    const uint32_t e = b.epoch;
+    const uint32_t bin = e % 20u;
+    if (b.have_last && ((ip < 0) != (b.last_ip < 0))) {
+        b.hist[bin] += 1;
+        b.n_changes += 1;
+    }
+    b.last_ip = ip;
+    b.have_last = 1;
+    if (b.sync) {
+        if (bin == b.edge) {
+            if (b.bit_active) {
+                b.bits = (b.bits << 1) | (b.bit_acc < 0 ? 1ull : 0ull);
+                b.n_bits += 1;
+            } else {
+                b.first_bit_epoch = e;
+            }
+            b.bit_active = 1;
+            b.bit_acc = 0;
+        }
+        if (b.bit_active) b.bit_acc += ip;
+    } else {
+        uint32_t m = 0;
+        for (uint32_t j = 1; j < 20; ++j)
+            if (b.hist[j] > b.hist[m]) m = j;
+        uint32_t second = 0;
+        for (uint32_t j = 0; j < 20; ++j)
+            if (j != m && b.hist[j] > second) second = b.hist[j];
+        if (b.hist[m] >= k && b.hist[m] >= 3u * second) {
+            b.sync = 1;
+            b.edge = m;
+        }
+    }
+    b.epoch = e + 1;
+}
+
+// RX_EPOCH_CODE, one CTA per channel: walk the call's samples epoch by epoch.
+// From code phase phi the open epoch ends after b = ceil((1023 2^32 - phi) / r)
+// more samples; the CTA correlates min(b, rest) samples with the current words
+// (all threads, chunks of SPT), and at the end of the period thread 0 dumps the
+// sums, runs the loops with T = (epoch samples) / fs, steps the bit
+// synchroniser and loads the new words for the next sample.
+__global__ void __launch_bounds__(kPlainThreads)
+    k_plain_code(const int8_t *__restrict__ iq, uint32_t nsamp, PlainState st, uint32_t ntaps,
+                 uint32_t cap, CodeLoop cl, int tap_e, int tap_p, int tap_l, uint32_t sync_k,
+                 const uint32_t *__restrict__ code_tab, const uint32_t *__restrict__ carrier_tab,
+                 const uint16_t *__restrict__ pair_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int4 *s_slices = reinterpret_cast<int4 *>(smem);
+    uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_slices + kPlainThreads * SLICE_INT4);
+    int64_t *s_taps = reinterpret_cast<int64_t *>(s_pair + PAIR_LEN);
+    uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + ntaps);
+    uint32_t *s_code = s_tab + 64;
+    int32_t *s_red = reinterpret_cast<int32_t *>(s_code + EXT_WORDS);
+    __shared__ uint32_t s_theta, s_w, s_stop;
+    __shared__ unsigned long long s_phi, s_r;
+
+    const uint32_t ch = blockIdx.x;
+    const uint32_t prn = st.prn[ch];
+    for (uint32_t i = threadIdx.x; i < ntaps; i += blockDim.x) s_taps[i] = st.taps[(size_t)ch * ntaps + i];
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) s_tab[i] = carrier_tab[i];
+    for (uint32_t i = threadIdx.x; i < EXT_WORDS; i += blockDim.x)
+        s_code[i] = code_tab[(size_t)prn * EXT_WORDS + i];
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) s_red[i] = st.acc[(size_t)ch * ntaps * 2 + i];
+    for (uint32_t i = threadIdx.x; i < PAIR_LEN / 8; i += blockDim.x)
+        reinterpret_cast<uint4 *>(s_pair)[i] =
+            reinterpret_cast<const uint4 *>(pair_tab + (size_t)prn * PAIR_LEN)[i];
+    // thread 0 owns the loop state for the whole call
+    rx_code_state cs;
+    double v = 0, fcarr = 0, fcode = 0;
+    uint32_t epochs = 0, closed = 0;
+    if (threadIdx.x == 0) {
+        cs = st.cs[ch];
+        v = st.v[ch];
+        fcarr = st.fcarr[ch];
+        fcode = st.fcode[ch];
+        epochs = st.epochs[ch];
+        s_theta = st.theta[ch];
+        s_w = (uint32_t)st.w[ch];
+        s_phi = st.phi[ch];
+        s_r = st.r[ch];
+        s_stop = st.r[ch] >= (1ull << 32) ? 1u : 0u;
+    }
+    __syncthreads();
+
+    uint32_t pos = 0;
+    while (pos < nsamp && !s_stop) {
+        const uint32_t theta = s_theta, w = s_w;
+        const uint64_t phi = s_phi, r = s_r;
+        const uint64_t b = r ? (CODE_MOD - phi + r - 1) / r : ~0ull;
+        const uint32_t seg = (uint32_t)min(b, (uint64_t)(nsamp - pos));
+        const int8_t *blk = iq + 2 * (size_t)pos;
+        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+        for (uint32_t s0 = threadIdx.x * SPT; s0 < seg; s0 += kPlainThreads * SPT) {
+            uint32_t x[SPT];
+            load_chunk(blk, s0, seg, a16, a4, x);
+            plain_chunk(x, theta + s0 * w, w, reduce_code_phase(phi + (uint64_t)s0 * r), (uint32_t)r,
+                        ntaps, s_taps, s_code, s_tab, s_pair, s_slices, s_red);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_theta = theta + seg * w;
+            s_phi = reduce_code_phase(phi + (uint64_t)seg * r);
+            cs.samples_in_epoch += seg;
+            if ((uint64_t)seg == b) {
+                if (closed < cap) {
+                    int32_t *d = st.cdump + ((size_t)ch * cap + closed) * ntaps * 2;
+                    for (uint32_t i = 0; i < 2 * ntaps; ++i) d[i] = s_red[i];
+                    st.clen[(size_t)ch * cap + closed] = cs.samples_in_epoch;
+                } else {
+                    atomicOr(st.cerr, 1u);
+                }
+                LoopConsts lc;
+                lc.k1 = __dmul_rn(cl.w0sq, __ddiv_rn((double)cs.samples_in_epoch, cl.fs));
+                lc.k2 = cl.k2;
+                lc.kdll = cl.kdll;
+                lc.sfs = cl.sfs;
+                LoopOut o = loop_update(v, s_red[2 * tap_e], s_red[2 * tap_e + 1], s_red[2 * tap_p],
+                                        s_red[2 * tap_p + 1], s_red[2 * tap_l], s_red[2 * tap_l + 1],
+                                        s_taps[tap_e], s_taps[tap_l], lc);
+                v = o.v;
+                fcarr = o.f_carr;
+                fcode = o.f_code;
+                epochs += 1;
+                bitsync_step(cs, s_red[2 * tap_p], sync_k);
+                for (uint32_t i = 0; i < 2 * ntaps; ++i) s_red[i] = 0;
+                cs.samples_in_epoch = 0;
+                closed += 1;
+                s_w = (uint32_t)o.w;
+                s_r = o.r;
+                if (o.r >= (1ull << 32)) {
+                    atomicOr(st.cerr, 2u);
+                    s_stop = 1;
+                }
+            }
+        }
+        __syncthreads();
+        pos += seg;
+    }
+    if (threadIdx.x == 0) {
+        st.cs[ch] = cs;
+        st.v[ch] = v;
+        st.fcarr[ch] = fcarr;
+        st.fcode[ch] = fcode;
+        st.epochs[ch] = epochs;
+        st.theta[ch] = s_theta;
+        st.w[ch] = (int32_t)s_w;
+        st.phi[ch] = s_phi;
+        st.r[ch] = s_r;
+        st.cnum[ch] = min(closed, cap);
+    }
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) st.acc[(size_t)ch * ntaps * 2 + i] = s_red[i];
+}
+
 }  // namespace
 
 struct rx_handle_s {
@@ -213,6 +394,7 @@ struct rx_handle_s {
     int8_t *d_stage = nullptr; // staging buffer for host input
     uint64_t n_since_fold = 0;
     uint64_t n_accum = 0;
+    uint32_t code_cap = 0;     // RX_EPOCH_CODE: epochs per channel and call the ring holds
     std::string err;
 };
 
@@ -236,7 +418,8 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
         cfg->tap_early < 0 || cfg->tap_prompt < 0 || cfg->tap_late < 0 ||
         (uint32_t)cfg->tap_early >= cfg->max_taps || (uint32_t)cfg->tap_prompt >= cfg->max_taps ||
         (uint32_t)cfg->tap_late >= cfg->max_taps || !(cfg->pll_bn_hz >= 0) || !(cfg->dll_bn_hz >= 0) ||
-        cfg->loop_set > RX_LOOPS_TABLE3 || !(cfg->fll_bn_hz >= 0))
+        cfg->loop_set > RX_LOOPS_TABLE3 || !(cfg->fll_bn_hz >= 0) || cfg->epoch_mode > RX_EPOCH_CODE ||
+        (cfg->epoch_mode == RX_EPOCH_CODE && cfg->loop_set != RX_LOOPS_PLL2_DLL1))
         return RX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= cfg->device || cfg->device < 0) {
@@ -268,6 +451,16 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
            o_prn = take(C * 4), o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8),
            o_ep = take(C * 4), o_taps = take(C * T * 8), o_acc = take(C * T * 8),
            o_ext = take(C * sizeof(LoopExt)), o_stage = take(2 * (size_t)cfg->max_block_samples + 64);
+    // RX_EPOCH_CODE: a ring of the epochs each channel closes in one call.  An epoch
+    // lasts 1023 2^32 / r samples; the ring allows code rates up to 1.1 x 1.023 Mchip/s.
+    if (cfg->epoch_mode == RX_EPOCH_CODE) {
+        uint64_t min_epoch = (uint64_t)std::floor(0.9 * cfg->fs_hz / 1000.0);
+        if (min_epoch == 0) min_epoch = 1;
+        h->code_cap = (uint32_t)(cfg->max_block_samples / min_epoch + 2);
+    }
+    const size_t E = h->code_cap;
+    size_t o_cs = take(C * sizeof(rx_code_state)), o_cdump = take(C * E * T * 8 + 8),
+           o_clen = take(C * E * 4 + 4), o_cnum = take(C * 4), o_cerr = take(4);
     if (cudaMalloc(&h->d_block, off) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -287,6 +480,11 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
     h->st.acc = (int32_t *)(b + o_acc);
     h->st.ext = (LoopExt *)(b + o_ext);
     h->d_stage = (int8_t *)(b + o_stage);
+    h->st.cs = (rx_code_state *)(b + o_cs);
+    h->st.cdump = (int32_t *)(b + o_cdump);
+    h->st.clen = (uint32_t *)(b + o_clen);
+    h->st.cnum = (uint32_t *)(b + o_cnum);
+    h->st.cerr = (uint32_t *)(b + o_cerr);
     if (cudaMemsetAsync(h->d_block, 0, off, h->stream) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(h->d_block);
@@ -350,6 +548,8 @@ extern "C" rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn
     RX_CUDA_TRY(cudaMemcpy(h->st.taps, tap_offsets, (size_t)n * ntaps * 8, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemset(h->st.acc, 0, (size_t)n * ntaps * 8), E);
     RX_CUDA_TRY(cudaMemset(h->st.ext, 0, (size_t)n * sizeof(LoopExt)), E);
+    RX_CUDA_TRY(cudaMemset(h->st.cs, 0, (size_t)n * sizeof(rx_code_state)), E);
+    RX_CUDA_TRY(cudaMemset(h->st.cnum, 0, (size_t)n * 4), E);
     h->n_ch = n;
     h->n_taps = ntaps;
     h->n_since_fold = 0;
@@ -360,6 +560,8 @@ extern "C" rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn
 extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp) {
     if (!h) return RX_EINVAL;
     if (h->n_ch == 0) return set_err(h, RX_ESTATE, "rx_set_channels has not been called");
+    if (h->cfg.epoch_mode != RX_EPOCH_BLOCKS)
+        return set_err(h, RX_ESTATE, "RX_EPOCH_CODE handle: use rx_track_code");
     if (!iq || nsamp == 0 || nsamp > h->cfg.max_block_samples)
         return set_err(h, RX_EINVAL, rxh::fmt("nsamp=%u outside 1..%u", nsamp, h->cfg.max_block_samples));
     cudaSetDevice(h->cfg.device);
@@ -393,6 +595,8 @@ extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp)
 
 extern "C" rx_status rx_track_epoch(rx_handle h) {
     if (!h) return RX_EINVAL;
+    if (h->cfg.epoch_mode != RX_EPOCH_BLOCKS)
+        return set_err(h, RX_ESTATE, "RX_EPOCH_CODE handle: use rx_track_code");
     if (h->n_ch == 0 || h->n_accum == 0)
         return set_err(h, RX_ESTATE, "no samples correlated since the last boundary");
     cudaSetDevice(h->cfg.device);
@@ -557,5 +761,95 @@ extern "C" rx_status rx_write_health(rx_handle h, const rx_channel_health *in, u
     cudaSetDevice(h->cfg.device);
     RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
     if (n) RX_CUDA_TRY(cudaMemcpy(h->st.ext, ex.data(), n * sizeof(LoopExt), cudaMemcpyHostToDevice), h->err);
+    return RX_OK;
+}
+
+extern "C" rx_status rx_track_code(rx_handle h, const int8_t *iq, uint32_t nsamp) {
+    if (!h) return RX_EINVAL;
+    if (h->cfg.epoch_mode != RX_EPOCH_CODE)
+        return set_err(h, RX_ESTATE, "rx_track_code needs epoch_mode RX_EPOCH_CODE");
+    if (h->n_ch == 0) return set_err(h, RX_ESTATE, "rx_set_channels has not been called");
+    if (!iq || nsamp == 0 || nsamp > h->cfg.max_block_samples)
+        return set_err(h, RX_EINVAL, rxh::fmt("nsamp=%u outside 1..%u", nsamp, h->cfg.max_block_samples));
+    cudaSetDevice(h->cfg.device);
+    std::string &E = h->err;
+    const int8_t *src = iq;
+    if (rxh::is_device_pointer(iq)) {
+        if (((uintptr_t)iq & 1) != 0) return set_err(h, RX_EINVAL, "device iq must be 2-byte aligned");
+    } else {
+        RX_CUDA_TRY(cudaMemcpyAsync(h->d_stage, iq, 2 * (size_t)nsamp, cudaMemcpyHostToDevice, h->stream), E);
+        src = h->d_stage;
+    }
+    const double fs = h->cfg.fs_hz;
+    const LoopConsts base = make_loop_consts(fs, 1, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz);
+    CodeLoop cl;
+    const double w0 = h->cfg.pll_bn_hz / 0.53;
+    cl.w0sq = w0 * w0;
+    cl.k2 = base.k2;
+    cl.kdll = base.kdll;
+    cl.sfs = base.sfs;
+    cl.fs = fs;
+    const uint32_t sync_k = h->cfg.bitsync_count ? h->cfg.bitsync_count : 8u;
+    size_t smem = (size_t)kPlainThreads * SLICE_INT4 * 16 + PAIR_LEN * 2 + (size_t)h->n_taps * 8 +
+                  64 * 4 + EXT_WORDS * 4 + (size_t)h->n_taps * 8;
+    RX_CUDA_TRY(cudaMemsetAsync(h->st.cerr, 0, 4, h->stream), E);
+    k_plain_code<<<h->n_ch, kPlainThreads, smem, h->stream>>>(src, nsamp, h->st, h->n_taps, h->code_cap, cl,
+                                                             h->cfg.tap_early, h->cfg.tap_prompt,
+                                                             h->cfg.tap_late, sync_k, h->tables->code,
+                                                             h->tables->tab, h->tables->pair);
+    RX_CUDA_TRY(cudaGetLastError(), E);
+    uint32_t cerr = 0;
+    RX_CUDA_TRY(cudaMemcpyAsync(&cerr, h->st.cerr, 4, cudaMemcpyDeviceToHost, h->stream), E);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), E);
+    if (cerr & 2u) return set_err(h, RX_EINVAL, "a channel's code word reached 2^32");
+    if (cerr & 1u)
+        return set_err(h, RX_EINVAL, rxh::fmt("a channel closed more than %u epochs in one call", h->code_cap));
+    return RX_OK;
+}
+
+extern "C" rx_status rx_read_code_epochs(rx_handle h, int32_t *dumps, uint32_t *epoch_samples,
+                                         uint32_t *n_epochs, uint32_t max_epochs) {
+    if (!h || !dumps || !epoch_samples || !n_epochs) return RX_EINVAL;
+    if (h->cfg.epoch_mode != RX_EPOCH_CODE) return set_err(h, RX_ESTATE, "not an RX_EPOCH_CODE handle");
+    const uint32_t n = h->n_ch, T = h->n_taps, cap = h->code_cap;
+    cudaSetDevice(h->cfg.device);
+    std::string &E = h->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), E);
+    RX_CUDA_TRY(cudaMemcpy(n_epochs, h->st.cnum, (size_t)n * 4, cudaMemcpyDeviceToHost), E);
+    for (uint32_t c = 0; c < n; ++c)
+        if (n_epochs[c] > max_epochs)
+            return set_err(h, RX_EINVAL, rxh::fmt("channel %u closed %u epochs > max_epochs %u", c,
+                                                  n_epochs[c], max_epochs));
+    std::memset(dumps, 0, (size_t)n * max_epochs * T * 8);
+    std::memset(epoch_samples, 0, (size_t)n * max_epochs * 4);
+    for (uint32_t c = 0; c < n; ++c) {
+        if (n_epochs[c] == 0) continue;
+        RX_CUDA_TRY(cudaMemcpy(dumps + (size_t)c * max_epochs * T * 2, h->st.cdump + (size_t)c * cap * T * 2,
+                               (size_t)n_epochs[c] * T * 8, cudaMemcpyDeviceToHost), E);
+        RX_CUDA_TRY(cudaMemcpy(epoch_samples + (size_t)c * max_epochs, h->st.clen + (size_t)c * cap,
+                               (size_t)n_epochs[c] * 4, cudaMemcpyDeviceToHost), E);
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_read_code_state(rx_handle h, rx_code_state *out, uint32_t cap) {
+    if (!h || !out) return RX_EINVAL;
+    if (cap < h->n_ch) return set_err(h, RX_EINVAL, "cap < channels");
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    if (h->n_ch)
+        RX_CUDA_TRY(cudaMemcpy(out, h->st.cs, h->n_ch * sizeof(rx_code_state), cudaMemcpyDeviceToHost), h->err);
+    return RX_OK;
+}
+
+extern "C" rx_status rx_write_code_state(rx_handle h, const rx_code_state *in, uint32_t n) {
+    if (!h || !in) return RX_EINVAL;
+    if (n != h->n_ch) return set_err(h, RX_EINVAL, "n != channels");
+    for (uint32_t c = 0; c < n; ++c)
+        if (in[c].edge >= 20 || in[c].sync > 1 || in[c].bit_active > 1 || in[c].have_last > 1)
+            return set_err(h, RX_EINVAL, rxh::fmt("channel %u: bit-sync state out of range", c));
+    cudaSetDevice(h->cfg.device);
+    RX_CUDA_TRY(cudaStreamSynchronize(h->stream), h->err);
+    if (n) RX_CUDA_TRY(cudaMemcpy(h->st.cs, in, n * sizeof(rx_code_state), cudaMemcpyHostToDevice), h->err);
     return RX_OK;
 }

@@ -25,6 +25,8 @@ RX_SCHED_STATIC = 1
 RX_SCHED_PIPE = 2
 RX_SCHED_BALANCED = 3
 RX_WAIT_TEST_STALL = 1
+RX_EPOCH_BLOCKS = 0
+RX_EPOCH_CODE = 1
 RX_LOOPS_PLL2_DLL1 = 0
 RX_LOOPS_TABLE3 = 1
 
@@ -41,7 +43,21 @@ class rx_config(C.Structure):
                 ("pll_bn_hz", C.c_double), ("dll_bn_hz", C.c_double),
                 ("tap_early", C.c_int32), ("tap_prompt", C.c_int32), ("tap_late", C.c_int32),
                 ("device", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("loop_set", C.c_uint32), ("health_window", C.c_uint32), ("fll_bn_hz", C.c_double)]
+                ("loop_set", C.c_uint32), ("health_window", C.c_uint32), ("fll_bn_hz", C.c_double),
+                ("epoch_mode", C.c_uint32), ("bitsync_count", C.c_uint32)]
+
+
+class rx_code_state(C.Structure):
+    _fields_ = [("last_ip", C.c_int32), ("have_last", C.c_uint32), ("hist", C.c_uint32 * 20),
+                ("n_changes", C.c_uint32), ("epoch", C.c_uint32), ("sync", C.c_uint32),
+                ("edge", C.c_uint32), ("bit_active", C.c_uint32), ("n_bits", C.c_uint32),
+                ("bit_acc", C.c_int64), ("bits", C.c_uint64), ("first_bit_epoch", C.c_uint32),
+                ("samples_in_epoch", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["hist"] = list(self.hist)
+        return d
 
 
 class rx_channel_health(C.Structure):
@@ -142,6 +158,10 @@ SIGNATURES = [
     ("rx_write_state", C.c_int, [P, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_read_health", C.c_int, [P, C.POINTER(rx_channel_health), C.c_uint32]),
     ("rx_write_health", C.c_int, [P, C.POINTER(rx_channel_health), C.c_uint32]),
+    ("rx_track_code", C.c_int, [P, P, C.c_uint32]),
+    ("rx_read_code_epochs", C.c_int, [P, P, P, P, C.c_uint32]),
+    ("rx_read_code_state", C.c_int, [P, C.POINTER(rx_code_state), C.c_uint32]),
+    ("rx_write_code_state", C.c_int, [P, C.POINTER(rx_code_state), C.c_uint32]),
     ("rx_last_error", C.c_char_p, [P]),
     ("rx_batch_create", C.c_int, [C.POINTER(rx_receiver_desc), C.c_uint32, C.c_uint32, C.c_int32,
                                   P, C.POINTER(P)]),
@@ -253,11 +273,12 @@ def _check(h, s, err_fn):
 def rx_create(fs_hz: float, max_block_samples: int, max_channels: int, max_taps: int,
               pll_bn_hz: float = 15.0, dll_bn_hz: float = 1.0, tap_early: int = 2,
               tap_prompt: int = 1, tap_late: int = 0, device: int = 0, stream=None,
-              loop_set: int = 0, health_window: int = 0, fll_bn_hz: float = 0.0):
+              loop_set: int = 0, health_window: int = 0, fll_bn_hz: float = 0.0,
+              epoch_mode: int = 0, bitsync_count: int = 0):
     lib = load()
     cfg = rx_config(fs_hz, max_block_samples, max_channels, max_taps, pll_bn_hz, dll_bn_hz,
                     tap_early, tap_prompt, tap_late, device, _stream_handle(stream), loop_set,
-                    health_window, fll_bn_hz)
+                    health_window, fll_bn_hz, epoch_mode, bitsync_count)
     h = P()
     s = lib.rx_create(C.byref(cfg), C.byref(h))
     if s != RX_OK:
@@ -335,6 +356,39 @@ def rx_write_health(h, health) -> None:
     n = len(health)
     arr = (rx_channel_health * n)(*health)
     _check(h, lib.rx_write_health(h, arr, n), lib.rx_last_error)
+
+
+def rx_track_code(h, iq, nsamp: int | None = None) -> None:
+    """RX_EPOCH_CODE: correlate nsamp samples, closing code-period epochs as they end."""
+    lib = load()
+    if nsamp is None:
+        nsamp = (iq.numel() if hasattr(iq, "numel") else iq.size) // 2
+    _check(h, lib.rx_track_code(h, _ptr(iq), nsamp), lib.rx_last_error)
+
+
+def rx_read_code_epochs(h, n_ch: int, n_taps: int, max_epochs: int):
+    """(dumps [n_ch, max_epochs, n_taps, 2], epoch sample counts [n_ch, max_epochs],
+    epochs closed per channel [n_ch]) of the last rx_track_code."""
+    lib = load()
+    d = np.zeros((n_ch, max_epochs, n_taps, 2), np.int32)
+    ln = np.zeros((n_ch, max_epochs), np.uint32)
+    n = np.zeros(n_ch, np.uint32)
+    _check(h, lib.rx_read_code_epochs(h, _ptr(d), _ptr(ln), _ptr(n), max_epochs), lib.rx_last_error)
+    return d, ln, n
+
+
+def rx_read_code_state(h, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_code_state * n_ch)()
+    _check(h, lib.rx_read_code_state(h, arr, n_ch), lib.rx_last_error)
+    return list(arr)
+
+
+def rx_write_code_state(h, states) -> None:
+    lib = load()
+    n = len(states)
+    arr = (rx_code_state * n)(*states)
+    _check(h, lib.rx_write_code_state(h, arr, n), lib.rx_last_error)
 
 
 def rx_last_error(h) -> str:
