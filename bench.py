@@ -278,6 +278,39 @@ def plain_form(rx, receivers, buf, offs, dev, stream, n_rx=4, n_blocks=100) -> d
             "launches": 2 * n_rx * n_blocks}
 
 
+def code_epoch_form(rx, receivers, buf, offs, dev, stream, n_rx=4, n_blocks=100) -> dict:
+    """The plain form in code-period epochs (RX_EPOCH_CODE): one rx_track_code call per
+    receiver per 1 ms block; each channel closes its epochs where its own code period
+    ends, runs its loops there and steps its bit synchroniser."""
+    import torch
+    from paper_1907_00463_gb300 import synth
+    handles = []
+    for r in receivers[:n_rx]:
+        h = rx.rx_create(r.fs, r.block_samples, len(r.channels), r.n_taps, r.pll_bn, r.dll_bn,
+                         r.tap_early, r.tap_prompt, r.tap_late, device=dev, stream=stream,
+                         epoch_mode=rx.RX_EPOCH_CODE)
+        rx.rx_set_channels(h, *synth.channel_arrays(r))
+        handles.append(h)
+    N = receivers[0].block_samples
+    views = [buf[int(o):int(o) + 2 * N * n_blocks].view(-1, 2) for o in offs[:n_rx]]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(n_blocks):
+        for h, v in zip(handles, views):
+            rx.rx_track_code(h, v[b * N:(b + 1) * N], N)
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    epochs = sum(s.epochs for h, r in zip(handles, receivers) for s in rx.rx_read_state(h, len(r.channels)))
+    synced = sum(c.sync for h, r in zip(handles, receivers) for c in rx.rx_read_code_state(h, len(r.channels)))
+    for h in handles:
+        rx.rx_destroy(h)
+    sc = sample_channels(receivers[:n_rx], n_blocks)
+    return {"value": sc / dt / 1e6, "unit": "Msample*channel/s",
+            "sample": f"{n_rx} receivers x {n_blocks} blocks, one synchronous launch per receiver-block",
+            "epochs_closed": int(epochs), "channels_bit_synced": int(synced),
+            "launches": n_rx * n_blocks}
+
+
 def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_blocks=100,
                 probe_counts=(1024, 2048, 4096, 8192), probe_s=1.0) -> dict:
     """The serving workload: n_streams streams at 8.184 MHz, 12 channels x 5 taps, 1 ms blocks
@@ -583,6 +616,7 @@ def run_ours(args):
     if rank == 0 and world == 1:
         if not args.no_plain:
             plain = plain_form(rx, receivers, buf, offs, local, stream)
+            plain["code_epochs"] = code_epoch_form(rx, receivers, buf, offs, local, stream)
         if not args.no_cpu_baseline:
             host_cache = {}
 
