@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(kPlainThreads)
         const uint32_t seg = (uint32_t)min(b, (uint64_t)(nsamp - pos));
         const int8_t *blk = iq + 2 * (size_t)pos;
         const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-        for (uint32_t s0 = threadIdx.x * SPT; s0 < seg; s0 += kPlainThreads * SPT) {
+        // every thread takes part in every round: plain_chunk reduces across full warps,
+        // and a chunk past the segment's end loads as zeros (and adds nothing)
+        for (uint32_t base = 0; base < seg; base += kPlainThreads * SPT) {
+            const uint32_t s0 = base + threadIdx.x * SPT;
             uint32_t x[SPT];
             load_chunk(blk, s0, seg, a16, a4, x);
             plain_chunk(x, theta + s0 * w, w, reduce_code_phase(phi + (uint64_t)s0 * r), (uint32_t)r,
