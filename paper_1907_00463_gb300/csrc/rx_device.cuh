@@ -225,16 +225,7 @@ __device__ __forceinline__ void corr_chunk(const uint32_t (&x)[SPT], uint32_t th
 
 constexpr int PAIR_BASE = 64;     // pair table entry of chip c is c + PAIR_BASE
 constexpr int PAIR_LEN = 1168;    // chips -64 .. 1103
-constexpr int SLICE_INT4 = 9;     // shared memory reserved per thread for running sums (16 B units)
-
-// A thread's running sums: 16 int2 entries, warp-interleaved (entry e of lane l
-// at int2 index e * 32 + l of its warp's 512-entry region), so that every lane
-// reading an entry of its own choice (the chip boundary differs per lane) lands
-// in its own bank pair: two wavefronts per warp-wide 64-bit read, whatever the
-// entries.  Uses 128 of the SLICE_INT4 * 16 bytes reserved per thread.
-__device__ __forceinline__ int2 *seg_slice(int4 *slices) {
-    return reinterpret_cast<int2 *>(slices) + (threadIdx.x >> 5) * 512 + (threadIdx.x & 31);
-}
+constexpr int SLICE_INT4 = 9;     // per-thread running-sum slice: 8 int4 + 1 pad (bank spread)
 
 // 16 if a 16-sample run crosses at most one chip boundary per tap, 8 if an 8-sample
 // run does, 0 if neither (the direct form is used then).
@@ -248,11 +239,11 @@ __device__ __forceinline__ uint32_t seg_magic(uint32_t r) {
     return (uint32_t)(((1ull << 32) + r - 1) / r);
 }
 
-// Mix a chunk and store running sums: entry e (pre[32 e]) holds the sums of I', Q'
+// Mix a chunk and store running sums: viewed as int2, entry e holds the sums of I', Q'
 // over samples 0..e of its run (S = 16: one run; S = 8: runs 0..7 and 8..15 restart).
 template <int S>
 __device__ __forceinline__ void seg_prefix(const uint32_t (&x)[SPT], uint32_t theta0, uint32_t w,
-                                           const uint32_t *tab, int2 *pre) {
+                                           const uint32_t *tab, int4 *slice) {
     uint32_t th = theta0;
     int32_t sI = 0, sQ = 0;
 #pragma unroll
@@ -270,8 +261,7 @@ __device__ __forceinline__ void seg_prefix(const uint32_t (&x)[SPT], uint32_t th
         th += w;
         sI = __dp2a_lo((int)x[i + 1], (int)e1, sI);
         sQ = __dp2a_hi((int)x[i + 1], (int)e1, sQ);
-        pre[32 * i] = make_int2(aI, aQ);
-        pre[32 * (i + 1)] = make_int2(sI, sQ);
+        slice[i >> 1] = make_int4(aI, aQ, sI, sQ);
     }
 }
 
@@ -280,7 +270,7 @@ __device__ __forceinline__ void seg_run_taps(const int2 *pre, uint64_t phi0, uin
                                              uint32_t magic, const int64_t *off,
                                              const uint16_t *pair, int32_t (&aI)[TT],
                                              int32_t (&aQ)[TT]) {
-    const int2 tot = pre[32 * (S - 1)];
+    const int2 tot = pre[S - 1];
 #pragma unroll
     for (int k = 0; k < TT; ++k) {
         const int64_t p = (int64_t)phi0 + off[k];
@@ -289,7 +279,7 @@ __device__ __forceinline__ void seg_run_taps(const int2 *pre, uint64_t phi0, uin
         // samples i >= 1 still on chip c0: i r <= nf; their count, capped at S - 1
         uint32_t q = min(__umulhi(nf, magic), (uint32_t)(S - 1));
         if (q * r > nf) q -= 1;
-        const int2 pb = pre[32 * q];                       // P_b with b = q + 1
+        const int2 pb = pre[q];                            // P_b with b = q + 1
         const uint32_t e = pair[c0 + PAIR_BASE];
         const int32_t g1 = (int32_t)prmt(e, 0u, 0x8880u);  // g(c0 + 1)
         const int32_t dg = (int32_t)prmt(e, 0u, 0x9991u);  // g(c0) - g(c0 + 1)
@@ -300,21 +290,22 @@ __device__ __forceinline__ void seg_run_taps(const int2 *pre, uint64_t phi0, uin
 
 // Taps of one chunk from its running sums; phi0 is the code phase of sample 0.
 template <int S, int TT>
-__device__ __forceinline__ void seg_taps(const int2 *pre, uint64_t phi0, uint32_t r,
+__device__ __forceinline__ void seg_taps(const int4 *slice, uint64_t phi0, uint32_t r,
                                          uint32_t magic, const int64_t *off, const uint16_t *pair,
                                          int32_t (&aI)[TT], int32_t (&aQ)[TT]) {
+    const int2 *pre = reinterpret_cast<const int2 *>(slice);
     if (S == 16) {
         seg_run_taps<16, TT>(pre, phi0, r, magic, off, pair, aI, aQ);
     } else {
         seg_run_taps<8, TT>(pre, phi0, r, magic, off, pair, aI, aQ);
-        seg_run_taps<8, TT>(pre + 32 * 8, phi0 + 8ull * r, r, magic, off, pair, aI, aQ);
+        seg_run_taps<8, TT>(pre + 8, phi0 + 8ull * r, r, magic, off, pair, aI, aQ);
     }
 }
 
 // Taps of one tap group for one chunk, reduced over the warp and added to s_red
 // ([TT][2] int32 in shared memory).  Every lane of the warp must call it.
 template <int S, int TT>
-__device__ __forceinline__ void seg_group_reduce(const int2 *slice, uint64_t ph0, uint32_t r,
+__device__ __forceinline__ void seg_group_reduce(const int4 *slice, uint64_t ph0, uint32_t r,
                                                  uint32_t magic, const int64_t *s_taps,
                                                  const uint16_t *s_pair, int32_t *s_red) {
     int32_t aI[TT], aQ[TT];

@@ -48,7 +48,7 @@ struct ItemSmem {
     int32_t *acc;      // [cpg * mt * 2]
     uint32_t *theta, *w, *ab, *r;  // [cpg]
     uint64_t *phi;     // [cpg]
-    int4 *slices;      // NT x SLICE_INT4 x 16 B, running sums (seg_slice)
+    int4 *slices;      // [NT][SLICE_INT4]
     uint16_t *pair;    // [cpg][PAIR_LEN]
 };
 
@@ -123,7 +123,7 @@ __device__ __forceinline__ void item_seg(const int8_t *blk, uint32_t N, bool a16
                                          uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                          uint32_t magic, const int64_t *s_taps,
                                          const uint16_t *s_pair, const uint32_t *s_tab,
-                                         int2 *slice, int32_t *s_red, uint32_t rot = 0,
+                                         int4 *slice, int32_t *s_red, uint32_t rot = 0,
                                          uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     int32_t aI[TT], aQ[TT];
 #pragma unroll
@@ -156,7 +156,7 @@ __device__ __forceinline__ void item_seg_many(const int8_t *blk, uint32_t N, boo
                                               uint32_t theta, uint32_t w, uint64_t phi,
                                               uint32_t r, uint32_t magic, uint32_t nt,
                                               const int64_t *s_taps, const uint16_t *s_pair,
-                                              const uint32_t *s_tab, int2 *slice,
+                                              const uint32_t *s_tab, int4 *slice,
                                               int32_t *s_red, uint32_t rot = 0, uint32_t jbeg = 0,
                                               uint32_t jend = 0xffffffffu) {
     const uint32_t jlim = min(jend, (N + SPT - 1) / SPT);
@@ -195,7 +195,7 @@ template <int S, int NT, bool SH = false>
 __device__ __forceinline__ void channel_seg(const int8_t *blk, uint32_t N, bool a16, bool a4,
                                             uint32_t theta, uint32_t w, uint64_t phi, uint32_t r,
                                             uint32_t nt, const int64_t *tp, const uint16_t *pr,
-                                            const uint32_t *s_tab, int2 *slice, int32_t *red,
+                                            const uint32_t *s_tab, int4 *slice, int32_t *red,
                                             uint32_t rot = 0, uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
     const uint32_t mg = seg_magic(r);
     switch (nt) {
@@ -263,7 +263,7 @@ __device__ __forceinline__ void correlate_channel_at(uint32_t j, uint32_t nt, ui
                                                      const ItemSmem &sm, int32_t *red, uint32_t theta,
                                                      uint32_t w, uint64_t phi, uint32_t r, uint32_t rot = 0,
                                                      uint32_t jbeg = 0, uint32_t jend = 0xffffffffu) {
-    int2 *slice = seg_slice(sm.slices);
+    int4 *slice = sm.slices + threadIdx.x * SLICE_INT4;
     const int64_t *tp = sm.taps + (size_t)j * nt;
     const int mode = seg_mode(r);
     if (mode == 16) {

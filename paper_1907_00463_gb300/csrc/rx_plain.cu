@@ -73,7 +73,7 @@ __device__ __forceinline__ void plain_chunk(const uint32_t (&x)[SPT], uint32_t t
     const int mode = seg_mode(r);
     if (mode != 0) {
         // chip-segment form: mix once, every tap group reads the running sums
-        int2 *slice = seg_slice(s_slices);
+        int4 *slice = s_slices + threadIdx.x * SLICE_INT4;
         const uint32_t mg = seg_magic(r);
         if (mode == 16) seg_prefix<16>(x, theta0, w, s_tab, slice);
         else seg_prefix<8>(x, theta0, w, s_tab, slice);
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kPlainThreads)
                       const uint32_t *__restrict__ code_tab, const uint32_t *__restrict__ carrier_tab,
                       const uint16_t *__restrict__ pair_tab) {
     extern __shared__ __align__(16) unsigned char smem[];
-    int4 *s_slices = reinterpret_cast<int4 *>(smem);            // running sums (seg_slice)
+    int4 *s_slices = reinterpret_cast<int4 *>(smem);                                 // [threads][SLICE_INT4]
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_slices + kPlainThreads * SLICE_INT4);  // [PAIR_LEN]
     int64_t *s_taps = reinterpret_cast<int64_t *>(s_pair + PAIR_LEN);               // [ntaps]
     uint32_t *s_tab = reinterpret_cast<uint32_t *>(s_taps + ntaps);                  // [64]
