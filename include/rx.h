@@ -308,6 +308,12 @@ typedef struct {
     double pll_bn_hz;
     double dll_bn_hz;
     int32_t tap_early, tap_prompt, tap_late;
+    uint32_t loop_set;           /* RX_LOOPS_PLL2_DLL1 (0) or RX_LOOPS_TABLE3 (1), as in rx_config;
+                                    RX_LOOPS_TABLE3 runs in the batched form's dynamic, static and
+                                    pipelined schedules (RX_EINVAL for the balanced schedule, the
+                                    served form and rx_track_static) */
+    uint32_t health_window;      /* RX_LOOPS_TABLE3: integrations per C/N0 / lock estimate */
+    double fll_bn_hz;            /* RX_LOOPS_TABLE3: FLL bandwidth; dll_bn_hz is a 2nd-order DLL's */
 } rx_receiver_desc;
 
 typedef struct rx_batch_s *rx_batch;
@@ -355,6 +361,11 @@ rx_status rx_batch_read_dumps(rx_batch b, uint32_t rx, int32_t *out,
                               size_t cap, uint32_t *n_dumps);
 
 /* Per-channel state of receiver rx after the last run.  Synchronises. */
+/* RX_LOOPS_TABLE3 state and health indicators of receiver rx's channels
+ * (cap >= n_channels; zero for a receiver with RX_LOOPS_PLL2_DLL1).
+ * Synchronises the batch's stream. */
+rx_status rx_batch_read_health(rx_batch b, uint32_t rx, rx_channel_health *out, uint32_t cap);
+
 rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
                               uint32_t cap);
 

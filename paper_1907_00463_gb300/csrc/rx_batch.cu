@@ -45,6 +45,7 @@ struct BatchState {
     uint32_t *epochs;      // dumps done
     uint32_t *acc_blocks;  // blocks integrated since the last dump
     int32_t *acc;          // [tap_base*2 ...]: running sums when L > 1
+    LoopExt *ext;          // RX_LOOPS_TABLE3 extra loop state and health
 };
 
 struct BatchArgs {
@@ -166,9 +167,7 @@ __global__ void __launch_bounds__(NT, (NT <= 256 ? 768 / NT : 1)) k_batch_static
                 sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
                 if (boundary) {
                     const int64_t *tp = sm.taps + (size_t)j * nt;
-                    LoopOut o = loop_update(s_v[j], A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p],
-                                            A[2 * gd.tap_p + 1], A[2 * gd.tap_l], A[2 * gd.tap_l + 1],
-                                            tp[gd.tap_e], tp[gd.tap_l], gd.lc);
+                    LoopOut o = close_loops(gd, j, s_v[j], A, tp, gd.lc);
                     s_v[j] = o.v;
                     s_fc[j] = o.f_carr;
                     s_fk[j] = o.f_code;
@@ -262,6 +261,15 @@ namespace {
 rx_status berr(rx_batch b, rx_status s, const std::string &m) {
     if (b) b->err = m;
     return s;
+}
+
+// Some receiver runs Table 3's full loop set: its extra per-channel state has one
+// writer per channel, which the balanced schedule's duplicated loop updates of cut
+// channels would break.
+bool any_table3(const rx_batch b) {
+    for (const rx_receiver_desc &d : b->rx)
+        if (d.loop_set == RX_LOOPS_TABLE3) return true;
+    return false;
 }
 
 uint32_t default_cpg(const rx_batch b) {
@@ -373,6 +381,13 @@ GroupDesc make_group(rx_batch b, uint32_t r, uint32_t c0, uint32_t nch) {
     g.dump_wrap = 0;
     g.src = r;
     g.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz, d.dll_bn_hz);
+    if (d.loop_set == RX_LOOPS_TABLE3) {
+        g.ext = b->st.ext + ch;
+        g.lc3 = make_loop_consts3(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
+                                  d.dll_bn_hz, d.fll_bn_hz);
+        g.loop_set = RX_LOOPS_TABLE3;
+        g.window = d.health_window;
+    }
     return g;
 }
 
@@ -607,8 +622,9 @@ rx_status build_groups(rx_batch b) {
         for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
         const uint32_t fw = pipe_filter_warps(b->cpg);
         const uint32_t sb = (uint32_t)pipe_stage_bytes(max_n);
-        const int occ_st = pipe_occupancy(b->threads, fw, true, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, sb));
-        const int occ_gl = pipe_occupancy(b->threads, fw, false, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, 0));
+        const bool t3 = any_table3(b);
+        const int occ_st = t3 ? 0 : pipe_occupancy(b->threads, fw, true, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, sb));
+        const int occ_gl = pipe_occupancy(b->threads, fw, false, pipe_smem_bytes(b->cpg, b->max_taps, b->threads, 0), t3);
         const bool one_wave = (uint64_t)occ_st * b->tables->sm_count >= b->G;
         b->pipe_stage = (occ_st > 0 && (one_wave || occ_st >= occ_gl)) ? sb : 0u;
         occ = b->pipe_stage ? occ_st : occ_gl;
@@ -659,7 +675,7 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     }
     if (b->schedule == RX_SCHED_PIPE) {
         PipeArgs pa{b->d_groups, b->d_rxoff, iq,       ba.tb,      ba.err,        b->timeout_ns,
-                    n_blocks,    b->cpg,     b->max_taps, b->stall, b->pipe_stage};
+                    n_blocks,    b->cpg,     b->max_taps, b->stall, b->pipe_stage, any_table3(b) ? 1u : 0u};
         cudaError_t ce = pipe_launch(b->threads, pipe_filter_warps(b->cpg), b->G,
                                      pipe_smem_bytes(b->cpg, b->max_taps, b->threads, b->pipe_stage), b->stream,
                                      pa);
@@ -708,7 +724,8 @@ extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, 
             d.block_samples > RX_MAX_BLOCK_SAMPLES || d.n_channels == 0 || d.n_taps == 0 ||
             d.n_taps > RX_MAX_TAPS || d.integ_blocks == 0 || d.tap_early < 0 || d.tap_prompt < 0 ||
             d.tap_late < 0 || (uint32_t)d.tap_early >= d.n_taps ||
-            (uint32_t)d.tap_prompt >= d.n_taps || (uint32_t)d.tap_late >= d.n_taps)
+            (uint32_t)d.tap_prompt >= d.n_taps || (uint32_t)d.tap_late >= d.n_taps ||
+            d.loop_set > RX_LOOPS_TABLE3 || !(d.fll_bn_hz >= 0))
             return RX_EINVAL;
         n_ch += d.n_channels;
     }
@@ -765,7 +782,7 @@ extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, 
     };
     size_t o_theta = take(C * 4), o_w = take(C * 4), o_phi = take(C * 8), o_r = take(C * 8),
            o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8), o_ep = take(C * 4),
-           o_ab = take(C * 4), o_acc = take(taps * 8);
+           o_ab = take(C * 4), o_acc = take(taps * 8), o_ext = take(C * sizeof(LoopExt));
     b->state_bytes = off;
     auto fail = [&](rx_status s) {
         rx_batch_destroy(b);
@@ -791,6 +808,7 @@ extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, 
     b->st.epochs = (uint32_t *)(p + o_ep);
     b->st.acc_blocks = (uint32_t *)(p + o_ab);
     b->st.acc = (int32_t *)(p + o_acc);
+    b->st.ext = (LoopExt *)(p + o_ext);
     if (cudaMemset(b->d_state, 0, off) != cudaSuccess || cudaMemset(b->d_snap, 0, off) != cudaSuccess ||
         cudaMemset(b->d_prn, 0, C * 4) != cudaSuccess) {
         cudaGetLastError();
@@ -855,6 +873,7 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
     RX_CUDA_TRY(cudaMemcpy(s.epochs + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemcpy(s.acc_blocks + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemset(s.acc + b->rx_tap0[rxi] * 2, 0, (size_t)n * nt * 8), E);
+    RX_CUDA_TRY(cudaMemset(s.ext + c0, 0, (size_t)n * sizeof(LoopExt)), E);
     RX_CUDA_TRY(cudaMemcpy(b->d_prn + c0, vprn.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemcpy(b->d_taps + b->rx_tap0[rxi], tap_offsets, (size_t)n * nt * 8, cudaMemcpyHostToDevice), E);
     // The restart snapshot mirrors the state block byte for byte.
@@ -872,6 +891,7 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
     RX_CUDA_TRY(snap(s.epochs + c0, n * 4), E);
     RX_CUDA_TRY(snap(s.acc_blocks + c0, n * 4), E);
     RX_CUDA_TRY(snap(s.acc + b->rx_tap0[rxi] * 2, (size_t)n * nt * 8), E);
+    RX_CUDA_TRY(snap(s.ext + c0, (size_t)n * sizeof(LoopExt)), E);
     b->rx_set[rxi] = 1;
     return RX_OK;
 }
@@ -891,6 +911,8 @@ extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threa
     if (threads == 224 && schedule == RX_SCHED_PIPE && cpg > 3)
         return berr(b, RX_EINVAL, "224 threads take at most 3 channels per item");
     if (schedule == RX_SCHED_BALANCED && ctas_per_sm > 8) return berr(b, RX_EINVAL, "ctas_per_sm must be <= 8");
+    if (schedule == RX_SCHED_BALANCED && any_table3(b))
+        return berr(b, RX_EINVAL, "the balanced schedule does not run RX_LOOPS_TABLE3 receivers");
     if (cpg > 64) return berr(b, RX_EINVAL, "channels_per_item must be <= 64");
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
@@ -1124,6 +1146,7 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
     std::vector<std::array<uint32_t, 4>> cands;
     for (uint32_t nt : {192u, 224u, 128u, 256u, 512u})
         for (uint32_t per_sm : {1u, 2u, 3u, 4u, 6u}) {
+            if (any_table3(b)) break;
             if (per_sm > bal_default_per_sm(nt) + 2) continue;
             cands.push_back({0u, nt, per_sm, RX_SCHED_BALANCED});
         }
@@ -1180,3 +1203,31 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
 extern "C" uint32_t rx_batch_last_launches(rx_batch b) { return b ? b->last_launches : 0; }
 
 extern "C" const char *rx_batch_last_error(rx_batch b) { return b ? b->err.c_str() : "null handle"; }
+
+extern "C" rx_status rx_batch_read_health(rx_batch b, uint32_t rxi, rx_channel_health *out, uint32_t cap) {
+    if (!b || !out) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    const uint32_t n = b->rx[rxi].n_channels;
+    if (cap < n) return berr(b, RX_EINVAL, "cap < n_channels");
+    std::vector<LoopExt> ex(n);
+    cudaSetDevice(b->device);
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), b->err);
+    RX_CUDA_TRY(cudaMemcpy(ex.data(), b->st.ext + b->rx_ch0[rxi], n * sizeof(LoopExt), cudaMemcpyDeviceToHost),
+                b->err);
+    for (uint32_t c = 0; c < n; ++c) {
+        rx_channel_health &o = out[c];
+        o.cn0_hz = ex[c].cn0;
+        o.lock_ratio = ex[c].lock;
+        o.lock_fail_count = ex[c].lock_fail;
+        o.window_count = ex[c].window_count;
+        o.sum_abs_ip = ex[c].sum_abs;
+        o.sum_power = ex[c].sum_pow;
+        o.sum_diff = ex[c].sum_diff;
+        o.dll_integrator_hz = ex[c].dll_u;
+        o.prev_ip = ex[c].prev_ip;
+        o.prev_qp = ex[c].prev_qp;
+        o.have_prev = ex[c].have_prev;
+        o.pad = 0;
+    }
+    return RX_OK;
+}

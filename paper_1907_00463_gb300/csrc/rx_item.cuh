@@ -31,7 +31,50 @@ struct GroupDesc {
     uint32_t src;         // index into the sample-offset table
     uint32_t pad;
     LoopConsts lc;        // loop constants for one integration (L blocks)
+    // RX_LOOPS_TABLE3 (zero / null for RX_LOOPS_PLL2_DLL1)
+    LoopExt *ext;         // per-channel extra loop state and health indicators
+    LoopConsts3 lc3;
+    uint32_t loop_set, window;
 };
+
+// The loops of channel j of a group at an integration boundary, by the group's
+// loop set (Table 3's full set reads and writes the channel's gd.ext entry).  The
+// extra state goes through L2 (ld/st.cg): successive blocks of a group may run on
+// different SMs.  T3 = false compiles the basic loops only.
+template <bool T3 = true>
+__device__ __forceinline__ LoopOut close_loops(const GroupDesc &gd, uint32_t j, double v, const int32_t *A,
+                                               const int64_t *tp, const LoopConsts &lc) {
+    if (!T3 || gd.loop_set != 1u)
+        return loop_update(v, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p], A[2 * gd.tap_p + 1],
+                           A[2 * gd.tap_l], A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], lc);
+    LoopExt *p = gd.ext + j;
+    LoopExt ex;
+    ex.prev_ip = __ldcg(&p->prev_ip);
+    ex.prev_qp = __ldcg(&p->prev_qp);
+    ex.have_prev = __ldcg(&p->have_prev);
+    ex.window_count = __ldcg(&p->window_count);
+    ex.dll_u = __ldcg(&p->dll_u);
+    ex.sum_abs = __ldcg(&p->sum_abs);
+    ex.sum_pow = __ldcg(&p->sum_pow);
+    ex.sum_diff = __ldcg(&p->sum_diff);
+    ex.cn0 = __ldcg(&p->cn0);
+    ex.lock = __ldcg(&p->lock);
+    ex.lock_fail = __ldcg(&p->lock_fail);
+    LoopOut o = loop_update3(v, ex, A[2 * gd.tap_e], A[2 * gd.tap_e + 1], A[2 * gd.tap_p], A[2 * gd.tap_p + 1],
+                             A[2 * gd.tap_l], A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.lc3, gd.window);
+    __stcg(&p->prev_ip, ex.prev_ip);
+    __stcg(&p->prev_qp, ex.prev_qp);
+    __stcg(&p->have_prev, ex.have_prev);
+    __stcg(&p->window_count, ex.window_count);
+    __stcg(&p->dll_u, ex.dll_u);
+    __stcg(&p->sum_abs, ex.sum_abs);
+    __stcg(&p->sum_pow, ex.sum_pow);
+    __stcg(&p->sum_diff, ex.sum_diff);
+    __stcg(&p->cn0, ex.cn0);
+    __stcg(&p->lock, ex.lock);
+    __stcg(&p->lock_fail, ex.lock_fail);
+    return o;
+}
 
 struct Tables {
     const uint32_t *code;     // extended bit-packed C/A codes [33][EXT_WORDS]
@@ -358,9 +401,7 @@ __device__ __forceinline__ void process_item(const GroupDesc &gd, const int8_t *
         if (ab == gd.L) {
             const int32_t *A = sm.acc + (size_t)j * per_ch;
             const int64_t *tp = sm.taps + (size_t)j * nt;
-            LoopOut o = loop_update(__ldcg(gd.v + j), A[2 * gd.tap_e], A[2 * gd.tap_e + 1],
-                                    A[2 * gd.tap_p], A[2 * gd.tap_p + 1], A[2 * gd.tap_l],
-                                    A[2 * gd.tap_l + 1], tp[gd.tap_e], tp[gd.tap_l], gd.lc);
+            LoopOut o = close_loops(gd, j, __ldcg(gd.v + j), A, tp, gd.lc);
             __stcg(gd.v + j, o.v);
             __stcg(gd.fcarr + j, o.f_carr);
             __stcg(gd.fcode + j, o.f_code);
@@ -392,6 +433,7 @@ struct PipeArgs {
     uint32_t max_taps;
     uint32_t stall;            // 1: CTA 0 first waits on a barrier that nothing completes
     uint32_t stage_bytes;      // bytes of one staging buffer (0: samples read from global)
+    uint32_t table3;           // 1: some group runs RX_LOOPS_TABLE3 (unstaged kernels only)
 };
 
 // Staging buffer for blocks of at most max_n samples.
@@ -399,7 +441,7 @@ size_t pipe_stage_bytes(uint32_t max_n);
 // Dynamic shared memory of one CTA with nt correlation threads (stage_bytes 0: unstaged).
 size_t pipe_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t stage_bytes);
 // Resident CTAs per SM for nt correlation threads and filter_warps filter warps.
-int pipe_occupancy(uint32_t nt, uint32_t filter_warps, bool staged, size_t smem);
+int pipe_occupancy(uint32_t nt, uint32_t filter_warps, bool staged, size_t smem, bool table3 = false);
 // One CTA per group (grid = number of groups).
 cudaError_t pipe_launch(uint32_t nt, uint32_t filter_warps, uint32_t grid, size_t smem,
                         cudaStream_t stream, const PipeArgs &a);

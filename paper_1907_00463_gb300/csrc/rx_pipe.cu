@@ -51,7 +51,7 @@ constexpr int pipe_max_threads() { return NT == 224 ? NT + 32 : NT + 64; }
 template <int NT>
 constexpr int pipe_min_blocks() { return NT == 128 ? 4 : NT == 224 ? 3 : NT == 256 ? 2 : 1; }
 
-template <int NT, bool SH>
+template <int NT, bool SH, bool T3 = false>
 __global__ void __launch_bounds__(pipe_max_threads<NT>(), pipe_min_blocks<NT>()) k_batch_pipe(PipeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t cpg = a.cpg, mt = a.max_taps;
@@ -164,7 +164,6 @@ __global__ void __launch_bounds__(pipe_max_threads<NT>(), pipe_min_blocks<NT>())
         // dependency chain would wait behind the sample stream.
         const uint32_t f = warp - NT / 32, nf = (nthreads - NT) / 32;
         const LoopConsts lc = gd.lc;
-        const int32_t tap_e = gd.tap_e, tap_p = gd.tap_p, tap_l = gd.tap_l;
         const uint32_t L = gd.L, dump_wrap = gd.dump_wrap, dump_slots = gd.dump_slots, dump_stride = gd.dump_stride;
         int32_t *const dumps = gd.dumps;
         bool ok = true;
@@ -197,9 +196,7 @@ __global__ void __launch_bounds__(pipe_max_threads<NT>(), pipe_min_blocks<NT>())
                     sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
                     if (boundary) {
                         const int64_t *tp = sm.taps + (size_t)j * nt;
-                        LoopOut o = loop_update(s_v[j], A[2 * tap_e], A[2 * tap_e + 1], A[2 * tap_p],
-                                                A[2 * tap_p + 1], A[2 * tap_l], A[2 * tap_l + 1], tp[tap_e],
-                                                tp[tap_l], lc);
+                        LoopOut o = close_loops<T3>(gd, j, s_v[j], A, tp, lc);
                         s_v[j] = o.v;
                         s_fc[j] = o.f_carr;
                         s_fk[j] = o.f_code;
@@ -233,9 +230,9 @@ __global__ void __launch_bounds__(pipe_max_threads<NT>(), pipe_min_blocks<NT>())
     for (uint32_t i = tid; i < nch * per_ch; i += nthreads) gd.acc[i] = run[i];
 }
 
-template <int NT, bool SH>
+template <int NT, bool SH, bool T3 = false>
 int occupancy_nt(uint32_t fw, size_t smem) {
-    auto kern = k_batch_pipe<NT, SH>;
+    auto kern = k_batch_pipe<NT, SH, T3>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -249,9 +246,9 @@ int occupancy_nt(uint32_t fw, size_t smem) {
     return n;
 }
 
-template <int NT, bool SH>
+template <int NT, bool SH, bool T3 = false>
 cudaError_t launch_nt(uint32_t fw, uint32_t grid, size_t smem, cudaStream_t stream, const PipeArgs &a) {
-    auto kern = k_batch_pipe<NT, SH>;
+    auto kern = k_batch_pipe<NT, SH, T3>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -269,8 +266,17 @@ size_t pipe_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t stage_by
            (size_t)cpg * 24 + (size_t)cpg * mt * 8 + (size_t)cpg * 4 + 16;
 }
 
-int pipe_occupancy(uint32_t nt, uint32_t fw, bool staged, size_t smem) {
+int pipe_occupancy(uint32_t nt, uint32_t fw, bool staged, size_t smem, bool table3) {
     if (fw < 1 || fw > 2) return 0;
+    if (table3) {
+        // Table 3's loops: unstaged kernels with the full loop set compiled in
+        if (staged) return 0;
+        if (nt == 224) return fw == 1 ? occupancy_nt<224, false, true>(fw, smem) : 0;
+        if (nt == 128) return occupancy_nt<128, false, true>(fw, smem);
+        if (nt == 256) return occupancy_nt<256, false, true>(fw, smem);
+        if (nt == 512) return occupancy_nt<512, false, true>(fw, smem);
+        return 0;
+    }
     if (nt == 224) return fw == 1 ? (staged ? occupancy_nt<224, true>(fw, smem) : occupancy_nt<224, false>(fw, smem)) : 0;
     if (nt == 128) return staged ? occupancy_nt<128, true>(fw, smem) : occupancy_nt<128, false>(fw, smem);
     if (nt == 256) return staged ? occupancy_nt<256, true>(fw, smem) : occupancy_nt<256, false>(fw, smem);
@@ -282,6 +288,14 @@ cudaError_t pipe_launch(uint32_t nt, uint32_t fw, uint32_t grid, size_t smem, cu
                         const PipeArgs &a) {
     if (fw < 1 || fw > 2) return cudaErrorInvalidValue;
     const bool st = a.stage_bytes != 0;
+    if (a.table3) {
+        if (st) return cudaErrorInvalidValue;
+        if (nt == 224) return fw == 1 ? launch_nt<224, false, true>(fw, grid, smem, stream, a) : cudaErrorInvalidValue;
+        if (nt == 128) return launch_nt<128, false, true>(fw, grid, smem, stream, a);
+        if (nt == 256) return launch_nt<256, false, true>(fw, grid, smem, stream, a);
+        if (nt == 512) return launch_nt<512, false, true>(fw, grid, smem, stream, a);
+        return cudaErrorInvalidValue;
+    }
     if (nt == 224) {
         if (fw != 1) return cudaErrorInvalidValue;
         return st ? launch_nt<224, true>(fw, grid, smem, stream, a) : launch_nt<224, false>(fw, grid, smem, stream, a);

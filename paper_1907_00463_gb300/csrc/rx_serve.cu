@@ -568,7 +568,7 @@ extern "C" rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *d, const
         d->n_channels == 0 || d->n_channels > s->cfg.max_channels_per_stream || d->n_taps == 0 ||
         d->n_taps > s->cfg.max_taps || d->integ_blocks == 0 || d->tap_early < 0 || d->tap_prompt < 0 ||
         d->tap_late < 0 || (uint32_t)d->tap_early >= d->n_taps || (uint32_t)d->tap_prompt >= d->n_taps ||
-        (uint32_t)d->tap_late >= d->n_taps)
+        (uint32_t)d->tap_late >= d->n_taps || d->loop_set != RX_LOOPS_PLL2_DLL1)
         return serr(s, RX_EINVAL, "stream descriptor outside the server's limits");
     for (uint32_t c = 0; c < d->n_channels; ++c) {
         std::string m = rxh::check_channel(prn[c], code_rate_word[c], tap_offsets + (size_t)c * d->n_taps, d->n_taps);

@@ -354,7 +354,8 @@ extern "C" rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx, 
             d.n_taps > RX_MAX_TAPS || d.integ_blocks == 0 || (n_blocks % d.integ_blocks) != 0 ||
             d.tap_early < 0 || d.tap_prompt < 0 || d.tap_late < 0 ||
             (uint32_t)d.tap_early >= d.n_taps || (uint32_t)d.tap_prompt >= d.n_taps ||
-            (uint32_t)d.tap_late >= d.n_taps || (rx_byte_offset[r] & 15))
+            (uint32_t)d.tap_late >= d.n_taps || (rx_byte_offset[r] & 15) ||
+            d.loop_set != RX_LOOPS_PLL2_DLL1)
             return RX_EINVAL;
         n_ch += d.n_channels;
         n_taps += (uint64_t)d.n_channels * d.n_taps;

@@ -86,7 +86,8 @@ class rx_receiver_desc(C.Structure):
                 ("n_channels", C.c_uint32), ("n_taps", C.c_uint32),
                 ("integ_blocks", C.c_uint32), ("pll_bn_hz", C.c_double),
                 ("dll_bn_hz", C.c_double), ("tap_early", C.c_int32),
-                ("tap_prompt", C.c_int32), ("tap_late", C.c_int32)]
+                ("tap_prompt", C.c_int32), ("tap_late", C.c_int32), ("loop_set", C.c_uint32),
+                ("health_window", C.c_uint32), ("fll_bn_hz", C.c_double)]
 
 
 class rx_serve_config(C.Structure):
@@ -171,6 +172,7 @@ SIGNATURES = [
     ("rx_batch_sync", C.c_int, [P]),
     ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_batch_read_health", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_health), C.c_uint32]),
     ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     ("rx_batch_set_wait_limit", C.c_int, [P, C.c_uint64, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -453,6 +455,13 @@ def rx_batch_read_state(b, rx: int, n_ch: int) -> list:
     return list(arr)
 
 
+def rx_batch_read_health(b, rx: int, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_health * n_ch)()
+    _check(b, lib.rx_batch_read_health(b, rx, arr, n_ch), lib.rx_batch_last_error)
+    return list(arr)
+
+
 def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per_sm: int = 0,
                        schedule: int = RX_SCHED_DYNAMIC):
     lib = load()
@@ -492,11 +501,12 @@ def rx_batch_last_error(b) -> str:
     return load().rx_batch_last_error(b).decode()
 
 
-def receiver_desc(rx) -> rx_receiver_desc:
+def receiver_desc(rx, loop_set: int = 0, health_window: int = 0,
+                  fll_bn_hz: float = 0.0) -> rx_receiver_desc:
     """rx_receiver_desc from a synth.Receiver-like object (fields fs, block_samples, ...)."""
     return rx_receiver_desc(rx.fs, rx.block_samples, len(rx.channels), rx.n_taps,
                             rx.integ_blocks, rx.pll_bn, rx.dll_bn, rx.tap_early, rx.tap_prompt,
-                            rx.tap_late)
+                            rx.tap_late, loop_set, health_window, fll_bn_hz)
 
 
 # ----------------------------------------------------------------------------

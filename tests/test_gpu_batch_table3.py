@@ -1,0 +1,146 @@
+"""GPU parity of Table 3's full loop set (RX_LOOPS_TABLE3: FLL-assisted 2nd-order PLL,
+2nd-order DLL) and the channel-health indicators in the batched persistent form,
+against the oracle: dumps, loop state and health bit-exact for every schedule that
+runs it (dynamic, static, pipelined), in a batch mixing receivers of both loop
+sets and of uneven shape; a restart reproduces the run; the forms that keep the
+basic loops refuse Table 3 receivers."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1907_00463_gb300 import rx, synth
+
+from helpers import assert_states_equal, batch_layout, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+WINDOW, FLL = 10, 10.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _receivers(n_blocks):
+    recv = [synth.uneven_receiver(i, n_blocks=n_blocks) for i in range(6)]
+    table3 = [i % 2 == 0 for i in range(len(recv))]
+    return recv, table3
+
+
+def _pack(receivers):
+    offs, total = batch_layout(receivers)
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for r, o in zip(receivers, offs):
+        iq = synth.generate_iq(r).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    return buf, offs, sigs
+
+
+def _oracle(r, iq, t3):
+    if not t3:
+        d, s = oracle_run(r, iq)
+        return d, s, None
+    prn, w, phi, rate, taps = synth.channel_arrays(r)
+    chans = [oracle.chan_init(int(w[i]), int(phi[i]), int(rate[i]), r.fs) for i in range(len(prn))]
+    return oracle.run_receiver_table3(iq, r.n_blocks, r.block_samples, r.fs, prn, taps, r.integ_blocks,
+                                      r.tap_early, r.tap_prompt, r.tap_late, r.pll_bn, r.dll_bn, FLL,
+                                      WINDOW, chans)
+
+
+def _health_equal(gpu, ext):
+    assert len(gpu) == len(ext)
+    for i, (g, o) in enumerate(zip(gpu, ext)):
+        assert (g.cn0_hz, g.lock_ratio, g.lock_fail_count, g.window_count) == \
+            (o.cn0_hz, o.lock_ratio, o.lock_fail, o.window_count), i
+        assert (g.sum_abs_ip, g.sum_power, g.sum_diff, g.dll_integrator_hz) == \
+            (o.sum_abs_ip, o.sum_power, o.sum_diff, o.dll_u), i
+        assert (g.prev_ip, g.prev_qp, g.have_prev) == (o.prev_ip, o.prev_qp, o.have_prev), i
+
+
+def _run(receivers, table3, buf, offs, tiles, n_runs=1):
+    descs = [rx.receiver_desc(r, 1 if t else 0, WINDOW if t else 0, FLL if t else 0.0)
+             for r, t in zip(receivers, table3)]
+    n_blocks = receivers[0].n_blocks
+    b = rx.rx_batch_create(descs, n_blocks)
+    try:
+        for i, r in enumerate(receivers):
+            rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+        if tiles:
+            rx.rx_batch_set_tiles(b, *tiles)
+        out = []
+        dev = torch.from_numpy(buf).cuda()
+        for _ in range(n_runs):
+            rx.rx_batch_run(b, dev, offs, n_blocks, rx.RX_RUN_RESTART)
+            res = []
+            for i, r in enumerate(receivers):
+                d = rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, n_blocks // r.integ_blocks)
+                s = rx.rx_batch_read_state(b, i, len(r.channels))
+                h = rx.rx_batch_read_health(b, i, len(r.channels))
+                res.append((d, s, h))
+            out.append(res)
+    finally:
+        rx.rx_batch_destroy(b)
+    return out
+
+
+@pytest.mark.parametrize("tiles", [None, (2, 128, 0, rx.RX_SCHED_STATIC), (2, 224, 0, rx.RX_SCHED_PIPE),
+                                   (3, 256, 0, rx.RX_SCHED_DYNAMIC)])
+def test_mixed_loop_sets_match_oracle(tiles):
+    recv, table3 = _receivers(40)
+    for r in recv:
+        assert r.n_blocks % r.integ_blocks == 0
+    buf, offs, sigs = _pack(recv)
+    runs = _run(recv, table3, buf, offs, tiles, n_runs=2)
+    for res in runs:
+        for r, t, iq, (d, s, h) in zip(recv, table3, sigs, res):
+            od, os_, oext = _oracle(r, iq, t)
+            assert np.array_equal(d, od), r.meta
+            assert_states_equal(s, os_)
+            if t:
+                _health_equal(h, oext)
+            else:
+                assert all(x.window_count == 0 and x.cn0_hz == 0.0 and x.have_prev == 0 for x in h)
+
+
+def test_health_indicators_read_sensible_values():
+    """A 1 s run of Table 3 receivers at 35-50 dB-Hz: every channel's C/N0 estimate is
+    within 3 dB of the generator's and the lock ratio of the strong ones is high."""
+    recv = [synth.uniform_receiver(i, n_blocks=600, fs=4.092e6) for i in range(2)]
+    buf, offs, sigs = _pack(recv)
+    res = _run(recv, [True, True], buf, offs, (2, 224, 0, rx.RX_SCHED_PIPE))[0]
+    for r, (d, s, h) in zip(recv, res):
+        for sv, x in zip(r.svs, h):
+            cn0 = 10 * np.log10(x.cn0_hz)
+            assert abs(cn0 - sv.cn0_dbhz) < 3.0, (sv.prn, cn0, sv.cn0_dbhz)
+            if sv.cn0_dbhz > 40:
+                assert x.lock_ratio > 0.85, (sv.prn, x.lock_ratio)
+
+
+def test_forms_without_table3_refuse_it():
+    recv, _ = _receivers(20)
+    d3 = rx.receiver_desc(recv[0], 1, WINDOW, FLL)
+    b = rx.rx_batch_create([d3], 20)
+    try:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 0, 224, 3, rx.RX_SCHED_BALANCED)
+        assert e.value.status == rx.RX_EINVAL
+    finally:
+        rx.rx_batch_destroy(b)
+    bad = rx.receiver_desc(recv[0], 2, 0, 0.0)
+    with pytest.raises(rx.RxError) as e:
+        rx.rx_batch_create([bad], 20)
+    assert e.value.status == rx.RX_EINVAL
+    st = synth.serving_stream(0, n_blocks=4)
+    s = rx.rx_serve_create(4, 16, 8, 8184, ring_blocks=64, dump_slots=4, hbm_budget_bytes=1 << 28)
+    try:
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_serve_admit(s, rx.receiver_desc(st, 1, WINDOW, FLL), *synth.channel_arrays(st))
+        assert e.value.status == rx.RX_EINVAL
+        rx.rx_serve_admit(s, rx.receiver_desc(st), *synth.channel_arrays(st))    # the basic loops are fine
+    finally:
+        rx.rx_serve_destroy(s)
