@@ -309,9 +309,9 @@ typedef struct {
     double dll_bn_hz;
     int32_t tap_early, tap_prompt, tap_late;
     uint32_t loop_set;           /* RX_LOOPS_PLL2_DLL1 (0) or RX_LOOPS_TABLE3 (1), as in rx_config;
-                                    RX_LOOPS_TABLE3 runs in the batched form's dynamic, static and
-                                    pipelined schedules (RX_EINVAL for the balanced schedule, the
-                                    served form and rx_track_static) */
+                                    RX_LOOPS_TABLE3 runs in the served form and the batched form's
+                                    dynamic, static and pipelined schedules (RX_EINVAL for the
+                                    balanced schedule and rx_track_static) */
     uint32_t health_window;      /* RX_LOOPS_TABLE3: integrations per C/N0 / lock estimate */
     double fll_bn_hz;            /* RX_LOOPS_TABLE3: FLL bandwidth; dll_bn_hz is a 2nd-order DLL's */
 } rx_receiver_desc;
@@ -509,6 +509,9 @@ rx_status rx_serve_read_dumps(rx_serve s, uint32_t id, int32_t *out, size_t cap,
 rx_status rx_serve_read_state(rx_serve s, uint32_t id, rx_channel_state *out,
                               uint32_t cap);
 
+/* RX_LOOPS_TABLE3 state and health indicators of an active stream's channels
+ * (zero for RX_LOOPS_PLL2_DLL1 streams).  Drains first. */
+rx_status rx_serve_read_health(rx_serve s, uint32_t id, rx_channel_health *out, uint32_t cap);
 const char *rx_serve_last_error(rx_serve s);
 
 /* Replay of recorded streams (the receiver's offline "simulation" mode,

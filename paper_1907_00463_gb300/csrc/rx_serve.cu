@@ -150,6 +150,7 @@ struct Stream {
     uint64_t *phi_d = nullptr, *r_d = nullptr;
     double *v = nullptr, *fcarr = nullptr, *fcode = nullptr;
     int64_t *taps_d = nullptr;
+    LoopExt *ext = nullptr;       // RX_LOOPS_TABLE3 extra loop state and health
 };
 
 struct Pending {
@@ -221,6 +222,7 @@ size_t stream_bytes(const rx_receiver_desc &d, uint32_t dump_slots) {
     b += align_up(C * 8, 16) * 5;          // phi, r, v, fcarr, fcode
     b += align_up(C * T * 8, 16) * 2;      // taps, acc
     b += align_up((size_t)dump_slots * C * T * 8, 16);
+    if (d.loop_set == RX_LOOPS_TABLE3) b += align_up(C * sizeof(LoopExt), 16);   // Table 3 state
     return align_up(b, kAlign);
 }
 
@@ -253,6 +255,7 @@ rx_status activate(rx_serve s, uint32_t id) {
     st.taps_d = (int64_t *)take(C * T * 8);
     st.acc = (int32_t *)take(C * T * 8);
     st.dumps = (int32_t *)take((size_t)s->cfg.dump_slots * C * T * 8);
+    st.ext = d.loop_set == RX_LOOPS_TABLE3 ? (LoopExt *)take(C * sizeof(LoopExt)) : nullptr;
     std::vector<uint32_t> zero(C, 0), vprn(C);
     std::vector<uint64_t> phi(C);
     std::vector<double> v(C), fk(C);
@@ -279,6 +282,7 @@ rx_status activate(rx_serve s, uint32_t id) {
     up(st.fcarr, v.data(), C * 8);
     up(st.fcode, fk.data(), C * 8);
     up(st.taps_d, st.taps.data(), C * T * 8);
+    if (st.ext && e == cudaSuccess) e = cudaMemsetAsync(st.ext, 0, C * sizeof(LoopExt), cs);
     std::vector<GroupDesc> gds(ng);
     st.groups.clear();
     for (uint32_t k = 0; k < ng; ++k) {
@@ -314,6 +318,13 @@ rx_status activate(rx_serve s, uint32_t id) {
         gd.src = id;
         gd.lc = make_loop_consts(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
                                  d.dll_bn_hz);
+        if (st.ext) {
+            gd.ext = st.ext + c0;
+            gd.lc3 = make_loop_consts3(d.fs_hz, (uint64_t)d.integ_blocks * d.block_samples, d.pll_bn_hz,
+                                       d.dll_bn_hz, d.fll_bn_hz);
+            gd.loop_set = RX_LOOPS_TABLE3;
+            gd.window = d.health_window;
+        }
         up(s->d_groups + g, &gd, sizeof(GroupDesc));
         if (e == cudaSuccess) e = cudaMemsetAsync(s->d_done + g, 0, 4, cs);
     }
@@ -568,7 +579,7 @@ extern "C" rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *d, const
         d->n_channels == 0 || d->n_channels > s->cfg.max_channels_per_stream || d->n_taps == 0 ||
         d->n_taps > s->cfg.max_taps || d->integ_blocks == 0 || d->tap_early < 0 || d->tap_prompt < 0 ||
         d->tap_late < 0 || (uint32_t)d->tap_early >= d->n_taps || (uint32_t)d->tap_prompt >= d->n_taps ||
-        (uint32_t)d->tap_late >= d->n_taps || d->loop_set != RX_LOOPS_PLL2_DLL1)
+        (uint32_t)d->tap_late >= d->n_taps || d->loop_set > RX_LOOPS_TABLE3 || !(d->fll_bn_hz >= 0))
         return serr(s, RX_EINVAL, "stream descriptor outside the server's limits");
     for (uint32_t c = 0; c < d->n_channels; ++c) {
         std::string m = rxh::check_channel(prn[c], code_rate_word[c], tap_offsets + (size_t)c * d->n_taps, d->n_taps);
@@ -779,6 +790,36 @@ extern "C" rx_status rx_serve_read_state(rx_serve s, uint32_t id, rx_channel_sta
         out[c].code_hz = fk[c];
         out[c].prn = st.prn[c];
         out[c].epochs = ep[c];
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_serve_read_health(rx_serve s, uint32_t id, rx_channel_health *out, uint32_t cap) {
+    if (!s || !out || id >= s->cfg.max_streams) return RX_EINVAL;
+    rx_status r = rx_serve_drain(s);
+    if (r != RX_OK) return r;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const Stream &st = s->streams[id];
+    if (st.state != kActive) return serr(s, RX_ESTATE, "stream is not active");
+    const size_t C = st.desc.n_channels;
+    if (cap < C) return serr(s, RX_EINVAL, "cap < channels");
+    std::vector<LoopExt> ex(C);
+    if (st.ext && cudaMemcpy(ex.data(), st.ext, C * sizeof(LoopExt), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RX_ECUDA;
+    for (size_t c = 0; c < C; ++c) {
+        rx_channel_health &o = out[c];
+        o.cn0_hz = ex[c].cn0;
+        o.lock_ratio = ex[c].lock;
+        o.lock_fail_count = ex[c].lock_fail;
+        o.window_count = ex[c].window_count;
+        o.sum_abs_ip = ex[c].sum_abs;
+        o.sum_power = ex[c].sum_pow;
+        o.sum_diff = ex[c].sum_diff;
+        o.dll_integrator_hz = ex[c].dll_u;
+        o.prev_ip = ex[c].prev_ip;
+        o.prev_qp = ex[c].prev_qp;
+        o.have_prev = ex[c].have_prev;
+        o.pad = 0;
     }
     return RX_OK;
 }

@@ -196,6 +196,7 @@ SIGNATURES = [
                                          C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     ("rx_serve_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_serve_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
+    ("rx_serve_read_health", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_health), C.c_uint32]),
     ("rx_serve_last_error", C.c_char_p, [P]),
     ("rx_serve_replay", C.c_int, [P, C.POINTER(rx_replay_stream), C.c_uint32,
                                   C.POINTER(rx_replay_config), C.POINTER(C.c_uint32)]),
@@ -733,3 +734,12 @@ def rx_acq_handoff(fs_hz: float, block_samples: int, n_ms: int, code_rate_word: 
     if s != RX_OK:
         raise RxError(s, "rx_acq_handoff")
     return phi.value, r.value
+
+
+def rx_serve_read_health(s, sid: int, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_channel_health * n_ch)()
+    st = lib.rx_serve_read_health(s, sid, arr, n_ch)
+    if st != RX_OK:
+        raise RxError(st, lib.rx_serve_last_error(s).decode())
+    return list(arr)

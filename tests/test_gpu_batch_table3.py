@@ -3,7 +3,7 @@
 against the oracle: dumps, loop state and health bit-exact for every schedule that
 runs it (dynamic, static, pipelined), in a batch mixing receivers of both loop
 sets and of uneven shape; a restart reproduces the run; the forms that keep the
-basic loops refuse Table 3 receivers."""
+basic loops refuse Table 3 receivers; the served form runs it per stream."""
 import numpy as np
 import pytest
 import torch
@@ -127,7 +127,7 @@ def test_health_indicators_read_sensible_values():
     assert checked >= 8
 
 
-def test_forms_without_table3_refuse_it():
+def test_balanced_and_static_forms_refuse_table3():
     recv, _ = _receivers(20)
     d3 = rx.receiver_desc(recv[0], 1, WINDOW, FLL)
     b = rx.rx_batch_create([d3], 20)
@@ -142,11 +142,42 @@ def test_forms_without_table3_refuse_it():
         rx.rx_batch_create([bad], 20)
     assert e.value.status == rx.RX_EINVAL
     st = synth.serving_stream(0, n_blocks=4)
-    s = rx.rx_serve_create(4, 16, 8, 8184, ring_blocks=64, dump_slots=4, hbm_budget_bytes=1 << 28)
+    dev = torch.zeros(4096, dtype=torch.int8, device="cuda")     # never touched: the descriptor is refused
+    with pytest.raises(rx.RxError) as e:
+        rx.rx_track_static([rx.receiver_desc(st, 1, WINDOW, FLL)], dev, [0], 4, dev, dev, dev)
+    assert e.value.status == rx.RX_EINVAL
+
+
+def test_served_table3_stream_matches_oracle():
+    """A served stream with Table 3's loops next to a basic-loop stream: dumps, state
+    and health of each bit-exact with the oracle."""
+    r3 = synth.serving_stream(5, n_blocks=40)
+    rb = synth.serving_stream(6, n_blocks=40)
+    iq3, iqb = synth.generate_iq(r3).numpy(), synth.generate_iq(rb).numpy()
+    s = rx.rx_serve_create(8, 16, 8, 8184, ring_blocks=128, dump_slots=64)
     try:
-        with pytest.raises(rx.RxError) as e:
-            rx.rx_serve_admit(s, rx.receiver_desc(st, 1, WINDOW, FLL), *synth.channel_arrays(st))
-        assert e.value.status == rx.RX_EINVAL
-        rx.rx_serve_admit(s, rx.receiver_desc(st), *synth.channel_arrays(st))    # the basic loops are fine
+        id3, a3 = rx.rx_serve_admit(s, rx.receiver_desc(r3, 1, WINDOW, FLL), *synth.channel_arrays(r3))
+        idb, ab = rx.rx_serve_admit(s, rx.receiver_desc(rb), *synth.channel_arrays(rb))
+        assert a3 and ab
+        N = r3.block_samples
+        for b in range(40):
+            for sid, iq in ((id3, iq3), (idb, iqb)):
+                while rx.rx_serve_push(s, sid, iq[b * N:(b + 1) * N]) != rx.RX_OK:
+                    pass
+        rx.rx_serve_drain(s)
+        d3 = rx.rx_serve_read_dumps(s, id3, 12, 5, 64)
+        s3 = rx.rx_serve_read_state(s, id3, 12)
+        h3 = rx.rx_serve_read_health(s, id3, 12)
+        db = rx.rx_serve_read_dumps(s, idb, 12, 5, 64)
+        sb = rx.rx_serve_read_state(s, idb, 12)
+        hb = rx.rx_serve_read_health(s, idb, 12)
     finally:
         rx.rx_serve_destroy(s)
+    od, os_, oext = _oracle(r3, iq3, True)
+    assert np.array_equal(d3, od)
+    assert_states_equal(s3, os_)
+    _health_equal(h3, oext)
+    od, os_, _ = _oracle(rb, iqb, False)
+    assert np.array_equal(db, od)
+    assert_states_equal(sb, os_)
+    assert all(x.window_count == 0 and x.have_prev == 0 for x in hb)
