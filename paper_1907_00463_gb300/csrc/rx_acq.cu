@@ -62,7 +62,11 @@ struct AcqRow {
 template <int LOGM>
 struct Shape {
     static constexpr uint32_t M = 1u << LOGM;
-    static constexpr uint32_t NT = LOGM >= 14 ? 512u : (M / 32);
+    // The largest transform holds one CTA per SM (its padded buffer is 147 KB), so it
+    // runs 1024 threads with a 16-element register stage to fit 64 registers; the
+    // others run up to 512 threads with 32-element register stages.
+    static constexpr int RL = LOGM == 15 ? 4 : 5;
+    static constexpr uint32_t NT = LOGM == 15 ? 1024u : LOGM >= 14 ? 512u : (M / 32);
     static constexpr uint32_t WORDS = M + M / 8;            // padded data
     static constexpr size_t SMEM = (size_t)WORDS * 4 + 64 * 16;  // + reduction scratch
 };
@@ -73,28 +77,29 @@ struct Shape {
 template <int LOGM>
 __device__ __forceinline__ void forward(uint32_t *s, const uint2 *__restrict__ T) {
     constexpr uint32_t M = Shape<LOGM>::M, NT = Shape<LOGM>::NT;
+    constexpr int RL = Shape<LOGM>::RL, R = 1 << RL;
     const uint32_t tid = threadIdx.x;
     int lg = LOGM - 1;
-    if (rxn::smem_stages(LOGM) & 1) {
+    if (rxn::smem_stages(LOGM, RL) & 1) {
         rxn::dif_pass2(s, lg, tid, NT, M, T);
         __syncthreads();
         lg -= 1;
     }
-    for (; lg >= 6; lg -= 2) {
+    for (; lg >= RL + 1; lg -= 2) {
         rxn::dif_pass4(s, lg - 1, tid, NT, M, T);
         __syncthreads();
     }
-    for (uint32_t q = tid; q < M / 32; q += NT) {
-        uint4 *c = reinterpret_cast<uint4 *>(s + rxn::pad(32 * q));
-        uint32_t x[32];
+    for (uint32_t q = tid; q < M / R; q += NT) {
+        uint4 *c = reinterpret_cast<uint4 *>(s + rxn::pad(R * q));
+        uint32_t x[R];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        for (int e = 0; e < R / 4; ++e) {
             uint4 v = c[e];
             x[4 * e] = v.x; x[4 * e + 1] = v.y; x[4 * e + 2] = v.z; x[4 * e + 3] = v.w;
         }
-        rxn::dif_reg32(x, TwF{});
+        rxn::dif_reg<RL>(x, TwF{});
 #pragma unroll
-        for (int e = 0; e < 8; ++e) c[e] = make_uint4(x[4 * e], x[4 * e + 1], x[4 * e + 2], x[4 * e + 3]);
+        for (int e = 0; e < R / 4; ++e) c[e] = make_uint4(x[4 * e], x[4 * e + 1], x[4 * e + 2], x[4 * e + 3]);
     }
     __syncthreads();
 }
@@ -202,8 +207,9 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
                const uint32_t *__restrict__ A, const uint2 *__restrict__ H, uint32_t N,
                uint32_t n_ms, uint32_t n_dopp, uint32_t n_prn, const uint2 *__restrict__ Ti) {
     using SH = Shape<LOGM>;
-    using LH = rxn::LastHalf<LOGM, SH::NT>;
+    using LH = rxn::LastHalf<LOGM, SH::NT, SH::RL>;
     constexpr uint32_t M = SH::M, NT = SH::NT, SLOTS = LH::kSlots;
+    constexpr int RL = SH::RL, R = 1 << RL;
     extern __shared__ __align__(16) uint32_t s[];
     const uint32_t tid = threadIdx.x;
     const uint32_t p = blockIdx.x % n_prn;
@@ -228,24 +234,24 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
                 *reinterpret_cast<uint4 *>(s + rxn::pad(4 * i4)) = v;
             }
             __syncthreads();
-            for (uint32_t q = tid; q < M / 32; q += NT) {
-                uint4 *c = reinterpret_cast<uint4 *>(s + rxn::pad(32 * q));
-                uint32_t x[32];
+            for (uint32_t q = tid; q < M / R; q += NT) {
+                uint4 *c = reinterpret_cast<uint4 *>(s + rxn::pad(R * q));
+                uint32_t x[R];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+                for (int e = 0; e < R / 4; ++e) {
                     uint4 v = c[e];
                     x[4 * e] = v.x; x[4 * e + 1] = v.y; x[4 * e + 2] = v.z; x[4 * e + 3] = v.w;
                 }
-                rxn::dit_reg32(x, TwI{});
+                rxn::dit_reg<RL>(x, TwI{});
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
+                for (int e = 0; e < R / 4; ++e)
                     c[e] = make_uint4(x[4 * e], x[4 * e + 1], x[4 * e + 2], x[4 * e + 3]);
             }
             __syncthreads();
-            constexpr int ns = LOGM - 5;
+            constexpr int ns = LOGM - RL;
             constexpr int npairs = (ns & 1) ? (ns - 1) / 2 : ns / 2 - 1;
 #pragma unroll 1
-            for (int pp = 0, lgH = 5; pp < npairs; ++pp, lgH += 2) {
+            for (int pp = 0, lgH = RL; pp < npairs; ++pp, lgH += 2) {
                 rxn::dit_pass4(s, lgH, tid, NT, M, Ti);
                 __syncthreads();
             }

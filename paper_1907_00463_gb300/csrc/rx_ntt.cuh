@@ -29,10 +29,10 @@
 //   - inverse: decimation in time, bit-reversed in, natural order out, inputs
 //     in [0, 4p), outputs in [0, 4p), without the 1/M factor (the caller folds
 //     it into one operand of the product).
-//   - shared-memory layout: element i at word pad(i) = i + 4 (i / 32), so that a
-//     thread's 32 consecutive elements start 36 words after its neighbour's
-//     (128-bit accesses of 8 threads fill the 32 banks) and strided accesses
-//     of consecutive elements stay conflict-free.
+//   - shared-memory layout: element i at word pad(i) = i + 4 (i / 32), so that
+//     128-bit accesses to a thread's run of 16 or 32 consecutive elements fill
+//     the 32 banks with 8 threads, and strided accesses of consecutive elements
+//     stay conflict-free.
 //
 // Every routine here handles the part of one pass that thread `tid` of `nt`
 // owns; the caller separates passes with a block barrier.  The routines are
@@ -122,7 +122,7 @@ RXN_HD void dif_pass2(uint32_t *s, int lgL, uint32_t tid, uint32_t nt, uint32_t 
     }
 }
 
-// Two stages fused: half-length L = 2^(lgH+1) then H = L / 2 (H >= 32).
+// Two stages fused: half-length L = 2^(lgH+1) then H = L / 2 (H >= the register stage).
 RXN_HD void dif_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t M,
                       const uint2 *T) {
     const uint32_t H = 1u << lgH, L = 2 * H;
@@ -142,47 +142,48 @@ RXN_HD void dif_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t 
     }
 }
 
-// The last five stages (L = 16, 8, 4, 2, 1) of 32 consecutive elements held in
-// registers.  tw[L + j] = T[L + j] for L + j < 32.  One template level per stage
+// The last RL stages (L = R/2, ..., 2, 1) of R = 2^RL consecutive elements held in
+// registers.  tw[L + j] = T[L + j] for L + j < R.  One template level per stage
 // keeps every index a compile-time constant, so x stays in registers.
-template <int LG>
+template <int LG, int R>
 struct DifReg {
     template <class TW>
-    RXN_HD static void run(uint32_t (&x)[32], const TW &tw) {
+    RXN_HD static void run(uint32_t (&x)[R], const TW &tw) {
         constexpr int L = 1 << LG;
 #pragma unroll
-        for (int st = 0; st < 32; st += 2 * L) {
+        for (int st = 0; st < R; st += 2 * L) {
 #pragma unroll
             for (int j = 0; j < L; ++j) bf_dif(x[st + j], x[st + j + L], tw[L + j]);
         }
-        if constexpr (LG > 0) DifReg<LG - 1>::run(x, tw);
+        if constexpr (LG > 0) DifReg<LG - 1, R>::run(x, tw);
     }
 };
-template <class TW>
-RXN_HD void dif_reg32(uint32_t (&x)[32], const TW &tw) { DifReg<4>::run(x, tw); }
+template <int RL, class TW>
+RXN_HD void dif_reg(uint32_t (&x)[1 << RL], const TW &tw) { DifReg<RL - 1, 1 << RL>::run(x, tw); }
 
 // ---------------------------------------------------------------------------
 // Inverse transform (decimation in time, unscaled)
 // ---------------------------------------------------------------------------
 
-// The first five stages (L = 1, 2, 4, 8, 16) in registers.  twi[L + j] = Ti[L + j].
-template <int LG>
+// The first RL stages (L = 1, 2, ..., R/2) of R = 2^RL elements in registers.
+// twi[L + j] = Ti[L + j].
+template <int LG, int R>
 struct DitReg {
     template <class TW>
-    RXN_HD static void run(uint32_t (&x)[32], const TW &twi) {
+    RXN_HD static void run(uint32_t (&x)[R], const TW &twi) {
         constexpr int L = 1 << LG;
 #pragma unroll
-        for (int st = 0; st < 32; st += 2 * L) {
+        for (int st = 0; st < R; st += 2 * L) {
 #pragma unroll
             for (int j = 0; j < L; ++j) bf_dit(x[st + j], x[st + j + L], twi[L + j]);
         }
-        if constexpr (LG < 4) DitReg<LG + 1>::run(x, twi);
+        if constexpr ((2 << LG) < R) DitReg<LG + 1, R>::run(x, twi);
     }
 };
-template <class TW>
-RXN_HD void dit_reg32(uint32_t (&x)[32], const TW &twi) { DitReg<0>::run(x, twi); }
+template <int RL, class TW>
+RXN_HD void dit_reg(uint32_t (&x)[1 << RL], const TW &twi) { DitReg<0, 1 << RL>::run(x, twi); }
 
-// Two stages fused: half-length H = 2^lgH then L = 2 H (H >= 32).
+// Two stages fused: half-length H = 2^lgH then L = 2 H (H >= the register stage).
 RXN_HD void dit_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t M,
                       const uint2 *Ti) {
     const uint32_t H = 1u << lgH, L = 2 * H;
@@ -216,8 +217,8 @@ RXN_HD void dit_pass2(uint32_t *s, int lgL, uint32_t tid, uint32_t nt, uint32_t 
     }
 }
 
-// Number of stages done in shared memory (all but the five register stages).
-RXN_HD int smem_stages(int logM) { return logM - 5; }
+// Number of stages done in shared memory (all but the RL register stages).
+RXN_HD constexpr int smem_stages(int logM, int RL) { return logM - RL; }
 
 // The outputs of the inverse's last stage that fall below M / 2, for the
 // elements thread tid owns, as signed integers.  With an even number of
@@ -226,10 +227,10 @@ RXN_HD int smem_stages(int logM) { return logM - 5; }
 // it is radix-2 (L = M/2) and owns output b = tid + q nt (slot q).  Both give
 // M / (2 nt) slots per thread, and the counts are compile-time so that per-slot
 // accumulators stay in registers.  out_slot(slot, index, value) receives each.
-template <int LOGM, uint32_t NT>
+template <int LOGM, uint32_t NT, int RL>
 struct LastHalf {
     static constexpr uint32_t M = 1u << LOGM;
-    static constexpr bool kRadix4 = ((LOGM - 5) & 1) == 0;
+    static constexpr bool kRadix4 = ((LOGM - RL) & 1) == 0;
     static constexpr uint32_t kSlots = M / (2 * NT);
 
     RXN_HD static uint32_t index(uint32_t tid, uint32_t slot) {
