@@ -62,11 +62,12 @@ struct AcqRow {
 template <int LOGM>
 struct Shape {
     static constexpr uint32_t M = 1u << LOGM;
-    // The largest transform holds one CTA per SM (its padded buffer is 147 KB), so it
-    // runs 1024 threads with a 16-element register stage to fit 64 registers; the
-    // others run up to 512 threads with 32-element register stages.
-    static constexpr int RL = LOGM == 15 ? 4 : 5;
-    static constexpr uint32_t NT = LOGM == 15 ? 1024u : LOGM >= 14 ? 512u : (M / 32);
+    // 32-element register stages; at most 512 threads (the 2^15 transform holds one
+    // CTA per SM: its padded buffer is 147 KB).  1024 threads with a 16-element
+    // register stage (to fit 64 registers) measured slower: one more shared-memory
+    // stage, and its half-length-16 pass conflicts two-way in the padded layout.
+    static constexpr int RL = 5;
+    static constexpr uint32_t NT = LOGM >= 14 ? 512u : (M / 32);
     static constexpr uint32_t WORDS = M + M / 8;            // padded data
     static constexpr size_t SMEM = (size_t)WORDS * 4 + 64 * 16;  // + reduction scratch
 };
