@@ -1214,20 +1214,6 @@ extern "C" rx_status rx_batch_read_health(rx_batch b, uint32_t rxi, rx_channel_h
     RX_CUDA_TRY(cudaStreamSynchronize(b->stream), b->err);
     RX_CUDA_TRY(cudaMemcpy(ex.data(), b->st.ext + b->rx_ch0[rxi], n * sizeof(LoopExt), cudaMemcpyDeviceToHost),
                 b->err);
-    for (uint32_t c = 0; c < n; ++c) {
-        rx_channel_health &o = out[c];
-        o.cn0_hz = ex[c].cn0;
-        o.lock_ratio = ex[c].lock;
-        o.lock_fail_count = ex[c].lock_fail;
-        o.window_count = ex[c].window_count;
-        o.sum_abs_ip = ex[c].sum_abs;
-        o.sum_power = ex[c].sum_pow;
-        o.sum_diff = ex[c].sum_diff;
-        o.dll_integrator_hz = ex[c].dll_u;
-        o.prev_ip = ex[c].prev_ip;
-        o.prev_qp = ex[c].prev_qp;
-        o.have_prev = ex[c].have_prev;
-        o.pad = 0;
-    }
+    for (size_t c = 0; c < n; ++c) out[c] = health_record<rx_channel_health>(ex[c]);
     return RX_OK;
 }

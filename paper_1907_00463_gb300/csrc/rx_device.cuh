@@ -549,6 +549,26 @@ struct LoopExt {
     uint32_t lock_fail;         // windows with lock ratio below 0.85
 };
 
+// The public record of a channel's extra loop state and health indicators
+// (rx_channel_health in rx.h), from the device form.
+template <class Health>
+__host__ inline Health health_record(const LoopExt &x) {
+    Health o{};
+    o.cn0_hz = x.cn0;
+    o.lock_ratio = x.lock;
+    o.lock_fail_count = x.lock_fail;
+    o.window_count = x.window_count;
+    o.sum_abs_ip = x.sum_abs;
+    o.sum_power = x.sum_pow;
+    o.sum_diff = x.sum_diff;
+    o.dll_integrator_hz = x.dll_u;
+    o.prev_ip = x.prev_ip;
+    o.prev_qp = x.prev_qp;
+    o.have_prev = x.have_prev;
+    o.pad = 0;
+    return o;
+}
+
 // One update of the full loop set (Table 3):
 //   e_p = atan(Q_P / I_P) / (2 pi);  e_f = atan2(s cross, s dot) / (2 pi) / T with
 //   cross = I1 Q2 - I2 Q1, dot = I1 I2 + Q1 Q2 of the previous and this prompt and

@@ -806,21 +806,7 @@ extern "C" rx_status rx_serve_read_health(rx_serve s, uint32_t id, rx_channel_he
     std::vector<LoopExt> ex(C);
     if (st.ext && cudaMemcpy(ex.data(), st.ext, C * sizeof(LoopExt), cudaMemcpyDeviceToHost) != cudaSuccess)
         return RX_ECUDA;
-    for (size_t c = 0; c < C; ++c) {
-        rx_channel_health &o = out[c];
-        o.cn0_hz = ex[c].cn0;
-        o.lock_ratio = ex[c].lock;
-        o.lock_fail_count = ex[c].lock_fail;
-        o.window_count = ex[c].window_count;
-        o.sum_abs_ip = ex[c].sum_abs;
-        o.sum_power = ex[c].sum_pow;
-        o.sum_diff = ex[c].sum_diff;
-        o.dll_integrator_hz = ex[c].dll_u;
-        o.prev_ip = ex[c].prev_ip;
-        o.prev_qp = ex[c].prev_qp;
-        o.have_prev = ex[c].have_prev;
-        o.pad = 0;
-    }
+    for (size_t c = 0; c < C; ++c) out[c] = health_record<rx_channel_health>(ex[c]);
     return RX_OK;
 }
 
