@@ -401,6 +401,35 @@ def table3_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, ste
             "channels_locked_at_end": locked, "channels": len(health)}
 
 
+def code_batch_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, steps, warmup) -> dict:
+    """The same batched workload in code-period epochs (rx_batch_run_code): every channel
+    closes its loops where its own code period ends and runs the bit synchroniser; one
+    launch (one CTA per channel over the whole second) per step."""
+    import torch
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], n_blocks, device=dev_index,
+                           stream=stream)
+    try:
+        for i, r in enumerate(receivers):
+            rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+        for _ in range(warmup):
+            rx.rx_batch_run_code(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
+        times = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rx.rx_batch_run_code(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        epochs = sum(st.epochs for i, r in enumerate(receivers) for st in rx.rx_batch_read_state(b, i, len(r.channels)))
+    finally:
+        rx.rx_batch_destroy(b)
+    sc = sample_channels(receivers, n_blocks)
+    return {"value": sc / (ms / 1000) / 1e6, "unit": "Msample*channel/s", "ms_per_step": ms, "steps": steps,
+            "epochs_closed_per_step": int(epochs)}
+
+
 ACQ_BINS_HZ = np.arange(-7000.0, 7001.0, 500.0)     # 29 Doppler bins: +-7 kHz at 500 Hz
 ACQ_PRNS = list(range(1, 33))
 
@@ -661,6 +690,10 @@ def run_ours(args):
             del host_cache
     rx.rx_batch_destroy(b)
 
+    code_batch = None
+    if not args.no_code:
+        code_batch = code_batch_leg(rx, synth, receivers, buf, offs, n_blocks, local, stream, 3, args.warmup)
+
     table3 = None
     if not args.no_table3:
         table3 = table3_leg(rx, synth, receivers, buf, offs, n_blocks, local, stream, max(3, args.steps // 2),
@@ -717,6 +750,7 @@ def run_ours(args):
         "serving": serving,
         "plain_form": plain,
         "batched_table3": table3,
+        "batched_code_epochs": code_batch,
         "acquisition": acquisition,
     }
     if rank == 0:
@@ -743,6 +777,7 @@ def main():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-acq", action="store_true")
     p.add_argument("--no-table3", action="store_true")
+    p.add_argument("--no-code", action="store_true")
     p.add_argument("--acq-receivers", type=int, default=N_RX,
                    help="receivers searched by the acquisition leg (default: all of the workload)")
     args = p.parse_args()

@@ -361,6 +361,24 @@ rx_status rx_batch_read_dumps(rx_batch b, uint32_t rx, int32_t *out,
                               size_t cap, uint32_t *n_dumps);
 
 /* Per-channel state of receiver rx after the last run.  Synchronises. */
+/* Code-period epochs for the whole batch (RX_EPOCH_CODE of the plain form, per
+ * channel of every receiver): each channel walks its receiver's n_blocks blocks
+ * as one stream of samples, closing an epoch whenever its prompt code period
+ * ends, with the loops (RX_LOOPS_PLL2_DLL1; RX_EINVAL for a Table 3 receiver)
+ * run at each epoch with T = its samples / fs and the bit synchroniser stepped
+ * (bitsync_count 8); integ_blocks does not apply.  iq must be device memory.
+ * One launch (one CTA per channel), synchronous.  The state continues from the
+ * previous code-period run, or from the starting state with RX_RUN_RESTART;
+ * switching between block runs and code-period runs needs RX_RUN_RESTART
+ * (RX_ESTATE otherwise). */
+rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
+                            uint32_t n_blocks, uint32_t flags);
+/* The epochs receiver rx's channels closed in the last code-period run, laid out
+ * as rx_read_code_epochs; and their RX_EPOCH_CODE state. */
+rx_status rx_batch_read_code_epochs(rx_batch b, uint32_t rx, int32_t *dumps, uint32_t *epoch_samples,
+                                    uint32_t *n_epochs, uint32_t max_epochs);
+rx_status rx_batch_read_code_state(rx_batch b, uint32_t rx, rx_code_state *out, uint32_t cap);
+
 /* RX_LOOPS_TABLE3 state and health indicators of receiver rx's channels
  * (cap >= n_channels; zero for a receiver with RX_LOOPS_PLL2_DLL1).
  * Synchronises the batch's stream. */

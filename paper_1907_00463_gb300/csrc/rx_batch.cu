@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "rx_code.cuh"
 #include "rx_internal.h"
 #include "rx_item.cuh"
 
@@ -46,6 +47,7 @@ struct BatchState {
     uint32_t *acc_blocks;  // blocks integrated since the last dump
     int32_t *acc;          // [tap_base*2 ...]: running sums when L > 1
     LoopExt *ext;          // RX_LOOPS_TABLE3 extra loop state and health
+    rx_code_state *cs;     // code-period runs: open epoch and bit synchroniser
 };
 
 struct BatchArgs {
@@ -253,6 +255,14 @@ struct rx_batch_s {
     uint32_t *d_smmap = nullptr;    // per %smid: group + 1, next slot; then the group counter
     uint32_t n_slots = 0, bal_maxseg = 0, bal_groups = 0;
     size_t bal_smem = 0;
+    // code-period runs (rx_batch_run_code): epoch ring, per-channel walk descriptors
+    int32_t *d_cdump = nullptr;     // [cap][total taps][2]: channel ch at cap * tap0(ch) * 2
+    uint32_t *d_clen = nullptr;     // [channels][cap]
+    uint32_t *d_cnum = nullptr;     // [channels]
+    uint32_t *d_cerr = nullptr;     // [1]
+    CodeWalk *d_walks = nullptr;    // [channels]
+    uint32_t code_cap = 0;          // epochs per channel the ring holds
+    uint32_t last_mode = 0;         // 0: nothing run or restart pending, 1: blocks, 2: code periods
     std::string err;
 };
 
@@ -782,7 +792,8 @@ extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, 
     };
     size_t o_theta = take(C * 4), o_w = take(C * 4), o_phi = take(C * 8), o_r = take(C * 8),
            o_v = take(C * 8), o_fc = take(C * 8), o_fk = take(C * 8), o_ep = take(C * 4),
-           o_ab = take(C * 4), o_acc = take(taps * 8), o_ext = take(C * sizeof(LoopExt));
+           o_ab = take(C * 4), o_acc = take(taps * 8), o_ext = take(C * sizeof(LoopExt)),
+           o_cs = take(C * sizeof(rx_code_state));
     b->state_bytes = off;
     auto fail = [&](rx_status s) {
         rx_batch_destroy(b);
@@ -809,6 +820,7 @@ extern "C" rx_status rx_batch_create(const rx_receiver_desc *rx, uint32_t n_rx, 
     b->st.acc_blocks = (uint32_t *)(p + o_ab);
     b->st.acc = (int32_t *)(p + o_acc);
     b->st.ext = (LoopExt *)(p + o_ext);
+    b->st.cs = (rx_code_state *)(p + o_cs);
     if (cudaMemset(b->d_state, 0, off) != cudaSuccess || cudaMemset(b->d_snap, 0, off) != cudaSuccess ||
         cudaMemset(b->d_prn, 0, C * 4) != cudaSuccess) {
         cudaGetLastError();
@@ -823,8 +835,9 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
-    void *ptrs[] = {b->d_state, b->d_snap, b->d_prn,   b->d_taps, b->d_dumps, b->d_groups, b->d_rxoff,
-                    b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart, b->d_xflag, b->d_smmap};
+    void *ptrs[] = {b->d_state, b->d_snap,  b->d_prn,   b->d_taps,  b->d_dumps, b->d_groups,
+                    b->d_rxoff, b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart,
+                    b->d_xflag, b->d_smmap, b->d_cdump, b->d_clen, b->d_cnum, b->d_cerr, b->d_walks};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_err) cudaFreeHost(b->h_err);
@@ -874,6 +887,7 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
     RX_CUDA_TRY(cudaMemcpy(s.acc_blocks + c0, zero.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemset(s.acc + b->rx_tap0[rxi] * 2, 0, (size_t)n * nt * 8), E);
     RX_CUDA_TRY(cudaMemset(s.ext + c0, 0, (size_t)n * sizeof(LoopExt)), E);
+    RX_CUDA_TRY(cudaMemset(s.cs + c0, 0, (size_t)n * sizeof(rx_code_state)), E);
     RX_CUDA_TRY(cudaMemcpy(b->d_prn + c0, vprn.data(), n * 4, cudaMemcpyHostToDevice), E);
     RX_CUDA_TRY(cudaMemcpy(b->d_taps + b->rx_tap0[rxi], tap_offsets, (size_t)n * nt * 8, cudaMemcpyHostToDevice), E);
     // The restart snapshot mirrors the state block byte for byte.
@@ -892,6 +906,8 @@ extern "C" rx_status rx_batch_set_channels(rx_batch b, uint32_t rxi, const uint8
     RX_CUDA_TRY(snap(s.acc_blocks + c0, n * 4), E);
     RX_CUDA_TRY(snap(s.acc + b->rx_tap0[rxi] * 2, (size_t)n * nt * 8), E);
     RX_CUDA_TRY(snap(s.ext + c0, (size_t)n * sizeof(LoopExt)), E);
+    RX_CUDA_TRY(snap(s.cs + c0, (size_t)n * sizeof(rx_code_state)), E);
+    b->last_mode = 0;
     b->rx_set[rxi] = 1;
     return RX_OK;
 }
@@ -993,6 +1009,9 @@ extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *
         }
         src = b->d_stage;
     }
+    if (b->last_mode == 2 && !(flags & RX_RUN_RESTART))
+        return berr(b, RX_ESTATE, "after a code-period run, a block run needs RX_RUN_RESTART");
+    b->last_mode = 1;
     std::vector<uint64_t> off(rx_byte_offset, rx_byte_offset + b->n_rx);
     if (b->g_off != off) {
         RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
@@ -1215,5 +1234,140 @@ extern "C" rx_status rx_batch_read_health(rx_batch b, uint32_t rxi, rx_channel_h
     RX_CUDA_TRY(cudaMemcpy(ex.data(), b->st.ext + b->rx_ch0[rxi], n * sizeof(LoopExt), cudaMemcpyDeviceToHost),
                 b->err);
     for (size_t c = 0; c < n; ++c) out[c] = health_record<rx_channel_health>(ex[c]);
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
+                                       uint32_t n_blocks, uint32_t flags) {
+    if (!b) return RX_EINVAL;
+    if (!iq || !rx_byte_offset || n_blocks == 0) return berr(b, RX_EINVAL, "null input or zero blocks");
+    if (n_blocks > b->max_blocks) return berr(b, RX_EINVAL, "n_blocks > max_blocks");
+    if (!rxh::is_device_pointer(iq)) return berr(b, RX_EINVAL, "code-period runs read device samples only");
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        if (!b->rx_set[r]) return berr(b, RX_ESTATE, rxh::fmt("receiver %u has no channels set", r));
+        if (rx_byte_offset[r] & 15) return berr(b, RX_EINVAL, "receiver offsets must be 16-byte aligned");
+        if (b->rx[r].loop_set != RX_LOOPS_PLL2_DLL1)
+            return berr(b, RX_EINVAL, "code-period runs use the basic loops (RX_LOOPS_PLL2_DLL1)");
+        if ((uint64_t)n_blocks * b->rx[r].block_samples >= (1ull << 31))
+            return berr(b, RX_EINVAL, "run longer than 2^31 samples");
+    }
+    if (b->last_mode == 1 && !(flags & RX_RUN_RESTART))
+        return berr(b, RX_ESTATE, "after a block run, a code-period run needs RX_RUN_RESTART");
+    cudaSetDevice(b->device);
+    std::string &E = b->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+    // the epoch ring: every channel's epochs of this run
+    uint32_t cap = 0;
+    for (const rx_receiver_desc &d : b->rx)
+        cap = std::max(cap, rxh::code_ring_epochs(d.fs_hz, (uint64_t)n_blocks * d.block_samples));
+    if (cap > b->code_cap || !b->d_walks) {
+        for (void *q : {(void *)b->d_cdump, (void *)b->d_clen, (void *)b->d_cnum, (void *)b->d_cerr,
+                        (void *)b->d_walks})
+            if (q) cudaFree(q);
+        b->d_cdump = nullptr;
+        b->d_clen = b->d_cnum = b->d_cerr = nullptr;
+        b->d_walks = nullptr;
+        b->code_cap = 0;
+        if (cudaMalloc(&b->d_cdump, (size_t)cap * b->n_taps_total * 8) != cudaSuccess ||
+            cudaMalloc(&b->d_clen, (size_t)cap * b->n_ch * 4) != cudaSuccess ||
+            cudaMalloc(&b->d_cnum, (size_t)b->n_ch * 4) != cudaSuccess ||
+            cudaMalloc(&b->d_cerr, 4) != cudaSuccess ||
+            cudaMalloc(&b->d_walks, (size_t)b->n_ch * sizeof(CodeWalk)) != cudaSuccess) {
+            cudaGetLastError();
+            return berr(b, RX_ENOMEM, "code-period epoch ring");
+        }
+        b->code_cap = cap;
+    }
+    std::vector<CodeWalk> walks(b->n_ch);
+    std::vector<uint32_t> prn(b->n_ch);
+    RX_CUDA_TRY(cudaMemcpy(prn.data(), b->d_prn, (size_t)b->n_ch * 4, cudaMemcpyDeviceToHost), E);
+    const BatchState &s = b->st;
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        const rx_receiver_desc &d = b->rx[r];
+        const CodeLoop cl = rxh::code_loop(d.fs_hz, d.pll_bn_hz, d.dll_bn_hz);
+        for (uint32_t c = 0; c < d.n_channels; ++c) {
+            const uint32_t ch = b->rx_ch0[r] + c;
+            const uint64_t tap0 = b->rx_tap0[r] + (uint64_t)c * d.n_taps;
+            CodeWalk &a = walks[ch];
+            a.iq = iq + rx_byte_offset[r];
+            a.nsamp = n_blocks * d.block_samples;
+            a.prn = prn[ch];
+            a.ntaps = d.n_taps;
+            a.cap = b->code_cap;
+            a.tap_e = d.tap_early;
+            a.tap_p = d.tap_prompt;
+            a.tap_l = d.tap_late;
+            a.sync_k = 8;
+            a.cl = cl;
+            a.theta = s.theta + ch;
+            a.w = s.w + ch;
+            a.phi = s.phi + ch;
+            a.r = s.r + ch;
+            a.v = s.v + ch;
+            a.fcarr = s.fcarr + ch;
+            a.fcode = s.fcode + ch;
+            a.epochs = s.epochs + ch;
+            a.acc = s.acc + tap0 * 2;
+            a.taps = b->d_taps + tap0;
+            a.cs = s.cs + ch;
+            a.dumps = b->d_cdump + (size_t)b->code_cap * tap0 * 2;
+            a.lens = b->d_clen + (size_t)ch * b->code_cap;
+            a.nclosed = b->d_cnum + ch;
+            a.err = b->d_cerr;
+        }
+    }
+    RX_CUDA_TRY(cudaMemcpy(b->d_walks, walks.data(), walks.size() * sizeof(CodeWalk), cudaMemcpyHostToDevice), E);
+    if (flags & RX_RUN_RESTART)
+        RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
+    RX_CUDA_TRY(cudaMemsetAsync(b->d_cerr, 0, 4, b->stream), E);
+    RX_CUDA_TRY(rxh::launch_code_walks(b->d_walks, b->n_ch, b->max_taps, b->tables, b->stream), E);
+    uint32_t cerr = 0;
+    RX_CUDA_TRY(cudaMemcpyAsync(&cerr, b->d_cerr, 4, cudaMemcpyDeviceToHost, b->stream), E);
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+    b->last_mode = 2;
+    b->last_launches = 1;
+    if (cerr & 2u) return berr(b, RX_EINVAL, "a channel's code word reached 2^32");
+    if (cerr & 1u) return berr(b, RX_EINVAL, "a channel closed more epochs than the ring holds");
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_read_code_epochs(rx_batch b, uint32_t rxi, int32_t *dumps, uint32_t *epoch_samples,
+                                               uint32_t *n_epochs, uint32_t max_epochs) {
+    if (!b || !dumps || !epoch_samples || !n_epochs) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    if (b->last_mode != 2) return berr(b, RX_ESTATE, "no code-period run yet");
+    const rx_receiver_desc &d = b->rx[rxi];
+    const uint32_t n = d.n_channels, T = d.n_taps, cap = b->code_cap;
+    cudaSetDevice(b->device);
+    std::string &E = b->err;
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+    RX_CUDA_TRY(cudaMemcpy(n_epochs, b->d_cnum + b->rx_ch0[rxi], (size_t)n * 4, cudaMemcpyDeviceToHost), E);
+    for (uint32_t c = 0; c < n; ++c)
+        if (n_epochs[c] > max_epochs)
+            return berr(b, RX_EINVAL, rxh::fmt("channel %u closed %u epochs > max_epochs %u", c, n_epochs[c],
+                                               max_epochs));
+    std::memset(dumps, 0, (size_t)n * max_epochs * T * 8);
+    std::memset(epoch_samples, 0, (size_t)n * max_epochs * 4);
+    for (uint32_t c = 0; c < n; ++c) {
+        if (n_epochs[c] == 0) continue;
+        const uint64_t tap0 = b->rx_tap0[rxi] + (uint64_t)c * T;
+        RX_CUDA_TRY(cudaMemcpy(dumps + (size_t)c * max_epochs * T * 2, b->d_cdump + (size_t)cap * tap0 * 2,
+                               (size_t)n_epochs[c] * T * 8, cudaMemcpyDeviceToHost), E);
+        RX_CUDA_TRY(cudaMemcpy(epoch_samples + (size_t)c * max_epochs,
+                               b->d_clen + (size_t)(b->rx_ch0[rxi] + c) * cap, (size_t)n_epochs[c] * 4,
+                               cudaMemcpyDeviceToHost), E);
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_read_code_state(rx_batch b, uint32_t rxi, rx_code_state *out, uint32_t cap) {
+    if (!b || !out) return RX_EINVAL;
+    if (rxi >= b->n_rx) return berr(b, RX_EINVAL, "receiver index out of range");
+    const uint32_t n = b->rx[rxi].n_channels;
+    if (cap < n) return berr(b, RX_EINVAL, "cap < n_channels");
+    cudaSetDevice(b->device);
+    RX_CUDA_TRY(cudaStreamSynchronize(b->stream), b->err);
+    RX_CUDA_TRY(cudaMemcpy(out, b->st.cs + b->rx_ch0[rxi], n * sizeof(rx_code_state), cudaMemcpyDeviceToHost),
+                b->err);
     return RX_OK;
 }

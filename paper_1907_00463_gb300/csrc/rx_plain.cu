@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "rx_code.cuh"
 #include "rx_device.cuh"
 #include "rx_internal.h"
 
@@ -219,13 +220,6 @@ __global__ void k_plain_track3(PlainState st, uint32_t n_ch, uint32_t ntaps, uin
     for (uint32_t i = 0; i < 2 * ntaps; ++i) a[i] = 0;
 }
 
-// Loop constants of RX_EPOCH_CODE: k1 = w0^2 T depends on each epoch's length,
-// so only w0^2 is precomputed and k1 = w0sq (n / fs) is formed per epoch with
-// the same two correctly rounded operations as make_loop_consts.
-struct CodeLoop {
-    double w0sq, k2, kdll, sfs, fs;
-};
-
 // One closed epoch of the bit synchroniser (the rules are in rx_code_state's
 // description in rx.h).
 __device__ void bitsync_step(rx_code_state &b, int32_t ip, uint32_t k) {
@@ -264,18 +258,15 @@ __device__ void bitsync_step(rx_code_state &b, int32_t ip, uint32_t k) {
     b.epoch = e + 1;
 }
 
-// RX_EPOCH_CODE, one CTA per channel: walk the call's samples epoch by epoch.
-// From code phase phi the open epoch ends after b = ceil((1023 2^32 - phi) / r)
-// more samples; the CTA correlates min(b, rest) samples with the current words
-// (all threads, chunks of SPT), and at the end of the period thread 0 dumps the
-// sums, runs the loops with T = (epoch samples) / fs, steps the bit
-// synchroniser and loads the new words for the next sample.
-__global__ void __launch_bounds__(kPlainThreads)
-    k_plain_code(const int8_t *__restrict__ iq, uint32_t nsamp, PlainState st, uint32_t ntaps,
-                 uint32_t cap, CodeLoop cl, int tap_e, int tap_p, int tap_l, uint32_t sync_k,
-                 const uint32_t *__restrict__ code_tab, const uint32_t *__restrict__ carrier_tab,
-                 const uint16_t *__restrict__ pair_tab) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// RX_EPOCH_CODE, one CTA per channel: walk the samples epoch by epoch.  From code
+// phase phi the open epoch ends after b = ceil((1023 2^32 - phi) / r) more samples;
+// the CTA correlates min(b, rest) samples with the current words (all threads,
+// chunks of SPT), and at the end of the period thread 0 dumps the sums, runs the
+// loops with T = (epoch samples) / fs, steps the bit synchroniser and loads the new
+// words for the next sample.  smem: the plain correlator's layout for ntaps taps.
+__device__ void code_walk(const CodeWalk &a, unsigned char *smem, const uint32_t *__restrict__ code_tab,
+                          const uint32_t *__restrict__ carrier_tab, const uint16_t *__restrict__ pair_tab) {
+    const uint32_t ntaps = a.ntaps;
     int4 *s_slices = reinterpret_cast<int4 *>(smem);
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_slices + kPlainThreads * SLICE_INT4);
     int64_t *s_taps = reinterpret_cast<int64_t *>(s_pair + PAIR_LEN);
@@ -285,34 +276,35 @@ __global__ void __launch_bounds__(kPlainThreads)
     __shared__ uint32_t s_theta, s_w, s_stop;
     __shared__ unsigned long long s_phi, s_r;
 
-    const uint32_t ch = blockIdx.x;
-    const uint32_t prn = st.prn[ch];
-    for (uint32_t i = threadIdx.x; i < ntaps; i += blockDim.x) s_taps[i] = st.taps[(size_t)ch * ntaps + i];
+    const uint32_t prn = a.prn;
+    for (uint32_t i = threadIdx.x; i < ntaps; i += blockDim.x) s_taps[i] = a.taps[i];
     for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) s_tab[i] = carrier_tab[i];
     for (uint32_t i = threadIdx.x; i < EXT_WORDS; i += blockDim.x)
         s_code[i] = code_tab[(size_t)prn * EXT_WORDS + i];
-    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) s_red[i] = st.acc[(size_t)ch * ntaps * 2 + i];
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) s_red[i] = a.acc[i];
     for (uint32_t i = threadIdx.x; i < PAIR_LEN / 8; i += blockDim.x)
         reinterpret_cast<uint4 *>(s_pair)[i] =
             reinterpret_cast<const uint4 *>(pair_tab + (size_t)prn * PAIR_LEN)[i];
-    // thread 0 owns the loop state for the whole call
+    // thread 0 owns the loop state for the whole walk
     rx_code_state cs;
     double v = 0, fcarr = 0, fcode = 0;
     uint32_t epochs = 0, closed = 0;
     if (threadIdx.x == 0) {
-        cs = st.cs[ch];
-        v = st.v[ch];
-        fcarr = st.fcarr[ch];
-        fcode = st.fcode[ch];
-        epochs = st.epochs[ch];
-        s_theta = st.theta[ch];
-        s_w = (uint32_t)st.w[ch];
-        s_phi = st.phi[ch];
-        s_r = st.r[ch];
-        s_stop = st.r[ch] >= (1ull << 32) ? 1u : 0u;
+        cs = *a.cs;
+        v = *a.v;
+        fcarr = *a.fcarr;
+        fcode = *a.fcode;
+        epochs = *a.epochs;
+        s_theta = *a.theta;
+        s_w = (uint32_t)*a.w;
+        s_phi = *a.phi;
+        s_r = *a.r;
+        s_stop = *a.r >= (1ull << 32) ? 1u : 0u;
     }
     __syncthreads();
 
+    const int8_t *iq = a.iq;
+    const uint32_t nsamp = a.nsamp, cap = a.cap;
     uint32_t pos = 0;
     while (pos < nsamp && !s_stop) {
         const uint32_t theta = s_theta, w = s_w;
@@ -337,32 +329,32 @@ __global__ void __launch_bounds__(kPlainThreads)
             cs.samples_in_epoch += seg;
             if ((uint64_t)seg == b) {
                 if (closed < cap) {
-                    int32_t *d = st.cdump + ((size_t)ch * cap + closed) * ntaps * 2;
+                    int32_t *d = a.dumps + (size_t)closed * ntaps * 2;
                     for (uint32_t i = 0; i < 2 * ntaps; ++i) d[i] = s_red[i];
-                    st.clen[(size_t)ch * cap + closed] = cs.samples_in_epoch;
+                    a.lens[closed] = cs.samples_in_epoch;
                 } else {
-                    atomicOr(st.cerr, 1u);
+                    atomicOr(a.err, 1u);
                 }
                 LoopConsts lc;
-                lc.k1 = __dmul_rn(cl.w0sq, __ddiv_rn((double)cs.samples_in_epoch, cl.fs));
-                lc.k2 = cl.k2;
-                lc.kdll = cl.kdll;
-                lc.sfs = cl.sfs;
-                LoopOut o = loop_update(v, s_red[2 * tap_e], s_red[2 * tap_e + 1], s_red[2 * tap_p],
-                                        s_red[2 * tap_p + 1], s_red[2 * tap_l], s_red[2 * tap_l + 1],
-                                        s_taps[tap_e], s_taps[tap_l], lc);
+                lc.k1 = __dmul_rn(a.cl.w0sq, __ddiv_rn((double)cs.samples_in_epoch, a.cl.fs));
+                lc.k2 = a.cl.k2;
+                lc.kdll = a.cl.kdll;
+                lc.sfs = a.cl.sfs;
+                LoopOut o = loop_update(v, s_red[2 * a.tap_e], s_red[2 * a.tap_e + 1], s_red[2 * a.tap_p],
+                                        s_red[2 * a.tap_p + 1], s_red[2 * a.tap_l], s_red[2 * a.tap_l + 1],
+                                        s_taps[a.tap_e], s_taps[a.tap_l], lc);
                 v = o.v;
                 fcarr = o.f_carr;
                 fcode = o.f_code;
                 epochs += 1;
-                bitsync_step(cs, s_red[2 * tap_p], sync_k);
+                bitsync_step(cs, s_red[2 * a.tap_p], a.sync_k);
                 for (uint32_t i = 0; i < 2 * ntaps; ++i) s_red[i] = 0;
                 cs.samples_in_epoch = 0;
                 closed += 1;
                 s_w = (uint32_t)o.w;
                 s_r = o.r;
                 if (o.r >= (1ull << 32)) {
-                    atomicOr(st.cerr, 2u);
+                    atomicOr(a.err, 2u);
                     s_stop = 1;
                 }
             }
@@ -371,18 +363,65 @@ __global__ void __launch_bounds__(kPlainThreads)
         pos += seg;
     }
     if (threadIdx.x == 0) {
-        st.cs[ch] = cs;
-        st.v[ch] = v;
-        st.fcarr[ch] = fcarr;
-        st.fcode[ch] = fcode;
-        st.epochs[ch] = epochs;
-        st.theta[ch] = s_theta;
-        st.w[ch] = (int32_t)s_w;
-        st.phi[ch] = s_phi;
-        st.r[ch] = s_r;
-        st.cnum[ch] = min(closed, cap);
+        *a.cs = cs;
+        *a.v = v;
+        *a.fcarr = fcarr;
+        *a.fcode = fcode;
+        *a.epochs = epochs;
+        *a.theta = s_theta;
+        *a.w = (int32_t)s_w;
+        *a.phi = s_phi;
+        *a.r = s_r;
+        *a.nclosed = min(closed, cap);
     }
-    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) st.acc[(size_t)ch * ntaps * 2 + i] = s_red[i];
+    for (uint32_t i = threadIdx.x; i < 2 * ntaps; i += blockDim.x) a.acc[i] = s_red[i];
+}
+
+// RX_EPOCH_CODE for the plain form: CTA ch walks channel ch over the call's samples.
+__global__ void __launch_bounds__(kPlainThreads)
+    k_plain_code(const int8_t *__restrict__ iq, uint32_t nsamp, PlainState st, uint32_t ntaps,
+                 uint32_t cap, CodeLoop cl, int tap_e, int tap_p, int tap_l, uint32_t sync_k,
+                 const uint32_t *__restrict__ code_tab, const uint32_t *__restrict__ carrier_tab,
+                 const uint16_t *__restrict__ pair_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t ch = blockIdx.x;
+    CodeWalk a;
+    a.iq = iq;
+    a.nsamp = nsamp;
+    a.prn = st.prn[ch];
+    a.ntaps = ntaps;
+    a.cap = cap;
+    a.tap_e = tap_e;
+    a.tap_p = tap_p;
+    a.tap_l = tap_l;
+    a.sync_k = sync_k;
+    a.cl = cl;
+    a.theta = st.theta + ch;
+    a.w = st.w + ch;
+    a.phi = st.phi + ch;
+    a.r = st.r + ch;
+    a.v = st.v + ch;
+    a.fcarr = st.fcarr + ch;
+    a.fcode = st.fcode + ch;
+    a.epochs = st.epochs + ch;
+    a.acc = st.acc + (size_t)ch * ntaps * 2;
+    a.taps = st.taps + (size_t)ch * ntaps;
+    a.cs = st.cs + ch;
+    a.dumps = st.cdump + (size_t)ch * cap * ntaps * 2;
+    a.lens = st.clen + (size_t)ch * cap;
+    a.nclosed = st.cnum + ch;
+    a.err = st.cerr;
+    code_walk(a, smem, code_tab, carrier_tab, pair_tab);
+}
+
+// RX_EPOCH_CODE for the batched form: CTA k walks walks[k], one channel of one
+// receiver over the receiver's whole run.
+__global__ void __launch_bounds__(kPlainThreads, 6)
+    k_batch_code(const CodeWalk *__restrict__ walks, const uint32_t *__restrict__ code_tab,
+                 const uint32_t *__restrict__ carrier_tab, const uint16_t *__restrict__ pair_tab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CodeWalk a = walks[blockIdx.x];
+    code_walk(a, smem, code_tab, carrier_tab, pair_tab);
 }
 
 }  // namespace
@@ -456,11 +495,7 @@ extern "C" rx_status rx_create(const rx_config *cfg, rx_handle *out) {
            o_ext = take(C * sizeof(LoopExt)), o_stage = take(2 * (size_t)cfg->max_block_samples + 64);
     // RX_EPOCH_CODE: a ring of the epochs each channel closes in one call.  An epoch
     // lasts 1023 2^32 / r samples; the ring allows code rates up to 1.1 x 1.023 Mchip/s.
-    if (cfg->epoch_mode == RX_EPOCH_CODE) {
-        uint64_t min_epoch = (uint64_t)std::floor(0.9 * cfg->fs_hz / 1000.0);
-        if (min_epoch == 0) min_epoch = 1;
-        h->code_cap = (uint32_t)(cfg->max_block_samples / min_epoch + 2);
-    }
+    if (cfg->epoch_mode == RX_EPOCH_CODE) h->code_cap = rxh::code_ring_epochs(cfg->fs_hz, cfg->max_block_samples);
     const size_t E = h->code_cap;
     size_t o_cs = take(C * sizeof(rx_code_state)), o_cdump = take(C * E * T * 8 + 8),
            o_clen = take(C * E * 4 + 4), o_cnum = take(C * 4), o_cerr = take(4);
@@ -769,15 +804,7 @@ extern "C" rx_status rx_track_code(rx_handle h, const int8_t *iq, uint32_t nsamp
         RX_CUDA_TRY(cudaMemcpyAsync(h->d_stage, iq, 2 * (size_t)nsamp, cudaMemcpyHostToDevice, h->stream), E);
         src = h->d_stage;
     }
-    const double fs = h->cfg.fs_hz;
-    const LoopConsts base = make_loop_consts(fs, 1, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz);
-    CodeLoop cl;
-    const double w0 = h->cfg.pll_bn_hz / 0.53;
-    cl.w0sq = w0 * w0;
-    cl.k2 = base.k2;
-    cl.kdll = base.kdll;
-    cl.sfs = base.sfs;
-    cl.fs = fs;
+    const CodeLoop cl = rxh::code_loop(h->cfg.fs_hz, h->cfg.pll_bn_hz, h->cfg.dll_bn_hz);
     const uint32_t sync_k = h->cfg.bitsync_count ? h->cfg.bitsync_count : 8u;
     size_t smem = (size_t)kPlainThreads * SLICE_INT4 * 16 + PAIR_LEN * 2 + (size_t)h->n_taps * 8 +
                   64 * 4 + EXT_WORDS * 4 + (size_t)h->n_taps * 8;
@@ -842,3 +869,36 @@ extern "C" rx_status rx_write_code_state(rx_handle h, const rx_code_state *in, u
     if (n) RX_CUDA_TRY(cudaMemcpy(h->st.cs, in, n * sizeof(rx_code_state), cudaMemcpyHostToDevice), h->err);
     return RX_OK;
 }
+
+namespace rxh {
+
+size_t code_walk_smem(uint32_t max_taps) {
+    return (size_t)kPlainThreads * SLICE_INT4 * 16 + PAIR_LEN * 2 + (size_t)max_taps * 8 + 64 * 4 +
+           EXT_WORDS * 4 + (size_t)max_taps * 8;
+}
+
+cudaError_t launch_code_walks(const CodeWalk *walks, uint32_t n, uint32_t max_taps, const DeviceTables *t,
+                              cudaStream_t stream) {
+    k_batch_code<<<n, kPlainThreads, code_walk_smem(max_taps), stream>>>(walks, t->code, t->tab, t->pair);
+    return cudaGetLastError();
+}
+
+CodeLoop code_loop(double fs, double pll_bn, double dll_bn) {
+    const LoopConsts base = make_loop_consts(fs, 1, pll_bn, dll_bn);
+    CodeLoop cl;
+    const double w0 = pll_bn / 0.53;
+    cl.w0sq = w0 * w0;
+    cl.k2 = base.k2;
+    cl.kdll = base.kdll;
+    cl.sfs = base.sfs;
+    cl.fs = fs;
+    return cl;
+}
+
+uint32_t code_ring_epochs(double fs, uint64_t samples) {
+    uint64_t min_epoch = (uint64_t)std::floor(0.9 * fs / 1000.0);
+    if (min_epoch == 0) min_epoch = 1;
+    return (uint32_t)(samples / min_epoch + 2);
+}
+
+}  // namespace rxh

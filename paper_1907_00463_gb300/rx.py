@@ -173,6 +173,9 @@ SIGNATURES = [
     ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_batch_read_health", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_health), C.c_uint32]),
+    ("rx_batch_run_code", C.c_int, [P, P, P, C.c_uint32, C.c_uint32]),
+    ("rx_batch_read_code_epochs", C.c_int, [P, C.c_uint32, P, P, P, C.c_uint32]),
+    ("rx_batch_read_code_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_code_state), C.c_uint32]),
     ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     ("rx_batch_set_wait_limit", C.c_int, [P, C.c_uint64, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -742,4 +745,28 @@ def rx_serve_read_health(s, sid: int, n_ch: int) -> list:
     st = lib.rx_serve_read_health(s, sid, arr, n_ch)
     if st != RX_OK:
         raise RxError(st, lib.rx_serve_last_error(s).decode())
+    return list(arr)
+
+
+def rx_batch_run_code(b, iq, rx_byte_offset, n_blocks: int, flags: int = 0) -> None:
+    """Code-period epochs for every channel of the batch over n_blocks blocks (device iq)."""
+    lib = load()
+    off = _arr(rx_byte_offset, np.uint64)
+    _check(b, lib.rx_batch_run_code(b, _ptr(iq), _ptr(off), n_blocks, flags), lib.rx_batch_last_error)
+
+
+def rx_batch_read_code_epochs(b, rx: int, n_ch: int, n_taps: int, max_epochs: int):
+    lib = load()
+    d = np.zeros((n_ch, max_epochs, n_taps, 2), np.int32)
+    ln = np.zeros((n_ch, max_epochs), np.uint32)
+    n = np.zeros(n_ch, np.uint32)
+    _check(b, lib.rx_batch_read_code_epochs(b, rx, _ptr(d), _ptr(ln), _ptr(n), max_epochs),
+           lib.rx_batch_last_error)
+    return d, ln, n
+
+
+def rx_batch_read_code_state(b, rx: int, n_ch: int) -> list:
+    lib = load()
+    arr = (rx_code_state * n_ch)()
+    _check(b, lib.rx_batch_read_code_state(b, rx, arr, n_ch), lib.rx_batch_last_error)
     return list(arr)
