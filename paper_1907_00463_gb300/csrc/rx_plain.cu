@@ -13,6 +13,7 @@
 #include "rx_code.cuh"
 #include "rx_device.cuh"
 #include "rx_internal.h"
+#include "rx_item.cuh"
 
 using namespace rxd;
 
@@ -275,6 +276,12 @@ __device__ void code_walk(const CodeWalk &a, unsigned char *smem, const uint32_t
     int32_t *s_red = reinterpret_cast<int32_t *>(s_code + EXT_WORDS);
     __shared__ uint32_t s_theta, s_w, s_stop;
     __shared__ unsigned long long s_phi, s_r;
+    ItemSmem view{};   // the fields the correlator reads, over this CTA's shared memory
+    view.taps = s_taps;
+    view.tab = s_tab;
+    view.code = s_code;
+    view.pair = s_pair;
+    view.slices = s_slices;
 
     const uint32_t prn = a.prn;
     for (uint32_t i = threadIdx.x; i < ntaps; i += blockDim.x) s_taps[i] = a.taps[i];
@@ -313,15 +320,10 @@ __device__ void code_walk(const CodeWalk &a, unsigned char *smem, const uint32_t
         const uint32_t seg = (uint32_t)min(b, (uint64_t)(nsamp - pos));
         const int8_t *blk = iq + 2 * (size_t)pos;
         const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-        // every thread takes part in every round: plain_chunk reduces across full warps,
-        // and a chunk past the segment's end loads as zeros (and adds nothing)
-        for (uint32_t base = 0; base < seg; base += kPlainThreads * SPT) {
-            const uint32_t s0 = base + threadIdx.x * SPT;
-            uint32_t x[SPT];
-            load_chunk(blk, s0, seg, a16, a4, x);
-            plain_chunk(x, theta + s0 * w, w, reduce_code_phase(phi + (uint64_t)s0 * r), (uint32_t)r,
-                        ntaps, s_taps, s_code, s_tab, s_pair, s_slices, s_red);
-        }
+        // the segment as one range of the batched correlator: each thread sums its chunks
+        // in registers and every thread reaches the one warp reduction at the end
+        correlate_channel_at<kPlainThreads, false>(0, ntaps, seg, blk, a16, a4, view, s_red, theta, w, phi,
+                                                   (uint32_t)r);
         __syncthreads();
         if (threadIdx.x == 0) {
             s_theta = theta + seg * w;
