@@ -324,6 +324,12 @@ __device__ void code_walk(const CodeWalk &a, unsigned char *smem, const uint32_t
         // in registers and every thread reaches the one warp reduction at the end
         correlate_channel_at<kPlainThreads, false>(0, ntaps, seg, blk, a16, a4, view, s_red, theta, w, phi,
                                                    (uint32_t)r);
+        // while thread 0 closes the loops, have the next epoch's samples (about one
+        // code period) fetched into L2
+        if (threadIdx.x == 32 && (uint64_t)seg == b && pos + seg < nsamp) {
+            const uint64_t next = min((uint64_t)(nsamp - pos - seg), b + 64);
+            prefetch_l2(blk + 2 * (size_t)seg, (uint32_t)(2 * next));
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             s_theta = theta + seg * w;
