@@ -343,14 +343,28 @@ rx_status rx_batch_set_channels(rx_batch b, uint32_t rx, const uint8_t *prn,
  * loops at its own integration boundaries, in one persistent kernel launch.
  * Receiver r's samples are the 2*N_r*n_blocks int8 values at iq +
  * rx_byte_offset[r] (16-byte aligned offsets; host array of n_rx entries).
- * iq is a device pointer (read in stream order) or host memory (copied to a
- * library-owned device buffer inside the call).  The launch is recorded in a
- * CUDA graph on first use and replayed while iq, offsets and n_blocks repeat.
- * Dumps append to each receiver's dump buffer.  A device wait that exceeds its
- * bound returns RX_ETIMEOUT (the stream is synchronised in that case). */
+ * iq is a device pointer (read in stream order) or host memory, copied in
+ * stream order to a library-owned device buffer (pinned memory is copied
+ * asynchronously: keep it unchanged until rx_batch_sync or a read returns).
+ * Large host inputs are copied and tracked in chunks of blocks, one launch
+ * per chunk, so that copying overlaps tracking (rx_batch_set_host_chunk).
+ * Otherwise the launch is recorded in a CUDA graph on first use and replayed
+ * while iq, offsets and n_blocks repeat.  Dumps append to each receiver's dump
+ * buffer.  A device wait that exceeds its bound is reported as RX_ETIMEOUT by
+ * the next synchronising call. */
 rx_status rx_batch_run(rx_batch b, const int8_t *iq,
                        const uint64_t *rx_byte_offset, uint32_t n_blocks,
                        uint32_t flags);
+
+/* Blocks per chunk when rx_batch_run gets host memory.  Chunk c's blocks of
+ * every receiver are copied on a library stream, and its launch, which
+ * continues the state chunk c-1 left, waits only for that copy, so the copy of
+ * chunk c+1 overlaps the tracking of chunk c (as the producer/consumer loops
+ * of Sec. 3.2-3.3 overlap acquisition of the next block with tracking of the
+ * current one).  0, the default, takes sixteen chunks when the run's host
+ * input is at least 64 MiB and one otherwise.  Every chunking gives the same dumps
+ * and state. */
+rx_status rx_batch_set_host_chunk(rx_batch b, uint32_t chunk_blocks);
 
 /* Block until the batch's stream is idle; report a device-side timeout. */
 rx_status rx_batch_sync(rx_batch b);
@@ -359,6 +373,13 @@ rx_status rx_batch_sync(rx_batch b);
  * out (cap elements).  *n_dumps receives the count.  Synchronises. */
 rx_status rx_batch_read_dumps(rx_batch b, uint32_t rx, int32_t *out,
                               size_t cap, uint32_t *n_dumps);
+
+/* Every receiver's dumps in one call: receiver r's int32
+ * [n_dumps[r]][n_channels][n_taps][2], receivers in order, each packed right
+ * after the previous one in out (cap elements); n_dumps has n_rx entries.
+ * Synchronises.  One device-to-host copy when every receiver's dump buffer is
+ * full (n_dumps[r] = max_blocks / integ_blocks), else one per receiver. */
+rx_status rx_batch_read_all_dumps(rx_batch b, int32_t *out, size_t cap, uint32_t *n_dumps);
 
 /* Per-channel state of receiver rx after the last run.  Synchronises. */
 /* Code-period epochs for the whole batch (RX_EPOCH_CODE of the plain form, per

@@ -235,6 +235,14 @@ struct rx_batch_s {
     uint32_t *h_err = nullptr;      // pinned copy of err[4]
     int8_t *d_stage = nullptr;
     size_t stage_bytes = 0;
+    // host input in chunks: copies on copy_stream, chunk c's launch waits on chunk_ev[c]
+    uint32_t host_chunk = 0;        // blocks per chunk (0: automatic)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
+    uint64_t *d_chunk_off = nullptr;  // [chunks][n_rx] receiver offsets of each chunk's first block
+    uint32_t chunk_off_cap = 0;       // chunks d_chunk_off holds
+    std::vector<uint64_t> c_off;      // host copy of what d_chunk_off holds
     // tiles
     uint32_t cpg = 0, threads = 0, ctas_per_sm = 0, G = 0, grid = 0, schedule = RX_SCHED_DYNAMIC;
     bool groups_dirty = true;
@@ -653,14 +661,24 @@ void drop_graph(rx_batch b) {
 }
 
 // Enqueue one run on b->stream (also used under stream capture).
-rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t flags) {
+// One launch over n_blocks blocks whose receiver r starts at iq + rxoff[r] (device
+// array; b->d_rxoff by default).  keep_err leaves the error words of an earlier
+// launch of the same call in place, so that the call reports them.
+rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t flags,
+                      const uint64_t *rxoff = nullptr, bool keep_err = false) {
     std::string &E = b->err;
+    if (!rxoff) rxoff = b->d_rxoff;
     if (flags & RX_RUN_RESTART)
         RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
-    RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, (5 + (size_t)b->G) * 4, b->stream), E);
+    if (keep_err) {   // ticket and done[G] only
+        RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, 4, b->stream), E);
+        RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch + 5, 0, (size_t)b->G * 4, b->stream), E);
+    } else {
+        RX_CUDA_TRY(cudaMemsetAsync(b->d_scratch, 0, (5 + (size_t)b->G) * 4, b->stream), E);
+    }
     BatchArgs ba;
     ba.groups = b->d_groups;
-    ba.src_off = b->d_rxoff;
+    ba.src_off = rxoff;
     ba.iq = iq;
     ba.tb = Tables{b->tables->code, b->tables->tab, b->tables->pair};
     ba.ticket = b->d_scratch;
@@ -675,7 +693,7 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     if (b->schedule == RX_SCHED_BALANCED) {
         RX_CUDA_TRY(cudaMemsetAsync(b->d_xflag, 0, std::max<size_t>(1, b->n_slots) * 4, b->stream), E);
         RX_CUDA_TRY(cudaMemsetAsync(b->d_smmap, 0, (2 * 1024 + 1) * 4, b->stream), E);
-        BalArgs la{b->d_segs,   b->d_nseg,      b->d_rxoff,      iq,         ba.tb,          b->d_xpart,
+        BalArgs la{b->d_segs,   b->d_nseg,      rxoff,           iq,         ba.tb,          b->d_xpart,
                    b->d_xflag,  ba.err,         b->timeout_ns,   n_blocks,   b->bal_maxseg,  b->max_taps,
                    b->ctas_per_sm, b->bal_groups, b->d_smmap,   b->d_smmap + 2 * 1024};
         cudaError_t ce = bal_launch(b->threads, b->grid, b->bal_smem, b->stream, la);
@@ -684,7 +702,7 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
         return RX_OK;
     }
     if (b->schedule == RX_SCHED_PIPE) {
-        PipeArgs pa{b->d_groups, b->d_rxoff, iq,       ba.tb,      ba.err,        b->timeout_ns,
+        PipeArgs pa{b->d_groups, rxoff,      iq,       ba.tb,      ba.err,        b->timeout_ns,
                     n_blocks,    b->cpg,     b->max_taps, b->stall, b->pipe_stage, any_table3(b) ? 1u : 0u};
         cudaError_t ce = pipe_launch(b->threads, pipe_filter_warps(b->cpg), b->G,
                                      pipe_smem_bytes(b->cpg, b->max_taps, b->threads, b->pipe_stage), b->stream,
@@ -694,7 +712,7 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
         return RX_OK;
     }
     if (b->schedule == RX_SCHED_STATIC) {
-        StaticArgs sa{b->d_groups, b->d_rxoff, iq, ba.tb, n_blocks, b->cpg, b->max_taps};
+        StaticArgs sa{b->d_groups, rxoff, iq, ba.tb, n_blocks, b->cpg, b->max_taps};
         const size_t ss = static_smem_bytes(b->cpg, b->max_taps, b->threads);
         if (b->threads == 128) s = launch_static<128>(b, sa, ss);
         else if (b->threads == 512) s = launch_static<512>(b, sa, ss);
@@ -834,6 +852,7 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     if (!b) return RX_OK;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);
     drop_graph(b);
     void *ptrs[] = {b->d_state, b->d_snap,  b->d_prn,   b->d_taps,  b->d_dumps, b->d_groups,
                     b->d_rxoff, b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart,
@@ -841,6 +860,10 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_err) cudaFreeHost(b->h_err);
+    if (b->d_chunk_off) cudaFree(b->d_chunk_off);
+    for (cudaEvent_t e : b->chunk_ev) cudaEventDestroy(e);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     cudaGetLastError();
     delete b;
@@ -969,6 +992,74 @@ extern "C" rx_status rx_batch_get_tiles(rx_batch b, uint32_t *cpg, uint32_t *thr
     return RX_OK;
 }
 
+// Host input of at least this many bytes is copied in kAutoChunks chunks by default.
+constexpr size_t kAutoChunkMin = 64ull << 20;
+constexpr uint32_t kAutoChunks = 16;
+
+// Host input in chunks of cb blocks (the staging buffer holds the whole run, laid out
+// as the host buffer): chunk c's copies go on the copy stream, and its launch, which
+// continues the state chunk c-1 left, waits only for them, so the copy of chunk c+1
+// overlaps the tracking of chunk c.  Chunk c reads receiver r at d_stage + off[r] +
+// c cb 2 N_r.
+static rx_status run_host_chunks(rx_batch b, const int8_t *iq, const uint64_t *off, uint32_t n_blocks,
+                                 uint32_t cb, uint32_t flags) {
+    std::string &E = b->err;
+    const uint32_t C = (n_blocks + cb - 1) / cb, R = b->n_rx;
+    if (!b->copy_stream) RX_CUDA_TRY(cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking), E);
+    if (!b->ev_start) RX_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming), E);
+    while (b->chunk_ev.size() < C) {
+        cudaEvent_t e = nullptr;
+        RX_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), E);
+        b->chunk_ev.push_back(e);
+    }
+    std::vector<uint64_t> co((size_t)C * R);
+    for (uint32_t c = 0; c < C; ++c)
+        for (uint32_t r = 0; r < R; ++r)
+            co[(size_t)c * R + r] = off[r] + (uint64_t)c * cb * 2 * b->rx[r].block_samples;
+    if (co != b->c_off) {
+        // an earlier run may still read the offsets: wait for it before replacing them
+        RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+        if (b->chunk_off_cap < C) {
+            if (b->d_chunk_off) cudaFree(b->d_chunk_off);
+            b->d_chunk_off = nullptr;
+            b->chunk_off_cap = 0;
+            b->c_off.clear();
+            if (cudaMalloc(&b->d_chunk_off, co.size() * 8) != cudaSuccess) {
+                cudaGetLastError();
+                return berr(b, RX_ENOMEM, "chunk offsets");
+            }
+            b->chunk_off_cap = C;
+        }
+        RX_CUDA_TRY(cudaMemcpy(b->d_chunk_off, co.data(), co.size() * 8, cudaMemcpyHostToDevice), E);
+        b->c_off = co;
+    }
+    // the copies overwrite the staging buffer only after the work already on the stream
+    RX_CUDA_TRY(cudaEventRecord(b->ev_start, b->stream), E);
+    RX_CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_start, 0), E);
+    b->last_launches = 0;
+    for (uint32_t c = 0; c < C; ++c) {
+        const uint32_t b0 = c * cb, nb = std::min(cb, n_blocks - b0);
+        for (uint32_t r = 0; r < R; ++r) {
+            const size_t blk = 2 * (size_t)b->rx[r].block_samples, o = off[r] + (size_t)b0 * blk;
+            RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + o, iq + o, (size_t)nb * blk, cudaMemcpyHostToDevice,
+                                        b->copy_stream), E);
+        }
+        RX_CUDA_TRY(cudaEventRecord(b->chunk_ev[c], b->copy_stream), E);
+        RX_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->chunk_ev[c], 0), E);
+        rx_status s = enqueue_run(b, b->d_stage, nb, c == 0 ? (flags & RX_RUN_RESTART) : 0u,
+                                  b->d_chunk_off + (size_t)c * R, c > 0);
+        if (s != RX_OK) return s;
+        b->last_launches = c + 1;
+    }
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_set_host_chunk(rx_batch b, uint32_t chunk_blocks) {
+    if (!b) return RX_EINVAL;
+    b->host_chunk = chunk_blocks;
+    return RX_OK;
+}
+
 extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
                                   uint32_t n_blocks, uint32_t flags) {
     if (!b) return RX_EINVAL;
@@ -985,14 +1076,21 @@ extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *
         drop_graph(b);
         if ((s = build_groups(b)) != RX_OK) return s;
     }
+    if (b->last_mode == 2 && !(flags & RX_RUN_RESTART))
+        return berr(b, RX_ESTATE, "after a code-period run, a block run needs RX_RUN_RESTART");
     const int8_t *src = iq;
     if (!rxh::is_device_pointer(iq)) {
         // Host input: copy each receiver's span into the device staging buffer.
-        size_t need = 0;
-        for (uint32_t r = 0; r < b->n_rx; ++r)
-            need = std::max(need, (size_t)rx_byte_offset[r] + (size_t)n_blocks * 2 * b->rx[r].block_samples);
+        size_t need = 0, bytes = 0;
+        for (uint32_t r = 0; r < b->n_rx; ++r) {
+            const size_t span = (size_t)n_blocks * 2 * b->rx[r].block_samples;
+            need = std::max(need, (size_t)rx_byte_offset[r] + span);
+            bytes += span;
+        }
         if (need > b->stage_bytes) {
             drop_graph(b);
+            RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
+            if (b->copy_stream) RX_CUDA_TRY(cudaStreamSynchronize(b->copy_stream), E);
             if (b->d_stage) cudaFree(b->d_stage);
             b->d_stage = nullptr;
             b->stage_bytes = 0;
@@ -1002,15 +1100,20 @@ extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *
             }
             b->stage_bytes = need;
         }
+        const uint32_t cb = b->host_chunk ? std::min(b->host_chunk, n_blocks)
+                            : bytes >= kAutoChunkMin ? (n_blocks + kAutoChunks - 1) / kAutoChunks
+                                                     : n_blocks;
+        if (cb < n_blocks) {
+            b->last_mode = 1;
+            return run_host_chunks(b, iq, rx_byte_offset, n_blocks, cb, flags);
+        }
         for (uint32_t r = 0; r < b->n_rx; ++r) {
-            size_t bytes = (size_t)n_blocks * 2 * b->rx[r].block_samples;
-            RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + rx_byte_offset[r], iq + rx_byte_offset[r], bytes,
+            const size_t span = (size_t)n_blocks * 2 * b->rx[r].block_samples;
+            RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + rx_byte_offset[r], iq + rx_byte_offset[r], span,
                                         cudaMemcpyHostToDevice, b->stream), E);
         }
         src = b->d_stage;
     }
-    if (b->last_mode == 2 && !(flags & RX_RUN_RESTART))
-        return berr(b, RX_ESTATE, "after a code-period run, a block run needs RX_RUN_RESTART");
     b->last_mode = 1;
     std::vector<uint64_t> off(rx_byte_offset, rx_byte_offset + b->n_rx);
     if (b->g_off != off) {
@@ -1074,6 +1177,39 @@ extern "C" rx_status rx_batch_read_dumps(rx_batch b, uint32_t rxi, int32_t *out,
     if (elems)
         RX_CUDA_TRY(cudaMemcpy(out, b->d_dumps + b->rx_dump0[rxi], elems * 4, cudaMemcpyDeviceToHost), b->err);
     *n_dumps = nd;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_batch_read_all_dumps(rx_batch b, int32_t *out, size_t cap, uint32_t *n_dumps) {
+    if (!b || !out || !n_dumps) return RX_EINVAL;
+    rx_status s = rx_batch_sync(b);
+    if (s != RX_OK) return s;
+    std::vector<uint32_t> ep(b->n_ch);
+    if (b->n_ch) RX_CUDA_TRY(cudaMemcpy(ep.data(), b->st.epochs, (size_t)b->n_ch * 4, cudaMemcpyDeviceToHost), b->err);
+    std::vector<size_t> elems(b->n_rx);
+    size_t total = 0;
+    bool full = true;
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        const rx_receiver_desc &d = b->rx[r];
+        const uint32_t slots = b->max_blocks / d.integ_blocks;
+        const uint32_t nd = std::min(ep[b->rx_ch0[r]], slots);
+        n_dumps[r] = nd;
+        elems[r] = (size_t)nd * d.n_channels * d.n_taps * 2;
+        total += elems[r];
+        full = full && nd == slots;
+    }
+    if (cap < total) return berr(b, RX_EINVAL, rxh::fmt("cap %zu < %zu", cap, total));
+    if (full) {   // the receivers' dump buffers are full and adjacent: one copy
+        if (total) RX_CUDA_TRY(cudaMemcpy(out, b->d_dumps, total * 4, cudaMemcpyDeviceToHost), b->err);
+        return RX_OK;
+    }
+    size_t o = 0;
+    for (uint32_t r = 0; r < b->n_rx; ++r) {
+        if (elems[r])
+            RX_CUDA_TRY(cudaMemcpy(out + o, b->d_dumps + b->rx_dump0[r], elems[r] * 4, cudaMemcpyDeviceToHost),
+                        b->err);
+        o += elems[r];
+    }
     return RX_OK;
 }
 

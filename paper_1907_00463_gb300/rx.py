@@ -171,6 +171,7 @@ SIGNATURES = [
     ("rx_batch_run", C.c_int, [P, P, P, C.c_uint32, C.c_uint32]),
     ("rx_batch_sync", C.c_int, [P]),
     ("rx_batch_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
+    ("rx_batch_read_all_dumps", C.c_int, [P, P, C.c_size_t, P]),
     ("rx_batch_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_batch_read_health", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_health), C.c_uint32]),
     ("rx_batch_run_code", C.c_int, [P, P, P, C.c_uint32, C.c_uint32]),
@@ -178,6 +179,7 @@ SIGNATURES = [
     ("rx_batch_read_code_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_code_state), C.c_uint32]),
     ("rx_batch_set_tiles", C.c_int, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     ("rx_batch_set_wait_limit", C.c_int, [P, C.c_uint64, C.c_uint32]),
+    ("rx_batch_set_host_chunk", C.c_int, [P, C.c_uint32]),
     ("rx_batch_get_tiles", C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                      C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     ("rx_batch_autotune", C.c_int, [P, P, P, C.c_uint32, C.POINTER(C.c_uint32),
@@ -452,6 +454,28 @@ def rx_batch_read_dumps(b, rx: int, n_ch: int, n_taps: int, max_dumps: int) -> n
     return out[:nd.value]
 
 
+def rx_batch_read_all_dumps(b, shapes, out=None) -> list:
+    """Every receiver's dumps in one call.  shapes: (n_channels, n_taps, max_dumps) per
+    receiver; out: optional caller-owned contiguous int32 array (pinned memory makes
+    the copy direct) of at least sum(max_dumps n_channels n_taps 2) elements.
+    Returns one [n_dumps][n_channels][n_taps][2] view into out per receiver."""
+    lib = load()
+    cap = sum(int(m) * int(c) * int(t) * 2 for c, t, m in shapes)
+    if out is None:
+        out = np.zeros(cap, np.int32)
+    if out.dtype != np.int32 or not out.flags["C_CONTIGUOUS"] or out.size < cap:
+        raise ValueError("out must be a contiguous int32 array of at least %d elements" % cap)
+    nd = np.zeros(len(shapes), np.uint32)
+    _check(b, lib.rx_batch_read_all_dumps(b, _ptr(out), out.size, _ptr(nd)), lib.rx_batch_last_error)
+    views, o = [], 0
+    flat = out.reshape(-1)
+    for (c, t, _), n in zip(shapes, nd):
+        k = int(n) * int(c) * int(t) * 2
+        views.append(flat[o:o + k].reshape(int(n), int(c), int(t), 2))
+        o += k
+    return views
+
+
 def rx_batch_read_state(b, rx: int, n_ch: int) -> list:
     lib = load()
     arr = (rx_channel_state * n_ch)()
@@ -476,6 +500,11 @@ def rx_batch_set_tiles(b, channels_per_item: int = 0, threads: int = 0, ctas_per
 def rx_batch_set_wait_limit(b, timeout_ns: int, flags: int = 0):
     lib = load()
     _check(b, lib.rx_batch_set_wait_limit(b, int(timeout_ns), int(flags)), lib.rx_batch_last_error)
+
+
+def rx_batch_set_host_chunk(b, chunk_blocks: int):
+    lib = load()
+    _check(b, lib.rx_batch_set_host_chunk(b, int(chunk_blocks)), lib.rx_batch_last_error)
 
 
 def rx_batch_get_tiles(b) -> tuple[int, int, int, int]:

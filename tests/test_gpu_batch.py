@@ -1,7 +1,7 @@
 """GPU parity of the batched persistent kernel (rx_batch_* through the C ABI)
 against the CPU oracle, for the uniform, uneven and multi-correlator workloads:
 dumps and final loop state bit-exact; results independent of the batch mix,
-the tile shape, graph replay and host-vs-device input."""
+the tile shape, graph replay and host-vs-device input (whole or in chunks)."""
 import numpy as np
 import pytest
 import torch
@@ -163,6 +163,87 @@ def test_graph_replay_restart_continue_and_host_input(schedule):
     _check_against_oracle(recv, sigs, first, 16)
     for x, y, z in zip(first, second, cont):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[0], z[0])
+
+
+def _same_runs(x, y):
+    for (dx, sx), (dy, sy) in zip(x, y):
+        assert np.array_equal(dx, dy)
+        key = lambda c: (c.carrier_word, c.code_rate, c.carrier_phase, c.code_phase, c.pll_integrator_hz,
+                         c.carrier_hz, c.code_hz, c.epochs)
+        assert [key(c) for c in sx] == [key(c) for c in sy]
+
+
+@pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE,
+                                      rx.RX_SCHED_BALANCED])
+def test_host_input_in_chunks(schedule):
+    """Host input copied and tracked in chunks of 3 blocks: 16 blocks make five chunks
+    and a ragged one, and an integration of 5 blocks spans chunk boundaries.  One
+    launch per chunk; dumps and state bit-exact with the oracle and with one launch
+    over device input, from pageable and from pinned memory, also for two runs
+    enqueued back to back; with automatic chunking the small input takes one launch."""
+    recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
+    recv[1].integ_blocks = 5
+    buf, offs, sigs = _pack(recv, 16)
+    tiles = (0, 128, 0, schedule) if schedule == rx.RX_SCHED_BALANCED else (2, 128, 0, schedule)
+    b = _batch(recv, 16, tiles)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 16, rx.RX_RUN_RESTART)
+        whole = _read(b, recv, 16)
+        rx.rx_batch_set_host_chunk(b, 3)
+        rx.rx_batch_run(b, buf, offs, 16, rx.RX_RUN_RESTART)
+        assert rx.rx_batch_last_launches(b) == 6
+        pageable = _read(b, recv, 16)
+        pinned = torch.from_numpy(buf).pin_memory()
+        rx.rx_batch_run(b, pinned, offs, 16, rx.RX_RUN_RESTART)
+        rx.rx_batch_run(b, pinned, offs, 16, rx.RX_RUN_RESTART)
+        back_to_back = _read(b, recv, 16)
+        rx.rx_batch_set_host_chunk(b, 0)
+        rx.rx_batch_run(b, buf, offs, 16, rx.RX_RUN_RESTART)
+        assert rx.rx_batch_last_launches(b) == 1
+        one = _read(b, recv, 16)
+        every = rx.rx_batch_read_all_dumps(b, [(len(r.channels), r.n_taps, 16 // r.integ_blocks) for r in recv])
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, whole, 16)
+    for res in (pageable, back_to_back, one):
+        _same_runs(whole, res)
+    for d, (x, _) in zip(every, one):
+        assert np.array_equal(d, x)
+
+
+def test_large_host_input_is_chunked_automatically():
+    """At 64 MiB of host input or more the run is copied and tracked in sixteen chunks
+    (here 2 receivers x 1100 blocks at 16.368 MHz, 72 MB, seeded int8 noise: chunks of
+    69 blocks and a ragged one), with the same dumps and state as one launch over
+    device input; a continuing run after it continues exactly."""
+    n = 1100
+    recv = [synth.uniform_receiver(i, n_blocks=n) for i in range(2)]
+    offs, total = batch_layout(recv)
+    g = np.random.Generator(np.random.Philox(key=463077))
+    buf = g.integers(-40, 41, total, dtype=np.int8)
+    assert total >= 64 << 20
+    pinned = torch.from_numpy(buf).pin_memory()
+    dev = torch.from_numpy(buf).cuda()
+    b = _batch(recv, 2 * n, (2, 224, 0, rx.RX_SCHED_PIPE))
+    try:
+        rx.rx_batch_run(b, dev, offs, n, rx.RX_RUN_RESTART)
+        rx.rx_batch_run(b, dev, offs, n, 0)
+        whole = _read(b, recv, 2 * n)
+        rx.rx_batch_run(b, pinned, offs, n, rx.RX_RUN_RESTART)
+        assert rx.rx_batch_last_launches(b) == 16
+        shapes = [(len(r.channels), r.n_taps, 2 * n) for r in recv]
+        half = rx.rx_batch_read_all_dumps(b, shapes)                 # buffers half full: one copy each
+        rx.rx_batch_run(b, pinned, offs, n, 0)
+        chunked = _read(b, recv, 2 * n)
+        out = torch.empty(sum(c * t * m * 2 for c, t, m in shapes), dtype=torch.int32).pin_memory()
+        every = rx.rx_batch_read_all_dumps(b, shapes, out=out.numpy())   # full: one copy
+    finally:
+        rx.rx_batch_destroy(b)
+    assert len(whole[0][0]) == 2 * n
+    _same_runs(whole, chunked)
+    for h, e, (x, _) in zip(half, every, whole):
+        assert len(h) == n and np.array_equal(h, x[:n])
+        assert np.array_equal(e, x)
 
 
 def test_batch_invalid_arguments():
