@@ -1,6 +1,7 @@
 """Host-side argument checks of the plain and batched forms that run before any
 device is touched (so they hold with or without a GPU): the epoch mode and loop set
-of rx_create, and the loop-set fields of rx_receiver_desc in rx_batch_create."""
+of rx_create, the loop-set fields of rx_receiver_desc in rx_batch_create, null
+handles, and the caller buffer of the one-call dump read."""
 import pytest
 
 from paper_1907_00463_gb300 import rx, synth
@@ -33,3 +34,27 @@ def test_batch_descriptor_loop_fields_checked():
     import torch
     if not torch.cuda.is_available():
         assert _status(lambda: rx.rx_batch_create([rx.receiver_desc(r, 1, 20, 10.0)], 10)) == rx.RX_ECUDA
+
+
+def test_null_handles_are_refused():
+    """Every entry point of the batched form refuses a null handle with RX_EINVAL
+    before it touches a device, the host-input chunking and the one-call dump read
+    included."""
+    import numpy as np
+    assert _status(lambda: rx.rx_batch_set_host_chunk(None, 3)) == rx.RX_EINVAL
+    assert _status(lambda: rx.rx_batch_read_all_dumps(None, [(2, 3, 4)])) == rx.RX_EINVAL
+    assert _status(lambda: rx.rx_batch_set_tiles(None, 2, 128, 0)) == rx.RX_EINVAL
+    assert _status(lambda: rx.rx_batch_sync(None)) == rx.RX_EINVAL
+    assert _status(lambda: rx.rx_batch_run(None, np.zeros(16, np.int8), [0], 1)) == rx.RX_EINVAL
+
+
+def test_read_all_dumps_checks_the_caller_buffer():
+    """The binding refuses a caller buffer that is too small, not int32 or not
+    contiguous before calling the library."""
+    import numpy as np
+    with pytest.raises(ValueError):
+        rx.rx_batch_read_all_dumps(None, [(2, 3, 4)], out=np.zeros(10, np.int32))
+    with pytest.raises(ValueError):
+        rx.rx_batch_read_all_dumps(None, [(2, 3, 4)], out=np.zeros(48, np.int64))
+    with pytest.raises(ValueError):
+        rx.rx_batch_read_all_dumps(None, [(2, 3, 4)], out=np.zeros(96, np.int32)[::2])
