@@ -452,8 +452,10 @@ rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
 
 /* Autotuner: time each candidate tile shape (both schedules; 1-16 channels per
  * item; 128/256/512 threads) on the first probe_blocks blocks of the caller's
- * input (arguments as in rx_batch_run), keep the fastest, and return the
- * receivers to their starting state.  The choice is cached in the process per
+ * input (arguments as in rx_batch_run; host input is copied whole before each
+ * timed run, never in overlapped chunks, so the candidates differ by their
+ * tracking alone), keep the fastest, and return the receivers to their
+ * starting state.  The choice is cached in the process per
  * workload shape (sample rates, block sizes, channel/tap counts, integration
  * lengths, device); a cached shape is applied without timing (*ms_out = -1).
  * tiles_out (4 entries, optional) receives {channels_per_item, threads,

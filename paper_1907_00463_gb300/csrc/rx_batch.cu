@@ -1315,6 +1315,14 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
                 cands.push_back({cpg, nt, 0u, sched});
             }
         }
+    // Host input is copied whole before each timed run, never in overlapped chunks, so
+    // that every candidate's time holds the same copy and differs by its tracking.
+    struct ChunkGuard {
+        rx_batch b;
+        uint32_t saved;
+        ~ChunkGuard() { b->host_chunk = saved; }
+    } guard{b, b->host_chunk};
+    b->host_chunk = probe_blocks;
     cudaEvent_t e0, e1;
     std::string &E = b->err;
     RX_CUDA_TRY(cudaEventCreate(&e0), E);
