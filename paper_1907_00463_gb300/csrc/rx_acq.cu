@@ -31,6 +31,7 @@
 
 #include "rx_internal.h"
 #include "rx_ntt.cuh"
+#include "rx_trace.h"
 
 namespace {
 
@@ -633,6 +634,7 @@ extern "C" rx_status rx_acq_set_search(rx_acq a, uint32_t n_prn, const uint8_t *
 }
 
 extern "C" rx_status rx_acq_run(rx_acq a, const int8_t *iq, uint32_t n_rx) {
+    rxh::TraceRange trace_("rx_acq_run");
     if (!a) return RX_EINVAL;
     if (!a->have_search) return acq_fail(a, RX_ESTATE, "rx_acq_set_search has not been called");
     if (!iq || n_rx == 0 || n_rx > a->cfg.max_receivers)

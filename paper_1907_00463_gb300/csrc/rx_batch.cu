@@ -31,6 +31,7 @@
 #include "rx_code.cuh"
 #include "rx_internal.h"
 #include "rx_item.cuh"
+#include "rx_trace.h"
 
 using namespace rxd;
 
@@ -1062,6 +1063,7 @@ extern "C" rx_status rx_batch_set_host_chunk(rx_batch b, uint32_t chunk_blocks) 
 
 extern "C" rx_status rx_batch_run(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
                                   uint32_t n_blocks, uint32_t flags) {
+    rxh::TraceRange trace_("rx_batch_run");
     if (!b) return RX_EINVAL;
     if (!iq || !rx_byte_offset || n_blocks == 0) return berr(b, RX_EINVAL, "null input or zero blocks");
     if (n_blocks > b->max_blocks) return berr(b, RX_EINVAL, "n_blocks > max_blocks");
@@ -1281,6 +1283,7 @@ TuneKey tune_key(rx_batch b, int device) {
 
 extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
                                        uint32_t probe_blocks, uint32_t *tiles_out, float *ms_out) {
+    rxh::TraceRange trace_("rx_batch_autotune");
     if (!b || !iq || !rx_byte_offset || probe_blocks == 0) return RX_EINVAL;
     probe_blocks = std::min(probe_blocks, b->max_blocks);
     cudaSetDevice(b->device);
@@ -1383,6 +1386,7 @@ extern "C" rx_status rx_batch_read_health(rx_batch b, uint32_t rxi, rx_channel_h
 
 extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint64_t *rx_byte_offset,
                                        uint32_t n_blocks, uint32_t flags) {
+    rxh::TraceRange trace_("rx_batch_run_code");
     if (!b) return RX_EINVAL;
     if (!iq || !rx_byte_offset || n_blocks == 0) return berr(b, RX_EINVAL, "null input or zero blocks");
     if (n_blocks > b->max_blocks) return berr(b, RX_EINVAL, "n_blocks > max_blocks");

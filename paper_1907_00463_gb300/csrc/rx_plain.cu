@@ -14,6 +14,7 @@
 #include "rx_device.cuh"
 #include "rx_internal.h"
 #include "rx_item.cuh"
+#include "rx_trace.h"
 
 using namespace rxd;
 
@@ -604,6 +605,7 @@ extern "C" rx_status rx_set_channels(rx_handle h, uint32_t n, const uint8_t *prn
 }
 
 extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp) {
+    rxh::TraceRange trace_("rx_correlate");
     if (!h) return RX_EINVAL;
     if (h->n_ch == 0) return set_err(h, RX_ESTATE, "rx_set_channels has not been called");
     if (h->cfg.epoch_mode != RX_EPOCH_BLOCKS)
@@ -640,6 +642,7 @@ extern "C" rx_status rx_correlate(rx_handle h, const int8_t *iq, uint32_t nsamp)
 }
 
 extern "C" rx_status rx_track_epoch(rx_handle h) {
+    rxh::TraceRange trace_("rx_track_epoch");
     if (!h) return RX_EINVAL;
     if (h->cfg.epoch_mode != RX_EPOCH_BLOCKS)
         return set_err(h, RX_ESTATE, "RX_EPOCH_CODE handle: use rx_track_code");
@@ -797,6 +800,7 @@ extern "C" rx_status rx_write_health(rx_handle h, const rx_channel_health *in, u
 }
 
 extern "C" rx_status rx_track_code(rx_handle h, const int8_t *iq, uint32_t nsamp) {
+    rxh::TraceRange trace_("rx_track_code");
     if (!h) return RX_EINVAL;
     if (h->cfg.epoch_mode != RX_EPOCH_CODE)
         return set_err(h, RX_ESTATE, "rx_track_code needs epoch_mode RX_EPOCH_CODE");

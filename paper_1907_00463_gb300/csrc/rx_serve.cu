@@ -29,6 +29,7 @@
 
 #include "rx_internal.h"
 #include "rx_item.cuh"
+#include "rx_trace.h"
 
 using namespace rxd;
 
@@ -394,6 +395,7 @@ void reap(rx_serve s, bool block) {
 
 // Launch one tick over the pending blocks.  s->mu held.
 rx_status launch_tick(rx_serve s) {
+    rxh::TraceRange trace_("rx_serve_tick");
     std::vector<Pending> blocks;
     blocks.swap(s->pending);
     const int buf = s->next_buf;

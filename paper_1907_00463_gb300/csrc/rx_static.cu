@@ -21,6 +21,7 @@
 
 #include "rx_device.cuh"
 #include "rx_internal.h"
+#include "rx_trace.h"
 
 using namespace rxd;
 
@@ -341,6 +342,7 @@ extern "C" rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx, 
                                      const uint64_t *rx_byte_offset, uint32_t n_blocks,
                                      rx_channel_state *state, const int64_t *tap_offsets,
                                      int32_t *dumps, int32_t device, void *cuda_stream) {
+    rxh::TraceRange trace_("rx_track_static");
     if (!rx || !rx_byte_offset || !iq || !state || !tap_offsets || !dumps || n_rx == 0 || n_blocks == 0)
         return RX_EINVAL;
     if (((uintptr_t)iq & 1) || ((uintptr_t)state & 7) || ((uintptr_t)tap_offsets & 7) || ((uintptr_t)dumps & 3))
