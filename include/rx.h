@@ -542,6 +542,12 @@ rx_status rx_serve_reset_stats(rx_serve s);
 rx_status rx_serve_stream_status(rx_serve s, uint32_t id, uint32_t *state,
                                  uint64_t *pushed, uint64_t *done);
 
+/* Blocks of stream id that completed more than 1 ms (the real-time deadline of
+ * a 1 ms block) after their push, since the stream was admitted.  A stream
+ * that misses deadlines is marked by this count and keeps being served; the
+ * count is not cleared by rx_serve_reset_stats. */
+rx_status rx_serve_stream_misses(rx_serve s, uint32_t id, uint64_t *misses);
+
 /* The stream's latest dumps, oldest first, int32 [n][C][T][2] (at most
  * dump_slots of them); drains first. */
 rx_status rx_serve_read_dumps(rx_serve s, uint32_t id, int32_t *out, size_t cap,

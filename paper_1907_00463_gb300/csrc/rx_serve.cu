@@ -145,6 +145,7 @@ struct Stream {
     std::vector<uint32_t> groups;
     uint32_t seq_next = 0;        // next block sequence number (per group, all groups alike)
     uint64_t pushed = 0, done = 0;
+    uint64_t misses = 0;          // blocks completed more than 1 ms after their push
     // device arrays (inside the pool)
     uint32_t *theta = nullptr, *prn_d = nullptr, *epochs = nullptr, *acc_blocks = nullptr;
     int32_t *w_d = nullptr, *acc = nullptr, *dumps = nullptr;
@@ -337,7 +338,7 @@ rx_status activate(rx_serve s, uint32_t id) {
     }
     st.state = kActive;
     st.seq_next = 0;
-    st.pushed = st.done = 0;
+    st.pushed = st.done = st.misses = 0;
     return RX_OK;
 }
 
@@ -378,9 +379,12 @@ void reap(rx_serve s, bool block) {
         for (const Pending &p : t.blocks) {
             const float us = std::chrono::duration<float, std::micro>(now - p.arrival).count();
             s->lat_us.push_back(us);
-            if (us > 1000.0f) ++s->misses;
-            s->slot_busy[p.slot] = 0;
             Stream &st = s->streams[p.stream];
+            if (us > 1000.0f) {   // counted against the stream, never fatal to it
+                ++s->misses;
+                ++st.misses;
+            }
+            s->slot_busy[p.slot] = 0;
             st.done += 1;
             if (st.state == kReleasing && st.done == st.pushed) {
                 deactivate(s, p.stream);
@@ -731,6 +735,13 @@ extern "C" rx_status rx_serve_stream_status(rx_serve s, uint32_t id, uint32_t *s
     *state = st.state;
     if (pushed) *pushed = st.pushed;
     if (done) *done = st.done;
+    return RX_OK;
+}
+
+extern "C" rx_status rx_serve_stream_misses(rx_serve s, uint32_t id, uint64_t *misses) {
+    if (!s || id >= s->cfg.max_streams || !misses) return RX_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *misses = s->streams[id].misses;
     return RX_OK;
 }
 

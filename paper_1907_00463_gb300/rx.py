@@ -199,6 +199,7 @@ SIGNATURES = [
     ("rx_serve_reset_stats", C.c_int, [P]),
     ("rx_serve_stream_status", C.c_int, [P, C.c_uint32, C.POINTER(C.c_uint32),
                                          C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    ("rx_serve_stream_misses", C.c_int, [P, C.c_uint32, C.POINTER(C.c_uint64)]),
     ("rx_serve_read_dumps", C.c_int, [P, C.c_uint32, P, C.c_size_t, C.POINTER(C.c_uint32)]),
     ("rx_serve_read_state", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_state), C.c_uint32]),
     ("rx_serve_read_health", C.c_int, [P, C.c_uint32, C.POINTER(rx_channel_health), C.c_uint32]),
@@ -635,6 +636,13 @@ def rx_serve_stream_status(s, sid: int) -> tuple[int, int, int]:
     _check(s, lib.rx_serve_stream_status(s, sid, C.byref(st), C.byref(pu), C.byref(do)),
            lib.rx_serve_last_error)
     return st.value, pu.value, do.value
+
+
+def rx_serve_stream_misses(s, sid: int) -> int:
+    lib = load()
+    m = C.c_uint64()
+    _check(s, lib.rx_serve_stream_misses(s, sid, C.byref(m)), lib.rx_serve_last_error)
+    return m.value
 
 
 def rx_serve_read_dumps(s, sid: int, n_ch: int, n_taps: int, max_dumps: int) -> np.ndarray:

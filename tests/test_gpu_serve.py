@@ -72,9 +72,12 @@ def test_alone_equals_in_the_mix():
             d = rx.rx_serve_read_dumps(s, ids[0], 12, 5, 64)
             st = rx.rx_serve_read_state(s, ids[0], 12)
             stats = rx.rx_serve_get_stats(s)
+            misses = rx.rx_serve_stream_misses(s, ids[0])
         finally:
             rx.rx_serve_destroy(s)
         assert stats["device_timeouts"] == 0
+        # the target's late blocks are its share of the server's (all of them when alone)
+        assert misses == stats["deadline_misses"] if not mix else misses <= stats["deadline_misses"]
         if mix:
             assert stats["blocks_done"] > 2000 and stats["mean_items_per_tick"] > 6
         results.append((d, st))

@@ -37,15 +37,16 @@ def test_batch_descriptor_loop_fields_checked():
 
 
 def test_null_handles_are_refused():
-    """Every entry point of the batched form refuses a null handle with RX_EINVAL
-    before it touches a device, the host-input chunking and the one-call dump read
-    included."""
+    """Entry points of the batched and served forms refuse a null handle with
+    RX_EINVAL before they touch a device, the host-input chunking, the one-call dump
+    read and the per-stream deadline-miss count included."""
     import numpy as np
     assert _status(lambda: rx.rx_batch_set_host_chunk(None, 3)) == rx.RX_EINVAL
     assert _status(lambda: rx.rx_batch_read_all_dumps(None, [(2, 3, 4)])) == rx.RX_EINVAL
     assert _status(lambda: rx.rx_batch_set_tiles(None, 2, 128, 0)) == rx.RX_EINVAL
     assert _status(lambda: rx.rx_batch_sync(None)) == rx.RX_EINVAL
     assert _status(lambda: rx.rx_batch_run(None, np.zeros(16, np.int8), [0], 1)) == rx.RX_EINVAL
+    assert _status(lambda: rx.rx_serve_stream_misses(None, 0)) == rx.RX_EINVAL
 
 
 def test_read_all_dumps_checks_the_caller_buffer():
