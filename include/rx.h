@@ -340,7 +340,8 @@ rx_status rx_batch_set_channels(rx_batch b, uint32_t rx, const uint8_t *prn,
 #define RX_RUN_NO_GRAPH 2u  /* launch directly instead of through a CUDA graph */
 
 /* Track n_blocks consecutive blocks of every receiver, closing each receiver's
- * loops at its own integration boundaries, in one persistent kernel launch.
+ * loops at its own integration boundaries, in one persistent kernel launch
+ * (one per chunk when large host input is copied in chunks, below).
  * Receiver r's samples are the 2*N_r*n_blocks int8 values at iq +
  * rx_byte_offset[r] (16-byte aligned offsets; host array of n_rx entries).
  * iq is a device pointer (read in stream order) or host memory, copied in
