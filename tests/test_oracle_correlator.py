@@ -6,7 +6,9 @@ brute force via a replica matrix built with exact integer arithmetic, code
 autocorrelation values (1023 and the Gold three values, times the table gain),
 the quarter-turn rotation of the carrier table, the zero imaginary part left by
 mixing a sample equal to the replica, block splitting, and the periodicity of
-tap offsets.
+tap offsets.  At signal level: the prompt peak at the injected code phase and
+Doppler, and the shape a delayed second path gives the multicorrelator's
+correlation function.
 """
 import numpy as np
 import pytest
@@ -141,3 +143,47 @@ def test_prompt_peaks_at_injected_code_phase_and_doppler():
     # early/late symmetric around the prompt within 25 %
     e, l = env[0.0][3], env[0.0][1]
     assert abs(e - l) < 0.25 * (e + l)
+
+
+def _multipath_envelope(mp_phase, mp_db=-3.0, delay=0.4, n_blocks=4):
+    """|R(o)| over the multicorrelator's 101 taps (+-2.5 chips at 0.05) for one SV at
+    60 dB-Hz with a second path delay chips late, the NCO at the direct path's truth."""
+    fs, N = 25.0e6, 25000
+    sv = synth.SV(13, 1500.0, 321.25, 60.0, mp_delay_chips=delay, mp_rel_power_db=mp_db,
+                  mp_doppler_offset_hz=0.0, mp_phase_cycles=mp_phase)
+    if mp_db is None:
+        sv.mp_rel_power_db = None
+    rcv = synth.Receiver(fs, N, n_blocks, [sv], [], nav_bits=False, seed=463099)
+    iq = synth.generate_iq(rcv).numpy()
+    taps = np.array([int(np.rint(j * TWO32 / 20)) for j in range(-50, 51)], np.int64)
+    w = int(np.rint(sv.doppler_hz / fs * TWO32))
+    r = int(np.rint(1.023e6 * (1 + sv.doppler_hz / 1575.42e6) / fs * TWO32))
+    phi = int(np.rint(sv.code_phase_chips * TWO32)) % M
+    acc, _, _ = oracle.correlate_block(iq, 0, w, phi, r, taps, oracle.ca_code(sv.prn))
+    return taps / TWO32, np.hypot(acc[:, 0].astype(float), acc[:, 1].astype(float))
+
+
+def test_multipath_shapes_the_correlation_function():
+    """Signal level, the multicorrelator workload's second path: with the replica at
+    the direct path, a path delay chips late appears at the late (negative) tap
+    offsets.  In phase it raises the late side and the peak stays inside the
+    injected delay bounds [-delay, 0]; in antiphase it lowers the late side; without
+    it the function is symmetric.  This pins the generator's path delay sign against
+    the correlator's tap convention (replica chip = code phase + offset)."""
+    delay = 0.4
+    off, ref = _multipath_envelope(0.0, mp_db=None)
+    _, inph = _multipath_envelope(0.0, delay=delay)
+    _, anti = _multipath_envelope(0.5, delay=delay)
+    late = (off < -0.1) & (off > -0.9)
+    early = (off > 0.1) & (off < 0.9)
+    # no second path: symmetric to within the noise (60 dB-Hz over 4 ms)
+    assert abs(ref[late].sum() - ref[early].sum()) < 0.03 * ref[late].sum()
+    # in phase: late side heavier, peak between the two paths
+    assert inph[late].sum() > 1.2 * inph[early].sum()
+    k = int(np.argmax(inph))
+    assert -delay - 1e-9 <= off[k] <= 0.0 + 1e-9
+    # early offsets past the second path's reach (1 - delay) see the direct path alone
+    far_early = (off > 1 - delay + 0.05) & (off < 0.95)
+    assert np.allclose(inph[far_early], ref[far_early], rtol=0.03, atol=0.01 * ref.max())
+    # antiphase: late side lighter than early
+    assert anti[late].sum() < 0.8 * anti[early].sum()
