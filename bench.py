@@ -43,16 +43,33 @@ sys.path.insert(0, ROOT)
 N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 
 # DRAM bytes (read + write) per receiver-block of the timed kernel and its executed
-# thread instructions per sample*channel, from the ncu captures summarised under
-# profiles/ (64 receivers x 100 blocks, larger than L2; a launch of B blocks is B/100
-# times that case).  Keyed by (schedule, correlating threads, channels per item).  An
-# entry is removed whenever its kernel changes and restored from a new capture.
+# thread instructions per sample*channel, from one ncu capture of 64 receivers x 100
+# blocks (larger than L2; a launch of B blocks is B/100 times that case).  Keyed by
+# (schedule, correlating threads, channels per item).  Each entry records the SHA-256
+# of the kernel's source files at the capture; when the sources differ from it the
+# figures describe another kernel, and the line reports them as null.
 PROFILED = {
     ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
-                            "capture": "profiles/k_batch_pipe224_uniform_64rx_100blk.md"},
+                            "src_sha256": "capture predates source hashing"},
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
-                         "capture": "profiles/k_batch_static128_uniform_64rx_100blk.md"},
+                         "src_sha256": "capture predates source hashing"},
 }
+KERNEL_SOURCES = {
+    "pipelined": ["rx_pipe.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
+    "static": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
+    "dynamic": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
+    "balanced": ["rx_balance.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
+}
+
+
+def kernel_sources_sha256(schedule: str) -> str:
+    """SHA-256 over the source files that define a schedule's kernel, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES.get(schedule, []):
+        with open(os.path.join(ROOT, "paper_1907_00463_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 METRIC = "Msample*channel/s correlated"
 INT32_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x one 32-lane warp instruction per clock
 
@@ -506,7 +523,7 @@ def acquisition_leg(rx, synth, receivers, buf, offs, dev, stream, steps, warmup,
     out = {
         "metric": "acquisition search cells/s (PRN x Doppler bin x code delay, 1 ms coherent)",
         "value": cells / (ms / 1000) / 1e9, "unit": "Gcell/s", "ms_per_step": ms,
-        "steps": steps, "warmup": warmup, "dtype": "int32 (exact field transform mod 15*2^27+1)",
+        "steps": steps, "warmup": warmup, "dtype": "int32 (exact field transform mod 2^30 - 2^18 + 1)",
         "config": {"workload": f"{n_rx} receivers x {n_prn} PRNs x {len(words)} Doppler bins "
                                f"(+-7 kHz at 500 Hz) x {N} code delays, first 1 ms of each receiver "
                                "of the tracking workload, fs 16.368 MHz",
@@ -710,12 +727,15 @@ def run_ours(args):
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
     sched_name = ["dynamic", "static", "pipelined", "balanced"][tiles[3]]
     prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
+    if prof and prof["src_sha256"] != kernel_sources_sha256(sched_name):
+        prof = None                      # the kernel changed since its counters were taken
     traffic = prof["bytes_per_rx_block"] * len(receivers) * n_blocks if prof else None
     executed = None
     if prof:
         ex_rate = sc * prof["thread_inst_per_sample_channel"] / (launch_ms / 1000) / 1e12
         executed = {"thread_inst_per_sample_channel": prof["thread_inst_per_sample_channel"],
-                    "achieved": ex_rate, "frac": ex_rate / peak_tops, "capture": prof["capture"]}
+                    "achieved": ex_rate, "frac": ex_rate / peak_tops,
+                    "src_sha256": prof["src_sha256"]}
     line = {
         "metric": METRIC, "value": value, "unit": "Msample*channel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

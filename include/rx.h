@@ -599,9 +599,9 @@ rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *streams, uint32_t 
 /* The paper has no counterpart to this call.  It runs the batched closed-loop
  * tracking of rx_batch_run for callers that cannot allocate GPU memory: a
  * host with a fixed memory plan that forbids allocation once it is running
- * (a real-time receiver loop), a plug-in that lives inside another program's
- * allocator, or a program capturing a CUDA graph around the call.  It calls no
- * cudaMalloc / cudaFree and no allocating library routine.  The caller passes
+ * (a real-time receiver loop), or a plug-in that lives inside another
+ * program's allocator.  It calls no cudaMalloc / cudaFree and no allocating
+ * library routine.  The caller passes
  * every input and output buffer; the kernel's scratch (tickets, per-channel
  * progress counters, the error word, the work table and multi-block running
  * sums) lives in one fixed 4 MiB __device__ array inside librx, which every GPU
@@ -624,15 +624,20 @@ rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *streams, uint32_t 
  *   tap_offsets   device int64, each channel's n_taps offsets in order.
  *   dumps         device int32 output; per receiver [n_blocks/L][C][T][2],
  *                 receivers back to back.
- * Synchronous: returns once the work has finished.  Returns RX_EINVAL for
- * arguments beyond the limits and for device-resident inputs out of range (PRN
- * outside 1..32, code rate >= 2^32, tap offset beyond 64 chips), RX_ETIMEOUT if
- * a bounded device wait gave up, RX_ECUDA on a CUDA error.
+ * Synchronous: it copies the descriptors from host memory, waits for the
+ * stream and reads the error word back, and returns once the work has
+ * finished.  Returns RX_EINVAL for arguments beyond the limits (also when
+ * n_channels * (n_blocks + 1) exceeds 2^32) and for device-resident inputs out
+ * of range (PRN outside 1..32, code rate >= 2^32, tap offset beyond 64 chips;
+ * the channels' state may then be partly advanced), RX_ETIMEOUT if a bounded
+ * device wait gave up, RX_ECUDA on a CUDA error.
  * The first call on a device looks up the array's device address and loads the
  * code tables into fixed device arrays, with that device current; make that
- * first call before any stream capture.  All calls on a GPU share the one
- * scratch array and each call re-initialises what it needs, so calls whose
- * work overlaps on the same GPU race with each other. */
+ * first call before any stream capture.  The addresses are kept for the life of
+ * the process, so a program that destroys the device's primary context
+ * (cudaDeviceReset) must not call rx_track_static again.  All calls on a GPU
+ * share the one scratch array and each call re-initialises what it needs, so
+ * calls whose work overlaps on the same GPU race with each other. */
 rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
                           const int8_t *iq, const uint64_t *rx_byte_offset,
                           uint32_t n_blocks, rx_channel_state *state,

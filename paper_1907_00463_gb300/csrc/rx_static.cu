@@ -1,20 +1,25 @@
 // Allocation-free variant of the batched tracking kernel.
 //
 // Some callers cannot call cudaMalloc: code running where the CUDA allocator is
-// off limits (a host that pre-allocates every buffer at start-up and forbids
-// allocation afterwards, such as a real-time receiver loop with a fixed memory
-// plan, or a plug-in living inside another framework's allocator), or code that
-// must not allocate while a CUDA graph is being captured by its host program.
+// off limits, such as a host that pre-allocates every buffer at start-up and
+// forbids allocation afterwards (a real-time receiver loop with a fixed memory
+// plan), or a plug-in living inside another framework's allocator.
 // rx_track_static gives them the batched closed-loop tracking of rx_batch_run
 // with no allocation at all: the caller passes every input and output buffer,
 // and the kernel's scratch (work-item tickets, per-group progress counters, the
 // error word, the work-item table and the running sums of multi-block
 // integrations) lives in one file-scope __device__ array of fixed size.
 //
+// The call is synchronous: it copies the receiver descriptors from host memory,
+// waits for the stream and reads the error word back before it returns.
+//
 // The array belongs to the library image: every GPU that loads librx holds it
 // until the process exits, every call on that GPU shares it, and it keeps the
 // previous call's contents, so each call clears the parts that must start at
-// zero.  Calls whose work overlaps on the same GPU race on it.
+// zero.  Calls whose work overlaps on the same GPU race on it.  The device
+// addresses are looked up once per device; a caller that destroys the device's
+// primary context (cudaDeviceReset) must not call this entry point again in the
+// same process.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -47,11 +52,22 @@ struct SGroup {            // one channel's work unit
     LoopConsts lc;
 };
 
+// Where receiver r's channels, taps and dumps begin (prefix sums over the
+// receivers before it, computed on the host).
+struct RxPrefix {
+    uint32_t ch0;
+    uint32_t pad;
+    uint64_t tap0;
+    uint64_t dump0;
+};
+static_assert(sizeof(RxPrefix) == 24, "RxPrefix layout");
+
 // Scratch layout (byte offsets inside the array).
 constexpr size_t kOffHeader = 0;                                   // ticket, err[4]
 constexpr size_t kOffRx = 256;                                     // rx_receiver_desc[kMaxRx]
 constexpr size_t kOffRxOff = kOffRx + kMaxRx * sizeof(rx_receiver_desc);
-constexpr size_t kOffDone = kOffRxOff + kMaxRx * 8;                // uint32[kMaxChannels]
+constexpr size_t kOffRxPre = kOffRxOff + kMaxRx * 8;                // RxPrefix[kMaxRx]
+constexpr size_t kOffDone = kOffRxPre + kMaxRx * 24;               // uint32[kMaxChannels]
 constexpr size_t kOffGroups = kOffDone + kMaxChannels * 4;         // SGroup[kMaxChannels]
 constexpr size_t kOffAcc = kOffGroups + kMaxChannels * sizeof(SGroup);  // int32[2*kMaxChannelTaps]
 constexpr size_t kScratchUsed = kOffAcc + kMaxChannelTaps * 8;
@@ -105,42 +121,44 @@ rx_status static_setup(int device, StaticDev *out) {
     return RX_OK;
 }
 
-// Expand the receiver descriptors into one work unit per channel (one thread).
-__global__ void k_static_setup(unsigned char *scratch, uint32_t n_rx, uint32_t n_blocks) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// Expand the receiver descriptors into one work unit per channel: thread i fills
+// channel i, finding its receiver by binary search over the receivers' first
+// channels.
+__global__ void k_static_setup(unsigned char *scratch, uint32_t n_rx, uint32_t n_ch) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ch) return;
     const rx_receiver_desc *rx = reinterpret_cast<const rx_receiver_desc *>(scratch + kOffRx);
+    const RxPrefix *pre = reinterpret_cast<const RxPrefix *>(scratch + kOffRxPre);
     SGroup *gs = reinterpret_cast<SGroup *>(scratch + kOffGroups);
-    uint32_t ch = 0;
-    uint64_t tap = 0, dump = 0;
-    for (uint32_t r = 0; r < n_rx; ++r) {
-        const rx_receiver_desc d = rx[r];
-        for (uint32_t c = 0; c < d.n_channels; ++c) {
-            SGroup g;
-            g.rx = r;
-            g.ch = ch + c;
-            g.ntaps = d.n_taps;
-            g.N = d.block_samples;
-            g.L = d.integ_blocks;
-            g.tap_e = d.tap_early;
-            g.tap_p = d.tap_prompt;
-            g.tap_l = d.tap_late;
-            g.rx_nch = d.n_channels;
-            g.ch_in_rx = c;
-            g.tap_base = tap + (uint64_t)c * d.n_taps;
-            g.dump_base = dump;
-            // loop constants, same operations and order as make_loop_consts on the host
-            const double T = __ddiv_rn((double)((uint64_t)d.integ_blocks * d.block_samples), d.fs_hz);
-            const double w0 = __ddiv_rn(d.pll_bn_hz, 0.53);
-            g.lc.k1 = __dmul_rn(__dmul_rn(w0, w0), T);
-            g.lc.k2 = __dmul_rn(RXD_SQRT2, w0);
-            g.lc.kdll = __dmul_rn(4.0, d.dll_bn_hz);
-            g.lc.sfs = __ddiv_rn(4294967296.0, d.fs_hz);
-            gs[ch + c] = g;
-        }
-        ch += d.n_channels;
-        tap += (uint64_t)d.n_channels * d.n_taps;
-        dump += (uint64_t)(n_blocks / d.integ_blocks) * d.n_channels * d.n_taps * 2;
+    uint32_t lo = 0, hi = n_rx - 1;                 // last receiver with ch0 <= i
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid].ch0 <= i) lo = mid; else hi = mid - 1;
     }
+    const uint32_t r = lo;
+    const rx_receiver_desc d = rx[r];
+    const uint32_t c = i - pre[r].ch0;
+    SGroup g;
+    g.rx = r;
+    g.ch = i;
+    g.ntaps = d.n_taps;
+    g.N = d.block_samples;
+    g.L = d.integ_blocks;
+    g.tap_e = d.tap_early;
+    g.tap_p = d.tap_prompt;
+    g.tap_l = d.tap_late;
+    g.rx_nch = d.n_channels;
+    g.ch_in_rx = c;
+    g.tap_base = pre[r].tap0 + (uint64_t)c * d.n_taps;
+    g.dump_base = pre[r].dump0;
+    // loop constants, same operations and order as make_loop_consts on the host
+    const double T = __ddiv_rn((double)((uint64_t)d.integ_blocks * d.block_samples), d.fs_hz);
+    const double w0 = __ddiv_rn(d.pll_bn_hz, 0.53);
+    g.lc.k1 = __dmul_rn(__dmul_rn(w0, w0), T);
+    g.lc.k2 = __dmul_rn(RXD_SQRT2, w0);
+    g.lc.kdll = __dmul_rn(4.0, d.dll_bn_hz);
+    g.lc.sfs = __ddiv_rn(4294967296.0, d.fs_hz);
+    gs[i] = g;
 }
 
 template <int TT>
@@ -364,7 +382,9 @@ extern "C" rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx, 
         if (d.n_taps > max_taps) max_taps = d.n_taps;
     }
     if (n_ch > kMaxChannels || n_taps > kMaxChannelTaps) return RX_EINVAL;
-    if ((uint64_t)n_ch * n_blocks >= (1ull << 32)) return RX_EINVAL;
+    // Every CTA draws one ticket past the last item, so the largest ticket is
+    // n_ch * n_blocks + grid - 1 with grid <= n_ch: it must not wrap.
+    if ((uint64_t)n_ch * ((uint64_t)n_blocks + 1) > (1ull << 32)) return RX_EINVAL;
     if (device < 0 || device >= kDevices) return RX_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
@@ -374,14 +394,27 @@ extern "C" rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx, 
     if (static_setup(device, &sd) != RX_OK) return RX_ECUDA;
     unsigned char *scratch = sd.scratch;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    RxPrefix pre[kMaxRx];       // pageable: each copy below has read it before it returns
+    {
+        uint32_t ch = 0;
+        uint64_t tap = 0, dump = 0;
+        for (uint32_t r = 0; r < n_rx; ++r) {
+            const rx_receiver_desc &d = rx[r];
+            pre[r] = RxPrefix{ch, 0u, tap, dump};
+            ch += d.n_channels;
+            tap += (uint64_t)d.n_channels * d.n_taps;
+            dump += (uint64_t)(n_blocks / d.integ_blocks) * d.n_channels * d.n_taps * 2;
+        }
+    }
     if (cudaMemcpyAsync(scratch + kOffRx, rx, n_rx * sizeof(rx_receiver_desc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(scratch + kOffRxOff, rx_byte_offset, n_rx * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(scratch + kOffRxPre, pre, n_rx * sizeof(RxPrefix), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(scratch + kOffHeader, 0, 256, s) != cudaSuccess ||
         cudaMemsetAsync(scratch + kOffDone, 0, n_ch * 4, s) != cudaSuccess) {
         cudaGetLastError();
         return RX_ECUDA;
     }
-    k_static_setup<<<1, 1, 0, s>>>(scratch, n_rx, n_blocks);
+    k_static_setup<<<(uint32_t)((n_ch + 127) / 128), 128, 0, s>>>(scratch, n_rx, (uint32_t)n_ch);
     if (cudaGetLastError() != cudaSuccess) return RX_ECUDA;
     size_t smem = (size_t)max_taps * 8 + 64 * 4 + EXT_WORDS * 4 + (size_t)max_taps * 8;
     int occ = 0;

@@ -115,9 +115,14 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
             results.append(_read(b, recv, 20))
         finally:
             rx.rx_batch_destroy(b)
+    # the default tiles against the oracle, then every other tile shape against them
+    _check_against_oracle(recv, sigs, results[0], 20)
     for other in results[1:]:
-        for (d0, _), (d1, _) in zip(results[0], other):
+        for (d0, s0), (d1, s1) in zip(results[0], other):
             assert np.array_equal(d0, d1)
+            assert [(x.carrier_word, x.code_rate, x.carrier_phase, x.code_phase, x.pll_integrator_hz)
+                    for x in s0] == [(x.carrier_word, x.code_rate, x.carrier_phase, x.code_phase,
+                                      x.pll_integrator_hz) for x in s1]
     # receiver 4 alone
     alone = [recv[4]]
     b = _batch(alone, 20)

@@ -87,4 +87,4 @@ def test_uneven_128_receivers_full_second():
 def test_multicorrelator_16_receivers_two_seconds():
     recv = [synth.multicorrelator_receiver(i, n_blocks=2000) for i in range(16)]
     buf, offs, dumps, states, tiles = _run_full(recv, 2000)
-    _check(recv, buf, offs, dumps, states, {0: 3, 9: 3})
+    _check(recv, buf, offs, dumps, states, {0: 50, 5: 50, 9: 50, 15: 50})

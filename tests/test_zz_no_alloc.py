@@ -1,7 +1,8 @@
 """The allocation-free entry point rx_track_static (for callers that cannot
-allocate GPU memory) gives the same dumps and loop state as rx_batch_run on the
-same inputs, over two calls in a row, the second continuing from the state the
-first left in the caller's buffer.  This file is collected last on purpose."""
+allocate GPU memory) gives the same dumps and loop state as rx_batch_run and as the
+oracle on the same inputs, over two calls in a row, the second continuing from the
+state the first left in the caller's buffer.  Device-resident inputs out of range
+are refused without harm to the next call.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -10,36 +11,15 @@ import torch
 
 from paper_1907_00463_gb300 import rx, synth
 
-pytestmark = pytest.mark.gpu
+from helpers import assert_states_equal, initial_states, oracle_run, states_from_device
 
-TWO32 = 4294967296.0
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
     import __graft_entry__
     __graft_entry__.build()
-
-
-def _initial_states(receivers):
-    """rx_channel_state records a caller fills for new channels."""
-    recs = []
-    for r in receivers:
-        prn, w, phi, rate, _ = synth.channel_arrays(r)
-        for c in range(len(prn)):
-            v = float(int(w[c])) * r.fs / TWO32
-            recs.append(rx.rx_channel_state(0, int(w[c]), int(phi[c]) % (1023 << 32), int(rate[c]),
-                                            v, v, float(int(rate[c])) * r.fs / TWO32, int(prn[c]),
-                                            0))
-    arr = (rx.rx_channel_state * len(recs))(*recs)
-    host = np.frombuffer(bytes(arr), np.uint8).copy()
-    return torch.from_numpy(host).cuda(), len(recs)
-
-
-def _states_from_device(dev_bytes, n):
-    raw = dev_bytes.cpu().numpy().tobytes()
-    arr = (rx.rx_channel_state * n).from_buffer_copy(raw)
-    return list(arr)
 
 
 def test_static_entry_matches_batched_entry_two_calls():
@@ -76,7 +56,7 @@ def test_static_entry_matches_batched_entry_two_calls():
         rx.rx_batch_destroy(b)
 
     # allocation-free entry point: caller-owned buffers, two calls in a row
-    state, n_ch = _initial_states(recv)
+    state, n_ch = initial_states(recv)
     taps = torch.from_numpy(np.concatenate([synth.channel_arrays(r)[4].reshape(-1)
                                             for r in recv])).cuda()
     per_rx = [(half // r.integ_blocks) * len(r.channels) * r.n_taps * 2 for r in recv]
@@ -84,7 +64,7 @@ def test_static_entry_matches_batched_entry_two_calls():
         dumps = torch.full((sum(per_rx),), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
         rx.rx_track_static(descs, bufs[k], offs, half, state, taps, dumps)
         got = dumps.cpu().numpy()
-        st = _states_from_device(state, n_ch)
+        st = states_from_device(state, n_ch)
         base, ch = 0, 0
         for i, r in enumerate(recv):
             nd = half // r.integ_blocks
@@ -99,6 +79,65 @@ def test_static_entry_matches_batched_entry_two_calls():
                     (s.pll_integrator_hz, s.carrier_hz, s.code_hz), (k, i, c)
             base += per_rx[i]
             ch += len(r.channels)
+        # and against the oracle directly, over the blocks run so far
+        base = ch = 0
+        for i, r in enumerate(recv):
+            od, os_ = oracle_run(r, sigs[i], (k + 1) * half)
+            nd = half // r.integ_blocks
+            mine = got[base:base + per_rx[i]].reshape(nd, len(r.channels), r.n_taps, 2)
+            assert np.array_equal(mine, od[k * nd:(k + 1) * nd]), (k, i)
+            assert_states_equal(st[ch:ch + len(r.channels)], os_)
+            base += per_rx[i]
+            ch += len(r.channels)
+
+
+def _one_call(recv, n_blocks, sigs, state, taps):
+    offs, pos = [], 0
+    for r in recv:
+        offs.append(pos)
+        pos += ((2 * n_blocks * r.block_samples + 15) // 16) * 16
+    buf = np.zeros(pos, np.int8)
+    for r, o, s in zip(recv, offs, sigs):
+        part = s[:n_blocks * r.block_samples].reshape(-1)
+        buf[int(o):int(o) + part.size] = part
+    per_rx = [(n_blocks // r.integ_blocks) * len(r.channels) * r.n_taps * 2 for r in recv]
+    dumps = torch.zeros(sum(per_rx), dtype=torch.int32, device="cuda")
+    rx.rx_track_static([rx.receiver_desc(r) for r in recv], torch.from_numpy(buf).cuda(),
+                       np.array(offs, np.uint64), n_blocks, state, taps, dumps)
+    return dumps.cpu().numpy(), per_rx
+
+
+@pytest.mark.parametrize("fault", ["prn0", "tap65"])
+def test_static_entry_refuses_out_of_range_device_inputs_then_runs_exactly(fault):
+    """A PRN outside 1..32 or a tap offset beyond 64 chips in the caller's device buffers
+    is found by the kernel before it indexes a table with it: the call returns RX_EINVAL,
+    and the next call with valid buffers is bit-exact with the oracle."""
+    recv = [synth.uniform_receiver(i, n_blocks=4, fs=4.092e6, n_ch=3) for i in range(2)]
+    sigs = [synth.generate_iq(r).numpy() for r in recv]
+    state, n_ch = initial_states(recv)
+    taps_np = np.concatenate([synth.channel_arrays(r)[4].reshape(-1) for r in recv])
+    bad_state = state.clone()
+    bad_taps = torch.from_numpy(taps_np.copy()).cuda()
+    if fault == "prn0":
+        rec_size = ctypes.sizeof(rx.rx_channel_state)
+        prn_at = rx.rx_channel_state.prn.offset
+        raw = bad_state.cpu().numpy()
+        raw[4 * rec_size + prn_at:4 * rec_size + prn_at + 4] = 0          # channel 4: PRN 0
+        bad_state = torch.from_numpy(raw).cuda()
+    else:
+        bad_taps[7] = 65 << 32                                             # beyond 64 chips
+    with pytest.raises(rx.RxError) as e:
+        _one_call(recv, 4, sigs, bad_state, bad_taps)
+    assert e.value.status == rx.RX_EINVAL
+    got, per_rx = _one_call(recv, 4, sigs, state, torch.from_numpy(taps_np).cuda())
+    st = states_from_device(state, n_ch)
+    base = ch = 0
+    for i, r in enumerate(recv):
+        od, os_ = oracle_run(r, sigs[i], 4)
+        assert np.array_equal(got[base:base + per_rx[i]].reshape(od.shape), od), i
+        assert_states_equal(st[ch:ch + len(r.channels)], os_)
+        base += per_rx[i]
+        ch += len(r.channels)
 
 
 def test_static_entry_rejects_sizes_beyond_its_limit():
