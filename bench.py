@@ -59,6 +59,7 @@ KERNEL_SOURCES = {
     "static": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
     "dynamic": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
     "balanced": ["rx_balance.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
+    "segment": ["rx_cseg.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
 }
 
 
@@ -725,7 +726,7 @@ def run_ours(args):
                                       cpu_leg=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
-    sched_name = ["dynamic", "static", "pipelined", "balanced"][tiles[3]]
+    sched_name = ["dynamic", "static", "pipelined", "balanced", "segment"][tiles[3]]
     prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
     if prof and prof["src_sha256"] != kernel_sources_sha256(sched_name):
         prof = None                      # the kernel changed since its counters were taken

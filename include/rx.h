@@ -417,6 +417,12 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
                                 each with an equal share of the whole job: channels
                                 cut between CTAs exchange partial sums each block;
                                 enqueued directly, not through a graph */
+#define RX_SCHED_SEGMENT 4u  /* as PIPE, with the carrier-segment correlator: per block
+                                the CTA builds prefix sums of the raw samples once for
+                                all its channels; each channel's tap sums are then
+                                evaluated only at the carrier-table and code-value
+                                changes (one filter warp per channel, at most 8
+                                channels per item, 256 or 512 threads) */
 
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
  * correlated together by one CTA (0 = choose; for RX_SCHED_BALANCED the
@@ -427,10 +433,11 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
  * item, RX_SCHED_BALANCED two, three with 512, one with 224);
  * ctas_per_sm: resident CTAs per SM for the dynamic and balanced schedules
  * (0 = as many as fit; at most 8 for RX_SCHED_BALANCED); schedule:
- * RX_SCHED_DYNAMIC, RX_SCHED_STATIC, RX_SCHED_PIPE or RX_SCHED_BALANCED.
+ * RX_SCHED_DYNAMIC, RX_SCHED_STATIC, RX_SCHED_PIPE, RX_SCHED_BALANCED or
+ * RX_SCHED_SEGMENT (256 or 512 threads, 0 = 512; at most 8 channels per item).
  * All schedules give identical results.
  * Takes effect at the next run (the graph is re-recorded).  A wait inside a
- * CTA of RX_SCHED_PIPE that exceeds the handle's time limit ends the run with
+ * CTA of RX_SCHED_PIPE or RX_SCHED_SEGMENT that exceeds the handle's time limit ends the run with
  * RX_ETIMEOUT at the next synchronising call. */
 rx_status rx_batch_set_tiles(rx_batch b, uint32_t channels_per_item,
                              uint32_t threads, uint32_t ctas_per_sm,
@@ -441,8 +448,8 @@ rx_status rx_batch_set_tiles(rx_batch b, uint32_t channels_per_item,
 /* Time limit of every wait inside the persistent kernel (default 2 s; from
  * 1 us to 60 s), after which the run stops and the next synchronising call
  * returns RX_ETIMEOUT; the handle stays usable.  flags: 0, or
- * RX_WAIT_TEST_STALL, which makes the first CTA of every RX_SCHED_PIPE run
- * wait on a barrier that nothing completes, so that the limit and its report
+ * RX_WAIT_TEST_STALL, which makes the first CTA of every RX_SCHED_PIPE or
+ * RX_SCHED_SEGMENT run wait on a barrier that nothing completes, so that the limit and its report
  * can be tested without any device fault.  Takes effect at the next run. */
 rx_status rx_batch_set_wait_limit(rx_batch b, uint64_t timeout_ns, uint32_t flags);
 
@@ -451,8 +458,8 @@ rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
                              uint32_t *threads, uint32_t *ctas_per_sm,
                              uint32_t *schedule);
 
-/* Autotuner: time each candidate tile shape (both schedules; 1-16 channels per
- * item; 128/256/512 threads) on the first probe_blocks blocks of the caller's
+/* Autotuner: time each candidate tile shape (every schedule; 1-16 channels per
+ * item; 128/192/224/256/512 threads as each schedule allows) on the first probe_blocks blocks of the caller's
  * input (arguments as in rx_batch_run; host input is copied whole before each
  * timed run, never in overlapped chunks, so the candidates differ by their
  * tracking alone), keep the fastest, and return the receivers to their
@@ -507,6 +514,8 @@ typedef struct {
     uint64_t active_channels;
     uint64_t pool_bytes_used, pool_bytes_total;
     uint32_t device_timeouts;
+    uint64_t timed_pushes;            /* pushes that carried their scheduled arrival (rx_serve_push_at) */
+    double p99_push_lag_ms, max_push_lag_ms;  /* how late those pushes came after their arrival */
 } rx_serve_stats;
 
 /* Create a server (allocates the budget pool, rings, and starts its service
@@ -530,8 +539,18 @@ rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *desc, const uint8_t
 rx_status rx_serve_release(rx_serve s, uint32_t id);
 
 /* Queue the stream's next block (2*N int8 of host memory, copied before
- * return).  RX_EAGAIN if the ring is full or the stream is still queued. */
+ * return).  RX_EAGAIN if the ring is full or the stream is still queued.  The
+ * block's latency is measured from this call. */
 rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block);
+
+/* As rx_serve_push for a block that arrived at arrival_ns on the library's
+ * clock (rx_serve_clock_ns): its latency is measured from that arrival, so a
+ * producer that falls behind its arrivals shows up in the latency, and the lag
+ * of the push itself is kept in the statistics. */
+rx_status rx_serve_push_at(rx_serve s, uint32_t id, const int8_t *block, uint64_t arrival_ns);
+
+/* The serving clock (monotonic, nanoseconds). */
+uint64_t rx_serve_clock_ns(void);
 
 /* Block until every pushed block has been processed. */
 rx_status rx_serve_drain(rx_serve s);
@@ -588,9 +607,33 @@ typedef struct {
 } rx_replay_config;
 
 /* Admit the n streams, run the arrival processes for duration_s, then drain.
+ * Each block is pushed with its scheduled arrival (rx_serve_push_at), so its
+ * latency counts from when it was due, not from when a producer got to it.
  * ids_out (optional, n entries) receives each stream's final id. */
 rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *streams, uint32_t n,
                           const rx_replay_config *cfg, uint32_t *ids_out);
+
+/* The plain per-receiver form under the same arrivals, for comparison with the
+ * served form: one rx_handle per stream (rx_create, rx_set_channels), and at
+ * each scheduled arrival the producer thread that owns the stream calls
+ * rx_correlate on the block (host memory) and, at every integ_blocks-th
+ * block, rx_track_epoch, then waits for the handle's stream: the paper's
+ * per-call tracking (Sec. 3.4-3.5, do_tracking per block) on the GPU.  Each
+ * producer thread has its own CUDA stream; a block's latency runs from its
+ * scheduled arrival to that wait's return, so a thread that falls behind adds
+ * its backlog to the latency.  Arrival process and rates as rx_serve_replay
+ * (churn ignored); loop sets and bandwidths from each stream's descriptor.
+ * Creates and destroys the handles itself. */
+typedef struct {
+    uint64_t blocks_done;
+    uint64_t deadline_misses;         /* blocks whose latency exceeded 1 ms */
+    double p50_ms, p99_ms, max_ms, mean_ms;
+    uint32_t producer_threads;
+    uint32_t pad;
+} rx_plain_replay_stats;
+
+rx_status rx_plain_replay(const rx_replay_stream *streams, uint32_t n, const rx_replay_config *cfg,
+                          int32_t device, rx_plain_replay_stats *out);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free batched tracking                                         */
@@ -643,6 +686,22 @@ rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
                           uint32_t n_blocks, rx_channel_state *state,
                           const int64_t *tap_offsets, int32_t *dumps,
                           int32_t device, void *cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* INT32 issue rate of the device, the denominator of the correlator's
+ * roofline (the correlator is bound by 32-bit integer instruction issue; the
+ * paper reports CPU timings only, Sec. 4, so this is the build's own
+ * measurement, not a step of the method).  One launch of enough 256-thread
+ * CTAs to fill every SM, each thread running eight independent chains of
+ * multiply-add, three-input logic and add (IMAD, LOP3, IADD3), timed with CUDA
+ * events; the best of five timed launches after a warm-up.  *tops_out receives
+ * tera-operations per second (one operation per thread per instruction), *ms_out
+ * (optional) the launch time.  Allocates and frees a small output buffer.
+ * RX_EINVAL for a null tops_out, RX_ECUDA on a CUDA error. */
+rx_status rx_measure_int32_peak(int32_t device, double *tops_out, double *ms_out);
 
 /* ------------------------------------------------------------------------ */
 /* Acquisition (Sec. 3.3 ACQ module, Sec. 3.6 outputs, Sec. 3.7 PCS search) */

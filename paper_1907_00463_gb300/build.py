@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librx.so")
 
 SOURCES = ["rx_tables.cpp", "rx_plain.cu", "rx_batch.cu", "rx_static.cu", "rx_serve.cu", "rx_pipe.cu",
-           "rx_balance.cu", "rx_acq.cu"]
+           "rx_balance.cu", "rx_acq.cu", "rx_cseg.cu", "rx_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I", os.path.join(ROOT, "include")]

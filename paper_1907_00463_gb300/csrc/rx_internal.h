@@ -12,6 +12,14 @@
 
 namespace rxh {
 
+// Extended chip axis of the carrier-segment correlator's code tables: chip c, for c in
+// [-CS_CBASE, CS_CLEN - CS_CBASE), sits at index c + CS_CBASE and has the code value
+// of chip (c mod 1023).  It covers a tap offset of up to 64 chips either side plus
+// more than two code periods.
+constexpr int CS_CBASE = 128;
+constexpr int CS_CLEN = 2560;
+constexpr int CS_LMAX = 1536;   // transition-list entries per PRN (at least the transitions of CS_CLEN chips)
+
 // Per-device constant tables, built once per device on first use and kept
 // until process exit: the extended bit-packed C/A codes of PRN 1..32
 // ([33][EXT_WORDS] words, row 0 unused) and the 64 packed carrier entries.
@@ -19,6 +27,9 @@ struct DeviceTables {
     uint32_t *code = nullptr;   // device
     uint32_t *tab = nullptr;    // device
     uint16_t *pair = nullptr;   // device, [33][PAIR_LEN] chip-pair entries
+    uint16_t *tlist = nullptr;  // device, [33][CS_LMAX] code transitions (carrier-segment form)
+    uint16_t *tcount = nullptr; // device, [33][CS_CLEN + 1]
+    uint32_t *tbits = nullptr;  // device, [33][CS_CLEN / 32]
     int sm_count = 0;
     int max_smem_optin = 0;
 };
@@ -33,6 +44,15 @@ void build_carrier_table(uint32_t *out /* [64] */);
 // Chip-pair table: entry c + PAIR_BASE (c in [-PAIR_BASE, PAIR_LEN - PAIR_BASE)) holds the
 // code values around chip c as int8 bytes: low byte g(c+1), next byte g(c) - g(c+1).
 void build_pair_table(uint16_t *out /* [33][PAIR_LEN] */);
+// Code transitions over the extended chip axis, per PRN:
+//   list[p][u]  the u-th index i in [1, CS_CLEN) (ascending) at which the code value
+//               changes, g(i - 1) != g(i), as i | 0x8000 when g(i - 1) - g(i) = -2 and
+//               as i when it is +2; entries past the last are 0;
+//   count[p][i] the number of transitions at indices below i, i in [0, CS_CLEN];
+//   bits[p]     the logic levels (1 = code value -1), index i at bit 31 - (i mod 32)
+//               of word i / 32.
+void build_transition_tables(uint16_t *list /* [33][CS_LMAX] */, uint16_t *count /* [33][CS_CLEN + 1] */,
+                             uint32_t *bits /* [33][CS_CLEN / 32] */);
 
 inline std::string fmt(const char *f, ...) {
     char buf[512];

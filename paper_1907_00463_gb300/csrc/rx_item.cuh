@@ -80,6 +80,9 @@ struct Tables {
     const uint32_t *code;     // extended bit-packed C/A codes [33][EXT_WORDS]
     const uint32_t *carrier;  // 64 packed (c, s, -s, c)
     const uint16_t *pair;     // chip-pair entries [33][PAIR_LEN]
+    const uint16_t *tlist;    // code transitions over the extended chip axis [33][CS_LMAX]
+    const uint16_t *tcount;   // transitions below each index [33][CS_CLEN + 1]
+    const uint32_t *tbits;    // code logic levels over the extended chip axis [33][CS_CLEN / 32]
 };
 
 // Shared-memory carve-up for a CTA of NT threads handling at most cpg channels of
@@ -445,6 +448,34 @@ int pipe_occupancy(uint32_t nt, uint32_t filter_warps, bool staged, size_t smem,
 // One CTA per group (grid = number of groups).
 cudaError_t pipe_launch(uint32_t nt, uint32_t filter_warps, uint32_t grid, size_t smem,
                         cudaStream_t stream, const PipeArgs &a);
+
+// ----------------------------------------------------------------------------
+// Carrier-segment form in the pipelined arrangement (rx_cseg.cu)
+// ----------------------------------------------------------------------------
+
+struct CsArgs {
+    const GroupDesc *groups;
+    const uint64_t *src_off;   // byte offset of each receiver's samples
+    const int8_t *iq;
+    Tables tb;
+    uint32_t *err;             // [4]: code, 0xffffffff, group, block
+    uint64_t timeout_ns;       // limit on any one wait inside a CTA
+    uint32_t n_blocks;
+    uint32_t cpg;
+    uint32_t max_taps;
+    uint32_t max_n;            // largest block of any receiver (sizes the prefix buffer)
+    uint32_t stall;            // 1: CTA 0 first waits on a barrier that nothing completes
+    uint32_t table3;           // 1: some group runs RX_LOOPS_TABLE3
+};
+
+// Filter warps for cpg channels per CTA (one per channel, at most 8).
+uint32_t cs_filter_warps(uint32_t cpg);
+// Dynamic shared memory of one CTA with nt correlation threads.
+size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t max_n);
+// Resident CTAs per SM.
+int cs_occupancy(uint32_t nt, uint32_t nf, size_t smem, bool table3);
+// One CTA per group (grid = number of groups).
+cudaError_t cs_launch(uint32_t nt, uint32_t nf, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a);
 
 // ----------------------------------------------------------------------------
 // Balanced schedule (rx_balance.cu)

@@ -204,6 +204,7 @@ struct rx_serve_s {
     bool running = false, stop = false;
     // statistics
     std::vector<float> lat_us;
+    std::vector<float> lag_us;                    // how late timed pushes came after their arrival
     uint64_t blocks_done = 0, misses = 0, dropped = 0, ticks = 0, items_total = 0;
     uint32_t timeouts = 0;
     std::string err;
@@ -440,7 +441,8 @@ rx_status launch_tick(rx_serve s) {
     a.groups = s->d_groups;
     a.items = s->d_items[buf];
     a.ring = s->d_ring;
-    a.tb = Tables{s->tables->code, s->tables->tab, s->tables->pair};
+    a.tb = Tables{s->tables->code, s->tables->tab, s->tables->pair, s->tables->tlist, s->tables->tcount,
+                   s->tables->tbits};
     a.ticket = s->d_scratch[buf];
     a.err = s->d_scratch[buf] + 1;
     a.done = s->d_done;
@@ -637,9 +639,12 @@ extern "C" rx_status rx_serve_release(rx_serve s, uint32_t id) {
     return RX_OK;
 }
 
-extern "C" rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block) {
+namespace {
+
+// Queue a block that arrived at `arrival` (timed: the arrival was scheduled, not the
+// moment of the call, and the lag of the call is kept).
+rx_status push_block(rx_serve s, uint32_t id, const int8_t *block, Clock::time_point arrival, bool timed) {
     if (!s || !block || id >= s->cfg.max_streams) return RX_EINVAL;
-    const Clock::time_point arrival = Clock::now();
     uint32_t slot, seq;
     size_t bytes;
     {
@@ -661,10 +666,26 @@ extern "C" rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block)
     std::memcpy(s->h_ring + (size_t)slot * s->slot_bytes, block, bytes);
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        if (timed) s->lag_us.push_back(std::chrono::duration<float, std::micro>(Clock::now() - arrival).count());
         s->pending.push_back(Pending{slot, id, seq, arrival});
     }
     s->cv.notify_one();
     return RX_OK;
+}
+
+}  // namespace
+
+extern "C" rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block) {
+    return push_block(s, id, block, Clock::now(), false);
+}
+
+extern "C" uint64_t rx_serve_clock_ns(void) {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+extern "C" rx_status rx_serve_push_at(rx_serve s, uint32_t id, const int8_t *block, uint64_t arrival_ns) {
+    const Clock::time_point arrival{std::chrono::duration_cast<Clock::duration>(std::chrono::nanoseconds(arrival_ns))};
+    return push_block(s, id, block, arrival, true);
 }
 
 extern "C" rx_status rx_serve_drain(rx_serve s) {
@@ -716,6 +737,14 @@ extern "C" rx_status rx_serve_get_stats(rx_serve s, rx_serve_stats *out) {
     out->pool_bytes_used = s->pool->used();
     out->pool_bytes_total = s->pool->size();
     out->device_timeouts = s->timeouts;
+    out->timed_pushes = s->lag_us.size();
+    if (!s->lag_us.empty()) {
+        std::vector<float> v = s->lag_us;
+        const size_t k = (size_t)(0.99 * (v.size() - 1));
+        std::nth_element(v.begin(), v.begin() + k, v.end());
+        out->p99_push_lag_ms = (double)v[k] / 1000.0;
+        out->max_push_lag_ms = (double)*std::max_element(v.begin(), v.end()) / 1000.0;
+    }
     return RX_OK;
 }
 
@@ -723,6 +752,7 @@ extern "C" rx_status rx_serve_reset_stats(rx_serve s) {
     if (!s) return RX_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     s->lat_us.clear();
+    s->lag_us.clear();
     s->blocks_done = s->misses = s->dropped = s->ticks = s->items_total = 0;
     return RX_OK;
 }
@@ -897,7 +927,7 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
             if (rs[k].max_blocks == 0 || sent[k] < rs[k].max_blocks) {
                 const uint64_t blk = sent[k] % rs[k].rec_blocks;
                 const int8_t *src = rs[k].recording + blk * 2 * (uint64_t)rs[k].desc->block_samples;
-                if (rx_serve_push(s, ids[k], src) == RX_OK) sent[k] += 1;
+                if (push_block(s, ids[k], src, when, true) == RX_OK) sent[k] += 1;
                 pq.push({ev.t - std::log(1.0 - U(rng)) / rate[k], k});
             }
         }
@@ -909,4 +939,127 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
     if (ids_out)
         for (uint32_t k = 0; k < n; ++k) ids_out[k] = ids[k];
     return r;
+}
+
+// ----------------------------------------------------------------------------
+// The plain per-receiver form under the same arrivals (comparator)
+// ----------------------------------------------------------------------------
+
+extern "C" rx_status rx_plain_replay(const rx_replay_stream *rs, uint32_t n, const rx_replay_config *cfg,
+                                     int32_t device, rx_plain_replay_stats *out) {
+    if (!rs || !cfg || !out || n == 0 || !(cfg->rate_hz > 0) || !(cfg->duration_s > 0) || cfg->rate_jitter < 0 ||
+        cfg->rate_jitter >= 1)
+        return RX_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return RX_ECUDA;
+    }
+    const uint32_t nthr = std::max<uint32_t>(1, std::min<uint32_t>(cfg->producer_threads ? cfg->producer_threads : 4, n));
+    std::vector<cudaStream_t> streams(nthr, nullptr);
+    std::vector<rx_handle> h(n, nullptr);
+    rx_status rc = RX_OK;
+    for (uint32_t t = 0; t < nthr && rc == RX_OK; ++t)
+        if (cudaStreamCreateWithFlags(&streams[t], cudaStreamNonBlocking) != cudaSuccess) rc = RX_ECUDA;
+    for (uint32_t k = 0; k < n && rc == RX_OK; ++k) {
+        const rx_receiver_desc &d = *rs[k].desc;
+        rx_config c{};
+        c.fs_hz = d.fs_hz;
+        c.max_block_samples = d.block_samples;
+        c.max_channels = d.n_channels;
+        c.max_taps = d.n_taps;
+        c.pll_bn_hz = d.pll_bn_hz;
+        c.dll_bn_hz = d.dll_bn_hz;
+        c.tap_early = d.tap_early;
+        c.tap_prompt = d.tap_prompt;
+        c.tap_late = d.tap_late;
+        c.device = device;
+        c.cuda_stream = streams[k % nthr];
+        c.loop_set = d.loop_set;
+        c.health_window = d.health_window;
+        c.fll_bn_hz = d.fll_bn_hz;
+        rc = rx_create(&c, &h[k]);
+        if (rc == RX_OK)
+            rc = rx_set_channels(h[k], d.n_channels, rs[k].prn, rs[k].carrier_word, rs[k].code_phase_word,
+                                 rs[k].code_rate_word, rs[k].tap_offsets, d.n_taps);
+    }
+    std::vector<std::vector<float>> lat(nthr);
+    std::atomic<uint32_t> failed{0};
+    if (rc == RX_OK) {
+        for (cudaStream_t st : streams) cudaStreamSynchronize(st);
+        const auto t0 = Clock::now() + std::chrono::milliseconds(2);
+        const auto t_end = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(cfg->duration_s));
+        auto producer = [&](uint32_t tid) {
+            cudaSetDevice(device);
+            std::mt19937_64 rng(cfg->seed * 1000003ull + tid);
+            std::uniform_real_distribution<double> U(0.0, 1.0);
+            struct Ev {
+                double t;
+                uint32_t k;
+                bool operator>(const Ev &o) const { return t > o.t; }
+            };
+            std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> pq;
+            std::vector<double> rate(n, 0.0);
+            std::vector<uint64_t> sent(n, 0);
+            for (uint32_t k = tid; k < n; k += nthr) {
+                rate[k] = cfg->rate_hz * (1.0 - cfg->rate_jitter + 2.0 * cfg->rate_jitter * U(rng));
+                pq.push({-std::log(1.0 - U(rng)) / rate[k], k});
+            }
+            while (!pq.empty()) {
+                const Ev ev = pq.top();
+                const auto when = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(ev.t));
+                if (when >= t_end) break;
+                while (Clock::now() < when) {
+                    const auto left = when - Clock::now();
+                    if (left > std::chrono::microseconds(60)) std::this_thread::sleep_for(left - std::chrono::microseconds(50));
+                }
+                pq.pop();
+                const uint32_t k = ev.k;
+                if (rs[k].max_blocks == 0 || sent[k] < rs[k].max_blocks) {
+                    const rx_receiver_desc &d = *rs[k].desc;
+                    const uint64_t blk = sent[k] % rs[k].rec_blocks;
+                    const int8_t *src = rs[k].recording + blk * 2 * (uint64_t)d.block_samples;
+                    rx_status r = rx_correlate(h[k], src, d.block_samples);
+                    sent[k] += 1;
+                    if (r == RX_OK && sent[k] % d.integ_blocks == 0) r = rx_track_epoch(h[k]);
+                    if (r == RX_OK && cudaStreamSynchronize(streams[tid]) != cudaSuccess) r = RX_ECUDA;
+                    if (r != RX_OK) {
+                        failed.fetch_add(1);
+                        return;
+                    }
+                    lat[tid].push_back(std::chrono::duration<float, std::micro>(Clock::now() - when).count());
+                    pq.push({ev.t - std::log(1.0 - U(rng)) / rate[k], k});
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (uint32_t t = 0; t < nthr; ++t) th.emplace_back(producer, t);
+        for (auto &x : th) x.join();
+        if (failed.load()) rc = RX_ECUDA;
+    }
+    for (uint32_t k = 0; k < n; ++k)
+        if (h[k]) rx_destroy(h[k]);
+    for (cudaStream_t st : streams)
+        if (st) cudaStreamDestroy(st);
+    std::vector<float> all;
+    for (auto &v : lat) all.insert(all.end(), v.begin(), v.end());
+    out->producer_threads = nthr;
+    out->blocks_done = all.size();
+    if (!all.empty()) {
+        double sum = 0;
+        for (float x : all) {
+            sum += x;
+            if (x > 1000.0f) out->deadline_misses += 1;
+        }
+        out->mean_ms = sum / all.size() / 1000.0;
+        auto pct = [&](double q) {
+            const size_t k = (size_t)(q * (all.size() - 1));
+            std::nth_element(all.begin(), all.begin() + k, all.end());
+            return (double)all[k] / 1000.0;
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = (double)*std::max_element(all.begin(), all.end()) / 1000.0;
+    }
+    return rc;
 }

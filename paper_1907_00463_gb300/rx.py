@@ -24,6 +24,7 @@ RX_SCHED_DYNAMIC = 0
 RX_SCHED_STATIC = 1
 RX_SCHED_PIPE = 2
 RX_SCHED_BALANCED = 3
+RX_SCHED_SEGMENT = 4
 RX_WAIT_TEST_STALL = 1
 RX_EPOCH_BLOCKS = 0
 RX_EPOCH_CODE = 1
@@ -98,6 +99,15 @@ class rx_serve_config(C.Structure):
                 ("hbm_budget_bytes", C.c_uint64)]
 
 
+class rx_plain_replay_stats(C.Structure):
+    _fields_ = [("blocks_done", C.c_uint64), ("deadline_misses", C.c_uint64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("mean_ms", C.c_double), ("producer_threads", C.c_uint32), ("pad", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class rx_serve_stats(C.Structure):
     _fields_ = [("blocks_done", C.c_uint64), ("deadline_misses", C.c_uint64),
                 ("dropped_blocks", C.c_uint64), ("ticks", C.c_uint64),
@@ -105,7 +115,9 @@ class rx_serve_stats(C.Structure):
                 ("p99_ms", C.c_double), ("max_ms", C.c_double), ("mean_ms", C.c_double),
                 ("active_streams", C.c_uint32), ("queued_streams", C.c_uint32),
                 ("active_channels", C.c_uint64), ("pool_bytes_used", C.c_uint64),
-                ("pool_bytes_total", C.c_uint64), ("device_timeouts", C.c_uint32)]
+                ("pool_bytes_total", C.c_uint64), ("device_timeouts", C.c_uint32),
+                ("timed_pushes", C.c_uint64), ("p99_push_lag_ms", C.c_double),
+                ("max_push_lag_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -194,6 +206,8 @@ SIGNATURES = [
                                  C.POINTER(C.c_uint32)]),
     ("rx_serve_release", C.c_int, [P, C.c_uint32]),
     ("rx_serve_push", C.c_int, [P, C.c_uint32, P]),
+    ("rx_serve_push_at", C.c_int, [P, C.c_uint32, P, C.c_uint64]),
+    ("rx_serve_clock_ns", C.c_uint64, []),
     ("rx_serve_drain", C.c_int, [P]),
     ("rx_serve_get_stats", C.c_int, [P, C.POINTER(rx_serve_stats)]),
     ("rx_serve_reset_stats", C.c_int, [P]),
@@ -206,6 +220,9 @@ SIGNATURES = [
     ("rx_serve_last_error", C.c_char_p, [P]),
     ("rx_serve_replay", C.c_int, [P, C.POINTER(rx_replay_stream), C.c_uint32,
                                   C.POINTER(rx_replay_config), C.POINTER(C.c_uint32)]),
+    ("rx_plain_replay", C.c_int, [C.POINTER(rx_replay_stream), C.c_uint32, C.POINTER(rx_replay_config),
+                                  C.c_int32, C.POINTER(rx_plain_replay_stats)]),
+    ("rx_measure_int32_peak", C.c_int, [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rx_acq_create", C.c_int, [C.POINTER(rx_acq_config), C.POINTER(P)]),
     ("rx_acq_destroy", C.c_int, [P]),
     ("rx_acq_set_search", C.c_int, [P, C.c_uint32, P, C.c_uint32, P, C.c_uint64]),
@@ -613,6 +630,19 @@ def rx_serve_push(s, sid: int, block) -> int:
     return st
 
 
+def rx_serve_push_at(s, sid: int, block, arrival_ns: int) -> int:
+    """As rx_serve_push, with the block's arrival on the serving clock (rx_serve_clock_ns)."""
+    lib = load()
+    st = lib.rx_serve_push_at(s, sid, _ptr(block), arrival_ns)
+    if st not in (RX_OK, RX_EAGAIN):
+        _check(s, st, lib.rx_serve_last_error)
+    return st
+
+
+def rx_serve_clock_ns() -> int:
+    return load().rx_serve_clock_ns()
+
+
 def rx_serve_drain(s) -> None:
     lib = load()
     _check(s, lib.rx_serve_drain(s), lib.rx_serve_last_error)
@@ -807,3 +837,46 @@ def rx_batch_read_code_state(b, rx: int, n_ch: int) -> list:
     arr = (rx_code_state * n_ch)()
     _check(b, lib.rx_batch_read_code_state(b, rx, arr, n_ch), lib.rx_batch_last_error)
     return list(arr)
+
+
+def rx_measure_int32_peak(device: int = 0) -> tuple[float, float]:
+    """(INT32 tera-operations per second, launch ms) measured on the device."""
+    lib = load()
+    tops, ms = C.c_double(), C.c_double()
+    st = lib.rx_measure_int32_peak(device, C.byref(tops), C.byref(ms))
+    if st != RX_OK:
+        raise RxError(st, "rx_measure_int32_peak")
+    return tops.value, ms.value
+
+
+def _replay_arrays(streams):
+    keep = []
+    arr = (rx_replay_stream * len(streams))()
+    for k, d in enumerate(streams):
+        desc = d["desc"]
+        prn = _arr(d["prn"], np.uint8)
+        w = _arr(d["carrier_word"], np.int32)
+        phi = _arr(d["code_phase_word"], np.uint64)
+        r = _arr(d["code_rate_word"], np.uint64)
+        taps = _arr(d["tap_offsets"], np.int64)
+        rec = np.ascontiguousarray(d["recording"], dtype=np.int8)
+        nblk = rec.size // (2 * desc.block_samples)
+        keep += [desc, prn, w, phi, r, taps, rec]
+        arr[k] = rx_replay_stream(C.pointer(desc), _ptr(prn), _ptr(w), _ptr(phi), _ptr(r),
+                                  _ptr(taps), _ptr(rec), nblk, d.get("max_blocks", 0),
+                                  1 if d.get("churn", False) else 0)
+    return arr, keep
+
+
+def rx_plain_replay(streams, rate_hz: float = 1000.0, rate_jitter: float = 0.1, duration_s: float = 1.0,
+                    seed: int = 0, producer_threads: int = 0, device: int = 0) -> dict:
+    """The plain per-receiver form under Poisson arrivals (streams as in rx_serve_replay)."""
+    lib = load()
+    arr, keep = _replay_arrays(streams)
+    cfg = rx_replay_config(rate_hz, rate_jitter, duration_s, 0.0, seed, producer_threads)
+    out = rx_plain_replay_stats()
+    st = lib.rx_plain_replay(arr, len(streams), C.byref(cfg), device, C.byref(out))
+    del keep
+    if st != RX_OK:
+        raise RxError(st, "rx_plain_replay")
+    return out.as_dict()

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "rx.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:rx_status|const char \*|uint32_t)\s*\*?\s*(rx_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:rx_status|const char \*|uint32_t|uint64_t)\s*\*?\s*(rx_\w+)\s*\(",
                                  src, flags=re.M)))
 
 

@@ -56,7 +56,8 @@ def _check_against_oracle(receivers, sigs, results, n_blocks):
         assert_states_equal(s, os_)
 
 
-@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED)])
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 512, 0, rx.RX_SCHED_SEGMENT),
+                                   (3, 256, 0, rx.RX_SCHED_SEGMENT)])
 def test_uniform_batch_matches_oracle(tiles):
     recv = [synth.uniform_receiver(i, n_blocks=12) for i in range(4)]
     buf, offs, sigs = _pack(recv, 12)
@@ -69,7 +70,8 @@ def test_uniform_batch_matches_oracle(tiles):
     _check_against_oracle(recv, sigs, res, 12)
 
 
-@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED)])
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 512, 0, rx.RX_SCHED_SEGMENT),
+                                   (2, 256, 0, rx.RX_SCHED_SEGMENT)])
 def test_uneven_batch_matches_oracle(tiles):
     recv = [synth.uneven_receiver(i, n_blocks=40) for i in range(8)]
     assert len({r.fs for r in recv}) >= 3 and len({r.integ_blocks for r in recv}) >= 3
@@ -83,7 +85,8 @@ def test_uneven_batch_matches_oracle(tiles):
     _check_against_oracle(recv, sigs, res, 40)
 
 
-@pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE), (0, 224, 3, rx.RX_SCHED_BALANCED)])
+@pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE), (0, 224, 3, rx.RX_SCHED_BALANCED),
+                                   (4, 512, 0, rx.RX_SCHED_SEGMENT)])
 def test_multicorrelator_101_taps_matches_oracle(tiles):
     recv = [synth.multicorrelator_receiver(i, n_blocks=3) for i in range(2)]
     buf, offs, sigs = _pack(recv, 3)
@@ -108,7 +111,9 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
                   (2, 224, 0, rx.RX_SCHED_PIPE), (3, 224, 0, rx.RX_SCHED_PIPE),
                   (0, 224, 3, rx.RX_SCHED_BALANCED), (0, 128, 4, rx.RX_SCHED_BALANCED),
                   (0, 256, 1, rx.RX_SCHED_BALANCED), (0, 512, 1, rx.RX_SCHED_BALANCED),
-                  (0, 192, 3, rx.RX_SCHED_BALANCED)]:
+                  (0, 192, 3, rx.RX_SCHED_BALANCED), (1, 256, 0, rx.RX_SCHED_SEGMENT),
+                  (2, 256, 0, rx.RX_SCHED_SEGMENT), (3, 512, 0, rx.RX_SCHED_SEGMENT),
+                  (8, 512, 0, rx.RX_SCHED_SEGMENT)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -135,15 +140,22 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
     assert np.array_equal(d, results[0][4][0])
 
 
+def _tiles_for(schedule):
+    if schedule == rx.RX_SCHED_BALANCED:
+        return (0, 128, 0, schedule)
+    if schedule == rx.RX_SCHED_SEGMENT:
+        return (2, 256, 0, schedule)
+    return (2, 128, 0, schedule)
+
+
 @pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE,
-                                      rx.RX_SCHED_BALANCED])
+                                      rx.RX_SCHED_BALANCED, rx.RX_SCHED_SEGMENT])
 def test_graph_replay_restart_continue_and_host_input(schedule):
     recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
     recv[1].integ_blocks = 5                     # an integration spans the two runs (8 + 8 blocks)
     buf, offs, sigs = _pack(recv, 16)
     dev = torch.from_numpy(buf).cuda()
-    tiles = (0, 128, 0, schedule) if schedule == rx.RX_SCHED_BALANCED else (2, 128, 0, schedule)
-    b = _batch(recv, 16, tiles)
+    b = _batch(recv, 16, _tiles_for(schedule))
     try:
         # first half, then the second half continuing (device input, no graph)
         half = [np.ascontiguousarray(s[:8 * r.block_samples]) for s, r in zip(sigs, recv)]
@@ -179,7 +191,7 @@ def _same_runs(x, y):
 
 
 @pytest.mark.parametrize("schedule", [rx.RX_SCHED_DYNAMIC, rx.RX_SCHED_STATIC, rx.RX_SCHED_PIPE,
-                                      rx.RX_SCHED_BALANCED])
+                                      rx.RX_SCHED_BALANCED, rx.RX_SCHED_SEGMENT])
 def test_host_input_in_chunks(schedule):
     """Host input copied and tracked in chunks of 3 blocks: 16 blocks make five chunks
     and a ragged one, and an integration of 5 blocks spans chunk boundaries.  One
@@ -189,8 +201,7 @@ def test_host_input_in_chunks(schedule):
     recv = [synth.uniform_receiver(i, n_blocks=16, fs=4.092e6) for i in range(3)]
     recv[1].integ_blocks = 5
     buf, offs, sigs = _pack(recv, 16)
-    tiles = (0, 128, 0, schedule) if schedule == rx.RX_SCHED_BALANCED else (2, 128, 0, schedule)
-    b = _batch(recv, 16, tiles)
+    b = _batch(recv, 16, _tiles_for(schedule))
     try:
         rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 16, rx.RX_RUN_RESTART)
         whole = _read(b, recv, 16)
@@ -279,13 +290,14 @@ def test_batch_invalid_arguments():
         rx.rx_batch_destroy(b)
 
 
-def test_wait_limit_reports_timeout_and_the_handle_recovers():
+@pytest.mark.parametrize("schedule", [rx.RX_SCHED_PIPE, rx.RX_SCHED_SEGMENT])
+def test_wait_limit_reports_timeout_and_the_handle_recovers(schedule):
     """A wait that cannot finish (the test hook's barrier, which nothing completes)
     ends the run with RX_ETIMEOUT after the limit; the next run is exact."""
     recv = [synth.uniform_receiver(i, n_blocks=6, fs=4.092e6) for i in range(3)]
     buf, offs, sigs = _pack(recv, 6)
     dev = torch.from_numpy(buf).cuda()
-    b = _batch(recv, 6, (2, 128, 0, rx.RX_SCHED_PIPE))
+    b = _batch(recv, 6, _tiles_for(schedule))
     try:
         rx.rx_batch_set_wait_limit(b, 1_000_000, rx.RX_WAIT_TEST_STALL)
         rx.rx_batch_run(b, dev, offs, 6, rx.RX_RUN_RESTART)
@@ -304,3 +316,44 @@ def test_wait_limit_reports_timeout_and_the_handle_recovers():
     finally:
         rx.rx_batch_destroy(b)
     _check_against_oracle(recv, sigs, res, 6)
+
+
+@pytest.mark.parametrize("tiles", [(3, 512, 0, rx.RX_SCHED_SEGMENT), (6, 256, 0, rx.RX_SCHED_SEGMENT)])
+def test_segment_form_takes_any_words(tiles):
+    """Carrier words drawn over the whole int32 range (most blocks then have too many
+    carrier segments and take the direct form) next to Doppler up to 15 kHz (the segment
+    form), tap offsets up to 64 chips either side, code phases anywhere, uniform int8
+    noise: every dump and final state bit-exact with the oracle."""
+    g = np.random.Generator(np.random.Philox(key=[463088, 1]))
+    recv, sigs = [], []
+    for k, fs in enumerate([4.092e6, 16.368e6, 25.0e6]):
+        N = int(round(fs / 1000))
+        chans = []
+        for c in range(6):
+            prn = int(g.integers(1, 33))
+            if c < 3:
+                w = int(g.integers(-(1 << 31), 1 << 31))
+                dop = float(w) * fs / 2 ** 32
+            else:
+                dop = float(g.uniform(-15000, 15000))
+                w = int(np.rint(dop / fs * 2 ** 32))
+            r = int(np.rint(1.023e6 * (1 + dop / 1575.42e6) / fs * 2 ** 32))
+            phi = int(g.integers(0, 1023 << 32))
+            taps = sorted(int(x) for x in g.integers(-(64 << 32), (64 << 32) + 1, 5))
+            taps[2] = 0
+            chans.append(synth.Channel(prn, w, phi, r, taps))
+        rec = synth.Receiver(fs, N, 4, [], chans, 1, 15.0, 1.0, 3, 2, 1, sigma=0.0,
+                             meta={"workload": "any words", "fs": fs})
+        recv.append(rec)
+        sigs.append(g.integers(-128, 128, size=(4 * N, 2)).astype(np.int8))
+    offs, total = batch_layout(recv)
+    buf = np.zeros(total, np.int8)
+    for o, s in zip(offs, sigs):
+        buf[int(o):int(o) + s.size] = s.reshape(-1)
+    b = _batch(recv, 4, tiles)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 4)
+        res = _read(b, recv, 4)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 4)

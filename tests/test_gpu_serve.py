@@ -115,3 +115,80 @@ def test_admission_is_bounded_by_the_memory_budget():
         assert rx.rx_serve_stream_status(s, qid)[2] == 1
     finally:
         rx.rx_serve_destroy(s)
+
+
+def test_multicorrelator_stream_served_alone_and_in_the_mix():
+    """A 101-tap stream at 25 MHz (the signal-quality multicorrelator workload) through
+    the same request loop: bit-exact with the oracle when served alone and when its
+    blocks arrive as a Poisson process among 15 other such streams."""
+    target = synth.multicorrelator_receiver(0, n_blocks=20)
+    tiq = synth.generate_iq(target).numpy()
+    others = [synth.multicorrelator_receiver(k, n_blocks=6) for k in range(1, 16)]
+    oiq = [synth.generate_iq(o).numpy() for o in others]
+    results = []
+    for mix in (False, True):
+        s = rx.rx_serve_create(32, 16, 101, 25000, ring_blocks=1024, dump_slots=32,
+                               hbm_budget_bytes=1 << 30)
+        try:
+            streams = [_stream_dict(target, tiq, max_blocks=20)]
+            if mix:
+                streams += [_stream_dict(o, q) for o, q in zip(others, oiq)]
+            ids = rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=0.08,
+                                     seed=11)
+            _, pushed, done = rx.rx_serve_stream_status(s, ids[0])
+            assert pushed == done == 20
+            d = rx.rx_serve_read_dumps(s, ids[0], 16, 101, 32)
+            st = rx.rx_serve_read_state(s, ids[0], 16)
+            stats = rx.rx_serve_get_stats(s)
+        finally:
+            rx.rx_serve_destroy(s)
+        assert stats["device_timeouts"] == 0
+        assert stats["timed_pushes"] == stats["blocks_done"]
+        if mix:
+            assert stats["blocks_done"] > 200
+        results.append((d, st))
+    od, os_ = oracle_run(target, tiq)
+    for d, st in results:
+        assert np.array_equal(d, od)
+        assert_states_equal(st, os_)
+
+
+def test_latency_counts_from_the_scheduled_arrival():
+    """A block pushed 5 ms after its arrival counts 5 ms more latency (and a deadline
+    miss) than one pushed on time; the lag itself is in the statistics."""
+    r = synth.serving_stream(1, n_blocks=3)
+    iq = synth.generate_iq(r).numpy()
+    N = r.block_samples
+    s = rx.rx_serve_create(4, 16, 8, 25000, ring_blocks=16, dump_slots=8)
+    try:
+        sid, _ = _admit(s, r)
+        assert rx.rx_serve_push(s, sid, iq[:N]) == rx.RX_OK        # first tick: kernel load
+        rx.rx_serve_drain(s)
+        rx.rx_serve_reset_stats(s)
+        assert rx.rx_serve_push_at(s, sid, iq[N:2 * N], rx.rx_serve_clock_ns()) == rx.RX_OK
+        rx.rx_serve_drain(s)
+        on_time = rx.rx_serve_get_stats(s)
+        rx.rx_serve_reset_stats(s)
+        assert rx.rx_serve_push_at(s, sid, iq[2 * N:3 * N], rx.rx_serve_clock_ns() - 5_000_000) == rx.RX_OK
+        rx.rx_serve_drain(s)
+        late = rx.rx_serve_get_stats(s)
+    finally:
+        rx.rx_serve_destroy(s)
+    assert on_time["timed_pushes"] == 1 and on_time["deadline_misses"] == 0
+    assert late["timed_pushes"] == 1 and late["deadline_misses"] == 1
+    assert late["max_ms"] >= 5.0 and late["max_push_lag_ms"] >= 5.0
+    assert late["max_ms"] - late["max_push_lag_ms"] < 1.0
+
+
+def test_plain_replay_tracks_every_arrival():
+    """The plain per-receiver comparator under Poisson arrivals: every block that
+    arrives inside the window is tracked (one rx_correlate + rx_track_epoch each) and
+    timed from its arrival."""
+    recs = [synth.serving_stream(k, n_blocks=10) for k in range(8)]
+    streams = [_stream_dict(r, synth.generate_iq(r).numpy()) for r in recs]
+    out = rx.rx_plain_replay(streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=0.2, seed=3,
+                             producer_threads=4)
+    assert out["producer_threads"] == 4
+    # 8 streams x ~1 kHz x 0.2 s = ~1600 arrivals
+    assert 1100 < out["blocks_done"] < 2100
+    assert 0 < out["p50_ms"] <= out["p99_ms"] <= out["max_ms"]

@@ -5,9 +5,9 @@ carrier table's entry, turned by a quarter turn per receiver so that the large s
 lands on I or Q with either sign), so that channel's prompt adds about 127^2 per
 sample and its true integrate-and-dump sum passes 2^31 (at 25 MHz, 2^32) within one
 integration.  The library must still equal the oracle bit for bit: the plain form,
-every batched schedule and the allocation-free entry point, at sample rates that
-select the direct form (4.092 MHz), the 8-sample chip-segment form (8.184 MHz) and
-the 16-sample one (16.368 and 25 MHz)."""
+every batched schedule (the carrier-segment one included) and the allocation-free
+entry point, at sample rates that select the direct form (4.092 MHz), the 8-sample
+chip-segment form (8.184 MHz) and the 16-sample one (16.368 and 25 MHz)."""
 import numpy as np
 import pytest
 import torch
@@ -88,7 +88,8 @@ def test_plain_form_wraps_like_the_oracle(wrap_set):
 
 @pytest.mark.parametrize("tiles", [None, (1, 128, 0, rx.RX_SCHED_DYNAMIC), (2, 128, 0, rx.RX_SCHED_STATIC),
                                    (3, 256, 0, rx.RX_SCHED_PIPE), (2, 224, 0, rx.RX_SCHED_PIPE),
-                                   (0, 224, 3, rx.RX_SCHED_BALANCED)])
+                                   (0, 224, 3, rx.RX_SCHED_BALANCED), (3, 512, 0, rx.RX_SCHED_SEGMENT),
+                                   (2, 256, 0, rx.RX_SCHED_SEGMENT)])
 def test_batched_schedules_wrap_like_the_oracle(wrap_set, tiles):
     recs, sigs, expected = wrap_set
     offs, total = batch_layout(recs)
