@@ -72,6 +72,7 @@ def kernel_sources_sha256(schedule: str) -> str:
             h.update(f.read())
     return h.hexdigest()
 METRIC = "Msample*channel/s correlated"
+SCHEDULES = ["dynamic", "static", "pipelined", "balanced", "segment"]
 INT32_LANES_PER_SM_CLK = 128          # 4 SM sub-partitions x one 32-lane warp instruction per clock
 
 
@@ -329,30 +330,72 @@ def code_epoch_form(rx, receivers, buf, offs, dev, stream, n_rx=4, n_blocks=100)
             "launches": n_rx * n_blocks}
 
 
+def _probe_ok(st: dict) -> bool:
+    """A load is carried in real time when p99 latency (from each block's scheduled
+    arrival) stays under the 1 ms deadline, nothing is dropped and nothing is left
+    behind (blocks done within 3% of those offered)."""
+    return (st["p99_ms"] < 1.0 and st.get("dropped_blocks", 0) == 0
+            and st["blocks_done"] >= 0.97 * st["offered_blocks"])
+
+
+def _bracket(run, start: int, limit: int, steps: int = 2):
+    """Double the stream count from `start` until a probe fails (or `limit`), then bisect
+    the last interval `steps` times.  Returns (largest passing, smallest failing, probes)."""
+    probes, ok_n, bad_n, n = [], 0, None, start
+    while n <= limit:
+        st = run(n)
+        good = _probe_ok(st)
+        probes.append({"streams": n, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                       "dropped": st.get("dropped_blocks", 0), "done": st["blocks_done"],
+                       "offered": st["offered_blocks"], "ok": good})
+        if not good:
+            bad_n = n
+            break
+        ok_n, n = n, 2 * n
+    for _ in range(steps if bad_n else 0):
+        mid = (ok_n + bad_n) // 2
+        if mid in (ok_n, bad_n):
+            break
+        st = run(mid)
+        good = _probe_ok(st)
+        probes.append({"streams": mid, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                       "dropped": st.get("dropped_blocks", 0), "done": st["blocks_done"],
+                       "offered": st["offered_blocks"], "ok": good})
+        if good:
+            ok_n = mid
+        else:
+            bad_n = mid
+    return ok_n, bad_n, probes
+
+
 def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_blocks=100,
-                probe_counts=(1024, 2048, 4096, 8192), probe_s=1.0) -> dict:
+                probe_s=1.0, capacity_limit=32768, plain_limit=4096) -> dict:
     """The serving workload: n_streams streams at 8.184 MHz, 12 channels x 5 taps, 1 ms blocks
     arriving as Poisson processes (mean 1 kHz, rate jitter 10%), streams leaving and rejoining
     at random, served by continuous batching.  Streams replay `distinct` seeded recordings of
-    rec_blocks blocks in turn.  Then a capacity probe: the largest stream count whose p99
-    latency stays under 1 ms with nothing dropped and no backlog."""
+    rec_blocks blocks in turn.  Latency counts from each block's scheduled arrival.  Then the
+    real-time capacity of the served form and of the plain per-receiver form (one
+    rx_correlate + rx_track_epoch per arriving block, from the same number of producer
+    threads) under the same arrivals, each bracketed by doubling the stream count until a
+    probe misses the deadline at p99, drops or falls behind, then bisecting."""
     recs = [synth.serving_stream(k, n_blocks=rec_blocks) for k in range(distinct)]
     host = [synth.generate_iq(r, device=dev).cpu().numpy() for r in recs]
     arrays = [synth.channel_arrays(r) for r in recs]
     cores = os.cpu_count() or 4
     producers = max(2, min(12, cores - 4))
 
-    def streams(n):
+    def streams(n, churn=True):
         out = []
         for k in range(n):
             prn, w, phi, rate, taps = arrays[k % distinct]
             out.append(dict(desc=rx.receiver_desc(recs[k % distinct]), prn=prn, carrier_word=w,
                             code_phase_word=phi, code_rate_word=rate, tap_offsets=taps,
-                            recording=host[k % distinct], churn=True))
+                            recording=host[k % distinct], churn=churn))
         return out
 
     def run(n, dur, churn):
-        s = rx.rx_serve_create(n + 64, 16, 8, 8184, ring_blocks=32768, dump_slots=8,
+        ring = min(max(32768, 4 * n), 65536)
+        s = rx.rx_serve_create(n + 64, 16, 8, 8184, ring_blocks=ring, dump_slots=8,
                                hbm_budget_bytes=2 << 30, device=dev.index or 0)
         try:
             t0 = time.perf_counter()
@@ -366,25 +409,236 @@ def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_
         st["offered_blocks"] = n * 1000.0 * dur
         return st
 
+    def run_plain(n):
+        st = rx.rx_plain_replay(streams(n, churn=False), rate_hz=1000.0, rate_jitter=0.1, duration_s=probe_s,
+                                seed=463004, producer_threads=producers, device=dev.index or 0)
+        st["offered_blocks"] = n * 1000.0 * probe_s
+        return st
+
     base = run(n_streams, duration_s, churn=20.0)
-    cap = 0
-    probes = []
-    for n in probe_counts:
-        st = run(n, probe_s, churn=0.0)
-        ok = (st["p99_ms"] < 1.0 and st["dropped_blocks"] == 0
-              and st["blocks_done"] >= 0.97 * st["offered_blocks"])
-        probes.append({"streams": n, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                       "dropped": st["dropped_blocks"], "done": st["blocks_done"], "ok": ok})
-        if not ok:
-            break
-        cap = n
+    cap_ok, cap_bad, probes = _bracket(lambda n: run(n, probe_s, 0.0), 1024, capacity_limit)
+    pcap_ok, pcap_bad, pprobes = _bracket(run_plain, 8, plain_limit)
     return {"streams": n_streams, "channels": 12 * n_streams, "fs_hz": 8.184e6, "taps": 5,
             "duration_s": duration_s, "arrivals": "Poisson, mean 1 kHz per stream, rate jitter 10%",
+            "latency_from": "each block's scheduled arrival",
             "churn_per_s": 20.0, "producer_threads": producers,
             "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "max_ms": base["max_ms"],
             "deadline_misses": base["deadline_misses"], "blocks_done": base["blocks_done"],
             "dropped": base["dropped_blocks"], "mean_items_per_tick": base["mean_items_per_tick"],
-            "realtime_channels_p99_under_1ms": 12 * cap, "capacity_probes": probes}
+            "p99_push_lag_ms": base["p99_push_lag_ms"],
+            "realtime_channels_p99_under_1ms": 12 * cap_ok,
+            "capacity_bracket_streams": [cap_ok, cap_bad], "capacity_probes": probes,
+            "plain_form": {"form": "one rx_correlate + rx_track_epoch per arriving block, one handle per "
+                                   "stream, producer threads as above",
+                           "realtime_channels_p99_under_1ms": 12 * pcap_ok,
+                           "capacity_bracket_streams": [pcap_ok, pcap_bad], "capacity_probes": pprobes},
+            "served_over_plain_capacity": (cap_ok / pcap_ok) if pcap_ok else None}
+
+
+def serving_multicorrelator_leg(rx, synth, dev, n_streams=16, duration_s=2.0, rec_blocks=50) -> dict:
+    """The signal-quality multicorrelator served through the same request loop: 16 streams
+    at 25 MHz, 16 channels x 101 taps (+-2.5 chip at 0.05 chip), 1 ms blocks arriving as
+    Poisson processes (mean 1 kHz, rate jitter 10%)."""
+    recs = [synth.multicorrelator_receiver(k, n_blocks=rec_blocks) for k in range(n_streams)]
+    host = [synth.generate_iq(r, device=dev).cpu().numpy() for r in recs]
+    streams = []
+    for r, h in zip(recs, host):
+        prn, w, phi, rate, taps = synth.channel_arrays(r)
+        streams.append(dict(desc=rx.receiver_desc(r), prn=prn, carrier_word=w, code_phase_word=phi,
+                            code_rate_word=rate, tap_offsets=taps, recording=h))
+    cores = os.cpu_count() or 4
+    s = rx.rx_serve_create(n_streams + 4, 16, 101, 25000, ring_blocks=4096, dump_slots=8,
+                           hbm_budget_bytes=1 << 30, device=dev.index or 0)
+    try:
+        rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=0.2, seed=463005,
+                           producer_threads=max(2, min(8, cores - 4)))
+        rx.rx_serve_reset_stats(s)
+        rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=duration_s, seed=463006,
+                           producer_threads=max(2, min(8, cores - 4)))
+        st = rx.rx_serve_get_stats(s)
+    finally:
+        rx.rx_serve_destroy(s)
+    sc = st["blocks_done"] * 25000 * 16
+    return {"streams": n_streams, "channels": 16 * n_streams, "fs_hz": 25e6, "taps": 101,
+            "duration_s": duration_s, "arrivals": "Poisson, mean 1 kHz per stream, rate jitter 10%",
+            "latency_from": "each block's scheduled arrival",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "deadline_misses": st["deadline_misses"], "blocks_done": st["blocks_done"],
+            "dropped": st["dropped_blocks"], "mean_items_per_tick": st["mean_items_per_tick"],
+            "Msample_channel_per_s": sc / duration_s / 1e6}
+
+
+def config1_leg(rx, synth, dev, stream, cpu_leg: bool) -> dict:
+    """The plain method, small (one receiver, fs 4.092 MHz, 8 channels x E/P/L, 100 ms):
+    one rx_correlate + one rx_track_epoch per 1 ms epoch.  Latency per epoch (submit to
+    result, one epoch at a time), throughput with the epochs queued back to back, the
+    paper's real-time channel count (1 ms / time per channel-epoch, Sec. 4 Table 5), the
+    end-to-end rate from host memory (each epoch's block copied in and its accumulators
+    read back), and the oracle over the whole receiver on one host core."""
+    import torch
+    r = synth.single_receiver(n_blocks=100)
+    N, n_ch, T = r.block_samples, len(r.channels), r.n_taps
+    iq = synth.generate_iq(r, device=dev)
+    h = rx.rx_create(r.fs, N, n_ch, T, r.pll_bn, r.dll_bn, r.tap_early, r.tap_prompt, r.tap_late,
+                     device=dev.index or 0, stream=stream)
+    try:
+        def restart():
+            rx.rx_set_channels(h, *synth.channel_arrays(r))
+        restart()
+        for b in range(10):                                   # warm-up
+            rx.rx_correlate(h, iq[b * N:(b + 1) * N], N)
+            rx.rx_track_epoch(h)
+        restart()
+        stream.synchronize()
+        lat = []
+        for b in range(r.n_blocks):                           # one epoch at a time
+            t0 = time.perf_counter()
+            rx.rx_correlate(h, iq[b * N:(b + 1) * N], N)
+            rx.rx_track_epoch(h)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t0)
+        restart()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for b in range(r.n_blocks):                           # epochs queued back to back
+            rx.rx_correlate(h, iq[b * N:(b + 1) * N], N)
+            rx.rx_track_epoch(h)
+        stream.synchronize()
+        dt_q = time.perf_counter() - t0
+        host = torch.empty((r.n_samples, 2), dtype=torch.int8, pin_memory=True)
+        host.copy_(iq)
+        restart()
+        t0 = time.perf_counter()
+        for b in range(r.n_blocks):                           # from host memory, results read back
+            rx.rx_correlate(h, host[b * N:(b + 1) * N], N)
+            rx.rx_read_accumulators(h, n_ch, T)
+            rx.rx_track_epoch(h)
+        stream.synchronize()
+        dt_e = time.perf_counter() - t0
+    finally:
+        rx.rx_destroy(h)
+    sc = N * n_ch * r.n_blocks
+    lat_ms = 1000 * statistics.median(lat)
+    per_ch_epoch_ms = lat_ms / n_ch
+    out = {
+        "metric": METRIC, "value": sc / dt_q / 1e6, "unit": "Msample*channel/s",
+        "ms_per_step": 1000 * dt_q, "dtype": "int32",
+        "config": {"workload": "1 receiver, fs 4.092 MHz, 8 channels x E/P/L (0.5 chip), 100 ms, "
+                               "PLL 15 Hz / DLL 1 Hz every 1 ms; plain form (rx_correlate + rx_track_epoch)"},
+        "epoch_latency_ms": {"p50": lat_ms, "p99": 1000 * float(np.percentile(lat, 99)),
+                             "max": 1000 * max(lat)},
+        "time_per_channel_epoch_ns": per_ch_epoch_ms * 1e6,
+        "realtime_channels_paper_definition": 1.0 / per_ch_epoch_ms,
+        "launches_per_epoch": 2,
+        "e2e": {"value": sc / dt_e / 1e6, "unit": "Msample*channel/s", "ms_per_step": 1000 * dt_e,
+                "h2d_bytes_per_step": 2 * r.n_samples, "d2h_bytes_per_step": r.n_blocks * n_ch * T * 8},
+    }
+    if cpu_leg:
+        import oracle
+        prn, w, phi, rate, taps = synth.channel_arrays(r)
+        chans = [oracle.chan_init(int(w[c]), int(phi[c]), int(rate[c]), r.fs) for c in range(n_ch)]
+        host_iq = iq.cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.run_receiver(host_iq, r.n_blocks, N, r.fs, prn, taps, 1, r.tap_early, r.tap_prompt,
+                            r.tap_late, r.pll_bn, r.dll_bn, chans)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sc / dt / 1e6, "unit": "Msample*channel/s", "cores": 1,
+                               "kind": "oracle", "sample": f"the whole workload (100 ms), one thread, {dt:.2f} s"}
+    return out
+
+
+def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stream, steps: int, warmup: int,
+                       peak_tops: float, cpu_leg: bool, cpu_receivers: int, workload: str) -> dict:
+    """One batched workload through the same path as the headline: seeded receivers
+    generated on the device, autotuned tiles, one persistent launch per step (graph
+    replay), the direct-model roofline, the end-to-end rate with host buffers, and the
+    oracle on a bounded sample of the receivers."""
+    import torch
+    offs, total = layout(receivers)
+    buf = torch.zeros(total, dtype=torch.int8, device=dev)
+    for r, o in zip(receivers, offs):
+        iq = synth.generate_iq(r, device=dev)
+        buf[int(o):int(o) + iq.numel()] = iq.view(-1)
+    torch.cuda.synchronize()
+    b = rx.rx_batch_create([rx.receiver_desc(r) for r in receivers], n_blocks, device=dev.index or 0,
+                           stream=stream)
+    try:
+        for i, r in enumerate(receivers):
+            rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+        tiles, probe_ms = rx.rx_batch_autotune(b, buf, offs, min(64, n_blocks))
+        for _ in range(warmup):
+            rx.rx_batch_run(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
+        rx.rx_batch_sync(b)
+        times = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rx.rx_batch_run(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches = rx.rx_batch_last_launches(b)
+        got = rx.rx_batch_get_tiles(b)
+        # end to end: host input (chunked copies under tracking) and every dump read back
+        hbuf = torch.empty(total, dtype=torch.int8, pin_memory=True)
+        hbuf.copy_(buf)
+        shapes = [(len(r.channels), r.n_taps, n_blocks // r.integ_blocks) for r in receivers]
+        hdump = torch.empty(sum(c * t * m * 2 for c, t, m in shapes), dtype=torch.int32, pin_memory=True)
+        rx.rx_batch_run(b, hbuf, offs, n_blocks, rx.RX_RUN_RESTART)
+        rx.rx_batch_sync(b)
+        t0 = time.perf_counter()
+        rx.rx_batch_run(b, hbuf, offs, n_blocks, rx.RX_RUN_RESTART)
+        dumps = rx.rx_batch_read_all_dumps(b, shapes, out=hdump.numpy())
+        e2e_s = time.perf_counter() - t0
+        d2h = sum(d.nbytes for d in dumps)
+        del hbuf, hdump, dumps
+    finally:
+        rx.rx_batch_destroy(b)
+    ms = statistics.mean(times)
+    sc = sum(r.block_samples * len(r.channels) * n_blocks for r in receivers)
+    ops = sum(r.block_samples * len(r.channels) * n_blocks * ops_per_sample_channel(r.n_taps) for r in receivers)
+    achieved = ops / (ms / 1000) / 1e12
+    in_bytes = sum(2 * r.block_samples * n_blocks for r in receivers)
+    out = {
+        "metric": METRIC, "value": sc / (ms / 1000) / 1e6, "unit": "Msample*channel/s", "ms_per_step": ms,
+        "steps": steps, "warmup": warmup, "dtype": "int32",
+        "config": {"workload": workload, "receivers": len(receivers), "blocks": n_blocks,
+                   "channels": sum(len(r.channels) for r in receivers),
+                   "tiles": {"channels_per_item": got[0], "threads": got[1], "ctas_per_sm": got[2],
+                             "schedule": SCHEDULES[got[3]]},
+                   "autotune_best_probe_ms": probe_ms,
+                   "l2": "inputs larger than L2; no flush" if in_bytes > 129e6 else "inputs fit in L2"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "model": "direct form, 8 + 3T INT32 ops per sample*channel with each receiver's T; "
+                              "peak = the measured INT32 issue rate",
+                     "hbm_gbs": in_bytes / (ms / 1000) / 1e9},
+        "e2e": {"value": sc / e2e_s / 1e6, "unit": "Msample*channel/s", "ms_per_step": e2e_s * 1000,
+                "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches * steps,
+    }
+    if cpu_leg:
+        sub = receivers[:cpu_receivers]
+
+        def get_iq(i, blocks):
+            rr = sub[i]
+            o = int(offs[i])
+            return buf[o:o + 2 * blocks * rr.block_samples].cpu().numpy()
+        cores = os.cpu_count() or 1
+        iq1 = [get_iq(0, 1)]
+        t1 = oracle_sample(sub[:1], iq1, 1, 1)
+        # about 10 s of oracle work, one thread per receiver on the host's cores
+        blocks = int(max(1, min(n_blocks, 10.0 * min(len(sub), cores) / len(sub) / max(t1, 1e-6))))
+        iqs = [get_iq(i, blocks) for i in range(len(sub))]
+        dt = oracle_sample(sub, iqs, blocks, min(len(sub), cores))
+        scs = sum(rr.block_samples * len(rr.channels) * blocks for rr in sub)
+        out["cpu_baseline"] = {"value": scs / dt / 1e6, "unit": "Msample*channel/s",
+                               "cores": min(len(sub), cores), "kind": "oracle",
+                               "sample": f"{len(sub)} receivers x {blocks} blocks, one oracle thread per "
+                                         f"receiver, {dt:.1f} s"}
+    del buf
+    torch.cuda.empty_cache()
+    return out
 
 
 def table3_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, steps, warmup) -> dict:
@@ -652,7 +906,9 @@ def run_ours(args):
     # roofline of the persistent kernel (all of a step's device time)
     props = torch.cuda.get_device_properties(dev)
     sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak_tops = props.multi_processor_count * INT32_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    derived_tops = props.multi_processor_count * INT32_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+    measured_tops, peak_probe_ms = rx.rx_measure_int32_peak(local)
+    peak_tops = measured_tops
     launch_ms = statistics.mean(per_launch)
     alg_ops = sc * ops_per_sample_channel(5)
     achieved = alg_ops / (launch_ms / 1000) / 1e12
@@ -719,6 +975,26 @@ def run_ours(args):
         table3 = table3_leg(rx, synth, receivers, buf, offs, n_blocks, local, stream, max(3, args.steps // 2),
                             args.warmup)
 
+    single = uneven = multicorr = serving5 = None
+    if rank == 0 and world == 1:
+        cpu_on = not args.no_cpu_baseline
+        if not args.no_config1:
+            single = config1_leg(rx, synth, dev, stream, cpu_on)
+        if not args.no_config3:
+            uneven = batched_config_leg(
+                rx, synth, "uneven", [synth.uneven_receiver(i, n_blocks=1000) for i in range(128)], 1000,
+                dev, stream, 3, args.warmup, peak_tops, cpu_on, 16,
+                "128 receivers, fs in {2.046, 4.092, 8.184, 16.368, 25} MHz, 4-32 channels x 3-7 taps at "
+                "0.1-0.5 chip, integration 1-20 ms, C/N0 25-50 dB-Hz, Doppler +-5 kHz at 0-50 Hz/s, 1 s")
+        if not args.no_config5:
+            multicorr = batched_config_leg(
+                rx, synth, "multicorrelator", [synth.multicorrelator_receiver(i, n_blocks=2000) for i in range(16)],
+                2000, dev, stream, 3, args.warmup, peak_tops, cpu_on, 16,
+                "16 receivers x 16 channels x 101 taps (+-2.5 chip at 0.05 chip), fs 25 MHz, 2 s, "
+                "second path per PRN (0.1-1 chip, -3..-10 dB, +0-20 Hz)")
+        if not args.no_serve:
+            serving5 = serving_multicorrelator_leg(rx, synth, dev)
+
     acquisition = None
     if not args.no_acq:
         acquisition = acquisition_leg(rx, synth, receivers[:args.acq_receivers], buf, offs, dev,
@@ -726,7 +1002,7 @@ def run_ours(args):
                                       cpu_leg=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     rt_channels = value * 1e6 / FS                # channels sustainable at 16.368 MHz in real time
-    sched_name = ["dynamic", "static", "pipelined", "balanced", "segment"][tiles[3]]
+    sched_name = SCHEDULES[tiles[3]]
     prof = PROFILED.get((sched_name, tiles[1], tiles[0]))
     if prof and prof["src_sha256"] != kernel_sources_sha256(sched_name):
         prof = None                      # the kernel changed since its counters were taken
@@ -755,8 +1031,14 @@ def run_ours(args):
                    "parallelism": f"receivers sharded over {world} GPU(s), no collective"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved / peak_tops, "traffic": traffic,
-                     "model": "INT32 ops = sample*channel x (8 + 3T), T = 5; peak = SMs x 128 "
-                              "lanes x max SM clock (derived, not measured)",
+                     "model": "INT32 ops = sample*channel x (8 + 3T), T = 5 (the direct form's "
+                              "operations; the carrier-segment form executes fewer, so its rate "
+                              "against this model is an effective rate); peak = the INT32 issue "
+                              "rate measured in this run (rx_measure_int32_peak: IMAD/LOP3/IADD3 "
+                              "chains on every SM)",
+                     "peak_measured": measured_tops, "peak_probe_ms": peak_probe_ms,
+                     "peak_derived": derived_tops,
+                     "frac_of_derived_peak": achieved / derived_tops,
                      "executed": executed,
                      "smem_lookup_bound_Msample_channel_s": peak_tops * 1e6 / 4,
                      "launch_ms": launch_ms,
@@ -775,6 +1057,10 @@ def run_ours(args):
         "batched_table3": table3,
         "batched_code_epochs": code_batch,
         "acquisition": acquisition,
+        "config1_plain_small": single,
+        "config3_batched_uneven": uneven,
+        "config5_multicorrelator": multicorr,
+        "config5_served": serving5,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -803,6 +1089,9 @@ def main():
     p.add_argument("--no-acq", action="store_true")
     p.add_argument("--no-table3", action="store_true")
     p.add_argument("--no-code", action="store_true")
+    p.add_argument("--no-config1", action="store_true")
+    p.add_argument("--no-config3", action="store_true")
+    p.add_argument("--no-config5", action="store_true")
     p.add_argument("--acq-receivers", type=int, default=N_RX,
                    help="receivers searched by the acquisition leg (default: all of the workload)")
     args = p.parse_args()

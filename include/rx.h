@@ -417,12 +417,13 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
                                 each with an equal share of the whole job: channels
                                 cut between CTAs exchange partial sums each block;
                                 enqueued directly, not through a graph */
-#define RX_SCHED_SEGMENT 4u  /* as PIPE, with the carrier-segment correlator: per block
-                                the CTA builds prefix sums of the raw samples once for
-                                all its channels; each channel's tap sums are then
-                                evaluated only at the carrier-table and code-value
-                                changes (one filter warp per channel, at most 8
-                                channels per item, 256 or 512 threads) */
+#define RX_SCHED_SEGMENT 4u  /* one CTA per channel group for the whole run, with the
+                                carrier-segment correlator: per block the CTA builds
+                                prefix sums of the raw samples once for all its
+                                channels; each channel's tap sums are then evaluated
+                                only where the carrier-table entry or the code value
+                                changes.  One team of 128 threads per channel
+                                (threads: 128 or 0), at most 6 channels per item */
 
 /* Work decomposition of the persistent kernel.  channels_per_item: channels
  * correlated together by one CTA (0 = choose; for RX_SCHED_BALANCED the
@@ -434,7 +435,7 @@ rx_status rx_batch_read_state(rx_batch b, uint32_t rx, rx_channel_state *out,
  * ctas_per_sm: resident CTAs per SM for the dynamic and balanced schedules
  * (0 = as many as fit; at most 8 for RX_SCHED_BALANCED); schedule:
  * RX_SCHED_DYNAMIC, RX_SCHED_STATIC, RX_SCHED_PIPE, RX_SCHED_BALANCED or
- * RX_SCHED_SEGMENT (256 or 512 threads, 0 = 512; at most 8 channels per item).
+ * RX_SCHED_SEGMENT (128 threads per channel; at most 6 channels per item).
  * All schedules give identical results.
  * Takes effect at the next run (the graph is re-recorded).  A wait inside a
  * CTA of RX_SCHED_PIPE or RX_SCHED_SEGMENT that exceeds the handle's time limit ends the run with

@@ -256,6 +256,7 @@ struct rx_batch_s {
     uint64_t timeout_ns = 2000000000ull;
     uint32_t stall = 0;
     uint32_t pipe_stage = 0;        // staging buffer bytes of the pipelined schedule (0: none)
+    uint32_t cs_nbuf = 2;           // prefix buffers of the segment schedule
     // balanced schedule: per-CTA segments and the exchange of cut channels
     SegDesc *d_segs = nullptr;
     uint32_t *d_nseg = nullptr;
@@ -594,10 +595,10 @@ rx_status build_balanced(rx_batch b) {
 }
 
 rx_status build_groups(rx_batch b) {
-    if (b->cpg == 0 && b->schedule == RX_SCHED_SEGMENT) b->cpg = 4;
+    if (b->cpg == 0 && b->schedule == RX_SCHED_SEGMENT) b->cpg = 6;
     if (b->cpg == 0 && b->schedule != RX_SCHED_BALANCED) b->cpg = default_cpg(b);
-    if (b->threads == 0) b->threads = b->schedule == RX_SCHED_BALANCED ? 224 : b->schedule == RX_SCHED_SEGMENT ? 512 : 256;
-    if (b->schedule == RX_SCHED_SEGMENT && b->cpg > 8) b->cpg = 8;
+    if (b->threads == 0) b->threads = b->schedule == RX_SCHED_BALANCED ? 224 : b->schedule == RX_SCHED_SEGMENT ? 128 : 256;
+    if (b->schedule == RX_SCHED_SEGMENT && b->cpg > cs_max_channels()) b->cpg = cs_max_channels();
     if (b->schedule == RX_SCHED_BALANCED) {
         rx_status s = build_balanced(b);
         if (s == RX_OK) {
@@ -637,12 +638,13 @@ rx_status build_groups(rx_batch b) {
         occ = b->threads == 128 ? occupancy_static<128>(ss)
                                 : b->threads == 512 ? occupancy_static<512>(ss) : occupancy_static<256>(ss);
     } else if (b->schedule == RX_SCHED_SEGMENT) {
+        // two prefix buffers where they fit, else one
         uint32_t max_n = 0;
         for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
-        const size_t cs = cs_smem_bytes(b->cpg, b->max_taps, b->threads, max_n);
-        occ = (int)cs <= b->tables->max_smem_optin
-                  ? cs_occupancy(b->threads, cs_filter_warps(b->cpg), cs, any_table3(b))
-                  : 0;
+        b->cs_nbuf = 2;
+        if (cs_smem_bytes(b->cpg, b->max_taps, max_n, 2) > (size_t)b->tables->max_smem_optin) b->cs_nbuf = 1;
+        const size_t cs = cs_smem_bytes(b->cpg, b->max_taps, max_n, b->cs_nbuf);
+        occ = cs <= (size_t)b->tables->max_smem_optin ? cs_occupancy(b->cpg, cs, any_table3(b)) : 0;
     } else if (b->schedule == RX_SCHED_PIPE) {
         // Stage blocks in shared memory when that still lets every group be resident
         // at once (or at least keeps as many resident as reading from global would).
@@ -715,10 +717,10 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     if (b->schedule == RX_SCHED_SEGMENT) {
         uint32_t max_n = 0;
         for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
-        CsArgs ca{b->d_groups, rxoff,       iq,    ba.tb,   ba.err,  b->timeout_ns,
-                  n_blocks,    b->cpg,      b->max_taps, max_n, b->stall, any_table3(b) ? 1u : 0u};
-        cudaError_t ce = cs_launch(b->threads, cs_filter_warps(b->cpg), b->G,
-                                   cs_smem_bytes(b->cpg, b->max_taps, b->threads, max_n), b->stream, ca);
+        CsArgs ca{b->d_groups, rxoff,   iq,          ba.tb, ba.err,   b->timeout_ns,
+                  n_blocks,    b->max_taps, max_n, b->cs_nbuf, b->stall, any_table3(b) ? 1u : 0u};
+        cudaError_t ce = cs_launch(b->cpg, b->G, cs_smem_bytes(b->cpg, b->max_taps, max_n, b->cs_nbuf),
+                                   b->stream, ca);
         if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(ce)));
         RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
         return RX_OK;
@@ -964,9 +966,11 @@ extern "C" rx_status rx_batch_set_tiles(rx_batch b, uint32_t cpg, uint32_t threa
         schedule != RX_SCHED_BALANCED && schedule != RX_SCHED_SEGMENT)
         return berr(b, RX_EINVAL, "unknown schedule");
     if (schedule == RX_SCHED_SEGMENT) {
-        if (threads != 0 && threads != 256 && threads != 512)
-            return berr(b, RX_EINVAL, "the segment schedule takes 256 or 512 threads");
-        if (cpg > 8) return berr(b, RX_EINVAL, "the segment schedule takes at most 8 channels per item");
+        if (threads != 0 && threads != 128)
+            return berr(b, RX_EINVAL, "the segment schedule takes 128 threads per channel");
+        if (cpg > cs_max_channels())
+            return berr(b, RX_EINVAL, rxh::fmt("the segment schedule takes at most %u channels per item",
+                                               cs_max_channels()));
     } else if (threads != 0 && threads != 128 && threads != 256 && threads != 512 &&
         !(threads == 224 && (schedule == RX_SCHED_PIPE || schedule == RX_SCHED_BALANCED)) &&
         !(threads == 192 && schedule == RX_SCHED_BALANCED))
@@ -1333,11 +1337,10 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
             if (per_sm > bal_default_per_sm(nt) + 2) continue;
             cands.push_back({0u, nt, per_sm, RX_SCHED_BALANCED});
         }
-    for (uint32_t cpg : {2u, 3u, 4u, 6u, 8u})
-        for (uint32_t nt : {512u, 256u}) {
-            if (cpg > max_ch && cpg != 2u) continue;
-            cands.push_back({std::min(cpg, max_ch), nt, 0u, RX_SCHED_SEGMENT});
-        }
+    for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u}) {
+        if (cpg > max_ch) continue;
+        cands.push_back({cpg, 128u, 0u, RX_SCHED_SEGMENT});
+    }
     for (uint32_t sched : {RX_SCHED_PIPE, RX_SCHED_STATIC, RX_SCHED_DYNAMIC})
         for (uint32_t cpg : {1u, 2u, 3u, 4u, 6u, 8u, 12u, 16u}) {
             if (cpg > max_ch) continue;

@@ -41,11 +41,18 @@
 // code word that would leave the extended chip axis) is correlated by the direct form
 // instead, with the same result.
 //
-// The warp organisation is the pipelined schedule's (rx_pipe.cu): NT correlation
-// threads take the group's channels one after the other, and one filter warp per
-// channel folds the block into its integrate-and-dump sums and closes its loops
-// (Table 3) while the correlation threads move on; two shared-memory mbarriers per
-// channel carry the hand-off, and every wait is bounded and reports a time-out.
+// Work organisation.  A CTA owns a group of channels of one receiver for the whole run,
+// and each channel has its own team of GT threads with its own named barrier: the
+// team correlates its channel over a block, folds the block into the channel's
+// integrate-and-dump sums and closes the loops (Table 3, the PLL and DLL parts on two
+// warps at once), then goes on to the next block.  Teams do not wait for one another
+// except through the shared prefix sums: every team computes a share of the next
+// block's prefix sums after it has correlated the current block, into the other of
+// two buffers, and arrives on that buffer's mbarrier; a team starts a block once the
+// block's buffer is complete (which also means every team is done with the buffer's
+// previous block).  Where two buffers do not fit in shared memory (large blocks),
+// one buffer is used and a second mbarrier tells when every team is done reading it.
+// Every wait is bounded and reports a time-out.
 #include <cuda_runtime.h>
 
 #include "rx_internal.h"
@@ -60,9 +67,10 @@ using rxh::CS_CBASE;
 using rxh::CS_CLEN;
 using rxh::CS_LMAX;
 
-constexpr uint32_t CS_SEG_MAX = 1024;   // segments per channel-block
+constexpr uint32_t CS_SEG_MAX = 512;    // segments per channel-block
 constexpr uint32_t CS_NMAX = 65536;     // samples per block
-constexpr uint32_t CS_MAX_FILTER = 8;   // filter warps per CTA
+constexpr int CS_GT = 128;              // threads per channel team
+constexpr uint32_t CS_MAX_TEAMS = 6;    // channels per CTA
 
 struct CsTap {          // one tap's constants for one channel-block
     uint32_t c0p;       // chip of sample 0 + CS_CBASE
@@ -95,9 +103,23 @@ __device__ __forceinline__ uint32_t dp2a_hi_us(uint32_t a, uint32_t b, uint32_t 
     return d;
 }
 
-template <int NT>
-__device__ __forceinline__ void corr_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+// Named barrier `id` over the GT threads of one team.
+__device__ __forceinline__ void team_sync(uint32_t id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(CS_GT) : "memory");
+}
+
+// As team_sync; returns true when every thread of the team passes ok.
+__device__ __forceinline__ bool team_and(uint32_t id, bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(id), "n"(CS_GT)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ CsChan cs_chan(uint32_t theta, uint32_t w, uint32_t r) {
@@ -167,15 +189,16 @@ __device__ __forceinline__ void cs_load16(const int8_t *blk, uint32_t n0, uint32
     }
 }
 
-// The biased local prefix W of one block (see the file comment), by the NT correlation
-// threads: thread q takes samples 16 q .. 16 q + 15; the 16 threads of a 256-group
+// One warp's share of the biased local prefix W of a block (see the file comment): the
+// warp with index wq among nw warps takes the 32-chunk runs wq, wq + nw, ... (chunk q
+// = samples 16 q .. 16 q + 15, its lane q mod 32); the 16 lanes of a 256-sample group
 // scan their totals with shuffles.  Wp holds at least N rounded up to 16 words.
-template <int NT>
-__device__ __forceinline__ void cs_prefix(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t *Wp) {
+__device__ __forceinline__ void cs_prefix_share(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t *Wp,
+                                                uint32_t wq, uint32_t nw) {
     const uint32_t nq = (N + 15) >> 4;
     const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t q0 = 0; q0 < nq; q0 += NT) {
-        const uint32_t q = q0 + threadIdx.x;
+    for (uint32_t q0 = 32u * wq; q0 < nq; q0 += 32u * nw) {
+        const uint32_t q = q0 + lane;
         uint32_t x[8];
         cs_load16(blk, q * 16, N, a16, a4, x);
         uint32_t s[16];
@@ -208,16 +231,15 @@ __device__ __forceinline__ void cs_prefix(const int8_t *blk, uint32_t N, bool a1
 // start the empty sum is 0x80008000.
 __device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { return Wp[n] - 0x00800080u * (n + 1u); }
 
-// Segment table, first part.  Thread t walks samples [p0, p1) of its span, cut at carrier
-// crossings and group starts, sums the rotated samples (DI, DQ) and writes, for each
-// segment that starts in its span, K relative to the span's start.  Returns the range of
-// segment indices written (any = false if none).
-template <int NT>
-__device__ __forceinline__ void cs_seg_local(const uint32_t *Wp, uint32_t N, const CsChan &c, const uint32_t *tab,
-                                             uint4 *seg, uint32_t &DI, uint32_t &DQ, uint32_t &sfirst,
-                                             uint32_t &slast, bool &any) {
-    const uint32_t span = 32u * ((N + 32u * NT - 1u) / (32u * NT));
-    const uint32_t p0 = threadIdx.x * span, p1 = min(p0 + span, N);
+// Segment table, first part.  Team thread t walks samples [p0, p1) of its span, cut at
+// carrier crossings and group starts, sums the rotated samples (DI, DQ) and writes, for
+// each segment that starts in its span, K relative to the span's start.  Returns the
+// range of segment indices written (any = false if none).
+__device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uint32_t N, const CsChan &c,
+                                             const uint32_t *tab, uint4 *seg, uint32_t &DI, uint32_t &DQ,
+                                             uint32_t &sfirst, uint32_t &slast, bool &any) {
+    const uint32_t span = 32u * ((N + 32u * CS_GT - 1u) / (32u * CS_GT));
+    const uint32_t p0 = t * span, p1 = min(p0 + span, N);
     DI = 0u;
     DQ = 0u;
     sfirst = slast = 0u;
@@ -259,13 +281,11 @@ __device__ __forceinline__ void cs_seg_local(const uint32_t *Wp, uint32_t N, con
     }
 }
 
-// Segment table, second part: exclusive scan of the spans' totals over the NT threads
-// (M at each span's start), added to the entries the thread wrote.  Contains a barrier
-// of the correlation threads.
-template <int NT>
-__device__ __forceinline__ void cs_seg_scan(uint32_t DI, uint32_t DQ, uint2 *s_warp, uint4 *seg, uint32_t sfirst,
-                                            uint32_t slast, bool any) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Segment table, second part: exclusive scan of the spans' totals over the team (M at
+// each span's start), added to the entries the thread wrote.  Contains a team barrier.
+__device__ __forceinline__ void cs_seg_scan(uint32_t t, uint32_t bar, uint32_t DI, uint32_t DQ, uint2 *s_warp,
+                                            uint4 *seg, uint32_t sfirst, uint32_t slast, bool any) {
+    const uint32_t lane = t & 31, warp = t >> 5;
     uint32_t iI = DI, iQ = DQ;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -277,12 +297,15 @@ __device__ __forceinline__ void cs_seg_scan(uint32_t DI, uint32_t DQ, uint2 *s_w
         }
     }
     if (lane == 31) s_warp[warp] = make_uint2(iI, iQ);
-    corr_sync<NT>();
+    team_sync(bar);
     uint32_t bI = iI - DI, bQ = iQ - DQ;
-    for (uint32_t v = 0; v < warp; ++v) {
-        const uint2 t = s_warp[v];
-        bI += t.x;
-        bQ += t.y;
+#pragma unroll
+    for (uint32_t v = 0; v < CS_GT / 32; ++v) {
+        if (v < warp) {
+            const uint2 x = s_warp[v];
+            bI += x.x;
+            bQ += x.y;
+        }
     }
     if (any)
         for (uint32_t s = sfirst; s <= slast; ++s) {
@@ -320,39 +343,47 @@ __device__ __forceinline__ void cs_total(const uint32_t *Wp, const uint4 *seg, c
     mQ = dp2a_hi_us(V, e.z, e.y);
 }
 
-// The transitions of TT taps, spread over the NT threads (thread t takes the items whose
-// running index over all taps is t mod NT), reduced per warp into red[TT][2].
-template <int NT, int TT>
-__device__ __forceinline__ void cs_items(const CsTap *tp, uint32_t &run, const uint16_t *list, const uint32_t *Wp,
-                                         const uint4 *seg, const CsChan &c, int32_t *red) {
+// +-M(b) at one code transition (list entry e) of a tap.
+__device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsChan &c, const uint32_t *Wp,
+                                        const uint4 *seg, uint32_t &SI, uint32_t &SQ) {
+    const uint32_t j = (e & 0x7fffu) - tp.c0p;                 // chips after the first
+    const float bf = fmaf((float)j, c.Dr, -tp.F);
+    uint32_t b = bf > 0.0f ? (uint32_t)ceilf(bf) : 0u;          // ceil((j 2^32 - frac) / r) or one less
+    if ((uint64_t)b * c.r < (((uint64_t)j << 32) - tp.frac)) ++b;
+    const uint32_t n = b - 1u;
+    const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
+    const uint32_t V = Wp[n] - 0x00800080u * b;
+    uint32_t mI = dp2a_lo_us(V, en.z, en.x), mQ = dp2a_hi_us(V, en.z, en.y);
+    if (e & 0x8000u) {
+        mI = 0u - mI;
+        mQ = 0u - mQ;
+    }
+    SI += mI;
+    SQ += mQ;
+}
+
+// The transitions of TT taps, spread over the team (thread t takes the items whose
+// running index over all taps is t mod GT), reduced per warp into red[TT][2].
+template <int TT>
+__device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &run, const uint16_t *list,
+                                         const uint32_t *Wp, const uint4 *seg, const CsChan &c, int32_t *red) {
     uint32_t SI[TT], SQ[TT];
 #pragma unroll
     for (int k = 0; k < TT; ++k) SI[k] = SQ[k] = 0u;
 #pragma unroll
     for (int k = 0; k < TT; ++k) {
-        const CsTap t = tp[k];
-        uint32_t i = (threadIdx.x - run) & (uint32_t)(NT - 1);
-        run += t.cnt;
-        const uint16_t *L = list + t.u0;
-        for (; i < t.cnt; i += NT) {
-            const uint32_t e = L[i];
-            const uint32_t j = (e & 0x7fffu) - t.c0p;               // chips after the first
-            const float bf = fmaf((float)j, c.Dr, -t.F);
-            uint32_t b = bf > 0.0f ? (uint32_t)ceilf(bf) : 0u;     // ceil((j 2^32 - frac) / r) or one less
-            if ((uint64_t)b * c.r < (((uint64_t)j << 32) - t.frac)) ++b;
-            const uint32_t n = b - 1u;
-            const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
-            const uint32_t V = Wp[n] - 0x00800080u * b;
-            uint32_t mI = dp2a_lo_us(V, en.z, en.x), mQ = dp2a_hi_us(V, en.z, en.y);
-            if (e & 0x8000u) {
-                mI = 0u - mI;
-                mQ = 0u - mQ;
-            }
-            SI[k] += mI;
-            SQ[k] += mQ;
+        const CsTap tk = tp[k];
+        uint32_t i = (t - run) & (uint32_t)(CS_GT - 1);
+        run += tk.cnt;
+        const uint16_t *L = list + tk.u0;
+        for (; i + CS_GT < tk.cnt; i += 2 * CS_GT) {           // two independent items per pass
+            const uint32_t e0 = L[i], e1 = L[i + CS_GT];
+            cs_item(e0, tk, c, Wp, seg, SI[k], SQ[k]);
+            cs_item(e1, tk, c, Wp, seg, SI[k], SQ[k]);
         }
+        if (i < tk.cnt) cs_item(L[i], tk, c, Wp, seg, SI[k], SQ[k]);
     }
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lane = t & 31;
 #pragma unroll
     for (int k = 0; k < TT; ++k) {
         const uint32_t vi = __reduce_add_sync(0xffffffffu, SI[k]);
@@ -364,332 +395,338 @@ __device__ __forceinline__ void cs_items(const CsTap *tp, uint32_t &run, const u
     }
 }
 
-template <int NT>
-__device__ __forceinline__ void cs_items_all(const CsTap *tp, uint32_t nt, const uint16_t *list, const uint32_t *Wp,
-                                             const uint4 *seg, const CsChan &c, int32_t *red) {
+__device__ __forceinline__ void cs_items_all(uint32_t t, const CsTap *tp, uint32_t nt, const uint16_t *list,
+                                             const uint32_t *Wp, const uint4 *seg, const CsChan &c, int32_t *red) {
     uint32_t run = 0;
     for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
         const CsTap *p = tp + t0;
         int32_t *rd = red + 2 * t0;
         switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-            case 1: cs_items<NT, 1>(p, run, list, Wp, seg, c, rd); break;
-            case 2: cs_items<NT, 2>(p, run, list, Wp, seg, c, rd); break;
-            case 3: cs_items<NT, 3>(p, run, list, Wp, seg, c, rd); break;
-            case 4: cs_items<NT, 4>(p, run, list, Wp, seg, c, rd); break;
-            case 5: cs_items<NT, 5>(p, run, list, Wp, seg, c, rd); break;
-            case 6: cs_items<NT, 6>(p, run, list, Wp, seg, c, rd); break;
-            case 7: cs_items<NT, 7>(p, run, list, Wp, seg, c, rd); break;
-            default: cs_items<NT, 8>(p, run, list, Wp, seg, c, rd); break;
+            case 1: cs_items<1>(t, p, run, list, Wp, seg, c, rd); break;
+            case 2: cs_items<2>(t, p, run, list, Wp, seg, c, rd); break;
+            case 3: cs_items<3>(t, p, run, list, Wp, seg, c, rd); break;
+            case 4: cs_items<4>(t, p, run, list, Wp, seg, c, rd); break;
+            case 5: cs_items<5>(t, p, run, list, Wp, seg, c, rd); break;
+            case 6: cs_items<6>(t, p, run, list, Wp, seg, c, rd); break;
+            case 7: cs_items<7>(t, p, run, list, Wp, seg, c, rd); break;
+            default: cs_items<8>(t, p, run, list, Wp, seg, c, rd); break;
         }
     }
 }
 
-// Direct form for a channel-block the segment form does not cover.
-template <int NT>
-__device__ __forceinline__ void cs_direct(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t theta, uint32_t w,
-                                          uint64_t phi, uint32_t r, uint32_t nt, const int64_t *tp,
+// Direct form for a channel-block the segment form does not cover (team threads only:
+// item_direct spreads chunks by threadIdx.x mod GT, which is the team thread index).
+__device__ __forceinline__ void cs_direct(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t theta,
+                                          uint32_t w, uint64_t phi, uint32_t r, uint32_t nt, const int64_t *tp,
                                           const uint32_t *code, const uint32_t *tab, int32_t *red) {
     for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
         switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-            case 1: item_direct<1, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 2: item_direct<2, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 3: item_direct<3, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 4: item_direct<4, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 5: item_direct<5, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 6: item_direct<6, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            case 7: item_direct<7, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
-            default: item_direct<8, NT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 1: item_direct<1, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 2: item_direct<2, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 3: item_direct<3, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 4: item_direct<4, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 5: item_direct<5, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 6: item_direct<6, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            case 7: item_direct<7, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
+            default: item_direct<8, CS_GT>(blk, N, a16, a4, theta, w, phi, r, tp + t0, code, tab, red + 2 * t0); break;
         }
     }
 }
 
-// Shared-memory carve-up (every piece 16-byte aligned).
-struct CsSmem {
-    uint32_t *Wp;        // [round16(max_n)]
+// One team's shared memory (every piece 16-byte aligned).
+struct CsTeam {
     uint4 *seg;          // [CS_SEG_MAX]
-    int64_t *taps;       // [cpg][mt]
-    int32_t *acc;        // [cpg][mt][2]  block sums (correlation -> filter)
-    int32_t *run;        // [cpg][mt][2]  open integrate-and-dump sums
     CsTap *tap;          // [mt]
-    uint32_t *code;      // [cpg][EXT_WORDS]
-    uint16_t *list;      // [cpg][CS_LMAX]
-    uint32_t *theta, *w, *ab, *r, *ep;   // [cpg]
-    uint64_t *phi;       // [cpg]
-    double *v, *fc, *fk; // [cpg]
-    uint64_t *full, *ready, *never;
-    uint2 *s_warp;       // [NT / 32]
-    uint32_t *abort;
+    int64_t *taps;       // [mt]
+    int32_t *acc;        // [mt][2]  the block's sums
+    int32_t *run;        // [mt][2]  open integrate-and-dump sums
+    uint32_t *code;      // [EXT_WORDS]
+    uint16_t *list;      // [CS_LMAX]
+    uint2 *s_warp;       // [GT / 32]
+    uint32_t *u;         // theta, w, r, ab, ep
+    uint64_t *phi;       // [1]
+    double *d;           // v, fc, fk, DLL correction
 };
 
 __host__ __device__ inline size_t cs_a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t cs_layout(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t max_n, size_t *o) {
+__host__ __device__ inline size_t cs_team_bytes(uint32_t mt) {
+    return (size_t)CS_SEG_MAX * 16 + cs_a16((size_t)mt * sizeof(CsTap)) + cs_a16((size_t)mt * 8) * 3 +
+           cs_a16((size_t)EXT_WORDS * 4) + cs_a16((size_t)CS_LMAX * 2) + cs_a16((CS_GT / 32) * 8) + 32 + 16 + 32;
+}
+
+__host__ __device__ inline size_t cs_wp_words(uint32_t max_n) { return (size_t)((max_n + 15) & ~15u); }
+
+// Layout: prefix buffers [nbuf][round16(max_n)] words, the CTA's mbarriers and abort
+// flag, then one team area per team.
+__host__ __device__ inline size_t cs_layout(uint32_t teams, uint32_t mt, uint32_t max_n, uint32_t nbuf, size_t *o) {
     size_t s = 0;
-    o[0] = s; s = cs_a16(s + (size_t)((max_n + 15) & ~15u) * 4);          // Wp
-    o[1] = s; s = cs_a16(s + (size_t)CS_SEG_MAX * 16);                    // seg
-    o[2] = s; s = cs_a16(s + (size_t)cpg * mt * 8);                       // taps
-    o[3] = s; s = cs_a16(s + (size_t)cpg * mt * 8);                       // acc
-    o[4] = s; s = cs_a16(s + (size_t)cpg * mt * 8);                       // run
-    o[5] = s; s = cs_a16(s + (size_t)mt * sizeof(CsTap));                 // tap
-    o[6] = s; s = cs_a16(s + (size_t)cpg * EXT_WORDS * 4);                // code
-    o[7] = s; s = cs_a16(s + (size_t)cpg * CS_LMAX * 2);                  // list
-    o[8] = s; s = cs_a16(s + (size_t)cpg * 5 * 4);                        // theta, w, ab, r, ep
-    o[9] = s; s = cs_a16(s + (size_t)cpg * 8);                            // phi
-    o[10] = s; s = cs_a16(s + (size_t)cpg * 3 * 8);                       // v, fc, fk
-    o[11] = s; s = cs_a16(s + (size_t)(2 * cpg + 1) * 8);                 // full, ready, never
-    o[12] = s; s = cs_a16(s + (size_t)(nt / 32) * 8);                     // s_warp
-    o[13] = s; s = cs_a16(s + 4);                                         // abort
+    o[0] = s; s = cs_a16(s + cs_wp_words(max_n) * 4 * nbuf);   // Wp
+    o[1] = s; s = cs_a16(s + 4 * 8);                           // pfx_full[2], pfx_free, never
+    o[2] = s; s = cs_a16(s + 4);                               // abort
+    o[3] = s; s += (size_t)teams * cs_team_bytes(mt);          // teams
     return s;
 }
 
-__device__ inline CsSmem cs_carve(unsigned char *base, uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t max_n) {
-    size_t o[14];
-    cs_layout(cpg, mt, nt, max_n, o);
-    CsSmem m;
-    m.Wp = reinterpret_cast<uint32_t *>(base + o[0]);
-    m.seg = reinterpret_cast<uint4 *>(base + o[1]);
-    m.taps = reinterpret_cast<int64_t *>(base + o[2]);
-    m.acc = reinterpret_cast<int32_t *>(base + o[3]);
-    m.run = reinterpret_cast<int32_t *>(base + o[4]);
-    m.tap = reinterpret_cast<CsTap *>(base + o[5]);
-    m.code = reinterpret_cast<uint32_t *>(base + o[6]);
-    m.list = reinterpret_cast<uint16_t *>(base + o[7]);
-    m.theta = reinterpret_cast<uint32_t *>(base + o[8]);
-    m.w = m.theta + cpg;
-    m.ab = m.w + cpg;
-    m.r = m.ab + cpg;
-    m.ep = m.r + cpg;
-    m.phi = reinterpret_cast<uint64_t *>(base + o[9]);
-    m.v = reinterpret_cast<double *>(base + o[10]);
-    m.fc = m.v + cpg;
-    m.fk = m.fc + cpg;
-    m.full = reinterpret_cast<uint64_t *>(base + o[11]);
-    m.ready = m.full + cpg;
-    m.never = m.ready + cpg;
-    m.s_warp = reinterpret_cast<uint2 *>(base + o[12]);
-    m.abort = reinterpret_cast<uint32_t *>(base + o[13]);
+__device__ inline CsTeam cs_team(unsigned char *base, uint32_t mt) {
+    CsTeam m;
+    size_t o = 0;
+    m.seg = reinterpret_cast<uint4 *>(base + o);
+    o += (size_t)CS_SEG_MAX * 16;
+    m.tap = reinterpret_cast<CsTap *>(base + o);
+    o += cs_a16((size_t)mt * sizeof(CsTap));
+    m.taps = reinterpret_cast<int64_t *>(base + o);
+    o += cs_a16((size_t)mt * 8);
+    m.acc = reinterpret_cast<int32_t *>(base + o);
+    o += cs_a16((size_t)mt * 8);
+    m.run = reinterpret_cast<int32_t *>(base + o);
+    o += cs_a16((size_t)mt * 8);
+    m.code = reinterpret_cast<uint32_t *>(base + o);
+    o += cs_a16((size_t)EXT_WORDS * 4);
+    m.list = reinterpret_cast<uint16_t *>(base + o);
+    o += cs_a16((size_t)CS_LMAX * 2);
+    m.s_warp = reinterpret_cast<uint2 *>(base + o);
+    o += cs_a16((CS_GT / 32) * 8);
+    m.u = reinterpret_cast<uint32_t *>(base + o);
+    o += 32;
+    m.phi = reinterpret_cast<uint64_t *>(base + o);
+    o += 16;
+    m.d = reinterpret_cast<double *>(base + o);
     return m;
 }
 
-template <int NT, bool T3>
-__global__ void __launch_bounds__(NT + 32 * CS_MAX_FILTER, 1) k_batch_cseg(CsArgs a) {
+// Correlate the team's channel over one block into tm.acc (zero on entry).
+__device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
+                                                 const int8_t *blk, uint32_t N, uint32_t nt, uint32_t prn,
+                                                 const Tables &tb, const uint32_t *tab) {
+    const uint32_t theta = tm.u[0], w = tm.u[1], r = tm.u[2];
+    const uint64_t phi = tm.phi[0];
+    const CsChan c = cs_chan(theta, w, r);
+    if (cs_eligible(c, N, phi)) {
+        for (uint32_t k = t; k < nt; k += CS_GT)
+            tm.tap[k] = cs_tap(c, phi, tm.taps[k], N, tb.tcount + (size_t)prn * (CS_CLEN + 1),
+                               tb.tbits + (size_t)prn * (CS_CLEN / 32));
+        uint32_t DI, DQ, sf, sl;
+        bool any;
+        cs_seg_local(t, Wp, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
+        cs_seg_scan(t, bar, DI, DQ, tm.s_warp, tm.seg, sf, sl, any);
+        team_sync(bar);                                   // segment table and tap constants complete
+        uint32_t mI = 0u, mQ = 0u;
+        if (t < nt) cs_total(Wp, tm.seg, c, N, mI, mQ);
+        for (uint32_t k = t; k < nt; k += CS_GT) {
+            const int32_t g = tm.tap[k].g_end;
+            atomicAdd((unsigned *)&tm.acc[2 * k], (uint32_t)g * mI);
+            atomicAdd((unsigned *)&tm.acc[2 * k + 1], (uint32_t)g * mQ);
+        }
+        cs_items_all(t, tm.tap, nt, tm.list, Wp, tm.seg, c, tm.acc);
+    } else {
+        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+        cs_direct(blk, N, a16, a4, theta, w, phi, r, nt, tm.taps, tm.code, tab, tm.acc);
+    }
+}
+
+template <bool T3>
+__global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const uint32_t cpg = a.cpg, mt = a.max_taps;
-    const CsSmem sm = cs_carve(smem, cpg, mt, NT, a.max_n);
+    const uint32_t mt = a.max_taps, nbuf = a.nbuf;
+    size_t o[4];
+    cs_layout(blockDim.x / CS_GT, mt, a.max_n, nbuf, o);
+    uint32_t *Wp0 = reinterpret_cast<uint32_t *>(smem + o[0]);
+    uint64_t *pfx_full = reinterpret_cast<uint64_t *>(smem + o[1]);   // [2]
+    uint64_t *pfx_free = pfx_full + 2;
+    uint64_t *never = pfx_full + 3;
+    volatile uint32_t *s_abort = reinterpret_cast<uint32_t *>(smem + o[2]);
     uint32_t *tab = g_item_tab;
-    volatile uint32_t *s_abort = sm.abort;
 
     const GroupDesc gd = a.groups[blockIdx.x];
     const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
-    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t nthreads = blockDim.x;
+    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT, twarp = t >> 5, lane = t & 31;
+    const uint32_t bar = 2 + g;
+    const CsTeam tm = cs_team(smem + o[3] + (size_t)g * cs_team_bytes(mt), mt);
+    const bool active = g < nch;
+    const uint32_t wpw = (uint32_t)cs_wp_words(a.max_n);
 
-    for (uint32_t i = tid; i < 64; i += nthreads) tab[i] = a.tb.carrier[i];
-    for (uint32_t i = tid; i < nch * nt; i += nthreads) sm.taps[i] = gd.taps[i];
-    for (uint32_t i = tid; i < nch * EXT_WORDS; i += nthreads) {
-        const uint32_t j = i / EXT_WORDS;
-        sm.code[i] = a.tb.code[(size_t)gd.prn[j] * EXT_WORDS + (i - j * EXT_WORDS)];
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
+    if (active) {
+        const uint32_t prn = gd.prn[g];
+        for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = gd.taps[(size_t)g * nt + i];
+        for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = a.tb.code[(size_t)prn * EXT_WORDS + i];
+        for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
+            reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)prn * CS_LMAX)[i];
+        for (uint32_t i = t; i < per_ch; i += CS_GT) {
+            tm.run[i] = gd.acc_blocks[g] ? gd.acc[(size_t)g * per_ch + i] : 0;
+            tm.acc[i] = 0;
+        }
+        if (t == 0) {
+            tm.u[0] = gd.theta[g];
+            tm.u[1] = (uint32_t)gd.w[g];
+            tm.u[2] = (uint32_t)gd.r[g];
+            tm.u[3] = gd.acc_blocks[g];
+            tm.u[4] = gd.epochs[g];
+            tm.phi[0] = gd.phi[g];
+            tm.d[0] = gd.v[g];
+            tm.d[1] = gd.fcarr[g];
+            tm.d[2] = gd.fcode[g];
+        }
     }
-    for (uint32_t i = tid; i < nch * (CS_LMAX / 8); i += nthreads) {
-        const uint32_t j = i / (CS_LMAX / 8), q = i - j * (CS_LMAX / 8);
-        reinterpret_cast<uint4 *>(sm.list + (size_t)j * CS_LMAX)[q] =
-            reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)gd.prn[j] * CS_LMAX)[q];
-    }
-    for (uint32_t j = tid; j < nch; j += nthreads) {
-        sm.theta[j] = gd.theta[j];
-        sm.w[j] = (uint32_t)gd.w[j];
-        sm.phi[j] = gd.phi[j];
-        sm.r[j] = (uint32_t)gd.r[j];
-        sm.ab[j] = gd.acc_blocks[j];
-        sm.ep[j] = gd.epochs[j];
-        sm.v[j] = gd.v[j];
-        sm.fc[j] = gd.fcarr[j];
-        sm.fk[j] = gd.fcode[j];
-        mbar_init(sm.full + j, NT);
-        mbar_init(sm.ready + j, 32);
-    }
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         *s_abort = 0u;
-        mbar_init(sm.never, 1);
-    }
-    __syncthreads();
-    for (uint32_t i = tid; i < nch * per_ch; i += nthreads) {
-        sm.run[i] = sm.ab[i / per_ch] ? gd.acc[i] : 0;
-        sm.acc[i] = 0;
+        mbar_init(pfx_full, blockDim.x);
+        mbar_init(pfx_full + 1, blockDim.x);
+        mbar_init(pfx_free, blockDim.x);
+        mbar_init(never, 1);
     }
     __syncthreads();
 
     const int8_t *base = a.iq + a.src_off[gd.src];
     const uint32_t blk_bytes = 2 * N;
-    if (tid < NT) {
-        // correlation threads
-        bool ok = true;
-        if (a.stall && blockIdx.x == 0 && warp == 0) ok = pipe_wait(sm.never, 0u, s_abort, a.err, a.timeout_ns, 0u);
-        const uint16_t *tcount = a.tb.tcount;
-        for (uint32_t b = 0; b < a.n_blocks; ++b) {
-            const int8_t *blk = base + (size_t)b * blk_bytes;
-            // every correlation thread is done with the previous block's prefix sums
-            if (!corr_barrier_and<NT>(ok)) {
-                ok = false;
-                break;
+    const uint32_t wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    {
+        const bool a16 = ((uintptr_t)base & 15) == 0, a4 = ((uintptr_t)base & 3) == 0;
+        if (a.n_blocks) cs_prefix_share(base, N, a16, a4, Wp0, wq, nw);
+        mbar_arrive(pfx_full);
+    }
+    bool ok = true;
+    if (a.stall && blockIdx.x == 0 && g == 0 && twarp == 0) ok = pipe_wait(never, 0u, s_abort, a.err, a.timeout_ns, 0u);
+    const LoopConsts lc = gd.lc;
+    for (uint32_t b = 0; b < a.n_blocks; ++b) {
+        const uint32_t buf = nbuf == 2 ? (b & 1u) : 0u;
+        const uint32_t *Wp = Wp0 + (size_t)buf * wpw;
+        const int8_t *blk = base + (size_t)b * blk_bytes;
+        if (ok) ok = pipe_wait(pfx_full + buf, (b / nbuf) & 1u, s_abort, a.err, a.timeout_ns, b);
+        if (!team_and(bar, ok)) break;
+        if (t == 0 && b + 1 < a.n_blocks && g == 0) prefetch_l2(blk + blk_bytes, blk_bytes);
+        if (active) cs_channel_block(t, bar, tm, Wp, blk, N, nt, gd.prn[g], a.tb, tab);
+        team_sync(bar);                                   // the block's sums are in tm.acc
+        if (b + 1 < a.n_blocks) {
+            // this team's share of the next block's prefix sums
+            const uint32_t nb = nbuf == 2 ? ((b + 1) & 1u) : 0u;
+            if (nbuf == 1) {
+                mbar_arrive(pfx_free);                    // done reading the only buffer
+                bool okf = pipe_wait(pfx_free, b & 1u, s_abort, a.err, a.timeout_ns, b);
+                if (!team_and(bar, okf)) break;
             }
-            if (tid == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + blk_bytes, blk_bytes);
-            const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-            cs_prefix<NT>(blk, N, a16, a4, sm.Wp);
-            for (uint32_t j = 0; j < nch; ++j) {
-                bool okw = true;
-                if (b > 0) okw = pipe_wait(sm.ready + j, (b - 1) & 1u, s_abort, a.err, a.timeout_ns, b);
-                // the channel's words are in place, and (first channel) the prefix sums
-                if (!corr_barrier_and<NT>(okw)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t theta = sm.theta[j], w = sm.w[j], r = sm.r[j];
-                const uint64_t phi = sm.phi[j];
-                const CsChan c = cs_chan(theta, w, r);
-                int32_t *red = sm.acc + (size_t)j * per_ch;
-                const int64_t *tp = sm.taps + (size_t)j * nt;
-                if (cs_eligible(c, N, phi)) {
-                    const uint32_t prn = gd.prn[j];
-                    for (uint32_t k = tid; k < nt; k += NT)
-                        sm.tap[k] = cs_tap(c, phi, tp[k], N, tcount + (size_t)prn * (CS_CLEN + 1),
-                                           a.tb.tbits + (size_t)prn * (CS_CLEN / 32));
-                    uint32_t DI, DQ, sf, sl;
-                    bool any;
-                    cs_seg_local<NT>(sm.Wp, N, c, tab, sm.seg, DI, DQ, sf, sl, any);
-                    cs_seg_scan<NT>(DI, DQ, sm.s_warp, sm.seg, sf, sl, any);
-                    corr_sync<NT>();                    // the segment table and tap constants are complete
-                    uint32_t mI = 0u, mQ = 0u;
-                    if (tid < nt) cs_total(sm.Wp, sm.seg, c, N, mI, mQ);
-                    for (uint32_t k = tid; k < nt; k += NT) {
-                        const int32_t g = sm.tap[k].g_end;
-                        atomicAdd((unsigned *)&red[2 * k], (uint32_t)g * mI);
-                        atomicAdd((unsigned *)&red[2 * k + 1], (uint32_t)g * mQ);
-                    }
-                    cs_items_all<NT>(sm.tap, nt, sm.list + (size_t)j * CS_LMAX, sm.Wp, sm.seg, c, red);
+            const int8_t *nblk = blk + blk_bytes;
+            const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
+            cs_prefix_share(nblk, N, a16, a4, Wp0 + (size_t)nb * wpw, wq, nw);
+            mbar_arrive(pfx_full + nb);
+        }
+        if (active) {
+            // fold the block into the channel's integrate-and-dump sums; dump and close the
+            // loops at the integration boundary
+            const bool boundary = tm.u[3] + 1 == gd.L;
+            const uint32_t ep = tm.u[4];
+            const bool store = boundary && (gd.dump_wrap || ep < gd.dump_slots);
+            int32_t *dst = gd.dumps + (uint64_t)(gd.dump_wrap ? ep % gd.dump_slots : ep) * gd.dump_stride +
+                           (uint64_t)g * per_ch;
+            for (uint32_t e = t; e < per_ch; e += CS_GT) {
+                const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
+                if (boundary) {
+                    tm.acc[e] = (int32_t)val;
+                    tm.run[e] = 0;
+                    if (store) dst[e] = (int32_t)val;
                 } else {
-                    cs_direct<NT>(blk, N, a16, a4, theta, w, phi, r, nt, tp, sm.code + (size_t)j * EXT_WORDS, tab,
-                                  red);
+                    tm.run[e] = (int32_t)val;
                 }
-                mbar_arrive(sm.full + j);
             }
-            if (!ok) break;
-        }
-    } else {
-        // filter warps: warp f of nf takes channels f, f + nf, ...
-        const uint32_t f = warp - NT / 32, nf = (nthreads - NT) / 32;
-        const LoopConsts lc = gd.lc;
-        const uint32_t L = gd.L, dump_wrap = gd.dump_wrap, dump_slots = gd.dump_slots, dump_stride = gd.dump_stride;
-        int32_t *const dumps = gd.dumps;
-        bool ok = true;
-        for (uint32_t b = 0; b < a.n_blocks && ok; ++b) {
-            for (uint32_t j = f; j < nch; j += nf) {
-                if (!pipe_wait(sm.full + j, b & 1u, s_abort, a.err, a.timeout_ns, b)) {
-                    ok = false;
-                    break;
-                }
-                const bool boundary = sm.ab[j] + 1 == L;
-                int32_t *A = sm.acc + (size_t)j * per_ch;
-                int32_t *R = sm.run + (size_t)j * per_ch;
-                const uint32_t ep = sm.ep[j];
-                const bool store = boundary && (dump_wrap || ep < dump_slots);
-                int32_t *dst = dumps + (uint64_t)(dump_wrap ? ep % dump_slots : ep) * dump_stride + (uint64_t)j * per_ch;
-                for (uint32_t e = lane; e < per_ch; e += 32) {
-                    const uint32_t val = (uint32_t)A[e] + (uint32_t)R[e];
-                    if (boundary) {
-                        A[e] = (int32_t)val;
-                        R[e] = 0;
-                        if (store) dst[e] = (int32_t)val;
-                    } else {
-                        R[e] = (int32_t)val;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    const uint32_t w = sm.w[j];
-                    sm.theta[j] = sm.theta[j] + N * w;
-                    sm.phi[j] = reduce_code_phase(sm.phi[j] + (uint64_t)N * sm.r[j]);
-                    if (boundary) {
-                        const int64_t *tp = sm.taps + (size_t)j * nt;
-                        LoopOut o = close_loops<T3>(gd, j, sm.v[j], A, tp, lc);
-                        sm.v[j] = o.v;
-                        sm.fc[j] = o.f_carr;
-                        sm.fk[j] = o.f_code;
-                        sm.w[j] = (uint32_t)o.w;
-                        sm.r[j] = (uint32_t)o.r;
-                        sm.ep[j] = ep + 1;
-                        sm.ab[j] = 0;
-                    } else {
-                        sm.ab[j] = sm.ab[j] + 1;
-                    }
-                }
-                __syncwarp();
-                for (uint32_t e = lane; e < per_ch; e += 32) A[e] = 0;
-                __syncwarp();
-                mbar_arrive(sm.ready + j);
+            team_sync(bar);
+            const int32_t *A = tm.acc;
+            const bool split = !T3 || gd.loop_set != 1u;
+            if (boundary && split && twarp == 1 && lane < 2) {
+                // DLL part on the second warp: the two envelopes on two lanes
+                const uint32_t k = lane == 0 ? (uint32_t)gd.tap_e : (uint32_t)gd.tap_l;
+                const double m = loop_envelope(A[2 * k], A[2 * k + 1]);
+                const double ml = __shfl_sync(0x3u, m, 1);
+                if (lane == 0) tm.d[3] = loop_dll(m, ml, tm.taps[gd.tap_e], tm.taps[gd.tap_l], lc);
             }
+            PllOut po{0.0, 0.0};
+            LoopOut o3{};
+            if (boundary && twarp == 0 && lane == 0) {
+                if (split) po = loop_pll(tm.d[0], A[2 * gd.tap_p], A[2 * gd.tap_p + 1], lc);
+                else o3 = close_loops<T3>(gd, g, tm.d[0], A, tm.taps, lc);
+            }
+            if (boundary) team_sync(bar);                 // the DLL part is in tm.d[3]
+            if (t == 0) {
+                const uint32_t w = tm.u[1];
+                tm.u[0] = tm.u[0] + N * w;
+                tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)N * tm.u[2]);
+                if (boundary) {
+                    const LoopOut lo = split ? loop_finish(po, tm.d[3], lc) : o3;
+                    tm.d[0] = lo.v;
+                    tm.d[1] = lo.f_carr;
+                    tm.d[2] = lo.f_code;
+                    tm.u[1] = (uint32_t)lo.w;
+                    tm.u[2] = (uint32_t)lo.r;
+                    tm.u[4] = ep + 1;
+                    tm.u[3] = 0;
+                } else {
+                    tm.u[3] = tm.u[3] + 1;
+                }
+            }
+            for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
         }
+        team_sync(bar);                                   // state and sums ready for the next block
     }
     __syncthreads();
-    for (uint32_t j = tid; j < nch; j += nthreads) {
-        gd.theta[j] = sm.theta[j];
-        gd.w[j] = (int32_t)sm.w[j];
-        gd.phi[j] = sm.phi[j];
-        gd.r[j] = sm.r[j];
-        gd.acc_blocks[j] = sm.ab[j];
-        gd.epochs[j] = sm.ep[j];
-        gd.v[j] = sm.v[j];
-        gd.fcarr[j] = sm.fc[j];
-        gd.fcode[j] = sm.fk[j];
+    if (active) {
+        if (t == 0) {
+            gd.theta[g] = tm.u[0];
+            gd.w[g] = (int32_t)tm.u[1];
+            gd.r[g] = tm.u[2];
+            gd.acc_blocks[g] = tm.u[3];
+            gd.epochs[g] = tm.u[4];
+            gd.phi[g] = tm.phi[0];
+            gd.v[g] = tm.d[0];
+            gd.fcarr[g] = tm.d[1];
+            gd.fcode[g] = tm.d[2];
+        }
+        for (uint32_t i = t; i < per_ch; i += CS_GT) gd.acc[(size_t)g * per_ch + i] = tm.run[i];
     }
-    for (uint32_t i = tid; i < nch * per_ch; i += nthreads) gd.acc[i] = sm.run[i];
 }
 
-template <int NT, bool T3>
-int cs_occ(uint32_t nf, size_t smem) {
-    auto kern = k_batch_cseg<NT, T3>;
+template <bool T3>
+int cs_occ(uint32_t threads, size_t smem) {
+    auto kern = k_batch_cseg<T3>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT + 32 * (int)nf, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, (int)threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-template <int NT, bool T3>
-cudaError_t cs_go(uint32_t nf, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a) {
-    auto kern = k_batch_cseg<NT, T3>;
+template <bool T3>
+cudaError_t cs_go(uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a) {
+    auto kern = k_batch_cseg<T3>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, NT + 32 * nf, smem, stream>>>(a);
+    kern<<<grid, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-uint32_t cs_filter_warps(uint32_t cpg) { return cpg < 1 ? 1u : cpg > CS_MAX_FILTER ? CS_MAX_FILTER : cpg; }
+uint32_t cs_max_channels() { return CS_MAX_TEAMS; }
+uint32_t cs_threads(uint32_t cpg) { return CS_GT * (cpg < 1 ? 1u : cpg); }
 
-size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t max_n) {
-    size_t o[14];
-    return cs_layout(cpg, mt, nt, max_n, o);
+size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n, uint32_t nbuf) {
+    size_t o[4];
+    return cs_layout(cpg, mt, max_n, nbuf, o);
 }
 
-int cs_occupancy(uint32_t nt, uint32_t nf, size_t smem, bool table3) {
-    if (nf < 1 || nf > CS_MAX_FILTER) return 0;
-    if (nt == 256) return table3 ? cs_occ<256, true>(nf, smem) : cs_occ<256, false>(nf, smem);
-    if (nt == 512) return table3 ? cs_occ<512, true>(nf, smem) : cs_occ<512, false>(nf, smem);
-    return 0;
+int cs_occupancy(uint32_t cpg, size_t smem, bool table3) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return 0;
+    return table3 ? cs_occ<true>(cs_threads(cpg), smem) : cs_occ<false>(cs_threads(cpg), smem);
 }
 
-cudaError_t cs_launch(uint32_t nt, uint32_t nf, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a) {
-    if (nf < 1 || nf > CS_MAX_FILTER) return cudaErrorInvalidValue;
-    if (nt == 256) return a.table3 ? cs_go<256, true>(nf, grid, smem, stream, a) : cs_go<256, false>(nf, grid, smem, stream, a);
-    if (nt == 512) return a.table3 ? cs_go<512, true>(nf, grid, smem, stream, a) : cs_go<512, false>(nf, grid, smem, stream, a);
-    return cudaErrorInvalidValue;
+cudaError_t cs_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS || (a.nbuf != 1 && a.nbuf != 2)) return cudaErrorInvalidValue;
+    return a.table3 ? cs_go<true>(cs_threads(cpg), grid, smem, stream, a)
+                    : cs_go<false>(cs_threads(cpg), grid, smem, stream, a);
 }
 
 }  // namespace rxd

@@ -448,11 +448,16 @@ struct LoopOut {
 //   e_p = atan(Q_P / I_P) / (2 pi) (+-1/4 if I_P = 0);  v += k1 e_p;  f_carr = v + k2 e_p
 //   e_c = (1 - d/2) (|E| - |L|) / (|E| + |L|);  f_code = 1.023e6 + f_carr / 1540 + kdll e_c
 //   w = rn(f_carr sfs) mod 2^32,  r = rn(f_code sfs)
-__device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
-                                               int32_t qpr, int32_t il, int32_t ql,
-                                               int64_t off_e, int64_t off_l,
-                                               const LoopConsts &lc) {
-    LoopOut o;
+// It is written as three parts so that the PLL part and the DLL part, which share no
+// operation, can run on different threads; each part is the same sequence of
+// correctly rounded operations wherever it runs.
+
+// PLL part: the integrator v and f_carr.
+struct PllOut {
+    double v, f_carr;
+};
+
+__device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc) {
     const double ip = (double)ipr, qp = (double)qpr;
     double e_pll;
     if (ip != 0.0) {
@@ -463,13 +468,18 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
     const double dv = __dmul_rn(lc.k1, e_pll);
     v = __dadd_rn(v, dv);
     const double df = __dmul_rn(lc.k2, e_pll);
-    const double f_carr = __dadd_rn(v, df);
+    return PllOut{v, __dadd_rn(v, df)};
+}
 
-    const double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
-    const double ie2 = __dmul_rn(dIe, dIe), qe2 = __dmul_rn(dQe, dQe);
-    const double il2 = __dmul_rn(dIl, dIl), ql2 = __dmul_rn(dQl, dQl);
-    const double mag_e = __dsqrt_rn(__dadd_rn(ie2, qe2));
-    const double mag_l = __dsqrt_rn(__dadd_rn(il2, ql2));
+// Envelope of one DLL tap, sqrt(I^2 + Q^2).
+__device__ __forceinline__ double loop_envelope(int32_t i, int32_t q) {
+    const double di = (double)i, dq = (double)q;
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(di, di), __dmul_rn(dq, dq)));
+}
+
+// DLL part from the two envelopes: the code-rate correction kdll e_c.
+__device__ __forceinline__ double loop_dll(double mag_e, double mag_l, int64_t off_e, int64_t off_l,
+                                           const LoopConsts &lc) {
     const double den = __dadd_rn(mag_e, mag_l);
     const double d_el = __dmul_rn((double)(off_e - off_l), RXD_TWO_M32);
     const double kd = __dsub_rn(1.0, __dmul_rn(d_el, 0.5));
@@ -479,12 +489,16 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
         num = __dmul_rn(kd, num);
         e_dll = __ddiv_rn(num, den);
     }
-    const double aid = __dmul_rn(f_carr, RXD_KAID);
-    const double corr = __dmul_rn(lc.kdll, e_dll);
+    return __dmul_rn(lc.kdll, e_dll);
+}
+
+// The code frequency and both quantised words.
+__device__ __forceinline__ LoopOut loop_finish(PllOut p, double corr, const LoopConsts &lc) {
+    LoopOut o;
+    const double aid = __dmul_rn(p.f_carr, RXD_KAID);
     double f_code = __dadd_rn(1.023e6, aid);
     f_code = __dadd_rn(f_code, corr);
-
-    double xw = __dmul_rn(f_carr, lc.sfs);
+    double xw = __dmul_rn(p.f_carr, lc.sfs);
     double xr = __dmul_rn(f_code, lc.sfs);
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
@@ -492,10 +506,19 @@ __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe,
     if (xr > 1099511627776.0) xr = 1099511627776.0;
     o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
     o.r = (uint64_t)__double2ll_rn(xr);
-    o.v = v;
-    o.f_carr = f_carr;
+    o.v = p.v;
+    o.f_carr = p.f_carr;
     o.f_code = f_code;
     return o;
+}
+
+__device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
+                                               int32_t qpr, int32_t il, int32_t ql,
+                                               int64_t off_e, int64_t off_l,
+                                               const LoopConsts &lc) {
+    const PllOut p = loop_pll(v, ipr, qpr, lc);
+    const double corr = loop_dll(loop_envelope(ie, qe), loop_envelope(il, ql), off_e, off_l, lc);
+    return loop_finish(p, corr, lc);
 }
 
 // ----------------------------------------------------------------------------

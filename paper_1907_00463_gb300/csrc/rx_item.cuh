@@ -461,21 +461,23 @@ struct CsArgs {
     uint32_t *err;             // [4]: code, 0xffffffff, group, block
     uint64_t timeout_ns;       // limit on any one wait inside a CTA
     uint32_t n_blocks;
-    uint32_t cpg;
     uint32_t max_taps;
-    uint32_t max_n;            // largest block of any receiver (sizes the prefix buffer)
+    uint32_t max_n;            // largest block of any receiver (sizes the prefix buffers)
+    uint32_t nbuf;             // prefix buffers: 2, or 1 where two do not fit
     uint32_t stall;            // 1: CTA 0 first waits on a barrier that nothing completes
     uint32_t table3;           // 1: some group runs RX_LOOPS_TABLE3
 };
 
-// Filter warps for cpg channels per CTA (one per channel, at most 8).
-uint32_t cs_filter_warps(uint32_t cpg);
-// Dynamic shared memory of one CTA with nt correlation threads.
-size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t nt, uint32_t max_n);
+// Channels per CTA the carrier-segment kernel takes (one team of threads each).
+uint32_t cs_max_channels();
+// Threads of a CTA with cpg channels.
+uint32_t cs_threads(uint32_t cpg);
+// Dynamic shared memory of one CTA with cpg channels and nbuf prefix buffers.
+size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n, uint32_t nbuf);
 // Resident CTAs per SM.
-int cs_occupancy(uint32_t nt, uint32_t nf, size_t smem, bool table3);
+int cs_occupancy(uint32_t cpg, size_t smem, bool table3);
 // One CTA per group (grid = number of groups).
-cudaError_t cs_launch(uint32_t nt, uint32_t nf, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a);
+cudaError_t cs_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a);
 
 // ----------------------------------------------------------------------------
 // Balanced schedule (rx_balance.cu)

@@ -56,8 +56,8 @@ def _check_against_oracle(receivers, sigs, results, n_blocks):
         assert_states_equal(s, os_)
 
 
-@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 512, 0, rx.RX_SCHED_SEGMENT),
-                                   (3, 256, 0, rx.RX_SCHED_SEGMENT)])
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 128, 0, rx.RX_SCHED_SEGMENT),
+                                   (3, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_uniform_batch_matches_oracle(tiles):
     recv = [synth.uniform_receiver(i, n_blocks=12) for i in range(4)]
     buf, offs, sigs = _pack(recv, 12)
@@ -70,8 +70,8 @@ def test_uniform_batch_matches_oracle(tiles):
     _check_against_oracle(recv, sigs, res, 12)
 
 
-@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 512, 0, rx.RX_SCHED_SEGMENT),
-                                   (2, 256, 0, rx.RX_SCHED_SEGMENT)])
+@pytest.mark.parametrize("tiles", [None, (0, 224, 3, rx.RX_SCHED_BALANCED), (6, 128, 0, rx.RX_SCHED_SEGMENT),
+                                   (2, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_uneven_batch_matches_oracle(tiles):
     recv = [synth.uneven_receiver(i, n_blocks=40) for i in range(8)]
     assert len({r.fs for r in recv}) >= 3 and len({r.integ_blocks for r in recv}) >= 3
@@ -86,7 +86,7 @@ def test_uneven_batch_matches_oracle(tiles):
 
 
 @pytest.mark.parametrize("tiles", [None, (2, 256, 0, rx.RX_SCHED_PIPE), (0, 224, 3, rx.RX_SCHED_BALANCED),
-                                   (4, 512, 0, rx.RX_SCHED_SEGMENT)])
+                                   (4, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_multicorrelator_101_taps_matches_oracle(tiles):
     recv = [synth.multicorrelator_receiver(i, n_blocks=3) for i in range(2)]
     buf, offs, sigs = _pack(recv, 3)
@@ -111,9 +111,9 @@ def test_alone_equals_in_the_mix_and_tiles_do_not_matter():
                   (2, 224, 0, rx.RX_SCHED_PIPE), (3, 224, 0, rx.RX_SCHED_PIPE),
                   (0, 224, 3, rx.RX_SCHED_BALANCED), (0, 128, 4, rx.RX_SCHED_BALANCED),
                   (0, 256, 1, rx.RX_SCHED_BALANCED), (0, 512, 1, rx.RX_SCHED_BALANCED),
-                  (0, 192, 3, rx.RX_SCHED_BALANCED), (1, 256, 0, rx.RX_SCHED_SEGMENT),
-                  (2, 256, 0, rx.RX_SCHED_SEGMENT), (3, 512, 0, rx.RX_SCHED_SEGMENT),
-                  (8, 512, 0, rx.RX_SCHED_SEGMENT)]:
+                  (0, 192, 3, rx.RX_SCHED_BALANCED), (1, 128, 0, rx.RX_SCHED_SEGMENT),
+                  (2, 128, 0, rx.RX_SCHED_SEGMENT), (3, 128, 0, rx.RX_SCHED_SEGMENT),
+                  (6, 128, 0, rx.RX_SCHED_SEGMENT)]:
         b = _batch(recv, 20, tiles)
         try:
             rx.rx_batch_run(b, dev, offs, 20)
@@ -144,7 +144,7 @@ def _tiles_for(schedule):
     if schedule == rx.RX_SCHED_BALANCED:
         return (0, 128, 0, schedule)
     if schedule == rx.RX_SCHED_SEGMENT:
-        return (2, 256, 0, schedule)
+        return (2, 128, 0, schedule)
     return (2, 128, 0, schedule)
 
 
@@ -318,7 +318,7 @@ def test_wait_limit_reports_timeout_and_the_handle_recovers(schedule):
     _check_against_oracle(recv, sigs, res, 6)
 
 
-@pytest.mark.parametrize("tiles", [(3, 512, 0, rx.RX_SCHED_SEGMENT), (6, 256, 0, rx.RX_SCHED_SEGMENT)])
+@pytest.mark.parametrize("tiles", [(3, 128, 0, rx.RX_SCHED_SEGMENT), (6, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_segment_form_takes_any_words(tiles):
     """Carrier words drawn over the whole int32 range (most blocks then have too many
     carrier segments and take the direct form) next to Doppler up to 15 kHz (the segment

@@ -89,7 +89,7 @@ def _run(receivers, table3, buf, offs, tiles, n_runs=1):
 
 
 @pytest.mark.parametrize("tiles", [None, (2, 128, 0, rx.RX_SCHED_STATIC), (2, 224, 0, rx.RX_SCHED_PIPE),
-                                   (3, 256, 0, rx.RX_SCHED_DYNAMIC), (3, 512, 0, rx.RX_SCHED_SEGMENT)])
+                                   (3, 256, 0, rx.RX_SCHED_DYNAMIC), (3, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_mixed_loop_sets_match_oracle(tiles):
     recv, table3 = _receivers(40)
     for r in recv:

@@ -88,8 +88,8 @@ def test_plain_form_wraps_like_the_oracle(wrap_set):
 
 @pytest.mark.parametrize("tiles", [None, (1, 128, 0, rx.RX_SCHED_DYNAMIC), (2, 128, 0, rx.RX_SCHED_STATIC),
                                    (3, 256, 0, rx.RX_SCHED_PIPE), (2, 224, 0, rx.RX_SCHED_PIPE),
-                                   (0, 224, 3, rx.RX_SCHED_BALANCED), (3, 512, 0, rx.RX_SCHED_SEGMENT),
-                                   (2, 256, 0, rx.RX_SCHED_SEGMENT)])
+                                   (0, 224, 3, rx.RX_SCHED_BALANCED), (3, 128, 0, rx.RX_SCHED_SEGMENT),
+                                   (2, 128, 0, rx.RX_SCHED_SEGMENT)])
 def test_batched_schedules_wrap_like_the_oracle(wrap_set, tiles):
     recs, sigs, expected = wrap_set
     offs, total = batch_layout(recs)
