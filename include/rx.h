@@ -697,8 +697,9 @@ rx_status rx_track_static(const rx_receiver_desc *rx, uint32_t n_rx,
  * paper reports CPU timings only, Sec. 4, so this is the build's own
  * measurement, not a step of the method).  One launch of enough 256-thread
  * CTAs to fill every SM, each thread running eight independent chains of
- * multiply-add, three-input logic and add (IMAD, LOP3, IADD3), timed with CUDA
- * events; the best of five timed launches after a warm-up.  *tops_out receives
+ * multiply-add and three-input logic operations in equal numbers (IMAD on the
+ * multiply-add pipe, LOP3 on the integer ALU pipe), timed with CUDA events;
+ * the best of five timed launches after a warm-up.  *tops_out receives
  * tera-operations per second (one operation per thread per instruction), *ms_out
  * (optional) the launch time.  Allocates and frees a small output buffer.
  * RX_EINVAL for a null tops_out, RX_ECUDA on a CUDA error. */

@@ -256,7 +256,6 @@ struct rx_batch_s {
     uint64_t timeout_ns = 2000000000ull;
     uint32_t stall = 0;
     uint32_t pipe_stage = 0;        // staging buffer bytes of the pipelined schedule (0: none)
-    uint32_t cs_nbuf = 2;           // prefix buffers of the segment schedule
     // balanced schedule: per-CTA segments and the exchange of cut channels
     SegDesc *d_segs = nullptr;
     uint32_t *d_nseg = nullptr;
@@ -638,12 +637,9 @@ rx_status build_groups(rx_batch b) {
         occ = b->threads == 128 ? occupancy_static<128>(ss)
                                 : b->threads == 512 ? occupancy_static<512>(ss) : occupancy_static<256>(ss);
     } else if (b->schedule == RX_SCHED_SEGMENT) {
-        // two prefix buffers where they fit, else one
         uint32_t max_n = 0;
         for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
-        b->cs_nbuf = 2;
-        if (cs_smem_bytes(b->cpg, b->max_taps, max_n, 2) > (size_t)b->tables->max_smem_optin) b->cs_nbuf = 1;
-        const size_t cs = cs_smem_bytes(b->cpg, b->max_taps, max_n, b->cs_nbuf);
+        const size_t cs = cs_smem_bytes(b->cpg, b->max_taps, max_n);
         occ = cs <= (size_t)b->tables->max_smem_optin ? cs_occupancy(b->cpg, cs, any_table3(b)) : 0;
     } else if (b->schedule == RX_SCHED_PIPE) {
         // Stage blocks in shared memory when that still lets every group be resident
@@ -692,7 +688,7 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     ba.groups = b->d_groups;
     ba.src_off = rxoff;
     ba.iq = iq;
-    ba.tb = Tables{b->tables->code, b->tables->tab, b->tables->pair, b->tables->tlist, b->tables->tcount,
+    ba.tb = Tables{b->tables->code, b->tables->tab, b->tables->pair, b->tables->tlist, b->tables->tmask, b->tables->tcoarse,
                    b->tables->tbits};
     ba.ticket = b->d_scratch;
     ba.err = b->d_scratch + 1;
@@ -717,10 +713,9 @@ rx_status enqueue_run(rx_batch b, const int8_t *iq, uint32_t n_blocks, uint32_t 
     if (b->schedule == RX_SCHED_SEGMENT) {
         uint32_t max_n = 0;
         for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
-        CsArgs ca{b->d_groups, rxoff,   iq,          ba.tb, ba.err,   b->timeout_ns,
-                  n_blocks,    b->max_taps, max_n, b->cs_nbuf, b->stall, any_table3(b) ? 1u : 0u};
-        cudaError_t ce = cs_launch(b->cpg, b->G, cs_smem_bytes(b->cpg, b->max_taps, max_n, b->cs_nbuf),
-                                   b->stream, ca);
+        CsArgs ca{b->d_groups, rxoff,       iq,    ba.tb,    ba.err,  b->timeout_ns,
+                  n_blocks,    b->max_taps, max_n, b->stall, any_table3(b) ? 1u : 0u};
+        cudaError_t ce = cs_launch(b->cpg, b->G, cs_smem_bytes(b->cpg, b->max_taps, max_n), b->stream, ca);
         if (ce != cudaSuccess) return berr(b, RX_ECUDA, rxh::fmt("launch: %s", cudaGetErrorString(ce)));
         RX_CUDA_TRY(cudaMemcpyAsync(b->h_err, b->d_scratch + 1, 16, cudaMemcpyDeviceToHost, b->stream), E);
         return RX_OK;

@@ -41,18 +41,22 @@
 // code word that would leave the extended chip axis) is correlated by the direct form
 // instead, with the same result.
 //
-// Work organisation.  A CTA owns a group of channels of one receiver for the whole run,
-// and each channel has its own team of GT threads with its own named barrier: the
-// team correlates its channel over a block, folds the block into the channel's
-// integrate-and-dump sums and closes the loops (Table 3, the PLL and DLL parts on two
-// warps at once), then goes on to the next block.  Teams do not wait for one another
-// except through the shared prefix sums: every team computes a share of the next
-// block's prefix sums after it has correlated the current block, into the other of
-// two buffers, and arrives on that buffer's mbarrier; a team starts a block once the
-// block's buffer is complete (which also means every team is done with the buffer's
-// previous block).  Where two buffers do not fit in shared memory (large blocks),
-// one buffer is used and a second mbarrier tells when every team is done reading it.
-// Every wait is bounded and reports a time-out.
+// Work organisation.  A CTA owns a group of up to six channels of one receiver for the
+// whole run, and each channel has a team of GT threads with its own named barrier that
+// correlates the channel over a block and folds the block into the channel's
+// integrate-and-dump sums.  Then, once per block for the whole CTA, warp 0 closes the
+// loops of every channel at an integration boundary, one channel per lane (Table 3's
+// PLL part), while warp 1 computes their DLL parts (the two envelopes of a channel on
+// two lanes), and every other warp builds the next block's prefix sums into the one
+// buffer: a loop update costs the SM's FP64 pipe per warp instruction whatever the
+// active lanes, so one pass over all channels costs no more than one.  Two CTA-wide
+// barriers a block separate the phases.  The only wait that can fail is the test hook's
+// (RX_WAIT_TEST_STALL): it is bounded and reports a time-out.
+//
+// Shared-memory layout of the prefix sums: sample n is at word n ^ (4 ((n >> 5) & 7)),
+// which keeps every run of four words together (for 16-byte stores) and spreads the
+// samples one chip apart (16 at 16.368 MHz) over all 32 banks.  The threads of the
+// segment pass take spans of an odd number of samples for the same reason.
 #include <cuda_runtime.h>
 
 #include "rx_internal.h"
@@ -108,20 +112,6 @@ __device__ __forceinline__ void team_sync(uint32_t id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(CS_GT) : "memory");
 }
 
-// As team_sync; returns true when every thread of the team passes ok.
-__device__ __forceinline__ bool team_and(uint32_t id, bool ok) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)ok), "r"(id), "n"(CS_GT)
-        : "memory");
-    return r != 0;
-}
-
 __device__ __forceinline__ CsChan cs_chan(uint32_t theta, uint32_t w, uint32_t r) {
     CsChan c;
     const bool neg = (int32_t)w < 0;
@@ -158,12 +148,14 @@ __device__ __forceinline__ uint32_t cs_first(const CsChan &c, uint32_t k) {
 }
 
 // Whether the block is covered: at most CS_SEG_MAX segments, and every tap's chips
-// (|offset| <= 64 chips) stay on the extended chip axis.
+// (|offset| <= 64 chips) stay on the extended chip axis with one index to spare (the
+// transition count below the index after the last chip is read).  The last chip of a
+// tap is at most (phi >> 32) + 64 + floor((N - 1) r / 2^32) + 1.
 __device__ __forceinline__ bool cs_eligible(const CsChan &c, uint32_t N, uint64_t phi) {
     if (N < 2 || N > CS_NMAX || c.r == 0) return false;
     if (cs_kappa(c, N - 1) + ((N - 1) >> 8) + 1 > CS_SEG_MAX) return false;
     const uint64_t chips = ((uint64_t)(N - 1) * c.r) >> 32;
-    return (phi >> 32) + 65u + chips <= (uint64_t)(CS_CLEN - CS_CBASE - 1);
+    return (phi >> 32) + 65u + chips <= (uint64_t)(CS_CLEN - CS_CBASE - 2);
 }
 
 // Raw samples n0 .. n0+15 of the block as 8 words (bytes I, Q, I, Q); zero past N.
@@ -188,6 +180,9 @@ __device__ __forceinline__ void cs_load16(const int8_t *blk, uint32_t n0, uint32
         }
     }
 }
+
+// Word of sample n in the prefix buffer (see the file comment).
+__device__ __forceinline__ uint32_t cs_sw(uint32_t n) { return n ^ (((n >> 5) & 7u) << 2); }
 
 // One warp's share of the biased local prefix W of a block (see the file comment): the
 // warp with index wq among nw warps takes the 32-chunk runs wq, wq + nw, ... (chunk q
@@ -219,17 +214,17 @@ __device__ __forceinline__ void cs_prefix_share(const int8_t *blk, uint32_t N, b
         }
         const uint32_t base = inc - acc + 0x80008000u * ((q >> 4) + 1u);
         if (q < nq) {
-            uint4 *dst = reinterpret_cast<uint4 *>(Wp + 16 * (size_t)q);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                dst[k] = make_uint4(s[4 * k] + base, s[4 * k + 1] + base, s[4 * k + 2] + base, s[4 * k + 3] + base);
+                *reinterpret_cast<uint4 *>(Wp + cs_sw(16 * q + 4 * k)) =
+                    make_uint4(s[4 * k] + base, s[4 * k + 1] + base, s[4 * k + 2] + base, s[4 * k + 3] + base);
         }
     }
 }
 
 // V(n) = W[n] - 0x00800080 (n + 1): the fields L_I(n) + 2^15, L_Q(n) + 2^15.  At a group
 // start the empty sum is 0x80008000.
-__device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { return Wp[n] - 0x00800080u * (n + 1u); }
+__device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { return Wp[cs_sw(n)] - 0x00800080u * (n + 1u); }
 
 // Segment table, first part.  Team thread t walks samples [p0, p1) of its span, cut at
 // carrier crossings and group starts, sums the rotated samples (DI, DQ) and writes, for
@@ -238,7 +233,7 @@ __device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { retur
 __device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uint32_t N, const CsChan &c,
                                              const uint32_t *tab, uint4 *seg, uint32_t &DI, uint32_t &DQ,
                                              uint32_t &sfirst, uint32_t &slast, bool &any) {
-    const uint32_t span = 32u * ((N + 32u * CS_GT - 1u) / (32u * CS_GT));
+    const uint32_t span = ((N + CS_GT - 1u) / CS_GT) | 1u;
     const uint32_t p0 = t * span, p1 = min(p0 + span, N);
     DI = 0u;
     DQ = 0u;
@@ -314,10 +309,16 @@ __device__ __forceinline__ void cs_seg_scan(uint32_t t, uint32_t bar, uint32_t D
         }
 }
 
+// Transitions at extended-axis indices below i, from the PRN's coarse counts and bits.
+__device__ __forceinline__ uint32_t cs_count_below(const uint32_t *mask, const uint32_t *coarse, uint32_t i) {
+    const uint32_t w = i >> 5, r = i & 31u;
+    return coarse[w] + (r ? (uint32_t)__popc(mask[w] >> (32u - r)) : 0u);
+}
+
 // Constants of one tap (offset off) for the block: its chip range, transition range
-// and final code value, from the per-PRN tables in global memory.
+// and final code value, from the team's copy of the PRN's tables.
 __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t off, uint32_t N,
-                                        const uint16_t *tcount, const uint32_t *tbits) {
+                                        const uint32_t *mask, const uint32_t *coarse, const uint32_t *bits) {
     CsTap t;
     const int64_t psi = (int64_t)phi + off;
     const int32_t c0 = (int32_t)(psi >> 32);
@@ -325,10 +326,10 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     t.c0p = (uint32_t)(c0 + CS_CBASE);
     t.frac = (uint32_t)psi;
     t.F = __fadd_rn(__fmul_rn((float)t.frac, __frcp_rn((float)c.r)), 0.0625f);
-    t.u0 = __ldg(tcount + c0 + 1 + CS_CBASE);
-    t.cnt = (uint32_t)__ldg(tcount + cN + 1 + CS_CBASE) - t.u0;
+    t.u0 = cs_count_below(mask, coarse, (uint32_t)(c0 + 1 + CS_CBASE));
+    t.cnt = cs_count_below(mask, coarse, (uint32_t)(cN + 1 + CS_CBASE)) - t.u0;
     const uint32_t i = (uint32_t)(cN + CS_CBASE);
-    t.g_end = ((__ldg(tbits + (i >> 5)) >> (31u - (i & 31u))) & 1u) ? -1 : 1;
+    t.g_end = ((bits[i >> 5] >> (31u - (i & 31u))) & 1u) ? -1 : 1;
     t.pad0 = t.pad1 = 0u;
     return t;
 }
@@ -352,7 +353,7 @@ __device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsCha
     if ((uint64_t)b * c.r < (((uint64_t)j << 32) - tp.frac)) ++b;
     const uint32_t n = b - 1u;
     const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
-    const uint32_t V = Wp[n] - 0x00800080u * b;
+    const uint32_t V = Wp[cs_sw(n)] - 0x00800080u * b;
     uint32_t mI = dp2a_lo_us(V, en.z, en.x), mQ = dp2a_hi_us(V, en.z, en.y);
     if (e & 0x8000u) {
         mI = 0u - mI;
@@ -376,12 +377,17 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
         uint32_t i = (t - run) & (uint32_t)(CS_GT - 1);
         run += tk.cnt;
         const uint16_t *L = list + tk.u0;
-        for (; i + CS_GT < tk.cnt; i += 2 * CS_GT) {           // two independent items per pass
-            const uint32_t e0 = L[i], e1 = L[i + CS_GT];
-            cs_item(e0, tk, c, Wp, seg, SI[k], SQ[k]);
-            cs_item(e1, tk, c, Wp, seg, SI[k], SQ[k]);
+        for (; i + 3 * CS_GT < tk.cnt; i += 4 * CS_GT) {       // four independent items per pass
+            const uint32_t e0 = L[i], e1 = L[i + CS_GT], e2 = L[i + 2 * CS_GT], e3 = L[i + 3 * CS_GT];
+            uint32_t aI = 0u, aQ = 0u, bI = 0u, bQ = 0u;
+            cs_item(e0, tk, c, Wp, seg, aI, aQ);
+            cs_item(e1, tk, c, Wp, seg, bI, bQ);
+            cs_item(e2, tk, c, Wp, seg, aI, aQ);
+            cs_item(e3, tk, c, Wp, seg, bI, bQ);
+            SI[k] += aI + bI;
+            SQ[k] += aQ + bQ;
         }
-        if (i < tk.cnt) cs_item(L[i], tk, c, Wp, seg, SI[k], SQ[k]);
+        for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, Wp, seg, SI[k], SQ[k]);
     }
     const uint32_t lane = t & 31;
 #pragma unroll
@@ -442,6 +448,7 @@ struct CsTeam {
     int32_t *run;        // [mt][2]  open integrate-and-dump sums
     uint32_t *code;      // [EXT_WORDS]
     uint16_t *list;      // [CS_LMAX]
+    uint32_t *tmask, *tcoarse, *tbits;   // [CS_CLEN / 32] each
     uint2 *s_warp;       // [GT / 32]
     uint32_t *u;         // theta, w, r, ab, ep
     uint64_t *phi;       // [1]
@@ -452,19 +459,23 @@ __host__ __device__ inline size_t cs_a16(size_t x) { return (x + 15) & ~(size_t)
 
 __host__ __device__ inline size_t cs_team_bytes(uint32_t mt) {
     return (size_t)CS_SEG_MAX * 16 + cs_a16((size_t)mt * sizeof(CsTap)) + cs_a16((size_t)mt * 8) * 3 +
-           cs_a16((size_t)EXT_WORDS * 4) + cs_a16((size_t)CS_LMAX * 2) + cs_a16((CS_GT / 32) * 8) + 32 + 16 + 32;
+           cs_a16((size_t)EXT_WORDS * 4) + cs_a16((size_t)CS_LMAX * 2) + 3 * (CS_CLEN / 32) * 4 +
+           cs_a16((CS_GT / 32) * 8) + 32 + 16 + 32;
 }
 
-__host__ __device__ inline size_t cs_wp_words(uint32_t max_n) { return (size_t)((max_n + 15) & ~15u); }
+// Words of the prefix buffer: whole 32-word rows, since the swizzle permutes words within
+// a row (the stores write whole 16-sample chunks, and a row holds two).
+__host__ __device__ inline size_t cs_wp_words(uint32_t max_n) { return ((size_t)max_n + 31) & ~(size_t)31; }
 
-// Layout: prefix buffers [nbuf][round16(max_n)] words, the CTA's mbarriers and abort
-// flag, then one team area per team.
-__host__ __device__ inline size_t cs_layout(uint32_t teams, uint32_t mt, uint32_t max_n, uint32_t nbuf, size_t *o) {
+// Layout: the prefix buffer [round32(max_n)] words, the CTA's test-hook mbarrier, the
+// per-channel DLL corrections, boundary flags and the abort flag, then one team area
+// per team.
+__host__ __device__ inline size_t cs_layout(uint32_t teams, uint32_t mt, uint32_t max_n, size_t *o) {
     size_t s = 0;
-    o[0] = s; s = cs_a16(s + cs_wp_words(max_n) * 4 * nbuf);   // Wp
-    o[1] = s; s = cs_a16(s + 4 * 8);                           // pfx_full[2], pfx_free, never
-    o[2] = s; s = cs_a16(s + 4);                               // abort
-    o[3] = s; s += (size_t)teams * cs_team_bytes(mt);          // teams
+    o[0] = s; s = cs_a16(s + cs_wp_words(max_n) * 4);                      // Wp
+    o[1] = s; s = cs_a16(s + 8);                                            // never
+    o[2] = s; s = cs_a16(s + CS_MAX_TEAMS * 8 + CS_MAX_TEAMS * 4 + 4);      // s_corr, s_bnd, abort
+    o[3] = s; s += (size_t)teams * cs_team_bytes(mt);                       // teams
     return s;
 }
 
@@ -485,6 +496,10 @@ __device__ inline CsTeam cs_team(unsigned char *base, uint32_t mt) {
     o += cs_a16((size_t)EXT_WORDS * 4);
     m.list = reinterpret_cast<uint16_t *>(base + o);
     o += cs_a16((size_t)CS_LMAX * 2);
+    m.tmask = reinterpret_cast<uint32_t *>(base + o);
+    m.tcoarse = m.tmask + CS_CLEN / 32;
+    m.tbits = m.tcoarse + CS_CLEN / 32;
+    o += 3 * (CS_CLEN / 32) * 4;
     m.s_warp = reinterpret_cast<uint2 *>(base + o);
     o += cs_a16((CS_GT / 32) * 8);
     m.u = reinterpret_cast<uint32_t *>(base + o);
@@ -503,9 +518,7 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
     if (cs_eligible(c, N, phi)) {
-        for (uint32_t k = t; k < nt; k += CS_GT)
-            tm.tap[k] = cs_tap(c, phi, tm.taps[k], N, tb.tcount + (size_t)prn * (CS_CLEN + 1),
-                               tb.tbits + (size_t)prn * (CS_CLEN / 32));
+        for (uint32_t k = t; k < nt; k += CS_GT) tm.tap[k] = cs_tap(c, phi, tm.taps[k], N, tm.tmask, tm.tcoarse, tm.tbits);
         uint32_t DI, DQ, sf, sl;
         bool any;
         cs_seg_local(t, Wp, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
@@ -525,26 +538,32 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
     }
 }
 
+// Named barrier 15 over warps 0 and 1 (the loop-update pair).
+__device__ __forceinline__ void pair_sync() { asm volatile("bar.sync 15, 64;" ::: "memory"); }
+
 template <bool T3>
 __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const uint32_t mt = a.max_taps, nbuf = a.nbuf;
+    const uint32_t mt = a.max_taps;
     size_t o[4];
-    cs_layout(blockDim.x / CS_GT, mt, a.max_n, nbuf, o);
-    uint32_t *Wp0 = reinterpret_cast<uint32_t *>(smem + o[0]);
-    uint64_t *pfx_full = reinterpret_cast<uint64_t *>(smem + o[1]);   // [2]
-    uint64_t *pfx_free = pfx_full + 2;
-    uint64_t *never = pfx_full + 3;
-    volatile uint32_t *s_abort = reinterpret_cast<uint32_t *>(smem + o[2]);
+    cs_layout(blockDim.x / CS_GT, mt, a.max_n, o);
+    uint32_t *Wp = reinterpret_cast<uint32_t *>(smem + o[0]);
+    uint64_t *never = reinterpret_cast<uint64_t *>(smem + o[1]);
+    double *s_corr = reinterpret_cast<double *>(smem + o[2]);           // [CS_MAX_TEAMS]
+    uint32_t *s_bnd = reinterpret_cast<uint32_t *>(s_corr + CS_MAX_TEAMS); // [CS_MAX_TEAMS]
+    volatile uint32_t *s_abort = s_bnd + CS_MAX_TEAMS;
     uint32_t *tab = g_item_tab;
 
     const GroupDesc gd = a.groups[blockIdx.x];
     const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
-    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT, twarp = t >> 5, lane = t & 31;
+    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const uint32_t bar = 2 + g;
-    const CsTeam tm = cs_team(smem + o[3] + (size_t)g * cs_team_bytes(mt), mt);
+    unsigned char *teams = smem + o[3];
+    const size_t tbytes = cs_team_bytes(mt);
+    const CsTeam tm = cs_team(teams + (size_t)g * tbytes, mt);
     const bool active = g < nch;
-    const uint32_t wpw = (uint32_t)cs_wp_words(a.max_n);
+    const bool split = !T3 || gd.loop_set != 1u;   // the basic loops run as PLL and DLL parts
 
     for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
     if (active) {
@@ -553,10 +572,12 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
         for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = a.tb.code[(size_t)prn * EXT_WORDS + i];
         for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
             reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)prn * CS_LMAX)[i];
-        for (uint32_t i = t; i < per_ch; i += CS_GT) {
-            tm.run[i] = gd.acc_blocks[g] ? gd.acc[(size_t)g * per_ch + i] : 0;
-            tm.acc[i] = 0;
+        for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
+            tm.tmask[i] = a.tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
+            tm.tcoarse[i] = a.tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
+            tm.tbits[i] = a.tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
         }
+        for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = gd.acc_blocks[g] ? gd.acc[(size_t)g * per_ch + i] : 0;
         if (t == 0) {
             tm.u[0] = gd.theta[g];
             tm.u[1] = (uint32_t)gd.w[g];
@@ -571,49 +592,29 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
     }
     if (threadIdx.x == 0) {
         *s_abort = 0u;
-        mbar_init(pfx_full, blockDim.x);
-        mbar_init(pfx_full + 1, blockDim.x);
-        mbar_init(pfx_free, blockDim.x);
         mbar_init(never, 1);
     }
     __syncthreads();
 
     const int8_t *base = a.iq + a.src_off[gd.src];
     const uint32_t blk_bytes = 2 * N;
-    const uint32_t wq = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    {
+    if (a.n_blocks) {
         const bool a16 = ((uintptr_t)base & 15) == 0, a4 = ((uintptr_t)base & 3) == 0;
-        if (a.n_blocks) cs_prefix_share(base, N, a16, a4, Wp0, wq, nw);
-        mbar_arrive(pfx_full);
+        cs_prefix_share(base, N, a16, a4, Wp, warp, nw);
     }
     bool ok = true;
-    if (a.stall && blockIdx.x == 0 && g == 0 && twarp == 0) ok = pipe_wait(never, 0u, s_abort, a.err, a.timeout_ns, 0u);
+    if (a.stall && blockIdx.x == 0 && warp == 0) ok = pipe_wait(never, 0u, s_abort, a.err, a.timeout_ns, 0u);
+    ok = __syncthreads_and(ok);
     const LoopConsts lc = gd.lc;
-    for (uint32_t b = 0; b < a.n_blocks; ++b) {
-        const uint32_t buf = nbuf == 2 ? (b & 1u) : 0u;
-        const uint32_t *Wp = Wp0 + (size_t)buf * wpw;
+    for (uint32_t b = 0; ok && b < a.n_blocks; ++b) {
         const int8_t *blk = base + (size_t)b * blk_bytes;
-        if (ok) ok = pipe_wait(pfx_full + buf, (b / nbuf) & 1u, s_abort, a.err, a.timeout_ns, b);
-        if (!team_and(bar, ok)) break;
-        if (t == 0 && b + 1 < a.n_blocks && g == 0) prefetch_l2(blk + blk_bytes, blk_bytes);
-        if (active) cs_channel_block(t, bar, tm, Wp, blk, N, nt, gd.prn[g], a.tb, tab);
-        team_sync(bar);                                   // the block's sums are in tm.acc
-        if (b + 1 < a.n_blocks) {
-            // this team's share of the next block's prefix sums
-            const uint32_t nb = nbuf == 2 ? ((b + 1) & 1u) : 0u;
-            if (nbuf == 1) {
-                mbar_arrive(pfx_free);                    // done reading the only buffer
-                bool okf = pipe_wait(pfx_free, b & 1u, s_abort, a.err, a.timeout_ns, b);
-                if (!team_and(bar, okf)) break;
-            }
-            const int8_t *nblk = blk + blk_bytes;
-            const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
-            cs_prefix_share(nblk, N, a16, a4, Wp0 + (size_t)nb * wpw, wq, nw);
-            mbar_arrive(pfx_full + nb);
-        }
+        if (threadIdx.x == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + blk_bytes, blk_bytes);
         if (active) {
-            // fold the block into the channel's integrate-and-dump sums; dump and close the
-            // loops at the integration boundary
+            for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+            team_sync(bar);
+            cs_channel_block(t, bar, tm, Wp, blk, N, nt, gd.prn[g], a.tb, tab);
+            team_sync(bar);                               // the block's sums are in tm.acc
+            // fold the block into the integrate-and-dump sums; dump at the boundary
             const bool boundary = tm.u[3] + 1 == gd.L;
             const uint32_t ep = tm.u[4];
             const bool store = boundary && (gd.dump_wrap || ep < gd.dump_slots);
@@ -629,45 +630,58 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
                     tm.run[e] = (int32_t)val;
                 }
             }
-            team_sync(bar);
-            const int32_t *A = tm.acc;
-            const bool split = !T3 || gd.loop_set != 1u;
-            if (boundary && split && twarp == 1 && lane < 2) {
-                // DLL part on the second warp: the two envelopes on two lanes
-                const uint32_t k = lane == 0 ? (uint32_t)gd.tap_e : (uint32_t)gd.tap_l;
-                const double m = loop_envelope(A[2 * k], A[2 * k + 1]);
-                const double ml = __shfl_sync(0x3u, m, 1);
-                if (lane == 0) tm.d[3] = loop_dll(m, ml, tm.taps[gd.tap_e], tm.taps[gd.tap_l], lc);
+            if (t == 0) {
+                // the NCOs advance over the block with the words the block was correlated with
+                tm.u[0] = tm.u[0] + N * tm.u[1];
+                tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)N * tm.u[2]);
+                s_bnd[g] = boundary ? 1u : 0u;
+                if (!boundary) tm.u[3] = tm.u[3] + 1;
             }
+        }
+        __syncthreads();                                  // every channel's sums and flags are in place
+        if (warp == 0) {
+            // the loops of channel `lane` (PLL part, or the whole loop set of Table 3)
+            const uint32_t j = lane;
+            const bool doit = j < nch && s_bnd[j];
             PllOut po{0.0, 0.0};
             LoopOut o3{};
-            if (boundary && twarp == 0 && lane == 0) {
-                if (split) po = loop_pll(tm.d[0], A[2 * gd.tap_p], A[2 * gd.tap_p + 1], lc);
-                else o3 = close_loops<T3>(gd, g, tm.d[0], A, tm.taps, lc);
+            const CsTeam tj = cs_team(teams + (size_t)(doit ? j : 0) * tbytes, mt);
+            if (doit) {
+                if (split) po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
+                else o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
             }
-            if (boundary) team_sync(bar);                 // the DLL part is in tm.d[3]
-            if (t == 0) {
-                const uint32_t w = tm.u[1];
-                tm.u[0] = tm.u[0] + N * w;
-                tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)N * tm.u[2]);
-                if (boundary) {
-                    const LoopOut lo = split ? loop_finish(po, tm.d[3], lc) : o3;
-                    tm.d[0] = lo.v;
-                    tm.d[1] = lo.f_carr;
-                    tm.d[2] = lo.f_code;
-                    tm.u[1] = (uint32_t)lo.w;
-                    tm.u[2] = (uint32_t)lo.r;
-                    tm.u[4] = ep + 1;
-                    tm.u[3] = 0;
-                } else {
-                    tm.u[3] = tm.u[3] + 1;
-                }
+            pair_sync();                                  // the DLL parts are in s_corr
+            if (doit) {
+                const LoopOut lo = split ? loop_finish(po, s_corr[j], lc) : o3;
+                tj.d[0] = lo.v;
+                tj.d[1] = lo.f_carr;
+                tj.d[2] = lo.f_code;
+                tj.u[1] = (uint32_t)lo.w;
+                tj.u[2] = (uint32_t)lo.r;
+                tj.u[4] = tj.u[4] + 1;
+                tj.u[3] = 0;
             }
-            for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+        } else if (warp == 1) {
+            // DLL parts: the early and late envelopes of channel lane / 2 on two lanes
+            const uint32_t j = lane >> 1;
+            const bool doit = split && j < nch && s_bnd[j];
+            double m = 0.0;
+            const CsTeam tj = cs_team(teams + (size_t)(doit ? j : 0) * tbytes, mt);
+            if (doit) {
+                const uint32_t k = (lane & 1u) ? (uint32_t)gd.tap_l : (uint32_t)gd.tap_e;
+                m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
+            }
+            const double ml = __shfl_down_sync(0xffffffffu, m, 1);
+            if (doit && (lane & 1u) == 0u) s_corr[j] = loop_dll(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], lc);
+            pair_sync();
+        } else if (b + 1 < a.n_blocks) {
+            // the next block's prefix sums, by every other warp
+            const int8_t *nblk = blk + blk_bytes;
+            const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
+            cs_prefix_share(nblk, N, a16, a4, Wp, warp - 2, nw - 2);
         }
-        team_sync(bar);                                   // state and sums ready for the next block
+        __syncthreads();                                  // new words and the next prefix sums in place
     }
-    __syncthreads();
     if (active) {
         if (t == 0) {
             gd.theta[g] = tm.u[0];
@@ -713,9 +727,9 @@ cudaError_t cs_go(uint32_t threads, uint32_t grid, size_t smem, cudaStream_t str
 uint32_t cs_max_channels() { return CS_MAX_TEAMS; }
 uint32_t cs_threads(uint32_t cpg) { return CS_GT * (cpg < 1 ? 1u : cpg); }
 
-size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n, uint32_t nbuf) {
+size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n) {
     size_t o[4];
-    return cs_layout(cpg, mt, max_n, nbuf, o);
+    return cs_layout(cpg, mt, max_n, o);
 }
 
 int cs_occupancy(uint32_t cpg, size_t smem, bool table3) {
@@ -724,7 +738,7 @@ int cs_occupancy(uint32_t cpg, size_t smem, bool table3) {
 }
 
 cudaError_t cs_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a) {
-    if (cpg < 1 || cpg > CS_MAX_TEAMS || (a.nbuf != 1 && a.nbuf != 2)) return cudaErrorInvalidValue;
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return cudaErrorInvalidValue;
     return a.table3 ? cs_go<true>(cs_threads(cpg), grid, smem, stream, a)
                     : cs_go<false>(cs_threads(cpg), grid, smem, stream, a);
 }

@@ -28,7 +28,8 @@ struct DeviceTables {
     uint32_t *tab = nullptr;    // device
     uint16_t *pair = nullptr;   // device, [33][PAIR_LEN] chip-pair entries
     uint16_t *tlist = nullptr;  // device, [33][CS_LMAX] code transitions (carrier-segment form)
-    uint16_t *tcount = nullptr; // device, [33][CS_CLEN + 1]
+    uint32_t *tmask = nullptr;  // device, [33][CS_CLEN / 32] transition bits
+    uint32_t *tcoarse = nullptr;// device, [33][CS_CLEN / 32] transitions below each 32-index word
     uint32_t *tbits = nullptr;  // device, [33][CS_CLEN / 32]
     int sm_count = 0;
     int max_smem_optin = 0;
@@ -45,14 +46,17 @@ void build_carrier_table(uint32_t *out /* [64] */);
 // code values around chip c as int8 bytes: low byte g(c+1), next byte g(c) - g(c+1).
 void build_pair_table(uint16_t *out /* [33][PAIR_LEN] */);
 // Code transitions over the extended chip axis, per PRN:
-//   list[p][u]  the u-th index i in [1, CS_CLEN) (ascending) at which the code value
-//               changes, g(i - 1) != g(i), as i | 0x8000 when g(i - 1) - g(i) = -2 and
-//               as i when it is +2; entries past the last are 0;
-//   count[p][i] the number of transitions at indices below i, i in [0, CS_CLEN];
-//   bits[p]     the logic levels (1 = code value -1), index i at bit 31 - (i mod 32)
-//               of word i / 32.
-void build_transition_tables(uint16_t *list /* [33][CS_LMAX] */, uint16_t *count /* [33][CS_CLEN + 1] */,
-                             uint32_t *bits /* [33][CS_CLEN / 32] */);
+//   list[p][u]   the u-th index i in [1, CS_CLEN) (ascending) at which the code value
+//                changes, g(i - 1) != g(i), as i | 0x8000 when g(i - 1) - g(i) = -2 and
+//                as i when it is +2; entries past the last are 0;
+//   mask[p]      bit 31 - (i mod 32) of word i / 32 set where index i is a transition;
+//   coarse[p][k] the number of transitions at indices below 32 k;
+//   bits[p]      the logic levels (1 = code value -1), index i at bit 31 - (i mod 32)
+//                of word i / 32.
+// The transitions below index i are coarse[i / 32] plus the set bits of mask word i / 32
+// above bit 31 - (i mod 32).
+void build_transition_tables(uint16_t *list /* [33][CS_LMAX] */, uint32_t *mask /* [33][CS_CLEN / 32] */,
+                             uint32_t *coarse /* [33][CS_CLEN / 32] */, uint32_t *bits /* [33][CS_CLEN / 32] */);
 
 inline std::string fmt(const char *f, ...) {
     char buf[512];

@@ -81,7 +81,8 @@ struct Tables {
     const uint32_t *carrier;  // 64 packed (c, s, -s, c)
     const uint16_t *pair;     // chip-pair entries [33][PAIR_LEN]
     const uint16_t *tlist;    // code transitions over the extended chip axis [33][CS_LMAX]
-    const uint16_t *tcount;   // transitions below each index [33][CS_CLEN + 1]
+    const uint32_t *tmask;    // transition bits [33][CS_CLEN / 32]
+    const uint32_t *tcoarse;  // transitions below each 32-index word [33][CS_CLEN / 32]
     const uint32_t *tbits;    // code logic levels over the extended chip axis [33][CS_CLEN / 32]
 };
 
@@ -462,8 +463,7 @@ struct CsArgs {
     uint64_t timeout_ns;       // limit on any one wait inside a CTA
     uint32_t n_blocks;
     uint32_t max_taps;
-    uint32_t max_n;            // largest block of any receiver (sizes the prefix buffers)
-    uint32_t nbuf;             // prefix buffers: 2, or 1 where two do not fit
+    uint32_t max_n;            // largest block of any receiver (sizes the prefix buffer)
     uint32_t stall;            // 1: CTA 0 first waits on a barrier that nothing completes
     uint32_t table3;           // 1: some group runs RX_LOOPS_TABLE3
 };
@@ -472,8 +472,8 @@ struct CsArgs {
 uint32_t cs_max_channels();
 // Threads of a CTA with cpg channels.
 uint32_t cs_threads(uint32_t cpg);
-// Dynamic shared memory of one CTA with cpg channels and nbuf prefix buffers.
-size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n, uint32_t nbuf);
+// Dynamic shared memory of one CTA with cpg channels.
+size_t cs_smem_bytes(uint32_t cpg, uint32_t mt, uint32_t max_n);
 // Resident CTAs per SM.
 int cs_occupancy(uint32_t cpg, size_t smem, bool table3);
 // One CTA per group (grid = number of groups).

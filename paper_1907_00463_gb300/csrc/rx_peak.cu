@@ -2,11 +2,12 @@
 //
 // The correlator is bound by 32-bit integer instruction issue, not by HBM or tensor
 // cores, and no library publishes that rate for this part, so it is measured here:
-// every thread runs eight independent chains of a multiply-add, a three-input logic
-// operation and an add (IMAD, LOP3, IADD3: the instruction mix of the correlator's
-// inner loops), enough warps per SM to keep every scheduler issuing, timed with CUDA
-// events around one launch.  The rate counts one operation per thread per
-// instruction, as the correlator's operation model does.
+// every thread runs eight independent chains, each step one multiply-add and one
+// three-input logic operation (IMAD on the multiply-add pipe, LOP3 on the integer ALU
+// pipe, in equal numbers so that neither pipe alone limits the rate), with enough
+// warps per SM to keep every scheduler issuing, timed with CUDA events around one
+// launch.  The rate counts one operation per thread per instruction, as the
+// correlator's operation model does.
 #include <cuda_runtime.h>
 
 #include "rx_internal.h"
@@ -17,27 +18,25 @@ constexpr int kChains = 8;
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads) k_int32_peak(uint32_t iters, uint32_t x, uint32_t y, uint32_t *out) {
-    uint32_t a[kChains], b[kChains], c[kChains];
+    uint32_t a[kChains], b[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
         a[k] = threadIdx.x + k;
         b[k] = blockIdx.x ^ (uint32_t)k;
-        c[k] = (uint32_t)k * 7u;
     }
     for (uint32_t i = 0; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < kChains; ++k) {
             asm volatile(
-                "mad.lo.u32 %0, %0, %3, %4;\n\t"
-                "lop3.b32 %1, %1, %0, %3, 0x96;\n\t"
-                "add.u32 %2, %2, %1;"
-                : "+r"(a[k]), "+r"(b[k]), "+r"(c[k])
+                "mad.lo.u32 %0, %0, %2, %3;\n\t"
+                "lop3.b32 %1, %1, %0, %2, 0x96;"
+                : "+r"(a[k]), "+r"(b[k])
                 : "r"(x), "r"(y));
         }
     }
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) s += a[k] ^ b[k] ^ c[k];
+    for (int k = 0; k < kChains; ++k) s += a[k] ^ b[k];
     if (s == 0x12345678u) out[blockIdx.x * kThreads + threadIdx.x] = s;   // keeps the chains live
 }
 
@@ -86,7 +85,7 @@ extern "C" rx_status rx_measure_int32_peak(int32_t device, double *tops_out, dou
         cudaGetLastError();
         return rc;
     }
-    const double ops = (double)grid * kThreads * iters * kChains * 3.0;
+    const double ops = (double)grid * kThreads * iters * kChains * 2.0;
     *tops_out = ops / (best * 1e-3) / 1e12;
     if (ms_out) *ms_out = best;
     return RX_OK;

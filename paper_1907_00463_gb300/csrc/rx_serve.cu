@@ -441,7 +441,7 @@ rx_status launch_tick(rx_serve s) {
     a.groups = s->d_groups;
     a.items = s->d_items[buf];
     a.ring = s->d_ring;
-    a.tb = Tables{s->tables->code, s->tables->tab, s->tables->pair, s->tables->tlist, s->tables->tcount,
+    a.tb = Tables{s->tables->code, s->tables->tab, s->tables->pair, s->tables->tlist, s->tables->tmask, s->tables->tcoarse,
                    s->tables->tbits};
     a.ticket = s->d_scratch[buf];
     a.err = s->d_scratch[buf] + 1;

@@ -86,14 +86,15 @@ void build_pair_table(uint16_t *out) {
     }
 }
 
-void build_transition_tables(uint16_t *list, uint16_t *count, uint32_t *bits) {
+void build_transition_tables(uint16_t *list, uint32_t *mask, uint32_t *coarse, uint32_t *bits) {
     static const int g1_taps[] = {3, 10};
     static const int g2_taps[] = {2, 3, 6, 8, 9, 10};
     uint8_t g1[RX_CODE_LEN], g2[RX_CODE_LEN];
     m_sequence(g1_taps, 2, g1);
     m_sequence(g2_taps, 6, g2);
     std::memset(list, 0, sizeof(uint16_t) * 33 * CS_LMAX);
-    std::memset(count, 0, sizeof(uint16_t) * 33 * (CS_CLEN + 1));
+    std::memset(mask, 0, sizeof(uint32_t) * 33 * (CS_CLEN / 32));
+    std::memset(coarse, 0, sizeof(uint32_t) * 33 * (CS_CLEN / 32));
     std::memset(bits, 0, sizeof(uint32_t) * 33 * (CS_CLEN / 32));
     for (int prn = 1; prn <= 32; ++prn) {
         const int d = kG2Delay[prn - 1];
@@ -104,20 +105,21 @@ void build_transition_tables(uint16_t *list, uint16_t *count, uint32_t *bits) {
             return (int)(g1[n] ^ g2[m]);
         };
         uint16_t *L = list + (size_t)prn * CS_LMAX;
-        uint16_t *C = count + (size_t)prn * (CS_CLEN + 1);
+        uint32_t *M = mask + (size_t)prn * (CS_CLEN / 32);
+        uint32_t *K = coarse + (size_t)prn * (CS_CLEN / 32);
         uint32_t *B = bits + (size_t)prn * (CS_CLEN / 32);
         int u = 0;
         for (int i = 0; i < CS_CLEN; ++i) {
-            C[i] = (uint16_t)u;
+            if ((i & 31) == 0) K[i >> 5] = (uint32_t)u;
             const int li = logic(i);
             B[i >> 5] |= (uint32_t)li << (31 - (i & 31));
             if (i > 0 && logic(i - 1) != li) {
                 // logic 0 -> +1, 1 -> -1: g(i-1) - g(i) is -2 when level i-1 is 1
                 if (u < CS_LMAX) L[u] = (uint16_t)(i | (logic(i - 1) ? 0x8000 : 0));
+                M[i >> 5] |= 1u << (31 - (i & 31));
                 ++u;
             }
         }
-        C[CS_CLEN] = (uint16_t)u;
     }
 }
 
@@ -146,28 +148,33 @@ const DeviceTables *tables_for_device(int device, std::string &err) {
     DeviceTables *t = new DeviceTables();
     std::vector<uint32_t> code(33 * kExtWords), tab(64);
     std::vector<uint16_t> pair(33 * kPairLen);
-    std::vector<uint16_t> tlist(33 * CS_LMAX), tcount(33 * (CS_CLEN + 1));
-    std::vector<uint32_t> tbits(33 * (CS_CLEN / 32));
+    std::vector<uint16_t> tlist(33 * CS_LMAX);
+    std::vector<uint32_t> tmask(33 * (CS_CLEN / 32)), tcoarse(33 * (CS_CLEN / 32)), tbits(33 * (CS_CLEN / 32));
     build_code_table(code.data());
     build_carrier_table(tab.data());
     build_pair_table(pair.data());
-    build_transition_tables(tlist.data(), tcount.data(), tbits.data());
-    for (int prn = 1; prn <= 32; ++prn)
-        if (tcount[(size_t)prn * (CS_CLEN + 1) + CS_CLEN] > CS_LMAX) {
+    build_transition_tables(tlist.data(), tmask.data(), tcoarse.data(), tbits.data());
+    for (int prn = 1; prn <= 32; ++prn) {
+        const size_t last = (size_t)prn * (CS_CLEN / 32) + CS_CLEN / 32 - 1;
+        if (tcoarse[last] + (uint32_t)__builtin_popcount(tmask[last]) > (uint32_t)CS_LMAX) {
             err = "code transition list longer than CS_LMAX";
             delete t;
             return nullptr;
         }
+    }
     cudaError_t e = cudaMalloc(&t->code, code.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&t->tab, tab.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&t->pair, pair.size() * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&t->tlist, tlist.size() * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&t->tcount, tcount.size() * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&t->tmask, tmask.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&t->tcoarse, tcoarse.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&t->tbits, tbits.size() * sizeof(uint32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(t->tlist, tlist.data(), tlist.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(t->tcount, tcount.data(), tcount.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(t->tmask, tmask.data(), tmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->tcoarse, tcoarse.data(), tcoarse.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(t->tbits, tbits.data(), tbits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -186,7 +193,8 @@ const DeviceTables *tables_for_device(int device, std::string &err) {
         if (t->tab) cudaFree(t->tab);
         if (t->pair) cudaFree(t->pair);
         if (t->tlist) cudaFree(t->tlist);
-        if (t->tcount) cudaFree(t->tcount);
+        if (t->tmask) cudaFree(t->tmask);
+        if (t->tcoarse) cudaFree(t->tcoarse);
         if (t->tbits) cudaFree(t->tbits);
         delete t;
         return nullptr;
