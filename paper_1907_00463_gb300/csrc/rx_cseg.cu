@@ -83,7 +83,7 @@ struct CsTap {          // one tap's constants for one channel-block
     uint32_t u0;        // first transition after chip c0 in the transition list
     uint32_t cnt;       // transitions inside the block
     int32_t g_end;      // code value (+-1) at the block's last sample
-    uint32_t pad0, pad1;
+    uint32_t D, Fr;     // offset past the reference tap, off - off_ref = D r + (r - Fr), Fr in (0, r]
 };
 
 struct CsChan {         // one channel-block's carrier and code words
@@ -317,7 +317,7 @@ __device__ __forceinline__ uint32_t cs_count_below(const uint32_t *mask, const u
 
 // Constants of one tap (offset off) for the block: its chip range, transition range
 // and final code value, from the team's copy of the PRN's tables.
-__device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t off, uint32_t N,
+__device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t off, int64_t off_ref, uint32_t N,
                                         const uint32_t *mask, const uint32_t *coarse, const uint32_t *bits) {
     CsTap t;
     const int64_t psi = (int64_t)phi + off;
@@ -330,7 +330,10 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     t.cnt = cs_count_below(mask, coarse, (uint32_t)(cN + 1 + CS_CBASE)) - t.u0;
     const uint32_t i = (uint32_t)(cN + CS_CBASE);
     t.g_end = ((bits[i >> 5] >> (31u - (i & 31u))) & 1u) ? -1 : 1;
-    t.pad0 = t.pad1 = 0u;
+    const uint64_t dlt = (uint64_t)(off - off_ref);           // >= 0: the reference has the least offset
+    const uint64_t D = dlt / c.r;
+    t.D = (uint32_t)D;
+    t.Fr = c.r - (uint32_t)(dlt - D * c.r);
     return t;
 }
 
@@ -388,6 +391,58 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
             SQ[k] += aQ + bQ;
         }
         for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, Wp, seg, SI[k], SQ[k]);
+    }
+    const uint32_t lane = t & 31;
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const uint32_t vi = __reduce_add_sync(0xffffffffu, SI[k]);
+        const uint32_t vq = __reduce_add_sync(0xffffffffu, SQ[k]);
+        if (lane == 0) {
+            atomicAdd((unsigned *)&red[2 * k], 2u * vi);
+            atomicAdd((unsigned *)&red[2 * k + 1], 2u * vq);
+        }
+    }
+}
+
+// Transition-major form for up to eight taps.  Thread t takes the transitions t, t + GT,
+// ... of the union of the taps' ranges; for each it finds the sample b_ref at which the
+// reference tap (least offset) reaches the transition, exactly, and the remainder
+// rho = b_ref r - (j 2^32 - frac_ref) in [0, r).  Every other tap's sample then follows
+// exactly: with off_k - off_ref = D_k r + E_k, E_k in [0, r),
+//   b_k = ceil((j 2^32 - frac_ref - off_k + off_ref) / r) = b_ref - D_k - [rho + E_k >= r],
+// and the tap takes the transition when 1 <= b_k <= N - 1 (its chip range in the block).
+template <int TT>
+__device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_t ref, uint32_t mx,
+                                            const uint16_t *list, const uint32_t *Wp, const uint4 *seg,
+                                            const CsChan &c, uint32_t N, int32_t *red) {
+    uint32_t SI[TT], SQ[TT], D[TT], Fr[TT];
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        SI[k] = SQ[k] = 0u;
+        D[k] = tp[k].D;
+        Fr[k] = tp[k].Fr;
+    }
+    const CsTap tr = tp[ref];
+    const uint32_t u_end = tp[mx].u0 + tp[mx].cnt;
+    for (uint32_t u = tr.u0 + t; u < u_end; u += CS_GT) {
+        const uint32_t e = list[u];
+        const uint32_t j = (e & 0x7fffu) - tr.c0p;               // >= 1
+        const float bf = fmaf((float)j, c.Dr, -tr.F);
+        uint32_t b = bf > 0.0f ? (uint32_t)ceilf(bf) : 0u;
+        if ((uint64_t)b * c.r < (((uint64_t)j << 32) - tr.frac)) ++b;
+        const uint32_t rho = b * c.r + tr.frac;                   // b r - (j 2^32 - frac), exact modulo 2^32
+        const int32_t sg = (e & 0x8000u) ? -1 : 1;
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            const uint32_t bk = b - D[k] - (rho >= Fr[k] ? 1u : 0u);
+            const bool valid = bk - 1u < N - 1u;
+            const uint32_t n = valid ? bk - 1u : 0u;
+            const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
+            const uint32_t V = Wp[cs_sw(n)] - 0x00800080u * (n + 1u);
+            const uint32_t w = (uint32_t)(valid ? sg : 0);
+            SI[k] += w * dp2a_lo_us(V, en.z, en.x);
+            SQ[k] += w * dp2a_hi_us(V, en.z, en.y);
+        }
     }
     const uint32_t lane = t & 31;
 #pragma unroll
@@ -518,7 +573,9 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
     if (cs_eligible(c, N, phi)) {
-        for (uint32_t k = t; k < nt; k += CS_GT) tm.tap[k] = cs_tap(c, phi, tm.taps[k], N, tm.tmask, tm.tcoarse, tm.tbits);
+        const int64_t off_ref = tm.taps[tm.u[5]];
+        for (uint32_t k = t; k < nt; k += CS_GT)
+            tm.tap[k] = cs_tap(c, phi, tm.taps[k], off_ref, N, tm.tmask, tm.tcoarse, tm.tbits);
         uint32_t DI, DQ, sf, sl;
         bool any;
         cs_seg_local(t, Wp, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
@@ -531,7 +588,18 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
             atomicAdd((unsigned *)&tm.acc[2 * k], (uint32_t)g * mI);
             atomicAdd((unsigned *)&tm.acc[2 * k + 1], (uint32_t)g * mQ);
         }
-        cs_items_all(t, tm.tap, nt, tm.list, Wp, tm.seg, c, tm.acc);
+        const uint32_t ref = tm.u[5], mx = tm.u[6];
+        switch (nt) {
+            case 1: cs_items_tm<1>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 2: cs_items_tm<2>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 3: cs_items_tm<3>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 4: cs_items_tm<4>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 5: cs_items_tm<5>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 6: cs_items_tm<6>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 7: cs_items_tm<7>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            case 8: cs_items_tm<8>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
+            default: cs_items_all(t, tm.tap, nt, tm.list, Wp, tm.seg, c, tm.acc); break;
+        }
     } else {
         const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
         cs_direct(blk, N, a16, a4, theta, w, phi, r, nt, tm.taps, tm.code, tab, tm.acc);
@@ -584,6 +652,16 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
             tm.u[2] = (uint32_t)gd.r[g];
             tm.u[3] = gd.acc_blocks[g];
             tm.u[4] = gd.epochs[g];
+            // the taps with the least and the greatest offset (the transition-major reference
+            // and the end of the taps' union range)
+            uint32_t lo = 0, hi = 0;
+            for (uint32_t k = 1; k < nt; ++k) {
+                const int64_t o = gd.taps[(size_t)g * nt + k];
+                if (o < gd.taps[(size_t)g * nt + lo]) lo = k;
+                if (o > gd.taps[(size_t)g * nt + hi]) hi = k;
+            }
+            tm.u[5] = lo;
+            tm.u[6] = hi;
             tm.phi[0] = gd.phi[g];
             tm.d[0] = gd.v[g];
             tm.d[1] = gd.fcarr[g];

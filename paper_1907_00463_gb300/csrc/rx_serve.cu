@@ -199,6 +199,7 @@ struct rx_serve_s {
     uint64_t slot_head = 0;
     std::vector<Pending> pending;
     std::deque<Tick> inflight;
+    uint32_t launching = 0;                       // ticks taken from `pending` and not yet in `inflight`
     int next_buf = 0;
     std::thread worker;
     bool running = false, stop = false;
@@ -398,8 +399,11 @@ void reap(rx_serve s, bool block) {
     }
 }
 
-// Launch one tick over the pending blocks.  s->mu held.
-rx_status launch_tick(rx_serve s) {
+// Launch one tick over the pending blocks.  Called with `lk` (on s->mu) held: the
+// pending blocks and their work items are taken under the lock, which is then released
+// for the CUDA calls (so that producers are not held up by them) and taken again to
+// record the tick.
+rx_status launch_tick(rx_serve s, std::unique_lock<std::mutex> &lk) {
     rxh::TraceRange trace_("rx_serve_tick");
     std::vector<Pending> blocks;
     blocks.swap(s->pending);
@@ -416,6 +420,16 @@ rx_status launch_tick(rx_serve s) {
             ++n;
         }
     }
+    s->launching += 1;
+    lk.unlock();
+    struct Relock {
+        rx_serve s;
+        std::unique_lock<std::mutex> &l;
+        ~Relock() {
+            if (!l.owns_lock()) l.lock();
+            s->launching -= 1;
+        }
+    } relock{s, lk};
     // copy the ring slots of this tick (slots are taken in arrival order, so one or two
     // contiguous ranges cover them)
     std::vector<uint32_t> slots;
@@ -435,7 +449,7 @@ rx_status launch_tick(rx_serve s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_scratch[buf], 0, 5 * 4, s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return serr(s, RX_ECUDA, rxh::fmt("tick copies: %s", cudaGetErrorString(e)));
+        return serr(s, RX_ECUDA, rxh::fmt("tick copies: %s", cudaGetErrorString(e)));   // relocked on return
     }
     ServeArgs a;
     a.groups = s->d_groups;
@@ -460,6 +474,7 @@ rx_status launch_tick(rx_serve s) {
     Tick t;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(t.ev, s->stream);
+    lk.lock();
     if (e != cudaSuccess) {
         cudaGetLastError();
         return serr(s, RX_ECUDA, rxh::fmt("tick launch: %s", cudaGetErrorString(e)));
@@ -469,7 +484,7 @@ rx_status launch_tick(rx_serve s) {
     s->inflight.push_back(std::move(t));
     s->ticks += 1;
     s->items_total += n;
-    return RX_OK;
+    return RX_OK;                        // the guard ends the launch with the lock held
 }
 
 void service_loop(rx_serve s) {
@@ -478,7 +493,7 @@ void service_loop(rx_serve s) {
     for (;;) {
         reap(s, false);
         if (!s->pending.empty() && (int)s->inflight.size() < kMaxInflight) {
-            launch_tick(s);
+            launch_tick(s, lk);
             continue;
         }
         if (s->stop && s->pending.empty() && s->inflight.empty()) break;
@@ -693,7 +708,7 @@ extern "C" rx_status rx_serve_drain(rx_serve s) {
     for (;;) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            if (s->pending.empty() && s->inflight.empty()) break;
+            if (s->pending.empty() && s->inflight.empty() && s->launching == 0) break;
         }
         s->cv.notify_one();
         std::this_thread::sleep_for(std::chrono::microseconds(50));

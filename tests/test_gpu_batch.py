@@ -286,6 +286,12 @@ def test_batch_invalid_arguments():
         with pytest.raises(rx.RxError) as e:
             rx.rx_batch_set_tiles(b, 0, 224, 9, rx.RX_SCHED_BALANCED)
         assert e.value.status == rx.RX_EINVAL
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 7, 128, 0, rx.RX_SCHED_SEGMENT)   # at most 6 channels per item
+        assert e.value.status == rx.RX_EINVAL
+        with pytest.raises(rx.RxError) as e:
+            rx.rx_batch_set_tiles(b, 2, 256, 0, rx.RX_SCHED_SEGMENT)   # 128 threads per channel
+        assert e.value.status == rx.RX_EINVAL
     finally:
         rx.rx_batch_destroy(b)
 
