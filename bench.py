@@ -1034,8 +1034,8 @@ def run_ours(args):
                      "model": "INT32 ops = sample*channel x (8 + 3T), T = 5 (the direct form's "
                               "operations; the carrier-segment form executes fewer, so its rate "
                               "against this model is an effective rate); peak = the INT32 issue "
-                              "rate measured in this run (rx_measure_int32_peak: IMAD/LOP3/IADD3 "
-                              "chains on every SM)",
+                              "rate measured in this run (rx_measure_int32_peak: independent IMAD "
+                              "and LOP3 chains in equal numbers on every SM)",
                      "peak_measured": measured_tops, "peak_probe_ms": peak_probe_ms,
                      "peak_derived": derived_tops,
                      "frac_of_derived_peak": achieved / derived_tops,

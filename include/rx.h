@@ -497,10 +497,24 @@ typedef struct {
     uint32_t max_block_samples;       /* largest block of any stream */
     uint32_t ring_blocks;             /* blocks that can wait (pinned + device ring) */
     uint32_t dump_slots;              /* per-stream ring of the latest dumps */
-    uint32_t channels_per_item;       /* channels per work item (0 = 2) */
+    uint32_t channels_per_item;       /* channels per work item (0: 2 for the chunk forms,
+                                         4 for the carrier-segment form) */
     int32_t device;
     uint64_t hbm_budget_bytes;        /* device pool for per-stream state and dumps */
+    uint32_t form;                    /* RX_SERVE_FORM_* (0 = auto) */
+    uint32_t reserved;                /* must be 0 */
 } rx_serve_config;
+
+/* Serving kernels.  AUTO takes the carrier-segment form (the batched
+ * RX_SCHED_SEGMENT kernel's correlation, one 128-thread team per channel,
+ * at most 6 channels per item) when channels_per_item allows it and a CTA's
+ * shared memory (prefix sums of the largest block plus one team area per
+ * channel) fits the device; CHUNK the per-chunk direct and chip-segment
+ * forms; SEGMENT requires the carrier-segment form (RX_EINVAL when it does
+ * not fit).  Results are bit-identical across forms. */
+#define RX_SERVE_FORM_AUTO 0u
+#define RX_SERVE_FORM_CHUNK 1u
+#define RX_SERVE_FORM_SEGMENT 2u
 
 typedef struct rx_serve_s *rx_serve;
 

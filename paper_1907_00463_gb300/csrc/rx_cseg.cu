@@ -75,6 +75,7 @@ constexpr uint32_t CS_SEG_MAX = 512;    // segments per channel-block
 constexpr uint32_t CS_NMAX = 65536;     // samples per block
 constexpr int CS_GT = 128;              // threads per channel team
 constexpr uint32_t CS_MAX_TEAMS = 6;    // channels per CTA
+constexpr uint32_t CS_TGROUPS = (RX_MAX_TAPS + 7) / 8;   // transition-major tap groups
 
 struct CsTap {          // one tap's constants for one channel-block
     uint32_t c0p;       // chip of sample 0 + CS_CBASE
@@ -93,6 +94,7 @@ struct CsChan {         // one channel-block's carrier and code words
     uint32_t neg;       // w < 0: the index steps down
     uint32_t r;         // code word (< 2^32)
     float inv_a, Dr;    // 1 / a and 2^32 / r (estimates only)
+    float Ka, Kg;       // 2^26 / a and (2^26 - f) / a (estimates only)
 };
 
 __device__ __forceinline__ uint32_t dp2a_lo_us(uint32_t a, uint32_t b, uint32_t c) {
@@ -125,6 +127,8 @@ __device__ __forceinline__ CsChan cs_chan(uint32_t theta, uint32_t w, uint32_t r
     c.r = r;
     c.inv_a = c.a ? __frcp_rn((float)c.a) : 0.0f;
     c.Dr = r ? __fdiv_rn(4294967296.0f, (float)r) : 0.0f;
+    c.Ka = __fmul_rn(67108864.0f, c.inv_a);
+    c.Kg = __fmul_rn((float)(0x4000000u - c.f), c.inv_a);
     return c;
 }
 
@@ -136,23 +140,24 @@ __device__ __forceinline__ uint32_t cs_bin(const CsChan &c, uint32_t k) {
     return (c.neg ? c.bin0 - k : c.bin0 + k) & 63u;
 }
 
-// The first sample n with kappa(n) >= k (k >= 1, a >= 1): ceil((k 2^26 - f) / a).  The
-// float estimate is biased low by 1/16 against a relative error below 2^-21 (n < 2^16),
-// so it is the answer or one less, and one exact comparison corrects it.
+// The first sample n with kappa(n) >= k (k >= 1, a >= 1, f < 2^26): ceil((k 2^26 - f) / a)
+// = ceil((k - 1) 2^26 / a + (2^26 - f) / a).  Both terms are positive, so the float
+// estimate's error is a few roundings of 2^-24 relative to n < 2^16, below 1/50; biased
+// low by 1/16 it is the answer or one less, and one exact comparison corrects it.
 __device__ __forceinline__ uint32_t cs_first(const CsChan &c, uint32_t k) {
-    const uint64_t num = ((uint64_t)k << 26) - c.f;
-    const float nf = __fmul_rn(__ull2float_rn(num), c.inv_a) - 0.0625f;
+    const float nf = __fsub_rn(fmaf((float)(k - 1u), c.Ka, c.Kg), 0.0625f);
     uint32_t n = nf > 0.0f ? (uint32_t)ceilf(nf) : 0u;
-    if ((uint64_t)n * c.a < num) ++n;
+    if ((uint64_t)n * c.a + c.f < ((uint64_t)k << 26)) ++n;
     return n;
 }
 
-// Whether the block is covered: at most CS_SEG_MAX segments, and every tap's chips
-// (|offset| <= 64 chips) stay on the extended chip axis with one index to spare (the
-// transition count below the index after the last chip is read).  The last chip of a
-// tap is at most (phi >> 32) + 64 + floor((N - 1) r / 2^32) + 1.
+// Whether the block is covered: at most CS_SEG_MAX segments, a code word of at least
+// 2^16 (so that frac / r < 2^16 and the float boundary estimates keep their error below
+// 1/16), and every tap's chips (|offset| <= 64 chips) stay on the extended chip axis
+// with one index to spare (the transition count below the index after the last chip is
+// read).  The last chip of a tap is at most (phi >> 32) + 64 + floor((N - 1) r / 2^32) + 1.
 __device__ __forceinline__ bool cs_eligible(const CsChan &c, uint32_t N, uint64_t phi) {
-    if (N < 2 || N > CS_NMAX || c.r == 0) return false;
+    if (N < 2 || N > CS_NMAX || c.r < 0x10000u) return false;
     if (cs_kappa(c, N - 1) + ((N - 1) >> 8) + 1 > CS_SEG_MAX) return false;
     const uint64_t chips = ((uint64_t)(N - 1) * c.r) >> 32;
     return (phi >> 32) + 65u + chips <= (uint64_t)(CS_CLEN - CS_CBASE - 2);
@@ -330,10 +335,22 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     t.cnt = cs_count_below(mask, coarse, (uint32_t)(cN + 1 + CS_CBASE)) - t.u0;
     const uint32_t i = (uint32_t)(cN + CS_CBASE);
     t.g_end = ((bits[i >> 5] >> (31u - (i & 31u))) & 1u) ? -1 : 1;
-    const uint64_t dlt = (uint64_t)(off - off_ref);           // >= 0: the reference has the least offset
-    const uint64_t D = dlt / c.r;
+    // off - off_ref = D r + E with E in [0, r): D rounded from a float estimate and one
+    // exact correction either way.  D is used only when the taps' span is below 2^17 r;
+    // then the estimate's error (three roundings of 2^-24 relative) is below 1/20, so the
+    // rounded value is D or D + 1.
+    const int64_t dlt = off - off_ref;                        // >= 0: the reference has the least offset
+    int64_t D = (int64_t)__float2int_rn(__fmul_rn((float)dlt, __frcp_rn((float)c.r)));
+    int64_t E = dlt - D * (int64_t)c.r;
+    if (E < 0) {
+        D -= 1;
+        E += c.r;
+    } else if (E >= (int64_t)c.r) {
+        D += 1;
+        E -= c.r;
+    }
     t.D = (uint32_t)D;
-    t.Fr = c.r - (uint32_t)(dlt - D * c.r);
+    t.Fr = c.r - (uint32_t)E;
     return t;
 }
 
@@ -404,15 +421,16 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
     }
 }
 
-// Transition-major form for up to eight taps.  Thread t takes the transitions t, t + GT,
-// ... of the union of the taps' ranges; for each it finds the sample b_ref at which the
-// reference tap (least offset) reaches the transition, exactly, and the remainder
+// Transition-major form for a group of up to eight taps.  Thread t takes the transitions
+// of the union of the taps' ranges whose running index over the channel's groups is t mod
+// GT; for each it finds the sample b_ref at which the group's reference tap (its least
+// offset) reaches the transition, exactly, and the remainder
 // rho = b_ref r - (j 2^32 - frac_ref) in [0, r).  Every other tap's sample then follows
 // exactly: with off_k - off_ref = D_k r + E_k, E_k in [0, r),
 //   b_k = ceil((j 2^32 - frac_ref - off_k + off_ref) / r) = b_ref - D_k - [rho + E_k >= r],
 // and the tap takes the transition when 1 <= b_k <= N - 1 (its chip range in the block).
 template <int TT>
-__device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_t ref, uint32_t mx,
+__device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_t ref, uint32_t mx, uint32_t &run,
                                             const uint16_t *list, const uint32_t *Wp, const uint4 *seg,
                                             const CsChan &c, uint32_t N, int32_t *red) {
     uint32_t SI[TT], SQ[TT], D[TT], Fr[TT];
@@ -424,7 +442,9 @@ __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_
     }
     const CsTap tr = tp[ref];
     const uint32_t u_end = tp[mx].u0 + tp[mx].cnt;
-    for (uint32_t u = tr.u0 + t; u < u_end; u += CS_GT) {
+    const uint32_t u_beg = tr.u0 + ((t - run) & (uint32_t)(CS_GT - 1));
+    run += u_end > tr.u0 ? u_end - tr.u0 : 0u;
+    for (uint32_t u = u_beg; u < u_end; u += CS_GT) {
         const uint32_t e = list[u];
         const uint32_t j = (e & 0x7fffu) - tr.c0p;               // >= 1
         const float bf = fmaf((float)j, c.Dr, -tr.F);
@@ -452,25 +472,6 @@ __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_
         if (lane == 0) {
             atomicAdd((unsigned *)&red[2 * k], 2u * vi);
             atomicAdd((unsigned *)&red[2 * k + 1], 2u * vq);
-        }
-    }
-}
-
-__device__ __forceinline__ void cs_items_all(uint32_t t, const CsTap *tp, uint32_t nt, const uint16_t *list,
-                                             const uint32_t *Wp, const uint4 *seg, const CsChan &c, int32_t *red) {
-    uint32_t run = 0;
-    for (uint32_t t0 = 0; t0 < nt; t0 += TAP_GROUP) {
-        const CsTap *p = tp + t0;
-        int32_t *rd = red + 2 * t0;
-        switch (min((uint32_t)TAP_GROUP, nt - t0)) {
-            case 1: cs_items<1>(t, p, run, list, Wp, seg, c, rd); break;
-            case 2: cs_items<2>(t, p, run, list, Wp, seg, c, rd); break;
-            case 3: cs_items<3>(t, p, run, list, Wp, seg, c, rd); break;
-            case 4: cs_items<4>(t, p, run, list, Wp, seg, c, rd); break;
-            case 5: cs_items<5>(t, p, run, list, Wp, seg, c, rd); break;
-            case 6: cs_items<6>(t, p, run, list, Wp, seg, c, rd); break;
-            case 7: cs_items<7>(t, p, run, list, Wp, seg, c, rd); break;
-            default: cs_items<8>(t, p, run, list, Wp, seg, c, rd); break;
         }
     }
 }
@@ -505,6 +506,7 @@ struct CsTeam {
     uint16_t *list;      // [CS_LMAX]
     uint32_t *tmask, *tcoarse, *tbits;   // [CS_CLEN / 32] each
     uint2 *s_warp;       // [GT / 32]
+    uint32_t *grp;       // [CS_TGROUPS]  per tap group of eight: reference | end << 16
     uint32_t *u;         // theta, w, r, ab, ep
     uint64_t *phi;       // [1]
     double *d;           // v, fc, fk, DLL correction
@@ -515,7 +517,7 @@ __host__ __device__ inline size_t cs_a16(size_t x) { return (x + 15) & ~(size_t)
 __host__ __device__ inline size_t cs_team_bytes(uint32_t mt) {
     return (size_t)CS_SEG_MAX * 16 + cs_a16((size_t)mt * sizeof(CsTap)) + cs_a16((size_t)mt * 8) * 3 +
            cs_a16((size_t)EXT_WORDS * 4) + cs_a16((size_t)CS_LMAX * 2) + 3 * (CS_CLEN / 32) * 4 +
-           cs_a16((CS_GT / 32) * 8) + 32 + 16 + 32;
+           cs_a16((CS_GT / 32) * 8) + CS_TGROUPS * 4 + 32 + 16 + 32;
 }
 
 // Words of the prefix buffer: whole 32-word rows, since the swizzle permutes words within
@@ -557,6 +559,8 @@ __device__ inline CsTeam cs_team(unsigned char *base, uint32_t mt) {
     o += 3 * (CS_CLEN / 32) * 4;
     m.s_warp = reinterpret_cast<uint2 *>(base + o);
     o += cs_a16((CS_GT / 32) * 8);
+    m.grp = reinterpret_cast<uint32_t *>(base + o);
+    o += CS_TGROUPS * 4;
     m.u = reinterpret_cast<uint32_t *>(base + o);
     o += 32;
     m.phi = reinterpret_cast<uint64_t *>(base + o);
@@ -573,9 +577,9 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
     if (cs_eligible(c, N, phi)) {
-        const int64_t off_ref = tm.taps[tm.u[5]];
         for (uint32_t k = t; k < nt; k += CS_GT)
-            tm.tap[k] = cs_tap(c, phi, tm.taps[k], off_ref, N, tm.tmask, tm.tcoarse, tm.tbits);
+            tm.tap[k] = cs_tap(c, phi, tm.taps[k], tm.taps[tm.grp[k >> 3] & 0xffffu], N, tm.tmask, tm.tcoarse,
+                               tm.tbits);
         uint32_t DI, DQ, sf, sl;
         bool any;
         cs_seg_local(t, Wp, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
@@ -588,17 +592,33 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
             atomicAdd((unsigned *)&tm.acc[2 * k], (uint32_t)g * mI);
             atomicAdd((unsigned *)&tm.acc[2 * k + 1], (uint32_t)g * mQ);
         }
-        const uint32_t ref = tm.u[5], mx = tm.u[6];
-        switch (nt) {
-            case 1: cs_items_tm<1>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 2: cs_items_tm<2>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 3: cs_items_tm<3>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 4: cs_items_tm<4>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 5: cs_items_tm<5>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 6: cs_items_tm<6>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 7: cs_items_tm<7>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            case 8: cs_items_tm<8>(t, tm.tap, ref, mx, tm.list, Wp, tm.seg, c, N, tm.acc); break;
-            default: cs_items_all(t, tm.tap, nt, tm.list, Wp, tm.seg, c, tm.acc); break;
+        // taps in groups of eight; a group is transition-major while every boundary it
+        // derives stays below 2^18 (its reference tap's boundaries reach span / r + N),
+        // where the float estimates hold, and tap by tap otherwise
+        uint32_t run = 0;
+        for (uint32_t k0 = 0; k0 < nt; k0 += 8) {
+            const uint32_t gr = tm.grp[k0 >> 3], ref = (gr & 0xffffu) - k0, mx = (gr >> 16) - k0;
+            const bool tmj = (uint64_t)(tm.taps[k0 + mx] - tm.taps[k0 + ref]) < ((uint64_t)r << 17);
+            const CsTap *tp = tm.tap + k0;
+            int32_t *rd = tm.acc + 2 * k0;
+            switch ((tmj ? 8u : 0u) + min(8u, nt - k0)) {
+                case 1: cs_items<1>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 2: cs_items<2>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 3: cs_items<3>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 4: cs_items<4>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 5: cs_items<5>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 6: cs_items<6>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 7: cs_items<7>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 8: cs_items<8>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
+                case 9: cs_items_tm<1>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 10: cs_items_tm<2>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 11: cs_items_tm<3>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 12: cs_items_tm<4>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 13: cs_items_tm<5>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 14: cs_items_tm<6>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 15: cs_items_tm<7>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                default: cs_items_tm<8>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+            }
         }
     } else {
         const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
@@ -609,68 +629,185 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
 // Named barrier 15 over warps 0 and 1 (the loop-update pair).
 __device__ __forceinline__ void pair_sync() { asm volatile("bar.sync 15, 64;" ::: "memory"); }
 
+// The CTA's shared-memory areas (one layout for the batched and the serving kernels).
+struct CsShared {
+    uint32_t *Wp;
+    uint64_t *never;
+    double *s_corr;              // [CS_MAX_TEAMS] the DLL parts
+    uint32_t *s_bnd;             // [CS_MAX_TEAMS] integration boundary flags
+    volatile uint32_t *s_abort;
+    unsigned char *teams;
+    size_t tbytes;
+};
+
+__device__ __forceinline__ CsShared cs_shared(unsigned char *smem, uint32_t mt, uint32_t max_n) {
+    size_t o[4];
+    cs_layout(blockDim.x / CS_GT, mt, max_n, o);
+    CsShared h;
+    h.Wp = reinterpret_cast<uint32_t *>(smem + o[0]);
+    h.never = reinterpret_cast<uint64_t *>(smem + o[1]);
+    h.s_corr = reinterpret_cast<double *>(smem + o[2]);
+    h.s_bnd = reinterpret_cast<uint32_t *>(h.s_corr + CS_MAX_TEAMS);
+    h.s_abort = h.s_bnd + CS_MAX_TEAMS;
+    h.teams = smem + o[3];
+    h.tbytes = cs_team_bytes(mt);
+    return h;
+}
+
+// Channel g of the group into its team area: taps, the PRN's code and transition tables,
+// the open integrate-and-dump sums, the NCO words and loop state, and per group of eight
+// taps the taps with the least and the greatest offset (the transition-major reference and
+// the end of the group's union range).
+__device__ __forceinline__ void cs_team_load(uint32_t t, const CsTeam &tm, const GroupDesc &gd, uint32_t g,
+                                             const Tables &tb) {
+    const uint32_t nt = gd.ntaps, per_ch = 2 * nt, prn = gd.prn[g];
+    const int64_t *tp = gd.taps + (size_t)g * nt;
+    for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = tp[i];
+    for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = tb.code[(size_t)prn * EXT_WORDS + i];
+    for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
+        reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(tb.tlist + (size_t)prn * CS_LMAX)[i];
+    for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
+        tm.tmask[i] = tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
+        tm.tcoarse[i] = tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
+        tm.tbits[i] = tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
+    }
+    for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = gd.acc_blocks[g] ? gd.acc[(size_t)g * per_ch + i] : 0;
+    for (uint32_t k0 = 8 * t; k0 < nt; k0 += 8 * CS_GT) {
+        uint32_t lo = k0, hi = k0;
+        for (uint32_t k = k0 + 1; k < min(k0 + 8, nt); ++k) {
+            if (tp[k] < tp[lo]) lo = k;
+            if (tp[k] > tp[hi]) hi = k;
+        }
+        tm.grp[k0 >> 3] = lo | (hi << 16);
+    }
+    if (t == 0) {
+        tm.u[0] = gd.theta[g];
+        tm.u[1] = (uint32_t)gd.w[g];
+        tm.u[2] = (uint32_t)gd.r[g];
+        tm.u[3] = gd.acc_blocks[g];
+        tm.u[4] = gd.epochs[g];
+        tm.phi[0] = gd.phi[g];
+        tm.d[0] = gd.v[g];
+        tm.d[1] = gd.fcarr[g];
+        tm.d[2] = gd.fcode[g];
+    }
+}
+
+// The block's sums (tm.acc) into the integrate-and-dump sums; at the integration boundary
+// the sums are dumped and kept in tm.acc for the loops.  The NCOs advance over the block
+// with the words the block was correlated with; s_bnd[g] says whether the loops close.
+__device__ __forceinline__ void cs_team_fold(uint32_t t, const CsTeam &tm, const GroupDesc &gd, uint32_t g,
+                                             uint32_t *s_bnd) {
+    const uint32_t per_ch = 2 * gd.ntaps, N = gd.N;
+    const bool boundary = tm.u[3] + 1 == gd.L;
+    const uint32_t ep = tm.u[4];
+    const bool store = boundary && (gd.dump_wrap || ep < gd.dump_slots);
+    int32_t *dst = gd.dumps + (uint64_t)(gd.dump_wrap ? ep % gd.dump_slots : ep) * gd.dump_stride +
+                   (uint64_t)g * per_ch;
+    for (uint32_t e = t; e < per_ch; e += CS_GT) {
+        const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
+        if (boundary) {
+            tm.acc[e] = (int32_t)val;
+            tm.run[e] = 0;
+            if (store) dst[e] = (int32_t)val;
+        } else {
+            tm.run[e] = (int32_t)val;
+        }
+    }
+    if (t == 0) {
+        tm.u[0] = tm.u[0] + N * tm.u[1];
+        tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)N * tm.u[2]);
+        s_bnd[g] = boundary ? 1u : 0u;
+        if (!boundary) tm.u[3] = tm.u[3] + 1;
+    }
+}
+
+// The loops of every channel whose integration closed, on warps 0 and 1 (the other warps
+// do not call this): warp 0 lane j runs channel j's PLL part (or its whole loop set of
+// Table 3), warp 1 lanes 2j and 2j + 1 its early and late envelopes and the DLL part.
+template <bool T3>
+__device__ __forceinline__ void cs_loops(uint32_t warp, uint32_t lane, const GroupDesc &gd, const CsShared &h,
+                                         uint32_t mt) {
+    const uint32_t nch = gd.nch;
+    const bool split = !T3 || gd.loop_set != 1u;   // the basic loops run as PLL and DLL parts
+    const LoopConsts lc = gd.lc;
+    if (warp == 0) {
+        const uint32_t j = lane;
+        const bool doit = j < nch && h.s_bnd[j];
+        PllOut po{0.0, 0.0};
+        LoopOut o3{};
+        const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        if (doit) {
+            if (split) po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
+            else o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
+        }
+        pair_sync();                                  // the DLL parts are in s_corr
+        if (doit) {
+            const LoopOut lo = split ? loop_finish(po, h.s_corr[j], lc) : o3;
+            tj.d[0] = lo.v;
+            tj.d[1] = lo.f_carr;
+            tj.d[2] = lo.f_code;
+            tj.u[1] = (uint32_t)lo.w;
+            tj.u[2] = (uint32_t)lo.r;
+            tj.u[4] = tj.u[4] + 1;
+            tj.u[3] = 0;
+        }
+    } else if (warp == 1) {
+        const uint32_t j = lane >> 1;
+        const bool doit = split && j < nch && h.s_bnd[j];
+        double m = 0.0;
+        const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        if (doit) {
+            const uint32_t k = (lane & 1u) ? (uint32_t)gd.tap_l : (uint32_t)gd.tap_e;
+            m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
+        }
+        const double ml = __shfl_down_sync(0xffffffffu, m, 1);
+        if (doit && (lane & 1u) == 0u) h.s_corr[j] = loop_dll(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], lc);
+        pair_sync();
+    }
+}
+
+// The team's channel state back to the group's arrays.
+__device__ __forceinline__ void cs_team_store(uint32_t t, const CsTeam &tm, const GroupDesc &gd, uint32_t g) {
+    const uint32_t per_ch = 2 * gd.ntaps;
+    if (t == 0) {
+        gd.theta[g] = tm.u[0];
+        gd.w[g] = (int32_t)tm.u[1];
+        gd.r[g] = tm.u[2];
+        gd.acc_blocks[g] = tm.u[3];
+        gd.epochs[g] = tm.u[4];
+        gd.phi[g] = tm.phi[0];
+        gd.v[g] = tm.d[0];
+        gd.fcarr[g] = tm.d[1];
+        gd.fcode[g] = tm.d[2];
+    }
+    for (uint32_t i = t; i < per_ch; i += CS_GT) gd.acc[(size_t)g * per_ch + i] = tm.run[i];
+}
+
+// Batched form: one CTA per group runs all of its blocks.  Per block every team correlates
+// its channel (CTA-shared prefix sums of the block), then warps 0 and 1 close the loops
+// while the other warps build the next block's prefix sums.
 template <bool T3>
 __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t mt = a.max_taps;
-    size_t o[4];
-    cs_layout(blockDim.x / CS_GT, mt, a.max_n, o);
-    uint32_t *Wp = reinterpret_cast<uint32_t *>(smem + o[0]);
-    uint64_t *never = reinterpret_cast<uint64_t *>(smem + o[1]);
-    double *s_corr = reinterpret_cast<double *>(smem + o[2]);           // [CS_MAX_TEAMS]
-    uint32_t *s_bnd = reinterpret_cast<uint32_t *>(s_corr + CS_MAX_TEAMS); // [CS_MAX_TEAMS]
-    volatile uint32_t *s_abort = s_bnd + CS_MAX_TEAMS;
+    const CsShared h = cs_shared(smem, mt, a.max_n);
+    uint32_t *Wp = h.Wp;
     uint32_t *tab = g_item_tab;
 
     const GroupDesc gd = a.groups[blockIdx.x];
     const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
     const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t bar = 2 + g;
-    unsigned char *teams = smem + o[3];
-    const size_t tbytes = cs_team_bytes(mt);
-    const CsTeam tm = cs_team(teams + (size_t)g * tbytes, mt);
+    const CsTeam tm = cs_team(h.teams + (size_t)g * h.tbytes, mt);
     const bool active = g < nch;
-    const bool split = !T3 || gd.loop_set != 1u;   // the basic loops run as PLL and DLL parts
 
     for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
-    if (active) {
-        const uint32_t prn = gd.prn[g];
-        for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = gd.taps[(size_t)g * nt + i];
-        for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = a.tb.code[(size_t)prn * EXT_WORDS + i];
-        for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
-            reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)prn * CS_LMAX)[i];
-        for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
-            tm.tmask[i] = a.tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
-            tm.tcoarse[i] = a.tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
-            tm.tbits[i] = a.tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
-        }
-        for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = gd.acc_blocks[g] ? gd.acc[(size_t)g * per_ch + i] : 0;
-        if (t == 0) {
-            tm.u[0] = gd.theta[g];
-            tm.u[1] = (uint32_t)gd.w[g];
-            tm.u[2] = (uint32_t)gd.r[g];
-            tm.u[3] = gd.acc_blocks[g];
-            tm.u[4] = gd.epochs[g];
-            // the taps with the least and the greatest offset (the transition-major reference
-            // and the end of the taps' union range)
-            uint32_t lo = 0, hi = 0;
-            for (uint32_t k = 1; k < nt; ++k) {
-                const int64_t o = gd.taps[(size_t)g * nt + k];
-                if (o < gd.taps[(size_t)g * nt + lo]) lo = k;
-                if (o > gd.taps[(size_t)g * nt + hi]) hi = k;
-            }
-            tm.u[5] = lo;
-            tm.u[6] = hi;
-            tm.phi[0] = gd.phi[g];
-            tm.d[0] = gd.v[g];
-            tm.d[1] = gd.fcarr[g];
-            tm.d[2] = gd.fcode[g];
-        }
-    }
+    if (active) cs_team_load(t, tm, gd, g, a.tb);
     if (threadIdx.x == 0) {
-        *s_abort = 0u;
-        mbar_init(never, 1);
+        *h.s_abort = 0u;
+        mbar_init(h.never, 1);
     }
     __syncthreads();
 
@@ -681,9 +818,8 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
         cs_prefix_share(base, N, a16, a4, Wp, warp, nw);
     }
     bool ok = true;
-    if (a.stall && blockIdx.x == 0 && warp == 0) ok = pipe_wait(never, 0u, s_abort, a.err, a.timeout_ns, 0u);
+    if (a.stall && blockIdx.x == 0 && warp == 0) ok = pipe_wait(h.never, 0u, h.s_abort, a.err, a.timeout_ns, 0u);
     ok = __syncthreads_and(ok);
-    const LoopConsts lc = gd.lc;
     for (uint32_t b = 0; ok && b < a.n_blocks; ++b) {
         const int8_t *blk = base + (size_t)b * blk_bytes;
         if (threadIdx.x == 0 && b + 1 < a.n_blocks) prefetch_l2(blk + blk_bytes, blk_bytes);
@@ -692,66 +828,11 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
             team_sync(bar);
             cs_channel_block(t, bar, tm, Wp, blk, N, nt, gd.prn[g], a.tb, tab);
             team_sync(bar);                               // the block's sums are in tm.acc
-            // fold the block into the integrate-and-dump sums; dump at the boundary
-            const bool boundary = tm.u[3] + 1 == gd.L;
-            const uint32_t ep = tm.u[4];
-            const bool store = boundary && (gd.dump_wrap || ep < gd.dump_slots);
-            int32_t *dst = gd.dumps + (uint64_t)(gd.dump_wrap ? ep % gd.dump_slots : ep) * gd.dump_stride +
-                           (uint64_t)g * per_ch;
-            for (uint32_t e = t; e < per_ch; e += CS_GT) {
-                const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
-                if (boundary) {
-                    tm.acc[e] = (int32_t)val;
-                    tm.run[e] = 0;
-                    if (store) dst[e] = (int32_t)val;
-                } else {
-                    tm.run[e] = (int32_t)val;
-                }
-            }
-            if (t == 0) {
-                // the NCOs advance over the block with the words the block was correlated with
-                tm.u[0] = tm.u[0] + N * tm.u[1];
-                tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)N * tm.u[2]);
-                s_bnd[g] = boundary ? 1u : 0u;
-                if (!boundary) tm.u[3] = tm.u[3] + 1;
-            }
+            cs_team_fold(t, tm, gd, g, h.s_bnd);
         }
         __syncthreads();                                  // every channel's sums and flags are in place
-        if (warp == 0) {
-            // the loops of channel `lane` (PLL part, or the whole loop set of Table 3)
-            const uint32_t j = lane;
-            const bool doit = j < nch && s_bnd[j];
-            PllOut po{0.0, 0.0};
-            LoopOut o3{};
-            const CsTeam tj = cs_team(teams + (size_t)(doit ? j : 0) * tbytes, mt);
-            if (doit) {
-                if (split) po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
-                else o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
-            }
-            pair_sync();                                  // the DLL parts are in s_corr
-            if (doit) {
-                const LoopOut lo = split ? loop_finish(po, s_corr[j], lc) : o3;
-                tj.d[0] = lo.v;
-                tj.d[1] = lo.f_carr;
-                tj.d[2] = lo.f_code;
-                tj.u[1] = (uint32_t)lo.w;
-                tj.u[2] = (uint32_t)lo.r;
-                tj.u[4] = tj.u[4] + 1;
-                tj.u[3] = 0;
-            }
-        } else if (warp == 1) {
-            // DLL parts: the early and late envelopes of channel lane / 2 on two lanes
-            const uint32_t j = lane >> 1;
-            const bool doit = split && j < nch && s_bnd[j];
-            double m = 0.0;
-            const CsTeam tj = cs_team(teams + (size_t)(doit ? j : 0) * tbytes, mt);
-            if (doit) {
-                const uint32_t k = (lane & 1u) ? (uint32_t)gd.tap_l : (uint32_t)gd.tap_e;
-                m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
-            }
-            const double ml = __shfl_down_sync(0xffffffffu, m, 1);
-            if (doit && (lane & 1u) == 0u) s_corr[j] = loop_dll(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], lc);
-            pair_sync();
+        if (warp < 2) {
+            cs_loops<T3>(warp, threadIdx.x & 31, gd, h, mt);
         } else if (b + 1 < a.n_blocks) {
             // the next block's prefix sums, by every other warp
             const int8_t *nblk = blk + blk_bytes;
@@ -760,19 +841,60 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
         }
         __syncthreads();                                  // new words and the next prefix sums in place
     }
-    if (active) {
-        if (t == 0) {
-            gd.theta[g] = tm.u[0];
-            gd.w[g] = (int32_t)tm.u[1];
-            gd.r[g] = tm.u[2];
-            gd.acc_blocks[g] = tm.u[3];
-            gd.epochs[g] = tm.u[4];
-            gd.phi[g] = tm.phi[0];
-            gd.v[g] = tm.d[0];
-            gd.fcarr[g] = tm.d[1];
-            gd.fcode[g] = tm.d[2];
+    if (active) cs_team_store(t, tm, gd, g);
+}
+
+// Serving form: persistent CTAs take the tick's items (one block of one group each) by
+// ticket.  An item first waits, with a time limit, until its group has finished the block
+// before it (an earlier ticket, so its CTA is resident), loads the group's state, builds
+// the block's prefix sums with every warp, correlates one channel per team, closes the
+// loops, stores the state and publishes the group's new block count.
+template <bool T3>
+__global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_serve_cs(CsServeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_ticket, s_stop;
+    const uint32_t mt = a.max_taps;
+    const CsShared h = cs_shared(smem, mt, a.max_n);
+    uint32_t *tab = g_item_tab;
+    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
+    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t bar = 2 + g;
+    const CsTeam tm = cs_team(h.teams + (size_t)g * h.tbytes, mt);
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_ticket = atomicAdd(a.ticket, 1u);
+        __syncthreads();
+        const uint32_t q = s_ticket;
+        if (q >= a.n_items) return;
+        const ServeItem it = a.items[q];
+        if (threadIdx.x == 0) s_stop = wait_counter(a.done + it.group, it.seq, a.err, a.timeout_ns, q, it.group);
+        __syncthreads();
+        if (s_stop) return;
+        const GroupDesc gd = a.groups[it.group];
+        const uint32_t nt = gd.ntaps, N = gd.N, per_ch = 2 * nt;
+        const bool active = g < gd.nch;
+        if (active) cs_team_load(t, tm, gd, g, a.tb);
+        const int8_t *blk = a.ring + it.off;
+        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+        cs_prefix_share(blk, N, a16, a4, h.Wp, warp, nw);
+        __syncthreads();                                  // prefix sums and every team's state in place
+        if (active) {
+            for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+            team_sync(bar);
+            cs_channel_block(t, bar, tm, h.Wp, blk, N, nt, gd.prn[g], a.tb, tab);
+            team_sync(bar);
+            cs_team_fold(t, tm, gd, g, h.s_bnd);
         }
-        for (uint32_t i = t; i < per_ch; i += CS_GT) gd.acc[(size_t)g * per_ch + i] = tm.run[i];
+        __syncthreads();
+        if (warp < 2) cs_loops<T3>(warp, threadIdx.x & 31, gd, h, mt);
+        __syncthreads();
+        if (active) cs_team_store(t, tm, gd, g);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(a.done + it.group, it.seq + 1);
+        }
     }
 }
 
@@ -800,7 +922,43 @@ cudaError_t cs_go(uint32_t threads, uint32_t grid, size_t smem, cudaStream_t str
     return cudaGetLastError();
 }
 
+template <bool T3>
+int cs_serve_occ(uint32_t threads, size_t smem) {
+    auto kern = k_serve_cs<T3>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, (int)threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <bool T3>
+cudaError_t cs_serve_go(uint32_t threads, uint32_t grid, size_t smem, cudaStream_t stream, const CsServeArgs &a) {
+    auto kern = k_serve_cs<T3>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int cs_serve_occupancy(uint32_t cpg, size_t smem, bool table3) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return 0;
+    return table3 ? cs_serve_occ<true>(cs_threads(cpg), smem) : cs_serve_occ<false>(cs_threads(cpg), smem);
+}
+
+cudaError_t cs_serve_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, bool table3,
+                            const CsServeArgs &a) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return cudaErrorInvalidValue;
+    return table3 ? cs_serve_go<true>(cs_threads(cpg), grid, smem, stream, a)
+                  : cs_serve_go<false>(cs_threads(cpg), grid, smem, stream, a);
+}
 
 uint32_t cs_max_channels() { return CS_MAX_TEAMS; }
 uint32_t cs_threads(uint32_t cpg) { return CS_GT * (cpg < 1 ? 1u : cpg); }

@@ -479,6 +479,35 @@ int cs_occupancy(uint32_t cpg, size_t smem, bool table3);
 // One CTA per group (grid = number of groups).
 cudaError_t cs_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsArgs &a);
 
+// One work item of the serving form: block `seq` (counted from admission) of a group,
+// at byte offset `off` of the device ring.
+struct ServeItem {
+    uint32_t group;
+    uint32_t seq;
+    uint64_t off;
+};
+
+// The carrier-segment form in the serving loop: persistent CTAs of cpg teams take the
+// tick's items by ticket; an item waits until its group has finished block seq - 1.
+struct CsServeArgs {
+    const GroupDesc *groups;
+    const ServeItem *items;
+    const int8_t *ring;
+    Tables tb;
+    uint32_t *ticket;
+    uint32_t *err;             // [4]
+    uint32_t *done;            // per group: blocks completed since admission
+    uint32_t n_items;
+    uint32_t max_taps;
+    uint32_t max_n;
+    uint64_t timeout_ns;
+};
+
+// Resident serving CTAs per SM (0: the configuration does not fit).
+int cs_serve_occupancy(uint32_t cpg, size_t smem, bool table3);
+cudaError_t cs_serve_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, bool table3,
+                            const CsServeArgs &a);
+
 // ----------------------------------------------------------------------------
 // Balanced schedule (rx_balance.cu)
 // ----------------------------------------------------------------------------

@@ -37,12 +37,6 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-struct ServeItem {
-    uint32_t group;
-    uint32_t seq;     // block number of the group since admission
-    uint64_t off;     // byte offset of the block in the device ring
-};
-
 struct ServeArgs {
     const GroupDesc *groups;
     const ServeItem *items;
@@ -175,6 +169,9 @@ struct rx_serve_s {
     const rxh::DeviceTables *tables = nullptr;
     cudaStream_t stream = nullptr;
     uint32_t cpg = 2, max_groups = 0;
+    bool seg = false;                             // the carrier-segment serving kernel
+    size_t cs_smem = 0;
+    int cs_occ[2] = {0, 0};                       // its resident CTAs per SM (basic, Table 3 loops)
     size_t slot_bytes = 0;
     uint32_t n_slots = 0;
     // device memory
@@ -411,8 +408,10 @@ rx_status launch_tick(rx_serve s, std::unique_lock<std::mutex> &lk) {
     s->next_buf = (s->next_buf + 1) % kMaxInflight;
     ServeItem *hi = s->h_items[buf];
     uint32_t n = 0;
+    bool table3 = false;
     for (const Pending &p : blocks) {
         const Stream &st = s->streams[p.stream];
+        table3 = table3 || st.desc.loop_set == RX_LOOPS_TABLE3;
         for (uint32_t g : st.groups) {
             hi[n].group = g;
             hi[n].seq = p.seq;
@@ -451,25 +450,44 @@ rx_status launch_tick(rx_serve s, std::unique_lock<std::mutex> &lk) {
         cudaGetLastError();
         return serr(s, RX_ECUDA, rxh::fmt("tick copies: %s", cudaGetErrorString(e)));   // relocked on return
     }
-    ServeArgs a;
-    a.groups = s->d_groups;
-    a.items = s->d_items[buf];
-    a.ring = s->d_ring;
-    a.tb = Tables{s->tables->code, s->tables->tab, s->tables->pair, s->tables->tlist, s->tables->tmask, s->tables->tcoarse,
-                   s->tables->tbits};
-    a.ticket = s->d_scratch[buf];
-    a.err = s->d_scratch[buf] + 1;
-    a.done = s->d_done;
-    a.n_items = n;
-    a.cpg = s->cpg;
-    a.max_taps = s->cfg.max_taps;
-    a.timeout_ns = 2000000000ull;
-    const size_t smem = item_smem_bytes(s->cpg, s->cfg.max_taps, kThreads);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve<kThreads>, kThreads, smem);
-    uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((uint32_t)std::max(occ, 1) * s->tables->sm_count, n));
-    k_serve<kThreads><<<grid, kThreads, smem, s->stream>>>(a);
-    e = cudaGetLastError();
+    const Tables tb{s->tables->code, s->tables->tab, s->tables->pair, s->tables->tlist, s->tables->tmask,
+                    s->tables->tcoarse, s->tables->tbits};
+    if (s->seg) {
+        CsServeArgs a;
+        a.groups = s->d_groups;
+        a.items = s->d_items[buf];
+        a.ring = s->d_ring;
+        a.tb = tb;
+        a.ticket = s->d_scratch[buf];
+        a.err = s->d_scratch[buf] + 1;
+        a.done = s->d_done;
+        a.n_items = n;
+        a.max_taps = s->cfg.max_taps;
+        a.max_n = s->cfg.max_block_samples;
+        a.timeout_ns = 2000000000ull;
+        const uint32_t grid = std::max<uint32_t>(
+            1, std::min<uint32_t>((uint32_t)std::max(s->cs_occ[table3 ? 1 : 0], 1) * s->tables->sm_count, n));
+        e = cs_serve_launch(s->cpg, grid, s->cs_smem, s->stream, table3, a);
+    } else {
+        ServeArgs a;
+        a.groups = s->d_groups;
+        a.items = s->d_items[buf];
+        a.ring = s->d_ring;
+        a.tb = tb;
+        a.ticket = s->d_scratch[buf];
+        a.err = s->d_scratch[buf] + 1;
+        a.done = s->d_done;
+        a.n_items = n;
+        a.cpg = s->cpg;
+        a.max_taps = s->cfg.max_taps;
+        a.timeout_ns = 2000000000ull;
+        const size_t smem = item_smem_bytes(s->cpg, s->cfg.max_taps, kThreads);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve<kThreads>, kThreads, smem);
+        uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((uint32_t)std::max(occ, 1) * s->tables->sm_count, n));
+        k_serve<kThreads><<<grid, kThreads, smem, s->stream>>>(a);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_err[buf], s->d_scratch[buf] + 1, 16, cudaMemcpyDeviceToHost, s->stream);
     Tick t;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
@@ -510,7 +528,8 @@ extern "C" rx_status rx_serve_create(const rx_serve_config *cfg, rx_serve *out) 
     if (cfg->max_streams == 0 || cfg->max_streams > (1u << 20) || cfg->hbm_budget_bytes < (1u << 20) ||
         cfg->ring_blocks < 4 || cfg->max_block_samples == 0 || cfg->max_block_samples > RX_MAX_BLOCK_SAMPLES ||
         cfg->max_taps == 0 || cfg->max_taps > RX_MAX_TAPS || cfg->max_channels_per_stream == 0 ||
-        cfg->dump_slots == 0 || cfg->channels_per_item > 64)
+        cfg->dump_slots == 0 || cfg->channels_per_item > 64 || cfg->form > RX_SERVE_FORM_SEGMENT ||
+        cfg->reserved != 0)
         return RX_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -527,7 +546,28 @@ extern "C" rx_status rx_serve_create(const rx_serve_config *cfg, rx_serve *out) 
         delete s;
         return RX_ECUDA;
     }
-    s->cpg = cfg->channels_per_item ? cfg->channels_per_item : 2;
+    // the carrier-segment kernel where it is asked for or allowed and fits: one team per
+    // channel of an item, the block's prefix sums and the teams' areas in shared memory
+    if (cfg->form != RX_SERVE_FORM_CHUNK) {
+        const uint32_t cpg = cfg->channels_per_item ? cfg->channels_per_item : 4;
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device);
+        if (cpg <= cs_max_channels()) {
+            s->cs_smem = cs_smem_bytes(cpg, cfg->max_taps, cfg->max_block_samples);
+            if (s->cs_smem <= (size_t)optin) {
+                s->cs_occ[0] = cs_serve_occupancy(cpg, s->cs_smem, false);
+                s->cs_occ[1] = cs_serve_occupancy(cpg, s->cs_smem, true);
+            }
+            s->seg = s->cs_occ[0] > 0 && s->cs_occ[1] > 0;
+            if (s->seg) s->cpg = cpg;
+        }
+        cudaGetLastError();
+        if (!s->seg && cfg->form == RX_SERVE_FORM_SEGMENT) {
+            delete s;
+            return RX_EINVAL;
+        }
+    }
+    if (!s->seg) s->cpg = cfg->channels_per_item ? cfg->channels_per_item : 2;
     const uint32_t groups_per_stream = (cfg->max_channels_per_stream + s->cpg - 1) / s->cpg;
     s->max_groups = cfg->max_streams * groups_per_stream;
     s->slot_bytes = align_up(2 * (size_t)cfg->max_block_samples, kAlign);
@@ -550,7 +590,7 @@ extern "C" rx_status rx_serve_create(const rx_serve_config *cfg, rx_serve *out) 
     }
     for (int b = 0; b < kMaxInflight; ++b) std::memset(s->h_err[b], 0, 16);
     const size_t smem = item_smem_bytes(s->cpg, cfg->max_taps, kThreads);
-    if (smem > 48 * 1024)
+    if (!s->seg && smem > 48 * 1024)
         cudaFuncSetAttribute(k_serve<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     s->pool = new Pool(cfg->hbm_budget_bytes);
     s->streams.resize(cfg->max_streams);

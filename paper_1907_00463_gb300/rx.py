@@ -25,6 +25,9 @@ RX_SCHED_STATIC = 1
 RX_SCHED_PIPE = 2
 RX_SCHED_BALANCED = 3
 RX_SCHED_SEGMENT = 4
+RX_SERVE_FORM_AUTO = 0
+RX_SERVE_FORM_CHUNK = 1
+RX_SERVE_FORM_SEGMENT = 2
 RX_WAIT_TEST_STALL = 1
 RX_EPOCH_BLOCKS = 0
 RX_EPOCH_CODE = 1
@@ -96,7 +99,7 @@ class rx_serve_config(C.Structure):
                 ("max_taps", C.c_uint32), ("max_block_samples", C.c_uint32),
                 ("ring_blocks", C.c_uint32), ("dump_slots", C.c_uint32),
                 ("channels_per_item", C.c_uint32), ("device", C.c_int32),
-                ("hbm_budget_bytes", C.c_uint64)]
+                ("hbm_budget_bytes", C.c_uint64), ("form", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class rx_plain_replay_stats(C.Structure):
@@ -585,10 +588,10 @@ def rx_track_static(descs, iq, rx_byte_offset, n_blocks: int, state, tap_offsets
 def rx_serve_create(max_streams: int, max_channels_per_stream: int, max_taps: int,
                     max_block_samples: int, ring_blocks: int = 4096, dump_slots: int = 64,
                     channels_per_item: int = 0, hbm_budget_bytes: int = 1 << 30,
-                    device: int = 0):
+                    device: int = 0, form: int = RX_SERVE_FORM_AUTO):
     lib = load()
     cfg = rx_serve_config(max_streams, max_channels_per_stream, max_taps, max_block_samples,
-                          ring_blocks, dump_slots, channels_per_item, device, hbm_budget_bytes)
+                          ring_blocks, dump_slots, channels_per_item, device, hbm_budget_bytes, form, 0)
     s = P()
     st = lib.rx_serve_create(C.byref(cfg), C.byref(s))
     if st != RX_OK:

@@ -363,3 +363,45 @@ def test_segment_form_takes_any_words(tiles):
     finally:
         rx.rx_batch_destroy(b)
     _check_against_oracle(recv, sigs, res, 4)
+
+
+@pytest.mark.parametrize("tiles", [(2, 128, 0, rx.RX_SCHED_SEGMENT), (6, 128, 0, rx.RX_SCHED_SEGMENT)])
+def test_segment_form_at_slow_words(tiles):
+    """Code words around the segment form's limits (below 2^16 it takes the direct form;
+    above it the float boundary estimates must stay exact, with the transition-major
+    items gated on a tap span below 2^17 code words) and carrier words of a few units
+    (the first sample of a carrier segment from a tiny |w|), the loops held for the whole
+    run (one integration of 4 blocks) so that the words stay as set: every dump and final
+    state bit-exact with the oracle."""
+    g = np.random.Generator(np.random.Philox(key=[463088, 2]))
+    code_words = [1, 1 << 15, (1 << 16) - 1, 1 << 16, (1 << 16) + 1, 1 << 17, 1 << 20, 1 << 22,
+                  (1 << 22) + 12345, 1 << 23, 1 << 25, 0xFFFFFFFF]
+    carrier_words = [0, 1, -1, 150, -150, 1 << 20, -(1 << 20), 3, 70000, -70000, 7, -7]
+    recv, sigs = [], []
+    for k, fs in enumerate([4.092e6, 25.0e6]):
+        N = int(round(fs / 1000))
+        chans = []
+        for c in range(len(code_words)):
+            prn = int(g.integers(1, 33))
+            phi = int(g.integers(0, 1023 << 32))
+            if c % 3 == 0:
+                taps = sorted(int(x) for x in g.integers(-(64 << 32), (64 << 32) + 1, 5))
+                taps[2] = 0
+            else:
+                taps = [-(1 << 31), -(1 << 30), 0, 1 << 30, 1 << 31]
+            chans.append(synth.Channel(prn, carrier_words[c], phi, code_words[c], taps))
+        rec = synth.Receiver(fs, N, 4, [], chans, 4, 15.0, 1.0, 3, 2, 1, sigma=0.0,
+                             meta={"workload": "slow words", "fs": fs})
+        recv.append(rec)
+        sigs.append(g.integers(-128, 128, size=(4 * N, 2)).astype(np.int8))
+    offs, total = batch_layout(recv)
+    buf = np.zeros(total, np.int8)
+    for o, s in zip(offs, sigs):
+        buf[int(o):int(o) + s.size] = s.reshape(-1)
+    b = _batch(recv, 4, tiles)
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 4)
+        res = _read(b, recv, 4)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, res, 4)

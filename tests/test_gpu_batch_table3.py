@@ -148,13 +148,14 @@ def test_balanced_and_static_forms_refuse_table3():
     assert e.value.status == rx.RX_EINVAL
 
 
-def test_served_table3_stream_matches_oracle():
+@pytest.mark.parametrize("form", [rx.RX_SERVE_FORM_CHUNK, rx.RX_SERVE_FORM_SEGMENT])
+def test_served_table3_stream_matches_oracle(form):
     """A served stream with Table 3's loops next to a basic-loop stream: dumps, state
     and health of each bit-exact with the oracle."""
     r3 = synth.serving_stream(5, n_blocks=40)
     rb = synth.serving_stream(6, n_blocks=40)
     iq3, iqb = synth.generate_iq(r3).numpy(), synth.generate_iq(rb).numpy()
-    s = rx.rx_serve_create(8, 16, 8, 8184, ring_blocks=128, dump_slots=64)
+    s = rx.rx_serve_create(8, 16, 8, 8184, ring_blocks=128, dump_slots=64, form=form)
     try:
         id3, a3 = rx.rx_serve_admit(s, rx.receiver_desc(r3, 1, WINDOW, FLL), *synth.channel_arrays(r3))
         idb, ab = rx.rx_serve_admit(s, rx.receiver_desc(rb), *synth.channel_arrays(rb))

@@ -18,14 +18,18 @@ def _lib():
     __graft_entry__.build()
 
 
+FORMS = [pytest.param(rx.RX_SERVE_FORM_CHUNK, id="chunk"), pytest.param(rx.RX_SERVE_FORM_SEGMENT, id="segment")]
+
+
 def _admit(s, r):
     return rx.rx_serve_admit(s, rx.receiver_desc(r), *synth.channel_arrays(r))
 
 
-def test_served_stream_matches_oracle():
+@pytest.mark.parametrize("form", FORMS)
+def test_served_stream_matches_oracle(form):
     r = synth.serving_stream(3, n_blocks=30)
     iq = synth.generate_iq(r).numpy()
-    s = rx.rx_serve_create(8, 16, 8, 25000, ring_blocks=64, dump_slots=64)
+    s = rx.rx_serve_create(8, 16, 8, 25000, ring_blocks=64, dump_slots=64, form=form)
     try:
         sid, active = _admit(s, r)
         assert active
@@ -52,14 +56,15 @@ def _stream_dict(r, iq, max_blocks=0, churn=False):
                 churn=churn)
 
 
-def test_alone_equals_in_the_mix():
+@pytest.mark.parametrize("form", FORMS)
+def test_alone_equals_in_the_mix(form):
     target = synth.serving_stream(0, n_blocks=40)
     tiq = synth.generate_iq(target).numpy()
     others = [synth.serving_stream(k, n_blocks=8) for k in range(1, 64)]
     oiq = [synth.generate_iq(o).numpy() for o in others]
     results = []
     for mix in (False, True):
-        s = rx.rx_serve_create(128, 16, 8, 25000, ring_blocks=4096, dump_slots=64)
+        s = rx.rx_serve_create(128, 16, 8, 25000, ring_blocks=4096, dump_slots=64, form=form)
         try:
             streams = [_stream_dict(target, tiq, max_blocks=40)]
             if mix:
@@ -87,14 +92,15 @@ def test_alone_equals_in_the_mix():
     assert_states_equal(results[1][1], os_)
 
 
-def test_admission_is_bounded_by_the_memory_budget():
+@pytest.mark.parametrize("form", FORMS)
+def test_admission_is_bounded_by_the_memory_budget(form):
     r = synth.serving_stream(0, n_blocks=2)
     # per-stream footprint of a 12-channel, 5-tap stream with 64 dump slots: state arrays,
     # taps, running sums and the dump ring, each 16-byte aligned, rounded to 256 bytes
     one = 4 * 48 + 48 + 5 * 96 + 2 * 480 + 64 * 12 * 5 * 8
     per = (one + 255) // 256 * 256
     s = rx.rx_serve_create(64, 16, 8, 25000, ring_blocks=64, dump_slots=64,
-                           hbm_budget_bytes=1 << 20)
+                           hbm_budget_bytes=1 << 20, form=form)
     try:
         cap = rx.rx_serve_get_stats(s)["pool_bytes_total"] // per
         assert cap == 32
@@ -117,7 +123,8 @@ def test_admission_is_bounded_by_the_memory_budget():
         rx.rx_serve_destroy(s)
 
 
-def test_multicorrelator_stream_served_alone_and_in_the_mix():
+@pytest.mark.parametrize("form", FORMS)
+def test_multicorrelator_stream_served_alone_and_in_the_mix(form):
     """A 101-tap stream at 25 MHz (the signal-quality multicorrelator workload) through
     the same request loop: bit-exact with the oracle when served alone and when its
     blocks arrive as a Poisson process among 15 other such streams."""
@@ -128,7 +135,7 @@ def test_multicorrelator_stream_served_alone_and_in_the_mix():
     results = []
     for mix in (False, True):
         s = rx.rx_serve_create(32, 16, 101, 25000, ring_blocks=1024, dump_slots=32,
-                               hbm_budget_bytes=1 << 30)
+                               hbm_budget_bytes=1 << 30, form=form)
         try:
             streams = [_stream_dict(target, tiq, max_blocks=20)]
             if mix:
@@ -192,3 +199,17 @@ def test_plain_replay_tracks_every_arrival():
     # 8 streams x ~1 kHz x 0.2 s = ~1600 arrivals
     assert 1100 < out["blocks_done"] < 2100
     assert 0 < out["p50_ms"] <= out["p99_ms"] <= out["max_ms"]
+
+
+def test_serving_forms_and_limits():
+    """The carrier-segment serving kernel is what AUTO takes where it fits; a request for
+    it is refused where its shared memory cannot fit (prefix sums of a block of 2^20
+    samples), and a config with unknown form or a reserved field set is refused."""
+    s = rx.rx_serve_create(4, 16, 8, 25000, ring_blocks=8, dump_slots=8, form=rx.RX_SERVE_FORM_SEGMENT)
+    rx.rx_serve_destroy(s)
+    with pytest.raises(rx.RxError):
+        rx.rx_serve_create(4, 16, 8, 1 << 20, ring_blocks=8, dump_slots=8, form=rx.RX_SERVE_FORM_SEGMENT)
+    s = rx.rx_serve_create(4, 16, 8, 1 << 20, ring_blocks=8, dump_slots=8)      # AUTO: the chunk forms
+    rx.rx_serve_destroy(s)
+    with pytest.raises(rx.RxError):
+        rx.rx_serve_create(4, 16, 8, 25000, ring_blocks=8, dump_slots=8, form=3)
