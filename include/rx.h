@@ -814,7 +814,7 @@ const char *rx_acq_last_error(rx_acq a);
 /* Hand-over from a search result to a tracking channel (Sec. 3.3: tracking
  * starts on the coarsely found channels).  Host arithmetic, no device work:
  *   f = carrier_word fs / 2^32;  f_code = 1.023e6 + f / 1540
- *   *code_rate_out   = rn(f_code 2^32 / fs)   (round half even, clamped to [0, 2^40])
+ *   *code_rate_out   = rn(f_code 2^32 / fs)   (round half even, clamped to [0, 2^32 - 1])
  *   *code_phase_word = ((N - c) mod N) r0 + n_ms N (*code_rate_out)  (mod 1023 2^32)
  * i.e. the received code phase at the first sample after the buffer; the
  * carrier word is the bin's own.  code_rate_word 0 = rn(1.023e6 / fs 2^32). */

@@ -361,11 +361,11 @@ void orc_track(orc_chan *ch, const int32_t *acc, const int64_t *tap_off,
 
     double xw = f_carr * sfs;
     double xr = f_code * sfs;
-    /* words: carrier wraps modulo 2^32, code rate clamped to [0, 2^40] */
+    /* words: carrier wraps modulo 2^32, code rate clamped to [0, 2^32 - 1] (the range set-up accepts) */
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
     if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
     ch->w = (int32_t)(uint32_t)(uint64_t)(int64_t)nearbyint(xw);
     ch->r = (uint64_t)nearbyint(xr);
     ch->f_carr = f_carr;
@@ -510,7 +510,7 @@ void orc_track_table3(orc_chan *ch, orc_ext *ex, const int32_t *acc, const int64
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
     if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
     ch->w = (int32_t)(uint32_t)(uint64_t)(int64_t)nearbyint(xw);
     ch->r = (uint64_t)nearbyint(xr);
     ch->f_carr = f_carr;
@@ -764,7 +764,7 @@ void orc_acq_handoff(int32_t w, uint32_t code_phase, uint32_t N, uint32_t n_ms, 
     double sfs = 4294967296.0 / fs;
     double xr = f_code * sfs;
     if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
     *r = (uint64_t)nearbyint(xr);
     uint32_t lag = code_phase % N;
     lag = lag == 0 ? 0 : N - lag;

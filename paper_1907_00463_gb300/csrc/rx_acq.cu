@@ -726,7 +726,7 @@ extern "C" rx_status rx_acq_handoff(double fs_hz, uint32_t block_samples, uint32
     double sfs = 4294967296.0 / fs_hz;
     double xr = f_code * sfs;
     if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
     uint64_t r = (uint64_t)std::nearbyint(xr);
     uint32_t lag = code_phase % block_samples;
     lag = lag == 0 ? 0 : block_samples - lag;

@@ -375,13 +375,31 @@ static __constant__ float kAtanMid[64] = {
 static __constant__ double kAtanSeries[5] = {0.15915494309189535, -0.05305164769729845, 0.03183098861837907,
                                              -0.022736420441699334, 0.017683882565766147};
 
+// Where atan_cycles reads its tables: constant memory (AtanConst), or a copy the
+// caller keeps in shared memory (AtanShared: the midpoint search indexes differently on
+// every lane, which constant memory serialises).  The same values either way.
+struct AtanConst {
+    __device__ __forceinline__ float mid(int j) const { return kAtanMid[j]; }
+    __device__ __forceinline__ double tan(int k) const { return kAtanTan[k]; }
+    __device__ __forceinline__ double ser(int j) const { return kAtanSeries[j]; }
+};
+struct AtanShared {
+    const float *m;      // [64]
+    const double *t;     // [65]
+    const double *s;     // [5]
+    __device__ __forceinline__ float mid(int j) const { return m[j]; }
+    __device__ __forceinline__ double tan(int k) const { return t[k]; }
+    __device__ __forceinline__ double ser(int j) const { return s[j]; }
+};
+
 // atan(q / i) / (2 pi), in cycles, i != 0, two-quadrant, by table-driven argument
 // reduction: with a = |q|, b = |i| (swapped if a > b: atan(x) = pi/2 - atan(1/x)),
 // k = the number of midpoints at or below a/b (single-precision estimate, binary
 // search), atan(a/b) = k pi/256 + atan(t), t = (a - c_k b) / (b + c_k a), and
 // atan(t) / (2 pi) from the Gregory series to t^9 by Estrin's scheme.  k pi/256 is
 // k / 512 cycles and pi/2 is 1/4 cycle, exactly.  One division.
-__device__ __forceinline__ double atan_cycles(double q, double i) {
+template <class Tab>
+__device__ __forceinline__ double atan_cycles_t(double q, double i, const Tab &tb) {
     double a = fabs(q), b = fabs(i);
     const bool swap = a > b;
     if (swap) {
@@ -393,8 +411,8 @@ __device__ __forceinline__ double atan_cycles(double q, double i) {
     int k = 0;
 #pragma unroll
     for (int step = 32; step >= 1; step >>= 1)
-        if (rf >= kAtanMid[k + step - 1]) k += step;
-    const double c = kAtanTan[k];
+        if (rf >= tb.mid(k + step - 1)) k += step;
+    const double c = tb.tan(k);
     double num = __dmul_rn(c, b);
     num = __dsub_rn(a, num);
     double den = __dmul_rn(c, a);
@@ -402,11 +420,11 @@ __device__ __forceinline__ double atan_cycles(double q, double i) {
     const double t = __ddiv_rn(num, den);
     const double u = __dmul_rn(t, t);
     const double u2 = __dmul_rn(u, u);
-    double p01 = __dmul_rn(kAtanSeries[1], u);
-    p01 = __dadd_rn(kAtanSeries[0], p01);
-    double p23 = __dmul_rn(kAtanSeries[3], u);
-    p23 = __dadd_rn(kAtanSeries[2], p23);
-    const double p4 = __dmul_rn(kAtanSeries[4], u2);
+    double p01 = __dmul_rn(tb.ser(1), u);
+    p01 = __dadd_rn(tb.ser(0), p01);
+    double p23 = __dmul_rn(tb.ser(3), u);
+    p23 = __dadd_rn(tb.ser(2), p23);
+    const double p4 = __dmul_rn(tb.ser(4), u2);
     double hi = __dadd_rn(p23, p4);
     hi = __dmul_rn(hi, u2);
     const double p = __dadd_rn(p01, hi);
@@ -416,6 +434,8 @@ __device__ __forceinline__ double atan_cycles(double q, double i) {
     if ((q < 0.0) != (i < 0.0)) y = -y;
     return y;
 }
+
+__device__ __forceinline__ double atan_cycles(double q, double i) { return atan_cycles_t(q, i, AtanConst{}); }
 
 // Per-receiver loop constants, computed on the host once per integration length:
 //   T = n_accum / fs, w0 = Bn_pll / 0.53, k1 = (w0 w0) T, k2 = sqrt2 w0,
@@ -457,11 +477,12 @@ struct PllOut {
     double v, f_carr;
 };
 
-__device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc) {
+template <class Tab>
+__device__ __forceinline__ PllOut loop_pll_t(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc, const Tab &tb) {
     const double ip = (double)ipr, qp = (double)qpr;
     double e_pll;
     if (ip != 0.0) {
-        e_pll = atan_cycles(qp, ip);
+        e_pll = atan_cycles_t(qp, ip, tb);
     } else {
         e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
     }
@@ -469,6 +490,10 @@ __device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, c
     v = __dadd_rn(v, dv);
     const double df = __dmul_rn(lc.k2, e_pll);
     return PllOut{v, __dadd_rn(v, df)};
+}
+
+__device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc) {
+    return loop_pll_t(v, ipr, qpr, lc, AtanConst{});
 }
 
 // Envelope of one DLL tap, sqrt(I^2 + Q^2).
@@ -492,24 +517,43 @@ __device__ __forceinline__ double loop_dll(double mag_e, double mag_l, int64_t o
     return __dmul_rn(lc.kdll, e_dll);
 }
 
-// The code frequency and both quantised words.
-__device__ __forceinline__ LoopOut loop_finish(PllOut p, double corr, const LoopConsts &lc) {
-    LoopOut o;
+// The code frequency and both quantised words, in two parts: what needs only the PLL
+// (the carrier word and the carrier-aided code frequency before the DLL correction), and
+// what needs the DLL correction too.  Independent operations, each rounded as written.
+struct FinishPre {
+    double v, f_carr, aided;     // aided = 1.023e6 + f_carr / 1540
+    int32_t w;
+};
+
+__device__ __forceinline__ FinishPre loop_finish_pre(PllOut p, const LoopConsts &lc) {
+    FinishPre o;
     const double aid = __dmul_rn(p.f_carr, RXD_KAID);
-    double f_code = __dadd_rn(1.023e6, aid);
-    f_code = __dadd_rn(f_code, corr);
+    o.aided = __dadd_rn(1.023e6, aid);
     double xw = __dmul_rn(p.f_carr, lc.sfs);
-    double xr = __dmul_rn(f_code, lc.sfs);
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
-    if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
     o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
-    o.r = (uint64_t)__double2ll_rn(xr);
     o.v = p.v;
     o.f_carr = p.f_carr;
+    return o;
+}
+
+__device__ __forceinline__ LoopOut loop_finish_post(const FinishPre &q, double corr, const LoopConsts &lc) {
+    LoopOut o;
+    const double f_code = __dadd_rn(q.aided, corr);
+    double xr = __dmul_rn(f_code, lc.sfs);
+    if (!(xr > 0.0)) xr = 0.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
+    o.w = q.w;
+    o.r = (uint64_t)__double2ll_rn(xr);
+    o.v = q.v;
+    o.f_carr = q.f_carr;
     o.f_code = f_code;
     return o;
+}
+
+__device__ __forceinline__ LoopOut loop_finish(PllOut p, double corr, const LoopConsts &lc) {
+    return loop_finish_post(loop_finish_pre(p, lc), corr, lc);
 }
 
 __device__ __forceinline__ LoopOut loop_update(double v, int32_t ie, int32_t qe, int32_t ipr,
@@ -646,7 +690,7 @@ __device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t i
     if (xw > 9.0e18) xw = 9.0e18;
     if (xw < -9.0e18) xw = -9.0e18;
     if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 1099511627776.0) xr = 1099511627776.0;
+    if (xr > 4294967295.0) xr = 4294967295.0;
     o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
     o.r = (uint64_t)__double2ll_rn(xr);
     o.v = v;

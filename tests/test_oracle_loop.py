@@ -125,6 +125,22 @@ def test_requantisation_rounds_half_to_even():
         assert out.w == expect
 
 
+def test_code_word_is_clamped_to_the_range_set_up_accepts():
+    """A code frequency of fs or more (over one chip per sample) gives the largest word
+    set-up accepts, 2^32 - 1; a negative one gives 0.  The carrier word keeps wrapping."""
+    fs = 1.2e6
+    ch = oracle.chan_init(0, 0, 1 << 30, fs)
+    for v, want in ((1540.0 * 2e6, TWO32 - 1), (-1540.0 * 2e6, 0)):
+        ch.v = v
+        out = oracle.track(ch, _acc(10, 0), TAPS, 2, 1, 0, fs, 1200, 15.0, 1.0)
+        assert abs(out.f_code - (1.023e6 + v / 1540.0)) < 1e-9 * abs(v)
+        assert out.r == want
+    # just inside: a code frequency a little below fs keeps its rounded word
+    ch.v = 1540.0 * (fs * 0.999 - 1.023e6)
+    out = oracle.track(ch, _acc(10, 0), TAPS, 2, 1, 0, fs, 1200, 15.0, 1.0)
+    assert out.r == int(np.rint(out.f_code / fs * TWO32)) < TWO32
+
+
 def _true_code_phase(sv, t):
     dop = sv.doppler_hz * t + 0.5 * sv.doppler_rate_hz_s * t * t
     return (sv.code_phase_chips + 1.023e6 * t + dop / 1540.0) % 1023
