@@ -548,7 +548,8 @@ def config1_leg(rx, synth, dev, stream, cpu_leg: bool) -> dict:
 
 
 def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stream, steps: int, warmup: int,
-                       peak_tops: float, cpu_leg: bool, cpu_receivers: int, workload: str) -> dict:
+                       peak_tops: float, cpu_leg: bool, cpu_receivers: int, workload: str,
+                       tiles: str = "") -> dict:
     """One batched workload through the same path as the headline: seeded receivers
     generated on the device, autotuned tiles, one persistent launch per step (graph
     replay), the direct-model roofline, the end-to-end rate with host buffers, and the
@@ -565,7 +566,11 @@ def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stre
     try:
         for i, r in enumerate(receivers):
             rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
-        tiles, probe_ms = rx.rx_batch_autotune(b, buf, offs, min(64, n_blocks))
+        if tiles:
+            rx.rx_batch_set_tiles(b, *[int(x) for x in tiles.split(",")])
+            probe_ms = None
+        else:
+            _, probe_ms = rx.rx_batch_autotune(b, buf, offs, min(64, n_blocks))
         for _ in range(warmup):
             rx.rx_batch_run(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
         rx.rx_batch_sync(b)
@@ -987,11 +992,12 @@ def run_ours(args):
                 "128 receivers, fs in {2.046, 4.092, 8.184, 16.368, 25} MHz, 4-32 channels x 3-7 taps at "
                 "0.1-0.5 chip, integration 1-20 ms, C/N0 25-50 dB-Hz, Doppler +-5 kHz at 0-50 Hz/s, 1 s")
         if not args.no_config5:
+            nb5 = args.config5_blocks
             multicorr = batched_config_leg(
-                rx, synth, "multicorrelator", [synth.multicorrelator_receiver(i, n_blocks=2000) for i in range(16)],
-                2000, dev, stream, 3, args.warmup, peak_tops, cpu_on, 16,
-                "16 receivers x 16 channels x 101 taps (+-2.5 chip at 0.05 chip), fs 25 MHz, 2 s, "
-                "second path per PRN (0.1-1 chip, -3..-10 dB, +0-20 Hz)")
+                rx, synth, "multicorrelator", [synth.multicorrelator_receiver(i, n_blocks=nb5) for i in range(16)],
+                nb5, dev, stream, 3, args.warmup, peak_tops, cpu_on, 16,
+                f"16 receivers x 16 channels x 101 taps (+-2.5 chip at 0.05 chip), fs 25 MHz, {nb5 / 1000:g} s, "
+                "second path per PRN (0.1-1 chip, -3..-10 dB, +0-20 Hz)", tiles=args.config5_tiles)
         if not args.no_serve:
             serving5 = serving_multicorrelator_leg(rx, synth, dev)
 
@@ -1092,6 +1098,11 @@ def main():
     p.add_argument("--no-config1", action="store_true")
     p.add_argument("--no-config3", action="store_true")
     p.add_argument("--no-config5", action="store_true")
+    p.add_argument("--config5-blocks", type=int, default=2000,
+                   help="blocks per receiver of the multicorrelator workload (2000 = 2 s)")
+    p.add_argument("--config5-tiles", default="",
+                   help="channels_per_item,threads,ctas_per_sm,schedule for the multicorrelator leg "
+                        "(default: autotuned)")
     p.add_argument("--acq-receivers", type=int, default=N_RX,
                    help="receivers searched by the acquisition leg (default: all of the workload)")
     args = p.parse_args()

@@ -57,6 +57,14 @@ constexpr int bal_min_blocks() { return NT == 128 ? 4 : (NT == 192 || NT == 224)
 template <int NT>
 __global__ void __launch_bounds__(NT + 32 * bal_filter_warps<NT>(), bal_min_blocks<NT>()) k_batch_bal(BalArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    if (a.probe) {                       // placement probe: no work, no waits
+        if (threadIdx.x == 0) {
+            uint32_t smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            a.probe[blockIdx.x] = smid;
+        }
+        return;
+    }
     const uint32_t ms = a.maxseg, mt = a.max_taps, per = mt * 2;
     const ItemSmem sm = carve_item_smem(smem, ms, mt, NT);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + item_smem_bytes(ms, mt, NT));

@@ -414,6 +414,45 @@ uint32_t bal_default_per_sm(uint32_t nt) { return nt == 128 ? 4 : (nt == 192 || 
 
 // Balanced schedule: cut the (channel, chunk) sequence, receiver by receiver, into
 // equal-cost slices, one per CTA, and build each CTA's segment list.
+// Launch the balanced kernel once as a placement probe (same registers, threads and
+// shared memory, so the same residency) and check that every SM holds exactly per_sm of
+// its P CTAs.  1: even; 0: not (why says how); -1: a CUDA error.
+int bal_placement_even(rx_batch b, uint32_t P, uint32_t per_sm, size_t smem, std::string &why) {
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, (size_t)P * 4) != cudaSuccess) {
+        cudaGetLastError();
+        why = "placement probe: no device memory";
+        return -1;
+    }
+    BalArgs la{};
+    la.probe = d;
+    la.k = per_sm;
+    la.n_groups = (uint32_t)b->tables->sm_count;
+    std::vector<uint32_t> h(P, 0xffffffffu);
+    cudaError_t e = bal_launch(b->threads, P, smem, b->stream, la);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, (size_t)P * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        why = rxh::fmt("placement probe: %s", cudaGetErrorString(e));
+        return -1;
+    }
+    std::map<uint32_t, uint32_t> per;
+    for (uint32_t v : h) per[v] += 1;
+    for (const auto &kv : per)
+        if (kv.second != per_sm || kv.first >= 1024) {
+            why = rxh::fmt("uneven placement: SM %u holds %u of the %u CTAs (%u per SM expected)", kv.first, kv.second,
+                           P, per_sm);
+            return 0;
+        }
+    if (per.size() != (size_t)b->tables->sm_count) {
+        why = rxh::fmt("uneven placement: %zu SMs hold CTAs, %d expected", per.size(), b->tables->sm_count);
+        return 0;
+    }
+    return 1;
+}
+
 rx_status build_balanced(rx_batch b) {
     std::string &E = b->err;
     const uint32_t sms = (uint32_t)b->tables->sm_count;
@@ -559,6 +598,15 @@ rx_status build_balanced(rx_batch b) {
                 return berr(b, RX_EINVAL,
                             rxh::fmt("tile shape does not fit on an SM (%u CTAs of %zu bytes, %d fit)", per_sm,
                                      smem, occ));
+            continue;
+        }
+        // the kernel's work map assumes exactly per_sm CTAs on every SM; check the placement
+        // of this launch shape once here, instead of meeting an uneven one as a device timeout
+        std::string why;
+        const int even = bal_placement_even(b, P, per_sm, smem, why);
+        if (even < 0) return berr(b, RX_ECUDA, why);
+        if (even == 0) {
+            if (b->ctas_per_sm) return berr(b, RX_EINVAL, why);
             continue;
         }
         std::vector<SegDesc> flat((size_t)P * maxseg);

@@ -30,16 +30,20 @@
 // holds (K_I, K_Q, packed rotation) such that, for every sample n - 1 in it,
 //   M(n) = (dp2a.lo(V(n-1), R) + K_I, dp2a.hi(V(n-1), R) + K_Q)        (mod 2^32).
 // Threads walk contiguous sample ranges, break them at carrier crossings and group
-// starts, and combine their range totals in a CTA-wide scan.  Finally each thread takes
-// code transitions from the per-PRN transition list, finds the sample b where the tap
-// reaches the transition (one float estimate of ceil((j 2^32 - frac) / r) and one exact
-// integer correction), and adds +-M(b).
+// starts, and combine their range totals in a CTA-wide scan.  Finally the threads take
+// code transitions from the per-PRN transition list and add +-M(b) at the sample b where
+// a tap reaches each.  Taps go in groups of eight.  For each transition of the union of
+// a group's chip ranges, one float estimate of ceil((j 2^32 - frac) / r) and one exact
+// integer correction give the sample at which the group's reference tap (its least
+// offset) reaches it, and the remainder of that division gives every other tap's sample
+// by one comparison (cs_items_tm).  A group whose taps span too many samples for the
+// float estimates goes tap by tap instead (cs_items), each tap with its own estimate.
 //
 // All sums are modulo 2^32, so the results equal the direct per-sample definition bit
 // for bit.  A channel-block the form does not cover (a carrier word so large that the
-// block has more than CS_SEG_MAX segments, a block of more than 65536 samples, or a
-// code word that would leave the extended chip axis) is correlated by the direct form
-// instead, with the same result.
+// block has more than CS_SEG_MAX segments, a block of more than 65536 samples, a code
+// word below 2^16, or one that would leave the extended chip axis) is correlated by the
+// direct form instead, with the same result.
 //
 // Work organisation.  A CTA owns a group of up to six channels of one receiver for the
 // whole run, and each channel has a team of GT threads with its own named barrier that
@@ -50,8 +54,15 @@
 // two lanes), and every other warp builds the next block's prefix sums into the one
 // buffer: a loop update costs the SM's FP64 pipe per warp instruction whatever the
 // active lanes, so one pass over all channels costs no more than one.  Two CTA-wide
-// barriers a block separate the phases.  The only wait that can fail is the test hook's
+// barriers a block separate the phases.  The part of the loop update that needs only
+// the PLL (the carrier word, the carrier-aided code frequency) is done by warp 0 before
+// it waits for the DLL part.  The only wait that can fail is the test hook's
 // (RX_WAIT_TEST_STALL): it is bounded and reports a time-out.
+//
+// The serving form (k_serve_cs) runs the same phases per work item: persistent CTAs
+// take (group, block) items by ticket, wait (bounded) for the group's previous block,
+// load its state, build the block's prefix sums, correlate a channel per team, close the
+// loops and store the state.
 //
 // Shared-memory layout of the prefix sums: sample n is at word n ^ (4 ((n >> 5) & 7)),
 // which keeps every run of four words together (for 16-byte stores) and spreads the
@@ -737,13 +748,18 @@ __device__ __forceinline__ void cs_loops(uint32_t warp, uint32_t lane, const Gro
         PllOut po{0.0, 0.0};
         LoopOut o3{};
         const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        FinishPre fp{};
         if (doit) {
-            if (split) po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
-            else o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
+            if (split) {
+                po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
+                fp = loop_finish_pre(po, lc);         // the part that does not wait for the DLL
+            } else {
+                o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
+            }
         }
         pair_sync();                                  // the DLL parts are in s_corr
         if (doit) {
-            const LoopOut lo = split ? loop_finish(po, h.s_corr[j], lc) : o3;
+            const LoopOut lo = split ? loop_finish_post(fp, h.s_corr[j], lc) : o3;
             tj.d[0] = lo.v;
             tj.d[1] = lo.f_carr;
             tj.d[2] = lo.f_code;

@@ -375,21 +375,12 @@ static __constant__ float kAtanMid[64] = {
 static __constant__ double kAtanSeries[5] = {0.15915494309189535, -0.05305164769729845, 0.03183098861837907,
                                              -0.022736420441699334, 0.017683882565766147};
 
-// Where atan_cycles reads its tables: constant memory (AtanConst), or a copy the
-// caller keeps in shared memory (AtanShared: the midpoint search indexes differently on
-// every lane, which constant memory serialises).  The same values either way.
+// The atan's tables in constant memory (atan_cycles_t takes any source with the same
+// three accessors).
 struct AtanConst {
     __device__ __forceinline__ float mid(int j) const { return kAtanMid[j]; }
     __device__ __forceinline__ double tan(int k) const { return kAtanTan[k]; }
     __device__ __forceinline__ double ser(int j) const { return kAtanSeries[j]; }
-};
-struct AtanShared {
-    const float *m;      // [64]
-    const double *t;     // [65]
-    const double *s;     // [5]
-    __device__ __forceinline__ float mid(int j) const { return m[j]; }
-    __device__ __forceinline__ double tan(int k) const { return t[k]; }
-    __device__ __forceinline__ double ser(int j) const { return s[j]; }
 };
 
 // atan(q / i) / (2 pi), in cycles, i != 0, two-quadrant, by table-driven argument

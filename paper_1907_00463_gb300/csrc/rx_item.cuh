@@ -540,6 +540,7 @@ struct BalArgs {
     uint32_t n_groups;         // SM groups = SMs
     uint32_t *sm_map;          // [2 * 1024]: per %smid, group + 1 and the next slot; zeroed per run
     uint32_t *next_group;      // zeroed per run
+    uint32_t *probe;           // non-null: placement probe; CTA i writes its %smid to probe[i] and returns
 };
 
 size_t bal_smem_bytes(uint32_t maxseg, uint32_t mt, uint32_t nt);

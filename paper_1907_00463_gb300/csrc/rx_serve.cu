@@ -728,6 +728,58 @@ rx_status push_block(rx_serve s, uint32_t id, const int8_t *block, Clock::time_p
     return RX_OK;
 }
 
+// Several blocks at once (the replay producers' arrivals that are due): the slots and
+// sequence numbers of all of them under one acquisition of the lock, the copies outside
+// it, and the pending entries under a second one.  A stream's blocks are taken in order:
+// once one of them is refused, its later ones in the batch are refused too.  ok[i] says
+// whether block i was accepted.
+struct PushReq {
+    uint32_t id;
+    const int8_t *block;
+    Clock::time_point arrival;
+};
+
+void push_blocks(rx_serve s, const PushReq *rq, uint32_t n, uint8_t *ok) {
+    std::vector<uint32_t> slot(n), seq(n);
+    std::vector<size_t> bytes(n);
+    std::vector<uint32_t> refused;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (uint32_t i = 0; i < n; ++i) {
+            ok[i] = 0;
+            const uint32_t id = rq[i].id;
+            if (id >= s->cfg.max_streams || std::find(refused.begin(), refused.end(), id) != refused.end())
+                continue;
+            Stream &st = s->streams[id];
+            const uint32_t sl = (uint32_t)(s->slot_head % s->n_slots);
+            if (st.state != kActive || s->slot_busy[sl]) {
+                if (st.state == kActive) ++s->dropped;
+                refused.push_back(id);
+                continue;
+            }
+            s->slot_busy[sl] = 1;
+            ++s->slot_head;
+            slot[i] = sl;
+            seq[i] = st.seq_next++;
+            st.pushed += 1;
+            bytes[i] = 2 * (size_t)st.desc.block_samples;
+            ok[i] = 1;
+        }
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        if (ok[i]) std::memcpy(s->h_ring + (size_t)slot[i] * s->slot_bytes, rq[i].block, bytes[i]);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const auto now = Clock::now();
+        for (uint32_t i = 0; i < n; ++i) {
+            if (!ok[i]) continue;
+            s->lag_us.push_back(std::chrono::duration<float, std::micro>(now - rq[i].arrival).count());
+            s->pending.push_back(Pending{slot[i], rq[i].id, seq[i], rq[i].arrival});
+        }
+    }
+    s->cv.notify_one();
+}
+
 }  // namespace
 
 extern "C" rx_status rx_serve_push(rx_serve s, uint32_t id, const int8_t *block) {
@@ -942,7 +994,10 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
         };
         std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> pq;
         std::vector<double> rate(n, 0.0);
-        std::vector<uint64_t> sent(n, 0);
+        std::vector<uint64_t> sent(n, 0), inbatch(n, 0);
+        std::vector<PushReq> batch;
+        std::vector<uint32_t> keys;
+        std::vector<uint8_t> okv;
         for (uint32_t k = tid; k < n; k += nthr) {
             rate[k] = cfg->rate_hz * (1.0 - cfg->rate_jitter + 2.0 * cfg->rate_jitter * U(rng));
             pq.push({-std::log(1.0 - U(rng)) / rate[k], k});
@@ -977,13 +1032,33 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
                 next_churn += -std::log(1.0 - U(rng)) / (cfg->churn_per_s / nthr);
                 continue;
             }
-            pq.pop();
-            const uint32_t k = ev.k;
-            if (rs[k].max_blocks == 0 || sent[k] < rs[k].max_blocks) {
-                const uint64_t blk = sent[k] % rs[k].rec_blocks;
-                const int8_t *src = rs[k].recording + blk * 2 * (uint64_t)rs[k].desc->block_samples;
-                if (push_block(s, ids[k], src, when, true) == RX_OK) sent[k] += 1;
-                pq.push({ev.t - std::log(1.0 - U(rng)) / rate[k], k});
+            // every arrival of this producer that is due (before the next churn event) goes
+            // out as one batch; a producer that has fallen behind pushes larger batches
+            const double t_now = std::chrono::duration<double>(Clock::now() - t0).count();
+            batch.clear();
+            keys.clear();
+            while (!pq.empty() && pq.top().t <= std::max(t_now, ev.t) && pq.top().t < next_churn) {
+                const Ev e = pq.top();
+                const auto at = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(e.t));
+                if (at >= t_end) break;
+                pq.pop();
+                const uint32_t k = e.k;
+                if (rs[k].max_blocks == 0 || sent[k] + inbatch[k] < rs[k].max_blocks) {
+                    const uint64_t blk = (sent[k] + inbatch[k]) % rs[k].rec_blocks;
+                    batch.push_back(
+                        PushReq{ids[k], rs[k].recording + blk * 2 * (uint64_t)rs[k].desc->block_samples, at});
+                    keys.push_back(k);
+                    inbatch[k] += 1;
+                    pq.push({e.t - std::log(1.0 - U(rng)) / rate[k], k});
+                }
+            }
+            if (!batch.empty()) {
+                okv.assign(batch.size(), 0);
+                push_blocks(s, batch.data(), (uint32_t)batch.size(), okv.data());
+                for (size_t i = 0; i < batch.size(); ++i) {
+                    sent[keys[i]] += okv[i];
+                    inbatch[keys[i]] = 0;
+                }
             }
         }
     };
