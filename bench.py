@@ -49,6 +49,8 @@ N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 # of the kernel's source files at the capture; when the sources differ from it the
 # figures describe another kernel, and the line reports them as null.
 PROFILED = {
+    ("segment", 128, 3): {"bytes_per_rx_block": 34944, "thread_inst_per_sample_channel": 11.4,
+                          "src_sha256": "8ead9d31167ee8cf3f4fe5e8fb7bf1e3d643c8133cdcdd55a4ddeccafcd69e66"},
     ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
                             "src_sha256": "capture predates source hashing"},
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
