@@ -452,8 +452,12 @@ def serving_multicorrelator_leg(rx, synth, dev, n_streams=16, duration_s=2.0, re
     s = rx.rx_serve_create(n_streams + 4, 16, 101, 25000, ring_blocks=4096, dump_slots=8,
                            hbm_budget_bytes=1 << 30, device=dev.index or 0)
     try:
-        rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=0.2, seed=463005,
-                           producer_threads=max(2, min(8, cores - 4)))
+        warm = rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=0.2, seed=463005,
+                                  producer_threads=max(2, min(8, cores - 4)))
+        for sid in warm:                 # the warm-up's streams leave; the timed replay admits fresh ones
+            if sid != 0xFFFFFFFF:
+                rx.rx_serve_release(s, int(sid))
+        rx.rx_serve_drain(s)
         rx.rx_serve_reset_stats(s)
         rx.rx_serve_replay(s, streams, rate_hz=1000.0, rate_jitter=0.1, duration_s=duration_s, seed=463006,
                            producer_threads=max(2, min(8, cores - 4)))

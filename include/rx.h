@@ -543,7 +543,9 @@ rx_status rx_serve_destroy(rx_serve s);
 /* Admit a stream with its starting channel state (arrays as in
  * rx_set_channels).  *id receives the stream id in both outcomes: RX_OK = the
  * stream is active; RX_EBUDGET = it is queued and becomes active by itself
- * when released streams free enough of the budget (FIFO). */
+ * when released streams free enough of the budget (FIFO).  RX_EAGAIN: all
+ * max_streams slots are taken (active, queued or releasing); nothing is
+ * admitted or queued and *id is not written. */
 rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *desc, const uint8_t *prn,
                          const int32_t *carrier_word, const uint64_t *code_phase_word,
                          const uint64_t *code_rate_word, const int64_t *tap_offsets,
@@ -623,8 +625,12 @@ typedef struct {
 
 /* Admit the n streams, run the arrival processes for duration_s, then drain.
  * Each block is pushed with its scheduled arrival (rx_serve_push_at), so its
- * latency counts from when it was due, not from when a producer got to it.
- * ids_out (optional, n entries) receives each stream's final id. */
+ * latency counts from when it was due, not from when a producer got to it;
+ * each producer pushes the arrivals that are due together.  Streams stay
+ * admitted afterwards.  A stream that finds no free stream slot is not
+ * replayed.  ids_out (optional, n entries) receives each stream's final id,
+ * 0xFFFFFFFF for a stream that was not replayed.  Blocks of one stream go to
+ * the device in order whatever the interleaving of pushes. */
 rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *streams, uint32_t n,
                           const rx_replay_config *cfg, uint32_t *ids_out);
 

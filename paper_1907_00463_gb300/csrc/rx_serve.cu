@@ -138,6 +138,8 @@ struct Stream {
     size_t pool_off = 0, pool_bytes = 0;
     std::vector<uint32_t> groups;
     uint32_t seq_next = 0;        // next block sequence number (per group, all groups alike)
+    uint32_t seq_ticked = 0;      // next sequence number a tick may take (ticks take each stream's
+                                  // blocks in order, without gaps)
     uint64_t pushed = 0, done = 0;
     uint64_t misses = 0;          // blocks completed more than 1 ms after their push
     // device arrays (inside the pool)
@@ -337,6 +339,7 @@ rx_status activate(rx_serve s, uint32_t id) {
     }
     st.state = kActive;
     st.seq_next = 0;
+    st.seq_ticked = 0;
     st.pushed = st.done = st.misses = 0;
     return RX_OK;
 }
@@ -402,8 +405,42 @@ void reap(rx_serve s, bool block) {
 // record the tick.
 rx_status launch_tick(rx_serve s, std::unique_lock<std::mutex> &lk) {
     rxh::TraceRange trace_("rx_serve_tick");
-    std::vector<Pending> blocks;
-    blocks.swap(s->pending);
+    // Each stream's blocks go into ticks in sequence order and without gaps: an item waits
+    // for its group's previous block, which must be in this tick or an earlier one.  A
+    // block whose predecessor is not pending yet (its push still copying, from another
+    // thread) stays pending for a later tick.
+    std::vector<Pending> blocks, keep;
+    {
+        std::vector<Pending> all;
+        all.swap(s->pending);
+        for (const Pending &p : all) {
+            Stream &st = s->streams[p.stream];
+            if (p.seq == st.seq_ticked) {
+                st.seq_ticked += 1;
+                blocks.push_back(p);
+            } else {
+                keep.push_back(p);
+            }
+        }
+        // a kept block may follow one taken above (pushes of one stream that crossed)
+        bool more = true;
+        while (more && !keep.empty()) {
+            more = false;
+            for (auto it = keep.begin(); it != keep.end();) {
+                Stream &st = s->streams[it->stream];
+                if (it->seq == st.seq_ticked) {
+                    st.seq_ticked += 1;
+                    blocks.push_back(*it);
+                    it = keep.erase(it);
+                    more = true;
+                } else {
+                    ++it;
+                }
+            }
+        }
+        s->pending.swap(keep);
+    }
+    if (blocks.empty()) return RX_EAGAIN;     // nothing can go yet: the missing pushes are copying
     const int buf = s->next_buf;
     s->next_buf = (s->next_buf + 1) % kMaxInflight;
     ServeItem *hi = s->h_items[buf];
@@ -511,7 +548,8 @@ void service_loop(rx_serve s) {
     for (;;) {
         reap(s, false);
         if (!s->pending.empty() && (int)s->inflight.size() < kMaxInflight) {
-            launch_tick(s, lk);
+            if (launch_tick(s, lk) != RX_EAGAIN) continue;
+            s->cv.wait_for(lk, std::chrono::microseconds(5));
             continue;
         }
         if (s->stop && s->pending.empty() && s->inflight.empty()) break;
@@ -652,7 +690,7 @@ extern "C" rx_status rx_serve_admit(rx_serve s, const rx_receiver_desc *d, const
     std::lock_guard<std::mutex> lk(s->mu);
     uint32_t k = 0;
     while (k < s->streams.size() && s->streams[k].state != kFree) ++k;
-    if (k == s->streams.size()) return serr(s, RX_EBUDGET, "all stream slots in use");
+    if (k == s->streams.size()) return serr(s, RX_EAGAIN, "all stream slots in use");
     Stream &st = s->streams[k];
     st.desc = *d;
     const size_t C = d->n_channels, T = d->n_taps;
@@ -977,8 +1015,8 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
         uint32_t id = 0;
         rx_status r = rx_serve_admit(s, rs[k].desc, rs[k].prn, rs[k].carrier_word, rs[k].code_phase_word,
                                      rs[k].code_rate_word, rs[k].tap_offsets, &id);
-        if (r != RX_OK && r != RX_EBUDGET) return r;
-        ids[k] = id;
+        if (r != RX_OK && r != RX_EBUDGET && r != RX_EAGAIN) return r;
+        ids[k] = r == RX_EAGAIN ? 0xffffffffu : id;       // no free stream slot: not replayed
     }
     const uint32_t nthr = std::max<uint32_t>(1, std::min<uint32_t>(cfg->producer_threads ? cfg->producer_threads : 4, n));
     const auto t0 = Clock::now() + std::chrono::milliseconds(2);
@@ -1000,7 +1038,8 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
         std::vector<uint8_t> okv;
         for (uint32_t k = tid; k < n; k += nthr) {
             rate[k] = cfg->rate_hz * (1.0 - cfg->rate_jitter + 2.0 * cfg->rate_jitter * U(rng));
-            pq.push({-std::log(1.0 - U(rng)) / rate[k], k});
+            const double first = -std::log(1.0 - U(rng)) / rate[k];
+            if (ids[k] != 0xffffffffu) pq.push({first, k});
         }
         // churn: each producer handles its share of leave/join events
         double next_churn = cfg->churn_per_s > 0 ? -std::log(1.0 - U(rng)) / (cfg->churn_per_s / nthr) : 1e300;
@@ -1017,7 +1056,7 @@ extern "C" rx_status rx_serve_replay(rx_serve s, const rx_replay_stream *rs, uin
                 // a random stream of this producer leaves and a fresh copy of it joins
                 std::vector<uint32_t> mine;
                 for (uint32_t k = tid; k < n; k += nthr)
-                    if (rs[k].churn) mine.push_back(k);
+                    if (rs[k].churn && ids[k] != 0xffffffffu) mine.push_back(k);
                 if (!mine.empty()) {
                     const uint32_t k = mine[(size_t)(U(rng) * mine.size()) % mine.size()];
                     rx_serve_release(s, ids[k]);

@@ -213,3 +213,63 @@ def test_serving_forms_and_limits():
     rx.rx_serve_destroy(s)
     with pytest.raises(rx.RxError):
         rx.rx_serve_create(4, 16, 8, 25000, ring_blocks=8, dump_slots=8, form=3)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pushes_of_one_stream_from_several_threads(form):
+    """Four threads push one stream's blocks at once.  A push takes its sequence number
+    under the server's lock and joins the pending list after its copy, so pushes that
+    cross can reach the pending list out of order; ticks must still take each stream's
+    blocks in order (an item waits for its group's previous block, bounded).  Every
+    block is the same 1 ms of signal, so the result is defined whatever the order: the
+    oracle's run over that block repeated."""
+    import threading
+    r = synth.serving_stream(2, n_blocks=1)
+    blk = synth.generate_iq(r).numpy()
+    n_threads, per = 4, 40
+    s = rx.rx_serve_create(4, 16, 8, 25000, ring_blocks=512, dump_slots=n_threads * per, form=form)
+    try:
+        sid, active = _admit(s, r)
+        assert active
+
+        def pusher():
+            for _ in range(per):
+                while rx.rx_serve_push(s, sid, blk) != rx.RX_OK:
+                    pass
+        th = [threading.Thread(target=pusher) for _ in range(n_threads)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        rx.rx_serve_drain(s)
+        d = rx.rx_serve_read_dumps(s, sid, 12, 5, n_threads * per)
+        st = rx.rx_serve_read_state(s, sid, 12)
+        stats = rx.rx_serve_get_stats(s)
+    finally:
+        rx.rx_serve_destroy(s)
+    assert stats["device_timeouts"] == 0 and stats["blocks_done"] == n_threads * per
+    rep = synth.Receiver(r.fs, r.block_samples, n_threads * per, r.svs, r.channels, r.integ_blocks,
+                         r.pll_bn, r.dll_bn, r.tap_early, r.tap_prompt, r.tap_late, meta=r.meta)
+    od, os_ = oracle_run(rep, np.tile(blk, (n_threads * per, 1)))
+    assert np.array_equal(d, od)
+    assert_states_equal(st, os_)
+
+
+def test_admission_without_a_free_slot_is_refused():
+    """With every stream slot taken, admission says so (RX_EAGAIN) instead of queueing,
+    and a replay skips such a stream (its id is reported as 0xFFFFFFFF)."""
+    r = synth.serving_stream(0, n_blocks=4)
+    iq = synth.generate_iq(r).numpy()
+    s = rx.rx_serve_create(2, 16, 8, 25000, ring_blocks=64, dump_slots=8)
+    try:
+        a, _ = _admit(s, r)
+        b, _ = _admit(s, r)
+        with pytest.raises(rx.RxError) as e:
+            _admit(s, r)
+        assert "RX_EAGAIN" in str(e.value)
+        ids = rx.rx_serve_replay(s, [_stream_dict(r, iq)], rate_hz=1000.0, rate_jitter=0.1, duration_s=0.02,
+                                 seed=1)
+        assert ids == [0xFFFFFFFF]
+        assert rx.rx_serve_get_stats(s)["device_timeouts"] == 0
+    finally:
+        rx.rx_serve_destroy(s)
