@@ -270,6 +270,7 @@ struct rx_batch_s {
     uint32_t *d_cnum = nullptr;     // [channels]
     uint32_t *d_cerr = nullptr;     // [1]
     CodeWalk *d_walks = nullptr;    // [channels]
+    CsCodeGroup *d_cgroups = nullptr;  // [channels]: the carrier-segment walk's channel groups
     uint32_t code_cap = 0;          // epochs per channel the ring holds
     uint32_t last_mode = 0;         // 0: nothing run or restart pending, 1: blocks, 2: code periods
     std::string err;
@@ -923,7 +924,8 @@ extern "C" rx_status rx_batch_destroy(rx_batch b) {
     drop_graph(b);
     void *ptrs[] = {b->d_state, b->d_snap,  b->d_prn,   b->d_taps,  b->d_dumps, b->d_groups,
                     b->d_rxoff, b->d_scratch, b->d_stage, b->d_segs, b->d_nseg, b->d_xpart,
-                    b->d_xflag, b->d_smmap, b->d_cdump, b->d_clen, b->d_cnum, b->d_cerr, b->d_walks};
+                    b->d_xflag, b->d_smmap, b->d_cdump, b->d_clen, b->d_cnum, b->d_cerr, b->d_walks,
+                    b->d_cgroups};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_err) cudaFreeHost(b->h_err);
@@ -1486,8 +1488,9 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
         cap = std::max(cap, rxh::code_ring_epochs(d.fs_hz, (uint64_t)n_blocks * d.block_samples));
     if (cap > b->code_cap || !b->d_walks) {
         for (void *q : {(void *)b->d_cdump, (void *)b->d_clen, (void *)b->d_cnum, (void *)b->d_cerr,
-                        (void *)b->d_walks})
+                        (void *)b->d_walks, (void *)b->d_cgroups})
             if (q) cudaFree(q);
+        b->d_cgroups = nullptr;
         b->d_cdump = nullptr;
         b->d_clen = b->d_cnum = b->d_cerr = nullptr;
         b->d_walks = nullptr;
@@ -1496,7 +1499,8 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
             cudaMalloc(&b->d_clen, (size_t)cap * b->n_ch * 4) != cudaSuccess ||
             cudaMalloc(&b->d_cnum, (size_t)b->n_ch * 4) != cudaSuccess ||
             cudaMalloc(&b->d_cerr, 4) != cudaSuccess ||
-            cudaMalloc(&b->d_walks, (size_t)b->n_ch * sizeof(CodeWalk)) != cudaSuccess) {
+            cudaMalloc(&b->d_walks, (size_t)b->n_ch * sizeof(CodeWalk)) != cudaSuccess ||
+            cudaMalloc(&b->d_cgroups, (size_t)b->n_ch * sizeof(CsCodeGroup)) != cudaSuccess) {
             cudaGetLastError();
             return berr(b, RX_ENOMEM, "code-period epoch ring");
         }
@@ -1544,7 +1548,33 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
     if (flags & RX_RUN_RESTART)
         RX_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->d_snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), E);
     RX_CUDA_TRY(cudaMemsetAsync(b->d_cerr, 0, 4, b->stream), E);
-    RX_CUDA_TRY(rxh::launch_code_walks(b->d_walks, b->n_ch, b->max_taps, b->tables, b->stream), E);
+    // the carrier-segment walk (one team per channel, the channels of a receiver in groups
+    // of cpg sharing each block's prefix sums) with the default tiles or RX_SCHED_SEGMENT
+    // and where its shared memory fits; otherwise one CTA per channel in the chunk forms
+    bool seg_walk = b->schedule == RX_SCHED_SEGMENT || b->schedule == RX_SCHED_DYNAMIC;
+    const uint32_t cpg = b->schedule == RX_SCHED_SEGMENT && b->cpg ? std::min(b->cpg, cs_max_channels()) : 3u;
+    uint32_t max_n = 0;
+    for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
+    const size_t cs_smem = cs_smem_bytes(cpg, b->max_taps, max_n);
+    if (seg_walk) seg_walk = max_n <= 65536 && cs_code_occupancy(cpg, cs_smem) > 0;
+    if (seg_walk) {
+        std::vector<CsCodeGroup> groups;
+        for (uint32_t r = 0; r < b->n_rx; ++r) {
+            const rx_receiver_desc &d = b->rx[r];
+            for (uint32_t c0 = 0; c0 < d.n_channels; c0 += cpg)
+                groups.push_back(CsCodeGroup{b->rx_ch0[r] + c0, std::min(cpg, d.n_channels - c0), d.block_samples,
+                                             n_blocks});
+        }
+        RX_CUDA_TRY(cudaMemcpy(b->d_cgroups, groups.data(), groups.size() * sizeof(CsCodeGroup),
+                               cudaMemcpyHostToDevice), E);
+        CsCodeArgs ca{b->d_walks, b->d_cgroups,
+                      Tables{b->tables->code, b->tables->tab, b->tables->pair, b->tables->tlist, b->tables->tmask,
+                             b->tables->tcoarse, b->tables->tbits},
+                      b->max_taps, max_n};
+        RX_CUDA_TRY(cs_code_launch(cpg, (uint32_t)groups.size(), cs_smem, b->stream, ca), E);
+    } else {
+        RX_CUDA_TRY(rxh::launch_code_walks(b->d_walks, b->n_ch, b->max_taps, b->tables, b->stream), E);
+    }
     uint32_t cerr = 0;
     RX_CUDA_TRY(cudaMemcpyAsync(&cerr, b->d_cerr, 4, cudaMemcpyDeviceToHost, b->stream), E);
     RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);

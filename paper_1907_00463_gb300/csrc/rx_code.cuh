@@ -38,6 +38,50 @@ struct CodeWalk {
     uint32_t *err;             // bit 0: ring overflow, bit 1: code word reached 2^32
 };
 
+// One closed epoch of the bit synchroniser (the rules are in rx_code_state's
+// description in rx.h).
+__device__ inline void bitsync_step(rx_code_state &b, int32_t ip, uint32_t k) {
+    const uint32_t e = b.epoch;
+    const uint32_t bin = e % 20u;
+    if (b.have_last && ((ip < 0) != (b.last_ip < 0))) {
+        b.hist[bin] += 1;
+        b.n_changes += 1;
+    }
+    b.last_ip = ip;
+    b.have_last = 1;
+    if (b.sync) {
+        if (bin == b.edge) {
+            if (b.bit_active) {
+                b.bits = (b.bits << 1) | (b.bit_acc < 0 ? 1ull : 0ull);
+                b.n_bits += 1;
+            } else {
+                b.first_bit_epoch = e;
+            }
+            b.bit_active = 1;
+            b.bit_acc = 0;
+        }
+        if (b.bit_active) b.bit_acc += ip;
+    } else {
+        uint32_t m = 0;
+        for (uint32_t j = 1; j < 20; ++j)
+            if (b.hist[j] > b.hist[m]) m = j;
+        uint32_t second = 0;
+        for (uint32_t j = 0; j < 20; ++j)
+            if (j != m && b.hist[j] > second) second = b.hist[j];
+        if (b.hist[m] >= k && b.hist[m] >= 3u * second) {
+            b.sync = 1;
+            b.edge = m;
+        }
+    }
+    b.epoch = e + 1;
+}
+
+// Channel groups of the carrier-segment walk: walks[w0 .. w0 + n) are channels of one
+// receiver (n <= 6), whose blocks of N samples the CTA shares.
+struct CsCodeGroup {
+    uint32_t w0, n, N, n_blocks;
+};
+
 namespace rxh {
 struct DeviceTables;
 

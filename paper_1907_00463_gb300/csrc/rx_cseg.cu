@@ -70,6 +70,7 @@
 // segment pass take spans of an odd number of samples for the same reason.
 #include <cuda_runtime.h>
 
+#include "rx_code.cuh"
 #include "rx_internal.h"
 #include "rx_item.cuh"
 #include "rx_sync.cuh"
@@ -162,15 +163,16 @@ __device__ __forceinline__ uint32_t cs_first(const CsChan &c, uint32_t k) {
     return n;
 }
 
-// Whether the block is covered: at most CS_SEG_MAX segments, a code word of at least
-// 2^16 (so that frac / r < 2^16 and the float boundary estimates keep their error below
-// 1/16), and every tap's chips (|offset| <= 64 chips) stay on the extended chip axis
-// with one index to spare (the transition count below the index after the last chip is
-// read).  The last chip of a tap is at most (phi >> 32) + 64 + floor((N - 1) r / 2^32) + 1.
-__device__ __forceinline__ bool cs_eligible(const CsChan &c, uint32_t N, uint64_t phi) {
-    if (N < 2 || N > CS_NMAX || c.r < 0x10000u) return false;
-    if (cs_kappa(c, N - 1) + ((N - 1) >> 8) + 1 > CS_SEG_MAX) return false;
-    const uint64_t chips = ((uint64_t)(N - 1) * c.r) >> 32;
+// Whether the range of L samples from sample o0 of the block (the NCOs at o0) is
+// covered: at most CS_SEG_MAX segments, a code word of at least 2^16 (so that frac / r <
+// 2^16 and the float boundary estimates keep their error below 1/16), and every tap's
+// chips (|offset| <= 64 chips) stay on the extended chip axis with one index to spare
+// (the transition count below the index after the last chip is read).  The last chip of
+// a tap is at most (phi >> 32) + 64 + floor((L - 1) r / 2^32) + 1.
+__device__ __forceinline__ bool cs_eligible(const CsChan &c, uint32_t o0, uint32_t L, uint64_t phi) {
+    if (L < 2 || o0 + L > CS_NMAX || c.r < 0x10000u) return false;
+    if (cs_kappa(c, L - 1) + ((o0 + L - 1) >> 8) - (o0 >> 8) + 1 > CS_SEG_MAX) return false;
+    const uint64_t chips = ((uint64_t)(L - 1) * c.r) >> 32;
     return (phi >> 32) + 65u + chips <= (uint64_t)(CS_CLEN - CS_CBASE - 2);
 }
 
@@ -246,20 +248,23 @@ __device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { retur
 // carrier crossings and group starts, sums the rotated samples (DI, DQ) and writes, for
 // each segment that starts in its span, K relative to the span's start.  Returns the
 // range of segment indices written (any = false if none).
-__device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uint32_t N, const CsChan &c,
-                                             const uint32_t *tab, uint4 *seg, uint32_t &DI, uint32_t &DQ,
-                                             uint32_t &sfirst, uint32_t &slast, bool &any) {
-    const uint32_t span = ((N + CS_GT - 1u) / CS_GT) | 1u;
-    const uint32_t p0 = t * span, p1 = min(p0 + span, N);
+__device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uint32_t o0, uint32_t L,
+                                             const CsChan &c, const uint32_t *tab, uint4 *seg, uint32_t &DI,
+                                             uint32_t &DQ, uint32_t &sfirst, uint32_t &slast, bool &any) {
+    // positions p are relative to the range's first sample o0; prefix words and 256-sample
+    // groups are the block's (n = o0 + p)
+    const uint32_t span = ((L + CS_GT - 1u) / CS_GT) | 1u;
+    const uint32_t p0 = t * span, p1 = min(p0 + span, L), g0 = o0 >> 8;
     DI = 0u;
     DQ = 0u;
     sfirst = slast = 0u;
     any = false;
     if (p0 >= p1) return;
     uint32_t kap = cs_kappa(c, p0);
-    bool start = (p0 & 255u) == 0u || cs_kappa(c, p0 - 1u) != kap;
-    uint32_t Vprev = (p0 & 255u) == 0u ? 0x80008000u : cs_v(Wp, p0 - 1u);
-    uint32_t ng = (p0 | 255u) + 1u;
+    const uint32_t n0 = o0 + p0;
+    bool start = p0 == 0u || (n0 & 255u) == 0u || cs_kappa(c, p0 - 1u) != kap;
+    uint32_t Vprev = (n0 & 255u) == 0u ? 0x80008000u : cs_v(Wp, n0 - 1u);
+    uint32_t ng = (n0 | 255u) + 1u - o0;
     uint32_t nc = c.a ? cs_first(c, kap + 1u) : 0xffffffffu;
     uint32_t p = p0;
     for (;;) {
@@ -267,13 +272,13 @@ __device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uin
         const uint32_t R = tab[cs_bin(c, kap)];
         const uint32_t vI = dp2a_lo_us(Vprev, R, 0u), vQ = dp2a_hi_us(Vprev, R, 0u);
         if (start) {
-            const uint32_t sig = kap + (p >> 8);
+            const uint32_t sig = kap + ((o0 + p) >> 8) - g0;
             seg[sig] = make_uint4(DI - vI, DQ - vQ, R, 0u);
             if (!any) sfirst = sig;
             slast = sig;
             any = true;
         }
-        const uint32_t Vq = cs_v(Wp, q - 1u);
+        const uint32_t Vq = cs_v(Wp, o0 + q - 1u);
         DI = dp2a_lo_us(Vq, R, DI) - vI;
         DQ = dp2a_hi_us(Vq, R, DQ) - vQ;
         if (q >= p1) break;
@@ -365,26 +370,26 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     return t;
 }
 
-// M(N) for the block: the segment of sample N - 1.
-__device__ __forceinline__ void cs_total(const uint32_t *Wp, const uint4 *seg, const CsChan &c, uint32_t N,
-                                         uint32_t &mI, uint32_t &mQ) {
-    const uint32_t n = N - 1u;
-    const uint4 e = seg[cs_kappa(c, n) + (n >> 8)];
-    const uint32_t V = cs_v(Wp, n);
+// M(L) for the range: the segment of its last sample.
+__device__ __forceinline__ void cs_total(const uint32_t *Wp, const uint4 *seg, const CsChan &c, uint32_t o0,
+                                         uint32_t L, uint32_t &mI, uint32_t &mQ) {
+    const uint32_t n = L - 1u;
+    const uint4 e = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
+    const uint32_t V = cs_v(Wp, o0 + n);
     mI = dp2a_lo_us(V, e.z, e.x);
     mQ = dp2a_hi_us(V, e.z, e.y);
 }
 
 // +-M(b) at one code transition (list entry e) of a tap.
 __device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsChan &c, const uint32_t *Wp,
-                                        const uint4 *seg, uint32_t &SI, uint32_t &SQ) {
+                                        const uint4 *seg, uint32_t o0, uint32_t &SI, uint32_t &SQ) {
     const uint32_t j = (e & 0x7fffu) - tp.c0p;                 // chips after the first
     const float bf = fmaf((float)j, c.Dr, -tp.F);
     uint32_t b = bf > 0.0f ? (uint32_t)ceilf(bf) : 0u;          // ceil((j 2^32 - frac) / r) or one less
     if ((uint64_t)b * c.r < (((uint64_t)j << 32) - tp.frac)) ++b;
     const uint32_t n = b - 1u;
-    const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
-    const uint32_t V = Wp[cs_sw(n)] - 0x00800080u * b;
+    const uint4 en = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
+    const uint32_t V = cs_v(Wp, o0 + n);
     uint32_t mI = dp2a_lo_us(V, en.z, en.x), mQ = dp2a_hi_us(V, en.z, en.y);
     if (e & 0x8000u) {
         mI = 0u - mI;
@@ -398,7 +403,8 @@ __device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsCha
 // running index over all taps is t mod GT), reduced per warp into red[TT][2].
 template <int TT>
 __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &run, const uint16_t *list,
-                                         const uint32_t *Wp, const uint4 *seg, const CsChan &c, int32_t *red) {
+                                         const uint32_t *Wp, const uint4 *seg, const CsChan &c, uint32_t o0,
+                                         int32_t *red) {
     uint32_t SI[TT], SQ[TT];
 #pragma unroll
     for (int k = 0; k < TT; ++k) SI[k] = SQ[k] = 0u;
@@ -411,14 +417,14 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
         for (; i + 3 * CS_GT < tk.cnt; i += 4 * CS_GT) {       // four independent items per pass
             const uint32_t e0 = L[i], e1 = L[i + CS_GT], e2 = L[i + 2 * CS_GT], e3 = L[i + 3 * CS_GT];
             uint32_t aI = 0u, aQ = 0u, bI = 0u, bQ = 0u;
-            cs_item(e0, tk, c, Wp, seg, aI, aQ);
-            cs_item(e1, tk, c, Wp, seg, bI, bQ);
-            cs_item(e2, tk, c, Wp, seg, aI, aQ);
-            cs_item(e3, tk, c, Wp, seg, bI, bQ);
+            cs_item(e0, tk, c, Wp, seg, o0, aI, aQ);
+            cs_item(e1, tk, c, Wp, seg, o0, bI, bQ);
+            cs_item(e2, tk, c, Wp, seg, o0, aI, aQ);
+            cs_item(e3, tk, c, Wp, seg, o0, bI, bQ);
             SI[k] += aI + bI;
             SQ[k] += aQ + bQ;
         }
-        for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, Wp, seg, SI[k], SQ[k]);
+        for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, Wp, seg, o0, SI[k], SQ[k]);
     }
     const uint32_t lane = t & 31;
 #pragma unroll
@@ -443,7 +449,7 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
 template <int TT>
 __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_t ref, uint32_t mx, uint32_t &run,
                                             const uint16_t *list, const uint32_t *Wp, const uint4 *seg,
-                                            const CsChan &c, uint32_t N, int32_t *red) {
+                                            const CsChan &c, uint32_t o0, uint32_t N, int32_t *red) {
     uint32_t SI[TT], SQ[TT], D[TT], Fr[TT];
 #pragma unroll
     for (int k = 0; k < TT; ++k) {
@@ -468,8 +474,8 @@ __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_
             const uint32_t bk = b - D[k] - (rho >= Fr[k] ? 1u : 0u);
             const bool valid = bk - 1u < N - 1u;
             const uint32_t n = valid ? bk - 1u : 0u;
-            const uint4 en = seg[cs_kappa(c, n) + (n >> 8)];
-            const uint32_t V = Wp[cs_sw(n)] - 0x00800080u * (n + 1u);
+            const uint4 en = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
+            const uint32_t V = cs_v(Wp, o0 + n);
             const uint32_t w = (uint32_t)(valid ? sg : 0);
             SI[k] += w * dp2a_lo_us(V, en.z, en.x);
             SQ[k] += w * dp2a_hi_us(V, en.z, en.y);
@@ -581,23 +587,26 @@ __device__ inline CsTeam cs_team(unsigned char *base, uint32_t mt) {
 }
 
 // Correlate the team's channel over one block into tm.acc (zero on entry).
-__device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
-                                                 const int8_t *blk, uint32_t N, uint32_t nt, uint32_t prn,
-                                                 const Tables &tb, const uint32_t *tab) {
+// Correlate the team's channel over the L samples from sample o0 of the block (its NCO
+// words and phases, in the team area, are those of sample o0) into tm.acc (zero on
+// entry).  Wp holds the block's prefix sums.
+__device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
+                                                 const int8_t *blk, uint32_t o0, uint32_t N, uint32_t nt,
+                                                 const uint32_t *tab) {
     const uint32_t theta = tm.u[0], w = tm.u[1], r = tm.u[2];
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
-    if (cs_eligible(c, N, phi)) {
+    if (cs_eligible(c, o0, N, phi)) {
         for (uint32_t k = t; k < nt; k += CS_GT)
             tm.tap[k] = cs_tap(c, phi, tm.taps[k], tm.taps[tm.grp[k >> 3] & 0xffffu], N, tm.tmask, tm.tcoarse,
                                tm.tbits);
         uint32_t DI, DQ, sf, sl;
         bool any;
-        cs_seg_local(t, Wp, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
+        cs_seg_local(t, Wp, o0, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
         cs_seg_scan(t, bar, DI, DQ, tm.s_warp, tm.seg, sf, sl, any);
         team_sync(bar);                                   // segment table and tap constants complete
         uint32_t mI = 0u, mQ = 0u;
-        if (t < nt) cs_total(Wp, tm.seg, c, N, mI, mQ);
+        if (t < nt) cs_total(Wp, tm.seg, c, o0, N, mI, mQ);
         for (uint32_t k = t; k < nt; k += CS_GT) {
             const int32_t g = tm.tap[k].g_end;
             atomicAdd((unsigned *)&tm.acc[2 * k], (uint32_t)g * mI);
@@ -613,28 +622,36 @@ __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const
             const CsTap *tp = tm.tap + k0;
             int32_t *rd = tm.acc + 2 * k0;
             switch ((tmj ? 8u : 0u) + min(8u, nt - k0)) {
-                case 1: cs_items<1>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 2: cs_items<2>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 3: cs_items<3>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 4: cs_items<4>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 5: cs_items<5>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 6: cs_items<6>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 7: cs_items<7>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 8: cs_items<8>(t, tp, run, tm.list, Wp, tm.seg, c, rd); break;
-                case 9: cs_items_tm<1>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 10: cs_items_tm<2>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 11: cs_items_tm<3>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 12: cs_items_tm<4>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 13: cs_items_tm<5>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 14: cs_items_tm<6>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                case 15: cs_items_tm<7>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
-                default: cs_items_tm<8>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, N, rd); break;
+                case 1: cs_items<1>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 2: cs_items<2>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 3: cs_items<3>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 4: cs_items<4>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 5: cs_items<5>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 6: cs_items<6>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 7: cs_items<7>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 8: cs_items<8>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
+                case 9: cs_items_tm<1>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 10: cs_items_tm<2>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 11: cs_items_tm<3>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 12: cs_items_tm<4>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 13: cs_items_tm<5>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 14: cs_items_tm<6>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 15: cs_items_tm<7>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                default: cs_items_tm<8>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
             }
         }
     } else {
-        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-        cs_direct(blk, N, a16, a4, theta, w, phi, r, nt, tm.taps, tm.code, tab, tm.acc);
+        const int8_t *src = blk + 2 * (size_t)o0;
+        const bool a16 = ((uintptr_t)src & 15) == 0, a4 = ((uintptr_t)src & 3) == 0;
+        cs_direct(src, N, a16, a4, theta, w, phi, r, nt, tm.taps, tm.code, tab, tm.acc);
     }
+}
+
+// The whole block (o0 = 0, N samples).
+__device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
+                                                 const int8_t *blk, uint32_t N, uint32_t nt, uint32_t prn,
+                                                 const Tables &tb, const uint32_t *tab) {
+    cs_channel_range(t, bar, tm, Wp, blk, 0u, N, nt, tab);
 }
 
 // Named barrier 15 over warps 0 and 1 (the loop-update pair).
@@ -914,6 +931,211 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_serve_cs(CsServeArg
     }
 }
 
+// Code-period epoch walk in the carrier-segment form (RX_EPOCH_CODE, batched).  A CTA
+// walks a group of channels of one receiver over the receiver's blocks.  Per block,
+// every warp builds the block's prefix sums; then each team, on its own, correlates its
+// channel in stretches: from where it stands to the end of its open epoch or of the
+// block, whichever comes first (cs_channel_range, with the NCO words of that stretch),
+// adding the sums to the open epoch's.  Where an epoch ends the team dumps the epoch's
+// sums and closes the channel's loops on its first two warps (T = that epoch's samples
+// / fs: thread 0 the PLL part and the rest, two lanes of the second warp the early and
+// late envelopes and the DLL part, joined by the team's own 64-thread barrier), steps
+// the bit synchroniser and finds where the next epoch ends, ceil((1023 2^32 - phi) / r)
+// samples on.  Teams do not wait for one another inside a block: the epoch ends of a
+// CTA's channels fall at different samples, and a lockstep would cost every channel the
+// longest stretch of any.  A CTA barrier at each block's end frees the prefix buffer.
+// The same operations as the per-channel walker, on the same samples in the same
+// order, so the same results.
+struct CsWalkState {
+    uint64_t rem;                // samples to the end of the open epoch (~0: the code word is 0)
+    uint32_t pos;                // next sample of the block
+    uint32_t epochs, closed, stop;
+    rx_code_state cs;
+};
+
+__device__ __forceinline__ uint64_t cs_epoch_rest(uint64_t phi, uint32_t r) {
+    return r ? (CODE_MOD - phi + r - 1) / r : ~0ull;
+}
+
+__global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs(CsCodeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ CsWalkState s_ws[CS_MAX_TEAMS];
+    const uint32_t mt = a.max_taps;
+    const CsShared h = cs_shared(smem, mt, a.max_n);
+    uint32_t *tab = g_item_tab;
+    const CsCodeGroup grp = a.groups[blockIdx.x];
+    const uint32_t n = grp.n, N = grp.N;
+    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
+    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t bar = 2 + g;
+    const CsTeam tm = cs_team(h.teams + (size_t)g * h.tbytes, mt);
+    const bool active = g < n;
+    const CodeWalk *wk = a.walks + grp.w0;
+    CsWalkState &ws = s_ws[g];
+
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
+    uint32_t nt = 0, per_ch = 0;
+    if (active) {
+        const CodeWalk &cw = wk[g];
+        nt = cw.ntaps;
+        per_ch = 2 * nt;
+        const uint32_t prn = cw.prn;
+        for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = cw.taps[i];
+        for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = a.tb.code[(size_t)prn * EXT_WORDS + i];
+        for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
+            reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)prn * CS_LMAX)[i];
+        for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
+            tm.tmask[i] = a.tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
+            tm.tcoarse[i] = a.tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
+            tm.tbits[i] = a.tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
+        }
+        for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = cw.acc[i];
+        for (uint32_t k0 = 8 * t; k0 < nt; k0 += 8 * CS_GT) {
+            uint32_t lo = k0, hi = k0;
+            for (uint32_t k = k0 + 1; k < min(k0 + 8, nt); ++k) {
+                if (cw.taps[k] < cw.taps[lo]) lo = k;
+                if (cw.taps[k] > cw.taps[hi]) hi = k;
+            }
+            tm.grp[k0 >> 3] = lo | (hi << 16);
+        }
+        if (t == 0) {
+            const uint64_t r = *cw.r;
+            tm.u[0] = *cw.theta;
+            tm.u[1] = (uint32_t)*cw.w;
+            tm.u[2] = (uint32_t)r;
+            tm.phi[0] = *cw.phi;
+            tm.d[0] = *cw.v;
+            tm.d[1] = *cw.fcarr;
+            tm.d[2] = *cw.fcode;
+            ws.cs = *cw.cs;
+            ws.epochs = *cw.epochs;
+            ws.closed = 0;
+            ws.stop = r >= (1ull << 32) ? 1u : 0u;
+            ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)r);
+        }
+    }
+    __syncthreads();
+
+    const int8_t *base = wk[0].iq;
+    for (uint32_t b = 0; b < grp.n_blocks; ++b) {
+        const int8_t *blk = base + 2 * (size_t)b * N;
+        if (threadIdx.x == 0 && b + 1 < grp.n_blocks) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
+        {
+            const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+            cs_prefix_share(blk, N, a16, a4, h.Wp, warp, nw);
+        }
+        if (active && t == 0) ws.pos = 0;
+        __syncthreads();                                  // the block's prefix sums in place
+        if (active) {
+            const CodeWalk &cw = wk[g];
+            for (;;) {
+                // ws is written by the team's thread 0 only, before the team barrier that
+                // ends the previous stretch, so every thread of the team reads the same
+                if (ws.stop || ws.pos >= N) break;
+                const uint32_t o0 = ws.pos;
+                const uint32_t L = (uint32_t)min(ws.rem, (uint64_t)(N - o0));
+                const bool ends = (uint64_t)L == ws.rem;
+                for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+                team_sync(bar);
+                cs_channel_range(t, bar, tm, h.Wp, blk, o0, L, nt, tab);
+                team_sync(bar);                           // the stretch's sums are in tm.acc
+                const uint32_t slot = ws.closed;
+                const bool store = ends && slot < cw.cap;
+                int32_t *dst = cw.dumps + (size_t)slot * per_ch;
+                for (uint32_t e = t; e < per_ch; e += CS_GT) {
+                    const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
+                    if (ends) {
+                        tm.acc[e] = (int32_t)val;
+                        tm.run[e] = 0;
+                        if (store) dst[e] = (int32_t)val;
+                    } else {
+                        tm.run[e] = (int32_t)val;
+                    }
+                }
+                if (ends) {
+                    team_sync(bar);                       // the epoch's sums are in tm.acc
+                    // this channel's loops on the team's first two warps: thread 0 the PLL
+                    // part and the rest, threads 32 and 33 the early and late envelopes and
+                    // the DLL part
+                    const uint32_t pbar = 8 + g;
+                    if (t < 32) {
+                        LoopConsts lc{};
+                        PllOut po{0.0, 0.0};
+                        FinishPre fp{};
+                        if (t == 0) {
+                            lc.k1 = __dmul_rn(cw.cl.w0sq,
+                                              __ddiv_rn((double)(ws.cs.samples_in_epoch + L), cw.cl.fs));
+                            lc.k2 = cw.cl.k2;
+                            lc.kdll = cw.cl.kdll;
+                            lc.sfs = cw.cl.sfs;
+                            po = loop_pll(tm.d[0], tm.acc[2 * cw.tap_p], tm.acc[2 * cw.tap_p + 1], lc);
+                            fp = loop_finish_pre(po, lc);
+                        }
+                        asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");   // the DLL part is in s_corr
+                        if (t == 0) {
+                            const LoopOut lo = loop_finish_post(fp, h.s_corr[g], lc);
+                            const uint32_t seg_total = ws.cs.samples_in_epoch + L;
+                            if (store) cw.lens[slot] = seg_total;
+                            else atomicOr(cw.err, 1u);
+                            tm.d[0] = lo.v;
+                            tm.d[1] = lo.f_carr;
+                            tm.d[2] = lo.f_code;
+                            ws.epochs += 1;
+                            bitsync_step(ws.cs, tm.acc[2 * cw.tap_p], cw.sync_k);
+                            ws.cs.samples_in_epoch = 0;
+                            ws.closed = slot + 1;
+                            tm.u[0] = tm.u[0] + L * tm.u[1];   // the stretch ran on the old words
+                            tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
+                            tm.u[1] = (uint32_t)lo.w;
+                            tm.u[2] = (uint32_t)lo.r;
+                            if (lo.r >= (1ull << 32)) {
+                                atomicOr(cw.err, 2u);
+                                ws.stop = 1u;
+                            }
+                            ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)lo.r);
+                            ws.pos = o0 + L;
+                        }
+                    } else if (t < 64) {
+                        const LoopConsts lc{0.0, 0.0, cw.cl.kdll, 0.0};
+                        double m = 0.0;
+                        if (t < 34) {
+                            const uint32_t k = t == 33 ? (uint32_t)cw.tap_l : (uint32_t)cw.tap_e;
+                            m = loop_envelope(tm.acc[2 * k], tm.acc[2 * k + 1]);
+                        }
+                        const double ml = __shfl_down_sync(0xffffffffu, m, 1);
+                        if (t == 32) h.s_corr[g] = loop_dll(m, ml, tm.taps[cw.tap_e], tm.taps[cw.tap_l], lc);
+                        asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");
+                    }
+                } else if (t == 0) {
+                    tm.u[0] = tm.u[0] + L * tm.u[1];
+                    tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
+                    ws.pos = o0 + L;
+                    ws.rem -= L;
+                    ws.cs.samples_in_epoch += L;
+                }
+                team_sync(bar);                           // new words, position and state in place
+            }
+        }
+        __syncthreads();                                  // every team has reached the block's end
+    }
+    if (active) {
+        const CodeWalk &cw = wk[g];
+        if (t == 0) {
+            *cw.cs = ws.cs;
+            *cw.v = tm.d[0];
+            *cw.fcarr = tm.d[1];
+            *cw.fcode = tm.d[2];
+            *cw.epochs = ws.epochs;
+            *cw.theta = tm.u[0];
+            *cw.w = (int32_t)tm.u[1];
+            *cw.phi = tm.phi[0];
+            *cw.r = tm.u[2];
+            *cw.nclosed = min(ws.closed, cw.cap);
+        }
+        for (uint32_t i = t; i < per_ch; i += CS_GT) cw.acc[i] = tm.run[i];
+    }
+}
+
 template <bool T3>
 int cs_occ(uint32_t threads, size_t smem) {
     auto kern = k_batch_cseg<T3>;
@@ -974,6 +1196,29 @@ cudaError_t cs_serve_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream
     if (cpg < 1 || cpg > CS_MAX_TEAMS) return cudaErrorInvalidValue;
     return table3 ? cs_serve_go<true>(cs_threads(cpg), grid, smem, stream, a)
                   : cs_serve_go<false>(cs_threads(cpg), grid, smem, stream, a);
+}
+
+int cs_code_occupancy(uint32_t cpg, size_t smem) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return 0;
+    if (cudaFuncSetAttribute(k_batch_code_cs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_code_cs, (int)cs_threads(cpg), smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t cs_code_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsCodeArgs &a) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_code_cs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_code_cs<<<grid, cs_threads(cpg), smem, stream>>>(a);
+    return cudaGetLastError();
 }
 
 uint32_t cs_max_channels() { return CS_MAX_TEAMS; }

@@ -6,6 +6,9 @@
 
 #include "rx_device.cuh"
 
+struct CodeWalk;
+struct CsCodeGroup;
+
 namespace rxd {
 
 // A channel group's state, constants and outputs.  Every pointer is already
@@ -502,6 +505,19 @@ struct CsServeArgs {
     uint32_t max_n;
     uint64_t timeout_ns;
 };
+
+// The carrier-segment form of the code-period epoch walk (RX_EPOCH_CODE, batched): one
+// CTA per channel group (up to cpg channels of one receiver), one 128-thread team per
+// channel; walks[] and groups[] as rx_code.cuh describes.
+struct CsCodeArgs {
+    const CodeWalk *walks;
+    const CsCodeGroup *groups;
+    Tables tb;
+    uint32_t max_taps;
+    uint32_t max_n;            // largest block of any receiver
+};
+int cs_code_occupancy(uint32_t cpg, size_t smem);
+cudaError_t cs_code_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsCodeArgs &a);
 
 // Resident serving CTAs per SM (0: the configuration does not fit).
 int cs_serve_occupancy(uint32_t cpg, size_t smem, bool table3);

@@ -1,9 +1,11 @@
-"""GPU parity of code-period epochs in the batched form (rx_batch_run_code: one CTA per
-channel walks its receiver's whole run) against the oracle: every epoch's dump and
-sample count, the loop state, the open epoch and the bit synchroniser, bit-exact, for
-a batch of receivers of uneven rate, channel count and tap count; a run split in two
-continues exactly; restart reproduces; block and code-period runs do not mix without
-a restart."""
+"""GPU parity of code-period epochs in the batched form (rx_batch_run_code) against the
+oracle, for both walkers: the carrier-segment walk (default tiles or RX_SCHED_SEGMENT:
+the channels of a receiver in groups sharing each block's prefix sums, each correlated
+in stretches between its own epoch ends) and the per-channel walk in the chunk forms
+(the other schedules).  Every epoch's dump and sample count, the loop state, the open
+epoch and the bit synchroniser, bit-exact, for a batch of receivers of uneven rate,
+channel count and tap count; a run split in two continues exactly; restart
+reproduces; block and code-period runs do not mix without a restart."""
 import numpy as np
 import pytest
 import torch
@@ -36,10 +38,17 @@ def _setup(n_blocks, n_rx=5):
     return recv, offs, buf, sigs
 
 
-def _batch(recv, n_blocks):
+WALKS = [pytest.param(None, id="segment-default"), pytest.param((1, 128, 0, rx.RX_SCHED_SEGMENT), id="segment-1"),
+         pytest.param((6, 128, 0, rx.RX_SCHED_SEGMENT), id="segment-6"),
+         pytest.param((2, 224, 0, rx.RX_SCHED_PIPE), id="chunk")]
+
+
+def _batch(recv, n_blocks, tiles=None):
     b = rx.rx_batch_create([rx.receiver_desc(r) for r in recv], n_blocks)
     for i, r in enumerate(recv):
         rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+    if tiles:
+        rx.rx_batch_set_tiles(b, *tiles)
     return b
 
 
@@ -49,12 +58,13 @@ def _oracle_channels(r):
                                r.n_taps) for i in range(len(prn))], taps
 
 
-def test_uneven_batch_code_epochs_match_oracle_and_continue():
+@pytest.mark.parametrize("tiles", WALKS)
+def test_uneven_batch_code_epochs_match_oracle_and_continue(tiles):
     n_blocks = 24
     recv, offs, buf, sigs = _setup(n_blocks)
     assert len({r.fs for r in recv}) >= 3 and len({r.n_taps for r in recv}) >= 2
     dev = torch.from_numpy(buf).cuda()
-    b = _batch(recv, n_blocks)
+    b = _batch(recv, n_blocks, tiles)
     try:
         # one run of 24 blocks
         rx.rx_batch_run_code(b, dev, offs, n_blocks, rx.RX_RUN_RESTART)
@@ -95,7 +105,8 @@ def _check_run(b, recv, sigs, chans, first_block, n_blocks):
             assert gb == ch.bs.as_dict(), (i, c)
 
 
-def test_bit_sync_in_the_batched_form():
+@pytest.mark.parametrize("tiles", [WALKS[0], WALKS[3]])
+def test_bit_sync_in_the_batched_form(tiles):
     """Receivers whose data bits change on code-period boundaries: after 1.2 s every
     channel at 45 dB-Hz has found the bit edge and decodes the generator's bits."""
     fs, N, n_blocks = 2.046e6, 2046, 1200
@@ -116,7 +127,7 @@ def test_bit_sync_in_the_batched_form():
     for r, o in zip(recv, offs):
         iq = synth.generate_iq(r).numpy()
         buf[int(o):int(o) + iq.size] = iq.reshape(-1)
-    b = _batch(recv, n_blocks)
+    b = _batch(recv, n_blocks, tiles)
     try:
         rx.rx_batch_run_code(b, torch.from_numpy(buf).cuda(), offs, n_blocks, rx.RX_RUN_RESTART)
         for i, r in enumerate(recv):
@@ -161,3 +172,34 @@ def test_modes_need_a_restart_to_switch():
         assert e.value.status == rx.RX_EINVAL
     finally:
         rx.rx_batch_destroy(b)
+
+
+def test_both_walkers_agree_on_the_uniform_workload():
+    """The two walkers over 8 receivers x 12 channels x 5 taps at 16.368 MHz, 60 blocks:
+    every epoch's dump and length, the state and the bit synchroniser identical."""
+    recv = [synth.uniform_receiver(i, n_blocks=60) for i in range(8)]
+    offs, total = batch_layout(recv)
+    buf = torch.zeros(total, dtype=torch.int8, device="cuda")
+    for r, o in zip(recv, offs):
+        iq = synth.generate_iq(r, device="cuda")
+        buf[int(o):int(o) + iq.numel()] = iq.view(-1)
+    out = []
+    for tiles in (None, (2, 224, 0, rx.RX_SCHED_PIPE)):
+        b = _batch(recv, 60, tiles)
+        try:
+            rx.rx_batch_run_code(b, buf, offs, 60, rx.RX_RUN_RESTART)
+            res = []
+            for i, r in enumerate(recv):
+                d, ln, ne = rx.rx_batch_read_code_epochs(b, i, 12, 5, 64)
+                st = rx.rx_batch_read_state(b, i, 12)
+                cs = rx.rx_batch_read_code_state(b, i, 12)
+                res.append((d, ln, ne, [x.as_dict() if hasattr(x, "as_dict") else
+                                        (x.carrier_word, x.code_rate, x.carrier_phase, x.code_phase,
+                                         x.pll_integrator_hz, x.carrier_hz, x.code_hz, x.epochs) for x in st],
+                            [c.as_dict() for c in cs]))
+            out.append(res)
+        finally:
+            rx.rx_batch_destroy(b)
+    for (d0, l0, n0, s0, c0), (d1, l1, n1, s1, c1) in zip(*out):
+        assert np.array_equal(n0, n1) and np.array_equal(d0, d1) and np.array_equal(l0, l1)
+        assert s0 == s1 and c0 == c1
