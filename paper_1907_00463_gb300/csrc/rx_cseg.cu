@@ -338,9 +338,9 @@ __device__ __forceinline__ uint32_t cs_count_below(const uint32_t *mask, const u
 
 // Constants of one tap (offset off) for the block: its chip range, transition range
 // and final code value, from the team's copy of the PRN's tables.
-__device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t off, int64_t off_ref, uint32_t N,
-                                        const uint32_t *mask, const uint32_t *coarse, const uint32_t *bits) {
-    CsTap t;
+// A tap's chip range, transition range and final code value for the range.
+__device__ __forceinline__ void cs_tap_chips(CsTap &t, const CsChan &c, uint64_t phi, int64_t off, uint32_t N,
+                                             const uint32_t *mask, const uint32_t *coarse, const uint32_t *bits) {
     const int64_t psi = (int64_t)phi + off;
     const int32_t c0 = (int32_t)(psi >> 32);
     const int32_t cN = (int32_t)((psi + (int64_t)(N - 1) * (int64_t)c.r) >> 32);
@@ -351,10 +351,13 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     t.cnt = cs_count_below(mask, coarse, (uint32_t)(cN + 1 + CS_CBASE)) - t.u0;
     const uint32_t i = (uint32_t)(cN + CS_CBASE);
     t.g_end = ((bits[i >> 5] >> (31u - (i & 31u))) & 1u) ? -1 : 1;
-    // off - off_ref = D r + E with E in [0, r): D rounded from a float estimate and one
-    // exact correction either way.  D is used only when the taps' span is below 2^17 r;
-    // then the estimate's error (three roundings of 2^-24 relative) is below 1/20, so the
-    // rounded value is D or D + 1.
+}
+
+// off - off_ref = D r + E with E in [0, r): D rounded from a float estimate and one
+// exact correction either way.  D is used only when the taps' span is below 2^17 r;
+// then the estimate's error (three roundings of 2^-24 relative) is below 1/20, so the
+// rounded value is D or D + 1.
+__device__ __forceinline__ void cs_tap_diff(CsTap &t, const CsChan &c, int64_t off, int64_t off_ref) {
     const int64_t dlt = off - off_ref;                        // >= 0: the reference has the least offset
     int64_t D = (int64_t)__float2int_rn(__fmul_rn((float)dlt, __frcp_rn((float)c.r)));
     int64_t E = dlt - D * (int64_t)c.r;
@@ -367,7 +370,6 @@ __device__ __forceinline__ CsTap cs_tap(const CsChan &c, uint64_t phi, int64_t o
     }
     t.D = (uint32_t)D;
     t.Fr = c.r - (uint32_t)E;
-    return t;
 }
 
 // M(L) for the range: the segment of its last sample.
@@ -597,9 +599,24 @@ __device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
     if (cs_eligible(c, o0, N, phi)) {
-        for (uint32_t k = t; k < nt; k += CS_GT)
-            tm.tap[k] = cs_tap(c, phi, tm.taps[k], tm.taps[tm.grp[k >> 3] & 0xffffu], N, tm.tmask, tm.tcoarse,
-                               tm.tbits);
+        // the taps' constants: the chip part on the first warps and the part relative to
+        // each group's reference tap on the warps after them, so that no warp carries both
+        // chains before its share of the segment pass (one pass when 2 x 32-lane-rounded
+        // tap counts fit the team, else both parts tap by tap)
+        const uint32_t half = (nt + 31u) & ~31u;
+        if (2u * half <= CS_GT) {
+            if (t < nt) {
+                cs_tap_chips(tm.tap[t], c, phi, tm.taps[t], N, tm.tmask, tm.tcoarse, tm.tbits);
+            } else if (t >= half && t - half < nt) {
+                const uint32_t k = t - half;
+                cs_tap_diff(tm.tap[k], c, tm.taps[k], tm.taps[tm.grp[k >> 3] & 0xffffu]);
+            }
+        } else {
+            for (uint32_t k = t; k < nt; k += CS_GT) {
+                cs_tap_chips(tm.tap[k], c, phi, tm.taps[k], N, tm.tmask, tm.tcoarse, tm.tbits);
+                cs_tap_diff(tm.tap[k], c, tm.taps[k], tm.taps[tm.grp[k >> 3] & 0xffffu]);
+            }
+        }
         uint32_t DI, DQ, sf, sl;
         bool any;
         cs_seg_local(t, Wp, o0, N, c, tab, tm.seg, DI, DQ, sf, sl, any);

@@ -428,6 +428,57 @@ __device__ __forceinline__ double atan_cycles_t(double q, double i, const Tab &t
 
 __device__ __forceinline__ double atan_cycles(double q, double i) { return atan_cycles_t(q, i, AtanConst{}); }
 
+// k / 512 for k in [0, 64], exactly, from its bits (the exponent of k's leading bit
+// less 9, k's lower bits as the mantissa).
+__device__ __forceinline__ double k_over_512(int k) {
+    if (k == 0) return 0.0;
+    const int e = 31 - __clz(k);
+    const uint32_t hi = ((uint32_t)(1023 + e - 9) << 20) | (((uint32_t)k << (20 - e)) & 0xFFFFFu);
+    return __hiloint2double((int)hi, 0);
+}
+
+// atan_cycles((double)q, (double)i) of two int32 sums (i != 0), with the same
+// double-precision operations on the same values wherever an operand is not an exact
+// integer.  The steps whose operands are exact integers run in integer and
+// single-precision arithmetic and give the same values: the magnitudes and the swap
+// (|INT_MIN| is exact as an unsigned word), the ratio's single-precision operands
+// (rounding an exact integer to float is the same from a double as from an integer),
+// the quadrant sign, k / 512 and the final negation (the sign bit).  GB300's FP64 pipe
+// charges per warp instruction and this chain closes every channel's carrier loop.
+__device__ __forceinline__ double atan_cycles_int(int32_t qi, int32_t ii) {
+    const uint32_t aq = qi < 0 ? 0u - (uint32_t)qi : (uint32_t)qi;
+    const uint32_t ai = ii < 0 ? 0u - (uint32_t)ii : (uint32_t)ii;
+    const bool swap = aq > ai;
+    const uint32_t ua = swap ? ai : aq, ub = swap ? aq : ai;
+    const double a = __uint2double_rn(ua), b = __uint2double_rn(ub);
+    const float rf = __fdiv_rn(__uint2float_rn(ua), __uint2float_rn(ub));
+    int k = 0;
+#pragma unroll
+    for (int step = 32; step >= 1; step >>= 1)
+        if (rf >= kAtanMid[k + step - 1]) k += step;
+    const double c = kAtanTan[k];
+    double num = __dmul_rn(c, b);
+    num = __dsub_rn(a, num);
+    double den = __dmul_rn(c, a);
+    den = __dadd_rn(b, den);
+    const double t = __ddiv_rn(num, den);
+    const double u = __dmul_rn(t, t);
+    const double u2 = __dmul_rn(u, u);
+    double p01 = __dmul_rn(kAtanSeries[1], u);
+    p01 = __dadd_rn(kAtanSeries[0], p01);
+    double p23 = __dmul_rn(kAtanSeries[3], u);
+    p23 = __dadd_rn(kAtanSeries[2], p23);
+    const double p4 = __dmul_rn(kAtanSeries[4], u2);
+    double hi = __dadd_rn(p23, p4);
+    hi = __dmul_rn(hi, u2);
+    const double p = __dadd_rn(p01, hi);
+    double y = __dmul_rn(t, p);
+    y = __dadd_rn(k_over_512(k), y);
+    if (swap) y = __dsub_rn(0.25, y);
+    if ((qi < 0) != (ii < 0)) y = __longlong_as_double(__double_as_longlong(y) ^ (long long)0x8000000000000000ull);
+    return y;
+}
+
 // Per-receiver loop constants, computed on the host once per integration length:
 //   T = n_accum / fs, w0 = Bn_pll / 0.53, k1 = (w0 w0) T, k2 = sqrt2 w0,
 //   kdll = 4 Bn_dll, sfs = 2^32 / fs.
@@ -468,23 +519,19 @@ struct PllOut {
     double v, f_carr;
 };
 
-template <class Tab>
-__device__ __forceinline__ PllOut loop_pll_t(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc, const Tab &tb) {
-    const double ip = (double)ipr, qp = (double)qpr;
+// PLL part of the loop update: the discriminator e = atan(Q_P / I_P) / (2 pi) cycles
+// (+-1/4 when I_P = 0 and Q_P != 0, 0 when both are 0) and the 2nd-order filter.
+__device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc) {
     double e_pll;
-    if (ip != 0.0) {
-        e_pll = atan_cycles_t(qp, ip, tb);
+    if (ipr != 0) {
+        e_pll = atan_cycles_int(qpr, ipr);
     } else {
-        e_pll = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+        e_pll = qpr > 0 ? 0.25 : (qpr < 0 ? -0.25 : 0.0);
     }
     const double dv = __dmul_rn(lc.k1, e_pll);
     v = __dadd_rn(v, dv);
     const double df = __dmul_rn(lc.k2, e_pll);
     return PllOut{v, __dadd_rn(v, df)};
-}
-
-__device__ __forceinline__ PllOut loop_pll(double v, int32_t ipr, int32_t qpr, const LoopConsts &lc) {
-    return loop_pll_t(v, ipr, qpr, lc, AtanConst{});
 }
 
 // Envelope of one DLL tap, sqrt(I^2 + Q^2).
@@ -643,10 +690,10 @@ __device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t i
     LoopOut o;
     const double ip = (double)ipr, qp = (double)qpr;
     double e_p;
-    if (ip != 0.0) {
-        e_p = atan_cycles(qp, ip);
+    if (ipr != 0) {
+        e_p = atan_cycles_int(qpr, ipr);
     } else {
-        e_p = qp > 0.0 ? 0.25 : (qp < 0.0 ? -0.25 : 0.0);
+        e_p = qpr > 0 ? 0.25 : (qpr < 0 ? -0.25 : 0.0);
     }
     double e_f = 0.0;
     if (ex.have_prev) {
