@@ -390,12 +390,14 @@ rx_status rx_batch_read_all_dumps(rx_batch b, int32_t *out, size_t cap, uint32_t
  * run at each epoch with T = its samples / fs and the bit synchroniser stepped
  * (bitsync_count 8); integ_blocks does not apply.  iq must be device memory.
  * One launch, synchronous.  With the default tiles or RX_SCHED_SEGMENT it runs
- * the carrier-segment walk: a CTA takes channels_per_item channels (3 by
- * default, at most 6) of one receiver, builds each block's prefix sums once
- * for them, and correlates each channel in stretches between its own epoch
- * ends; with the other schedules, or where a block exceeds 65536 samples or the
- * CTA's shared memory does not fit, one CTA per channel walks in the chunk
- * forms.  The results are the same.  The state continues from the
+ * the carrier-segment walk: a CTA takes channels_per_item channels (at most 6;
+ * by default 6 with two prefix buffers where they fit, the next block's built
+ * by idle warps, else 3 with one) of one receiver, builds each block's prefix
+ * sums once for them, and correlates each channel in stretches between its own
+ * epoch ends; with the other schedules, or where a block exceeds 65536 samples
+ * or the CTA's shared memory does not fit, one CTA per channel walks in the
+ * chunk forms.  The results are the same.  RX_ETIMEOUT if the two-buffer
+ * walk's bounded wait for prefix sums runs out.  The state continues from the
  * previous code-period run, or from the starting state with RX_RUN_RESTART;
  * switching between block runs and code-period runs needs RX_RUN_RESTART
  * (RX_ESTATE otherwise). */

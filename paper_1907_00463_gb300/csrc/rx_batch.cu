@@ -1552,9 +1552,12 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
     // of cpg sharing each block's prefix sums) with the default tiles or RX_SCHED_SEGMENT
     // and where its shared memory fits; otherwise one CTA per channel in the chunk forms
     bool seg_walk = b->schedule == RX_SCHED_SEGMENT || b->schedule == RX_SCHED_DYNAMIC;
-    const uint32_t cpg = b->schedule == RX_SCHED_SEGMENT && b->cpg ? std::min(b->cpg, cs_max_channels()) : 3u;
     uint32_t max_n = 0;
     for (const rx_receiver_desc &d : b->rx) max_n = std::max(max_n, d.block_samples);
+    // channels per CTA: the caller's with RX_SCHED_SEGMENT; by default six with two prefix
+    // buffers where they fit (one CTA per SM), else three with one (two CTAs per SM)
+    uint32_t cpg = b->schedule == RX_SCHED_SEGMENT && b->cpg ? std::min(b->cpg, cs_max_channels()) : 0u;
+    if (cpg == 0) cpg = cs_code_db_occupancy(6, cs_code_db_smem(6, b->max_taps, max_n)) > 0 ? 6u : 3u;
     const size_t cs_smem = cs_smem_bytes(cpg, b->max_taps, max_n);
     if (seg_walk) seg_walk = max_n <= 65536 && cs_code_occupancy(cpg, cs_smem) > 0;
     if (seg_walk) {
@@ -1571,7 +1574,14 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
                       Tables{b->tables->code, b->tables->tab, b->tables->pair, b->tables->tlist, b->tables->tmask,
                              b->tables->tcoarse, b->tables->tbits},
                       b->max_taps, max_n};
-        RX_CUDA_TRY(cs_code_launch(cpg, (uint32_t)groups.size(), cs_smem, b->stream, ca), E);
+        // six channels per CTA take the double-buffered walk where its second prefix
+        // buffer fits (one CTA per SM): 14.1 ms against 15.8 ms for three channels with one
+        // buffer on the uniform workload
+        const size_t db_smem = cs_code_db_smem(cpg, b->max_taps, max_n);
+        if (cpg == 6 && cs_code_db_occupancy(cpg, db_smem) > 0)
+            RX_CUDA_TRY(cs_code_db_launch(cpg, (uint32_t)groups.size(), db_smem, b->stream, ca), E);
+        else
+            RX_CUDA_TRY(cs_code_launch(cpg, (uint32_t)groups.size(), cs_smem, b->stream, ca), E);
     } else {
         RX_CUDA_TRY(rxh::launch_code_walks(b->d_walks, b->n_ch, b->max_taps, b->tables, b->stream), E);
     }
@@ -1580,6 +1590,7 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
     RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
     b->last_mode = 2;
     b->last_launches = 1;
+    if (cerr & 4u) return berr(b, RX_ETIMEOUT, "a code-period walk's wait for prefix sums timed out");
     if (cerr & 2u) return berr(b, RX_EINVAL, "a channel's code word reached 2^32");
     if (cerr & 1u) return berr(b, RX_EINVAL, "a channel closed more epochs than the ring holds");
     return RX_OK;

@@ -206,37 +206,52 @@ __device__ __forceinline__ uint32_t cs_sw(uint32_t n) { return n ^ (((n >> 5) & 
 // warp with index wq among nw warps takes the 32-chunk runs wq, wq + nw, ... (chunk q
 // = samples 16 q .. 16 q + 15, its lane q mod 32); the 16 lanes of a 256-sample group
 // scan their totals with shuffles.  Wp holds at least N rounded up to 16 words.
+// One warp's unit of the prefix sums: the 32 chunks of 16 samples from chunk q0 (two
+// whole 256-sample groups), each lane one chunk.
+__device__ __forceinline__ void cs_prefix_unit(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t *Wp,
+                                               uint32_t q0) {
+    const uint32_t nq = (N + 15) >> 4;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t q = q0 + lane;
+    uint32_t x[8];
+    cs_load16(blk, q * 16, N, a16, a4, x);
+    uint32_t s[16];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t v = x[k] ^ 0x80808080u;    // each byte + 128, as unsigned
+        acc += prmt(v, 0u, 0x4140u);               // (I + 128) | (Q + 128) << 16, even sample
+        s[2 * k] = acc;
+        acc += prmt(v, 0u, 0x4342u);               // odd sample
+        s[2 * k + 1] = acc;
+    }
+    uint32_t inc = acc;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, d, 16);
+        if ((lane & 15u) >= (uint32_t)d) inc += t;
+    }
+    const uint32_t base = inc - acc + 0x80008000u * ((q >> 4) + 1u);
+    if (q < nq) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<uint4 *>(Wp + cs_sw(16 * q + 4 * k)) =
+                make_uint4(s[4 * k] + base, s[4 * k + 1] + base, s[4 * k + 2] + base, s[4 * k + 3] + base);
+    }
+}
+
 __device__ __forceinline__ void cs_prefix_share(const int8_t *blk, uint32_t N, bool a16, bool a4, uint32_t *Wp,
                                                 uint32_t wq, uint32_t nw) {
     const uint32_t nq = (N + 15) >> 4;
     const uint32_t lane = threadIdx.x & 31;
     for (uint32_t q0 = 32u * wq; q0 < nq; q0 += 32u * nw) {
-        const uint32_t q = q0 + lane;
-        uint32_t x[8];
-        cs_load16(blk, q * 16, N, a16, a4, x);
-        uint32_t s[16];
-        uint32_t acc = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t v = x[k] ^ 0x80808080u;    // each byte + 128, as unsigned
-            acc += prmt(v, 0u, 0x4140u);               // (I + 128) | (Q + 128) << 16, even sample
-            s[2 * k] = acc;
-            acc += prmt(v, 0u, 0x4342u);               // odd sample
-            s[2 * k + 1] = acc;
+        // the next step's samples towards L1 (no registers held), so that a warp's loads overlap
+        if (q0 + 32u * nw < nq && (lane & 3u) == 0u) {
+            const uint32_t qn = q0 + 32u * nw + lane;
+            if (qn < nq)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(blk + 32 * (size_t)qn) : "memory");
         }
-        uint32_t inc = acc;
-#pragma unroll
-        for (int d = 1; d < 16; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, d, 16);
-            if ((lane & 15u) >= (uint32_t)d) inc += t;
-        }
-        const uint32_t base = inc - acc + 0x80008000u * ((q >> 4) + 1u);
-        if (q < nq) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *reinterpret_cast<uint4 *>(Wp + cs_sw(16 * q + 4 * k)) =
-                    make_uint4(s[4 * k] + base, s[4 * k + 1] + base, s[4 * k + 2] + base, s[4 * k + 3] + base);
-        }
+        cs_prefix_unit(blk, N, a16, a4, Wp, q0);
     }
 }
 
@@ -968,10 +983,182 @@ struct CsWalkState {
     uint32_t pos;                // next sample of the block
     uint32_t epochs, closed, stop;
     rx_code_state cs;
+    double k1[3];                // w0^2 (n / fs) for epochs of n = N - 1, N, N + 1 samples (the
+                                 // same two operations as for any other n, done once)
 };
 
+// Samples to the end of the code period from code phase phi (< 1023 2^32): ceil((1023
+// 2^32 - phi) / r), ~0 for r = 0.  For r >= 2^16 the quotient is below 2^26 and a float
+// estimate of it (three roundings of 2^-24 relative, then truncation) is within 13 of the
+// ceiling, so at most 13 exact 64-bit steps move it there; slower code words take the
+// division.
 __device__ __forceinline__ uint64_t cs_epoch_rest(uint64_t phi, uint32_t r) {
-    return r ? (CODE_MOD - phi + r - 1) / r : ~0ull;
+    if (!r) return ~0ull;
+    const uint64_t X = CODE_MOD - phi;
+    if (r < 0x10000u) return (X + r - 1) / r;
+    const float qf = __fmul_rn(__ull2float_rn(X), __frcp_rn((float)r));
+    uint64_t q = (uint64_t)qf;
+    for (uint32_t i = 0; i < 20 && q * r < X; ++i) ++q;
+    for (uint32_t i = 0; i < 20 && q > 0 && (q - 1) * r >= X; ++i) --q;
+    return q;
+}
+
+// Load channel g's walk state into its team area (tm) and walk state (ws).
+__device__ __forceinline__ void cs_walk_load(uint32_t t, const CsTeam &tm, CsWalkState &ws, const CodeWalk &cw,
+                                             const Tables &tb, uint32_t N) {
+    const uint32_t nt = cw.ntaps, per_ch = 2 * nt, prn = cw.prn;
+    for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = cw.taps[i];
+    for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = tb.code[(size_t)prn * EXT_WORDS + i];
+    for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
+        reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(tb.tlist + (size_t)prn * CS_LMAX)[i];
+    for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
+        tm.tmask[i] = tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
+        tm.tcoarse[i] = tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
+        tm.tbits[i] = tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
+    }
+    for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = cw.acc[i];
+    for (uint32_t k0 = 8 * t; k0 < nt; k0 += 8 * CS_GT) {
+        uint32_t lo = k0, hi = k0;
+        for (uint32_t k = k0 + 1; k < min(k0 + 8, nt); ++k) {
+            if (cw.taps[k] < cw.taps[lo]) lo = k;
+            if (cw.taps[k] > cw.taps[hi]) hi = k;
+        }
+        tm.grp[k0 >> 3] = lo | (hi << 16);
+    }
+    if (t == 0) {
+        const uint64_t r = *cw.r;
+        tm.u[0] = *cw.theta;
+        tm.u[1] = (uint32_t)*cw.w;
+        tm.u[2] = (uint32_t)r;
+        tm.phi[0] = *cw.phi;
+        tm.d[0] = *cw.v;
+        tm.d[1] = *cw.fcarr;
+        tm.d[2] = *cw.fcode;
+        ws.cs = *cw.cs;
+        ws.epochs = *cw.epochs;
+        ws.closed = 0;
+        ws.stop = r >= (1ull << 32) ? 1u : 0u;
+        ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)r);
+        for (uint32_t i = 0; i < 3; ++i)
+            ws.k1[i] = __dmul_rn(cw.cl.w0sq, __ddiv_rn((double)(N - 1 + i), cw.cl.fs));
+    }
+}
+
+// One team's stretches over one block (its channel's state in tm and ws, the block's
+// prefix sums in Wp).  While its first two warps close an epoch's loops, the team's other
+// warps call idle() (the double-buffered walk builds the next block's prefix sums there).
+template <class Idle>
+__device__ __forceinline__ void cs_walk_block(uint32_t t, uint32_t g, uint32_t bar, const CsTeam &tm, CsWalkState &ws,
+                                              const CodeWalk &cw, const uint32_t *Wp, const int8_t *blk, uint32_t N,
+                                              uint32_t nt, uint32_t per_ch, const uint32_t *tab, double *s_corr,
+                                              Idle idle) {
+    for (;;) {
+        // ws is written by the team's thread 0 only, before the team barrier that
+        // ends the previous stretch, so every thread of the team reads the same
+        if (ws.stop || ws.pos >= N) break;
+        const uint32_t o0 = ws.pos;
+        const uint32_t L = (uint32_t)min(ws.rem, (uint64_t)(N - o0));
+        const bool ends = (uint64_t)L == ws.rem;
+        for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+        team_sync(bar);
+        cs_channel_range(t, bar, tm, Wp, blk, o0, L, nt, tab);
+        team_sync(bar);                           // the stretch's sums are in tm.acc
+        const uint32_t slot = ws.closed;
+        const bool store = ends && slot < cw.cap;
+        int32_t *dst = cw.dumps + (size_t)slot * per_ch;
+        for (uint32_t e = t; e < per_ch; e += CS_GT) {
+            const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
+            if (ends) {
+                tm.acc[e] = (int32_t)val;
+                tm.run[e] = 0;
+                if (store) dst[e] = (int32_t)val;
+            } else {
+                tm.run[e] = (int32_t)val;
+            }
+        }
+        if (ends) {
+            team_sync(bar);                       // the epoch's sums are in tm.acc
+            // this channel's loops on the team's first two warps: thread 0 the PLL
+            // part and the rest, threads 32 and 33 the early and late envelopes and
+            // the DLL part
+            const uint32_t pbar = 8 + g;
+            if (t < 32) {
+                LoopConsts lc{};
+                PllOut po{0.0, 0.0};
+                FinishPre fp{};
+                if (t == 0) {
+                    const uint32_t ne = ws.cs.samples_in_epoch + L, ki = ne + 1u - N;
+                    lc.k1 = ki < 3u ? ws.k1[ki] : __dmul_rn(cw.cl.w0sq, __ddiv_rn((double)ne, cw.cl.fs));
+                    lc.k2 = cw.cl.k2;
+                    lc.kdll = cw.cl.kdll;
+                    lc.sfs = cw.cl.sfs;
+                    po = loop_pll(tm.d[0], tm.acc[2 * cw.tap_p], tm.acc[2 * cw.tap_p + 1], lc);
+                    fp = loop_finish_pre(po, lc);
+                }
+                asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");   // the DLL part is in s_corr
+                if (t == 0) {
+                    const LoopOut lo = loop_finish_post(fp, s_corr[g], lc);
+                    const uint32_t seg_total = ws.cs.samples_in_epoch + L;
+                    if (store) cw.lens[slot] = seg_total;
+                    else atomicOr(cw.err, 1u);
+                    tm.d[0] = lo.v;
+                    tm.d[1] = lo.f_carr;
+                    tm.d[2] = lo.f_code;
+                    ws.epochs += 1;
+                    bitsync_step(ws.cs, tm.acc[2 * cw.tap_p], cw.sync_k);
+                    ws.cs.samples_in_epoch = 0;
+                    ws.closed = slot + 1;
+                    tm.u[0] = tm.u[0] + L * tm.u[1];   // the stretch ran on the old words
+                    tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
+                    tm.u[1] = (uint32_t)lo.w;
+                    tm.u[2] = (uint32_t)lo.r;
+                    if (lo.r >= (1ull << 32)) {
+                        atomicOr(cw.err, 2u);
+                        ws.stop = 1u;
+                    }
+                    ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)lo.r);
+                    ws.pos = o0 + L;
+                }
+            } else if (t < 64) {
+                const LoopConsts lc{0.0, 0.0, cw.cl.kdll, 0.0};
+                double m = 0.0;
+                if (t < 34) {
+                    const uint32_t k = t == 33 ? (uint32_t)cw.tap_l : (uint32_t)cw.tap_e;
+                    m = loop_envelope(tm.acc[2 * k], tm.acc[2 * k + 1]);
+                }
+                const double ml = __shfl_down_sync(0xffffffffu, m, 1);
+                if (t == 32) s_corr[g] = loop_dll(m, ml, tm.taps[cw.tap_e], tm.taps[cw.tap_l], lc);
+                asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");
+            } else {
+                idle();
+            }
+        } else if (t == 0) {
+            tm.u[0] = tm.u[0] + L * tm.u[1];
+            tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
+            ws.pos = o0 + L;
+            ws.rem -= L;
+            ws.cs.samples_in_epoch += L;
+        }
+        team_sync(bar);                           // new words, position and state in place
+    }
+}
+
+// The team's channel state back to its walk descriptor.
+__device__ __forceinline__ void cs_walk_store(uint32_t t, const CsTeam &tm, const CsWalkState &ws, const CodeWalk &cw,
+                                              uint32_t per_ch) {
+    if (t == 0) {
+        *cw.cs = ws.cs;
+        *cw.v = tm.d[0];
+        *cw.fcarr = tm.d[1];
+        *cw.fcode = tm.d[2];
+        *cw.epochs = ws.epochs;
+        *cw.theta = tm.u[0];
+        *cw.w = (int32_t)tm.u[1];
+        *cw.phi = tm.phi[0];
+        *cw.r = tm.u[2];
+        *cw.nclosed = min(ws.closed, cw.cap);
+    }
+    for (uint32_t i = t; i < per_ch; i += CS_GT) cw.acc[i] = tm.run[i];
 }
 
 __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs(CsCodeArgs a) {
@@ -989,50 +1176,10 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs(CsCod
     const bool active = g < n;
     const CodeWalk *wk = a.walks + grp.w0;
     CsWalkState &ws = s_ws[g];
-
     for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
-    uint32_t nt = 0, per_ch = 0;
-    if (active) {
-        const CodeWalk &cw = wk[g];
-        nt = cw.ntaps;
-        per_ch = 2 * nt;
-        const uint32_t prn = cw.prn;
-        for (uint32_t i = t; i < nt; i += CS_GT) tm.taps[i] = cw.taps[i];
-        for (uint32_t i = t; i < EXT_WORDS; i += CS_GT) tm.code[i] = a.tb.code[(size_t)prn * EXT_WORDS + i];
-        for (uint32_t i = t; i < CS_LMAX / 8; i += CS_GT)
-            reinterpret_cast<uint4 *>(tm.list)[i] = reinterpret_cast<const uint4 *>(a.tb.tlist + (size_t)prn * CS_LMAX)[i];
-        for (uint32_t i = t; i < CS_CLEN / 32; i += CS_GT) {
-            tm.tmask[i] = a.tb.tmask[(size_t)prn * (CS_CLEN / 32) + i];
-            tm.tcoarse[i] = a.tb.tcoarse[(size_t)prn * (CS_CLEN / 32) + i];
-            tm.tbits[i] = a.tb.tbits[(size_t)prn * (CS_CLEN / 32) + i];
-        }
-        for (uint32_t i = t; i < per_ch; i += CS_GT) tm.run[i] = cw.acc[i];
-        for (uint32_t k0 = 8 * t; k0 < nt; k0 += 8 * CS_GT) {
-            uint32_t lo = k0, hi = k0;
-            for (uint32_t k = k0 + 1; k < min(k0 + 8, nt); ++k) {
-                if (cw.taps[k] < cw.taps[lo]) lo = k;
-                if (cw.taps[k] > cw.taps[hi]) hi = k;
-            }
-            tm.grp[k0 >> 3] = lo | (hi << 16);
-        }
-        if (t == 0) {
-            const uint64_t r = *cw.r;
-            tm.u[0] = *cw.theta;
-            tm.u[1] = (uint32_t)*cw.w;
-            tm.u[2] = (uint32_t)r;
-            tm.phi[0] = *cw.phi;
-            tm.d[0] = *cw.v;
-            tm.d[1] = *cw.fcarr;
-            tm.d[2] = *cw.fcode;
-            ws.cs = *cw.cs;
-            ws.epochs = *cw.epochs;
-            ws.closed = 0;
-            ws.stop = r >= (1ull << 32) ? 1u : 0u;
-            ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)r);
-        }
-    }
+    const uint32_t nt = active ? wk[g].ntaps : 0u, per_ch = 2 * nt;
+    if (active) cs_walk_load(t, tm, ws, wk[g], a.tb, N);
     __syncthreads();
-
     const int8_t *base = wk[0].iq;
     for (uint32_t b = 0; b < grp.n_blocks; ++b) {
         const int8_t *blk = base + 2 * (size_t)b * N;
@@ -1043,114 +1190,135 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs(CsCod
         }
         if (active && t == 0) ws.pos = 0;
         __syncthreads();                                  // the block's prefix sums in place
-        if (active) {
-            const CodeWalk &cw = wk[g];
-            for (;;) {
-                // ws is written by the team's thread 0 only, before the team barrier that
-                // ends the previous stretch, so every thread of the team reads the same
-                if (ws.stop || ws.pos >= N) break;
-                const uint32_t o0 = ws.pos;
-                const uint32_t L = (uint32_t)min(ws.rem, (uint64_t)(N - o0));
-                const bool ends = (uint64_t)L == ws.rem;
-                for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
-                team_sync(bar);
-                cs_channel_range(t, bar, tm, h.Wp, blk, o0, L, nt, tab);
-                team_sync(bar);                           // the stretch's sums are in tm.acc
-                const uint32_t slot = ws.closed;
-                const bool store = ends && slot < cw.cap;
-                int32_t *dst = cw.dumps + (size_t)slot * per_ch;
-                for (uint32_t e = t; e < per_ch; e += CS_GT) {
-                    const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
-                    if (ends) {
-                        tm.acc[e] = (int32_t)val;
-                        tm.run[e] = 0;
-                        if (store) dst[e] = (int32_t)val;
-                    } else {
-                        tm.run[e] = (int32_t)val;
-                    }
-                }
-                if (ends) {
-                    team_sync(bar);                       // the epoch's sums are in tm.acc
-                    // this channel's loops on the team's first two warps: thread 0 the PLL
-                    // part and the rest, threads 32 and 33 the early and late envelopes and
-                    // the DLL part
-                    const uint32_t pbar = 8 + g;
-                    if (t < 32) {
-                        LoopConsts lc{};
-                        PllOut po{0.0, 0.0};
-                        FinishPre fp{};
-                        if (t == 0) {
-                            lc.k1 = __dmul_rn(cw.cl.w0sq,
-                                              __ddiv_rn((double)(ws.cs.samples_in_epoch + L), cw.cl.fs));
-                            lc.k2 = cw.cl.k2;
-                            lc.kdll = cw.cl.kdll;
-                            lc.sfs = cw.cl.sfs;
-                            po = loop_pll(tm.d[0], tm.acc[2 * cw.tap_p], tm.acc[2 * cw.tap_p + 1], lc);
-                            fp = loop_finish_pre(po, lc);
-                        }
-                        asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");   // the DLL part is in s_corr
-                        if (t == 0) {
-                            const LoopOut lo = loop_finish_post(fp, h.s_corr[g], lc);
-                            const uint32_t seg_total = ws.cs.samples_in_epoch + L;
-                            if (store) cw.lens[slot] = seg_total;
-                            else atomicOr(cw.err, 1u);
-                            tm.d[0] = lo.v;
-                            tm.d[1] = lo.f_carr;
-                            tm.d[2] = lo.f_code;
-                            ws.epochs += 1;
-                            bitsync_step(ws.cs, tm.acc[2 * cw.tap_p], cw.sync_k);
-                            ws.cs.samples_in_epoch = 0;
-                            ws.closed = slot + 1;
-                            tm.u[0] = tm.u[0] + L * tm.u[1];   // the stretch ran on the old words
-                            tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
-                            tm.u[1] = (uint32_t)lo.w;
-                            tm.u[2] = (uint32_t)lo.r;
-                            if (lo.r >= (1ull << 32)) {
-                                atomicOr(cw.err, 2u);
-                                ws.stop = 1u;
-                            }
-                            ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)lo.r);
-                            ws.pos = o0 + L;
-                        }
-                    } else if (t < 64) {
-                        const LoopConsts lc{0.0, 0.0, cw.cl.kdll, 0.0};
-                        double m = 0.0;
-                        if (t < 34) {
-                            const uint32_t k = t == 33 ? (uint32_t)cw.tap_l : (uint32_t)cw.tap_e;
-                            m = loop_envelope(tm.acc[2 * k], tm.acc[2 * k + 1]);
-                        }
-                        const double ml = __shfl_down_sync(0xffffffffu, m, 1);
-                        if (t == 32) h.s_corr[g] = loop_dll(m, ml, tm.taps[cw.tap_e], tm.taps[cw.tap_l], lc);
-                        asm volatile("bar.sync %0, 64;" ::"r"(pbar) : "memory");
-                    }
-                } else if (t == 0) {
-                    tm.u[0] = tm.u[0] + L * tm.u[1];
-                    tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
-                    ws.pos = o0 + L;
-                    ws.rem -= L;
-                    ws.cs.samples_in_epoch += L;
-                }
-                team_sync(bar);                           // new words, position and state in place
-            }
-        }
+        if (active) cs_walk_block(t, g, bar, tm, ws, wk[g], h.Wp, blk, N, nt, per_ch, tab, h.s_corr, [] {});
         __syncthreads();                                  // every team has reached the block's end
     }
-    if (active) {
-        const CodeWalk &cw = wk[g];
-        if (t == 0) {
-            *cw.cs = ws.cs;
-            *cw.v = tm.d[0];
-            *cw.fcarr = tm.d[1];
-            *cw.fcode = tm.d[2];
-            *cw.epochs = ws.epochs;
-            *cw.theta = tm.u[0];
-            *cw.w = (int32_t)tm.u[1];
-            *cw.phi = tm.phi[0];
-            *cw.r = tm.u[2];
-            *cw.nclosed = min(ws.closed, cw.cap);
+    if (active) cs_walk_store(t, tm, ws, wk[g], per_ch);
+}
+
+// The walk with two prefix buffers (where they fit): block b's prefix sums are in buffer
+// b & 1, and the next block's are built in 512-sample units, taken by ticket, by whichever
+// warps are idle: a team's two spare warps while its first two close an epoch's loops,
+// and any team that reaches a block before its prefix sums are complete.  Teams do not
+// wait for one another at block ends.  The last team to leave a block frees its buffer
+// for the block two on.  A team waits (bounded: 2 s, then an error) only for its next
+// block's prefix sums, whose units other warps are building without waiting, and for
+// that buffer to be free, which the slowest team always reaches; so every wait ends.
+struct CsDbState {
+    uint32_t next[2], done[2], readers[2];
+    volatile uint32_t tag[2];    // the block whose prefix sums buffer p holds or is being built for
+    volatile uint32_t fail;      // a wait timed out: every team stops
+};
+
+__device__ __forceinline__ void cs_db_help(CsDbState &db, uint32_t bb, uint32_t nb, uint32_t U, const int8_t *base,
+                                           uint32_t N, uint32_t *const *P) {
+    if (bb >= nb) return;
+    const uint32_t p = bb & 1u;
+    if (db.tag[p] != bb) return;
+    const int8_t *blk = base + 2 * (size_t)bb * N;
+    const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(&db.next[p], 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= U) break;
+        cs_prefix_unit(blk, N, a16, a4, P[p], 32u * u);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicAdd(&db.done[p], 1u);
         }
-        for (uint32_t i = t; i < per_ch; i += CS_GT) cw.acc[i] = tm.run[i];
     }
+}
+
+__global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs2(CsCodeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ CsWalkState s_ws[CS_MAX_TEAMS];
+    __shared__ CsDbState db;
+    const uint32_t mt = a.max_taps;
+    const CsShared h = cs_shared(smem, mt, a.max_n);
+    size_t o[4];
+    uint32_t *P[2] = {h.Wp, reinterpret_cast<uint32_t *>(smem + cs_layout(blockDim.x / CS_GT, mt, a.max_n, o))};
+    uint32_t *tab = g_item_tab;
+    const CsCodeGroup grp = a.groups[blockIdx.x];
+    const uint32_t n = grp.n, N = grp.N, nb = grp.n_blocks;
+    const uint32_t U = (((N + 15) >> 4) + 31) >> 5;          // units of 32 chunks
+    const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
+    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t bar = 2 + g;
+    const CsTeam tm = cs_team(h.teams + (size_t)g * h.tbytes, mt);
+    const bool active = g < n;
+    const CodeWalk *wk = a.walks + grp.w0;
+    CsWalkState &ws = s_ws[g];
+    for (uint32_t i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = a.tb.carrier[i];
+    const uint32_t nt = active ? wk[g].ntaps : 0u, per_ch = 2 * nt;
+    if (active) cs_walk_load(t, tm, ws, wk[g], a.tb, N);
+    const int8_t *base = wk[0].iq;
+    for (uint32_t bb = 0; bb < 2 && bb < nb; ++bb) {
+        const int8_t *blk = base + 2 * (size_t)bb * N;
+        const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
+        cs_prefix_share(blk, N, a16, a4, P[bb], warp, nw);
+    }
+    if (threadIdx.x == 0) {
+        for (uint32_t p = 0; p < 2; ++p) {
+            db.next[p] = U;
+            db.done[p] = U;
+            db.readers[p] = 0;
+            db.tag[p] = p;
+        }
+        db.fail = 0;
+    }
+    __syncthreads();
+    if (!active) return;
+    for (uint32_t b = 0; b < nb; ++b) {
+        const uint32_t p = b & 1u;
+        const int8_t *blk = base + 2 * (size_t)b * N;
+        if (t == 0 && b + 1 < nb) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
+        // this block's prefix sums: help build them, then wait for the last units (bounded)
+        {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 0;; ++it) {
+                if (db.fail) break;
+                if (db.tag[p] == b) {
+                    cs_db_help(db, b, nb, U, base, N, P);
+                    if (*(volatile uint32_t *)&db.done[p] >= U) break;
+                }
+                if (it > (1u << 24) || globaltimer_ns() - t0 > 2000000000ull) {
+                    if ((t & 31u) == 0) {
+                        db.fail = 1u;
+                        atomicOr(wk[g].err, 4u);
+                    }
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence_block();
+        }
+        team_sync(bar);
+        // the team's decision is thread 0's alone (another team may set the failure flag at
+        // any time): a failed walk stops this channel, which still takes part in the
+        // buffer releases below so that no other team waits for it
+        if (t == 0) {
+            ws.pos = 0;
+            if (db.fail) ws.stop = 1u;
+        }
+        team_sync(bar);
+        cs_walk_block(t, g, bar, tm, ws, wk[g], P[p], blk, N, nt, per_ch, tab, h.s_corr,
+                      [&] { cs_db_help(db, b + 1, nb, U, base, N, P); });
+        team_sync(bar);
+        if (t == 0) {
+            // the last team to leave block b frees its buffer for block b + 2
+            if (atomicAdd(&db.readers[p], 1u) == n - 1 && b + 2 < nb) {
+                db.next[p] = 0;
+                db.done[p] = 0;
+                db.readers[p] = 0;
+                __threadfence_block();
+                db.tag[p] = b + 2;
+            }
+        }
+    }
+    cs_walk_store(t, tm, ws, wk[g], per_ch);
 }
 
 template <bool T3>
@@ -1235,6 +1403,34 @@ cudaError_t cs_code_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(k_batch_code_cs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_batch_code_cs<<<grid, cs_threads(cpg), smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+size_t cs_code_db_smem(uint32_t cpg, uint32_t mt, uint32_t max_n) {
+    size_t o[4];
+    return cs_layout(cpg, mt, max_n, o) + cs_wp_words(max_n) * 4;
+}
+
+int cs_code_db_occupancy(uint32_t cpg, size_t smem) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return 0;
+    if (cudaFuncSetAttribute(k_batch_code_cs2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_code_cs2, (int)cs_threads(cpg), smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t cs_code_db_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsCodeArgs &a) {
+    if (cpg < 1 || cpg > CS_MAX_TEAMS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_code_cs2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_code_cs2<<<grid, cs_threads(cpg), smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -518,6 +518,11 @@ struct CsCodeArgs {
 };
 int cs_code_occupancy(uint32_t cpg, size_t smem);
 cudaError_t cs_code_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsCodeArgs &a);
+// The same walk with two prefix buffers (the next block's built by idle warps); its
+// shared memory, residency and launch.
+size_t cs_code_db_smem(uint32_t cpg, uint32_t mt, uint32_t max_n);
+int cs_code_db_occupancy(uint32_t cpg, size_t smem);
+cudaError_t cs_code_db_launch(uint32_t cpg, uint32_t grid, size_t smem, cudaStream_t stream, const CsCodeArgs &a);
 
 // Resident serving CTAs per SM (0: the configuration does not fit).
 int cs_serve_occupancy(uint32_t cpg, size_t smem, bool table3);

@@ -105,7 +105,7 @@ def _check_run(b, recv, sigs, chans, first_block, n_blocks):
             assert gb == ch.bs.as_dict(), (i, c)
 
 
-@pytest.mark.parametrize("tiles", [WALKS[0], WALKS[3]])
+@pytest.mark.parametrize("tiles", [WALKS[0], WALKS[2], WALKS[3]])
 def test_bit_sync_in_the_batched_form(tiles):
     """Receivers whose data bits change on code-period boundaries: after 1.2 s every
     channel at 45 dB-Hz has found the bit edge and decodes the generator's bits."""
@@ -175,8 +175,11 @@ def test_modes_need_a_restart_to_switch():
 
 
 def test_both_walkers_agree_on_the_uniform_workload():
-    """The two walkers over 8 receivers x 12 channels x 5 taps at 16.368 MHz, 60 blocks:
-    every epoch's dump and length, the state and the bit synchroniser identical."""
+    """The walkers over 8 receivers x 12 channels x 5 taps at 16.368 MHz, 60 blocks: the
+    carrier-segment walk with one prefix buffer (3 channels per CTA) and with two (6
+    channels per CTA, the next block's prefix sums built by idle warps), and the chunk
+    walker; every epoch's dump and length, the state and the bit synchroniser
+    identical."""
     recv = [synth.uniform_receiver(i, n_blocks=60) for i in range(8)]
     offs, total = batch_layout(recv)
     buf = torch.zeros(total, dtype=torch.int8, device="cuda")
@@ -184,7 +187,7 @@ def test_both_walkers_agree_on_the_uniform_workload():
         iq = synth.generate_iq(r, device="cuda")
         buf[int(o):int(o) + iq.numel()] = iq.view(-1)
     out = []
-    for tiles in (None, (2, 224, 0, rx.RX_SCHED_PIPE)):
+    for tiles in (None, (6, 128, 0, rx.RX_SCHED_SEGMENT), (2, 224, 0, rx.RX_SCHED_PIPE)):
         b = _batch(recv, 60, tiles)
         try:
             rx.rx_batch_run_code(b, buf, offs, 60, rx.RX_RUN_RESTART)
@@ -200,6 +203,35 @@ def test_both_walkers_agree_on_the_uniform_workload():
             out.append(res)
         finally:
             rx.rx_batch_destroy(b)
-    for (d0, l0, n0, s0, c0), (d1, l1, n1, s1, c1) in zip(*out):
-        assert np.array_equal(n0, n1) and np.array_equal(d0, d1) and np.array_equal(l0, l1)
-        assert s0 == s1 and c0 == c1
+    for other in out[1:]:
+        for (d0, l0, n0, s0, c0), (d1, l1, n1, s1, c1) in zip(out[0], other):
+            assert np.array_equal(n0, n1) and np.array_equal(d0, d1) and np.array_equal(l0, l1)
+            assert s0 == s1 and c0 == c1
+
+
+def test_double_buffered_walk_matches_oracle():
+    """Six channels per CTA at 8.184 MHz, where the two prefix buffers fit: 3 receivers x
+    12 channels, 24 blocks, bit-exact with the oracle, and a run split in two continues."""
+    n_blocks = 24
+    recv = [synth.serving_stream(k, n_blocks=n_blocks) for k in range(3)]
+    offs, total = batch_layout(recv)
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for r, o in zip(recv, offs):
+        iq = synth.generate_iq(r).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    dev = torch.from_numpy(buf).cuda()
+    b = _batch(recv, n_blocks, (6, 128, 0, rx.RX_SCHED_SEGMENT))
+    try:
+        rx.rx_batch_run_code(b, dev, offs, n_blocks, rx.RX_RUN_RESTART)
+        chans = [_oracle_channels(r) for r in recv]
+        _check_run(b, recv, sigs, chans, 0, n_blocks)
+        rx.rx_batch_run_code(b, dev, offs, 11, rx.RX_RUN_RESTART)
+        chans = [_oracle_channels(r) for r in recv]
+        _check_run(b, recv, sigs, chans, 0, 11)
+        offs2 = np.array([int(o) + 2 * 11 * r.block_samples for o, r in zip(offs, recv)], np.uint64)
+        rx.rx_batch_run_code(b, dev, offs2, 13, 0)
+        _check_run(b, recv, sigs, chans, 11, 13)
+    finally:
+        rx.rx_batch_destroy(b)
