@@ -56,6 +56,10 @@ PROFILED = {
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
                          "src_sha256": "capture predates source hashing"},
 }
+# The same, for the other batched workloads' legs, keyed by (workload, schedule, threads,
+# channels per item): executed thread instructions per sample*channel from a capture of
+# that workload's kernel at those tiles (16 receivers x 50 blocks of the multicorrelator).
+PROFILED_CONFIG = {}
 KERNEL_SOURCES = {
     "pipelined": ["rx_pipe.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
     "static": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
@@ -609,6 +613,12 @@ def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stre
     sc = sum(r.block_samples * len(r.channels) * n_blocks for r in receivers)
     ops = sum(r.block_samples * len(r.channels) * n_blocks * ops_per_sample_channel(r.n_taps) for r in receivers)
     achieved = ops / (ms / 1000) / 1e12
+    executed = None
+    prof = PROFILED_CONFIG.get((name, SCHEDULES[got[3]], got[1], got[0]))
+    if prof and prof["src_sha256"] == kernel_sources_sha256(SCHEDULES[got[3]]):
+        ex_rate = sc * prof["thread_inst_per_sample_channel"] / (ms / 1000) / 1e12
+        executed = {"thread_inst_per_sample_channel": prof["thread_inst_per_sample_channel"],
+                    "achieved": ex_rate, "frac": ex_rate / peak_tops, "src_sha256": prof["src_sha256"]}
     in_bytes = sum(2 * r.block_samples * n_blocks for r in receivers)
     out = {
         "metric": METRIC, "value": sc / (ms / 1000) / 1e6, "unit": "Msample*channel/s", "ms_per_step": ms,
@@ -623,6 +633,7 @@ def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stre
                      "frac": achieved / peak_tops, "traffic": None,
                      "model": "direct form, 8 + 3T INT32 ops per sample*channel with each receiver's T; "
                               "peak = the measured INT32 issue rate",
+                     "executed": executed,
                      "hbm_gbs": in_bytes / (ms / 1000) / 1e9},
         "e2e": {"value": sc / e2e_s / 1e6, "unit": "Msample*channel/s", "ms_per_step": e2e_s * 1000,
                 "h2d_bytes_per_step": int(in_bytes), "d2h_bytes_per_step": int(d2h)},
