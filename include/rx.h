@@ -390,14 +390,17 @@ rx_status rx_batch_read_all_dumps(rx_batch b, int32_t *out, size_t cap, uint32_t
  * run at each epoch with T = its samples / fs and the bit synchroniser stepped
  * (bitsync_count 8); integ_blocks does not apply.  iq must be device memory.
  * One launch, synchronous.  With the default tiles or RX_SCHED_SEGMENT it runs
- * the carrier-segment walk: a CTA takes channels_per_item channels (at most 6;
- * by default 6 with two prefix buffers where they fit, the next block's built
- * by idle warps, else 3 with one) of one receiver, builds each block's prefix
- * sums once for them, and correlates each channel in stretches between its own
- * epoch ends; with the other schedules, or where a block exceeds 65536 samples
- * or the CTA's shared memory does not fit, one CTA per channel walks in the
- * chunk forms.  The results are the same.  RX_ETIMEOUT if the two-buffer
- * walk's bounded wait for prefix sums runs out.  The state continues from the
+ * the carrier-segment walk: a CTA takes channels_per_item channels (at most 6)
+ * of one receiver and builds each block's prefix sums once for them.  With six
+ * channels and two prefix buffers, where they fit (the default), it walks in
+ * rounds of one block: each channel correlates from its last epoch end to its
+ * next as one range over two blocks' prefix sums, the loops of the channels
+ * that closed an epoch run together, and the other warps meanwhile build the
+ * block after next; otherwise (3 channels by default, one buffer) each channel
+ * is correlated in stretches between its own epoch ends within each block.
+ * With the other schedules, or where a block exceeds 65536 samples or the
+ * CTA's shared memory does not fit, one CTA per channel walks in the chunk
+ * forms.  The results are the same.  The state continues from the
  * previous code-period run, or from the starting state with RX_RUN_RESTART;
  * switching between block runs and code-period runs needs RX_RUN_RESTART
  * (RX_ESTATE otherwise). */

@@ -1590,7 +1590,6 @@ extern "C" rx_status rx_batch_run_code(rx_batch b, const int8_t *iq, const uint6
     RX_CUDA_TRY(cudaStreamSynchronize(b->stream), E);
     b->last_mode = 2;
     b->last_launches = 1;
-    if (cerr & 4u) return berr(b, RX_ETIMEOUT, "a code-period walk's wait for prefix sums timed out");
     if (cerr & 2u) return berr(b, RX_EINVAL, "a channel's code word reached 2^32");
     if (cerr & 1u) return berr(b, RX_EINVAL, "a channel closed more epochs than the ring holds");
     return RX_OK;

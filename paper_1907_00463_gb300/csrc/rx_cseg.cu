@@ -169,9 +169,10 @@ __device__ __forceinline__ uint32_t cs_first(const CsChan &c, uint32_t k) {
 // chips (|offset| <= 64 chips) stay on the extended chip axis with one index to spare
 // (the transition count below the index after the last chip is read).  The last chip of
 // a tap is at most (phi >> 32) + 64 + floor((L - 1) r / 2^32) + 1.
-__device__ __forceinline__ bool cs_eligible(const CsChan &c, uint32_t o0, uint32_t L, uint64_t phi) {
-    if (L < 2 || o0 + L > CS_NMAX || c.r < 0x10000u) return false;
-    if (cs_kappa(c, L - 1) + ((o0 + L - 1) >> 8) - (o0 >> 8) + 1 > CS_SEG_MAX) return false;
+template <class Win>
+__device__ __forceinline__ bool cs_eligible(const Win &win, const CsChan &c, uint32_t o0, uint32_t L, uint64_t phi) {
+    if (L < 2 || !win.fits(o0, L) || c.r < 0x10000u) return false;
+    if (cs_kappa(c, L - 1) + win.grp(o0 + L - 1) - win.grp(o0) + 1 > CS_SEG_MAX) return false;
     const uint64_t chips = ((uint64_t)(L - 1) * c.r) >> 32;
     return (phi >> 32) + 65u + chips <= (uint64_t)(CS_CLEN - CS_CBASE - 2);
 }
@@ -259,17 +260,50 @@ __device__ __forceinline__ void cs_prefix_share(const int8_t *blk, uint32_t N, b
 // start the empty sum is 0x80008000.
 __device__ __forceinline__ uint32_t cs_v(const uint32_t *Wp, uint32_t n) { return Wp[cs_sw(n)] - 0x00800080u * (n + 1u); }
 
+// The prefix sums a range reads, by sample index n from the first block's start: one
+// block's (CsWin1), or two consecutive blocks' (CsWin2: samples N.. are the second
+// block's, whose prefix words and 256-sample groups start afresh at its first sample,
+// so the first block's last group may be short).  grp numbers the groups across the
+// window (segments break at group starts).
+struct CsWin1 {
+    const uint32_t *W;
+    __device__ __forceinline__ uint32_t v(uint32_t n) const { return cs_v(W, n); }
+    __device__ __forceinline__ uint32_t grp(uint32_t n) const { return n >> 8; }
+    __device__ __forceinline__ bool gstart(uint32_t n) const { return (n & 255u) == 0u; }
+    __device__ __forceinline__ uint32_t next_gstart(uint32_t n) const { return (n | 255u) + 1u; }
+    __device__ __forceinline__ bool fits(uint32_t o0, uint32_t L) const { return o0 + L <= CS_NMAX; }
+};
+
+struct CsWin2 {
+    const uint32_t *W0;
+    int32_t d;                   // the second block's prefix words start at W0 + d
+    uint32_t N;
+    __device__ __forceinline__ uint32_t v(uint32_t n) const {
+        const uint32_t m = n < N ? n : n - N;
+        return W0[(n < N ? 0 : d) + (int32_t)cs_sw(m)] - 0x00800080u * (m + 1u);
+    }
+    __device__ __forceinline__ uint32_t grp(uint32_t n) const {
+        return n < N ? n >> 8 : ((N + 255u) >> 8) + ((n - N) >> 8);
+    }
+    __device__ __forceinline__ bool gstart(uint32_t n) const { return ((n < N ? n : n - N) & 255u) == 0u; }
+    __device__ __forceinline__ uint32_t next_gstart(uint32_t n) const {
+        return n < N ? min((n | 255u) + 1u, N) : N + (((n - N) | 255u) + 1u);
+    }
+    __device__ __forceinline__ bool fits(uint32_t o0, uint32_t L) const { return L <= CS_NMAX && o0 + L <= 2u * N; }
+};
+
 // Segment table, first part.  Team thread t walks samples [p0, p1) of its span, cut at
 // carrier crossings and group starts, sums the rotated samples (DI, DQ) and writes, for
 // each segment that starts in its span, K relative to the span's start.  Returns the
 // range of segment indices written (any = false if none).
-__device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uint32_t o0, uint32_t L,
+template <class Win>
+__device__ __forceinline__ void cs_seg_local(uint32_t t, const Win &win, uint32_t o0, uint32_t L,
                                              const CsChan &c, const uint32_t *tab, uint4 *seg, uint32_t &DI,
                                              uint32_t &DQ, uint32_t &sfirst, uint32_t &slast, bool &any) {
     // positions p are relative to the range's first sample o0; prefix words and 256-sample
     // groups are the block's (n = o0 + p)
     const uint32_t span = ((L + CS_GT - 1u) / CS_GT) | 1u;
-    const uint32_t p0 = t * span, p1 = min(p0 + span, L), g0 = o0 >> 8;
+    const uint32_t p0 = t * span, p1 = min(p0 + span, L), g0 = win.grp(o0);
     DI = 0u;
     DQ = 0u;
     sfirst = slast = 0u;
@@ -277,9 +311,9 @@ __device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uin
     if (p0 >= p1) return;
     uint32_t kap = cs_kappa(c, p0);
     const uint32_t n0 = o0 + p0;
-    bool start = p0 == 0u || (n0 & 255u) == 0u || cs_kappa(c, p0 - 1u) != kap;
-    uint32_t Vprev = (n0 & 255u) == 0u ? 0x80008000u : cs_v(Wp, n0 - 1u);
-    uint32_t ng = (n0 | 255u) + 1u - o0;
+    bool start = p0 == 0u || win.gstart(n0) || cs_kappa(c, p0 - 1u) != kap;
+    uint32_t Vprev = win.gstart(n0) ? 0x80008000u : win.v(n0 - 1u);
+    uint32_t ng = win.next_gstart(n0) - o0;
     uint32_t nc = c.a ? cs_first(c, kap + 1u) : 0xffffffffu;
     uint32_t p = p0;
     for (;;) {
@@ -287,19 +321,19 @@ __device__ __forceinline__ void cs_seg_local(uint32_t t, const uint32_t *Wp, uin
         const uint32_t R = tab[cs_bin(c, kap)];
         const uint32_t vI = dp2a_lo_us(Vprev, R, 0u), vQ = dp2a_hi_us(Vprev, R, 0u);
         if (start) {
-            const uint32_t sig = kap + ((o0 + p) >> 8) - g0;
+            const uint32_t sig = kap + win.grp(o0 + p) - g0;
             seg[sig] = make_uint4(DI - vI, DQ - vQ, R, 0u);
             if (!any) sfirst = sig;
             slast = sig;
             any = true;
         }
-        const uint32_t Vq = cs_v(Wp, o0 + q - 1u);
+        const uint32_t Vq = win.v(o0 + q - 1u);
         DI = dp2a_lo_us(Vq, R, DI) - vI;
         DQ = dp2a_hi_us(Vq, R, DQ) - vQ;
         if (q >= p1) break;
         start = true;
         if (q == ng) {
-            ng += 256u;
+            ng = win.next_gstart(o0 + q) - o0;
             Vprev = 0x80008000u;
         } else {
             Vprev = Vq;
@@ -388,25 +422,27 @@ __device__ __forceinline__ void cs_tap_diff(CsTap &t, const CsChan &c, int64_t o
 }
 
 // M(L) for the range: the segment of its last sample.
-__device__ __forceinline__ void cs_total(const uint32_t *Wp, const uint4 *seg, const CsChan &c, uint32_t o0,
+template <class Win>
+__device__ __forceinline__ void cs_total(const Win &win, const uint4 *seg, const CsChan &c, uint32_t o0,
                                          uint32_t L, uint32_t &mI, uint32_t &mQ) {
     const uint32_t n = L - 1u;
-    const uint4 e = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
-    const uint32_t V = cs_v(Wp, o0 + n);
+    const uint4 e = seg[cs_kappa(c, n) + win.grp(o0 + n) - win.grp(o0)];
+    const uint32_t V = win.v(o0 + n);
     mI = dp2a_lo_us(V, e.z, e.x);
     mQ = dp2a_hi_us(V, e.z, e.y);
 }
 
 // +-M(b) at one code transition (list entry e) of a tap.
-__device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsChan &c, const uint32_t *Wp,
+template <class Win>
+__device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsChan &c, const Win &win,
                                         const uint4 *seg, uint32_t o0, uint32_t &SI, uint32_t &SQ) {
     const uint32_t j = (e & 0x7fffu) - tp.c0p;                 // chips after the first
     const float bf = fmaf((float)j, c.Dr, -tp.F);
     uint32_t b = bf > 0.0f ? (uint32_t)ceilf(bf) : 0u;          // ceil((j 2^32 - frac) / r) or one less
     if ((uint64_t)b * c.r < (((uint64_t)j << 32) - tp.frac)) ++b;
     const uint32_t n = b - 1u;
-    const uint4 en = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
-    const uint32_t V = cs_v(Wp, o0 + n);
+    const uint4 en = seg[cs_kappa(c, n) + win.grp(o0 + n) - win.grp(o0)];
+    const uint32_t V = win.v(o0 + n);
     uint32_t mI = dp2a_lo_us(V, en.z, en.x), mQ = dp2a_hi_us(V, en.z, en.y);
     if (e & 0x8000u) {
         mI = 0u - mI;
@@ -418,9 +454,9 @@ __device__ __forceinline__ void cs_item(uint32_t e, const CsTap &tp, const CsCha
 
 // The transitions of TT taps, spread over the team (thread t takes the items whose
 // running index over all taps is t mod GT), reduced per warp into red[TT][2].
-template <int TT>
+template <int TT, class Win>
 __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &run, const uint16_t *list,
-                                         const uint32_t *Wp, const uint4 *seg, const CsChan &c, uint32_t o0,
+                                         const Win &win, const uint4 *seg, const CsChan &c, uint32_t o0,
                                          int32_t *red) {
     uint32_t SI[TT], SQ[TT];
 #pragma unroll
@@ -434,14 +470,14 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
         for (; i + 3 * CS_GT < tk.cnt; i += 4 * CS_GT) {       // four independent items per pass
             const uint32_t e0 = L[i], e1 = L[i + CS_GT], e2 = L[i + 2 * CS_GT], e3 = L[i + 3 * CS_GT];
             uint32_t aI = 0u, aQ = 0u, bI = 0u, bQ = 0u;
-            cs_item(e0, tk, c, Wp, seg, o0, aI, aQ);
-            cs_item(e1, tk, c, Wp, seg, o0, bI, bQ);
-            cs_item(e2, tk, c, Wp, seg, o0, aI, aQ);
-            cs_item(e3, tk, c, Wp, seg, o0, bI, bQ);
+            cs_item(e0, tk, c, win, seg, o0, aI, aQ);
+            cs_item(e1, tk, c, win, seg, o0, bI, bQ);
+            cs_item(e2, tk, c, win, seg, o0, aI, aQ);
+            cs_item(e3, tk, c, win, seg, o0, bI, bQ);
             SI[k] += aI + bI;
             SQ[k] += aQ + bQ;
         }
-        for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, Wp, seg, o0, SI[k], SQ[k]);
+        for (; i < tk.cnt; i += CS_GT) cs_item(L[i], tk, c, win, seg, o0, SI[k], SQ[k]);
     }
     const uint32_t lane = t & 31;
 #pragma unroll
@@ -463,9 +499,9 @@ __device__ __forceinline__ void cs_items(uint32_t t, const CsTap *tp, uint32_t &
 // exactly: with off_k - off_ref = D_k r + E_k, E_k in [0, r),
 //   b_k = ceil((j 2^32 - frac_ref - off_k + off_ref) / r) = b_ref - D_k - [rho + E_k >= r],
 // and the tap takes the transition when 1 <= b_k <= N - 1 (its chip range in the block).
-template <int TT>
+template <int TT, class Win>
 __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_t ref, uint32_t mx, uint32_t &run,
-                                            const uint16_t *list, const uint32_t *Wp, const uint4 *seg,
+                                            const uint16_t *list, const Win &win, const uint4 *seg,
                                             const CsChan &c, uint32_t o0, uint32_t N, int32_t *red) {
     uint32_t SI[TT], SQ[TT], D[TT], Fr[TT];
 #pragma unroll
@@ -491,8 +527,8 @@ __device__ __forceinline__ void cs_items_tm(uint32_t t, const CsTap *tp, uint32_
             const uint32_t bk = b - D[k] - (rho >= Fr[k] ? 1u : 0u);
             const bool valid = bk - 1u < N - 1u;
             const uint32_t n = valid ? bk - 1u : 0u;
-            const uint4 en = seg[cs_kappa(c, n) + ((o0 + n) >> 8) - (o0 >> 8)];
-            const uint32_t V = cs_v(Wp, o0 + n);
+            const uint4 en = seg[cs_kappa(c, n) + win.grp(o0 + n) - win.grp(o0)];
+            const uint32_t V = win.v(o0 + n);
             const uint32_t w = (uint32_t)(valid ? sg : 0);
             SI[k] += w * dp2a_lo_us(V, en.z, en.x);
             SQ[k] += w * dp2a_hi_us(V, en.z, en.y);
@@ -607,13 +643,14 @@ __device__ inline CsTeam cs_team(unsigned char *base, uint32_t mt) {
 // Correlate the team's channel over the L samples from sample o0 of the block (its NCO
 // words and phases, in the team area, are those of sample o0) into tm.acc (zero on
 // entry).  Wp holds the block's prefix sums.
-__device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
+template <class Win>
+__device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const CsTeam &tm, const Win &win,
                                                  const int8_t *blk, uint32_t o0, uint32_t N, uint32_t nt,
                                                  const uint32_t *tab) {
     const uint32_t theta = tm.u[0], w = tm.u[1], r = tm.u[2];
     const uint64_t phi = tm.phi[0];
     const CsChan c = cs_chan(theta, w, r);
-    if (cs_eligible(c, o0, N, phi)) {
+    if (cs_eligible(win, c, o0, N, phi)) {
         // the taps' constants: the chip part on the first warps and the part relative to
         // each group's reference tap on the warps after them, so that no warp carries both
         // chains before its share of the segment pass (one pass when 2 x 32-lane-rounded
@@ -634,11 +671,11 @@ __device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const
         }
         uint32_t DI, DQ, sf, sl;
         bool any;
-        cs_seg_local(t, Wp, o0, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
+        cs_seg_local(t, win, o0, N, c, tab, tm.seg, DI, DQ, sf, sl, any);
         cs_seg_scan(t, bar, DI, DQ, tm.s_warp, tm.seg, sf, sl, any);
         team_sync(bar);                                   // segment table and tap constants complete
         uint32_t mI = 0u, mQ = 0u;
-        if (t < nt) cs_total(Wp, tm.seg, c, o0, N, mI, mQ);
+        if (t < nt) cs_total(win, tm.seg, c, o0, N, mI, mQ);
         for (uint32_t k = t; k < nt; k += CS_GT) {
             const int32_t g = tm.tap[k].g_end;
             atomicAdd((unsigned *)&tm.acc[2 * k], (uint32_t)g * mI);
@@ -654,22 +691,22 @@ __device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const
             const CsTap *tp = tm.tap + k0;
             int32_t *rd = tm.acc + 2 * k0;
             switch ((tmj ? 8u : 0u) + min(8u, nt - k0)) {
-                case 1: cs_items<1>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 2: cs_items<2>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 3: cs_items<3>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 4: cs_items<4>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 5: cs_items<5>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 6: cs_items<6>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 7: cs_items<7>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 8: cs_items<8>(t, tp, run, tm.list, Wp, tm.seg, c, o0, rd); break;
-                case 9: cs_items_tm<1>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 10: cs_items_tm<2>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 11: cs_items_tm<3>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 12: cs_items_tm<4>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 13: cs_items_tm<5>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 14: cs_items_tm<6>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                case 15: cs_items_tm<7>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
-                default: cs_items_tm<8>(t, tp, ref, mx, run, tm.list, Wp, tm.seg, c, o0, N, rd); break;
+                case 1: cs_items<1>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 2: cs_items<2>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 3: cs_items<3>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 4: cs_items<4>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 5: cs_items<5>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 6: cs_items<6>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 7: cs_items<7>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 8: cs_items<8>(t, tp, run, tm.list, win, tm.seg, c, o0, rd); break;
+                case 9: cs_items_tm<1>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 10: cs_items_tm<2>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 11: cs_items_tm<3>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 12: cs_items_tm<4>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 13: cs_items_tm<5>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 14: cs_items_tm<6>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                case 15: cs_items_tm<7>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
+                default: cs_items_tm<8>(t, tp, ref, mx, run, tm.list, win, tm.seg, c, o0, N, rd); break;
             }
         }
     } else {
@@ -683,7 +720,7 @@ __device__ __forceinline__ void cs_channel_range(uint32_t t, uint32_t bar, const
 __device__ __forceinline__ void cs_channel_block(uint32_t t, uint32_t bar, const CsTeam &tm, const uint32_t *Wp,
                                                  const int8_t *blk, uint32_t N, uint32_t nt, uint32_t prn,
                                                  const Tables &tb, const uint32_t *tab) {
-    cs_channel_range(t, bar, tm, Wp, blk, 0u, N, nt, tab);
+    cs_channel_range(t, bar, tm, CsWin1{Wp}, blk, 0u, N, nt, tab);
 }
 
 // Named barrier 15 over warps 0 and 1 (the loop-update pair).
@@ -1044,25 +1081,27 @@ __device__ __forceinline__ void cs_walk_load(uint32_t t, const CsTeam &tm, CsWal
     }
 }
 
-// One team's stretches over one block (its channel's state in tm and ws, the block's
-// prefix sums in Wp).  While its first two warps close an epoch's loops, the team's other
-// warps call idle() (the double-buffered walk builds the next block's prefix sums there).
-template <class Idle>
-__device__ __forceinline__ void cs_walk_block(uint32_t t, uint32_t g, uint32_t bar, const CsTeam &tm, CsWalkState &ws,
-                                              const CodeWalk &cw, const uint32_t *Wp, const int8_t *blk, uint32_t N,
-                                              uint32_t nt, uint32_t per_ch, const uint32_t *tab, double *s_corr,
-                                              Idle idle) {
-    for (;;) {
-        // ws is written by the team's thread 0 only, before the team barrier that
-        // ends the previous stretch, so every thread of the team reads the same
-        if (ws.stop || ws.pos >= N) break;
-        const uint32_t o0 = ws.pos;
-        const uint32_t L = (uint32_t)min(ws.rem, (uint64_t)(N - o0));
+// One stretch of a team's walk (its channel's state in tm and ws): the L samples from
+// sample o0 of the prefix window win (blk: the window's first sample), added to the open
+// epoch's sums; where the stretch reaches the epoch's end, the epoch's sums are dumped
+// and the channel's loops closed.  Thread 0 calls ranged() once the team no longer reads
+// the window's prefix sums; while the team's first two warps close an epoch's loops, its
+// other warps call idle() (the double-buffered walk builds prefix sums there).  ws is
+// written by the team's thread 0 only, before the team barrier that ends a stretch, so
+// every thread of the team reads the same.
+template <class Win, class Ranged, class Idle>
+__device__ __forceinline__ void cs_walk_stretch(uint32_t t, uint32_t g, uint32_t bar, const CsTeam &tm,
+                                                CsWalkState &ws, const CodeWalk &cw, const Win &win,
+                                                const int8_t *blk, uint32_t o0, uint32_t L, uint32_t N, uint32_t nt,
+                                                uint32_t per_ch, const uint32_t *tab, double *s_corr, Ranged ranged,
+                                                Idle idle) {
+    {
         const bool ends = (uint64_t)L == ws.rem;
         for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
         team_sync(bar);
-        cs_channel_range(t, bar, tm, Wp, blk, o0, L, nt, tab);
+        cs_channel_range(t, bar, tm, win, blk, o0, L, nt, tab);
         team_sync(bar);                           // the stretch's sums are in tm.acc
+        if (t == 0) ranged();
         const uint32_t slot = ws.closed;
         const bool store = ends && slot < cw.cap;
         int32_t *dst = cw.dumps + (size_t)slot * per_ch;
@@ -1143,6 +1182,19 @@ __device__ __forceinline__ void cs_walk_block(uint32_t t, uint32_t g, uint32_t b
     }
 }
 
+// One team's stretches over one block (the block's prefix sums in Wp): from where the
+// team stands to the end of its open epoch or of the block, whichever comes first.
+__device__ __forceinline__ void cs_walk_block(uint32_t t, uint32_t g, uint32_t bar, const CsTeam &tm, CsWalkState &ws,
+                                              const CodeWalk &cw, const uint32_t *Wp, const int8_t *blk, uint32_t N,
+                                              uint32_t nt, uint32_t per_ch, const uint32_t *tab, double *s_corr) {
+    for (;;) {
+        if (ws.stop || ws.pos >= N) break;
+        const uint32_t o0 = ws.pos;
+        const uint32_t L = (uint32_t)min(ws.rem, (uint64_t)(N - o0));
+        cs_walk_stretch(t, g, bar, tm, ws, cw, CsWin1{Wp}, blk, o0, L, N, nt, per_ch, tab, s_corr, [] {}, [] {});
+    }
+}
+
 // The team's channel state back to its walk descriptor.
 __device__ __forceinline__ void cs_walk_store(uint32_t t, const CsTeam &tm, const CsWalkState &ws, const CodeWalk &cw,
                                               uint32_t per_ch) {
@@ -1190,52 +1242,134 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs(CsCod
         }
         if (active && t == 0) ws.pos = 0;
         __syncthreads();                                  // the block's prefix sums in place
-        if (active) cs_walk_block(t, g, bar, tm, ws, wk[g], h.Wp, blk, N, nt, per_ch, tab, h.s_corr, [] {});
+        if (active) cs_walk_block(t, g, bar, tm, ws, wk[g], h.Wp, blk, N, nt, per_ch, tab, h.s_corr);
         __syncthreads();                                  // every team has reached the block's end
     }
     if (active) cs_walk_store(t, tm, ws, wk[g], per_ch);
 }
 
-// The walk with two prefix buffers (where they fit): block b's prefix sums are in buffer
-// b & 1, and the next block's are built in 512-sample units, taken by ticket, by whichever
-// warps are idle: a team's two spare warps while its first two close an epoch's loops,
-// and any team that reaches a block before its prefix sums are complete.  Teams do not
-// wait for one another at block ends.  The last team to leave a block frees its buffer
-// for the block two on.  A team waits (bounded: 2 s, then an error) only for its next
-// block's prefix sums, whose units other warps are building without waiting, and for
-// that buffer to be free, which the slowest team always reaches; so every wait ends.
-struct CsDbState {
-    uint32_t next[2], done[2], readers[2];
-    volatile uint32_t tag[2];    // the block whose prefix sums buffer p holds or is being built for
-    volatile uint32_t fail;      // a wait timed out: every team stops
-};
+// The walk with two prefix buffers (where they fit), in rounds: in round j the prefix
+// sums of blocks j and j + 1 are resident (buffers j & 1 and (j + 1) & 1), and every
+// channel, standing at sample p of block j (0 <= p <= N), correlates from p to the end of
+// its open epoch as one range over the two blocks (CsWin2), or to the end of block j + 1
+// if the epoch ends later.  Code periods and blocks are both about a millisecond long, so
+// every channel's range is about one block and the teams keep step without waiting long
+// for one another; the few channels whose next epoch end also falls inside block j (an
+// epoch end close after the block's start, or the walk's first round) take a second
+// range in a second phase.  After each phase's ranges the loops of every channel that
+// ended an epoch close together on warps 0 and 1, one lane per channel (warp 0 lane g
+// the PLL part and the rest, warp 1 lanes 2g and 2g + 1 the early and late envelopes and
+// the DLL part), so that a warp instruction of the double-precision pipe serves every
+// closing channel; while they close the last phase's loops, the other warps build block
+// j + 2's prefix sums into the buffer that block j leaves.  Every wait is a CTA or team
+// barrier.  The same operations as the per-channel walker, on the same samples in the
+// same order, so the same results.
 
-__device__ __forceinline__ void cs_db_help(CsDbState &db, uint32_t bb, uint32_t nb, uint32_t U, const int8_t *base,
-                                           uint32_t N, uint32_t *const *P) {
-    if (bb >= nb) return;
-    const uint32_t p = bb & 1u;
-    if (db.tag[p] != bb) return;
-    const int8_t *blk = base + 2 * (size_t)bb * N;
-    const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
-    const uint32_t lane = threadIdx.x & 31;
-    for (;;) {
-        uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(&db.next[p], 1u);
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= U) break;
-        cs_prefix_unit(blk, N, a16, a4, P[p], 32u * u);
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();
-            atomicAdd(&db.done[p], 1u);
+// A team's share of a phase: the L samples from sample p of the window, folded into the
+// open epoch's sums; at an epoch end the sums are dumped and kept in tm.acc for the loops.
+// The NCOs advance over the range with the words it was correlated with.
+template <class Win>
+__device__ __forceinline__ void cs_round_stretch(uint32_t t, uint32_t g, uint32_t bar, const CsTeam &tm,
+                                                 CsWalkState &ws, const CodeWalk &cw, const Win &win,
+                                                 const int8_t *blk, uint32_t p, uint32_t L, uint32_t nt,
+                                                 uint32_t per_ch, const uint32_t *tab, uint32_t *s_bnd) {
+    const bool ends = (uint64_t)L == ws.rem;
+    for (uint32_t e = t; e < per_ch; e += CS_GT) tm.acc[e] = 0;
+    team_sync(bar);
+    cs_channel_range(t, bar, tm, win, blk, p, L, nt, tab);
+    team_sync(bar);                               // the range's sums are in tm.acc
+    const uint32_t slot = ws.closed;
+    const bool store = ends && slot < cw.cap;
+    int32_t *dst = cw.dumps + (size_t)slot * per_ch;
+    for (uint32_t e = t; e < per_ch; e += CS_GT) {
+        const uint32_t val = (uint32_t)tm.acc[e] + (uint32_t)tm.run[e];
+        if (ends) {
+            tm.acc[e] = (int32_t)val;
+            tm.run[e] = 0;
+            if (store) dst[e] = (int32_t)val;
+        } else {
+            tm.run[e] = (int32_t)val;
         }
+    }
+    if (t == 0) {
+        tm.u[0] = tm.u[0] + L * tm.u[1];
+        tm.phi[0] = reduce_code_phase(tm.phi[0] + (uint64_t)L * tm.u[2]);
+        ws.cs.samples_in_epoch += L;
+        if (!ends) ws.rem -= L;
+        s_bnd[g] = ends ? 1u : 0u;
+    }
+}
+
+// The loops of every channel whose epoch closed in the phase, on warps 0 and 1 (the other
+// warps do not call this).  Lane g of warp 0: T = the epoch's samples / fs, the PLL part,
+// after the DLL part the rest, then the dump's length, the bit synchroniser and the end of
+// the next epoch; warp 1 lanes 2g and 2g + 1: the envelopes and the DLL part.
+__device__ __forceinline__ void cs_round_loops(uint32_t warp, uint32_t lane, uint32_t n, const CodeWalk *wk,
+                                               CsWalkState *s_ws, const CsShared &h, uint32_t mt, uint32_t N) {
+    if (warp == 0) {
+        const uint32_t j = lane;
+        const bool doit = j < n && h.s_bnd[j];
+        const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        LoopConsts lc{};
+        PllOut po{0.0, 0.0};
+        FinishPre fp{};
+        if (doit) {
+            const CodeWalk &cw = wk[j];
+            const CsWalkState &w = s_ws[j];
+            const uint32_t ne = w.cs.samples_in_epoch, ki = ne + 1u - N;
+            lc.k1 = ki < 3u ? w.k1[ki] : __dmul_rn(cw.cl.w0sq, __ddiv_rn((double)ne, cw.cl.fs));
+            lc.k2 = cw.cl.k2;
+            lc.kdll = cw.cl.kdll;
+            lc.sfs = cw.cl.sfs;
+            po = loop_pll(tj.d[0], tj.acc[2 * cw.tap_p], tj.acc[2 * cw.tap_p + 1], lc);
+            fp = loop_finish_pre(po, lc);
+        }
+        pair_sync();                                  // the DLL parts are in s_corr
+        if (doit) {
+            const CodeWalk &cw = wk[j];
+            CsWalkState &w = s_ws[j];
+            const LoopOut lo = loop_finish_post(fp, h.s_corr[j], lc);
+            const uint32_t slot = w.closed;
+            if (slot < cw.cap) cw.lens[slot] = w.cs.samples_in_epoch;
+            else atomicOr(cw.err, 1u);
+            tj.d[0] = lo.v;
+            tj.d[1] = lo.f_carr;
+            tj.d[2] = lo.f_code;
+            w.epochs += 1;
+            bitsync_step(w.cs, tj.acc[2 * cw.tap_p], cw.sync_k);
+            w.cs.samples_in_epoch = 0;
+            w.closed = slot + 1;
+            tj.u[1] = (uint32_t)lo.w;
+            tj.u[2] = (uint32_t)lo.r;
+            if (lo.r >= (1ull << 32)) {
+                atomicOr(cw.err, 2u);
+                w.stop = 1u;
+            }
+            w.rem = cs_epoch_rest(tj.phi[0], (uint32_t)lo.r);
+        }
+    } else if (warp == 1) {
+        const uint32_t j = lane >> 1;
+        const bool doit = j < n && h.s_bnd[j];
+        const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        double m = 0.0;
+        if (doit) {
+            const CodeWalk &cw = wk[j];
+            const uint32_t k = (lane & 1u) ? (uint32_t)cw.tap_l : (uint32_t)cw.tap_e;
+            m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
+        }
+        const double ml = __shfl_down_sync(0xffffffffu, m, 1);
+        if (doit && (lane & 1u) == 0u) {
+            const CodeWalk &cw = wk[j];
+            const LoopConsts lc{0.0, 0.0, cw.cl.kdll, 0.0};
+            h.s_corr[j] = loop_dll(m, ml, tj.taps[cw.tap_e], tj.taps[cw.tap_l], lc);
+        }
+        pair_sync();
     }
 }
 
 __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs2(CsCodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ CsWalkState s_ws[CS_MAX_TEAMS];
-    __shared__ CsDbState db;
     const uint32_t mt = a.max_taps;
     const CsShared h = cs_shared(smem, mt, a.max_n);
     size_t o[4];
@@ -1243,7 +1377,6 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs2(CsCo
     uint32_t *tab = g_item_tab;
     const CsCodeGroup grp = a.groups[blockIdx.x];
     const uint32_t n = grp.n, N = grp.N, nb = grp.n_blocks;
-    const uint32_t U = (((N + 15) >> 4) + 31) >> 5;          // units of 32 chunks
     const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
     const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t bar = 2 + g;
@@ -1260,65 +1393,53 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_code_cs2(CsCo
         const bool a16 = ((uintptr_t)blk & 15) == 0, a4 = ((uintptr_t)blk & 3) == 0;
         cs_prefix_share(blk, N, a16, a4, P[bb], warp, nw);
     }
-    if (threadIdx.x == 0) {
-        for (uint32_t p = 0; p < 2; ++p) {
-            db.next[p] = U;
-            db.done[p] = U;
-            db.readers[p] = 0;
-            db.tag[p] = p;
-        }
-        db.fail = 0;
-    }
+    if (threadIdx.x == 0 && nb > 2) prefetch_l2(base + 4 * (size_t)N, 2 * N);
     __syncthreads();
-    if (!active) return;
-    for (uint32_t b = 0; b < nb; ++b) {
-        const uint32_t p = b & 1u;
-        const int8_t *blk = base + 2 * (size_t)b * N;
-        if (t == 0 && b + 1 < nb) prefetch_l2(blk + 2 * (size_t)N, 2 * N);
-        // this block's prefix sums: help build them, then wait for the last units (bounded)
-        {
-            const uint64_t t0 = globaltimer_ns();
-            for (uint32_t it = 0;; ++it) {
-                if (db.fail) break;
-                if (db.tag[p] == b) {
-                    cs_db_help(db, b, nb, U, base, N, P);
-                    if (*(volatile uint32_t *)&db.done[p] >= U) break;
-                }
-                if (it > (1u << 24) || globaltimer_ns() - t0 > 2000000000ull) {
-                    if ((t & 31u) == 0) {
-                        db.fail = 1u;
-                        atomicOr(wk[g].err, 4u);
-                    }
-                    break;
-                }
-                __nanosleep(64);
+    uint32_t p = 0;                                       // the team's sample in block j (<= N)
+    for (uint32_t j = 0; j < nb; ++j) {
+        const uint32_t lim = j + 1 < nb ? 2u * N : N;
+        const int8_t *blk = base + 2 * (size_t)j * N;
+        const CsWin2 win{P[j & 1u], (int32_t)(P[(j + 1u) & 1u] - P[j & 1u]), N};
+        bool built = false;
+        for (;;) {
+            // ws is written by the team's thread 0 and by the closing lanes, each before a
+            // barrier that every thread of the team passes before it reads ws again
+            const bool want = active && !ws.stop && p < N;
+            if (!__syncthreads_or(want)) break;
+            if (want) {
+                const uint32_t L = (uint32_t)min(min(ws.rem, (uint64_t)(lim - p)), (uint64_t)CS_NMAX);
+                cs_round_stretch(t, g, bar, tm, ws, wk[g], win, blk, p, L, nt, per_ch, tab, h.s_bnd);
+                p += L;
+            } else if (active && t == 0) {
+                h.s_bnd[g] = 0u;
             }
-            __threadfence_block();
-        }
-        team_sync(bar);
-        // the team's decision is thread 0's alone (another team may set the failure flag at
-        // any time): a failed walk stops this channel, which still takes part in the
-        // buffer releases below so that no other team waits for it
-        if (t == 0) {
-            ws.pos = 0;
-            if (db.fail) ws.stop = 1u;
-        }
-        team_sync(bar);
-        cs_walk_block(t, g, bar, tm, ws, wk[g], P[p], blk, N, nt, per_ch, tab, h.s_corr,
-                      [&] { cs_db_help(db, b + 1, nb, U, base, N, P); });
-        team_sync(bar);
-        if (t == 0) {
-            // the last team to leave block b frees its buffer for block b + 2
-            if (atomicAdd(&db.readers[p], 1u) == n - 1 && b + 2 < nb) {
-                db.next[p] = 0;
-                db.done[p] = 0;
-                db.readers[p] = 0;
-                __threadfence_block();
-                db.tag[p] = b + 2;
+            // the last phase of the round if no channel stands inside block j any more
+            const bool last = __syncthreads_and(!(want && p < N));
+            if (warp < 2) {
+                cs_round_loops(warp, threadIdx.x & 31u, n, wk, s_ws, h, mt, N);
+            } else if (last && j + 2 < nb) {
+                const int8_t *nblk = blk + 4 * (size_t)N;
+                const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
+                cs_prefix_share(nblk, N, a16, a4, P[j & 1u], warp - 2, nw - 2);
+                if (warp == 2 && (threadIdx.x & 31u) == 0 && j + 3 < nb) prefetch_l2(nblk + 2 * (size_t)N, 2 * N);
+            }
+            __syncthreads();                              // new words, state and prefix sums in place
+            if (last) {
+                built = true;
+                break;
             }
         }
+        if (!built && j + 2 < nb) {
+            // a round without a last phase (every channel stopped or past block j from the
+            // start): block j + 2's prefix sums by every warp
+            const int8_t *nblk = blk + 4 * (size_t)N;
+            const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
+            cs_prefix_share(nblk, N, a16, a4, P[j & 1u], warp, nw);
+            __syncthreads();
+        }
+        p = p > N ? p - N : 0u;
     }
-    cs_walk_store(t, tm, ws, wk[g], per_ch);
+    if (active) cs_walk_store(t, tm, ws, wk[g], per_ch);
 }
 
 template <bool T3>

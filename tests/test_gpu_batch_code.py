@@ -235,3 +235,36 @@ def test_double_buffered_walk_matches_oracle():
         _check_run(b, recv, sigs, chans, 11, 13)
     finally:
         rx.rx_batch_destroy(b)
+
+
+def test_double_buffered_walk_with_blocks_shorter_than_an_epoch():
+    """Blocks of a third of a code period (2728 samples at 8.184 MHz), six channels per
+    CTA: an epoch spans three or four blocks, so the double-buffered walk takes it as
+    stretches of at most two blocks' prefix sums, some ending exactly at a block's end;
+    runs of 1, 2 and 27 blocks continue one another, bit-exact with the oracle."""
+    n_blocks = 30
+    recv = [synth.serving_stream(k, n_blocks=n_blocks) for k in range(2)]
+    for r in recv:
+        r.block_samples = 2728
+    offs, total = batch_layout(recv)
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for r, o in zip(recv, offs):
+        iq = synth.generate_iq(r).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    dev = torch.from_numpy(buf).cuda()
+    b = _batch(recv, n_blocks, (6, 128, 0, rx.RX_SCHED_SEGMENT))
+    try:
+        rx.rx_batch_run_code(b, dev, offs, n_blocks, rx.RX_RUN_RESTART)
+        chans = [_oracle_channels(r) for r in recv]
+        _check_run(b, recv, sigs, chans, 0, n_blocks)
+        chans = [_oracle_channels(r) for r in recv]
+        first = 0
+        for k, nb in enumerate((1, 2, 27)):
+            o = np.array([int(x) + 2 * first * r.block_samples for x, r in zip(offs, recv)], np.uint64)
+            rx.rx_batch_run_code(b, dev, o, nb, rx.RX_RUN_RESTART if k == 0 else 0)
+            _check_run(b, recv, sigs, chans, first, nb)
+            first += nb
+    finally:
+        rx.rx_batch_destroy(b)
