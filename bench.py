@@ -49,8 +49,8 @@ N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 # of the kernel's source files at the capture; when the sources differ from it the
 # figures describe another kernel, and the line reports them as null.
 PROFILED = {
-    ("segment", 128, 3): {"bytes_per_rx_block": 34944, "thread_inst_per_sample_channel": 11.4,
-                          "src_sha256": "8ead9d31167ee8cf3f4fe5e8fb7bf1e3d643c8133cdcdd55a4ddeccafcd69e66"},
+    ("segment", 128, 3): {"bytes_per_rx_block": 34933, "thread_inst_per_sample_channel": 11.16,
+                          "src_sha256": "6f3a8ab3bd95079ce5ce47835d43d7221d5d301b221778e817de7d14bb6e79d2"},
     ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
                             "src_sha256": "capture predates source hashing"},
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
@@ -59,7 +59,11 @@ PROFILED = {
 # The same, for the other batched workloads' legs, keyed by (workload, schedule, threads,
 # channels per item): executed thread instructions per sample*channel from a capture of
 # that workload's kernel at those tiles (16 receivers x 50 blocks of the multicorrelator).
-PROFILED_CONFIG = {}
+PROFILED_CONFIG = {
+    ("multicorrelator", "segment", 128, 2): {
+        "thread_inst_per_sample_channel": 69.55,
+        "src_sha256": "6f3a8ab3bd95079ce5ce47835d43d7221d5d301b221778e817de7d14bb6e79d2"},
+}
 KERNEL_SOURCES = {
     "pipelined": ["rx_pipe.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
     "static": ["rx_batch.cu", "rx_item.cuh", "rx_device.cuh"],
