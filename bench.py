@@ -383,7 +383,8 @@ def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_
     """The serving workload: n_streams streams at 8.184 MHz, 12 channels x 5 taps, 1 ms blocks
     arriving as Poisson processes (mean 1 kHz, rate jitter 10%), streams leaving and rejoining
     at random, served by continuous batching.  Streams replay `distinct` seeded recordings of
-    rec_blocks blocks in turn.  Latency counts from each block's scheduled arrival.  Then the
+    rec_blocks blocks in turn.  Latency counts from each block's scheduled arrival, in a run
+    that follows a quarter-second warm-up run of the same streams.  Then the
     real-time capacity of the served form and of the plain per-receiver form (one
     rx_correlate + rx_track_epoch per arriving block, from the same number of producer
     threads) under the same arrivals, each bracketed by doubling the stream count until a
@@ -425,6 +426,7 @@ def serving_leg(rx, synth, dev, n_streams=512, duration_s=2.0, distinct=32, rec_
         st["offered_blocks"] = n * 1000.0 * probe_s
         return st
 
+    run(n_streams, 0.25, churn=20.0)          # warm-up: first launches, ring and thread set-up
     base = run(n_streams, duration_s, churn=20.0)
     cap_ok, cap_bad, probes = _bracket(lambda n: run(n, probe_s, 0.0), 1024, capacity_limit)
     pcap_ok, pcap_bad, pprobes = _bracket(run_plain, 8, plain_limit)
