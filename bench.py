@@ -672,14 +672,14 @@ def batched_config_leg(rx, synth, name: str, receivers, n_blocks: int, dev, stre
 def table3_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, steps, warmup) -> dict:
     """The same batched workload with Table 3's full loop set (FLL-assisted 2nd-order PLL,
     2nd-order DLL) and the channel-health indicators closed on the device every epoch,
-    in the pipelined schedule with 2 channels per item and 224 correlating threads."""
+    with the tiles the autotuner picks for it (outside the timed region)."""
     import torch
     descs = [rx.receiver_desc(r, 1, 20, 10.0) for r in receivers]
     b = rx.rx_batch_create(descs, n_blocks, device=dev_index, stream=stream)
     try:
         for i, r in enumerate(receivers):
             rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
-        rx.rx_batch_set_tiles(b, 2, 224, 0, rx.RX_SCHED_PIPE)
+        got, probe_ms = rx.rx_batch_autotune(b, buf, offs, min(64, n_blocks))
         for _ in range(warmup):
             rx.rx_batch_run(b, buf, offs, n_blocks, rx.RX_RUN_RESTART)
         rx.rx_batch_sync(b)
@@ -698,7 +698,10 @@ def table3_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, ste
     return {"value": sc / (ms / 1000) / 1e6, "unit": "Msample*channel/s", "ms_per_step": ms,
             "steps": steps, "loops": "Table 3: 2nd-order PLL + 1st-order FLL (10 Hz), 2nd-order DLL; "
                                      "C/N0, lock ratio, lock-fail count every 20 ms",
-            "channels_locked_at_end": locked, "channels": len(health)}
+            "channels_locked_at_end": locked, "channels": len(health),
+            "tiles": {"channels_per_item": got[0], "threads": got[1], "ctas_per_sm": got[2],
+                      "schedule": SCHEDULES[got[3]]},
+            "autotune_best_probe_ms": probe_ms}
 
 
 def code_batch_leg(rx, synth, receivers, buf, offs, n_blocks, dev_index, stream, steps, warmup) -> dict:

@@ -601,7 +601,7 @@ __host__ __device__ inline size_t cs_layout(uint32_t teams, uint32_t mt, uint32_
     size_t s = 0;
     o[0] = s; s = cs_a16(s + cs_wp_words(max_n) * 4);                      // Wp
     o[1] = s; s = cs_a16(s + 8);                                            // never
-    o[2] = s; s = cs_a16(s + CS_MAX_TEAMS * 8 + CS_MAX_TEAMS * 4 + 4);      // s_corr, s_bnd, abort
+    o[2] = s; s = cs_a16(s + CS_MAX_TEAMS * 16 + CS_MAX_TEAMS * 4 + 4);     // s_corr, s_ef, s_bnd, abort
     o[3] = s; s += (size_t)teams * cs_team_bytes(mt);                       // teams
     return s;
 }
@@ -731,6 +731,7 @@ struct CsShared {
     uint32_t *Wp;
     uint64_t *never;
     double *s_corr;              // [CS_MAX_TEAMS] the DLL parts
+    double *s_ef;                // [CS_MAX_TEAMS] the FLL discriminators (Table 3's loop set)
     uint32_t *s_bnd;             // [CS_MAX_TEAMS] integration boundary flags
     volatile uint32_t *s_abort;
     unsigned char *teams;
@@ -744,7 +745,8 @@ __device__ __forceinline__ CsShared cs_shared(unsigned char *smem, uint32_t mt, 
     h.Wp = reinterpret_cast<uint32_t *>(smem + o[0]);
     h.never = reinterpret_cast<uint64_t *>(smem + o[1]);
     h.s_corr = reinterpret_cast<double *>(smem + o[2]);
-    h.s_bnd = reinterpret_cast<uint32_t *>(h.s_corr + CS_MAX_TEAMS);
+    h.s_ef = h.s_corr + CS_MAX_TEAMS;
+    h.s_bnd = reinterpret_cast<uint32_t *>(h.s_ef + CS_MAX_TEAMS);
     h.s_abort = h.s_bnd + CS_MAX_TEAMS;
     h.teams = smem + o[3];
     h.tbytes = cs_team_bytes(mt);
@@ -819,33 +821,46 @@ __device__ __forceinline__ void cs_team_fold(uint32_t t, const CsTeam &tm, const
     }
 }
 
-// The loops of every channel whose integration closed, on warps 0 and 1 (the other warps
-// do not call this): warp 0 lane j runs channel j's PLL part (or its whole loop set of
-// Table 3), warp 1 lanes 2j and 2j + 1 its early and late envelopes and the DLL part.
+// Warps that close the loops: 0 and 1 for the basic loops, 0 to 2 for Table 3's set.
+template <bool T3>
+__device__ __forceinline__ uint32_t cs_loop_warps(const GroupDesc &gd) {
+    return T3 && gd.loop_set == 1u ? 3u : 2u;
+}
+
+// Named barrier 15 over the loop warps.
+__device__ __forceinline__ void loop_sync(uint32_t nw) { asm volatile("bar.sync 15, %0;" ::"r"(32u * nw) : "memory"); }
+
+// The loops of every channel whose integration closed, on the loop warps (the other
+// warps do not call this).  Basic loops: warp 0 lane j runs channel j's PLL part and,
+// after the DLL part, the rest; warp 1 lanes 2j and 2j + 1 its early and late envelopes
+// and the DLL part.  Table 3's set: warp 0 lane j the PLL discriminator, then (with the
+// FLL discriminator) the loop filter and the rest; warp 1 as for the basic loops with
+// the 2nd-order DLL; warp 2 lane j the FLL discriminator and then the health window.
+// Each channel's extra state is split between them: warp 1 owns the DLL integrator,
+// warp 2 the rest.
 template <bool T3>
 __device__ __forceinline__ void cs_loops(uint32_t warp, uint32_t lane, const GroupDesc &gd, const CsShared &h,
                                          uint32_t mt) {
     const uint32_t nch = gd.nch;
-    const bool split = !T3 || gd.loop_set != 1u;   // the basic loops run as PLL and DLL parts
-    const LoopConsts lc = gd.lc;
+    const bool full = T3 && gd.loop_set == 1u;
+    const uint32_t lw = full ? 3u : 2u;
+    const LoopConsts lc = full ? LoopConsts{0.0, 0.0, 0.0, gd.lc3.sfs} : gd.lc;
     if (warp == 0) {
         const uint32_t j = lane;
         const bool doit = j < nch && h.s_bnd[j];
-        PllOut po{0.0, 0.0};
-        LoopOut o3{};
         const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
         FinishPre fp{};
-        if (doit) {
-            if (split) {
-                po = loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc);
-                fp = loop_finish_pre(po, lc);         // the part that does not wait for the DLL
-            } else {
-                o3 = close_loops<T3>(gd, j, tj.d[0], tj.acc, tj.taps, lc);
-            }
+        if (full) {
+            double e_p = 0.0;
+            if (doit) e_p = loop_pll_disc(tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1]);
+            loop_sync(lw);                            // the FLL discriminators are in s_ef
+            if (doit) fp = loop_finish_pre(loop_filter3(tj.d[0], e_p, h.s_ef[j], gd.lc3), lc);
+        } else if (doit) {
+            fp = loop_finish_pre(loop_pll(tj.d[0], tj.acc[2 * gd.tap_p], tj.acc[2 * gd.tap_p + 1], lc), lc);
         }
-        pair_sync();                                  // the DLL parts are in s_corr
+        loop_sync(lw);                                // the DLL parts are in s_corr
         if (doit) {
-            const LoopOut lo = split ? loop_finish_post(fp, h.s_corr[j], lc) : o3;
+            const LoopOut lo = loop_finish_post(fp, h.s_corr[j], lc);
             tj.d[0] = lo.v;
             tj.d[1] = lo.f_carr;
             tj.d[2] = lo.f_code;
@@ -856,7 +871,7 @@ __device__ __forceinline__ void cs_loops(uint32_t warp, uint32_t lane, const Gro
         }
     } else if (warp == 1) {
         const uint32_t j = lane >> 1;
-        const bool doit = split && j < nch && h.s_bnd[j];
+        const bool doit = j < nch && h.s_bnd[j];
         double m = 0.0;
         const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
         if (doit) {
@@ -864,8 +879,56 @@ __device__ __forceinline__ void cs_loops(uint32_t warp, uint32_t lane, const Gro
             m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
         }
         const double ml = __shfl_down_sync(0xffffffffu, m, 1);
-        if (doit && (lane & 1u) == 0u) h.s_corr[j] = loop_dll(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], lc);
-        pair_sync();
+        if (doit && (lane & 1u) == 0u) {
+            if (full) {
+                double *pu = &gd.ext[j].dll_u;
+                double u = __ldcg(pu);
+                h.s_corr[j] = loop_dll3(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], u, gd.lc3);
+                __stcg(pu, u);
+            } else {
+                h.s_corr[j] = loop_dll(m, ml, tj.taps[gd.tap_e], tj.taps[gd.tap_l], lc);
+            }
+        }
+        if (full) loop_sync(lw);
+        loop_sync(lw);
+    } else if (full) {
+        // warp 2: the FLL discriminator, then the health window
+        const uint32_t j = lane;
+        const bool doit = j < nch && h.s_bnd[j];
+        const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        LoopExt *p = gd.ext + (doit ? j : 0);
+        LoopExt ex{};
+        int32_t ipr = 0, qpr = 0;
+        if (doit) {
+            ex.prev_ip = __ldcg(&p->prev_ip);
+            ex.prev_qp = __ldcg(&p->prev_qp);
+            ex.have_prev = __ldcg(&p->have_prev);
+            ex.window_count = __ldcg(&p->window_count);
+            ex.sum_abs = __ldcg(&p->sum_abs);
+            ex.sum_pow = __ldcg(&p->sum_pow);
+            ex.sum_diff = __ldcg(&p->sum_diff);
+            ex.cn0 = __ldcg(&p->cn0);
+            ex.lock = __ldcg(&p->lock);
+            ex.lock_fail = __ldcg(&p->lock_fail);
+            ipr = tj.acc[2 * gd.tap_p];
+            qpr = tj.acc[2 * gd.tap_p + 1];
+            h.s_ef[j] = loop_fll3(ex, ipr, qpr, gd.lc3);
+        }
+        loop_sync(lw);
+        if (doit) {
+            loop_health3(ex, ipr, qpr, gd.lc3, gd.window);
+            __stcg(&p->prev_ip, ex.prev_ip);
+            __stcg(&p->prev_qp, ex.prev_qp);
+            __stcg(&p->have_prev, ex.have_prev);
+            __stcg(&p->window_count, ex.window_count);
+            __stcg(&p->sum_abs, ex.sum_abs);
+            __stcg(&p->sum_pow, ex.sum_pow);
+            __stcg(&p->sum_diff, ex.sum_diff);
+            __stcg(&p->cn0, ex.cn0);
+            __stcg(&p->lock, ex.lock);
+            __stcg(&p->lock_fail, ex.lock_fail);
+        }
+        loop_sync(lw);
     }
 }
 
@@ -898,7 +961,7 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
     uint32_t *tab = g_item_tab;
 
     const GroupDesc gd = a.groups[blockIdx.x];
-    const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2;
+    const uint32_t nch = gd.nch, nt = gd.ntaps, N = gd.N, per_ch = nt * 2, lw = cs_loop_warps<T3>(gd);
     const uint32_t g = threadIdx.x / CS_GT, t = threadIdx.x - g * CS_GT;
     const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t bar = 2 + g;
@@ -933,13 +996,13 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_batch_cseg(CsArgs a
             cs_team_fold(t, tm, gd, g, h.s_bnd);
         }
         __syncthreads();                                  // every channel's sums and flags are in place
-        if (warp < 2) {
+        if (warp < lw) {
             cs_loops<T3>(warp, threadIdx.x & 31, gd, h, mt);
         } else if (b + 1 < a.n_blocks) {
             // the next block's prefix sums, by every other warp
             const int8_t *nblk = blk + blk_bytes;
             const bool a16 = ((uintptr_t)nblk & 15) == 0, a4 = ((uintptr_t)nblk & 3) == 0;
-            cs_prefix_share(nblk, N, a16, a4, Wp, warp - 2, nw - 2);
+            cs_prefix_share(nblk, N, a16, a4, Wp, warp - lw, nw - lw);
         }
         __syncthreads();                                  // new words and the next prefix sums in place
     }
@@ -989,7 +1052,7 @@ __global__ void __launch_bounds__(CS_GT * CS_MAX_TEAMS, 1) k_serve_cs(CsServeArg
             cs_team_fold(t, tm, gd, g, h.s_bnd);
         }
         __syncthreads();
-        if (warp < 2) cs_loops<T3>(warp, threadIdx.x & 31, gd, h, mt);
+        if (warp < cs_loop_warps<T3>(gd)) cs_loops<T3>(warp, threadIdx.x & 31, gd, h, mt);
         __syncthreads();
         if (active) cs_team_store(t, tm, gd, g);
         __syncthreads();

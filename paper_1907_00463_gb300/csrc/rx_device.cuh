@@ -683,20 +683,23 @@ __host__ inline Health health_record(const LoopExt &x) {
 // Health over `window` integrations: C/N0 = Pd / Pn / T (signal-to-noise variance:
 // Pd = mean(|I_P|)^2, Pn = mean(I_P^2 + Q_P^2) - Pd), lock = sum(I_P^2 - Q_P^2) /
 // sum(I_P^2 + Q_P^2), lock_fail += (lock < 0.85).  Same operations, same order,
-// as the CPU definition.
-__device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t ie, int32_t qe, int32_t ipr,
-                                                int32_t qpr, int32_t il, int32_t ql, int64_t off_e,
-                                                int64_t off_l, const LoopConsts3 &lc, uint32_t window) {
-    LoopOut o;
-    const double ip = (double)ipr, qp = (double)qpr;
-    double e_p;
-    if (ipr != 0) {
-        e_p = atan_cycles_int(qpr, ipr);
-    } else {
-        e_p = qpr > 0 ? 0.25 : (qpr < 0 ? -0.25 : 0.0);
-    }
+// as the CPU definition.  It is written in parts that share no operation, so that
+// they can run on different threads (the PLL discriminator, the FLL discriminator,
+// the loop filter that joins them, the DLL, and the health window); each part is the
+// same sequence of correctly rounded operations wherever it runs.
+
+// PLL discriminator e_p in cycles (+-1/4 when I_P = 0 and Q_P != 0, 0 when both are 0).
+__device__ __forceinline__ double loop_pll_disc(int32_t ipr, int32_t qpr) {
+    if (ipr != 0) return atan_cycles_int(qpr, ipr);
+    return qpr > 0 ? 0.25 : (qpr < 0 ? -0.25 : 0.0);
+}
+
+// FLL discriminator e_f in Hz (0 without a previous prompt); this prompt becomes the
+// previous one.
+__device__ __forceinline__ double loop_fll3(LoopExt &ex, int32_t ipr, int32_t qpr, const LoopConsts3 &lc) {
     double e_f = 0.0;
     if (ex.have_prev) {
+        const double ip = (double)ipr, qp = (double)qpr;
         const double i1 = (double)ex.prev_ip, q1 = (double)ex.prev_qp;
         double cross = __dsub_rn(__dmul_rn(i1, qp), __dmul_rn(ip, q1));
         double dot = __dadd_rn(__dmul_rn(i1, ip), __dmul_rn(q1, qp));
@@ -706,35 +709,37 @@ __device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t i
         }
         e_f = __dmul_rn(atan2_cycles(cross, dot), lc.inv_T);
     }
+    ex.prev_ip = ipr;
+    ex.prev_qp = qpr;
+    ex.have_prev = 1;
+    return e_f;
+}
+
+// The FLL-assisted 2nd-order PLL filter: the integrator v and f_carr.
+__device__ __forceinline__ PllOut loop_filter3(double v, double e_p, double e_f, const LoopConsts3 &lc) {
     v = __dadd_rn(v, __dmul_rn(lc.k1, e_p));
     v = __dadd_rn(v, __dmul_rn(lc.kf, e_f));
-    const double f_carr = __dadd_rn(v, __dmul_rn(lc.k2, e_p));
+    return PllOut{v, __dadd_rn(v, __dmul_rn(lc.k2, e_p))};
+}
 
-    const double dIe = (double)ie, dQe = (double)qe, dIl = (double)il, dQl = (double)ql;
-    const double mag_e = __dsqrt_rn(__dadd_rn(__dmul_rn(dIe, dIe), __dmul_rn(dQe, dQe)));
-    const double mag_l = __dsqrt_rn(__dadd_rn(__dmul_rn(dIl, dIl), __dmul_rn(dQl, dQl)));
+// 2nd-order DLL from the two envelopes: the rate integrator u += kd1 e_c (in dll_u) and
+// the code-rate correction u + kd2 e_c.
+__device__ __forceinline__ double loop_dll3(double mag_e, double mag_l, int64_t off_e, int64_t off_l, double &dll_u,
+                                            const LoopConsts3 &lc) {
     const double den = __dadd_rn(mag_e, mag_l);
     const double d_el = __dmul_rn((double)(off_e - off_l), RXD_TWO_M32);
     const double kd = __dsub_rn(1.0, __dmul_rn(d_el, 0.5));
     double e_c = 0.0;
     if (den > 0.0) e_c = __ddiv_rn(__dmul_rn(kd, __dsub_rn(mag_e, mag_l)), den);
-    const double u = __dadd_rn(ex.dll_u, __dmul_rn(lc.kd1, e_c));
-    ex.dll_u = u;
-    double f_code = __dadd_rn(1.023e6, __dmul_rn(f_carr, RXD_KAID));
-    f_code = __dadd_rn(f_code, __dadd_rn(u, __dmul_rn(lc.kd2, e_c)));
+    const double u = __dadd_rn(dll_u, __dmul_rn(lc.kd1, e_c));
+    dll_u = u;
+    return __dadd_rn(u, __dmul_rn(lc.kd2, e_c));
+}
 
-    double xw = __dmul_rn(f_carr, lc.sfs);
-    double xr = __dmul_rn(f_code, lc.sfs);
-    if (xw > 9.0e18) xw = 9.0e18;
-    if (xw < -9.0e18) xw = -9.0e18;
-    if (!(xr > 0.0)) xr = 0.0;
-    if (xr > 4294967295.0) xr = 4294967295.0;
-    o.w = (int32_t)(uint32_t)(uint64_t)__double2ll_rn(xw);
-    o.r = (uint64_t)__double2ll_rn(xr);
-    o.v = v;
-    o.f_carr = f_carr;
-    o.f_code = f_code;
-
+// The health window's sums, and at its end C/N0, the lock ratio and the lock-fail count.
+__device__ __forceinline__ void loop_health3(LoopExt &ex, int32_t ipr, int32_t qpr, const LoopConsts3 &lc,
+                                             uint32_t window) {
+    const double ip = (double)ipr, qp = (double)qpr;
     const double ip2 = __dmul_rn(ip, ip), qp2 = __dmul_rn(qp, qp);
     ex.sum_abs = __dadd_rn(ex.sum_abs, fabs(ip));
     ex.sum_pow = __dadd_rn(ex.sum_pow, __dadd_rn(ip2, qp2));
@@ -757,9 +762,18 @@ __device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t i
         ex.sum_diff = 0.0;
         ex.window_count = 0;
     }
-    ex.prev_ip = ipr;
-    ex.prev_qp = qpr;
-    ex.have_prev = 1;
+}
+
+__device__ __forceinline__ LoopOut loop_update3(double v, LoopExt &ex, int32_t ie, int32_t qe, int32_t ipr,
+                                                int32_t qpr, int32_t il, int32_t ql, int64_t off_e,
+                                                int64_t off_l, const LoopConsts3 &lc, uint32_t window) {
+    const double e_p = loop_pll_disc(ipr, qpr);
+    const double e_f = loop_fll3(ex, ipr, qpr, lc);
+    const PllOut p = loop_filter3(v, e_p, e_f, lc);
+    const double corr = loop_dll3(loop_envelope(ie, qe), loop_envelope(il, ql), off_e, off_l, ex.dll_u, lc);
+    const LoopConsts fc{0.0, 0.0, 0.0, lc.sfs};
+    const LoopOut o = loop_finish(p, corr, fc);
+    loop_health3(ex, ipr, qpr, lc, window);
     return o;
 }
 
