@@ -1085,6 +1085,9 @@ struct CsWalkState {
     rx_code_state cs;
     double k1[3];                // w0^2 (n / fs) for epochs of n = N - 1, N, N + 1 samples (the
                                  // same two operations as for any other n, done once)
+    CodeLoop cl;                 // the walk descriptor's loop constants and taps, kept here so
+    int32_t tap_e, tap_p, tap_l; // that a loop update reads them from shared memory
+    uint32_t sync_k, cap;
 };
 
 // Samples to the end of the code period from code phase phi (< 1023 2^32): ceil((1023
@@ -1141,6 +1144,12 @@ __device__ __forceinline__ void cs_walk_load(uint32_t t, const CsTeam &tm, CsWal
         ws.rem = cs_epoch_rest(tm.phi[0], (uint32_t)r);
         for (uint32_t i = 0; i < 3; ++i)
             ws.k1[i] = __dmul_rn(cw.cl.w0sq, __ddiv_rn((double)(N - 1 + i), cw.cl.fs));
+        ws.cl = cw.cl;
+        ws.tap_e = cw.tap_e;
+        ws.tap_p = cw.tap_p;
+        ws.tap_l = cw.tap_l;
+        ws.sync_k = cw.sync_k;
+        ws.cap = cw.cap;
     }
 }
 
@@ -1373,33 +1382,31 @@ __device__ __forceinline__ void cs_round_loops(uint32_t warp, uint32_t lane, uin
         const uint32_t j = lane;
         const bool doit = j < n && h.s_bnd[j];
         const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        CsWalkState &w = s_ws[doit ? j : 0];
         LoopConsts lc{};
         PllOut po{0.0, 0.0};
         FinishPre fp{};
         if (doit) {
-            const CodeWalk &cw = wk[j];
-            const CsWalkState &w = s_ws[j];
             const uint32_t ne = w.cs.samples_in_epoch, ki = ne + 1u - N;
-            lc.k1 = ki < 3u ? w.k1[ki] : __dmul_rn(cw.cl.w0sq, __ddiv_rn((double)ne, cw.cl.fs));
-            lc.k2 = cw.cl.k2;
-            lc.kdll = cw.cl.kdll;
-            lc.sfs = cw.cl.sfs;
-            po = loop_pll(tj.d[0], tj.acc[2 * cw.tap_p], tj.acc[2 * cw.tap_p + 1], lc);
+            lc.k1 = ki < 3u ? w.k1[ki] : __dmul_rn(w.cl.w0sq, __ddiv_rn((double)ne, w.cl.fs));
+            lc.k2 = w.cl.k2;
+            lc.kdll = w.cl.kdll;
+            lc.sfs = w.cl.sfs;
+            po = loop_pll(tj.d[0], tj.acc[2 * w.tap_p], tj.acc[2 * w.tap_p + 1], lc);
             fp = loop_finish_pre(po, lc);
         }
         pair_sync();                                  // the DLL parts are in s_corr
         if (doit) {
             const CodeWalk &cw = wk[j];
-            CsWalkState &w = s_ws[j];
             const LoopOut lo = loop_finish_post(fp, h.s_corr[j], lc);
             const uint32_t slot = w.closed;
-            if (slot < cw.cap) cw.lens[slot] = w.cs.samples_in_epoch;
+            if (slot < w.cap) cw.lens[slot] = w.cs.samples_in_epoch;
             else atomicOr(cw.err, 1u);
             tj.d[0] = lo.v;
             tj.d[1] = lo.f_carr;
             tj.d[2] = lo.f_code;
             w.epochs += 1;
-            bitsync_step(w.cs, tj.acc[2 * cw.tap_p], cw.sync_k);
+            bitsync_step(w.cs, tj.acc[2 * w.tap_p], w.sync_k);
             w.cs.samples_in_epoch = 0;
             w.closed = slot + 1;
             tj.u[1] = (uint32_t)lo.w;
@@ -1414,17 +1421,16 @@ __device__ __forceinline__ void cs_round_loops(uint32_t warp, uint32_t lane, uin
         const uint32_t j = lane >> 1;
         const bool doit = j < n && h.s_bnd[j];
         const CsTeam tj = cs_team(h.teams + (size_t)(doit ? j : 0) * h.tbytes, mt);
+        const CsWalkState &w = s_ws[doit ? j : 0];
         double m = 0.0;
         if (doit) {
-            const CodeWalk &cw = wk[j];
-            const uint32_t k = (lane & 1u) ? (uint32_t)cw.tap_l : (uint32_t)cw.tap_e;
+            const uint32_t k = (lane & 1u) ? (uint32_t)w.tap_l : (uint32_t)w.tap_e;
             m = loop_envelope(tj.acc[2 * k], tj.acc[2 * k + 1]);
         }
         const double ml = __shfl_down_sync(0xffffffffu, m, 1);
         if (doit && (lane & 1u) == 0u) {
-            const CodeWalk &cw = wk[j];
-            const LoopConsts lc{0.0, 0.0, cw.cl.kdll, 0.0};
-            h.s_corr[j] = loop_dll(m, ml, tj.taps[cw.tap_e], tj.taps[cw.tap_l], lc);
+            const LoopConsts lc{0.0, 0.0, w.cl.kdll, 0.0};
+            h.s_corr[j] = loop_dll(m, ml, tj.taps[w.tap_e], tj.taps[w.tap_l], lc);
         }
         pair_sync();
     }
