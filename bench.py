@@ -49,8 +49,8 @@ N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 # of the kernel's source files at the capture; when the sources differ from it the
 # figures describe another kernel, and the line reports them as null.
 PROFILED = {
-    ("segment", 128, 3): {"bytes_per_rx_block": 34933, "thread_inst_per_sample_channel": 11.16,
-                          "src_sha256": "6f3a8ab3bd95079ce5ce47835d43d7221d5d301b221778e817de7d14bb6e79d2"},
+    ("segment", 128, 3): {"bytes_per_rx_block": 34887, "thread_inst_per_sample_channel": 11.16,
+                          "src_sha256": "c012de77d90356cdfafc9821437f232ed3b8175034c514b5a08d0bc2a3d09979"},
     ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
                             "src_sha256": "capture predates source hashing"},
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
@@ -62,7 +62,7 @@ PROFILED = {
 PROFILED_CONFIG = {
     ("multicorrelator", "segment", 128, 2): {
         "thread_inst_per_sample_channel": 69.55,
-        "src_sha256": "6f3a8ab3bd95079ce5ce47835d43d7221d5d301b221778e817de7d14bb6e79d2"},
+        "src_sha256": "c012de77d90356cdfafc9821437f232ed3b8175034c514b5a08d0bc2a3d09979"},
 }
 KERNEL_SOURCES = {
     "pipelined": ["rx_pipe.cu", "rx_item.cuh", "rx_device.cuh", "rx_sync.cuh"],
