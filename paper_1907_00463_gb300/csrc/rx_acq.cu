@@ -250,11 +250,10 @@ __global__ void __launch_bounds__(Shape<LOGM>::NT, 1)
                     c[e] = make_uint4(x[4 * e], x[4 * e + 1], x[4 * e + 2], x[4 * e + 3]);
             }
             __syncthreads();
-            constexpr int ns = LOGM - RL;
-            constexpr int npairs = (ns & 1) ? (ns - 1) / 2 : ns / 2 - 1;
+            constexpr int npass = rxn::dit_middle_count(LOGM, RL);
 #pragma unroll 1
-            for (int pp = 0, lgH = RL; pp < npairs; ++pp, lgH += 2) {
-                rxn::dit_pass4(s, lgH, tid, NT, M, Ti);
+            for (int pp = 0; pp < npass; ++pp) {
+                rxn::dit_middle_pass(pp, s, LOGM, RL, tid, NT, Ti);
                 __syncthreads();
             }
             LH::run(s, tid, Ti, [&](uint32_t slot, uint32_t c, int32_t zi) {

@@ -104,6 +104,22 @@ RXN_HD void bf_dit(uint32_t &x, uint32_t &y, uint2 w) {
     y = u - t + k2P;
 }
 
+// The same butterflies with the twiddle 1 (j = 0 of every stage): the product is y
+// itself, brought into [0, 2p) by one conditional subtraction instead of a reduced
+// multiply.  The representative may differ from the multiply's by p; every value
+// stays in its range and the transform's outputs are the same residues.
+RXN_HD void bf_dif1(uint32_t &x, uint32_t &y) {
+    uint32_t s = csub(x + y, k2P);
+    y = csub(x - y + k2P, k2P);
+    x = s;
+}
+RXN_HD void bf_dit1(uint32_t &x, uint32_t &y) {
+    uint32_t u = csub(x, k2P);
+    uint32_t t = csub(y, k2P);
+    x = u + t;
+    y = u - t + k2P;
+}
+
 // ---------------------------------------------------------------------------
 // Forward transform (decimation in frequency)
 // ---------------------------------------------------------------------------
@@ -152,8 +168,9 @@ struct DifReg {
         constexpr int L = 1 << LG;
 #pragma unroll
         for (int st = 0; st < R; st += 2 * L) {
+            bf_dif1(x[st], x[st + L]);
 #pragma unroll
-            for (int j = 0; j < L; ++j) bf_dif(x[st + j], x[st + j + L], tw[L + j]);
+            for (int j = 1; j < L; ++j) bf_dif(x[st + j], x[st + j + L], tw[L + j]);
         }
         if constexpr (LG > 0) DifReg<LG - 1, R>::run(x, tw);
     }
@@ -174,8 +191,9 @@ struct DitReg {
         constexpr int L = 1 << LG;
 #pragma unroll
         for (int st = 0; st < R; st += 2 * L) {
+            bf_dit1(x[st], x[st + L]);
 #pragma unroll
-            for (int j = 0; j < L; ++j) bf_dit(x[st + j], x[st + j + L], twi[L + j]);
+            for (int j = 1; j < L; ++j) bf_dit(x[st + j], x[st + j + L], twi[L + j]);
         }
         if constexpr ((2 << LG) < R) DitReg<LG + 1, R>::run(x, twi);
     }
@@ -201,6 +219,56 @@ RXN_HD void dit_pass4(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t 
         s[pad(i + L)] = x2;
         s[pad(i + L + H)] = x3;
     }
+}
+
+// Four stages fused: half-lengths H, 2H, 4H, 8H (H = 2^lgH >= 32).  Group g owns the 16
+// elements i + k H (k < 16) of one block of 16 H, i = its block's start + j, j < H; the
+// stage of half-length 2^s H pairs k with k + 2^s and takes the twiddle Ti[2^s H + j +
+// (k mod 2^s) H].  In the padded layout element i + k H sits at pad(i) + k (H + H / 8),
+// and consecutive groups read consecutive words.
+RXN_HD void dit_pass16(uint32_t *s, int lgH, uint32_t tid, uint32_t nt, uint32_t M,
+                       const uint2 *Ti) {
+    const uint32_t H = 1u << lgH, step = H + (H >> 3);
+    for (uint32_t g = tid; g < M / 16; g += nt) {
+        const uint32_t j = g & (H - 1);
+        const uint32_t i = ((g >> lgH) << (lgH + 4)) + j;
+        uint32_t *b = s + pad(i);
+        uint32_t x[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = b[k * step];
+#pragma unroll
+        for (int sg = 0; sg < 4; ++sg) {
+            const int h = 1 << sg;
+#pragma unroll
+            for (int r = 0; r < h; ++r) {
+                const uint2 w = Ti[(uint32_t)h * H + j + (uint32_t)r * H];
+#pragma unroll
+                for (int k0 = 0; k0 < 16; k0 += 2 * h) bf_dit(x[k0 + r], x[k0 + r + h], w);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) b[k * step] = x[k];
+    }
+}
+
+// The inverse's shared-memory passes between the RL register stages and the last pass
+// (LastHalf): the stages of half-length 2^RL up to M / 8 (even shared-memory stage
+// count) or M / 4 (odd), as radix-16 passes while four or more stages remain, then
+// radix-4 passes.  Pass p of dit_middle_count(); the caller separates passes with a
+// block barrier.
+RXN_HD constexpr int dit_middle_stages(int logM, int RL) {
+    const int ns = logM - RL;
+    return (ns & 1) ? ns - 1 : ns - 2;
+}
+RXN_HD constexpr int dit_middle_count(int logM, int RL) {
+    const int n = dit_middle_stages(logM, RL);
+    return n / 4 + (n % 4) / 2;
+}
+RXN_HD void dit_middle_pass(int p, uint32_t *s, int logM, int RL, uint32_t tid, uint32_t nt, const uint2 *Ti) {
+    const uint32_t M = 1u << logM;
+    const int n16 = dit_middle_stages(logM, RL) / 4;
+    if (p < n16) dit_pass16(s, RL + 4 * p, tid, nt, M, Ti);
+    else dit_pass4(s, RL + 4 * n16 + 2 * (p - n16), tid, nt, M, Ti);
 }
 
 // One radix-2 stage of half-length L = 2^lgL.
