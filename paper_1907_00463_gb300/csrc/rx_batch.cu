@@ -1112,12 +1112,31 @@ static rx_status run_host_chunks(rx_batch b, const int8_t *iq, const uint64_t *o
     RX_CUDA_TRY(cudaEventRecord(b->ev_start, b->stream), E);
     RX_CUDA_TRY(cudaStreamWaitEvent(b->copy_stream, b->ev_start, 0), E);
     b->last_launches = 0;
+    int max_pitch = 0;
+    RX_CUDA_TRY(cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, b->device), E);
     for (uint32_t c = 0; c < C; ++c) {
         const uint32_t b0 = c * cb, nb = std::min(cb, n_blocks - b0);
-        for (uint32_t r = 0; r < R; ++r) {
-            const size_t blk = 2 * (size_t)b->rx[r].block_samples, o = off[r] + (size_t)b0 * blk;
-            RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + o, iq + o, (size_t)nb * blk, cudaMemcpyHostToDevice,
-                                        b->copy_stream), E);
+        // a run of receivers with one block size, equally spaced in the buffer, is one
+        // strided copy (rows of the chunk's span, one per receiver): the copy engine then
+        // streams at its full rate instead of paying a per-copy cost for every receiver
+        for (uint32_t r = 0; r < R;) {
+            const uint32_t Nr = b->rx[r].block_samples;
+            const size_t blk = 2 * (size_t)Nr, width = (size_t)nb * blk, o = off[r] + (size_t)b0 * blk;
+            uint32_t e = r + 1;
+            const uint64_t pitch = e < R && off[e] > off[r] ? off[e] - off[r] : 0;
+            const bool strided = pitch >= width && pitch <= (uint64_t)max_pitch && b->rx[e].block_samples == Nr;
+            if (strided) {
+                while (e + 1 < R && b->rx[e + 1].block_samples == Nr && off[e + 1] > off[e] &&
+                       off[e + 1] - off[e] == pitch)
+                    ++e;
+                ++e;
+                RX_CUDA_TRY(cudaMemcpy2DAsync(b->d_stage + o, (size_t)pitch, iq + o, (size_t)pitch, width, e - r,
+                                              cudaMemcpyHostToDevice, b->copy_stream), E);
+            } else {
+                RX_CUDA_TRY(cudaMemcpyAsync(b->d_stage + o, iq + o, width, cudaMemcpyHostToDevice, b->copy_stream),
+                            E);
+            }
+            r = e;
         }
         RX_CUDA_TRY(cudaEventRecord(b->chunk_ev[c], b->copy_stream), E);
         RX_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->chunk_ev[c], 0), E);

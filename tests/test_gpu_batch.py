@@ -227,6 +227,41 @@ def test_host_input_in_chunks(schedule):
         assert np.array_equal(d, x)
 
 
+def test_host_input_copies_for_mixed_layouts():
+    """Host input copied in chunks where some receivers form runs of one block size and
+    one spacing in the buffer (each run's chunk is one strided copy) and others break a
+    run (another block size; a gap in the buffer before the last one): dumps and state
+    equal those of one launch over device input, from pageable and from pinned memory,
+    and the oracle's."""
+    fss = [4.092e6, 4.092e6, 4.092e6, 2.046e6, 4.092e6, 4.092e6]
+    recv = [synth.uniform_receiver(i, n_blocks=12, fs=fs) for i, fs in enumerate(fss)]
+    offs, total = batch_layout(recv)
+    offs = offs.copy()
+    offs[-1] += 4096
+    total += 4096
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for r, o in zip(recv, offs):
+        iq = synth.generate_iq(r, 12 * r.block_samples).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    b = _batch(recv, 12, (2, 128, 0, rx.RX_SCHED_SEGMENT))
+    try:
+        rx.rx_batch_run(b, torch.from_numpy(buf).cuda(), offs, 12, rx.RX_RUN_RESTART)
+        whole = _read(b, recv, 12)
+        rx.rx_batch_set_host_chunk(b, 5)
+        rx.rx_batch_run(b, buf, offs, 12, rx.RX_RUN_RESTART)
+        assert rx.rx_batch_last_launches(b) == 3
+        pageable = _read(b, recv, 12)
+        rx.rx_batch_run(b, torch.from_numpy(buf).pin_memory(), offs, 12, rx.RX_RUN_RESTART)
+        pinned = _read(b, recv, 12)
+    finally:
+        rx.rx_batch_destroy(b)
+    _check_against_oracle(recv, sigs, whole, 12)
+    _same_runs(whole, pageable)
+    _same_runs(whole, pinned)
+
+
 def test_large_host_input_is_chunked_automatically():
     """At 64 MiB of host input or more the run is copied and tracked in sixteen chunks
     (here 2 receivers x 1100 blocks at 16.368 MHz, 72 MB, seeded int8 noise: chunks of
