@@ -51,6 +51,8 @@ N_RX, N_BLOCKS, FS = 64, 1000, 16.368e6
 PROFILED = {
     ("segment", 128, 3): {"bytes_per_rx_block": 34887, "thread_inst_per_sample_channel": 11.16,
                           "src_sha256": "c012de77d90356cdfafc9821437f232ed3b8175034c514b5a08d0bc2a3d09979"},
+    ("segment", 128, 6): {"bytes_per_rx_block": 34794, "thread_inst_per_sample_channel": 10.35,
+                          "src_sha256": "c012de77d90356cdfafc9821437f232ed3b8175034c514b5a08d0bc2a3d09979"},
     ("pipelined", 224, 2): {"bytes_per_rx_block": 33869, "thread_inst_per_sample_channel": 23.9,
                             "src_sha256": "capture predates source hashing"},
     ("static", 128, 1): {"bytes_per_rx_block": 33992, "thread_inst_per_sample_channel": 19.7,
