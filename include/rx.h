@@ -477,7 +477,8 @@ rx_status rx_batch_get_tiles(rx_batch b, uint32_t *channels_per_item,
  * tracking alone), keep the fastest, and return the receivers to their
  * starting state.  The choice is cached in the process per
  * workload shape (sample rates, block sizes, channel/tap counts, integration
- * lengths, device); a cached shape is applied without timing (*ms_out = -1).
+ * lengths, loop sets and health windows, device) and probe length; a cached
+ * shape is applied without timing (*ms_out = -1).
  * tiles_out (4 entries, optional) receives {channels_per_item, threads,
  * ctas_per_sm, schedule}; ms_out (optional) the best probe time. */
 rx_status rx_batch_autotune(rx_batch b, const int8_t *iq,

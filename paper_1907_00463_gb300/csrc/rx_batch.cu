@@ -1359,15 +1359,21 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, std::array<uint32_t, 4>> g_tune_cache;
 
-TuneKey tune_key(rx_batch b, int device) {
+// The cache key: everything that changes which shape is fastest, the loop set included
+// (Table 3's loops change the kernel and its balance; the balanced schedule refuses
+// them) and the probe length (a longer probe may rank close shapes differently).
+TuneKey tune_key(rx_batch b, int device, uint32_t probe_blocks) {
     TuneKey k;
     k.v.push_back(device);
+    k.v.push_back(probe_blocks);
     for (const rx_receiver_desc &d : b->rx) {
         k.v.push_back(d.fs_hz);
         k.v.push_back(d.block_samples);
         k.v.push_back(d.n_channels);
         k.v.push_back(d.n_taps);
         k.v.push_back(d.integ_blocks);
+        k.v.push_back(d.loop_set);
+        k.v.push_back(d.health_window);
     }
     return k;
 }
@@ -1380,7 +1386,7 @@ extern "C" rx_status rx_batch_autotune(rx_batch b, const int8_t *iq, const uint6
     if (!b || !iq || !rx_byte_offset || probe_blocks == 0) return RX_EINVAL;
     probe_blocks = std::min(probe_blocks, b->max_blocks);
     cudaSetDevice(b->device);
-    const TuneKey key = tune_key(b, b->device);
+    const TuneKey key = tune_key(b, b->device, probe_blocks);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
