@@ -182,3 +182,45 @@ def test_served_table3_stream_matches_oracle(form):
     assert np.array_equal(db, od)
     assert_states_equal(sb, os_)
     assert all(x.window_count == 0 and x.have_prev == 0 for x in hb)
+
+
+def test_autotune_keeps_a_shape_per_loop_set():
+    """The autotuner's cache holds a tile shape per loop set and probe length: a batch
+    with Table 3's loops on the same receivers as a tuned basic-loop batch is timed
+    anew (its probe time is returned), a second such batch takes the cached shape
+    without timing (-1), and a longer probe is timed anew; a run with the tuned
+    basic-loop shape is bit-exact with the oracle."""
+    recv = [synth.uniform_receiver(i, n_blocks=7, fs=4.092e6) for i in range(2)]
+    offs, total = batch_layout(recv)
+    buf = np.zeros(total, np.int8)
+    sigs = []
+    for r, o in zip(recv, offs):
+        iq = synth.generate_iq(r).numpy()
+        buf[int(o):int(o) + iq.size] = iq.reshape(-1)
+        sigs.append(iq)
+    dev = torch.from_numpy(buf).cuda()
+
+    def tuned(loop_set, probe):
+        descs = [rx.receiver_desc(r, 1, WINDOW, FLL) if loop_set else rx.receiver_desc(r) for r in recv]
+        b = rx.rx_batch_create(descs, 7)
+        try:
+            for i, r in enumerate(recv):
+                rx.rx_batch_set_channels(b, i, *synth.channel_arrays(r))
+            tiles, ms = rx.rx_batch_autotune(b, dev, offs, probe)
+            rx.rx_batch_run(b, dev, offs, 7, rx.RX_RUN_RESTART)
+            out = [(rx.rx_batch_read_dumps(b, i, len(r.channels), r.n_taps, 7 // r.integ_blocks),
+                    rx.rx_batch_read_state(b, i, len(r.channels))) for i, r in enumerate(recv)]
+        finally:
+            rx.rx_batch_destroy(b)
+        return tiles, ms, out
+
+    _, ms_basic, basic = tuned(0, 5)
+    _, ms_t3, _ = tuned(1, 5)
+    _, ms_again, _ = tuned(1, 5)
+    _, ms_longer, _ = tuned(1, 7)
+    assert ms_basic > 0 and ms_t3 > 0 and ms_longer > 0
+    assert ms_again == -1.0
+    for r, iq, (d, s) in zip(recv, sigs, basic):
+        od, os_ = oracle_run(r, iq, 7)
+        assert np.array_equal(d, od)
+        assert_states_equal(s, os_)
