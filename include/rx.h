@@ -364,7 +364,9 @@ rx_status rx_batch_run(rx_batch b, const int8_t *iq,
  * of Sec. 3.2-3.3 overlap acquisition of the next block with tracking of the
  * current one).  0, the default, takes sixteen chunks when the run's host
  * input is at least 64 MiB and one otherwise.  Every chunking gives the same dumps
- * and state. */
+ * and state.  Receivers that share a block size and sit equally spaced in the
+ * host buffer are copied as one strided copy per chunk (a row per receiver),
+ * which keeps the copy engine at its full rate; others as one copy each. */
 rx_status rx_batch_set_host_chunk(rx_batch b, uint32_t chunk_blocks);
 
 /* Block until the batch's stream is idle; report a device-side timeout. */
